@@ -1,0 +1,230 @@
+"""Seeded synthetic inputs shaped like the workloads of the paper and of its GPU-scale configs.
+
+This module only builds matrices and right-hand-side ingredients (exact solutions, random
+vectors).  It holds none of the method's arithmetic: b = A x* is computed by whichever side
+(the CUDA path or the CPU oracle) consumes the inputs.
+
+Matrices are CSR with int32 row pointers / column indices (columns strictly ascending in each
+row, diagonal always stored) and binary64 values; complex values are interleaved (re, im).
+A matrix is returned as the tuple (n, row_ptr, col, val) plus a flag for complex.
+
+Recipes (stand-ins for the SuiteSparse matrices mcfe/mpfe and dwg961b of Sec. 4, which are not
+available here):
+  convdiff2d  -k Lap(u) + v.grad(u) on the unit square, Dirichlet boundary eliminated, 5-point
+              first-order upwind, scaled by h^2, h = 1/(m+1), natural (x-fastest) ordering.
+              Cell Peclet Pe_d = |v_d| h / (2 k) per axis, so the row is
+              diag 4 + 2Pe_x + 2Pe_y, upwind neighbours -1 - 2Pe_d, downwind -1.
+  convdiff3d  same in 3-D with a cell-wise log-normal diffusivity k = exp(sigma g), g ~ N(0,1),
+              face diffusivity = harmonic mean of the two cells (the cell's own value at a
+              boundary face), velocity direction (1, 0.5, 0.25) normalised, one global cell
+              Peclet number Pe ~ U(pe_lo, pe_hi) per seeded instance measured against k = 1:
+              h v_d = 2 Pe vhat_d.  7-point, natural ordering.
+  helmholtz2d h^2 (-Lap - k^2 (1 - 0.5 i)) on the unit square, 5-point, Dirichlet eliminated.
+  random_sparse  n x n, K ~ U{kmin..kmax} entries per row (diagonal included) at distinct
+              uniform random columns, off-diagonals N(0,1), diagonal = (sum |off|) (1 + U(0, 0.2)),
+              a fraction of rows with the diagonal weakened by a factor.
+"""
+import math
+from decimal import Decimal, getcontext
+
+import numpy as np
+
+SEED_BASE = 2504_14498
+
+
+def _csr_from_rows(n, cols, vals):
+    """cols/vals: (n, k) arrays with -1 marking absent entries; columns ascending per row."""
+    mask = cols >= 0
+    counts = mask.sum(axis=1)
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=rp[1:])
+    ci = cols[mask].astype(np.int32)
+    if vals.ndim == 3:  # complex: (n, k, 2)
+        va = vals[mask].reshape(-1)
+    else:
+        va = vals[mask]
+    return rp.astype(np.int32), ci, np.ascontiguousarray(va, dtype=np.float64)
+
+
+def convdiff2d(m=64, pe=10.0, kappa=1.0, velocity=(1.0, 1.0)):
+    """Config 'plain method, small': 5-point upwind convection-diffusion on an m x m grid."""
+    n = m * m
+    vx, vy = velocity
+    vn = math.hypot(vx, vy)
+    # cell Peclet pe per component along the flow direction (1,1): h v_d / (2 kappa) = pe
+    pex = pe * abs(vx) / max(abs(vx), abs(vy)) if vn > 0 else 0.0
+    pey = pe * abs(vy) / max(abs(vx), abs(vy)) if vn > 0 else 0.0
+    idx = np.arange(n)
+    ix, iy = idx % m, idx // m
+    cols = np.full((n, 5), -1, dtype=np.int64)
+    vals = np.zeros((n, 5))
+    # order: south (i-m), west (i-1), centre, east (i+1), north (i+m)
+    up_x = -kappa - 2 * kappa * pex if vx >= 0 else -kappa
+    dn_x = -kappa if vx >= 0 else -kappa - 2 * kappa * pex
+    up_y = -kappa - 2 * kappa * pey if vy >= 0 else -kappa
+    dn_y = -kappa if vy >= 0 else -kappa - 2 * kappa * pey
+    diag = 4 * kappa + 2 * kappa * pex + 2 * kappa * pey
+    s = iy > 0
+    cols[s, 0] = idx[s] - m; vals[s, 0] = up_y
+    w_ = ix > 0
+    cols[w_, 1] = idx[w_] - 1; vals[w_, 1] = up_x
+    cols[:, 2] = idx; vals[:, 2] = diag
+    e = ix < m - 1
+    cols[e, 3] = idx[e] + 1; vals[e, 3] = dn_x
+    nn = iy < m - 1
+    cols[nn, 4] = idx[nn] + m; vals[nn, 4] = dn_y
+    rp, ci, va = _csr_from_rows(n, cols, vals)
+    return (n, rp, ci, va)
+
+
+def convdiff3d(m=128, sigma=1.0, pe_range=(1.0, 50.0), direction=(1.0, 0.5, 0.25), seed=SEED_BASE + 1):
+    """Config 'precision': 7-point upwind convection-diffusion with log-normal diffusivity."""
+    rng = np.random.default_rng(seed)
+    n = m ** 3
+    kap = np.exp(sigma * rng.standard_normal(n))
+    pe = float(rng.uniform(*pe_range))
+    d = np.asarray(direction, dtype=np.float64)
+    vh = d / np.linalg.norm(d)
+    hv = 2.0 * pe * vh  # h * v_d, measured against kappa = 1
+    idx = np.arange(n)
+    ix, iy, iz = idx % m, (idx // m) % m, idx // (m * m)
+    strides = (1, m, m * m)
+    coords = (ix, iy, iz)
+    cols = np.full((n, 7), -1, dtype=np.int64)
+    vals = np.zeros((n, 7))
+    diag = np.zeros(n)
+    # slots: 0: -m^2, 1: -m, 2: -1, 3: centre, 4: +1, 5: +m, 6: +m^2
+    for axis, (slot_lo, slot_hi) in enumerate(((2, 4), (1, 5), (0, 6))):
+        st, c = strides[axis], coords[axis]
+        has_lo, has_hi = c > 0, c < m - 1
+        k_lo = kap.copy()
+        k_lo[has_lo] = 2.0 / (1.0 / kap[has_lo] + 1.0 / kap[idx[has_lo] - st])
+        k_hi = kap.copy()
+        k_hi[has_hi] = 2.0 / (1.0 / kap[has_hi] + 1.0 / kap[idx[has_hi] + st])
+        diag += k_lo + k_hi + hv[axis]
+        cols[has_lo, slot_lo] = idx[has_lo] - st
+        vals[has_lo, slot_lo] = -k_lo[has_lo] - hv[axis]
+        cols[has_hi, slot_hi] = idx[has_hi] + st
+        vals[has_hi, slot_hi] = -k_hi[has_hi]
+    cols[:, 3] = idx
+    vals[:, 3] = diag
+    rp, ci, va = _csr_from_rows(n, cols, vals)
+    return (n, rp, ci, va), {"pe": pe, "sigma": sigma, "m": m}
+
+
+def helmholtz2d(m=1024, k=20 * math.pi, damping=0.5):
+    """Config 'complex': shifted-Laplacian Helmholtz, h^2(-Lap - k^2 (1 - i damping))."""
+    n = m * m
+    h = 1.0 / (m + 1)
+    kh2 = (k * h) ** 2
+    idx = np.arange(n)
+    ix, iy = idx % m, idx // m
+    cols = np.full((n, 5), -1, dtype=np.int64)
+    vals = np.zeros((n, 5, 2))
+    s = iy > 0
+    cols[s, 0] = idx[s] - m; vals[s, 0, 0] = -1.0
+    w_ = ix > 0
+    cols[w_, 1] = idx[w_] - 1; vals[w_, 1, 0] = -1.0
+    cols[:, 2] = idx; vals[:, 2, 0] = 4.0 - kh2; vals[:, 2, 1] = kh2 * damping
+    e = ix < m - 1
+    cols[e, 3] = idx[e] + 1; vals[e, 3, 0] = -1.0
+    nn = iy < m - 1
+    cols[nn, 4] = idx[nn] + m; vals[nn, 4, 0] = -1.0
+    rp, ci, va = _csr_from_rows(n, cols, vals)
+    return (n, rp, ci, va)
+
+
+def random_sparse(n, kmin=5, kmax=40, weak_frac=0.05, weak_factor=0.6, seed=SEED_BASE + 3, complex_=False):
+    """Nonsymmetric random sparse system (diagonally dominant except the weakened rows)."""
+    rng = np.random.default_rng(seed)
+    kmax = min(kmax, n)
+    kmin = min(kmin, kmax)
+    k = rng.integers(kmin, kmax + 1, size=n)
+    rows_c, rows_v = [], []
+    for i in range(n):
+        others = rng.choice(n - 1, size=k[i] - 1, replace=False)
+        others = others + (others >= i)
+        c = np.sort(np.concatenate([others, [i]]))
+        if complex_:
+            v = rng.standard_normal((k[i], 2))
+        else:
+            v = rng.standard_normal(k[i])
+        rows_c.append(c)
+        rows_v.append(v)
+    weak = rng.random(n) < weak_frac
+    grow = rng.uniform(0.0, 0.2, size=n)
+    rp = np.zeros(n + 1, dtype=np.int32)
+    rp[1:] = np.cumsum([len(c) for c in rows_c])
+    ci = np.concatenate(rows_c).astype(np.int32)
+    vals = []
+    for i in range(n):
+        c, v = rows_c[i], rows_v[i]
+        d = int(np.nonzero(c == i)[0][0])
+        if complex_:
+            off = np.abs(v[:, 0] + 1j * v[:, 1])
+            s = off.sum() - off[d]
+            v[d] = [s * (1 + grow[i]) * (weak_factor if weak[i] else 1.0), 0.0]
+        else:
+            s = np.abs(v).sum() - abs(v[d])
+            v[d] = s * (1 + grow[i]) * (weak_factor if weak[i] else 1.0)
+        vals.append(v.reshape(-1))
+    return (n, rp, ci, np.concatenate(vals).astype(np.float64))
+
+
+def tridiag(n, lo, di, up):
+    """Tridiagonal matrix with constant (or per-row array) diagonals."""
+    lo = np.broadcast_to(np.asarray(lo, dtype=np.float64), (n,))
+    di = np.broadcast_to(np.asarray(di, dtype=np.float64), (n,))
+    up = np.broadcast_to(np.asarray(up, dtype=np.float64), (n,))
+    idx = np.arange(n)
+    cols = np.full((n, 3), -1, dtype=np.int64)
+    vals = np.zeros((n, 3))
+    cols[1:, 0] = idx[1:] - 1; vals[1:, 0] = lo[1:]
+    cols[:, 1] = idx; vals[:, 1] = di
+    cols[:-1, 2] = idx[:-1] + 1; vals[:-1, 2] = up[:-1]
+    rp, ci, va = _csr_from_rows(n, cols, vals)
+    return (n, rp, ci, va)
+
+
+def ones(n, w, c=1):
+    """x* = ones as an n-vector of w-component numbers (c = 2: real part 1, imaginary 0)."""
+    x = np.zeros((n, c, w))
+    x[:, 0, 0] = 1.0
+    return x.reshape(-1)
+
+
+def _split_decimal(d, w):
+    comps = []
+    for _ in range(w):
+        f = float(d)
+        comps.append(f)
+        d = d - Decimal(f)
+    return comps
+
+
+def paper_xstar(n, w, complex_=False):
+    """Exact solution of Sec. 4: x = sqrt(2) [1..n] (real) or sqrt(2 + 3i) [1..n] (complex),
+    each entry rounded greedily to w binary64 components from a 100-digit decimal value."""
+    getcontext().prec = 100
+    if not complex_:
+        s = Decimal(2).sqrt()
+        return np.array([c for k in range(1, n + 1) for c in _split_decimal(s * k, w)])
+    # principal sqrt(2 + 3i) = a + b i, a = sqrt((|z| + 2)/2), b = sqrt((|z| - 2)/2)
+    mod = Decimal(13).sqrt()
+    a = ((mod + 2) / 2).sqrt()
+    b = ((mod - 2) / 2).sqrt()
+    out = []
+    for k in range(1, n + 1):
+        out += _split_decimal(a * k, w) + _split_decimal(b * k, w)
+    return np.array(out)
+
+
+def random_vector(n, w, c=1, seed=SEED_BASE + 7, scale=1.0):
+    """Random vector, leading components N(0, scale^2), lower components a random fraction of
+    an ulp so that every component is in use (w > 1)."""
+    rng = np.random.default_rng(seed)
+    v = np.zeros((n, c, w))
+    v[:, :, 0] = scale * rng.standard_normal((n, c))
+    for k in range(1, w):
+        v[:, :, k] = v[:, :, k - 1] * (2.0 ** -53) * rng.uniform(-0.5, 0.5, size=(n, c))
+    return v.reshape(-1)

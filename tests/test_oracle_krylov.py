@@ -1,0 +1,162 @@
+"""Pins for the oracle's Krylov solvers (Algorithm 3 BiCG; CGS, BiCGSTAB, GPBiCG as read in
+Sec. 3) against mathematics that does not depend on the oracle:
+  * finite termination: on tiny nonsymmetric systems every method reaches the solution within n
+    iterations (Krylov dimension), checked in QD where rounding is far below the test;
+  * manufactured solutions b = A x* (x* = ones, and the paper's x = sqrt(2)[1..n] of Sec. 4);
+  * reductions: GPBiCG with eta forced to 0 follows BiCGSTAB; BiCG without preconditioner on a
+    symmetric positive definite matrix follows conjugate gradients (scipy's cg);
+  * M = A (ILU(0) exact, exactly representable factors): convergence in one iteration;
+  * statuses: breakdown, NaN in b, maximum iterations; with / without ILU(0) (the qualitative
+    observation of Sec. 4 that the unpreconditioned methods need far more iterations).
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import oracle
+from paper_2504_14498_gb300 import inputs
+
+METHODS = ["bicg", "cgs", "bicgstab", "gpbicg"]
+
+
+def _rhs(A, x, w, c=1):
+    return oracle.spmv(A, x, w, c)
+
+
+def _hi(v, n, w, c=1):
+    v = v.reshape(n, c, w)
+    return v[:, 0, 0] + (1j * v[:, 1, 0] if c == 2 else 0)
+
+
+@pytest.mark.parametrize("method", METHODS)
+@pytest.mark.parametrize("c", [1, 2])
+def test_finite_termination(method, c):
+    n = 7
+    A = inputs.random_sparse(n, 3, 6, seed=100 + c, complex_=(c == 2), weak_frac=0.0)
+    w = 4
+    xs = inputs.random_vector(n, w, c, seed=4)
+    b = _rhs(A, xs, w, c)
+    out = oracle.krylov(method, A, b, w, c, ilu="none", tol_rel=1e-45, maxit=n)
+    assert out["status"] == "OK", out["status"]
+    assert out["iters"] <= n
+    err = np.max(np.abs(_hi(out["x"], n, w, c) - _hi(xs, n, w, c)))
+    assert err < 1e-40
+
+
+@pytest.mark.parametrize("method", METHODS)
+@pytest.mark.parametrize("ilu", ["fp64", "fp32", "bf16"])
+def test_manufactured_convdiff_dd(method, ilu):
+    m = 12
+    A = inputs.convdiff2d(m, pe=10.0)
+    n = A[0]
+    w = 2
+    xs = inputs.ones(n, w)
+    b = _rhs(A, xs, w)
+    out = oracle.krylov(method, A, b, w, ilu=ilu, tol_rel=1e-25, maxit=400)
+    assert out["status"] == "OK"
+    assert out["relres_true"] < 1e-24
+    assert np.max(np.abs(out["x"].reshape(n, w)[:, 0] - 1.0)) < 1e-20
+    # recursive residual history is what the stopping rule saw
+    assert out["hist"][-1] < 1e-25 * out["hist"][0]
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_manufactured_paper_xstar_complex_qd(method):
+    """Sec. 4 exact solution for complex systems, x = sqrt(2+3i) [1..n], QD vectors."""
+    A = inputs.helmholtz2d(6, k=4.0)
+    n, w, c = A[0], 4, 2
+    xs = inputs.paper_xstar(n, w, complex_=True)
+    b = _rhs(A, xs, w, c)
+    out = oracle.krylov(method, A, b, w, c, ilu="fp64", tol_rel=1e-55, maxit=300)
+    assert out["status"] == "OK"
+    rel = np.max(np.abs(_hi(out["x"], n, w, c) - _hi(xs, n, w, c))) / np.max(np.abs(_hi(xs, n, w, c)))
+    assert rel < 1e-15  # leading components agree to binary64 rounding
+    assert out["relres_true"] < 1e-54
+
+
+def test_gpbicg_eta0_is_bicgstab():
+    A = inputs.convdiff2d(10, pe=5.0)
+    n, w = A[0], 2
+    b = _rhs(A, inputs.ones(n, w), w)
+    g = oracle.krylov("gpbicg", A, b, w, ilu="fp64", tol_rel=1e-25, maxit=300, force_eta0=True)
+    s = oracle.krylov("bicgstab", A, b, w, ilu="fp64", tol_rel=1e-25, maxit=300)
+    k = min(len(g["hist"]), len(s["hist"]), 12)
+    np.testing.assert_allclose(g["hist"][:k], s["hist"][:k], rtol=1e-12)
+    assert abs(g["iters"] - s["iters"]) <= 1
+    # without the forcing, GPBiCG is a different method
+    full = oracle.krylov("gpbicg", A, b, w, ilu="fp64", tol_rel=1e-25, maxit=300)
+    assert not np.allclose(full["hist"][2:k], s["hist"][2:k], rtol=1e-6)
+
+
+def test_bicg_is_cg_on_spd():
+    m = 10
+    A = inputs.convdiff2d(m, pe=0.0)  # pure diffusion: symmetric positive definite
+    n, rp, ci, val = A
+    S = sp.csr_matrix((val, ci, rp), shape=(n, n))
+    bb = np.sin(np.arange(n) + 1.0)
+    res = []
+    spla.cg(S, bb, rtol=1e-30, maxiter=12, callback=lambda xk: res.append(np.linalg.norm(bb - S @ xk)))
+    out = oracle.krylov("bicg", A, bb.copy(), 1, ilu="none", tol_rel=1e-30, maxit=12)
+    k = min(len(res), 10)
+    np.testing.assert_allclose(out["hist"][1:k + 1], res[:k], rtol=1e-8)
+
+
+def _exact_lu_tridiag(n):
+    """A = L U with L unit lower bidiagonal (sub-diagonal 1/2) and U upper bidiagonal (diagonal 4,
+    super-diagonal -1): all entries of A and of its ILU(0) = LU factors are exact binary64."""
+    lo = np.full(n, 0.5 * 4.0)  # l_{i,i-1} u_{i-1,i-1} = 0.5 * 4
+    di = np.full(n, 4.0)
+    di[1:] = 4.0 + 0.5 * -1.0   # l u_{i-1,i} + u_ii
+    up = np.full(n, -1.0)
+    return inputs.tridiag(n, lo, di, up)
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_one_iteration_when_M_equals_A(method):
+    n = 50
+    A = _exact_lu_tridiag(n)
+    st, fac, _ = oracle.ilu0(A, "fp64")
+    assert st == 0
+    rp, ci = A[1], A[2]
+    for i in range(n):  # factors are exactly L (0.5) and U (4, -1)
+        for p in range(rp[i], rp[i + 1]):
+            expect = 0.5 if ci[p] < i else (4.0 if ci[p] == i else -1.0)
+            assert fac[p] == expect
+    w = 2
+    b = _rhs(A, inputs.paper_xstar(n, w), w)
+    out = oracle.krylov(method, A, b, w, ilu="fp64", tol_rel=1e-28, maxit=5)
+    assert out["status"] == "OK" and out["iters"] == 1
+
+
+def test_breakdown_status():
+    # A = [[0,1],[1,0]], b = e1: <r~, A r> = 0 at the first step
+    A = (2, np.array([0, 2, 4], np.int32), np.array([0, 1, 0, 1], np.int32), np.array([0.0, 1.0, 1.0, 0.0]))
+    b = np.array([1.0, 0.0, 0.0, 0.0])
+    for m in METHODS:
+        out = oracle.krylov(m, A, b, 2, ilu="none", maxit=10)
+        assert out["status"] == "BREAKDOWN", m
+
+
+def test_nan_and_maxit():
+    A = inputs.convdiff2d(8, pe=10.0)
+    n, w = A[0], 2
+    b = _rhs(A, inputs.ones(n, w), w)
+    bn = b.copy()
+    bn[5 * w] = np.nan
+    assert oracle.krylov("bicgstab", A, bn, w, ilu="fp64")["status"] == "NAN"
+    out = oracle.krylov("bicgstab", A, b, w, ilu="none", maxit=3)
+    assert out["status"] == "MAXIT" and out["iters"] == 3
+
+
+def test_ilu_needed_paper_setting():
+    """Sec. 4 setting (eps_r = 1e-13, eps_a = 1e-100, maxit = 3n) on the config-1 stand-in:
+    with ILU(0) each method converges, and needs far fewer iterations than without it."""
+    A = inputs.convdiff2d(24, pe=10.0)
+    n, w = A[0], 2
+    b = _rhs(A, inputs.paper_xstar(n, w), w)
+    for m in METHODS:
+        pre = oracle.krylov(m, A, b, w, ilu="fp64", tol_rel=1e-13, tol_abs=1e-100, maxit=3 * n)
+        non = oracle.krylov(m, A, b, w, ilu="none", tol_rel=1e-13, tol_abs=1e-100, maxit=3 * n)
+        assert pre["status"] == "OK"
+        assert 3 * pre["iters"] < non["iters"], (m, pre["iters"], non["iters"])
