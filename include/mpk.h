@@ -1,0 +1,163 @@
+/*
+ * mpk.h -- C ABI of the GB300 (sm_103a) library for mixed-precision ILU(0)-preconditioned
+ * multi-component Krylov solvers (Kouya, arXiv 2504.14498).
+ *
+ * Problem (Sec. 3, Eq. 1): solve A x = b with A an n x n nonsingular real or complex sparse
+ * matrix in CSR ("CRS") storage with binary64 entries (Sec. 3, last paragraph: the matrices
+ * are binary64, the vectors multi-component).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named *_dev are DEVICE pointers (e.g. torch CUDA tensors), owned by the caller,
+ *     16-byte aligned, and must stay valid until the stream work that uses them completes.
+ *     Pointers named *_host are host pointers.  `stream` is a cudaStream_t (NULL = default
+ *     stream); every call is ordered on it.
+ *   - Multi-component numbers: w = 1 (D), 2 (DD), 3 (TD), 4 (QD) binary64 components,
+ *     leading component first (Sec. 2).  A real entry is w doubles, a complex entry 2w doubles
+ *     (real part then imaginary part).  A vector of n entries is n*c*w contiguous doubles,
+ *     c = 1 (real) or 2 (complex).
+ *   - CSR: row_ptr int32[n+1] (row_ptr[0] = 0, nondecreasing), col_idx int32[nnz] strictly
+ *     ascending within each row, val double[nnz] (real) or double[2*nnz] interleaved (re, im)
+ *     (complex).  The diagonal must be stored for ILU(0).
+ *   - Return value: an mpk_status.  On failure mpk_last_error() returns a message (per host
+ *     thread).  Arguments are validated on the host before any launch: invalid pointers,
+ *     sizes or enum values give MPK_INVALID_ARG and launch nothing.
+ *   - Errors found on the device (zero pivot, a bounded device wait that ran out) are reported
+ *     through the status returned by the call that waits for them (mpk_ilu0_factor,
+ *     mpk_krylov_solve); device waits are bounded (about one second each) and never hang.
+ *
+ * Arithmetic: see paper_2504_14498_gb300/csrc/mp.cuh (DD: Joldes-Muller-Popescu double-word
+ * algorithms; TD/QD: exact evaluation then greedy rounding to w components).
+ */
+#ifndef MPK_H
+#define MPK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MPK_OK = 0,
+  MPK_MAXIT = 1,          /* iteration limit reached without convergence                   */
+  MPK_BREAKDOWN = 2,      /* an exactly zero denominator (rho, <r~,v>, LS determinant, ...)  */
+  MPK_ZERO_PIVOT = 3,     /* ILU(0): U_kk = 0 (Algorithm 1 tests U_kk != 0); fail_row = k    */
+  MPK_MISSING_DIAG = 4,   /* ILU(0): a row without a stored diagonal; fail_row = that row     */
+  MPK_NAN = 5,            /* a residual norm became NaN (e.g. NaN in b)                      */
+  MPK_INVALID_ARG = 6,    /* bad pointer / size / enum / unsorted columns                    */
+  MPK_CUDA_ERROR = 7,     /* a CUDA runtime call failed                                      */
+  MPK_TIMEOUT = 8,        /* a bounded device wait ran out (never expected)                  */
+  MPK_NOT_IMPLEMENTED = 9
+} mpk_status;
+
+/* Precision of the ILU(0) factor and of the substitutions (Sec. 3; Sec. 4 "_d" variants). */
+typedef enum {
+  MPK_ILU_NONE = -1, /* no preconditioner, M = I                                            */
+  MPK_ILU_FP64 = 0,  /* binary64 factor; substitutions multiply binary64 factor entries with
+                        the multi-component vector and accumulate in it (paper's "_d")      */
+  MPK_ILU_FP32 = 1,  /* A rounded to binary32, factor and substitutions in binary32: the
+                        right-hand side is scaled by 2^-e (e = exponent of its largest entry),
+                        rounded to binary32, solved, widened and scaled back                 */
+  MPK_ILU_BF16 = 2   /* binary32 factorisation, factor stored as bfloat16 (round to nearest
+                        even); substitutions as MPK_ILU_FP32                                 */
+} mpk_ilu_prec;
+
+/* Product-type Krylov methods (Sec. 3): BiCG is Algorithm 3; CGS, BiCGSTAB and GPBiCG are the
+ * standard right-preconditioned forms in which r is the residual b - A x of the original
+ * system (the paper names them without a listing). */
+typedef enum { MPK_BICG = 0, MPK_CGS = 1, MPK_BICGSTAB = 2, MPK_GPBICG = 3 } mpk_method;
+
+typedef struct {
+  int32_t n;               /* rows = columns, n >= 1                                          */
+  int32_t nnz;             /* row_ptr[n]                                                       */
+  const int32_t* row_ptr;  /* device, n+1                                                      */
+  const int32_t* col_idx;  /* device, nnz                                                      */
+  const double* val;       /* device, nnz (real) or 2*nnz (complex, interleaved re,im)         */
+  int32_t is_complex;      /* 0 real, 1 complex                                                */
+} mpk_csr;
+
+/* Opaque ILU(0) handle: factor values on A's pattern, a copy of the pattern, the conjugate
+ * transposed factor (built on first use by BiCG's M^H solve) and the flags of the
+ * dependency-driven substitutions.  One solve at a time per handle. */
+typedef struct mpk_ilu mpk_ilu;
+
+typedef struct {
+  double tol_rel;          /* eps_r of the stopping rule ||r|| < eps_r ||r0|| + eps_a (Alg. 3) */
+  double tol_abs;          /* eps_a                                                            */
+  int32_t maxit;           /* iteration limit (Sec. 4 uses 3n)                                  */
+  int32_t check_every;     /* iterations queued between host checks of the device "done" flag */
+  int32_t flags;           /* bit 0: GPBiCG with eta forced to 0 (reduces to BiCGSTAB)          */
+  int32_t reserved;
+  double* hist_dev;        /* nullable device array of maxit+1 doubles: leading component of
+                              ||r_k||_2, k = 0..iters                                            */
+} mpk_opts;
+
+typedef struct {
+  int32_t status;          /* mpk_status of the solve                                           */
+  int32_t iters;           /* iterations performed                                              */
+  int32_t fail_row;        /* ILU failures: the row; otherwise -1                               */
+  int32_t reserved;
+  double res0;             /* ||b - A x0|| (leading component)                                  */
+  double relres_rec;       /* ||r_k|| / ||r0|| of the recursively updated residual               */
+  double relres_true;      /* ||b - A x_k|| / ||r0|| recomputed at the end in the vector format */
+  float ms_solve;          /* device time of the solve (CUDA events on `stream`)                */
+  float reserved2;
+} mpk_info;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int mpk_version(void);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* mpk_last_error(void);
+
+/* y = A x (Sec. 3 "mixed-precision SpMV": binary64 A, w-component vectors).  Row i is
+ * accumulated in CSR order from 0: y_i = (((0 + a_i,j1 x_j1) + a_i,j2 x_j2) + ...), each
+ * product and sum in w-component arithmetic.  x_dev, y_dev: n*c*w doubles (c from A), must
+ * not overlap. */
+int mpk_spmv_mp(const mpk_csr* A, int w, const double* x_dev, double* y_dev, void* stream);
+
+/* out_dev[0 .. c*w) = <a, b> = sum_i conj(a_i) b_i in w-component arithmetic (Alg. 3 inner
+ * products), reduced in a fixed order (deterministic for a given n). */
+int mpk_dot(int n, int is_complex, int w, const double* a_dev, const double* b_dev, double* out_dev,
+            void* stream);
+
+/* ILU(0) of A (Algorithm 1; the "!= 0" tests read as membership in A's stored pattern; the
+ * update A_ij -= L_ik U_kj is one fused multiply-add; a zero pivot is an error instead of
+ * being skipped).  Rows are factored by a dependency-driven device kernel; the result equals
+ * the sequential KIJ order bit for bit.  On success *out receives a new handle (free with
+ * mpk_ilu0_destroy); on failure *out is NULL and *fail_row (if not NULL) the failing row.
+ * The call synchronises `stream` to read the device status. */
+int mpk_ilu0_factor(const mpk_csr* A, int prec, mpk_ilu** out, int* fail_row, void* stream);
+
+/* Copy the factor values (nnz*c doubles on A's pattern: strict lower part = L~ without its
+ * unit diagonal, upper part with diagonal = U~; binary32/bfloat16 values widened) to
+ * out_dev. */
+int mpk_ilu0_values(const mpk_ilu* M, double* out_dev, void* stream);
+
+/* Precision the handle was built with (mpk_ilu_prec), or -2 for a NULL handle. */
+int mpk_ilu0_prec(const mpk_ilu* M);
+
+void mpk_ilu0_destroy(mpk_ilu* M);
+
+/* z = M^-1 r (trans = 0) or z = M^-H r (trans = 1) with M = L~U~ (Algorithm 2; the M^H solve
+ * of Algorithm 3 is U~^H w = r then L~^H z = w).  r_dev, z_dev: n*c*w doubles, distinct. */
+int mpk_precond_apply(const mpk_ilu* M, int w, int trans, const double* r_dev, double* z_dev, void* stream);
+
+/* Solve A x = b with `method` in w-component arithmetic, preconditioned by M (NULL = none).
+ * x_dev holds x0 on entry (Alg. 3 starts from a given x0) and the last iterate on return, for
+ * every status.  Work vectors are allocated stream-ordered (cudaMallocAsync) and freed before
+ * return.  The call synchronises `stream`.  info is filled in every case. */
+int mpk_krylov_solve(int method, int w, const mpk_csr* A, const mpk_ilu* M, const double* b_dev, double* x_dev,
+                     const mpk_opts* opts, mpk_info* info, void* stream);
+
+/* End-to-end convenience: host CSR, host b and x (x0 in, solution out).  Copies A and b to
+ * the device, builds ILU(0) in `prec` (MPK_ILU_NONE: none), solves, copies x back and frees
+ * everything.  info->ms_solve covers the whole call. */
+int mpk_solve_host(int method, int w, int prec, int32_t n, int32_t is_complex, const int32_t* row_ptr_host,
+                   const int32_t* col_idx_host, const double* val_host, const double* b_host, double* x_host,
+                   const mpk_opts* opts, mpk_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPK_H */

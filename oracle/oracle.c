@@ -18,6 +18,8 @@
  *                                             standard right-preconditioned forms (Sonneveld
  *                                             1989; van der Vorst 1992; Zhang 1997)
  *   stopping rule ||r|| < eps_r ||r0|| + eps_a  Algorithm 3 and Sec. 4
+ *   inner products <a,b> = sum conj(a_i) b_i  Algorithm 3; the summation order (not given in the
+ *                                             paper) is fixed below: leaves of 16, pairwise tree
  *
  * Arithmetic definitions used here (the paper does not say which variants its library uses):
  *   DD  : Joldes, Muller, Popescu, "Tight and rigorous error bounds for basic building blocks
@@ -429,11 +431,28 @@ void orc_spmv(int n, const int *rp, const int *ci, const double *val, int c, int
   ctx t = {w, c};
   spmv(n, rp, ci, val, t, x, y);
 }
+/* The summation order of an inner product is fixed (the paper leaves it open): the products
+ * p_i = conj(a_i) b_i are grouped in leaves of DOT_LEAF consecutive indices, each leaf summed
+ * left to right starting from its first product, and the leaf sums s_0..s_{m-1} combined by a
+ * stride-doubling pairwise tree: for d = 1, 2, 4, ...: s_j := s_j + s_{j+d} for every j that is
+ * a multiple of 2d with j + d < m.  The result is s_0 (0 for n = 0). */
+#define DOT_LEAF 16
 static num dot(int n, ctx t, const double *a, const double *b) {
-  int s = t.c * t.w, i;
-  num acc = n_zero();
-  for (i = 0; i < n; ++i) acc = n_add(acc, n_mul_conj(n_load(a + (size_t)i * s, t), n_load(b + (size_t)i * s, t), t), t);
-  return acc;
+  int s = t.c * t.w, i, j, d, m = (n + DOT_LEAF - 1) / DOT_LEAF;
+  num *leaf, res;
+  if (n <= 0) return n_zero();
+  leaf = (num *)malloc(sizeof(num) * (size_t)m);
+  for (j = 0; j < m; ++j) {
+    int i0 = j * DOT_LEAF, i1 = i0 + DOT_LEAF < n ? i0 + DOT_LEAF : n;
+    num acc = n_mul_conj(n_load(a + (size_t)i0 * s, t), n_load(b + (size_t)i0 * s, t), t);
+    for (i = i0 + 1; i < i1; ++i) acc = n_add(acc, n_mul_conj(n_load(a + (size_t)i * s, t), n_load(b + (size_t)i * s, t), t), t);
+    leaf[j] = acc;
+  }
+  for (d = 1; d < m; d *= 2)
+    for (j = 0; j + d < m; j += 2 * d) leaf[j] = n_add(leaf[j], leaf[j + d], t);
+  res = leaf[0];
+  free(leaf);
+  return res;
 }
 void orc_dot(int n, int c, int w, const double *a, const double *b, double *out) {
   ctx t = {w, c};

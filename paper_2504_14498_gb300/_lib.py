@@ -1,0 +1,200 @@
+"""ctypes binding of libmpk.so (include/mpk.h).  Argument marshalling only: every step of the
+solver runs in the library's CUDA kernels; torch supplies device memory and the stream.
+
+There is no fallback: if libmpk.so is missing or cannot be loaded, every call raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmpk.so")
+
+STATUS = {0: "OK", 1: "MAXIT", 2: "BREAKDOWN", 3: "ZERO_PIVOT", 4: "MISSING_DIAG", 5: "NAN", 6: "INVALID_ARG",
+          7: "CUDA_ERROR", 8: "TIMEOUT", 9: "NOT_IMPLEMENTED"}
+METHODS = {"bicg": 0, "cgs": 1, "bicgstab": 2, "gpbicg": 3}
+ILUS = {"none": -1, "fp64": 0, "fp32": 1, "bf16": 2}
+
+
+class MpkError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = STATUS.get(status, status)
+
+
+class CsrDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int32), ("row_ptr", ctypes.c_void_p),
+                ("col_idx", ctypes.c_void_p), ("val", ctypes.c_void_p), ("is_complex", ctypes.c_int32)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("tol_rel", ctypes.c_double), ("tol_abs", ctypes.c_double), ("maxit", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("hist_dev", ctypes.c_void_p)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("fail_row", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("res0", ctypes.c_double), ("relres_rec", ctypes.c_double),
+                ("relres_true", ctypes.c_double), ("ms_solve", ctypes.c_float), ("reserved2", ctypes.c_float)]
+
+
+_lib = None
+
+# (name, restype, argtypes) of every entry point declared in include/mpk.h
+_VP, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+SIGNATURES = [
+    ("mpk_version", _I, []),
+    ("mpk_last_error", ctypes.c_char_p, []),
+    ("mpk_spmv_mp", _I, [ctypes.POINTER(CsrDesc), _I, _VP, _VP, _VP]),
+    ("mpk_dot", _I, [_I, _I, _I, _VP, _VP, _VP, _VP]),
+    ("mpk_ilu0_factor", _I, [ctypes.POINTER(CsrDesc), _I, ctypes.POINTER(_VP), ctypes.POINTER(_I), _VP]),
+    ("mpk_ilu0_values", _I, [_VP, _VP, _VP]),
+    ("mpk_ilu0_prec", _I, [_VP]),
+    ("mpk_ilu0_destroy", None, [_VP]),
+    ("mpk_precond_apply", _I, [_VP, _I, _I, _VP, _VP, _VP]),
+    ("mpk_krylov_solve", _I, [_I, _I, ctypes.POINTER(CsrDesc), _VP, _VP, _VP, ctypes.POINTER(Opts),
+                              ctypes.POINTER(Info), _VP]),
+    ("mpk_solve_host", _I, [_I, _I, _I, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP,
+                            ctypes.POINTER(Opts), ctypes.POINTER(Info)]),
+]
+
+
+def lib():
+    """Load libmpk.so (built by paper_2504_14498_gb300.build); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libmpk.so is not built (run paper_2504_14498_gb300.build.build()); "
+                               "there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st):
+    if st != 0:
+        raise MpkError(st, lib().mpk_last_error().decode())
+    return st
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Matrix:
+    """Device CSR matrix (torch tensors) with the C descriptor."""
+
+    def __init__(self, n, row_ptr, col_idx, val, is_complex=False, device="cuda"):
+        self.n = int(n)
+        self.row_ptr = torch.as_tensor(np.asarray(row_ptr, dtype=np.int32), device=device)
+        self.col_idx = torch.as_tensor(np.asarray(col_idx, dtype=np.int32), device=device)
+        self.val = torch.as_tensor(np.asarray(val, dtype=np.float64), device=device)
+        self.is_complex = bool(is_complex)
+        self.nnz = int(self.col_idx.numel())
+        self.cp = 2 if is_complex else 1
+        self.desc = CsrDesc(self.n, self.nnz, self.row_ptr.data_ptr(), self.col_idx.data_ptr(),
+                            self.val.data_ptr(), int(self.is_complex))
+
+    @classmethod
+    def from_tuple(cls, A, is_complex=False, device="cuda"):
+        n, rp, ci, val = A
+        return cls(n, rp, ci, val, is_complex, device)
+
+
+def spmv_mp(A: Matrix, x: torch.Tensor, w: int, y: torch.Tensor = None) -> torch.Tensor:
+    """y = A x with w-component vectors (n*c*w doubles)."""
+    if y is None:
+        y = torch.empty(A.n * A.cp * w, dtype=torch.float64, device=x.device)
+    _check(lib().mpk_spmv_mp(ctypes.byref(A.desc), w, _ptr(x), _ptr(y), _stream()))
+    return y
+
+
+def dot(a: torch.Tensor, b: torch.Tensor, n: int, w: int, is_complex=False) -> torch.Tensor:
+    """<a, b> = sum conj(a_i) b_i; returns a device tensor of c*w doubles."""
+    out = torch.empty((2 if is_complex else 1) * w, dtype=torch.float64, device=a.device)
+    _check(lib().mpk_dot(n, int(is_complex), w, _ptr(a), _ptr(b), _ptr(out), _stream()))
+    return out
+
+
+class ILU0:
+    """ILU(0) handle (Algorithm 1) in 'fp64', 'fp32' or 'bf16'."""
+
+    def __init__(self, A: Matrix, prec="fp64"):
+        self.A = A
+        self.prec = prec
+        h = ctypes.c_void_p()
+        fr = ctypes.c_int(-1)
+        st = lib().mpk_ilu0_factor(ctypes.byref(A.desc), ILUS[prec], ctypes.byref(h), ctypes.byref(fr), _stream())
+        self.fail_row = fr.value
+        if st != 0:
+            raise MpkError(st, lib().mpk_last_error().decode() + " (row %d)" % fr.value)
+        self.handle = h
+
+    def values(self) -> torch.Tensor:
+        out = torch.empty(self.A.nnz * self.A.cp, dtype=torch.float64, device="cuda")
+        _check(lib().mpk_ilu0_values(self.handle, _ptr(out), _stream()))
+        return out
+
+    def apply(self, r: torch.Tensor, w: int, trans=False, z: torch.Tensor = None) -> torch.Tensor:
+        if z is None:
+            z = torch.empty_like(r)
+        _check(lib().mpk_precond_apply(self.handle, w, int(trans), _ptr(r), _ptr(z), _stream()))
+        return z
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().mpk_ilu0_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def krylov_solve(method, w, A: Matrix, M: ILU0, b: torch.Tensor, x0: torch.Tensor = None, tol_rel=1e-25,
+                 tol_abs=0.0, maxit=1000, check_every=25, history=True, force_eta0=False):
+    """Solve A x = b; returns dict(status, iters, x, hist, res0, relres_rec, relres_true, ms)."""
+    x = torch.zeros_like(b) if x0 is None else x0.clone()
+    hist = torch.full((maxit + 1,), float("nan"), dtype=torch.float64, device=b.device) if history else None
+    opts = Opts(float(tol_rel), float(tol_abs), int(maxit), int(check_every), 1 if force_eta0 else 0, 0,
+                hist.data_ptr() if history else None)
+    info = Info()
+    st = lib().mpk_krylov_solve(METHODS[method], w, ctypes.byref(A.desc), M.handle if M is not None else None,
+                                _ptr(b), _ptr(x), ctypes.byref(opts), ctypes.byref(info), _stream())
+    if st not in (0, 1, 2, 5):
+        raise MpkError(st, lib().mpk_last_error().decode())
+    h = hist[: info.iters + 1].cpu().numpy() if history else None
+    return {"status": STATUS[info.status], "iters": info.iters, "x": x, "hist": h, "res0": info.res0,
+            "relres_rec": info.relres_rec, "relres_true": info.relres_true, "ms": info.ms_solve}
+
+
+def solve_host(method, w, prec, A_tuple, b: np.ndarray, x0: np.ndarray = None, is_complex=False, tol_rel=1e-25,
+               tol_abs=0.0, maxit=1000, check_every=25):
+    """End to end from host arrays: H2D copies, ILU(0), solve, D2H of x inside one C call."""
+    n, rp, ci, val = A_tuple
+    rp = np.ascontiguousarray(rp, dtype=np.int32)
+    ci = np.ascontiguousarray(ci, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros_like(b) if x0 is None else np.ascontiguousarray(x0, dtype=np.float64).copy()
+    opts = Opts(float(tol_rel), float(tol_abs), int(maxit), int(check_every), 0, 0, None)
+    info = Info()
+    st = lib().mpk_solve_host(METHODS[method], w, ILUS[prec], n, int(is_complex), rp.ctypes.data, ci.ctypes.data,
+                              val.ctypes.data, b.ctypes.data, x.ctypes.data, ctypes.byref(opts), ctypes.byref(info))
+    if st not in (0, 1, 2, 5):
+        raise MpkError(st, lib().mpk_last_error().decode())
+    return {"status": STATUS[info.status], "iters": info.iters, "x": x, "relres_true": info.relres_true,
+            "ms": info.ms_solve}

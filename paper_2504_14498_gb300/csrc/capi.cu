@@ -1,0 +1,84 @@
+// capi.cu -- library-wide helpers and the stateless C-ABI entry points (SpMV, inner product).
+#include <string>
+
+#include "internal.h"
+
+namespace mpk {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+int fail(int status, const std::string& msg) {
+  g_last_error = msg;
+  return status;
+}
+
+int sm_count() {
+  static int count = [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) return 1;
+    return v;
+  }();
+  return count;
+}
+
+const Ops* ops_w1(int cp);
+const Ops* ops_w2(int cp);
+const Ops* ops_w3(int cp);
+const Ops* ops_w4(int cp);
+
+const Ops* get_ops(int w, int cp) {
+  if (cp != 1 && cp != 2) return nullptr;
+  switch (w) {
+    case 1: return ops_w1(cp);
+    case 2: return ops_w2(cp);
+    case 3: return ops_w3(cp);
+    case 4: return ops_w4(cp);
+    default: return nullptr;
+  }
+}
+
+}  // namespace mpk
+
+using namespace mpk;
+
+extern "C" int mpk_version(void) { return 100; }
+
+extern "C" const char* mpk_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int mpk_spmv_mp(const mpk_csr* A, int w, const double* x_dev, double* y_dev, void* stream) {
+  if (A == nullptr || x_dev == nullptr || y_dev == nullptr || x_dev == y_dev)
+    return fail(MPK_INVALID_ARG, "null or aliased argument");
+  if (A->n < 1 || A->nnz < 0 || A->row_ptr == nullptr || (A->nnz > 0 && (A->col_idx == nullptr || A->val == nullptr)))
+    return fail(MPK_INVALID_ARG, "invalid CSR descriptor");
+  if (A->is_complex != 0 && A->is_complex != 1) return fail(MPK_INVALID_ARG, "is_complex must be 0 or 1");
+  if (w < 1 || w > 4) return fail(MPK_INVALID_ARG, "w must be 1..4");
+  const Ops* o = get_ops(w, A->is_complex ? 2 : 1);
+  Csr c{A->n, A->nnz, A->row_ptr, A->col_idx, A->val, A->is_complex};
+  o->spmv(c, x_dev, y_dev, nullptr, nullptr, (cudaStream_t)stream);
+  MPK_CUDA(cudaGetLastError());
+  return MPK_OK;
+}
+
+extern "C" int mpk_dot(int n, int is_complex, int w, const double* a_dev, const double* b_dev, double* out_dev,
+                       void* stream) {
+  if (n < 1 || a_dev == nullptr || b_dev == nullptr || out_dev == nullptr) return fail(MPK_INVALID_ARG, "bad argument");
+  if (w < 1 || w > 4 || (is_complex != 0 && is_complex != 1)) return fail(MPK_INVALID_ARG, "bad w / is_complex");
+  cudaStream_t s = (cudaStream_t)stream;
+  const Ops* o = get_ops(w, is_complex ? 2 : 1);
+  DotWs ws;
+  char* buf = nullptr;
+  const size_t pb = sizeof(double) * dot_partial_doubles(n);
+  MPK_CUDA(cudaMallocAsync((void**)&buf, pb + 64, s));
+  ws.partial = (double*)buf;
+  ws.counter = (unsigned*)(buf + pb);
+  MPK_CUDA(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s));
+  const double* av[1] = {a_dev};
+  const double* bv[1] = {b_dev};
+  double* ov[1] = {out_dev};
+  o->dots(n, 1, av, bv, ov, ws, nullptr, s);
+  MPK_CUDA(cudaGetLastError());
+  MPK_CUDA(cudaFreeAsync(buf, s));
+  return MPK_OK;
+}

@@ -1,0 +1,135 @@
+// internal.h -- host-side internals shared by the translation units of libmpk.
+#pragma once
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/mpk.h"
+
+namespace mpk {
+
+// Error reporting (thread-local last error; see mpk_last_error).
+void set_error(const std::string& msg);
+int fail(int status, const std::string& msg);
+#define MPK_CUDA(call)                                                                      \
+  do {                                                                                      \
+    cudaError_t err_ = (call);                                                              \
+    if (err_ != cudaSuccess)                                                                \
+      return ::mpk::fail(MPK_CUDA_ERROR, std::string(#call) + ": " + cudaGetErrorString(err_)); \
+  } while (0)
+
+struct Csr {  // device CSR view
+  int n = 0, nnz = 0;
+  const int* rp = nullptr;
+  const int* ci = nullptr;
+  const double* val = nullptr;  // c doubles per entry
+  int cplx = 0;
+};
+
+// Scalar slots of a solve: each slot holds one number (up to 8 doubles).
+enum Slot : int {
+  S_ONE = 0, S_MONE, S_ZERO,
+  S_RHO, S_RHO_OLD, S_SIG, S_ALPHA, S_NALPHA, S_NCALPHA, S_BETA, S_CBETA,
+  S_OMEGA, S_NOMEGA, S_ZETA, S_NZETA, S_ETA, S_NETA,
+  S_NORM,           // last ||r|| (number; leading component used)
+  S_R0N, S_TOL,     // plain doubles in component 0
+  S_D0, S_D1, S_D2, S_D3, S_D4, S_D5,  // dot outputs
+  S_COUNT
+};
+constexpr int kSlotDoubles = 8;
+// Integer state of a solve on the device.
+enum StateIdx : int { ST_DONE = 0, ST_STATUS, ST_ITERS, ST_IT, ST_MAXIT, ST_FLAGS, ST_COUNT };
+
+// Phases of the single-thread scalar kernel.
+enum Phase : int {
+  PH_INIT = 0,    // after ||r0||^2 in S_D0: r0 norm, tolerance, hist[0], early exit
+  PH_RHO,         // after <r~,r> (or BiCG's <z~,r>) in S_D0
+  PH_SIG,         // after the alpha denominator in S_D0
+  PH_OMEGA,       // BiCGSTAB: <t,s>, <t,t> in S_D0, S_D1
+  PH_ZETA,        // GPBiCG: cc, ct, yy, yt, cy, yc in S_D0..S_D5
+  PH_NORM,        // after ||r||^2 in S_D0: history, convergence, breakdown checks
+  PH_BETA,        // BiCG / GPBiCG: after the new rho in S_D0
+  PH_STORE_RHO,   // store S_D0 as rho (BiCG / GPBiCG initialisation)
+  PH_TRUE         // ||b - A x|| from S_D5 (final true residual)
+};
+
+struct DotWs {           // workspace of the fixed-order reduction
+  double* partial = nullptr;  // dot_partial_doubles(n) doubles
+  unsigned* counter = nullptr;
+};
+constexpr int kMaxDots = 6;
+// doubles of per-block partials needed by up to kMaxDots simultaneous inner products of length n
+inline size_t dot_partial_doubles(int n) { return ((size_t)(n > 0 ? n : 1) + 4095) / 4096 * kMaxDots * 8; }
+
+struct IluHandleView;  // forward
+
+// Kernel launchers for one (w, c) pair.  `done` (nullable) is the device flag that turns every
+// launch into a no-op once a solve has finished.
+struct Ops {
+  int w, cp;
+  void (*spmv)(const Csr& A, const double* x, double* y, const double* b_or_null, const int* done, cudaStream_t s);
+  void (*dots)(int n, int k, const double* const* a, const double* const* b, double* const* out, const DotWs& ws,
+               const int* done, cudaStream_t s);
+  // y = sum_k coef_k * v_k evaluated left to right; coef == nullptr means exactly 1
+  // copy_at_first (nullable, the solve's int state): y = v_0 when the iteration counter is 1
+  void (*lincomb)(int n, double* y, int nt, const double* const* coef, const double* const* v,
+                  const int* copy_at_first, const int* done, cudaStream_t s);
+  // y = v0 + s2 * (v1 + s1 * v2)
+  void (*nested)(int n, double* y, const double* v0, const double* v1, const double* v2, const double* s1,
+                 const double* s2, const int* copy_at_first, const int* done, cudaStream_t s);
+  void (*copy)(int n, double* y, const double* x, const int* done, cudaStream_t s);
+  void (*scalar)(int method, int phase, double* S, int* st, double* hist, const int* done, cudaStream_t s);
+  // Substitutions with a binary64 factor and w-component vectors (the paper's "_d").
+  int (*trsv_mp)(const IluHandleView& M, bool lower, bool unit, const double* in, double* out, const int* done,
+                 cudaStream_t s);
+  // Substitutions with a binary32 / bfloat16 factor: lower (in: w-component, out: binary32),
+  // upper (in: binary32, out: w-component); scaling by the handle's power of two.
+  int (*trsv_lo32)(const IluHandleView& M, bool unit, const double* in, const int* done, cudaStream_t s);
+  int (*trsv_up32)(const IluHandleView& M, bool unit, double* out, const int* done, cudaStream_t s);
+  void (*absmax)(int n, const double* v, unsigned long long* out, const int* done, cudaStream_t s);
+};
+const Ops* get_ops(int w, int cp);
+
+// Device-side view of an ILU(0) handle used by the substitution kernels (one triangle pair:
+// either the factor itself or its conjugate transpose).
+struct IluHandleView {
+  int n = 0, nnz = 0, cp = 1, prec = 0;
+  const int* rp = nullptr;
+  const int* ci = nullptr;
+  const int* diag = nullptr;
+  const void* fac = nullptr;   // double / float / uint16 (bfloat16), cp values per entry
+  int* flags = nullptr;        // n: epoch stamps of finished rows
+  int* ctl = nullptr;          // device control words, see CtlIdx
+  float* v32 = nullptr;        // n*cp binary32 intermediate
+  double* vmp = nullptr;       // n*cp*w multi-component intermediate (capacity for w = 4)
+  unsigned long long* absmax = nullptr;
+  int persist_blocks = 0;      // resident blocks to launch for the substitution kernels
+};
+enum CtlIdx : int { CTL_EPOCH = 0, CTL_TICKET_LO, CTL_TICKET_UP, CTL_ERR, CTL_FAIL_ROW, CTL_COUNT };
+
+// Launch helpers shared by the instantiation units.
+int sm_count();
+void launch_trsv_prep(const IluHandleView& M, const int* done, cudaStream_t s);
+
+}  // namespace mpk
+
+// The opaque handle.
+struct mpk_ilu {
+  int n = 0, nnz = 0, cp = 1, prec = 0;
+  int* rp = nullptr;
+  int* ci = nullptr;
+  int* diag = nullptr;
+  void* fac = nullptr;
+  // conjugate transpose (built on first M^H use)
+  int* rpT = nullptr;
+  int* ciT = nullptr;
+  int* diagT = nullptr;
+  void* facT = nullptr;
+  int* flags = nullptr;
+  int* ctl = nullptr;
+  float* v32 = nullptr;
+  double* vmp = nullptr;
+  unsigned long long* absmax = nullptr;
+  mpk::IluHandleView view(bool trans) const;
+};

@@ -1,0 +1,778 @@
+// kernels.cuh -- templated CUDA kernels of the Krylov iteration (instantiated per w in
+// inst_w*.cu).  Every kernel takes the solve's `done` flag (nullable) and returns at once when
+// it is set, so the host can queue several iterations ahead of its convergence check.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "internal.h"
+#include "mp.cuh"
+
+namespace mpk {
+
+constexpr int kBlock = 256;
+constexpr long long kWaitCycles = 1ll << 31;  // ~1 s at 2 GHz: bound of every device wait
+
+__device__ __forceinline__ bool is_done(const int* done) { return done != nullptr && *done != 0; }
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <int W, int CP>
+__device__ __forceinline__ N<W, CP> shfl_down_n(const N<W, CP>& a, int off) {
+  N<W, CP> z;
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    z.re.c[k] = __shfl_down_sync(0xffffffffu, a.re.c[k], off);
+    z.im.c[k] = CP == 2 ? __shfl_down_sync(0xffffffffu, a.im.c[k], off) : 0.0;
+  }
+  return z;
+}
+template <int W, int CP>
+__device__ __forceinline__ N<W, CP> warp_sum(N<W, CP> a) {  // fixed tree order
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) a = n_add<W, CP>(a, shfl_down_n<W, CP>(a, off));
+  return a;
+}
+
+// ---------------------------------------------------------------------------------------------
+// y = A x  (b != nullptr: y = b - A x), one thread per row, CSR order from 0.
+// ---------------------------------------------------------------------------------------------
+template <int W, int CP>
+__global__ void __launch_bounds__(kBlock) k_spmv(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                 const double* __restrict__ val, const double* __restrict__ x,
+                                                 double* __restrict__ y, const double* __restrict__ b,
+                                                 const int* __restrict__ done) {
+  if (is_done(done)) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  N<W, CP> acc = n_zero<W, CP>();
+  const int p1 = rp[i + 1];
+  for (int p = rp[i]; p < p1; ++p) {
+    const int j = ci[p];
+    double ar, ai = 0.0;
+    if constexpr (CP == 1) {
+      ar = val[p];
+    } else {
+      double2 v = reinterpret_cast<const double2*>(val)[p];
+      ar = v.x;
+      ai = v.y;
+    }
+    acc = n_add<W, CP>(acc, n_mul_fp<W, CP>(n_load<W, CP>(x, j), ar, ai));
+  }
+  if (b != nullptr) acc = n_add<W, CP>(n_load<W, CP>(b, i), n_mul<W, CP>(n_real<W, CP>(-1.0), acc));
+  n_store<W, CP>(y, i, acc);
+}
+
+// ---------------------------------------------------------------------------------------------
+// K inner products <a_k, b_k> = sum_i conj(a_k,i) b_k,i in the library's fixed summation order:
+// leaves of kDotLeaf consecutive products summed left to right (from the first product), leaf
+// sums combined by a stride-doubling pairwise tree (level d adds s_{j+d} into s_j for j a
+// multiple of 2d, j + d < m).  Thread t owns leaf t; levels d < 32 run across the lanes of a
+// warp, d = 32..128 across the warps of a block, d >= 256 across blocks (the last block to
+// finish walks the per-block partials).  The result depends on n only, not on the hardware.
+// ---------------------------------------------------------------------------------------------
+constexpr int kDotLeaf = 16;
+constexpr int kLeavesPerBlock = kBlock;  // one leaf per thread
+inline int dot_blocks(int n) {
+  const int m = (n + kDotLeaf - 1) / kDotLeaf;
+  return m < 1 ? 1 : (m + kLeavesPerBlock - 1) / kLeavesPerBlock;
+}
+
+template <int K>
+struct DotArgs {
+  const double* a[K];
+  const double* b[K];
+  double* out[K];
+};
+
+template <int W, int CP, int K>
+__global__ void __launch_bounds__(kBlock) k_dots(int n, DotArgs<K> args, double* __restrict__ partial,
+                                                 unsigned* __restrict__ counter, const int* __restrict__ done) {
+  if (is_done(done)) return;
+  __shared__ __align__(16) double sh[(kBlock / 32) * K * CP * W];
+  __shared__ bool last;
+  const int m = (n + kDotLeaf - 1) / kDotLeaf;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int block_leaf0 = blockIdx.x * kLeavesPerBlock;
+  const int leaf = block_leaf0 + threadIdx.x;
+  N<W, CP> acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = n_zero<W, CP>();
+  if (leaf < m) {
+    const int i0 = leaf * kDotLeaf, i1 = min(n, i0 + kDotLeaf);
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = n_mul_conj<W, CP>(n_load<W, CP>(args.a[k], i0), n_load<W, CP>(args.b[k], i0));
+    for (int i = i0 + 1; i < i1; ++i) {
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        acc[k] = n_add<W, CP>(acc[k], n_mul_conj<W, CP>(n_load<W, CP>(args.a[k], i), n_load<W, CP>(args.b[k], i)));
+    }
+  }
+  // levels d = 1..16 across lanes
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      N<W, CP> o = shfl_down_n<W, CP>(acc[k], d);
+      if ((lane & (2 * d - 1)) == 0 && leaf + d < m) acc[k] = n_add<W, CP>(acc[k], o);
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) n_store<W, CP>(sh, (int64_t)wid * K + k, acc[k]);
+  }
+  __syncthreads();
+  // levels d = 32, 64, 128 across the warps of the block
+  if (wid == 0) {
+    constexpr int NW = kBlock / 32;
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = lane < NW ? n_load<W, CP>(sh, (int64_t)lane * K + k) : n_zero<W, CP>();
+#pragma unroll
+    for (int d = 1; d < NW; d <<= 1) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        N<W, CP> o = shfl_down_n<W, CP>(acc[k], d);
+        if (lane < NW && (lane & (2 * d - 1)) == 0 && block_leaf0 + 32 * (lane + d) < m)
+          acc[k] = n_add<W, CP>(acc[k], o);
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) n_store<W, CP>(partial, (int64_t)blockIdx.x * K + k, acc[k]);
+      __threadfence();
+      const unsigned t = atomicAdd(counter, 1u);
+      last = (t == gridDim.x - 1);
+    }
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // levels d >= 256 across blocks, on the partials
+  const int G = gridDim.x;
+  for (int e = 1; e < G; e <<= 1) {
+    for (int b = threadIdx.x * 2 * e; b + e < G; b += blockDim.x * 2 * e) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        N<W, CP> x = n_load<W, CP>(partial, (int64_t)b * K + k);
+        N<W, CP> y = n_load<W, CP>(partial, (int64_t)(b + e) * K + k);
+        n_store<W, CP>(partial, (int64_t)b * K + k, n_add<W, CP>(x, y));
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) n_store<W, CP>(args.out[k], 0, n_load<W, CP>(partial, k));
+    *counter = 0u;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Vector updates
+// ---------------------------------------------------------------------------------------------
+struct LinArgs {
+  double* y;
+  const double* v[3];
+  const double* s[3];  // nullptr: the vector itself (no multiplication)
+  int nt;
+  const int* copy_at_first;  // non-null: at iteration 1 (st[ST_IT] == 1) y = v[0] instead
+};
+template <int W, int CP>
+__global__ void __launch_bounds__(kBlock) k_lincomb(int n, LinArgs a, const int* __restrict__ done) {
+  if (is_done(done)) return;
+  if (a.copy_at_first != nullptr && a.copy_at_first[ST_IT] == 1) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+      n_store<W, CP>(a.y, i, n_load<W, CP>(a.v[0], i));
+    return;
+  }
+  N<W, CP> s[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    if (k < a.nt && a.s[k] != nullptr) s[k] = n_load<W, CP>(a.s[k], 0);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    N<W, CP> acc = n_load<W, CP>(a.v[0], i);
+    if (a.s[0] != nullptr) acc = n_mul<W, CP>(s[0], acc);
+#pragma unroll
+    for (int k = 1; k < 3; ++k) {
+      if (k < a.nt) {
+        N<W, CP> t = n_load<W, CP>(a.v[k], i);
+        if (a.s[k] != nullptr) t = n_mul<W, CP>(s[k], t);
+        acc = n_add<W, CP>(acc, t);
+      }
+    }
+    n_store<W, CP>(a.y, i, acc);
+  }
+}
+template <int W, int CP>
+__global__ void __launch_bounds__(kBlock) k_nested(int n, double* y, const double* v0, const double* v1,
+                                                   const double* v2, const double* s1p, const double* s2p,
+                                                   const int* copy_at_first, const int* __restrict__ done) {
+  if (is_done(done)) return;
+  if (copy_at_first != nullptr && copy_at_first[ST_IT] == 1) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+      n_store<W, CP>(y, i, n_load<W, CP>(v0, i));
+    return;
+  }
+  const N<W, CP> s1 = n_load<W, CP>(s1p, 0), s2 = n_load<W, CP>(s2p, 0);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    N<W, CP> inner = n_add<W, CP>(n_load<W, CP>(v1, i), n_mul<W, CP>(s1, n_load<W, CP>(v2, i)));
+    n_store<W, CP>(y, i, n_add<W, CP>(n_load<W, CP>(v0, i), n_mul<W, CP>(s2, inner)));
+  }
+}
+template <int W, int CP>
+__global__ void __launch_bounds__(kBlock) k_copy(int n, double* __restrict__ y, const double* __restrict__ x,
+                                                 const int* __restrict__ done) {
+  if (is_done(done)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    n_store<W, CP>(y, i, n_load<W, CP>(x, i));
+}
+
+// Largest |leading component| (real and imaginary parts) as the bit pattern of a nonnegative
+// double, combined with atomicMax (bit order equals numeric order for nonnegative doubles).
+template <int W, int CP>
+__global__ void __launch_bounds__(kBlock) k_absmax(int n, const double* __restrict__ v,
+                                                   unsigned long long* __restrict__ out,
+                                                   const int* __restrict__ done) {
+  if (is_done(done)) return;
+  unsigned long long m = 0ull;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double* p = v + (int64_t)i * CP * W;
+    unsigned long long a = (unsigned long long)__double_as_longlong(fabs(p[0]));
+    m = a > m ? a : m;
+    if constexpr (CP == 2) {
+      unsigned long long b = (unsigned long long)__double_as_longlong(fabs(p[W]));
+      m = b > m ? b : m;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    unsigned long long o = __shfl_down_sync(0xffffffffu, m, off);
+    m = o > m ? o : m;
+  }
+  if ((threadIdx.x & 31) == 0 && m != 0ull) atomicMax(out, m);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Scalar logic of the methods (one thread).  Mirrors the control flow of BiCG (Algorithm 3),
+// CGS, BiCGSTAB and GPBiCG; see krylov.cu for the vector steps between phases.
+// ---------------------------------------------------------------------------------------------
+template <int W, int CP>
+__device__ __forceinline__ N<W, CP> slot(const double* S, int k) {
+  return n_load<W, CP>(S + k * kSlotDoubles, 0);
+}
+template <int W, int CP>
+__device__ __forceinline__ void set_slot(double* S, int k, const N<W, CP>& v) {
+  n_store<W, CP>(S + k * kSlotDoubles, 0, v);
+}
+__device__ __forceinline__ void finish(int* st, int status, int iters) {
+  st[ST_STATUS] = status;
+  st[ST_ITERS] = iters;
+  st[ST_DONE] = 1;
+}
+__device__ __forceinline__ void next_iter(int* st) {
+  const int it = st[ST_IT] + 1;
+  st[ST_IT] = it;
+  if (it > st[ST_MAXIT]) finish(st, MPK_MAXIT, st[ST_MAXIT]);
+}
+
+template <int W, int CP>
+__global__ void k_scalar(int method, int phase, double* __restrict__ S, int* __restrict__ st,
+                         double* __restrict__ hist, const int* __restrict__ done) {
+  if (is_done(done) || threadIdx.x != 0 || blockIdx.x != 0) return;
+  using Num = N<W, CP>;
+  const int it = st[ST_IT];
+  switch (phase) {
+    case PH_INIT: {
+      Num d = slot<W, CP>(S, S_D0);
+      R<W> nr = rsqrt_mp<W>(d.re);
+      const double r0n = nr.c[0];
+      const double tol = S[S_TOL * kSlotDoubles + 1] * r0n + S[S_TOL * kSlotDoubles + 2];
+      S[S_R0N * kSlotDoubles] = r0n;
+      S[S_TOL * kSlotDoubles] = tol;
+      Num nn = n_zero<W, CP>();
+      nn.re = nr;
+      set_slot<W, CP>(S, S_NORM, nn);
+      if (hist) hist[0] = r0n;
+      set_slot<W, CP>(S, S_ONE, n_real<W, CP>(1.0));
+      set_slot<W, CP>(S, S_MONE, n_real<W, CP>(-1.0));
+      set_slot<W, CP>(S, S_ZERO, n_zero<W, CP>());
+      set_slot<W, CP>(S, S_BETA, n_zero<W, CP>());
+      set_slot<W, CP>(S, S_NOMEGA, n_zero<W, CP>());
+      st[ST_IT] = 1;
+      if (r0n != r0n) finish(st, MPK_NAN, 0);
+      else if (r0n < tol || r0n == 0.0) finish(st, MPK_OK, 0);
+      else if (st[ST_MAXIT] < 1) finish(st, MPK_MAXIT, 0);
+      break;
+    }
+    case PH_TRUE: {  // ||b - A x|| of the final iterate (S_D5) into S_D4 component 0
+      R<W> nr = rsqrt_mp<W>(slot<W, CP>(S, S_D5).re);
+      S[S_D4 * kSlotDoubles] = nr.c[0];
+      break;
+    }
+    case PH_STORE_RHO:
+      set_slot<W, CP>(S, S_RHO, slot<W, CP>(S, S_D0));
+      break;
+    case PH_RHO: {
+      Num rho = (method == MPK_GPBICG) ? slot<W, CP>(S, S_RHO) : slot<W, CP>(S, S_D0);
+      if (n_is_zero<W, CP>(rho)) { finish(st, MPK_BREAKDOWN, it - 1); break; }
+      set_slot<W, CP>(S, S_RHO, rho);
+      if (method == MPK_BICGSTAB) {
+        if (it == 1) {
+          set_slot<W, CP>(S, S_BETA, n_zero<W, CP>());
+          set_slot<W, CP>(S, S_NOMEGA, n_zero<W, CP>());
+        } else {
+          Num beta = n_mul<W, CP>(n_div<W, CP>(rho, slot<W, CP>(S, S_RHO_OLD)),
+                                  n_div<W, CP>(slot<W, CP>(S, S_ALPHA), slot<W, CP>(S, S_OMEGA)));
+          set_slot<W, CP>(S, S_BETA, beta);
+        }
+      } else if (method == MPK_CGS) {
+        set_slot<W, CP>(S, S_BETA, it == 1 ? n_zero<W, CP>() : n_div<W, CP>(rho, slot<W, CP>(S, S_RHO_OLD)));
+      }
+      break;
+    }
+    case PH_SIG: {
+      Num sig = slot<W, CP>(S, S_D0), rho = slot<W, CP>(S, S_RHO);
+      if (n_is_zero<W, CP>(sig) || (method == MPK_BICG && n_is_zero<W, CP>(rho))) {
+        finish(st, MPK_BREAKDOWN, it - 1);
+        break;
+      }
+      Num alpha = n_div<W, CP>(rho, sig);
+      set_slot<W, CP>(S, S_SIG, sig);
+      set_slot<W, CP>(S, S_ALPHA, alpha);
+      set_slot<W, CP>(S, S_NALPHA, n_neg<W, CP>(alpha));
+      set_slot<W, CP>(S, S_NCALPHA, n_neg<W, CP>(n_conj<W, CP>(alpha)));
+      break;
+    }
+    case PH_OMEGA: {
+      Num ts = slot<W, CP>(S, S_D0), tt = slot<W, CP>(S, S_D1);
+      Num om = n_is_zero<W, CP>(tt) ? n_zero<W, CP>() : n_div<W, CP>(ts, tt);
+      set_slot<W, CP>(S, S_OMEGA, om);
+      set_slot<W, CP>(S, S_NOMEGA, n_neg<W, CP>(om));
+      break;
+    }
+    case PH_ZETA: {
+      Num cc = slot<W, CP>(S, S_D0), ct = slot<W, CP>(S, S_D1);
+      Num zeta, eta;
+      if (n_is_zero<W, CP>(cc)) {
+        zeta = n_zero<W, CP>();
+        eta = n_zero<W, CP>();
+      } else if (it == 1 || (st[ST_FLAGS] & 1)) {
+        zeta = n_div<W, CP>(ct, cc);
+        eta = n_zero<W, CP>();
+      } else {
+        Num yy = slot<W, CP>(S, S_D2), yt = slot<W, CP>(S, S_D3), cy = slot<W, CP>(S, S_D4), yc = slot<W, CP>(S, S_D5);
+        Num det = n_sub<W, CP>(n_mul<W, CP>(cc, yy), n_mul<W, CP>(cy, yc));
+        if (n_is_zero<W, CP>(det)) { finish(st, MPK_BREAKDOWN, it - 1); break; }
+        zeta = n_div<W, CP>(n_sub<W, CP>(n_mul<W, CP>(yy, ct), n_mul<W, CP>(cy, yt)), det);
+        eta = n_div<W, CP>(n_sub<W, CP>(n_mul<W, CP>(cc, yt), n_mul<W, CP>(yc, ct)), det);
+      }
+      set_slot<W, CP>(S, S_ZETA, zeta);
+      set_slot<W, CP>(S, S_NZETA, n_neg<W, CP>(zeta));
+      set_slot<W, CP>(S, S_ETA, eta);
+      set_slot<W, CP>(S, S_NETA, n_neg<W, CP>(eta));
+      break;
+    }
+    case PH_NORM: {
+      R<W> nr = rsqrt_mp<W>(slot<W, CP>(S, S_D0).re);
+      Num nn = n_zero<W, CP>();
+      nn.re = nr;
+      set_slot<W, CP>(S, S_NORM, nn);
+      if (hist) hist[it] = nr.c[0];
+      if (nr.c[0] != nr.c[0]) { finish(st, MPK_NAN, it); break; }
+      if (nr.c[0] < S[S_TOL * kSlotDoubles]) { finish(st, MPK_OK, it); break; }
+      if (method == MPK_BICGSTAB) {
+        if (n_is_zero<W, CP>(slot<W, CP>(S, S_OMEGA))) { finish(st, MPK_BREAKDOWN, it); break; }
+        set_slot<W, CP>(S, S_RHO_OLD, slot<W, CP>(S, S_RHO));
+        next_iter(st);
+      } else if (method == MPK_CGS) {
+        set_slot<W, CP>(S, S_RHO_OLD, slot<W, CP>(S, S_RHO));
+        next_iter(st);
+      } else if (method == MPK_GPBICG) {
+        if (n_is_zero<W, CP>(slot<W, CP>(S, S_ZETA))) { finish(st, MPK_BREAKDOWN, it); break; }
+      }
+      break;
+    }
+    case PH_BETA: {
+      Num rhon = slot<W, CP>(S, S_D0), rho = slot<W, CP>(S, S_RHO), beta;
+      if (method == MPK_BICG) {
+        beta = n_div<W, CP>(rhon, rho);
+        set_slot<W, CP>(S, S_CBETA, n_conj<W, CP>(beta));
+      } else {
+        beta = n_mul<W, CP>(n_div<W, CP>(slot<W, CP>(S, S_ALPHA), slot<W, CP>(S, S_ZETA)), n_div<W, CP>(rhon, rho));
+      }
+      set_slot<W, CP>(S, S_BETA, beta);
+      set_slot<W, CP>(S, S_RHO, rhon);
+      next_iter(st);
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Dependency-driven ("sync-free") row processing shared by the ILU(0) factorisation and the
+// substitutions.  Rows are handed out in dependency order through a ticket counter, 32
+// consecutive rows per warp (lower: ascending, upper: descending order).  A lane finishes its
+// row once every entry it depends on is finished: rows of its own warp are seen through a warp
+// ballot (memory ordered by __syncwarp), rows of other warps through their epoch flag
+// (st.release / ld.acquire).  A warp only waits for rows with earlier tickets, which belong to
+// running warps, so the scheme cannot deadlock; every wait is still bounded by kWaitCycles,
+// after which the kernel records MPK_TIMEOUT in ctl[CTL_ERR] and all warps leave.
+// `Row` provides: begin(i) -> (p, pend), consume(i, p, j), finish(i).
+// ---------------------------------------------------------------------------------------------
+template <class Row>
+__device__ __forceinline__ void syncfree_rows(int n, bool lower, const int* __restrict__ ci, int* __restrict__ flags,
+                                              int epoch, int* ticket, int* ctl, Row& row) {
+  const int lane = threadIdx.x & 31;
+  const int nchunks = (n + 31) >> 5;
+  for (;;) {
+    int chunk = 0;
+    if (lane == 0) chunk = atomicAdd(ticket, 1);
+    chunk = __shfl_sync(0xffffffffu, chunk, 0);
+    if (chunk >= nchunks) return;
+    const int base = chunk << 5;
+    const int k = base + lane;
+    const bool valid = k < n;
+    const int i = valid ? (lower ? k : n - 1 - k) : 0;
+    int p = 0, pend = 0;
+    if (valid) row.begin(i, p, pend);
+    bool fin = !valid;
+    unsigned finmask = __ballot_sync(0xffffffffu, fin);
+    long long t0 = clock64();
+    bool timeout = false;
+    while (finmask != 0xffffffffu) {
+      bool progressed = false;
+      if (!fin) {
+        while (p < pend) {
+          const int j = ci[p];
+          const int kj = lower ? j : n - 1 - j;
+          bool ready;
+          if (kj >= base) ready = (finmask >> (kj - base)) & 1u;
+          else ready = ld_acquire(flags + j) == epoch;
+          if (!ready) break;
+          row.consume(i, p, j);
+          ++p;
+          progressed = true;
+        }
+        if (p >= pend) {
+          row.finish(i);
+          fin = true;
+          progressed = true;
+          st_release(flags + i, epoch);
+        }
+        if (progressed) t0 = clock64();
+        else if (clock64() - t0 > kWaitCycles) timeout = true;
+      }
+      __syncwarp();
+      finmask = __ballot_sync(0xffffffffu, fin);
+      const bool any_timeout = __any_sync(0xffffffffu, timeout);
+      if (any_timeout) {
+        if (lane == 0) atomicCAS(ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
+        return;
+      }
+      if (finmask != 0xffffffffu) {
+        if (lane == 0 && ld_relaxed(ctl + CTL_ERR) != 0) timeout = true;
+        if (__shfl_sync(0xffffffffu, (int)timeout, 0)) return;
+        if (!__any_sync(0xffffffffu, progressed)) __nanosleep(40);
+      }
+    }
+  }
+}
+
+// binary32 / bfloat16 factor access
+__device__ __forceinline__ float ld_fac(const float* f, int64_t idx) { return f[idx]; }
+__device__ __forceinline__ float ld_fac(const uint16_t* f, int64_t idx) {
+  return __uint_as_float(((unsigned)f[idx]) << 16);
+}
+
+__device__ __forceinline__ int scale_exponent(const unsigned long long* absmax) {
+  const double mx = __longlong_as_double((long long)*absmax);
+  int e = 0;
+  if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);
+  return e;
+}
+
+// Lower triangle with a binary32 / bfloat16 factor: right-hand side = w-component vector scaled
+// by 2^-e and rounded to binary32; result (binary32) into v32.
+template <int W, int CP, typename TS>
+struct RowLo32 {
+  const int* rp;
+  const int* diag;
+  const TS* f;
+  const double* in;
+  float* v32;
+  bool unit;
+  int e;
+  float ar, ai;
+  __device__ void begin(int i, int& p, int& pend) {
+    p = rp[i];
+    pend = diag[i];
+    const double* q = in + (int64_t)i * CP * W;
+    ar = __double2float_rn(ldexp(q[0], -e));
+    ai = CP == 2 ? __double2float_rn(ldexp(q[W], -e)) : 0.0f;
+  }
+  __device__ void consume(int, int p, int j) {
+    if constexpr (CP == 1) {
+      ar = fmaf(-ld_fac(f, p), v32[j], ar);
+    } else {
+      const float lr = ld_fac(f, 2 * (int64_t)p), li = ld_fac(f, 2 * (int64_t)p + 1);
+      const float yr = v32[2 * (int64_t)j], yi = v32[2 * (int64_t)j + 1];
+      ar = fmaf(-lr, yr, ar);
+      ar = fmaf(li, yi, ar);
+      ai = fmaf(-lr, yi, ai);
+      ai = fmaf(-li, yr, ai);
+    }
+  }
+  __device__ void finish(int i) {
+    if (!unit) divide(i);
+    if constexpr (CP == 1) v32[i] = ar;
+    else { v32[2 * (int64_t)i] = ar; v32[2 * (int64_t)i + 1] = ai; }
+  }
+  __device__ void divide(int i) {
+    const int d = diag[i];
+    if constexpr (CP == 1) {
+      ar = ar / ld_fac(f, d);
+    } else {
+      const float yr = ld_fac(f, 2 * (int64_t)d), yi = ld_fac(f, 2 * (int64_t)d + 1);
+      const float den = fmaf(yr, yr, yi * yi), nr = fmaf(ar, yr, ai * yi), ni = fmaf(ai, yr, -(ar * yi));
+      ar = nr / den;
+      ai = ni / den;
+    }
+  }
+};
+// Upper triangle: right-hand side from v32 (in place), result to v32 and, widened and scaled
+// by 2^e, to the w-component output.
+template <int W, int CP, typename TS>
+struct RowUp32 {
+  const int* rp;
+  const int* diag;
+  const TS* f;
+  double* out;
+  float* v32;
+  bool unit;
+  int e;
+  float ar, ai;
+  __device__ void begin(int i, int& p, int& pend) {
+    p = diag[i] + 1;
+    pend = rp[i + 1];
+    if constexpr (CP == 1) { ar = v32[i]; ai = 0.0f; }
+    else { ar = v32[2 * (int64_t)i]; ai = v32[2 * (int64_t)i + 1]; }
+  }
+  __device__ void consume(int, int p, int j) {
+    if constexpr (CP == 1) {
+      ar = fmaf(-ld_fac(f, p), v32[j], ar);
+    } else {
+      const float lr = ld_fac(f, 2 * (int64_t)p), li = ld_fac(f, 2 * (int64_t)p + 1);
+      const float yr = v32[2 * (int64_t)j], yi = v32[2 * (int64_t)j + 1];
+      ar = fmaf(-lr, yr, ar);
+      ar = fmaf(li, yi, ar);
+      ai = fmaf(-lr, yi, ai);
+      ai = fmaf(-li, yr, ai);
+    }
+  }
+  __device__ void finish(int i) {
+    if (!unit) {
+      const int d = diag[i];
+      if constexpr (CP == 1) {
+        ar = ar / ld_fac(f, d);
+      } else {
+        const float yr = ld_fac(f, 2 * (int64_t)d), yi = ld_fac(f, 2 * (int64_t)d + 1);
+        const float den = fmaf(yr, yr, yi * yi), nr = fmaf(ar, yr, ai * yi), ni = fmaf(ai, yr, -(ar * yi));
+        ar = nr / den;
+        ai = ni / den;
+      }
+    }
+    N<W, CP> z = n_zero<W, CP>();
+    z.re.c[0] = ldexp((double)ar, e);
+    if constexpr (CP == 2) z.im.c[0] = ldexp((double)ai, e);
+    n_store<W, CP>(out, i, z);
+    if constexpr (CP == 1) v32[i] = ar;
+    else { v32[2 * (int64_t)i] = ar; v32[2 * (int64_t)i + 1] = ai; }
+  }
+};
+// Binary64 factor, w-component vectors (paper's "_d" substitutions).
+template <int W, int CP>
+struct RowMp {
+  const int* rp;
+  const int* diag;
+  const double* f;
+  const double* in;
+  double* out;
+  bool lower, unit;
+  N<W, CP> acc;
+  __device__ void begin(int i, int& p, int& pend) {
+    if (lower) { p = rp[i]; pend = diag[i]; }
+    else { p = diag[i] + 1; pend = rp[i + 1]; }
+    acc = n_load<W, CP>(in, i);
+  }
+  __device__ void consume(int, int p, int j) {
+    double fr, fi = 0.0;
+    if constexpr (CP == 1) fr = f[p];
+    else { fr = f[2 * (int64_t)p]; fi = f[2 * (int64_t)p + 1]; }
+    acc = n_sub<W, CP>(acc, n_mul_fp<W, CP>(n_load<W, CP>(out, j), fr, fi));
+  }
+  __device__ void finish(int i) {
+    if (!unit) {
+      const int d = diag[i];
+      double fr, fi = 0.0;
+      if constexpr (CP == 1) fr = f[d];
+      else { fr = f[2 * (int64_t)d]; fi = f[2 * (int64_t)d + 1]; }
+      acc = n_div_fp<W, CP>(acc, fr, fi);
+    }
+    n_store<W, CP>(out, i, acc);
+  }
+};
+
+template <int W, int CP, typename TS>
+__global__ void __launch_bounds__(kBlock) k_trsv_lo32(IluHandleView M, bool unit, const double* __restrict__ in,
+                                                      const int* __restrict__ done) {
+  if (is_done(done)) return;
+  RowLo32<W, CP, TS> row{M.rp, M.diag, (const TS*)M.fac, in, M.v32, unit, scale_exponent(M.absmax), 0.f, 0.f};
+  syncfree_rows(M.n, true, M.ci, M.flags, M.ctl[CTL_EPOCH], M.ctl + CTL_TICKET_LO, M.ctl, row);
+}
+template <int W, int CP, typename TS>
+__global__ void __launch_bounds__(kBlock) k_trsv_up32(IluHandleView M, bool unit, double* __restrict__ out,
+                                                      const int* __restrict__ done) {
+  if (is_done(done)) return;
+  RowUp32<W, CP, TS> row{M.rp, M.diag, (const TS*)M.fac, out, M.v32, unit, scale_exponent(M.absmax), 0.f, 0.f};
+  syncfree_rows(M.n, false, M.ci, M.flags, M.ctl[CTL_EPOCH] + 1, M.ctl + CTL_TICKET_UP, M.ctl, row);
+}
+template <int W, int CP>
+__global__ void __launch_bounds__(kBlock) k_trsv_mp(IluHandleView M, bool lower, bool unit,
+                                                    const double* __restrict__ in, double* __restrict__ out,
+                                                    const int* __restrict__ done) {
+  if (is_done(done)) return;
+  RowMp<W, CP> row;
+  row.rp = M.rp;
+  row.diag = M.diag;
+  row.f = (const double*)M.fac;
+  row.in = in;
+  row.out = out;
+  row.lower = lower;
+  row.unit = unit;
+  syncfree_rows(M.n, lower, M.ci, M.flags, M.ctl[CTL_EPOCH] + (lower ? 0 : 1),
+                M.ctl + (lower ? CTL_TICKET_LO : CTL_TICKET_UP), M.ctl, row);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------------------------
+inline int grid_for(int n) {
+  int g = (n + kBlock - 1) / kBlock;
+  const int cap = sm_count() * 8;
+  return g < 1 ? 1 : (g > cap ? cap : g);
+}
+template <class KernelT>
+inline int persistent_blocks(KernelT kernel) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  return per_sm * sm_count();
+}
+
+template <int W, int CP>
+struct Launch {
+  static void spmv(const Csr& A, const double* x, double* y, const double* b, const int* done, cudaStream_t s) {
+    k_spmv<W, CP><<<(A.n + kBlock - 1) / kBlock, kBlock, 0, s>>>(A.n, A.rp, A.ci, A.val, x, y, b, done);
+  }
+  template <int K>
+  static void dotsK(int n, const double* const* a, const double* const* b, double* const* out, const DotWs& ws,
+                    const int* done, cudaStream_t s) {
+    DotArgs<K> args;
+    for (int k = 0; k < K; ++k) {
+      args.a[k] = a[k];
+      args.b[k] = b[k];
+      args.out[k] = out[k];
+    }
+    k_dots<W, CP, K><<<dot_blocks(n), kBlock, 0, s>>>(n, args, ws.partial, ws.counter, done);
+  }
+  static void dots(int n, int k, const double* const* a, const double* const* b, double* const* out, const DotWs& ws,
+                   const int* done, cudaStream_t s) {
+    if (k == 1) dotsK<1>(n, a, b, out, ws, done, s);
+    else if (k == 2) dotsK<2>(n, a, b, out, ws, done, s);
+    else dotsK<6>(n, a, b, out, ws, done, s);
+  }
+  static void lincomb(int n, double* y, int nt, const double* const* coef, const double* const* v,
+                      const int* copy_at_first, const int* done, cudaStream_t s) {
+    LinArgs a;
+    a.y = y;
+    a.nt = nt;
+    a.copy_at_first = copy_at_first;
+    for (int k = 0; k < 3; ++k) {
+      a.v[k] = k < nt ? v[k] : nullptr;
+      a.s[k] = k < nt ? coef[k] : nullptr;
+    }
+    k_lincomb<W, CP><<<grid_for(n), kBlock, 0, s>>>(n, a, done);
+  }
+  static void nested(int n, double* y, const double* v0, const double* v1, const double* v2, const double* s1,
+                     const double* s2, const int* copy_at_first, const int* done, cudaStream_t s) {
+    k_nested<W, CP><<<grid_for(n), kBlock, 0, s>>>(n, y, v0, v1, v2, s1, s2, copy_at_first, done);
+  }
+  static void copy(int n, double* y, const double* x, const int* done, cudaStream_t s) {
+    k_copy<W, CP><<<grid_for(n), kBlock, 0, s>>>(n, y, x, done);
+  }
+  static void scalar(int method, int phase, double* S, int* st, double* hist, const int* done, cudaStream_t s) {
+    k_scalar<W, CP><<<1, 32, 0, s>>>(method, phase, S, st, hist, done);
+  }
+  static void absmax(int n, const double* v, unsigned long long* out, const int* done, cudaStream_t s) {
+    k_absmax<W, CP><<<grid_for(n), kBlock, 0, s>>>(n, v, out, done);
+  }
+  static int trsv_mp(const IluHandleView& M, bool lower, bool unit, const double* in, double* out, const int* done,
+                     cudaStream_t s) {
+    static int blocks = persistent_blocks(k_trsv_mp<W, CP>);
+    k_trsv_mp<W, CP><<<blocks, kBlock, 0, s>>>(M, lower, unit, in, out, done);
+    return cudaGetLastError() == cudaSuccess ? MPK_OK : MPK_CUDA_ERROR;
+  }
+  static int trsv_lo32(const IluHandleView& M, bool unit, const double* in, const int* done, cudaStream_t s) {
+    if (M.prec == MPK_ILU_BF16) {
+      static int blocks = persistent_blocks(k_trsv_lo32<W, CP, uint16_t>);
+      k_trsv_lo32<W, CP, uint16_t><<<blocks, kBlock, 0, s>>>(M, unit, in, done);
+    } else {
+      static int blocks = persistent_blocks(k_trsv_lo32<W, CP, float>);
+      k_trsv_lo32<W, CP, float><<<blocks, kBlock, 0, s>>>(M, unit, in, done);
+    }
+    return cudaGetLastError() == cudaSuccess ? MPK_OK : MPK_CUDA_ERROR;
+  }
+  static int trsv_up32(const IluHandleView& M, bool unit, double* out, const int* done, cudaStream_t s) {
+    if (M.prec == MPK_ILU_BF16) {
+      static int blocks = persistent_blocks(k_trsv_up32<W, CP, uint16_t>);
+      k_trsv_up32<W, CP, uint16_t><<<blocks, kBlock, 0, s>>>(M, unit, out, done);
+    } else {
+      static int blocks = persistent_blocks(k_trsv_up32<W, CP, float>);
+      k_trsv_up32<W, CP, float><<<blocks, kBlock, 0, s>>>(M, unit, out, done);
+    }
+    return cudaGetLastError() == cudaSuccess ? MPK_OK : MPK_CUDA_ERROR;
+  }
+  static Ops table() {
+    Ops o;
+    o.w = W;
+    o.cp = CP;
+    o.spmv = &spmv;
+    o.dots = &dots;
+    o.lincomb = &lincomb;
+    o.nested = &nested;
+    o.copy = &copy;
+    o.scalar = &scalar;
+    o.trsv_mp = &trsv_mp;
+    o.trsv_lo32 = &trsv_lo32;
+    o.trsv_up32 = &trsv_up32;
+    o.absmax = &absmax;
+    return o;
+  }
+};
+
+}  // namespace mpk

@@ -1,0 +1,425 @@
+// krylov.cu -- product-type Krylov solvers (Sec. 3): BiCG (Algorithm 3), CGS, BiCGSTAB and
+// GPBiCG with an optional ILU(0) preconditioner, in w-component real or complex arithmetic.
+//
+// All scalars (rho, alpha, beta, omega, zeta, eta, norms) stay on the device; the host queues
+// `check_every` iterations of kernels and then reads the device "done" flag once.  Kernels
+// queued after convergence return immediately.  Every vector step below names the exact
+// left-to-right evaluation it performs, term by term, so that each element sees the same
+// sequence of w-component operations as the CPU restatement of the method.
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+namespace mpk {
+int precond_apply(const mpk_ilu* M, const Ops* o, bool trans, const double* r, double* z, const int* done,
+                  cudaStream_t s);
+int prepare_trans(mpk_ilu* M, cudaStream_t s);
+int read_ctl_err(const mpk_ilu* M, cudaStream_t s);
+int transpose_matrix(const Csr& A, int* rpT, int* ciT, double* vT, cudaStream_t s);
+}  // namespace mpk
+
+using namespace mpk;
+
+namespace {
+
+struct Ctx {
+  const Ops* o;
+  Csr A, AH;
+  const mpk_ilu* M;
+  int method, n;
+  cudaStream_t s;
+  double* S;
+  int* st;
+  const int* done;
+  double* hist;
+  DotWs dws;
+  int err = MPK_OK;
+
+  double* slot(int k) const { return S + k * kSlotDoubles; }
+  void dot(const double* a, const double* b, int out_slot) {
+    const double* av[1] = {a};
+    const double* bv[1] = {b};
+    double* ov[1] = {slot(out_slot)};
+    o->dots(n, 1, av, bv, ov, dws, done, s);
+  }
+  void dots(int k, const double* const* a, const double* const* b, int first_slot) {
+    double* ov[kMaxDots];
+    for (int q = 0; q < k; ++q) ov[q] = slot(first_slot + q);
+    o->dots(n, k, a, b, ov, dws, done, s);
+  }
+  // y = t0 + t1 + t2, term k = coef_k * v_k (coef slot < 0: the vector itself)
+  void lin(double* y, int c0, const double* v0, int c1 = -2, const double* v1 = nullptr, int c2 = -2,
+           const double* v2 = nullptr, bool copy_at_first = false) {
+    const double* coef[3] = {c0 >= 0 ? slot(c0) : nullptr, c1 >= 0 ? slot(c1) : nullptr, c2 >= 0 ? slot(c2) : nullptr};
+    const double* v[3] = {v0, v1, v2};
+    const int nt = (c1 == -2) ? 1 : ((c2 == -2) ? 2 : 3);
+    o->lincomb(n, y, nt, coef, v, copy_at_first ? st : nullptr, done, s);
+  }
+  // y = v0 + s2 (v1 + s1 v2); copy_at_first: y = v0 at iteration 1
+  void nested(double* y, const double* v0, const double* v1, const double* v2, int s1, int s2, bool copy_at_first) {
+    o->nested(n, y, v0, v1, v2, slot(s1), slot(s2), copy_at_first ? st : nullptr, done, s);
+  }
+  void scalar(int phase) { o->scalar(method, phase, S, st, hist, done, s); }
+  void mv(const double* x, double* y) { o->spmv(A, x, y, nullptr, done, s); }
+  void mvh(const double* x, double* y) { o->spmv(AH, x, y, nullptr, done, s); }
+  void prec(bool trans, const double* r, double* z) {
+    if (M == nullptr) {
+      o->copy(n, z, r, done, s);
+      return;
+    }
+    int st_ = precond_apply(M, o, trans, r, z, done, s);
+    if (st_ != MPK_OK && err == MPK_OK) err = st_;
+  }
+};
+constexpr int ONE = -1;  // coefficient "exactly one"
+
+// ---- BiCGSTAB (van der Vorst), right-preconditioned, r = b - A x -----------------------------
+struct BiCGSTAB {
+  double *r, *rt, *p, *v, *ph, *sv, *sh, *tv;
+  void init(Ctx&) {}
+  void iter(Ctx& c) {
+    c.dot(rt, r, S_D0);                       // rho = <r~, r>
+    c.scalar(PH_RHO);                         // beta = (rho/rho_old)(alpha/omega); 0 at it = 1
+    c.nested(p, r, p, v, S_NOMEGA, S_BETA, true);  // p = r at it = 1, else r + beta (p + (-omega) v)
+    c.prec(false, p, ph);                     // p^ = M^-1 p
+    c.mv(ph, v);                              // v = A p^
+    c.dot(rt, v, S_D0);                       // <r~, v>
+    c.scalar(PH_SIG);                         // alpha = rho / <r~, v>
+    c.lin(sv, ONE, r, S_NALPHA, v);           // s = r + (-alpha) v
+    c.prec(false, sv, sh);                    // s^ = M^-1 s
+    c.mv(sh, tv);                             // t = A s^
+    const double* a[2] = {tv, tv};
+    const double* b[2] = {sv, tv};
+    c.dots(2, a, b, S_D0);                    // <t, s>, <t, t>
+    c.scalar(PH_OMEGA);                       // omega = <t,s> / <t,t> (0 if <t,t> = 0)
+    c.lin(xptr, ONE, xptr, S_ALPHA, ph, S_OMEGA, sh);  // x = (x + alpha p^) + omega s^
+    c.lin(r, ONE, sv, S_NOMEGA, tv);          // r = s + (-omega) t
+    c.dot(r, r, S_D0);
+    c.scalar(PH_NORM);                        // ||r||, stopping rule, omega = 0 breakdown
+  }
+  double* xptr;
+};
+
+// ---- CGS (Sonneveld), right-preconditioned ---------------------------------------------------
+struct CGS {
+  double *r, *rt, *u, *p, *q, *ph, *v, *uh, *uq, *tmp, *xptr;
+  void init(Ctx&) {}
+  void iter(Ctx& c) {
+    c.dot(rt, r, S_D0);                       // rho = <r~, r>
+    c.scalar(PH_RHO);                         // beta = rho / rho_old; 0 at it = 1
+    c.lin(u, ONE, r, S_BETA, q, -2, nullptr, true);  // u = r at it = 1, else r + beta q
+    c.nested(p, u, q, p, S_BETA, S_BETA, true);      // p = u at it = 1, else u + beta (q + beta p)
+    c.prec(false, p, ph);
+    c.mv(ph, v);                              // v = A M^-1 p
+    c.dot(rt, v, S_D0);
+    c.scalar(PH_SIG);                         // alpha = rho / <r~, v>
+    c.lin(q, ONE, u, S_NALPHA, v);            // q = u + (-alpha) v
+    c.lin(uq, ONE, u, S_ONE, q);              // u + 1 q
+    c.prec(false, uq, uh);                    // u^ = M^-1 (u + q)
+    c.lin(xptr, ONE, xptr, S_ALPHA, uh);      // x = x + alpha u^
+    c.mv(uh, tmp);
+    c.lin(r, ONE, r, S_NALPHA, tmp);          // r = r + (-alpha) A u^
+    c.dot(r, r, S_D0);
+    c.scalar(PH_NORM);
+  }
+};
+
+// ---- BiCG, Algorithm 3 -----------------------------------------------------------------------
+struct BiCG {
+  double *r, *rt, *z, *zt, *p, *pt, *q, *qt, *xptr;
+  void init(Ctx& c) {
+    c.prec(false, r, z);                      // M z = r
+    c.prec(true, rt, zt);                     // M^H z~ = r~
+    c.o->copy(c.n, p, z, c.done, c.s);        // p = z
+    c.o->copy(c.n, pt, zt, c.done, c.s);      // p~ = z~
+    c.dot(zt, r, S_D0);                       // rho = <z~, r>
+    c.scalar(PH_STORE_RHO);
+  }
+  void iter(Ctx& c) {
+    c.mv(p, q);                               // q = A p
+    c.mvh(pt, qt);                            // q~ = A^H p~
+    c.dot(pt, q, S_D0);
+    c.scalar(PH_SIG);                         // alpha = rho / <p~, q>
+    c.lin(xptr, ONE, xptr, S_ALPHA, p);       // x = x + alpha p
+    c.lin(r, ONE, r, S_NALPHA, q);            // r = r + (-alpha) q
+    c.lin(rt, ONE, rt, S_NCALPHA, qt);        // r~ = r~ + (-conj(alpha)) q~
+    c.dot(r, r, S_D0);
+    c.scalar(PH_NORM);
+    c.prec(false, r, z);
+    c.prec(true, rt, zt);
+    c.dot(zt, r, S_D0);                       // rho_new = <z~, r>
+    c.scalar(PH_BETA);                        // beta = rho_new / rho
+    c.lin(p, ONE, z, S_BETA, p);              // p = z + beta p
+    c.lin(pt, ONE, zt, S_CBETA, pt);          // p~ = z~ + conj(beta) p~
+  }
+};
+
+// ---- GPBiCG (Zhang) on A M^-1, carried in M^-1-images ("hat" vectors) ------------------------
+struct GPBiCG {
+  double *r, *rt, *rh, *ph, *q, *qh, *tv, *th, *cv, *y, *uh, *zh, *wv, *tprev, *thprev, *tmp, *xptr;
+  void init(Ctx& c) {
+    c.dot(rt, r, S_D0);
+    c.scalar(PH_STORE_RHO);                   // rho = <r~, r0>
+  }
+  void iter(Ctx& c) {
+    c.scalar(PH_RHO);                         // rho = 0 -> breakdown
+    c.prec(false, r, rh);                     // r^ = M^-1 r
+    c.nested(ph, rh, ph, uh, S_MONE, S_BETA, false);  // p^ = r^ + beta (p^ + (-1) u^)
+    c.mv(ph, q);                              // q = A p^
+    c.dot(rt, q, S_D0);
+    c.scalar(PH_SIG);                         // alpha = rho / <r~, q>
+    c.prec(false, q, qh);                     // q^ = M^-1 q
+    c.lin(tv, ONE, r, S_NALPHA, q);           // t = r + (-alpha) q
+    c.lin(th, ONE, rh, S_NALPHA, qh);         // t^ = r^ + (-alpha) q^
+    c.mv(th, cv);                             // c = A t^
+    c.lin(y, ONE, tprev, S_MONE, tv, S_NALPHA, wv);  // y = (t_prev + (-1) t) + (-alpha) w
+    const double* a[6] = {cv, cv, y, y, cv, y};
+    const double* b[6] = {cv, tv, y, tv, y, cv};
+    c.dots(6, a, b, S_D0);                    // cc, ct, yy, yt, cy, yc
+    c.scalar(PH_ZETA);                        // zeta, eta (eta = 0 at it = 1)
+    c.lin(tmp, ONE, thprev, S_MONE, rh, S_BETA, uh);  // (t^_prev + (-1) r^) + beta u^
+    c.lin(uh, S_ZETA, qh, S_ETA, tmp);        // u^ = zeta q^ + eta (...)
+    c.lin(zh, S_ZETA, rh, S_ETA, zh, S_NALPHA, uh);  // z^ = (zeta r^ + eta z^) + (-alpha) u^
+    c.lin(xptr, ONE, xptr, S_ALPHA, ph, S_ONE, zh);  // x = (x + alpha p^) + 1 z^
+    c.lin(r, ONE, tv, S_NETA, y, S_NZETA, cv);       // r = (t + (-eta) y) + (-zeta) c
+    c.dot(r, r, S_D0);
+    c.scalar(PH_NORM);
+    c.dot(rt, r, S_D0);
+    c.scalar(PH_BETA);                        // beta = (alpha/zeta) <r~,r_new>/<r~,r>
+    c.lin(wv, ONE, cv, S_BETA, q);            // w = c + beta q
+    c.o->copy(c.n, tprev, tv, c.done, c.s);
+    c.o->copy(c.n, thprev, th, c.done, c.s);
+  }
+};
+
+}  // namespace
+
+static int validate_csr(const mpk_csr* A) {
+  if (A == nullptr) return fail(MPK_INVALID_ARG, "null matrix");
+  if (A->n < 1 || A->nnz < 0 || A->row_ptr == nullptr || (A->nnz > 0 && (A->col_idx == nullptr || A->val == nullptr)))
+    return fail(MPK_INVALID_ARG, "invalid CSR descriptor");
+  if (A->is_complex != 0 && A->is_complex != 1) return fail(MPK_INVALID_ARG, "is_complex must be 0 or 1");
+  return MPK_OK;
+}
+
+static int solve_impl(int method, int w, const mpk_csr* Ac, const mpk_ilu* Mc, const double* b, double* x,
+                      const mpk_opts* opts, mpk_info* info, cudaStream_t s) {
+  const int n = Ac->n, cp = Ac->is_complex ? 2 : 1;
+  const int64_t vlen = (int64_t)n * cp * w;
+  mpk_ilu* M = const_cast<mpk_ilu*>(Mc);
+  const Ops* o = get_ops(w, cp);
+  if (o == nullptr) return fail(MPK_INVALID_ARG, "unsupported (w, complex)");
+  const int check_every = opts->check_every > 0 ? opts->check_every : 25;
+  const int maxit = opts->maxit;
+
+  Ctx c;
+  c.o = o;
+  c.A = Csr{n, Ac->nnz, Ac->row_ptr, Ac->col_idx, Ac->val, Ac->is_complex};
+  c.M = M;
+  c.method = method;
+  c.n = n;
+  c.s = s;
+  c.hist = opts->hist_dev;
+
+  cudaEvent_t e0, e1;
+  MPK_CUDA(cudaEventCreate(&e0));
+  MPK_CUDA(cudaEventCreate(&e1));
+  MPK_CUDA(cudaEventRecord(e0, s));
+
+  if (method == MPK_BICG && M != nullptr) {
+    int st = prepare_trans(M, s);
+    if (st != MPK_OK) return st;
+  }
+  const int nvec = 17;
+  const size_t vec_bytes = (sizeof(double) * (size_t)vlen + 255) & ~(size_t)255;
+  const size_t small_bytes = sizeof(double) * (S_COUNT * kSlotDoubles + dot_partial_doubles(n)) + 64;
+  char* base = nullptr;
+  MPK_CUDA(cudaMallocAsync((void**)&base, vec_bytes * nvec + small_bytes + 256, s));
+  MPK_CUDA(cudaMemsetAsync(base, 0, vec_bytes * nvec + small_bytes + 256, s));
+  std::vector<double*> V(nvec);
+  for (int k = 0; k < nvec; ++k) V[k] = (double*)(base + vec_bytes * k);
+  char* tail = base + vec_bytes * nvec;
+  c.S = (double*)tail;
+  c.dws.partial = c.S + S_COUNT * kSlotDoubles;
+  char* ints = (char*)(c.dws.partial + dot_partial_doubles(n));
+  c.st = (int*)ints;
+  c.dws.counter = (unsigned*)(ints + 32);
+  c.done = c.st + ST_DONE;
+
+  int* ahbuf = nullptr;
+  if (method == MPK_BICG) {  // A^H for q~ = A^H p~
+    const size_t nnz = (size_t)Ac->nnz;
+    MPK_CUDA(cudaMallocAsync((void**)&ahbuf, sizeof(int) * ((size_t)n + 1 + nnz) + sizeof(double) * nnz * cp + 16, s));
+    int* rpT = ahbuf;
+    int* ciT = ahbuf + n + 1;
+    double* vT = (double*)(((uintptr_t)(ciT + nnz) + 15) & ~(uintptr_t)15);
+    int st = transpose_matrix(c.A, rpT, ciT, vT, s);
+    if (st != MPK_OK) return st;
+    c.AH = Csr{n, Ac->nnz, rpT, ciT, vT, Ac->is_complex};
+  }
+
+  int st_init[ST_COUNT] = {0, MPK_MAXIT, 0, 0, maxit, opts->flags};
+  MPK_CUDA(cudaMemcpyAsync(c.st, st_init, sizeof(st_init), cudaMemcpyHostToDevice, s));
+  double tolv[2] = {opts->tol_rel, opts->tol_abs};
+  MPK_CUDA(cudaMemcpyAsync(c.slot(S_TOL) + 1, tolv, sizeof(tolv), cudaMemcpyHostToDevice, s));
+
+  double* r = V[0];
+  double* rt = V[1];
+  // r = b - A x0, r~ = r, ||r0||
+  o->spmv(c.A, x, r, b, c.done, s);
+  o->copy(n, rt, r, c.done, s);
+  c.dot(r, r, S_D0);
+  c.scalar(PH_INIT);
+
+  BiCGSTAB m_stab{r, rt, V[2], V[3], V[4], V[5], V[6], V[7], x};
+  CGS m_cgs{r, rt, V[2], V[3], V[4], V[5], V[6], V[7], V[8], V[9], x};
+  BiCG m_bicg{r, rt, V[2], V[3], V[4], V[5], V[6], V[7], x};
+  GPBiCG m_gp{r, rt, V[2], V[3], V[4], V[5], V[6], V[7], V[8], V[9], V[10], V[11], V[12], V[13], V[14], V[15], x};
+  switch (method) {
+    case MPK_BICG: m_bicg.init(c); break;
+    case MPK_GPBICG: m_gp.init(c); break;
+    default: break;
+  }
+  int hst[ST_COUNT];
+  int queued = 0;
+  for (;;) {
+    for (int k = 0; k < check_every; ++k) {
+      switch (method) {
+        case MPK_BICG: m_bicg.iter(c); break;
+        case MPK_CGS: m_cgs.iter(c); break;
+        case MPK_BICGSTAB: m_stab.iter(c); break;
+        default: m_gp.iter(c); break;
+      }
+    }
+    queued += check_every;
+    if (c.err != MPK_OK) break;
+    MPK_CUDA(cudaGetLastError());
+    MPK_CUDA(cudaMemcpyAsync(hst, c.st, sizeof(hst), cudaMemcpyDeviceToHost, s));
+    MPK_CUDA(cudaStreamSynchronize(s));
+    if (hst[ST_DONE] || queued > maxit + check_every) break;
+  }
+  if (c.err != MPK_OK) {
+    cudaFreeAsync(base, s);
+    if (ahbuf) cudaFreeAsync(ahbuf, s);
+    return c.err;
+  }
+  int dev_err = MPK_OK;
+  if (M != nullptr) dev_err = read_ctl_err(M, s);
+
+  // true residual b - A x with the final x (no done-gating)
+  o->spmv(c.A, x, V[16], b, nullptr, s);
+  {
+    const double* av[1] = {V[16]};
+    const double* bv[1] = {V[16]};
+    double* ov[1] = {c.slot(S_D5)};
+    o->dots(n, 1, av, bv, ov, c.dws, nullptr, s);
+    o->scalar(method, PH_TRUE, c.S, c.st, nullptr, nullptr, s);
+  }
+  MPK_CUDA(cudaEventRecord(e1, s));
+  double sl[3][kSlotDoubles];
+  MPK_CUDA(cudaMemcpyAsync(hst, c.st, sizeof(hst), cudaMemcpyDeviceToHost, s));
+  MPK_CUDA(cudaMemcpyAsync(sl[0], c.slot(S_R0N), sizeof(double) * kSlotDoubles, cudaMemcpyDeviceToHost, s));
+  MPK_CUDA(cudaMemcpyAsync(sl[1], c.slot(S_NORM), sizeof(double) * kSlotDoubles, cudaMemcpyDeviceToHost, s));
+  MPK_CUDA(cudaMemcpyAsync(sl[2], c.slot(S_D4), sizeof(double) * kSlotDoubles, cudaMemcpyDeviceToHost, s));
+  MPK_CUDA(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  MPK_CUDA(cudaFreeAsync(base, s));
+  if (ahbuf) MPK_CUDA(cudaFreeAsync(ahbuf, s));
+
+  const double r0n = sl[0][0];
+  info->status = hst[ST_DONE] ? hst[ST_STATUS] : MPK_MAXIT;
+  info->iters = hst[ST_DONE] ? hst[ST_ITERS] : maxit;
+  if (dev_err != MPK_OK) info->status = dev_err;
+  info->res0 = r0n;
+  info->relres_rec = r0n > 0 ? sl[1][0] / r0n : 0.0;
+  info->relres_true = r0n > 0 ? sl[2][0] / r0n : 0.0;
+  info->ms_solve = ms;
+  if (info->status != MPK_OK && info->status != MPK_MAXIT && info->status != MPK_BREAKDOWN &&
+      info->status != MPK_NAN)
+    return fail(info->status, "solve failed on the device");
+  return info->status;
+}
+
+extern "C" int mpk_krylov_solve(int method, int w, const mpk_csr* A, const mpk_ilu* M, const double* b_dev,
+                                double* x_dev, const mpk_opts* opts, mpk_info* info, void* stream) {
+  mpk_info dummy;
+  if (info == nullptr) info = &dummy;
+  std::memset(info, 0, sizeof(*info));
+  info->fail_row = -1;
+  info->status = MPK_INVALID_ARG;
+  int v = validate_csr(A);
+  if (v != MPK_OK) return v;
+  if (method < MPK_BICG || method > MPK_GPBICG) return fail(MPK_INVALID_ARG, "unknown method");
+  if (w < 1 || w > 4) return fail(MPK_INVALID_ARG, "w must be 1..4");
+  if (b_dev == nullptr || x_dev == nullptr || opts == nullptr || b_dev == x_dev)
+    return fail(MPK_INVALID_ARG, "null or aliased vector / options");
+  if (opts->maxit < 0) return fail(MPK_INVALID_ARG, "maxit must be >= 0");
+  if (M != nullptr && (M->n != A->n || M->cp != (A->is_complex ? 2 : 1)))
+    return fail(MPK_INVALID_ARG, "preconditioner does not match the matrix");
+  int st = solve_impl(method, w, A, M, b_dev, x_dev, opts, info, (cudaStream_t)stream);
+  info->status = st;
+  return st;
+}
+
+extern "C" int mpk_solve_host(int method, int w, int prec, int32_t n, int32_t is_complex, const int32_t* rp_h,
+                              const int32_t* ci_h, const double* val_h, const double* b_h, double* x_h,
+                              const mpk_opts* opts, mpk_info* info) {
+  mpk_info dummy;
+  if (info == nullptr) info = &dummy;
+  std::memset(info, 0, sizeof(*info));
+  info->fail_row = -1;
+  if (n < 1 || rp_h == nullptr || b_h == nullptr || x_h == nullptr || opts == nullptr)
+    return fail(MPK_INVALID_ARG, "null argument");
+  if (w < 1 || w > 4 || (is_complex != 0 && is_complex != 1)) return fail(MPK_INVALID_ARG, "bad w / is_complex");
+  const int nnz = rp_h[n];
+  const int cp = is_complex ? 2 : 1;
+  if (nnz < 0 || (nnz > 0 && (ci_h == nullptr || val_h == nullptr))) return fail(MPK_INVALID_ARG, "bad nnz");
+  cudaStream_t s;
+  MPK_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  cudaEvent_t e0, e1;
+  MPK_CUDA(cudaEventCreate(&e0));
+  MPK_CUDA(cudaEventCreate(&e1));
+  MPK_CUDA(cudaEventRecord(e0, s));
+  const size_t vb = sizeof(double) * (size_t)n * cp * w;
+  char* buf = nullptr;
+  const size_t bytes = sizeof(int) * ((size_t)n + 1 + nnz) + 16 + sizeof(double) * (size_t)nnz * cp + 2 * vb + 64;
+  MPK_CUDA(cudaMallocAsync((void**)&buf, bytes, s));
+  int* rp = (int*)buf;
+  int* ci = rp + n + 1;
+  double* val = (double*)(((uintptr_t)(ci + nnz) + 15) & ~(uintptr_t)15);
+  double* b = (double*)(((uintptr_t)(val + (size_t)nnz * cp) + 15) & ~(uintptr_t)15);
+  double* x = b + (size_t)n * cp * w;
+  MPK_CUDA(cudaMemcpyAsync(rp, rp_h, sizeof(int) * ((size_t)n + 1), cudaMemcpyHostToDevice, s));
+  MPK_CUDA(cudaMemcpyAsync(ci, ci_h, sizeof(int) * (size_t)nnz, cudaMemcpyHostToDevice, s));
+  MPK_CUDA(cudaMemcpyAsync(val, val_h, sizeof(double) * (size_t)nnz * cp, cudaMemcpyHostToDevice, s));
+  MPK_CUDA(cudaMemcpyAsync(b, b_h, vb, cudaMemcpyHostToDevice, s));
+  MPK_CUDA(cudaMemcpyAsync(x, x_h, vb, cudaMemcpyHostToDevice, s));
+  mpk_csr A{n, nnz, rp, ci, val, is_complex};
+  mpk_ilu* M = nullptr;
+  int st = MPK_OK;
+  if (prec != MPK_ILU_NONE) st = mpk_ilu0_factor(&A, prec, &M, &info->fail_row, s);
+  if (st == MPK_OK) st = mpk_krylov_solve(method, w, &A, M, b, x, opts, info, s);
+  if (M) mpk_ilu0_destroy(M);
+  int fr = info->fail_row;
+  float ms_inner = info->ms_solve;
+  (void)ms_inner;
+  MPK_CUDA(cudaMemcpyAsync(x_h, x, vb, cudaMemcpyDeviceToHost, s));
+  MPK_CUDA(cudaFreeAsync(buf, s));
+  MPK_CUDA(cudaEventRecord(e1, s));
+  MPK_CUDA(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  info->ms_solve = ms;
+  info->fail_row = fr;
+  info->status = st;
+  return st;
+}

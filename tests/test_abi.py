@@ -1,0 +1,73 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point include/mpk.h
+declares (no GPU needed: nothing is launched)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mpk.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mpk_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libmpk():
+    from paper_2504_14498_gb300 import build
+
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for required in ("mpk_spmv_mp", "mpk_ilu0_factor", "mpk_krylov_solve", "mpk_precond_apply", "mpk_dot"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(libmpk):
+    missing = [n for n in _declared() if not hasattr(libmpk, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_header():
+    from paper_2504_14498_gb300 import _lib
+
+    bound = {name for name, _, _ in _lib.SIGNATURES}
+    assert set(_declared()) <= bound, set(_declared()) - bound
+
+
+def test_version_and_error_without_gpu(libmpk):
+    libmpk.mpk_version.restype = ctypes.c_int
+    assert libmpk.mpk_version() >= 100
+    libmpk.mpk_last_error.restype = ctypes.c_char_p
+    assert isinstance(libmpk.mpk_last_error(), bytes)
+
+
+def test_invalid_arguments_rejected_on_host(libmpk):
+    """Argument checks happen before any CUDA call, so they work without a GPU."""
+    from paper_2504_14498_gb300 import _lib
+
+    L = _lib.lib()
+    assert L.mpk_spmv_mp(None, 2, None, None, None) == 6
+    assert L.mpk_dot(0, 0, 2, None, None, None, None) == 6
+    assert L.mpk_ilu0_factor(None, 0, None, None, None) == 6
+    d = _lib.CsrDesc(0, 0, None, None, None, 0)
+    h = ctypes.c_void_p()
+    assert L.mpk_ilu0_factor(ctypes.byref(d), 0, ctypes.byref(h), None, None) == 6
+    assert L.mpk_krylov_solve(7, 2, ctypes.byref(d), None, None, None, None, None, None) == 6
+
+
+def test_oracle_and_library_share_no_code():
+    """The CUDA sources never include or reference the oracle, and vice versa."""
+    csrc = os.path.join(ROOT, "paper_2504_14498_gb300", "csrc")
+    for f in os.listdir(csrc):
+        txt = open(os.path.join(csrc, f)).read()
+        assert "oracle" not in txt.lower(), f
+    otxt = open(os.path.join(ROOT, "oracle", "oracle.c")).read()
+    assert "mp.cuh" not in otxt and "mpk.h" not in otxt

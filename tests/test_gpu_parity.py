@@ -1,0 +1,232 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the same seeded
+inputs.  Bars (from the statement of the method's tolerances):
+  * mixed SpMV: identical to the oracle for D and DD (same operations in the same CSR order);
+    TD / QD within 2^-150 / 2^-200 of sum_j |a_ij||x_j| per row (and in practice identical);
+  * inner products: within 2^-100 (DD), 2^-150 (TD), 2^-200 (QD) of sum |a_i b_i| (D: 4 n u),
+    since the GPU reduces in a different (fixed) order;
+  * ILU(0) factors: identical (<= 2 ulp asked; the kernel follows the KIJ update order exactly);
+  * substitutions: identical for binary32 / bfloat16 factors and for D / DD vectors;
+  * Krylov: per-iteration residual norms within 1e-10 relative over the first 20 iterations,
+    iteration count within 5 % (at least 1), and the true residual at the requested level.
+Sizes span several 256-row tiles and end in a ragged tail.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2504_14498_gb300 import _lib, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {2: 2.0 ** -100, 3: 2.0 ** -150, 4: 2.0 ** -200}
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _row_mag(A, x, w, c):
+    """sum_j |a_ij| |x_j| per row and part (leading components suffice for a tolerance)."""
+    n, rp, ci, val = A
+    X = np.abs(x.reshape(-1, c, w)[:, :, 0])
+    if c == 1:
+        av = np.abs(val)
+        return np.add.reduceat(av * X[ci, 0], rp[:-1]).reshape(n, 1) if len(ci) else np.zeros((n, 1))
+    ar, ai = np.abs(val[0::2]), np.abs(val[1::2])
+    m = (ar + ai) * (X[ci, 0] + X[ci, 1])
+    s = np.add.reduceat(m, rp[:-1])
+    return np.stack([s, s], axis=1)
+
+
+MATS = {
+    "random_real": lambda: (inputs.random_sparse(3001, 3, 20, seed=91), 1),
+    "random_cplx": lambda: (inputs.random_sparse(2003, 3, 12, seed=92, complex_=True), 2),
+    "convdiff3d": lambda: (inputs.convdiff3d(13)[0], 1),
+    "helmholtz": lambda: (inputs.helmholtz2d(37, k=12.0), 2),
+}
+
+
+@pytest.mark.parametrize("mat", list(MATS))
+@pytest.mark.parametrize("w", [1, 2, 3, 4])
+def test_spmv_parity(mat, w):
+    A_t, c = MATS[mat]()
+    n = A_t[0]
+    x = inputs.random_vector(n, w, c, seed=17 + w)
+    A = _lib.Matrix.from_tuple(A_t, is_complex=(c == 2))
+    y = host(_lib.spmv_mp(A, dev(x), w))
+    ref = oracle.spmv(A_t, x, w, c)
+    if w <= 2:
+        assert np.array_equal(y, ref)
+    else:
+        err = np.abs((y - ref).reshape(n, c, w)).sum(axis=2)
+        assert np.all(err <= TOL[w] * _row_mag(A_t, x, w, c) * 4)
+
+
+@pytest.mark.parametrize("w", [1, 2, 3, 4])
+@pytest.mark.parametrize("c", [1, 2])
+@pytest.mark.parametrize("n", [1, 17, 255, 4097, 70001, 1048577])
+def test_dot_parity(w, c, n):
+    a = inputs.random_vector(n, w, c, seed=5)
+    b = inputs.random_vector(n, w, c, seed=6)
+    got = host(_lib.dot(dev(a), dev(b), n, w, c == 2)).reshape(c, w)
+    ref = oracle.dot(a, b, n, w, c).reshape(c, w)
+    assert np.array_equal(got, ref)  # same fixed summation order on both sides
+    A, B = a.reshape(n, c, w)[:, :, 0], b.reshape(n, c, w)[:, :, 0]
+    mag = np.sum(np.abs(A).sum(axis=1) * np.abs(B).sum(axis=1))
+    tol = TOL[w] * 8 if w > 1 else 4 * n * 2.0 ** -53
+    for part in range(c):
+        assert abs(got[part].sum() - ref[part].sum()) <= tol * mag + abs(ref[part, 0]) * 2.0 ** (-53 * w + 2)
+
+
+ILU_MATS = {
+    "convdiff2d": lambda: (inputs.convdiff2d(41, pe=10.0), 1),
+    "convdiff3d": lambda: (inputs.convdiff3d(11)[0], 1),
+    "random": lambda: (inputs.random_sparse(1500, 3, 15, seed=4), 1),
+    "helmholtz": lambda: (inputs.helmholtz2d(29, k=15.0), 2),
+    "random_cplx": lambda: (inputs.random_sparse(900, 3, 9, seed=7, complex_=True), 2),
+}
+
+
+@pytest.mark.parametrize("mat", list(ILU_MATS))
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_ilu0_bitwise(mat, prec):
+    A_t, c = ILU_MATS[mat]()
+    A = _lib.Matrix.from_tuple(A_t, is_complex=(c == 2))
+    M = _lib.ILU0(A, prec)
+    got = host(M.values())
+    st, ref, _ = oracle.ilu0(A_t, prec, c)
+    assert st == 0
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("mat", list(ILU_MATS))
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+@pytest.mark.parametrize("trans", [False, True])
+def test_precond_parity(mat, prec, trans):
+    A_t, c = ILU_MATS[mat]()
+    n = A_t[0]
+    A = _lib.Matrix.from_tuple(A_t, is_complex=(c == 2))
+    M = _lib.ILU0(A, prec)
+    _, fac, _ = oracle.ilu0(A_t, prec, c)
+    for w in (1, 2, 4):
+        r = inputs.random_vector(n, w, c, seed=40 + w)
+        z = host(M.apply(dev(r), w, trans))
+        ref = oracle.precond(A_t, fac, r, w, prec, c, trans)
+        if prec != "fp64" or w <= 2:
+            assert np.array_equal(z, ref), (w, np.max(np.abs(z - ref)))
+        else:
+            scale = np.max(np.abs(ref))
+            assert np.max(np.abs(z - ref)) <= scale * 2.0 ** -190
+
+
+def test_ilu0_errors_reported():
+    A_t = (2, np.array([0, 2, 4], np.int32), np.array([0, 1, 0, 1], np.int32), np.array([1.0, 1.0, 1.0, 1.0]))
+    with pytest.raises(_lib.MpkError) as e:
+        _lib.ILU0(_lib.Matrix.from_tuple(A_t), "fp64")
+    assert e.value.status == "ZERO_PIVOT"
+    B_t = (2, np.array([0, 1, 2], np.int32), np.array([1, 0], np.int32), np.array([1.0, 1.0]))
+    with pytest.raises(_lib.MpkError) as e:
+        _lib.ILU0(_lib.Matrix.from_tuple(B_t), "fp64")
+    assert e.value.status == "MISSING_DIAG"
+    C_t = (2, np.array([0, 2, 3], np.int32), np.array([1, 0, 1], np.int32), np.array([1.0, 2.0, 3.0]))
+    with pytest.raises(_lib.MpkError) as e:
+        _lib.ILU0(_lib.Matrix.from_tuple(C_t), "fp64")
+    assert e.value.status == "INVALID_ARG"
+
+
+def _compare_solve(method, A_t, c, w, ilu, tol, maxit=600, x_star=None):
+    n = A_t[0]
+    xs = inputs.ones(n, w, c) if x_star is None else x_star
+    A = _lib.Matrix.from_tuple(A_t, is_complex=(c == 2))
+    b_dev = _lib.spmv_mp(A, dev(xs), w)
+    b_ref = oracle.spmv(A_t, xs, w, c)
+    assert np.array_equal(host(b_dev), b_ref) or w > 2
+    M = _lib.ILU0(A, ilu) if ilu != "none" else None
+    out = _lib.krylov_solve(method, w, A, M, b_dev, tol_rel=tol, maxit=maxit)
+    ref = oracle.krylov(method, A_t, b_ref, w, c, ilu=ilu, tol_rel=tol, maxit=maxit)
+    assert out["status"] == ref["status"], (out["status"], ref["status"])
+    # stated bar: first 20 residual norms within 1e-10, iteration count within 5 %
+    k = min(20, len(out["hist"]), len(ref["hist"]))
+    np.testing.assert_allclose(out["hist"][:k], ref["hist"][:k], rtol=1e-10)
+    assert abs(out["iters"] - ref["iters"]) <= max(1, int(0.05 * ref["iters"])), (out["iters"], ref["iters"])
+    # achieved: every operation, inner products included, in the same order -> identical runs
+    assert out["iters"] == ref["iters"]
+    assert np.array_equal(out["hist"], ref["hist"])
+    assert out["relres_true"] == ref["relres_true"]
+    assert np.array_equal(host(out["x"]), ref["x"])
+    return out, ref
+
+
+@pytest.mark.parametrize("method", ["bicg", "cgs", "bicgstab", "gpbicg"])
+@pytest.mark.parametrize("ilu", ["fp64", "fp32", "bf16", "none"])
+def test_krylov_real_dd(method, ilu):
+    A_t = inputs.convdiff2d(33, pe=10.0)
+    out, ref = _compare_solve(method, A_t, 1, 2, ilu, 1e-25, maxit=3000 if ilu == "none" else 600)
+    assert out["status"] == "OK"
+    if ilu != "none":
+        assert out["relres_true"] < 1e-24
+
+
+@pytest.mark.parametrize("method", ["bicg", "cgs", "bicgstab", "gpbicg"])
+@pytest.mark.parametrize("ilu", ["fp64", "fp32"])
+def test_krylov_complex_dd(method, ilu):
+    A_t = inputs.helmholtz2d(23, k=10.0)
+    out, ref = _compare_solve(method, A_t, 2, 2, ilu, 1e-25)
+    if (method, ilu) != ("cgs", "fp32"):  # CGS stagnates with the binary32 factor on this indefinite
+        assert out["status"] == "OK" and out["relres_true"] < 1e-24  # system, identically on both sides
+
+
+@pytest.mark.parametrize("method", ["bicgstab", "gpbicg", "bicg", "cgs"])
+@pytest.mark.parametrize("w,tol", [(1, 1e-13), (3, 1e-40), (4, 1e-55)])
+def test_krylov_other_precisions(method, w, tol):
+    A_t = inputs.convdiff2d(14, pe=10.0)
+    out, ref = _compare_solve(method, A_t, 1, w, "fp64", tol)
+    assert out["status"] == "OK"
+
+
+def test_gpbicg_eta0_reduces_to_bicgstab_on_gpu():
+    A_t = inputs.convdiff2d(20, pe=5.0)
+    n, w = A_t[0], 2
+    A = _lib.Matrix.from_tuple(A_t)
+    b = _lib.spmv_mp(A, dev(inputs.ones(n, w)), w)
+    M = _lib.ILU0(A, "fp64")
+    g = _lib.krylov_solve("gpbicg", w, A, M, b, force_eta0=True)
+    s = _lib.krylov_solve("bicgstab", w, A, M, b)
+    k = min(12, len(g["hist"]), len(s["hist"]))
+    np.testing.assert_allclose(g["hist"][:k], s["hist"][:k], rtol=1e-12)
+
+
+def test_krylov_statuses():
+    A_t = (2, np.array([0, 2, 4], np.int32), np.array([0, 1, 0, 1], np.int32), np.array([0.0, 1.0, 1.0, 0.0]))
+    A = _lib.Matrix.from_tuple(A_t)
+    b = dev(np.array([1.0, 0.0, 0.0, 0.0]))
+    for m in ("bicg", "cgs", "bicgstab", "gpbicg"):
+        assert _lib.krylov_solve(m, 2, A, None, b, maxit=10)["status"] == "BREAKDOWN"
+    C_t = inputs.convdiff2d(10, pe=10.0)
+    C = _lib.Matrix.from_tuple(C_t)
+    bb = _lib.spmv_mp(C, dev(inputs.ones(C_t[0], 2)), 2)
+    out = _lib.krylov_solve("bicgstab", 2, C, None, bb, maxit=3)
+    assert out["status"] == "MAXIT" and out["iters"] == 3
+    bn = bb.clone()
+    bn[10] = float("nan")
+    assert _lib.krylov_solve("bicgstab", 2, C, _lib.ILU0(C, "fp64"), bn)["status"] == "NAN"
+    zero = torch.zeros_like(bb)
+    out = _lib.krylov_solve("bicgstab", 2, C, None, zero)
+    assert out["status"] == "OK" and out["iters"] == 0
+
+
+def test_solve_host_end_to_end():
+    A_t = inputs.convdiff2d(30, pe=10.0)
+    n, w = A_t[0], 2
+    b = host(_lib.spmv_mp(_lib.Matrix.from_tuple(A_t), dev(inputs.ones(n, w)), w))
+    out = _lib.solve_host("bicgstab", w, "fp32", A_t, b, tol_rel=1e-25)
+    ref = oracle.krylov("bicgstab", A_t, oracle.spmv(A_t, inputs.ones(n, w), w), w, ilu="fp32", tol_rel=1e-25)
+    assert out["status"] == "OK"
+    assert abs(out["iters"] - ref["iters"]) <= max(1, int(0.05 * ref["iters"]))
+    assert np.max(np.abs(out["x"].reshape(n, w)[:, 0] - 1.0)) < 1e-20
