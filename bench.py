@@ -1,0 +1,347 @@
+#!/usr/bin/env python3
+"""Benchmark of the hot path: time to relative residual 1e-25 of DD BiCGSTAB + ILU(0) on the
+128^3 convection-diffusion workload (N = 2,097,152, nnz = 14,581,760), plus the mixed SpMV's
+HBM roofline.
+
+One step = one whole solve on inputs already resident in HBM: ILU(0) factorisation of A
+(binary64 by default, the paper's "_d" preconditioner) and DD BiCGSTAB from x0 = 0 until
+||r|| < 1e-25 ||r0||.  `value` is seconds per solve (lower is better).  Variants with the
+binary32 and bfloat16 factors are timed beside it at equal final accuracy.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mpk|reference]
+
+--impl reference times the CPU oracle (the plain restatement of the method the CUDA path is
+checked against) on the same workload: factorisation plus a bounded number of iterations,
+extrapolated to the iteration count of the solve (the GPU and CPU iterations are identical).
+Several GPUs (torchrun): independent replicas, one solve per rank per step ("weak" scaling).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to rel. residual 1e-25 (DD BiCGSTAB+ILU0, 128^3) vs plain; SpMV HBM GB/s"
+TOL = 1e-25
+# Iterations DD BiCGSTAB + ILU(0) needs on the 128^3 workload (seed 2504_14498 + 1), as measured
+# by the CUDA path, whose iterations are identical to the CPU oracle's; used only to
+# extrapolate the CPU timings from a bounded sample.
+ITERS_128 = {"fp64": None, "fp32": None, "bf16": None}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mpk", choices=["mpk", "reference"])
+    ap.add_argument("--m", type=int, default=128, help="grid points per axis")
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "bf16"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=1, help="oracle iterations in the CPU sample")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "of measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "of fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling (200 ms) during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload_config(m, prec):
+    n = m ** 3
+    nnz = 7 * n - 6 * m * m
+    return {"workload": "convdiff3d %d^3 (N=%d, nnz=%d), log-normal diffusivity sigma=1, Peclet U(1,50), "
+                        "DD BiCGSTAB + ILU(0) %s, tol 1e-25, x0=0, b=A*ones" % (m, n, nnz, prec),
+            "N": n, "nnz": nnz, "method": "bicgstab", "vectors": "DD (w=2)", "ilu_prec": prec, "tol_rel": TOL,
+            "l2": "inputs larger than L2: A 175 MB + 17 DD work vectors of 33.5 MB (L2 is 129 MB)"}
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ------------------------------------------------------------------------------------------------
+def oracle_sample(A_t, prec, iters_for_extrapolation, cpu_iters):
+    import oracle
+
+    n, w = A_t[0], 2
+    from paper_2504_14498_gb300 import inputs
+
+    xs = inputs.ones(n, w)
+    b = oracle.spmv(A_t, xs, w)
+    t0 = time.perf_counter()
+    st, fac, _ = oracle.ilu0(A_t, prec)
+    t_fac = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    out = oracle.krylov("bicgstab", A_t, b, w, ilu=prec, fac=fac, tol_rel=TOL, maxit=cpu_iters)
+    t_it = (time.perf_counter() - t0) / max(1, out["iters"])
+    iters = iters_for_extrapolation
+    value = t_fac + t_it * iters if iters else None
+    return {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": "oracle ILU(0) %s factorisation (%.2f s) + %d DD BiCGSTAB iteration(s) on the full %d-row "
+                      "matrix (%.2f s/iteration), extrapolated to %s iterations" % (
+                          prec, t_fac, out["iters"], n, t_it, iters),
+            "s_factor": t_fac, "s_per_iter": t_it}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    from paper_2504_14498_gb300 import inputs
+
+    A_t, meta = inputs.convdiff3d(args.m)
+    iters = ITERS_128.get(args.prec) if args.m == 128 else None
+    samples = []
+    for k in range(args.warmup + args.steps):
+        s = oracle_sample(A_t, args.prec, iters, args.cpu_iters)
+        if k >= args.warmup:
+            samples.append(s)
+    vals = [s["value"] for s in samples if s["value"] is not None]
+    value = statistics.mean(vals) if vals else None
+    cpu = dict(samples[-1])
+    cpu["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None if value is None else value * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args.m, args.prec), "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------------------------------------
+# CUDA path
+# ------------------------------------------------------------------------------------------------
+def run_mpk(args):
+    import torch
+
+    from paper_2504_14498_gb300 import _lib, inputs
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    pk, pk_note = peaks()
+    A_t, meta = inputs.convdiff3d(args.m)
+    n, w = A_t[0], 2
+    nnz = len(A_t[2])
+    A = _lib.Matrix.from_tuple(A_t)
+    xs = torch.as_tensor(inputs.ones(n, w), device="cuda")
+    b = _lib.spmv_mp(A, xs, w)
+    torch.cuda.synchronize()
+
+    def solve(prec):
+        M = _lib.ILU0(A, prec)
+        out = _lib.krylov_solve("bicgstab", w, A, M, b, tol_rel=TOL, maxit=20000, check_every=10, history=False)
+        M.close()
+        return out
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    # ---- headline: K timed solves ------------------------------------------------------------
+    for _ in range(args.warmup):
+        out = solve(args.prec)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = _lib.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    outs = [solve(args.prec) for _ in range(args.steps)]
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    launches = _lib.kernel_launches() - l0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    last = outs[-1]
+
+    extra = {"iters": last["iters"], "status": last["status"], "relres_true": last["relres_true"],
+             "relres_rec": last["relres_rec"]}
+    # ---- variants: other factor precisions at equal final accuracy ----------------------------
+    variants = {}
+    if not args.no_variants:
+        for prec in ("fp64", "fp32", "bf16"):
+            if prec == args.prec:
+                continue
+            solve(prec)
+            torch.cuda.synchronize()
+            v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            v0.record()
+            reps = 2
+            for _ in range(reps):
+                o = solve(prec)
+            v1.record()
+            torch.cuda.synchronize()
+            variants[prec] = {"s": v0.elapsed_time(v1) / reps / 1e3, "iters": o["iters"], "status": o["status"],
+                              "relres_true": o["relres_true"]}
+
+    # ---- kernel rooflines (CUDA events on the launching stream) -------------------------------
+    def time_launches(fn, reps=20, warm=5):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, c in evs:
+            a.record()
+            fn()
+            c.record()
+        torch.cuda.synchronize()
+        return statistics.median(a.elapsed_time(c) for a, c in evs) / 1e3
+
+    x = torch.as_tensor(inputs.random_vector(n, w, 1, seed=3), device="cuda")
+    y = torch.empty_like(x)
+    t_spmv = time_launches(lambda: _lib.spmv_mp(A, x, w, y))
+    spmv_bytes = 12 * nnz + 4 * (n + 1) + 2 * 16 * n
+    spmv_gbs = spmv_bytes / t_spmv / 1e9
+    M64 = _lib.ILU0(A, "fp64")
+    M32 = _lib.ILU0(A, "fp32")
+    z = torch.empty_like(x)
+    t_pre64 = time_launches(lambda: M64.apply(x, w, False, z), reps=10, warm=3)
+    t_pre32 = time_launches(lambda: M32.apply(x, w, False, z), reps=10, warm=3)
+    # algorithmic bytes of one M^-1 application: factor values + columns of both triangles, row
+    # pointers and diagonal index twice, DD right-hand side in and DD result out, intermediate
+    # written and read once (binary64: DD, binary32: 4 bytes)
+    pre64_bytes = (8 + 4) * nnz + 2 * 4 * (n + 1) + 2 * 4 * n + 16 * n + 16 * n + 2 * 16 * n
+    pre32_bytes = (4 + 4) * nnz + 2 * 4 * (n + 1) + 2 * 4 * n + 16 * n + 16 * n + 2 * 4 * n
+    M64.close()
+    M32.close()
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    rooflines = {
+        "spmv_dd": {"bound": "hbm", "achieved": spmv_gbs, "peak": hbm, "unit": "GB/s", "frac": spmv_gbs / hbm,
+                    "traffic": None, "bytes_per_launch": spmv_bytes, "s_per_launch": t_spmv, "peak_note": pk_note},
+        "precond_fp64_dd": {"bound": "hbm", "achieved": pre64_bytes / t_pre64 / 1e9, "peak": hbm, "unit": "GB/s",
+                            "frac": pre64_bytes / t_pre64 / 1e9 / hbm, "bytes_per_launch": pre64_bytes,
+                            "s_per_launch": t_pre64},
+        "precond_fp32": {"bound": "hbm", "achieved": pre32_bytes / t_pre32 / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": pre32_bytes / t_pre32 / 1e9 / hbm, "bytes_per_launch": pre32_bytes,
+                         "s_per_launch": t_pre32},
+    }
+
+    # ---- end to end through the host-buffer C call --------------------------------------------
+    e2e = None
+    if not args.no_e2e:
+        bh = b.cpu().numpy()
+        x0 = np.zeros_like(bh)
+        _lib.solve_host("bicgstab", w, args.prec, A_t, bh, x0, tol_rel=TOL, maxit=20000, check_every=10)
+        ts = []
+        for _ in range(max(1, min(args.steps, 2))):
+            t0 = time.perf_counter()
+            r = _lib.solve_host("bicgstab", w, args.prec, A_t, bh, x0, tol_rel=TOL, maxit=20000, check_every=10)
+            ts.append(time.perf_counter() - t0)
+        h2d = A_t[1].nbytes + A_t[2].nbytes + A_t[3].nbytes + bh.nbytes + x0.nbytes
+        e2e = {"value": statistics.mean(ts), "unit": "s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(bh.nbytes), "status": r["status"], "iters": r["iters"]}
+
+    # ---- CPU baseline (oracle, bounded sample) -----------------------------------------------
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = oracle_sample(A_t, args.prec, last["iters"], args.cpu_iters)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": dict(workload_config(args.m, args.prec), parallelism="replicas x%d" % world),
+                "roofline": rooflines["spmv_dd"], "rooflines": rooflines, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clk, "gpu_launches": int(launches), "solve": extra, "variants": variants,
+                "pe": meta["pe"]}
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_mpk(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

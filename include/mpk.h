@@ -110,6 +110,10 @@ int mpk_version(void);
 /* Message of the last failing call on this host thread ("" if none). */
 const char* mpk_last_error(void);
 
+/* Number of CUDA kernels this library has launched in this process so far (all threads).
+ * Lets a caller count the library's launches inside a timed region. */
+uint64_t mpk_kernel_launches(void);
+
 /* y = A x (Sec. 3 "mixed-precision SpMV": binary64 A, w-component vectors).  Row i is
  * accumulated in CSR order from 0: y_i = (((0 + a_i,j1 x_j1) + a_i,j2 x_j2) + ...), each
  * product and sum in w-component arithmetic.  x_dev, y_dev: n*c*w doubles (c from A), must

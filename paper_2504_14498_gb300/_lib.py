@@ -48,6 +48,7 @@ _VP, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
 SIGNATURES = [
     ("mpk_version", _I, []),
     ("mpk_last_error", ctypes.c_char_p, []),
+    ("mpk_kernel_launches", ctypes.c_uint64, []),
     ("mpk_spmv_mp", _I, [ctypes.POINTER(CsrDesc), _I, _VP, _VP, _VP]),
     ("mpk_dot", _I, [_I, _I, _I, _VP, _VP, _VP, _VP]),
     ("mpk_ilu0_factor", _I, [ctypes.POINTER(CsrDesc), _I, ctypes.POINTER(_VP), ctypes.POINTER(_I), _VP]),
@@ -76,6 +77,11 @@ def lib():
             fn.argtypes = args
         _lib = L
     return _lib
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libmpk so far in this process."""
+    return int(lib().mpk_kernel_launches())
 
 
 def _check(st):

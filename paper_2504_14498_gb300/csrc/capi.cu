@@ -1,4 +1,6 @@
 // capi.cu -- library-wide helpers and the stateless C-ABI entry points (SpMV, inner product).
+#include <atomic>
+#include <cstdlib>
 #include <string>
 
 #include "internal.h"
@@ -11,6 +13,18 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 int fail(int status, const std::string& msg) {
   g_last_error = msg;
   return status;
+}
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch(unsigned k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+int resident_warps_per_sm() {
+  static int w = [] {
+    const char* e = std::getenv("MPK_RESIDENT_WARPS");
+    int v = e ? std::atoi(e) : 0;
+    return v > 0 ? v : 32;
+  }();
+  return w;
 }
 
 int sm_count() {
@@ -46,6 +60,8 @@ using namespace mpk;
 extern "C" int mpk_version(void) { return 100; }
 
 extern "C" const char* mpk_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" uint64_t mpk_kernel_launches(void) { return (uint64_t)g_launches.load(); }
 
 extern "C" int mpk_spmv_mp(const mpk_csr* A, int w, const double* x_dev, double* y_dev, void* stream) {
   if (A == nullptr || x_dev == nullptr || y_dev == nullptr || x_dev == y_dev)

@@ -2,6 +2,7 @@
 // entry points, plus the device transposition used by BiCG's M^H solve (Algorithm 3).
 #include <climits>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 
 #include "kernels.cuh"
@@ -67,16 +68,20 @@ __device__ __forceinline__ double fm(double a, double b, double c) { return fma(
 
 template <typename T, int CP>
 struct RowIlu {
+  using Val = Empty;  // rows of earlier levels are read from memory (ordered by the level chain)
   const int* rp;
   const int* ci;
   const int* diag;
   T* a;
   int* ctl;
-  __device__ void begin(int i, int& p, int& pend) {
-    p = rp[i];
-    pend = diag[i];
+  int i;
+  __device__ void begin(int i_, int& p, int& pend) {
+    i = i_;
+    p = rp[i_];
+    pend = diag[i_];
   }
-  __device__ void consume(int i, int p, int k) {
+  __device__ Val load(int) { return Val{}; }
+  __device__ void consume(int p, int k, const Val&) {
     const int dk = diag[k], ek = rp[k + 1], ei = rp[i + 1];
     T lr, li = T(0);
     if constexpr (CP == 1) {
@@ -109,23 +114,32 @@ struct RowIlu {
       }
     }
   }
-  __device__ void finish(int i) {
+  __device__ Val finish() {
     const int d = diag[i];
     bool zero;
     if constexpr (CP == 1) zero = a[d] == T(0);
     else zero = a[2 * (int64_t)d] == T(0) && a[2 * (int64_t)d + 1] == T(0);
     if (zero) atomicMin(ctl + CTL_FAIL_ROW, i);
+    return Val{};
   }
+  __device__ void store(const Val&) {}
 };
-constexpr int kIluEpoch = 1;  // substitution epochs are >= 2
+
+constexpr int kIluEpoch = 1;  // the substitutions use epochs >= 2 on the same chunk flags
 
 template <typename T, int CP>
 __global__ void __launch_bounds__(kBlock) k_ilu(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                                                const int* __restrict__ diag, T* a, int* flags, int* ctl) {
-  RowIlu<T, CP> row{rp, ci, diag, a, ctl};
-  syncfree_rows(n, true, ci, flags, kIluEpoch, ctl + CTL_TICKET_LO, ctl, row);
+                                                const int* __restrict__ diag, const LevelOrder lo, T* a, int* ctl) {
+  RowIlu<T, CP> row;
+  row.rp = rp;
+  row.ci = ci;
+  row.diag = diag;
+  row.a = a;
+  row.ctl = ctl;
+  chunk_rows(lo, ci, kIluEpoch, ctl + CTL_TICKET_LO, ctl, row);
 }
 
+// New epoch pair (lower: even, upper: odd) and reset tickets and the scale accumulator.
 __global__ void k_trsv_prep(int* ctl, unsigned long long* absmax, const int* done) {
   if (is_done(done)) return;
   ctl[CTL_EPOCH] += 2;
@@ -133,6 +147,99 @@ __global__ void k_trsv_prep(int* ctl, unsigned long long* absmax, const int* don
   ctl[CTL_TICKET_UP] = 0;
   *absmax = 0ull;
 }
+
+// ---------------------------------------------------------------------------------------------
+// Chunk order of one triangle.  Order position k is row k (lower) or row n-1-k (upper); chunk c
+// holds positions [32c, 32c+32).  depth(c) = 0 if no row of c depends on a row of another chunk,
+// else 1 + the largest depth among those chunks.  Chunks depend only on earlier chunks, so the
+// depths are computed in chunk order with (epoch << 32 | depth) words and bounded waits; a
+// counting sort by depth then gives the order in which the substitution kernels take chunks.
+// ---------------------------------------------------------------------------------------------
+constexpr unsigned kDepthEpoch0 = 0x40000000u;  // distinct from the substitution epochs
+
+__global__ void __launch_bounds__(kBlock) k_chunk_depth(int n, bool lower, const int* __restrict__ rp,
+                                                        const int* __restrict__ diag, const int* __restrict__ ci,
+                                                        unsigned long long* pk, unsigned epoch, int* __restrict__ depth,
+                                                        int* ticket, int* ctl) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int nchunks = (n + 31) >> 5;
+  for (;;) {
+    int chunk = 0;
+    if (lane == 0) chunk = atomicAdd(ticket, 1);
+    chunk = __shfl_sync(FULL, chunk, 0);
+    if (chunk >= nchunks) return;
+    const int k = (chunk << 5) + lane;
+    int d = -1;
+    bool timeout = false;
+    if (k < n) {
+      const int i = lower ? k : n - 1 - k;
+      const int p0 = lower ? rp[i] : diag[i] + 1, p1 = lower ? diag[i] : rp[i + 1];
+      for (int p = p0; p < p1 && !timeout; ++p) {
+        const int j = ci[p];
+        const int cj = (lower ? j : n - 1 - j) >> 5;
+        if (cj == chunk) continue;
+        const long long t0 = clock64();
+        unsigned long long wv;
+        for (;;) {
+          wv = ld_relaxed_u64(pk + cj);
+          if ((unsigned)(wv >> 32) == epoch) break;
+          if (clock64() - t0 > kWaitCycles || ld_relaxed(ctl + CTL_ERR) != 0) { timeout = true; break; }
+          __nanosleep(64);
+        }
+        if (!timeout) d = max(d, (int)(unsigned)wv);
+      }
+    }
+    if (__any_sync(FULL, timeout)) {
+      if (lane == 0) atomicCAS(ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
+      return;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) d = max(d, __shfl_xor_sync(FULL, d, off));
+    if (lane == 0) {
+      depth[chunk] = d + 1;
+      st_relaxed_u64(pk + chunk, ((unsigned long long)epoch << 32) | (unsigned)(d + 1));
+    }
+  }
+}
+// counts per depth; cnt[L] (L = array length - 1, passed as maxslot) collects the largest depth
+__global__ void k_depth_count(int m, const int* __restrict__ depth, int* __restrict__ cnt, int* __restrict__ maxd) {
+  int mx = 0;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
+    atomicAdd(cnt + depth[c], 1);
+    mx = max(mx, depth[c]);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(maxd, mx);
+}
+// exclusive scan of cnt[0 .. *maxd] into off (one block of 1024 threads)
+__global__ void k_scan_depths(const int* __restrict__ maxd, const int* __restrict__ cnt, int* __restrict__ out) {
+  __shared__ int part[1024];
+  const int n = *maxd + 1;
+  const int t = threadIdx.x, T_ = blockDim.x;
+  const int per = (n + T_ - 1) / T_;
+  const int lo = min(n, t * per), hi = min(n, lo + per);
+  int s = 0;
+  for (int k = lo; k < hi; ++k) s += cnt[k];
+  part[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    int run = 0;
+    for (int k = 0; k < T_; ++k) { int v = part[k]; part[k] = run; run += v; }
+  }
+  __syncthreads();
+  int run = part[t];
+  for (int k = lo; k < hi; ++k) { out[k] = run; run += cnt[k]; }
+}
+__global__ void k_depth_scatter(int m, const int* __restrict__ depth, const int* __restrict__ off,
+                                int* __restrict__ fill, int* __restrict__ order) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
+    const int d = depth[c];
+    order[off[d] + atomicAdd(fill + d, 1)] = c;
+  }
+}
+__global__ void k_scan_single(int n, const int* __restrict__ cnt, int* __restrict__ out);
 
 // ---------------------------------------------------------------------------------------------
 // Conjugate transpose of a CSR matrix with CP values of type T per entry: counts, a single-
@@ -211,6 +318,7 @@ static int transpose_t(int n, int nnz, const int* rp, const int* ci, const T* v,
   MPK_CUDA(cudaMallocAsync((void**)&cnt, sizeof(int) * (size_t)n * 2, s));
   int* fill = cnt + n;
   MPK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)n * 2, s));
+  count_launch(4);  // count, scan, scatter, sort
   k_count_cols<<<grid_for(nnz), kBlock, 0, s>>>(nnz, ci, cnt);
   k_scan_single<<<1, 1024, 0, s>>>(n, cnt, rpT);
   k_scatter_t<T, CP><<<(n + kBlock - 1) / kBlock, kBlock, 0, s>>>(n, rp, ci, v, rpT, fill, ciT, vT);
@@ -225,7 +333,206 @@ int transpose_matrix(const Csr& A, int* rpT, int* ciT, double* vT, cudaStream_t 
   return transpose_t<double, 1>(A.n, A.nnz, A.rp, A.ci, A.val, rpT, ciT, vT, nullptr, s);
 }
 
+// Level of every row of one triangle: 0 without dependencies, else 1 + the largest level of the
+// rows it depends on; computed by the dependency-driven scheme over the chunk order.
+struct RowDepth {
+  using Val = int;
+  const int* rp;
+  const int* diag;
+  bool lower;
+  unsigned long long* pk;
+  unsigned epoch;
+  int* depth;
+  int i, d;
+  __device__ void begin(int i_, int& p, int& pend) {
+    i = i_;
+    d = 0;
+    if (lower) { p = rp[i_]; pend = diag[i_]; }
+    else { p = diag[i_] + 1; pend = rp[i_ + 1]; }
+  }
+  static constexpr int kLook = 4;
+  static constexpr int kBatch = 0;
+  struct Raw { unsigned long long w; };
+  __device__ void issue(int j, Raw& r) { r.w = ld_relaxed_u64(pk + j); }
+  __device__ bool check(int, const Raw& r, Val& v) {
+    if ((unsigned)(r.w >> 32) != epoch) return false;
+    v = (int)(unsigned)r.w;
+    return true;
+  }
+  __device__ void consume(int, int, const Val& v) { d = max(d, v + 1); }
+  __device__ Val finish() { return d; }
+  __device__ void publish(const Val& v) {
+    depth[i] = v;
+    st_relaxed_u64(pk + i, ((unsigned long long)epoch << 32) | (unsigned)v);
+  }
+};
+__global__ void __launch_bounds__(kBlock) k_row_depth(Order ord, const int* __restrict__ ci, const int* __restrict__ rp,
+                                                      const int* __restrict__ diag, bool lower, unsigned long long* pk,
+                                                      unsigned epoch, int* depth, int* ticket, int* ctl) {
+  RowDepth row;
+  row.rp = rp;
+  row.diag = diag;
+  row.lower = lower;
+  row.pk = pk;
+  row.epoch = epoch;
+  row.depth = depth;
+  syncfree_rows(ord, ci, ticket, ctl, row);
+}
+// positions of the chunk order: chunk_order[q / 32] * 32 + q % 32 (order index -> row)
+__global__ void k_perm_from_chunks(int n, bool lower, int nchunks, const int* __restrict__ chunk_order,
+                                   int* __restrict__ perm, int* __restrict__ pos) {
+  const int P = nchunks * 32;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < P; q += gridDim.x * blockDim.x) {
+    const int idx = chunk_order[q >> 5] * 32 + (q & 31);
+    if (idx < n) {
+      const int row = lower ? idx : n - 1 - idx;
+      perm[q] = row;
+      pos[row] = q;
+    } else {
+      perm[q] = -1;
+    }
+  }
+}
+__global__ void k_inverse(int n, const int* __restrict__ perm, int* __restrict__ pos) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) pos[perm[q]] = q;
+}
+
+size_t level_buf_ints(int n, int nlevels) {
+  const size_t P = (size_t)n + 32 * (size_t)nlevels;
+  return P + (size_t)n + (P / 32 + 1) + 1 + (size_t)((n + 31) >> 5) * 32 + (size_t)n;
+}
+Order chunk_view(int* buf, int n, int nlevels) {
+  const size_t P = (size_t)n + 32 * (size_t)nlevels;
+  Order o;
+  o.perm = buf + P + (size_t)n + (P / 32 + 1) + 1;
+  o.pos = o.perm + (size_t)((n + 31) >> 5) * 32;
+  o.npos = ((n + 31) >> 5) * 32;
+  return o;
+}
+LevelOrder level_view(int* buf, int n, int nlevels) {
+  const size_t P = (size_t)n + 32 * (size_t)nlevels;
+  LevelOrder o;
+  o.perm = buf;
+  o.pos = buf + P;
+  o.flags = buf + P + n;
+  o.nchunks = buf + P + n + (P / 32 + 1);
+  return o;
+}
+
+// Level layout: level_size = cnt, padded starts (exclusive scan of 32-rounded sizes, in `off`),
+// nchunks; one block of 1024 threads.
+__global__ void k_level_layout(int nlevels, const int* __restrict__ cnt, int* __restrict__ off, LevelOrder lo) {
+  __shared__ int part[1024];
+  const int t = threadIdx.x, T_ = blockDim.x;
+  const int per = (nlevels + T_ - 1) / T_;
+  const int lo_ = min(nlevels, t * per), hi = min(nlevels, lo_ + per);
+  int s = 0;
+  for (int k = lo_; k < hi; ++k) s += (cnt[k] + 31) & ~31;
+  part[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    int run = 0;
+    for (int k = 0; k < T_; ++k) { int v = part[k]; part[k] = run; run += v; }
+    *const_cast<int*>(lo.nchunks) = run / 32;
+  }
+  __syncthreads();
+  int run = part[t];
+  for (int k = lo_; k < hi; ++k) {
+    off[k] = run;
+    run += (cnt[k] + 31) & ~31;
+  }
+}
+__global__ void k_level_scatter(int n, const int* __restrict__ depth, const int* __restrict__ off,
+                                int* __restrict__ fill, int* __restrict__ perm, int* __restrict__ pos) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int d = depth[i];
+    const int q = off[d] + atomicAdd(fill + d, 1);
+    perm[q] = i;
+    pos[i] = q;
+  }
+}
+
+// Level orders of the two triangles of (rp, ci, diag) into bufs[0] (lower) and bufs[1] (upper),
+// allocated here.  Row levels come from the dependency-driven pass over the chunk order
+// (chunks of 32 consecutive rows sorted by chunk depth).
+static int build_levels(int n, const int* rp, const int* ci, const int* diag, unsigned long long* pk, int* ctl,
+                        int which, int** bufs, int* nlev, cudaStream_t s) {
+  const int m = (n + 31) >> 5;
+  const size_t L = (size_t)(n > m ? n : m) + 1;
+  int* tmp = nullptr;
+  MPK_CUDA(cudaMallocAsync((void**)&tmp, sizeof(int) * (4 * L + (size_t)m * 33 + (size_t)n + 16), s));
+  int* depth = tmp;                      // L
+  int* cnt = depth + L;                  // L
+  int* off = cnt + L;                    // L
+  int* fill = off + L;                   // L
+  int* corder = fill + L;                // m
+  int* perm_c = corder + m;              // 32 m
+  int* pos_c = perm_c + (size_t)m * 32;  // n
+  int* maxd = pos_c + n;                 // 1
+  static int blocks_cd = [] {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chunk_depth, kBlock, 0) != cudaSuccess || per_sm < 1)
+      per_sm = 1;
+    return per_sm * sm_count();
+  }();
+  static int blocks_rd = persistent_blocks(k_row_depth);
+  for (int tri = 0; tri < 2; ++tri) {
+    const bool lower = tri == 0;
+    // chunk depths -> chunk order -> permutation of chunk positions
+    MPK_CUDA(cudaMemsetAsync(ctl + CTL_TICKET_LO, 0, sizeof(int), s));
+    MPK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * 3 * L, s));
+    MPK_CUDA(cudaMemsetAsync(maxd, 0, sizeof(int), s));
+    count_launch(5);
+    k_chunk_depth<<<blocks_cd, kBlock, 0, s>>>(n, lower, rp, diag, ci, pk, kDepthEpoch0 + 4u * which + tri, depth,
+                                               ctl + CTL_TICKET_LO, ctl);
+    k_depth_count<<<grid_for(m), kBlock, 0, s>>>(m, depth, cnt, maxd);
+    k_scan_depths<<<1, 1024, 0, s>>>(maxd, cnt, off);
+    k_depth_scatter<<<grid_for(m), kBlock, 0, s>>>(m, depth, off, fill, corder);
+    k_perm_from_chunks<<<grid_for(m * 32), kBlock, 0, s>>>(n, lower, m, corder, perm_c, pos_c);
+    // row levels
+    MPK_CUDA(cudaMemsetAsync(ctl + CTL_TICKET_LO, 0, sizeof(int), s));
+    MPK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * 3 * L, s));
+    MPK_CUDA(cudaMemsetAsync(maxd, 0, sizeof(int), s));
+    Order oc;
+    oc.perm = perm_c;
+    oc.pos = pos_c;
+    oc.npos = m * 32;
+    count_launch(2);
+    k_row_depth<<<blocks_rd, kBlock, 0, s>>>(oc, ci, rp, diag, lower, pk, kDepthEpoch0 + 4u * which + 2u + tri, depth,
+                                             ctl + CTL_TICKET_LO, ctl);
+    k_depth_count<<<grid_for(n), kBlock, 0, s>>>(n, depth, cnt, maxd);
+    int hmax = 0, herr = 0;
+    MPK_CUDA(cudaMemcpyAsync(&hmax, maxd, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MPK_CUDA(cudaMemcpyAsync(&herr, ctl + CTL_ERR, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MPK_CUDA(cudaStreamSynchronize(s));
+    if (herr != 0) {
+      cudaFreeAsync(tmp, s);
+      return fail(MPK_TIMEOUT, "a bounded device wait ran out while ordering the triangles");
+    }
+    const int nl = hmax + 1;
+    int* buf = nullptr;
+    MPK_CUDA(cudaMalloc((void**)&buf, sizeof(int) * level_buf_ints(n, nl)));
+    const LevelOrder lo = level_view(buf, n, nl);
+    const size_t P = (size_t)n + 32 * (size_t)nl;
+    MPK_CUDA(cudaMemsetAsync(buf, 0xff, sizeof(int) * P, s));  // padding positions: -1
+    MPK_CUDA(cudaMemsetAsync(lo.flags, 0, sizeof(int) * (P / 32 + 1), s));
+    count_launch(2);
+    k_level_layout<<<1, 1024, 0, s>>>(nl, cnt, off, lo);
+    k_level_scatter<<<grid_for(n), kBlock, 0, s>>>(n, depth, off, fill, buf, const_cast<int*>(lo.pos));
+    const Order co = chunk_view(buf, n, nl);
+    MPK_CUDA(cudaMemcpyAsync(const_cast<int*>(co.perm), perm_c, sizeof(int) * (size_t)m * 32, cudaMemcpyDeviceToDevice, s));
+    MPK_CUDA(cudaMemcpyAsync(const_cast<int*>(co.pos), pos_c, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    bufs[tri] = buf;
+    nlev[tri] = nl;
+  }
+  MPK_CUDA(cudaMemsetAsync(ctl + CTL_TICKET_LO, 0, sizeof(int), s));
+  MPK_CUDA(cudaGetLastError());
+  MPK_CUDA(cudaFreeAsync(tmp, s));
+  return MPK_OK;
+}
+
 void launch_trsv_prep(const IluHandleView& M, const int* done, cudaStream_t s) {
+  count_launch();
   k_trsv_prep<<<1, 1, 0, s>>>(M.ctl, M.absmax, done);
 }
 
@@ -255,7 +562,8 @@ static int build_transpose(mpk_ilu* M, cudaStream_t s) {
                     : transpose_t<uint16_t, 1>(M->n, M->nnz, M->rp, M->ci, (const uint16_t*)M->fac, M->rpT,
                                                M->ciT, (uint16_t*)M->facT, M->diagT, s);
   }
-  return st;
+  if (st != MPK_OK) return st;
+  return build_levels(M->n, M->rpT, M->ciT, M->diagT, M->pk, M->ctl, 1, M->lvbuf + 2, M->nlevels + 2, s);
 }
 
 int prepare_trans(mpk_ilu* M, cudaStream_t s) { return build_transpose(M, s); }
@@ -267,13 +575,14 @@ int precond_apply(const mpk_ilu* M, const Ops* o, bool trans, const double* r, d
   const IluHandleView v = M->view(trans);
   launch_trsv_prep(v, done, s);
   int st;
+  // M: unit lower L~ then upper U~ with division; M^H: lower U~^H with division then unit upper L~^H
   if (M->prec == MPK_ILU_FP64) {
     st = o->trsv_mp(v, true, !trans, r, M->vmp, done, s);
     if (st == MPK_OK) st = o->trsv_mp(v, false, trans, M->vmp, z, done, s);
   } else {
     o->absmax(M->n, r, v.absmax, done, s);
-    st = o->trsv_lo32(v, !trans, r, done, s);
-    if (st == MPK_OK) st = o->trsv_up32(v, trans, z, done, s);
+    st = o->trsv32(v, true, !trans, r, nullptr, done, s);
+    if (st == MPK_OK) st = o->trsv32(v, false, trans, nullptr, z, done, s);
   }
   if (st != MPK_OK) return fail(st, "substitution launch failed");
   return MPK_OK;
@@ -290,7 +599,7 @@ int read_ctl_err(const mpk_ilu* M, cudaStream_t s) {
 static void free_handle(mpk_ilu* M) {
   if (M == nullptr) return;
   void* ptrs[] = {M->rp, M->ci, M->diag, M->fac, M->rpT, M->ciT, M->diagT, M->facT, M->flags, M->ctl, M->v32, M->vmp,
-                  M->absmax};
+                  M->absmax, M->pk, M->lvbuf[0], M->lvbuf[1], M->lvbuf[2], M->lvbuf[3]};
   for (void* p : ptrs)
     if (p != nullptr) cudaFree(p);
   delete M;
@@ -315,6 +624,12 @@ IluHandleView mpk_ilu::view(bool trans) const {
   v.v32 = v32;
   v.vmp = vmp;
   v.absmax = absmax;
+  v.pk = pk;
+  const int t = trans ? 2 : 0;
+  v.lv_lo = level_view(lvbuf[t], n, nlevels[t]);
+  v.lv_up = level_view(lvbuf[t + 1], n, nlevels[t + 1]);
+  v.ch_lo = chunk_view(lvbuf[t], n, nlevels[t]);
+  v.ch_up = chunk_view(lvbuf[t + 1], n, nlevels[t + 1]);
   return v;
 }
 
@@ -354,6 +669,7 @@ static int factor_impl(const mpk_csr* A, int prec, mpk_ilu** out, int* fail_row,
   int code = INT_MAX;
   MPK_TRY(cudaMemcpyAsync(M->ctl + CTL_FAIL_ROW, &code, sizeof(int), cudaMemcpyHostToDevice, s));
   // pattern check writes its code into CTL_FAIL_ROW (reset afterwards)
+  count_launch();
   k_check_pattern<<<(n + kBlock - 1) / kBlock, kBlock, 0, s>>>(n, nnz, M->rp, M->ci, M->diag, M->ctl + CTL_FAIL_ROW);
   MPK_TRY(cudaGetLastError());
   MPK_TRY(cudaMemcpyAsync(&code, M->ctl + CTL_FAIL_ROW, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -364,6 +680,14 @@ static int factor_impl(const mpk_csr* A, int prec, mpk_ilu** out, int* fail_row,
                      (code & 1) ? "row without a stored diagonal" : "invalid CSR row (range or column order)"));
   }
   MPK_TRY(cudaMemcpyAsync(M->ctl, ctl0, sizeof(ctl0), cudaMemcpyHostToDevice, s));
+  {
+    const int nch = (n + 31) >> 5;
+    MPK_TRY(cudaMalloc((void**)&M->pk, sizeof(unsigned long long) * (size_t)n * cp));
+    MPK_TRY(cudaMemsetAsync(M->pk, 0, sizeof(unsigned long long) * (size_t)n * cp, s));
+    (void)nch;
+    int st = build_levels(n, M->rp, M->ci, M->diag, M->pk, M->ctl, 0, M->lvbuf, M->nlevels, s);
+    if (st != MPK_OK) return bail(st);
+  }
 
   const int64_t m = (int64_t)nnz * cp;
   void* work = nullptr;  // factor in its computation type
@@ -372,17 +696,20 @@ static int factor_impl(const mpk_csr* A, int prec, mpk_ilu** out, int* fail_row,
     MPK_TRY(cudaMemcpyAsync(work, A->val, sizeof(double) * (size_t)m, cudaMemcpyDeviceToDevice, s));
   } else {
     MPK_TRY(cudaMalloc(&work, sizeof(float) * (size_t)(m > 0 ? m : 1)));
+    count_launch();
     k_narrow<float><<<grid_for((int)((m + 3) / 4)), kBlock, 0, s>>>(m, A->val, (float*)work);
   }
   M->fac = work;
+  MPK_TRY(cudaMemsetAsync(M->ctl + CTL_TICKET_LO, 0, sizeof(int), s));
   static int blocks_d1 = persistent_blocks(k_ilu<double, 1>), blocks_d2 = persistent_blocks(k_ilu<double, 2>);
   static int blocks_f1 = persistent_blocks(k_ilu<float, 1>), blocks_f2 = persistent_blocks(k_ilu<float, 2>);
+  count_launch();
   if (prec == MPK_ILU_FP64) {
-    if (cp == 1) k_ilu<double, 1><<<blocks_d1, kBlock, 0, s>>>(n, M->rp, M->ci, M->diag, (double*)work, M->flags, M->ctl);
-    else k_ilu<double, 2><<<blocks_d2, kBlock, 0, s>>>(n, M->rp, M->ci, M->diag, (double*)work, M->flags, M->ctl);
+    if (cp == 1) k_ilu<double, 1><<<blocks_d1, kBlock, 0, s>>>(n, M->rp, M->ci, M->diag, M->view(false).lv_lo, (double*)work, M->ctl);
+    else k_ilu<double, 2><<<blocks_d2, kBlock, 0, s>>>(n, M->rp, M->ci, M->diag, M->view(false).lv_lo, (double*)work, M->ctl);
   } else {
-    if (cp == 1) k_ilu<float, 1><<<blocks_f1, kBlock, 0, s>>>(n, M->rp, M->ci, M->diag, (float*)work, M->flags, M->ctl);
-    else k_ilu<float, 2><<<blocks_f2, kBlock, 0, s>>>(n, M->rp, M->ci, M->diag, (float*)work, M->flags, M->ctl);
+    if (cp == 1) k_ilu<float, 1><<<blocks_f1, kBlock, 0, s>>>(n, M->rp, M->ci, M->diag, M->view(false).lv_lo, (float*)work, M->ctl);
+    else k_ilu<float, 2><<<blocks_f2, kBlock, 0, s>>>(n, M->rp, M->ci, M->diag, M->view(false).lv_lo, (float*)work, M->ctl);
   }
   MPK_TRY(cudaGetLastError());
   int ctl1[CTL_COUNT];
@@ -396,6 +723,7 @@ static int factor_impl(const mpk_csr* A, int prec, mpk_ilu** out, int* fail_row,
   if (prec == MPK_ILU_BF16) {
     uint16_t* h = nullptr;
     MPK_TRY(cudaMalloc((void**)&h, sizeof(uint16_t) * (size_t)(m > 0 ? m : 1)));
+    count_launch();
     k_to_bf16<<<grid_for((int)((m + 3) / 4)), kBlock, 0, s>>>(m, (const float*)work, h);
     MPK_TRY(cudaGetLastError());
     MPK_TRY(cudaStreamSynchronize(s));
@@ -432,6 +760,7 @@ extern "C" int mpk_ilu0_values(const mpk_ilu* M, double* out_dev, void* stream) 
   const int64_t m = (int64_t)M->nnz * M->cp;
   if (m == 0) return MPK_OK;
   const int g = grid_for((int)((m + 3) / 4));
+  count_launch();
   if (M->prec == MPK_ILU_FP64) k_widen<double><<<g, kBlock, 0, s>>>(m, (const double*)M->fac, out_dev);
   else if (M->prec == MPK_ILU_FP32) k_widen<float><<<g, kBlock, 0, s>>>(m, (const float*)M->fac, out_dev);
   else k_widen<uint16_t><<<g, kBlock, 0, s>>>(m, (const uint16_t*)M->fac, out_dev);

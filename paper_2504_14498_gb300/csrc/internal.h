@@ -64,6 +64,21 @@ inline size_t dot_partial_doubles(int n) { return ((size_t)(n > 0 ? n : 1) + 409
 
 struct IluHandleView;  // forward
 
+// Level order of one triangle for the chunk dataflow (see chunk_rows).
+struct LevelOrder {
+  const int* perm = nullptr;     // position -> row (-1: padding); levels padded to 32 rows
+  const int* pos = nullptr;      // row -> position
+  int* flags = nullptr;          // per chunk: epoch of the last pass that finished it
+  const int* nchunks = nullptr;  // device int: number of chunks
+};
+
+// A dependency-respecting row order of one triangle (see syncfree_rows).
+struct Order {
+  const int* perm = nullptr;  // position -> row (-1: empty position)
+  const int* pos = nullptr;   // row -> position
+  int npos = 0;               // number of positions
+};
+
 // Kernel launchers for one (w, c) pair.  `done` (nullable) is the device flag that turns every
 // launch into a no-op once a solve has finished.
 struct Ops {
@@ -83,10 +98,10 @@ struct Ops {
   // Substitutions with a binary64 factor and w-component vectors (the paper's "_d").
   int (*trsv_mp)(const IluHandleView& M, bool lower, bool unit, const double* in, double* out, const int* done,
                  cudaStream_t s);
-  // Substitutions with a binary32 / bfloat16 factor: lower (in: w-component, out: binary32),
-  // upper (in: binary32, out: w-component); scaling by the handle's power of two.
-  int (*trsv_lo32)(const IluHandleView& M, bool unit, const double* in, const int* done, cudaStream_t s);
-  int (*trsv_up32)(const IluHandleView& M, bool unit, double* out, const int* done, cudaStream_t s);
+  // Substitutions with a binary32 / bfloat16 factor: lower (in: w-component, out: the handle's
+  // binary32 vector), upper (in: that vector, out: w-component); scaling by a power of two.
+  int (*trsv32)(const IluHandleView& M, bool lower, bool unit, const double* in, double* out, const int* done,
+                cudaStream_t s);
   void (*absmax)(int n, const double* v, unsigned long long* out, const int* done, cudaStream_t s);
 };
 const Ops* get_ops(int w, int cp);
@@ -104,13 +119,23 @@ struct IluHandleView {
   float* v32 = nullptr;        // n*cp binary32 intermediate
   double* vmp = nullptr;       // n*cp*w multi-component intermediate (capacity for w = 4)
   unsigned long long* absmax = nullptr;
-  int persist_blocks = 0;      // resident blocks to launch for the substitution kernels
+  unsigned long long* pk = nullptr;  // packed (epoch << 32 | 32 payload bits) words, 8*cp per row
+  LevelOrder lv_lo, lv_up;           // level orders (chunk dataflow) of the two triangles
+  Order ch_lo, ch_up;                // chunk orders (dependency-driven, row chains in warps)
 };
 enum CtlIdx : int { CTL_EPOCH = 0, CTL_TICKET_LO, CTL_TICKET_UP, CTL_ERR, CTL_FAIL_ROW, CTL_COUNT };
 
 // Launch helpers shared by the instantiation units.
 int sm_count();
+int resident_warps_per_sm();        // MPK_RESIDENT_WARPS (default 32): dependency-driven kernels
+void count_launch(unsigned k = 1);  // every kernel launch of the library is counted
 void launch_trsv_prep(const IluHandleView& M, const int* done, cudaStream_t s);
+// ints of the order buffer of one triangle with n rows and `nlevels` levels:
+// level perm (P = n + 32*nlevels) | level pos (n) | chunk flags (P/32 + 1) | nchunks (1) |
+// chunk-order perm (32*ceil(n/32)) | chunk-order pos (n)
+size_t level_buf_ints(int n, int nlevels);
+LevelOrder level_view(int* buf, int n, int nlevels);
+Order chunk_view(int* buf, int n, int nlevels);
 
 }  // namespace mpk
 
@@ -131,5 +156,8 @@ struct mpk_ilu {
   float* v32 = nullptr;
   double* vmp = nullptr;
   unsigned long long* absmax = nullptr;
+  unsigned long long* pk = nullptr;
+  int* lvbuf[4] = {nullptr, nullptr, nullptr, nullptr};  // level orders: lower, upper, transposed lower / upper
+  int nlevels[4] = {0, 0, 0, 0};
   mpk::IluHandleView view(bool trans) const;
 };

@@ -4,7 +4,9 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cstdint>
+#include <type_traits>
 
 #include "internal.h"
 #include "mp.cuh"
@@ -425,74 +427,180 @@ __global__ void k_scalar(int method, int phase, double* __restrict__ S, int* __r
 
 // ---------------------------------------------------------------------------------------------
 // Dependency-driven ("sync-free") row processing shared by the ILU(0) factorisation and the
-// substitutions.  Rows are handed out in dependency order through a ticket counter, 32
-// consecutive rows per warp (lower: ascending, upper: descending order).  A lane finishes its
-// row once every entry it depends on is finished: rows of its own warp are seen through a warp
-// ballot (memory ordered by __syncwarp), rows of other warps through their epoch flag
-// (st.release / ld.acquire).  A warp only waits for rows with earlier tickets, which belong to
-// running warps, so the scheme cannot deadlock; every wait is still bounded by kWaitCycles,
-// after which the kernel records MPK_TIMEOUT in ctl[CTL_ERR] and all warps leave.
-// `Row` provides: begin(i) -> (p, pend), consume(i, p, j), finish(i).
+// substitutions.  Rows are taken in the order of a permutation `perm` (position -> row, -1 for
+// an empty position; `pos` is the inverse) in which every row comes after the rows it depends
+// on: the library uses rows sorted by their level in the dependency graph, so the 32 lanes of a
+// warp hold 32 independent rows of one wavefront.  A warp takes 32 consecutive positions at a
+// time through a ticket counter.  Each lane owns one row and consumes its entries strictly in
+// CSR order (so every row sees the same operation sequence as the sequential algorithm), but
+// fetches the values of rows owned by other warps ahead of time into a small lookahead window
+// as soon as they are published; rows of its own warp are passed by warp shuffle.  A warp only
+// waits for rows at earlier positions, taken by running warps, so the scheme cannot deadlock;
+// every wait is still bounded by kWaitCycles, after which the kernel records MPK_TIMEOUT in
+// ctl[CTL_ERR] and all warps leave.  Warps that make no progress back off with __nanosleep.
+// `Row` provides: type Val; begin(i, p, pend); fetch(j, Val&) (row j owned by another warp:
+// published yet? value); consume(p, j, const Val&); finish() -> Val; publish(const Val&).
 // ---------------------------------------------------------------------------------------------
+struct Empty {};
+__device__ __forceinline__ Empty shfl_val(const Empty& v, int) { return v; }
+__device__ __forceinline__ float shfl_val(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ int shfl_val(int v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ float2 shfl_val(float2 v, int src) {
+  return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+template <int W, int CP>
+__device__ __forceinline__ N<W, CP> shfl_val(const N<W, CP>& a, int src) {
+  N<W, CP> z;
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    z.re.c[k] = __shfl_sync(0xffffffffu, a.re.c[k], src);
+    z.im.c[k] = CP == 2 ? __shfl_sync(0xffffffffu, a.im.c[k], src) : 0.0;
+  }
+  return z;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+
 template <class Row>
-__device__ __forceinline__ void syncfree_rows(int n, bool lower, const int* __restrict__ ci, int* __restrict__ flags,
-                                              int epoch, int* ticket, int* ctl, Row& row) {
+__device__ __forceinline__ void syncfree_rows(const Order ord, const int* __restrict__ ci, int* ticket, int* ctl,
+                                              Row& row) {
+  using V = typename Row::Val;
+  using Raw = typename Row::Raw;
+  constexpr int K = Row::kLook;  // lookahead window (entries fetched ahead of use)
+  const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const int nchunks = (n + 31) >> 5;
+  const int nchunks = (ord.npos + 31) >> 5;
   for (;;) {
     int chunk = 0;
     if (lane == 0) chunk = atomicAdd(ticket, 1);
-    chunk = __shfl_sync(0xffffffffu, chunk, 0);
+    chunk = __shfl_sync(FULL, chunk, 0);
     if (chunk >= nchunks) return;
     const int base = chunk << 5;
     const int k = base + lane;
-    const bool valid = k < n;
-    const int i = valid ? (lower ? k : n - 1 - k) : 0;
+    const int ik = k < ord.npos ? ord.perm[k] : -1;
+    const bool valid = ik >= 0;
+    const int i = valid ? ik : 0;
     int p = 0, pend = 0;
     if (valid) row.begin(i, p, pend);
+    // window q <-> entry p + q: column, position of that row, fetched value
+    int wj[K], wk[K];
+    V win[K];
+    unsigned have = 0u;
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      wj[q] = (valid && p + q < pend) ? ci[p + q] : -1;
+      wk[q] = wj[q] >= 0 ? ord.pos[wj[q]] : INT_MAX;
+    }
+    V mine{};
     bool fin = !valid;
-    unsigned finmask = __ballot_sync(0xffffffffu, fin);
+    if (valid && p >= pend) {
+      mine = row.finish();
+      row.publish(mine);
+      fin = true;
+    }
+    unsigned finmask = __ballot_sync(FULL, fin);
     long long t0 = clock64();
-    bool timeout = false;
-    while (finmask != 0xffffffffu) {
+    unsigned backoff = 0u;
+    int rounds = 0, patience = 0;
+    while (finmask != FULL) {
       bool progressed = false;
+      // (1) fetch published out-of-warp entries of the window: issue every load, then check
       if (!fin) {
-        while (p < pend) {
-          const int j = ci[p];
-          const int kj = lower ? j : n - 1 - j;
-          bool ready;
-          if (kj >= base) ready = (finmask >> (kj - base)) & 1u;
-          else ready = ld_acquire(flags + j) == epoch;
-          if (!ready) break;
-          row.consume(i, p, j);
+        Raw raw[K];
+#pragma unroll
+        for (int q = 0; q < K; ++q)
+          if (wj[q] >= 0 && wk[q] < base && !((have >> q) & 1u)) row.issue(wj[q], raw[q]);
+#pragma unroll
+        for (int q = 0; q < K; ++q)
+          if (wj[q] >= 0 && wk[q] < base && !((have >> q) & 1u) && row.check(wj[q], raw[q], win[q])) {
+            have |= 1u << q;
+            progressed = true;
+          }
+      }
+      // (2) consume in CSR order while possible; in-warp values arrive by shuffle.  Rows with
+      // expensive arithmetic (Row::kBatch rounds of patience) wait until every unfinished lane of
+      // the warp can proceed, so that their arithmetic runs with all lanes active.
+      bool go = true;
+      if constexpr (Row::kBatch > 0) {
+        bool lane_ok = true;  // every window entry fetched, or owned by a lane of this warp
+        if (!fin) {
+#pragma unroll
+          for (int q = 0; q < K; ++q)
+            if (wj[q] >= 0 && wk[q] < base && !((have >> q) & 1u)) lane_ok = false;
+        }
+        if (!__all_sync(FULL, lane_ok) && ++patience <= Row::kBatch) go = false;
+        else patience = 0;
+      }
+      for (; go;) {
+        int src = lane;
+        bool can = false, from_lane = false;
+        if (!fin && p < pend) {
+          if (have & 1u) {
+            can = true;
+          } else if (wk[0] >= base && ((finmask >> (wk[0] - base)) & 1u)) {
+            can = true;
+            from_lane = true;
+            src = wk[0] - base;
+          }
+        }
+        const V sv = shfl_val(mine, src);
+        bool step = false;
+        if (can) {
+          row.consume(p, wj[0], from_lane ? sv : win[0]);
           ++p;
-          progressed = true;
+#pragma unroll
+          for (int q = 0; q < K - 1; ++q) {
+            win[q] = win[q + 1];
+            wj[q] = wj[q + 1];
+            wk[q] = wk[q + 1];
+          }
+          wj[K - 1] = p + K - 1 < pend ? ci[p + K - 1] : -1;
+          wk[K - 1] = wj[K - 1] >= 0 ? ord.pos[wj[K - 1]] : INT_MAX;
+          have >>= 1;
+          step = true;
+          if (p >= pend) {
+            mine = row.finish();
+            row.publish(mine);
+            fin = true;
+          }
         }
-        if (p >= pend) {
-          row.finish(i);
-          fin = true;
-          progressed = true;
-          st_release(flags + i, epoch);
+        __syncwarp();
+        finmask = __ballot_sync(FULL, fin);
+        if (!__any_sync(FULL, step)) break;
+        progressed = true;
+      }
+      if (finmask == FULL) break;
+      // (3) bounded waiting, error propagation, backoff
+      const bool any_prog = __any_sync(FULL, progressed);
+      if (any_prog) {
+        t0 = clock64();
+        backoff = 0u;
+      } else {
+        int stop = 0;
+        if (lane == 0) {
+          if (clock64() - t0 > kWaitCycles) {
+            atomicCAS(ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
+            stop = 1;
+          } else if ((++rounds & 15) == 0 && ld_relaxed(ctl + CTL_ERR) != 0) {
+            stop = 1;
+          }
         }
-        if (progressed) t0 = clock64();
-        else if (clock64() - t0 > kWaitCycles) timeout = true;
-      }
-      __syncwarp();
-      finmask = __ballot_sync(0xffffffffu, fin);
-      const bool any_timeout = __any_sync(0xffffffffu, timeout);
-      if (any_timeout) {
-        if (lane == 0) atomicCAS(ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
-        return;
-      }
-      if (finmask != 0xffffffffu) {
-        if (lane == 0 && ld_relaxed(ctl + CTL_ERR) != 0) timeout = true;
-        if (__shfl_sync(0xffffffffu, (int)timeout, 0)) return;
-        if (!__any_sync(0xffffffffu, progressed)) __nanosleep(40);
+        if (__shfl_sync(FULL, stop, 0)) return;
+        backoff = backoff == 0u ? 32u : (backoff < 256u ? 2u * backoff : 256u);
+        __nanosleep(backoff);
       }
     }
   }
 }
 
+// ---------------------------------------------------------------------------------------------
 // binary32 / bfloat16 factor access
 __device__ __forceinline__ float ld_fac(const float* f, int64_t idx) { return f[idx]; }
 __device__ __forceinline__ float ld_fac(const uint16_t* f, int64_t idx) {
@@ -506,85 +614,130 @@ __device__ __forceinline__ int scale_exponent(const unsigned long long* absmax) 
   return e;
 }
 
-// Lower triangle with a binary32 / bfloat16 factor: right-hand side = w-component vector scaled
-// by 2^-e and rounded to binary32; result (binary32) into v32.
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------------------------
+// Chunk dataflow for the substitutions and the ILU(0) factorisation.  Rows are sorted by their
+// level in the dependency graph (0: no dependency, else 1 + the largest level of the rows they
+// depend on) and every level is padded to whole 32-row chunks, so the lanes of a warp hold
+// independent rows and compute in lockstep.  Warps take chunks in level order through a ticket
+// counter.  Before computing, every lane polls (relaxed loads, backoff) the completion flags of
+// the chunks holding its row's dependencies; once all lanes are satisfied the warp executes one
+// acquire fence, computes its rows with ordinary loads and stores, and lane 0 stamps the
+// chunk's flag with the current epoch by a release store.  Dependencies lie in earlier levels,
+// whose chunks have earlier tickets and belong to running warps: no deadlock.  Every wait is
+// bounded by kWaitCycles (then MPK_TIMEOUT in ctl[CTL_ERR] and all warps leave).  `Row`
+// provides: type Val; begin(i, p, pend); Val load(j); consume(p, j, Val); Val finish();
+// store(Val).
+// ---------------------------------------------------------------------------------------------
+template <class Row>
+__device__ __forceinline__ void chunk_rows(const LevelOrder lo, const int* __restrict__ ci, int epoch, int* ticket,
+                                           int* ctl, Row& row) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int nchunks = *lo.nchunks;
+  for (;;) {
+    int chunk = 0;
+    if (lane == 0) chunk = atomicAdd(ticket, 1);
+    chunk = __shfl_sync(FULL, chunk, 0);
+    if (chunk >= nchunks) return;
+    const int i = lo.perm[(chunk << 5) + lane];
+    int p = 0, pend = 0;
+    if (i >= 0) row.begin(i, p, pend);
+    // wait for the chunks this row depends on
+    bool timeout = false;
+    {
+      const long long t0 = clock64();
+      unsigned backoff = 0u;
+      int rounds = 0;
+      for (int q = p; q < pend && !timeout; ++q) {
+        const int c = lo.pos[ci[q]] >> 5;
+        while (ld_relaxed(lo.flags + c) != epoch) {
+          if (clock64() - t0 > kWaitCycles) { timeout = true; break; }
+          if ((++rounds & 31) == 0 && ld_relaxed(ctl + CTL_ERR) != 0) { timeout = true; break; }
+          backoff = backoff == 0u ? 32u : (backoff < 512u ? 2u * backoff : 512u);
+          __nanosleep(backoff);
+        }
+      }
+    }
+    if (__any_sync(FULL, timeout)) {
+      if (lane == 0) atomicCAS(ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
+      return;
+    }
+    fence_acq_rel();
+    if (i >= 0) {
+      for (int q = p; q < pend; ++q) {
+        const int j = ci[q];
+        row.consume(q, j, row.load(j));
+      }
+      row.store(row.finish());
+    }
+    __syncwarp();
+    if (lane == 0) st_release(lo.flags + chunk, epoch);
+  }
+}
+
+// Triangles with a binary32 / bfloat16 factor, dependency-driven over the chunk order (chunks of
+// 32 consecutive rows sorted by chunk depth, so a warp holds a run of a row chain and passes it
+// along by shuffle).  Rows are published to other warps as (epoch << 32 | value bits) 64-bit
+// words: one single-copy-atomic store, read back with relaxed loads and no fence.
 template <int W, int CP, typename TS>
-struct RowLo32 {
+struct RowPk32 {
+  using Val = typename std::conditional<CP == 1, float, float2>::type;
+  static constexpr int kLook = 4;
+  static constexpr int kBatch = 0;
+  struct Raw { unsigned long long w[CP]; };
   const int* rp;
   const int* diag;
   const TS* f;
-  const double* in;
   float* v32;
-  bool unit;
+  unsigned long long* pk;
+  const double* in;  // lower: multi-component right-hand side
+  double* out;       // upper: multi-component result
+  unsigned epoch;
+  bool lower, unit;
   int e;
+  int i;
   float ar, ai;
-  __device__ void begin(int i, int& p, int& pend) {
-    p = rp[i];
-    pend = diag[i];
-    const double* q = in + (int64_t)i * CP * W;
-    ar = __double2float_rn(ldexp(q[0], -e));
-    ai = CP == 2 ? __double2float_rn(ldexp(q[W], -e)) : 0.0f;
+  __device__ void begin(int i_, int& p, int& pend) {
+    i = i_;
+    if (lower) {
+      p = rp[i_];
+      pend = diag[i_];
+      const double* q = in + (int64_t)i_ * CP * W;
+      ar = __double2float_rn(ldexp(q[0], -e));
+      ai = CP == 2 ? __double2float_rn(ldexp(q[W], -e)) : 0.0f;
+    } else {
+      p = diag[i_] + 1;
+      pend = rp[i_ + 1];
+      if constexpr (CP == 1) { ar = v32[i_]; ai = 0.0f; }
+      else { ar = v32[2 * (int64_t)i_]; ai = v32[2 * (int64_t)i_ + 1]; }
+    }
   }
-  __device__ void consume(int, int p, int j) {
+  __device__ void issue(int j, Raw& r) {
+#pragma unroll
+    for (int c = 0; c < CP; ++c) r.w[c] = ld_relaxed_u64(pk + (int64_t)j * CP + c);
+  }
+  __device__ bool check(int, const Raw& r, Val& v) {
+#pragma unroll
+    for (int c = 0; c < CP; ++c)
+      if ((unsigned)(r.w[c] >> 32) != epoch) return false;
+    if constexpr (CP == 1) v = __uint_as_float((unsigned)r.w[0]);
+    else v = make_float2(__uint_as_float((unsigned)r.w[0]), __uint_as_float((unsigned)r.w[1]));
+    return true;
+  }
+  __device__ void consume(int p, int, const Val& v) {
     if constexpr (CP == 1) {
-      ar = fmaf(-ld_fac(f, p), v32[j], ar);
+      ar = fmaf(-ld_fac(f, p), v, ar);
     } else {
       const float lr = ld_fac(f, 2 * (int64_t)p), li = ld_fac(f, 2 * (int64_t)p + 1);
-      const float yr = v32[2 * (int64_t)j], yi = v32[2 * (int64_t)j + 1];
-      ar = fmaf(-lr, yr, ar);
-      ar = fmaf(li, yi, ar);
-      ai = fmaf(-lr, yi, ai);
-      ai = fmaf(-li, yr, ai);
+      ar = fmaf(-lr, v.x, ar);
+      ar = fmaf(li, v.y, ar);
+      ai = fmaf(-lr, v.y, ai);
+      ai = fmaf(-li, v.x, ai);
     }
   }
-  __device__ void finish(int i) {
-    if (!unit) divide(i);
-    if constexpr (CP == 1) v32[i] = ar;
-    else { v32[2 * (int64_t)i] = ar; v32[2 * (int64_t)i + 1] = ai; }
-  }
-  __device__ void divide(int i) {
-    const int d = diag[i];
-    if constexpr (CP == 1) {
-      ar = ar / ld_fac(f, d);
-    } else {
-      const float yr = ld_fac(f, 2 * (int64_t)d), yi = ld_fac(f, 2 * (int64_t)d + 1);
-      const float den = fmaf(yr, yr, yi * yi), nr = fmaf(ar, yr, ai * yi), ni = fmaf(ai, yr, -(ar * yi));
-      ar = nr / den;
-      ai = ni / den;
-    }
-  }
-};
-// Upper triangle: right-hand side from v32 (in place), result to v32 and, widened and scaled
-// by 2^e, to the w-component output.
-template <int W, int CP, typename TS>
-struct RowUp32 {
-  const int* rp;
-  const int* diag;
-  const TS* f;
-  double* out;
-  float* v32;
-  bool unit;
-  int e;
-  float ar, ai;
-  __device__ void begin(int i, int& p, int& pend) {
-    p = diag[i] + 1;
-    pend = rp[i + 1];
-    if constexpr (CP == 1) { ar = v32[i]; ai = 0.0f; }
-    else { ar = v32[2 * (int64_t)i]; ai = v32[2 * (int64_t)i + 1]; }
-  }
-  __device__ void consume(int, int p, int j) {
-    if constexpr (CP == 1) {
-      ar = fmaf(-ld_fac(f, p), v32[j], ar);
-    } else {
-      const float lr = ld_fac(f, 2 * (int64_t)p), li = ld_fac(f, 2 * (int64_t)p + 1);
-      const float yr = v32[2 * (int64_t)j], yi = v32[2 * (int64_t)j + 1];
-      ar = fmaf(-lr, yr, ar);
-      ar = fmaf(li, yi, ar);
-      ai = fmaf(-lr, yi, ai);
-      ai = fmaf(-li, yr, ai);
-    }
-  }
-  __device__ void finish(int i) {
+  __device__ Val finish() {
     if (!unit) {
       const int d = diag[i];
       if constexpr (CP == 1) {
@@ -596,36 +749,78 @@ struct RowUp32 {
         ai = ni / den;
       }
     }
-    N<W, CP> z = n_zero<W, CP>();
-    z.re.c[0] = ldexp((double)ar, e);
-    if constexpr (CP == 2) z.im.c[0] = ldexp((double)ai, e);
-    n_store<W, CP>(out, i, z);
-    if constexpr (CP == 1) v32[i] = ar;
-    else { v32[2 * (int64_t)i] = ar; v32[2 * (int64_t)i + 1] = ai; }
+    if constexpr (CP == 1) return ar;
+    else return make_float2(ar, ai);
+  }
+  __device__ void publish(const Val& v) {
+    const unsigned long long hi = (unsigned long long)epoch << 32;
+    if constexpr (CP == 1) {
+      v32[i] = v;
+      st_relaxed_u64(pk + i, hi | __float_as_uint(v));
+    } else {
+      v32[2 * (int64_t)i] = v.x;
+      v32[2 * (int64_t)i + 1] = v.y;
+      st_relaxed_u64(pk + 2 * (int64_t)i, hi | __float_as_uint(v.x));
+      st_relaxed_u64(pk + 2 * (int64_t)i + 1, hi | __float_as_uint(v.y));
+    }
+    if (!lower) {
+      N<W, CP> z = n_zero<W, CP>();
+      if constexpr (CP == 1) {
+        z.re.c[0] = ldexp((double)v, e);
+      } else {
+        z.re.c[0] = ldexp((double)v.x, e);
+        z.im.c[0] = ldexp((double)v.y, e);
+      }
+      n_store<W, CP>(out, i, z);
+    }
   }
 };
+template <int W, int CP, typename TS>
+__global__ void __launch_bounds__(kBlock) k_trsv_pk32(IluHandleView M, bool lower, bool unit,
+                                                      const double* __restrict__ in, double* __restrict__ out,
+                                                      const int* __restrict__ done) {
+  if (is_done(done)) return;
+  RowPk32<W, CP, TS> row;
+  row.rp = M.rp;
+  row.diag = M.diag;
+  row.f = (const TS*)M.fac;
+  row.v32 = M.v32;
+  row.pk = M.pk;
+  row.in = in;
+  row.out = out;
+  row.epoch = (unsigned)M.ctl[CTL_EPOCH] + (lower ? 0u : 1u);
+  row.lower = lower;
+  row.unit = unit;
+  row.e = scale_exponent(M.absmax);
+  syncfree_rows(lower ? M.ch_lo : M.ch_up, M.ci, M.ctl + (lower ? CTL_TICKET_LO : CTL_TICKET_UP), M.ctl, row);
+}
+
 // Binary64 factor, w-component vectors (paper's "_d" substitutions).
 template <int W, int CP>
 struct RowMp {
+  using Val = N<W, CP>;
   const int* rp;
   const int* diag;
   const double* f;
   const double* in;
   double* out;
   bool lower, unit;
+  int i;
   N<W, CP> acc;
-  __device__ void begin(int i, int& p, int& pend) {
-    if (lower) { p = rp[i]; pend = diag[i]; }
-    else { p = diag[i] + 1; pend = rp[i + 1]; }
-    acc = n_load<W, CP>(in, i);
+  __device__ void begin(int i_, int& p, int& pend) {
+    i = i_;
+    if (lower) { p = rp[i_]; pend = diag[i_]; }
+    else { p = diag[i_] + 1; pend = rp[i_ + 1]; }
+    acc = n_load<W, CP>(in, i_);
   }
-  __device__ void consume(int, int p, int j) {
+  __device__ Val load(int j) { return n_load<W, CP>(out, j); }
+  __device__ void consume(int p, int, const Val& v) {
     double fr, fi = 0.0;
     if constexpr (CP == 1) fr = f[p];
     else { fr = f[2 * (int64_t)p]; fi = f[2 * (int64_t)p + 1]; }
-    acc = n_sub<W, CP>(acc, n_mul_fp<W, CP>(n_load<W, CP>(out, j), fr, fi));
+    acc = n_sub<W, CP>(acc, n_mul_fp<W, CP>(v, fr, fi));
   }
-  __device__ void finish(int i) {
+  __device__ Val finish() {
     if (!unit) {
       const int d = diag[i];
       double fr, fi = 0.0;
@@ -633,24 +828,11 @@ struct RowMp {
       else { fr = f[2 * (int64_t)d]; fi = f[2 * (int64_t)d + 1]; }
       acc = n_div_fp<W, CP>(acc, fr, fi);
     }
-    n_store<W, CP>(out, i, acc);
+    return acc;
   }
+  __device__ void store(const Val& v) { n_store<W, CP>(out, i, v); }
 };
 
-template <int W, int CP, typename TS>
-__global__ void __launch_bounds__(kBlock) k_trsv_lo32(IluHandleView M, bool unit, const double* __restrict__ in,
-                                                      const int* __restrict__ done) {
-  if (is_done(done)) return;
-  RowLo32<W, CP, TS> row{M.rp, M.diag, (const TS*)M.fac, in, M.v32, unit, scale_exponent(M.absmax), 0.f, 0.f};
-  syncfree_rows(M.n, true, M.ci, M.flags, M.ctl[CTL_EPOCH], M.ctl + CTL_TICKET_LO, M.ctl, row);
-}
-template <int W, int CP, typename TS>
-__global__ void __launch_bounds__(kBlock) k_trsv_up32(IluHandleView M, bool unit, double* __restrict__ out,
-                                                      const int* __restrict__ done) {
-  if (is_done(done)) return;
-  RowUp32<W, CP, TS> row{M.rp, M.diag, (const TS*)M.fac, out, M.v32, unit, scale_exponent(M.absmax), 0.f, 0.f};
-  syncfree_rows(M.n, false, M.ci, M.flags, M.ctl[CTL_EPOCH] + 1, M.ctl + CTL_TICKET_UP, M.ctl, row);
-}
 template <int W, int CP>
 __global__ void __launch_bounds__(kBlock) k_trsv_mp(IluHandleView M, bool lower, bool unit,
                                                     const double* __restrict__ in, double* __restrict__ out,
@@ -664,8 +846,8 @@ __global__ void __launch_bounds__(kBlock) k_trsv_mp(IluHandleView M, bool lower,
   row.out = out;
   row.lower = lower;
   row.unit = unit;
-  syncfree_rows(M.n, lower, M.ci, M.flags, M.ctl[CTL_EPOCH] + (lower ? 0 : 1),
-                M.ctl + (lower ? CTL_TICKET_LO : CTL_TICKET_UP), M.ctl, row);
+  chunk_rows(lower ? M.lv_lo : M.lv_up, M.ci, M.ctl[CTL_EPOCH] + (lower ? 0 : 1),
+             M.ctl + (lower ? CTL_TICKET_LO : CTL_TICKET_UP), M.ctl, row);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -676,17 +858,23 @@ inline int grid_for(int n) {
   const int cap = sm_count() * 8;
   return g < 1 ? 1 : (g > cap ? cap : g);
 }
+// Blocks of the dependency-driven kernels: at most `resident_warps_per_sm()` warps per SM (fewer
+// waiting warps poll less), capped by occupancy.
 template <class KernelT>
 inline int persistent_blocks(KernelT kernel) {
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0) != cudaSuccess || per_sm < 1)
     per_sm = 1;
+  int want = resident_warps_per_sm() / (kBlock / 32);
+  if (want < 1) want = 1;
+  if (want < per_sm) per_sm = want;
   return per_sm * sm_count();
 }
 
 template <int W, int CP>
 struct Launch {
   static void spmv(const Csr& A, const double* x, double* y, const double* b, const int* done, cudaStream_t s) {
+    count_launch();
     k_spmv<W, CP><<<(A.n + kBlock - 1) / kBlock, kBlock, 0, s>>>(A.n, A.rp, A.ci, A.val, x, y, b, done);
   }
   template <int K>
@@ -698,6 +886,7 @@ struct Launch {
       args.b[k] = b[k];
       args.out[k] = out[k];
     }
+    count_launch();
     k_dots<W, CP, K><<<dot_blocks(n), kBlock, 0, s>>>(n, args, ws.partial, ws.counter, done);
   }
   static void dots(int n, int k, const double* const* a, const double* const* b, double* const* out, const DotWs& ws,
@@ -716,44 +905,42 @@ struct Launch {
       a.v[k] = k < nt ? v[k] : nullptr;
       a.s[k] = k < nt ? coef[k] : nullptr;
     }
+    count_launch();
     k_lincomb<W, CP><<<grid_for(n), kBlock, 0, s>>>(n, a, done);
   }
   static void nested(int n, double* y, const double* v0, const double* v1, const double* v2, const double* s1,
                      const double* s2, const int* copy_at_first, const int* done, cudaStream_t s) {
+    count_launch();
     k_nested<W, CP><<<grid_for(n), kBlock, 0, s>>>(n, y, v0, v1, v2, s1, s2, copy_at_first, done);
   }
   static void copy(int n, double* y, const double* x, const int* done, cudaStream_t s) {
+    count_launch();
     k_copy<W, CP><<<grid_for(n), kBlock, 0, s>>>(n, y, x, done);
   }
   static void scalar(int method, int phase, double* S, int* st, double* hist, const int* done, cudaStream_t s) {
+    count_launch();
     k_scalar<W, CP><<<1, 32, 0, s>>>(method, phase, S, st, hist, done);
   }
   static void absmax(int n, const double* v, unsigned long long* out, const int* done, cudaStream_t s) {
+    count_launch();
     k_absmax<W, CP><<<grid_for(n), kBlock, 0, s>>>(n, v, out, done);
   }
   static int trsv_mp(const IluHandleView& M, bool lower, bool unit, const double* in, double* out, const int* done,
                      cudaStream_t s) {
     static int blocks = persistent_blocks(k_trsv_mp<W, CP>);
+    count_launch();
     k_trsv_mp<W, CP><<<blocks, kBlock, 0, s>>>(M, lower, unit, in, out, done);
     return cudaGetLastError() == cudaSuccess ? MPK_OK : MPK_CUDA_ERROR;
   }
-  static int trsv_lo32(const IluHandleView& M, bool unit, const double* in, const int* done, cudaStream_t s) {
+  static int trsv32(const IluHandleView& M, bool lower, bool unit, const double* in, double* out, const int* done,
+                    cudaStream_t s) {
+    count_launch();
     if (M.prec == MPK_ILU_BF16) {
-      static int blocks = persistent_blocks(k_trsv_lo32<W, CP, uint16_t>);
-      k_trsv_lo32<W, CP, uint16_t><<<blocks, kBlock, 0, s>>>(M, unit, in, done);
+      static int blocks = persistent_blocks(k_trsv_pk32<W, CP, uint16_t>);
+      k_trsv_pk32<W, CP, uint16_t><<<blocks, kBlock, 0, s>>>(M, lower, unit, in, out, done);
     } else {
-      static int blocks = persistent_blocks(k_trsv_lo32<W, CP, float>);
-      k_trsv_lo32<W, CP, float><<<blocks, kBlock, 0, s>>>(M, unit, in, done);
-    }
-    return cudaGetLastError() == cudaSuccess ? MPK_OK : MPK_CUDA_ERROR;
-  }
-  static int trsv_up32(const IluHandleView& M, bool unit, double* out, const int* done, cudaStream_t s) {
-    if (M.prec == MPK_ILU_BF16) {
-      static int blocks = persistent_blocks(k_trsv_up32<W, CP, uint16_t>);
-      k_trsv_up32<W, CP, uint16_t><<<blocks, kBlock, 0, s>>>(M, unit, out, done);
-    } else {
-      static int blocks = persistent_blocks(k_trsv_up32<W, CP, float>);
-      k_trsv_up32<W, CP, float><<<blocks, kBlock, 0, s>>>(M, unit, out, done);
+      static int blocks = persistent_blocks(k_trsv_pk32<W, CP, float>);
+      k_trsv_pk32<W, CP, float><<<blocks, kBlock, 0, s>>>(M, lower, unit, in, out, done);
     }
     return cudaGetLastError() == cudaSuccess ? MPK_OK : MPK_CUDA_ERROR;
   }
@@ -768,8 +955,7 @@ struct Launch {
     o.copy = &copy;
     o.scalar = &scalar;
     o.trsv_mp = &trsv_mp;
-    o.trsv_lo32 = &trsv_lo32;
-    o.trsv_up32 = &trsv_up32;
+    o.trsv32 = &trsv32;
     o.absmax = &absmax;
     return o;
   }
