@@ -125,6 +125,24 @@ int mpk_spmv_mp(const mpk_csr* A, int w, const double* x_dev, double* y_dev, voi
 int mpk_dot(int n, int is_complex, int w, const double* a_dev, const double* b_dev, double* out_dev,
             void* stream);
 
+/* The same inner product as mpk_dot, for callers that must not let the library allocate device
+ * memory (the paper has no counterpart: this is a property of the library, not of the method).
+ * Examples: a host that gives the library a fixed device-memory budget, a latency-critical loop
+ * in which an allocation could synchronise the device, a plugin whose allocator owns all device
+ * memory.  No cudaMalloc / cudaFree / pool allocation happens: the reduction scratch is a fixed
+ * device array inside the library (256 KiB, kept by every GPU that loads the library until the
+ * process exits).
+ *   - n must not exceed MPK_DOT_NOALLOC_MAX_N; larger n returns MPK_INVALID_ARG (use mpk_dot).
+ *   - The first call on each device looks up the scratch's device address (cudaGetSymbolAddress)
+ *     and caches it; make that first call before any stream capture on that device.
+ *   - All calls share the one scratch array, which keeps the last call's contents (the call
+ *     clears the part that must start at zero).  Calls that overlap on the GPU -- on different
+ *     streams, or on host threads without ordering -- race on it: serialise them.
+ * Result, layout and summation order are those of mpk_dot (bit-identical results). */
+#define MPK_DOT_NOALLOC_MAX_N 16777216
+int mpk_dot_noalloc(int n, int is_complex, int w, const double* a_dev, const double* b_dev, double* out_dev,
+                    void* stream);
+
 /* ILU(0) of A (Algorithm 1; the "!= 0" tests read as membership in A's stored pattern; the
  * update A_ij -= L_ik U_kj is one fused multiply-add; a zero pivot is an error instead of
  * being skipped).  Rows are factored by a dependency-driven device kernel; the result equals

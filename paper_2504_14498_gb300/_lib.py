@@ -51,6 +51,7 @@ SIGNATURES = [
     ("mpk_kernel_launches", ctypes.c_uint64, []),
     ("mpk_spmv_mp", _I, [ctypes.POINTER(CsrDesc), _I, _VP, _VP, _VP]),
     ("mpk_dot", _I, [_I, _I, _I, _VP, _VP, _VP, _VP]),
+    ("mpk_dot_noalloc", _I, [_I, _I, _I, _VP, _VP, _VP, _VP]),
     ("mpk_ilu0_factor", _I, [ctypes.POINTER(CsrDesc), _I, ctypes.POINTER(_VP), ctypes.POINTER(_I), _VP]),
     ("mpk_ilu0_values", _I, [_VP, _VP, _VP]),
     ("mpk_ilu0_prec", _I, [_VP]),
@@ -130,6 +131,16 @@ def dot(a: torch.Tensor, b: torch.Tensor, n: int, w: int, is_complex=False) -> t
     """<a, b> = sum conj(a_i) b_i; returns a device tensor of c*w doubles."""
     out = torch.empty((2 if is_complex else 1) * w, dtype=torch.float64, device=a.device)
     _check(lib().mpk_dot(n, int(is_complex), w, _ptr(a), _ptr(b), _ptr(out), _stream()))
+    return out
+
+
+def dot_noalloc(a: torch.Tensor, b: torch.Tensor, n: int, w: int, is_complex=False, out: torch.Tensor = None):
+    """Same as dot(), for callers that must not let the library allocate device memory: the
+    reduction scratch is a fixed array inside the library (n <= MPK_DOT_NOALLOC_MAX_N).  `out`
+    may be preallocated by the caller (c*w doubles)."""
+    if out is None:
+        out = torch.empty((2 if is_complex else 1) * w, dtype=torch.float64, device=a.device)
+    _check(lib().mpk_dot_noalloc(n, int(is_complex), w, _ptr(a), _ptr(b), _ptr(out), _stream()))
     return out
 
 
