@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=1, help="oracle iterations in the CPU sample")
+    ap.add_argument("--only", default=None, choices=["spmv", "precond_fp64", "precond_fp32", "precond_bf16", "ilu_fp64"],
+                    help="run just this kernel --reps times on the workload (for profiling) and exit")
+    ap.add_argument("--reps", type=int, default=3)
     return ap.parse_args()
 
 
@@ -336,8 +339,40 @@ def run_mpk(args):
     return 0
 
 
+def run_only(args):
+    """One kernel family on the bench workload, `reps` times: the case the ncu captures profile."""
+    import torch
+
+    from paper_2504_14498_gb300 import _lib, inputs
+
+    torch.cuda.set_device(0)
+    A_t, _ = inputs.convdiff3d(args.m)
+    n, w = A_t[0], 2
+    A = _lib.Matrix.from_tuple(A_t)
+    x = torch.as_tensor(inputs.random_vector(n, w, 1, seed=3), device="cuda")
+    y = torch.empty_like(x)
+    if args.only == "spmv":
+        fn = lambda: _lib.spmv_mp(A, x, w, y)
+    elif args.only == "ilu_fp64":
+        fn = lambda: _lib.ILU0(A, "fp64").close()
+    else:
+        M = _lib.ILU0(A, args.only.split("_")[1])
+        fn = lambda: M.apply(x, w, False, y)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"only": args.only, "m": args.m, "reps": args.reps, "ms_per_rep": e0.elapsed_time(e1) / args.reps}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.only:
+        return run_only(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_mpk(args)

@@ -531,6 +531,110 @@ static int build_levels(int n, const int* rp, const int* ci, const int* diag, un
   return MPK_OK;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Repacking of a binary64 triangle into the SELL-32 layout of the static substitution schedule
+// (see SellTri): one warp per chunk computes its width (the longest row of the triangle among
+// its 32 rows), a scan gives the slot-block offsets, then every position copies its row.
+// ---------------------------------------------------------------------------------------------
+__global__ void k_sell_width(int nchunks, const int* __restrict__ perm, const int* __restrict__ rp,
+                             const int* __restrict__ diag, bool lower, int* __restrict__ width) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += warps) {
+    const int i = perm[c * 32 + lane];
+    int len = 0;
+    if (i >= 0) len = lower ? diag[i] - rp[i] : rp[i + 1] - diag[i] - 1;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, off));
+    if (lane == 0) width[c] = len;
+  }
+}
+// Also records, per chunk, the dependency with the largest level-order position (rep): the
+// substitution polls that one value before checking all the others.  The 32 positions of a chunk
+// are the 32 lanes of one warp (blockDim and the stride are multiples of 32).
+template <int CP>
+__global__ void k_sell_fill(int nchunks, const int* __restrict__ perm, const int* __restrict__ pos,
+                            const int* __restrict__ rp, const int* __restrict__ ci, const int* __restrict__ diag,
+                            const double* __restrict__ fac, bool lower, const int* __restrict__ coff,
+                            int* __restrict__ col, double* __restrict__ val, double* __restrict__ dia,
+                            int* __restrict__ rep) {
+  const int64_t P = (int64_t)nchunks * 32;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < P; q += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(q >> 5), lane = (int)(q & 31);
+    const int i = perm[q];
+    int p = 0, len = 0;
+    if (i >= 0) {
+      p = lower ? rp[i] : diag[i] + 1;
+      len = lower ? diag[i] - rp[i] : rp[i + 1] - diag[i] - 1;
+    }
+    const int b0 = coff[c], w = coff[c + 1] - b0;
+    int last = -1;
+    for (int k = 0; k < w; ++k) {
+      const int64_t e = ((int64_t)(b0 + k) << 5) + lane;
+      col[e] = k < len ? ci[p + k] : -1;
+      if (k < len) last = max(last, pos[ci[p + k]]);
+#pragma unroll
+      for (int t = 0; t < CP; ++t) val[e * CP + t] = k < len ? fac[(int64_t)(p + k) * CP + t] : 0.0;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) last = max(last, __shfl_xor_sync(0xffffffffu, last, off));
+    if (lane == 0) rep[c] = last >= 0 ? perm[last] : -1;
+#pragma unroll
+    for (int t = 0; t < CP; ++t) dia[q * CP + t] = i >= 0 ? fac[(int64_t)diag[i] * CP + t] : (t == 0 ? 1.0 : 0.0);
+  }
+}
+
+// Repack one triangle of (rp, ci, diag, fac) in the positions of its level order into *buf
+// (allocated here) and describe it in *out.
+static int build_sell(int n, int cp, const int* rp, const int* ci, const int* diag, const double* fac, int* lvbuf,
+                      int nlevels, bool lower, void** buf, SellTri* out, cudaStream_t s) {
+  const LevelOrder lo = level_view(lvbuf, n, nlevels);
+  int nch = 0;
+  MPK_CUDA(cudaMemcpyAsync(&nch, lo.nchunks, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MPK_CUDA(cudaStreamSynchronize(s));
+  int* width = nullptr;
+  MPK_CUDA(cudaMallocAsync((void**)&width, sizeof(int) * ((size_t)nch + 1) * 2, s));
+  int* coff_tmp = width + nch + 1;
+  count_launch(2);
+  k_sell_width<<<grid_for(nch * 32), kBlock, 0, s>>>(nch, lo.perm, rp, diag, lower, width);
+  k_scan_single<<<1, 1024, 0, s>>>(nch, width, coff_tmp);
+  int total = 0;
+  MPK_CUDA(cudaMemcpyAsync(&total, coff_tmp + nch, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MPK_CUDA(cudaStreamSynchronize(s));
+  const size_t slots = (size_t)total * 32;
+  const size_t coff_b = ((sizeof(int) * ((size_t)nch + 1)) + 255) & ~(size_t)255;
+  const size_t col_b = ((sizeof(int) * slots) + 255) & ~(size_t)255;
+  const size_t val_b = ((sizeof(double) * slots * cp) + 255) & ~(size_t)255;
+  const size_t dia_b = ((sizeof(double) * (size_t)nch * 32 * cp) + 255) & ~(size_t)255;
+  const size_t rep_b = sizeof(int) * (size_t)nch;
+  char* b = nullptr;
+  MPK_CUDA(cudaMalloc((void**)&b, coff_b + col_b + val_b + dia_b + rep_b + 256));
+  int* coff = (int*)b;
+  int* col = (int*)(b + coff_b);
+  double* val = (double*)(b + coff_b + col_b);
+  double* dia = (double*)(b + coff_b + col_b + val_b);
+  int* rep = (int*)(b + coff_b + col_b + val_b + dia_b);
+  MPK_CUDA(cudaMemcpyAsync(coff, coff_tmp, sizeof(int) * ((size_t)nch + 1), cudaMemcpyDeviceToDevice, s));
+  count_launch();
+  if (cp == 1)
+    k_sell_fill<1><<<grid_for(nch * 32), kBlock, 0, s>>>(nch, lo.perm, lo.pos, rp, ci, diag, fac, lower, coff, col,
+                                                          val, dia, rep);
+  else
+    k_sell_fill<2><<<grid_for(nch * 32), kBlock, 0, s>>>(nch, lo.perm, lo.pos, rp, ci, diag, fac, lower, coff, col,
+                                                          val, dia, rep);
+  MPK_CUDA(cudaGetLastError());
+  MPK_CUDA(cudaFreeAsync(width, s));
+  *buf = b;
+  out->perm = lo.perm;
+  out->coff = coff;
+  out->col = col;
+  out->val = val;
+  out->dia = dia;
+  out->rep = rep;
+  out->nchunks = nch;
+  return MPK_OK;
+}
+
 void launch_trsv_prep(const IluHandleView& M, const int* done, cudaStream_t s) {
   count_launch();
   k_trsv_prep<<<1, 1, 0, s>>>(M.ctl, M.absmax, done);
@@ -563,7 +667,14 @@ static int build_transpose(mpk_ilu* M, cudaStream_t s) {
                                                M->ciT, (uint16_t*)M->facT, M->diagT, s);
   }
   if (st != MPK_OK) return st;
-  return build_levels(M->n, M->rpT, M->ciT, M->diagT, M->pk, M->ctl, 1, M->lvbuf + 2, M->nlevels + 2, s);
+  st = build_levels(M->n, M->rpT, M->ciT, M->diagT, M->pk, M->ctl, 1, M->lvbuf + 2, M->nlevels + 2, s);
+  if (st != MPK_OK || M->prec != MPK_ILU_FP64) return st;
+  for (int t = 2; t < 4; ++t) {
+    st = build_sell(M->n, M->cp, M->rpT, M->ciT, M->diagT, (const double*)M->facT, M->lvbuf[t], M->nlevels[t], t == 2,
+                    M->sellbuf + t, M->sell + t, s);
+    if (st != MPK_OK) return st;
+  }
+  return MPK_OK;
 }
 
 int prepare_trans(mpk_ilu* M, cudaStream_t s) { return build_transpose(M, s); }
@@ -599,7 +710,8 @@ int read_ctl_err(const mpk_ilu* M, cudaStream_t s) {
 static void free_handle(mpk_ilu* M) {
   if (M == nullptr) return;
   void* ptrs[] = {M->rp, M->ci, M->diag, M->fac, M->rpT, M->ciT, M->diagT, M->facT, M->flags, M->ctl, M->v32, M->vmp,
-                  M->absmax, M->pk, M->lvbuf[0], M->lvbuf[1], M->lvbuf[2], M->lvbuf[3]};
+                  M->absmax, M->pk, M->lvbuf[0], M->lvbuf[1], M->lvbuf[2], M->lvbuf[3],
+                  M->sellbuf[0], M->sellbuf[1], M->sellbuf[2], M->sellbuf[3]};
   for (void* p : ptrs)
     if (p != nullptr) cudaFree(p);
   delete M;
@@ -630,6 +742,8 @@ IluHandleView mpk_ilu::view(bool trans) const {
   v.lv_up = level_view(lvbuf[t + 1], n, nlevels[t + 1]);
   v.ch_lo = chunk_view(lvbuf[t], n, nlevels[t]);
   v.ch_up = chunk_view(lvbuf[t + 1], n, nlevels[t + 1]);
+  v.sl_lo = sell[t];
+  v.sl_up = sell[t + 1];
   return v;
 }
 
@@ -732,6 +846,11 @@ static int factor_impl(const mpk_csr* A, int prec, mpk_ilu** out, int* fail_row,
   }
   if (prec == MPK_ILU_FP64) {
     MPK_TRY(cudaMalloc((void**)&M->vmp, sizeof(double) * (size_t)n * cp * 4));
+    for (int t = 0; t < 2; ++t) {
+      int st = build_sell(n, cp, M->rp, M->ci, M->diag, (const double*)M->fac, M->lvbuf[t], M->nlevels[t], t == 0,
+                          M->sellbuf + t, M->sell + t, s);
+      if (st != MPK_OK) return bail(st);
+    }
   } else {
     MPK_TRY(cudaMalloc((void**)&M->v32, sizeof(float) * (size_t)n * cp));
   }

@@ -795,59 +795,220 @@ __global__ void __launch_bounds__(kBlock) k_trsv_pk32(IluHandleView M, bool lowe
   syncfree_rows(lower ? M.ch_lo : M.ch_up, M.ci, M.ctl + (lower ? CTL_TICKET_LO : CTL_TICKET_UP), M.ctl, row);
 }
 
-// Binary64 factor, w-component vectors (paper's "_d" substitutions).
+// Binary64 factor, w-component vectors (paper's "_d" substitutions): row i computes
+//   acc = in_i;  acc -= f_ij * out_j  for the row's entries of the triangle in CSR order;
+//   upper triangle: acc /= f_ii;  out_i = acc,
+// every product and difference in w-component arithmetic (the sequential order of Algorithm 2).
+//
+// Schedule (static, balanced): the rows come in their triangle's level order, every level
+// padded to whole 32-row chunks, from the repacked triangle (SellTri: coalesced columns and
+// values per chunk).  The grid has one block per SM and kTrsvWarps warps per block, all
+// co-resident (cooperative launch); chunk c belongs to warp c mod G (G = warps in the grid),
+// numbered so that consecutive chunks of a level fall on different SMs and, once every SM has
+// one, on the next sub-partition.  A level of up to G chunks thus puts at most one chunk on each
+// FP64 unit: on this GPU an FP64 warp instruction holds its sub-partition's unit for 64 cycles
+// whatever the number of active lanes, so a level costs one chunk's instruction count, not a
+// multiple of it.  Each warp walks its chunks in increasing order; every dependency of a chunk
+// lies in an earlier level, i.e. in a smaller chunk, so the smallest unfinished chunk can always
+// proceed (no deadlock).
+// Completion is carried by the values themselves: before the pass, `out` is filled with the
+// sentinel bit pattern kSent (k_fill_sent), a finished row stores its w-component value with
+// strong relaxed 64-bit stores (a computed value equal to kSent is stored as another NaN), and a
+// dependent row polls those words with strong relaxed loads until none is kSent.  Each word is
+// written once per pass, so a word that is not kSent is final: no flag, no fence.  The next
+// chunk's positions and slot block are fetched one chunk ahead.  Every wait is bounded by
+// kWaitCycles (then MPK_TIMEOUT in ctl[CTL_ERR] and all warps leave).
+constexpr int kTrsvWarps = 4;
+constexpr long long kSpinCycles = 40000;  // ~20 us of polling without sleeping
+constexpr unsigned long long kSent = 0xFFFFFFFFFFFFFFFFull;
+
+__device__ __forceinline__ double ld_relaxed_f64(const double* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return __longlong_as_double((long long)v);
+}
+__device__ __forceinline__ void st_relaxed_f64(double* p, double x) {
+  unsigned long long v = (unsigned long long)__double_as_longlong(x);
+  if (v == kSent) v = 0x7FF8000000000000ull;  // never publish the sentinel
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 template <int W, int CP>
-struct RowMp {
-  using Val = N<W, CP>;
-  const int* rp;
-  const int* diag;
-  const double* f;
-  const double* in;
-  double* out;
-  bool lower, unit;
-  int i;
-  N<W, CP> acc;
-  __device__ void begin(int i_, int& p, int& pend) {
-    i = i_;
-    if (lower) { p = rp[i_]; pend = diag[i_]; }
-    else { p = diag[i_] + 1; pend = rp[i_ + 1]; }
-    acc = n_load<W, CP>(in, i_);
+__device__ __forceinline__ void n_fetch(const double* __restrict__ v, int64_t i, N<W, CP>& z) {
+  const double* p = v + i * (CP * W);
+#pragma unroll
+  for (int k = 0; k < W; ++k) z.re.c[k] = ld_relaxed_f64(p + k);
+  if constexpr (CP == 2) {
+#pragma unroll
+    for (int k = 0; k < W; ++k) z.im.c[k] = ld_relaxed_f64(p + W + k);
   }
-  __device__ Val load(int j) { return n_load<W, CP>(out, j); }
-  __device__ void consume(int p, int, const Val& v) {
-    double fr, fi = 0.0;
-    if constexpr (CP == 1) fr = f[p];
-    else { fr = f[2 * (int64_t)p]; fi = f[2 * (int64_t)p + 1]; }
-    acc = n_sub<W, CP>(acc, n_mul_fp<W, CP>(v, fr, fi));
+}
+template <int W, int CP>
+__device__ __forceinline__ bool n_ready(const N<W, CP>& z) {  // no word is the sentinel
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < W; ++k) ok = ok && (unsigned long long)__double_as_longlong(z.re.c[k]) != kSent;
+  if constexpr (CP == 2) {
+#pragma unroll
+    for (int k = 0; k < W; ++k) ok = ok && (unsigned long long)__double_as_longlong(z.im.c[k]) != kSent;
   }
-  __device__ Val finish() {
-    if (!unit) {
-      const int d = diag[i];
-      double fr, fi = 0.0;
-      if constexpr (CP == 1) fr = f[d];
-      else { fr = f[2 * (int64_t)d]; fi = f[2 * (int64_t)d + 1]; }
-      acc = n_div_fp<W, CP>(acc, fr, fi);
-    }
-    return acc;
+  return ok;
+}
+template <int W, int CP>
+__device__ __forceinline__ bool n_poll(const double* __restrict__ v, int64_t i, N<W, CP>& z) {
+  n_fetch<W, CP>(v, i, z);
+  return n_ready<W, CP>(z);
+}
+template <int W, int CP>
+__device__ __forceinline__ void n_publish(double* __restrict__ v, int64_t i, const N<W, CP>& z) {
+  double* p = v + i * (CP * W);
+#pragma unroll
+  for (int k = 0; k < W; ++k) st_relaxed_f64(p + k, z.re.c[k]);
+  if constexpr (CP == 2) {
+#pragma unroll
+    for (int k = 0; k < W; ++k) st_relaxed_f64(p + W + k, z.im.c[k]);
   }
-  __device__ void store(const Val& v) { n_store<W, CP>(out, i, v); }
-};
+}
+static __global__ void __launch_bounds__(kBlock) k_fill_sent(int64_t m, double* __restrict__ a, int64_t mb,
+                                                      double* __restrict__ b, const int* __restrict__ done) {
+  if (is_done(done)) return;
+  const double s = __longlong_as_double((long long)kSent);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m + mb; k += (int64_t)gridDim.x * blockDim.x) {
+    if (k < m) a[k] = s;
+    else b[k - m] = s;
+  }
+}
 
 template <int W, int CP>
-__global__ void __launch_bounds__(kBlock) k_trsv_mp(IluHandleView M, bool lower, bool unit,
-                                                    const double* __restrict__ in, double* __restrict__ out,
-                                                    const int* __restrict__ done) {
+__global__ void __launch_bounds__(kTrsvWarps * 32, 1)
+    k_trsv_mp(IluHandleView M, bool lower, bool unit, const double* __restrict__ in, double* __restrict__ out,
+              const int* __restrict__ done) {
   if (is_done(done)) return;
-  RowMp<W, CP> row;
-  row.rp = M.rp;
-  row.diag = M.diag;
-  row.f = (const double*)M.fac;
-  row.in = in;
-  row.out = out;
-  row.lower = lower;
-  row.unit = unit;
-  chunk_rows(lower ? M.lv_lo : M.lv_up, M.ci, M.ctl[CTL_EPOCH] + (lower ? 0 : 1),
-             M.ctl + (lower ? CTL_TICKET_LO : CTL_TICKET_UP), M.ctl, row);
+  constexpr int kPre = 4;  // slots held in registers (longer rows stream the rest)
+  const unsigned FULL = 0xffffffffu;
+  const SellTri T = lower ? M.sl_lo : M.sl_up;
+  const int lane = threadIdx.x & 31;
+  const int G = gridDim.x * (blockDim.x >> 5);
+  const int g = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+  // one chunk ahead: position's row, the chunk's slot block and its latest dependency
+  int nx_i = -1, nx_b0 = 0, nx_b1 = 0, nx_rep = -1;
+  if (g < T.nchunks) {
+    nx_i = T.perm[(g << 5) + lane];
+    nx_b0 = T.coff[g];
+    nx_b1 = T.coff[g + 1];
+    nx_rep = T.rep[g];
+  }
+  for (int chunk = g; chunk < T.nchunks; chunk += G) {
+    const int i = nx_i, b0 = nx_b0, w = nx_b1 - nx_b0, rep = nx_rep;
+    // this chunk's slots, right-hand side and diagonal
+    int jj[kPre];
+    double fr[kPre], fi[kPre];
+#pragma unroll
+    for (int k = 0; k < kPre; ++k) {
+      jj[k] = -1;
+      fr[k] = 0.0;
+      fi[k] = 0.0;
+      if (k < w) {
+        const int64_t e = ((int64_t)(b0 + k) << 5) + lane;
+        jj[k] = T.col[e];
+        if constexpr (CP == 1) fr[k] = T.val[e];
+        else { fr[k] = T.val[2 * e]; fi[k] = T.val[2 * e + 1]; }
+      }
+    }
+    N<W, CP> acc = n_zero<W, CP>();
+    double dr = 1.0, di = 0.0;
+    if (i >= 0) {
+      acc = n_load<W, CP>(in, i);
+      if (!unit) {
+        const int64_t q = ((int64_t)chunk << 5) + lane;
+        if constexpr (CP == 1) dr = T.dia[q];
+        else { dr = T.dia[2 * q]; di = T.dia[2 * q + 1]; }
+      }
+    }
+    // fetch the next chunk's position and slot block while this one waits
+    const int nc = chunk + G;
+    if (nc < T.nchunks) {
+      nx_i = T.perm[(nc << 5) + lane];
+      nx_b0 = T.coff[nc];
+      nx_b1 = T.coff[nc + 1];
+      nx_rep = T.rep[nc];
+    }
+    // wait for the held dependencies: poll their values until no word is the sentinel
+    N<W, CP> v[kPre];
+    unsigned need = 0u;
+#pragma unroll
+    for (int k = 0; k < kPre; ++k) {
+      v[k] = n_zero<W, CP>();
+      if (jj[k] >= 0) need |= 1u << k;
+    }
+    bool timeout = false;
+    const long long t0 = clock64();
+    int polls = 0;
+    // lane 0 alone polls the latest dependency (one address instead of every lane's): polling
+    // from many lanes loads the SM enough to slow the FP64 arithmetic of its other warps
+    if (lane == 0 && rep >= 0) {
+      N<W, CP> r;
+      while (!n_poll<W, CP>(out, rep, r)) {
+        const long long dt = clock64() - t0;
+        if (dt > kWaitCycles || ((++polls & 63) == 0 && ld_relaxed(M.ctl + CTL_ERR) != 0)) {
+          timeout = true;
+          break;
+        }
+        if (dt > kSpinCycles) __nanosleep(128);
+      }
+    }
+    __syncwarp();
+    // the loop and the arithmetic after it are warp-uniform: lanes that leave the polling loop
+    // early must not run the FP64 arithmetic as a separate divergent group (every FP64 warp
+    // instruction costs the same pipe time however few lanes are active)
+    while (__any_sync(FULL, need != 0u && !timeout)) {
+      // every outstanding load of the round is issued before any is checked
+#pragma unroll
+      for (int k = 0; k < kPre; ++k)
+        if ((need >> k) & 1u) n_fetch<W, CP>(out, jj[k], v[k]);
+      unsigned got = 0u;
+#pragma unroll
+      for (int k = 0; k < kPre; ++k)
+        if (((need >> k) & 1u) && n_ready<W, CP>(v[k])) got |= 1u << k;
+      need &= ~got;
+      if (need != 0u && !timeout) {
+        const long long dt = clock64() - t0;
+        if (dt > kWaitCycles || ((++polls & 63) == 0 && ld_relaxed(M.ctl + CTL_ERR) != 0)) timeout = true;
+      }
+      __nanosleep(64);
+    }
+    __syncwarp();
+    if (!timeout && i >= 0) {
+#pragma unroll
+      for (int k = 0; k < kPre; ++k)
+        if (jj[k] >= 0) acc = n_sub<W, CP>(acc, n_mul_fp<W, CP>(v[k], fr[k], fi[k]));
+      for (int k = kPre; k < w && !timeout; ++k) {  // slots beyond the held ones, one at a time
+        const int64_t e = ((int64_t)(b0 + k) << 5) + lane;
+        const int j = T.col[e];
+        if (j < 0) break;
+        double gr, gi = 0.0;
+        if constexpr (CP == 1) gr = T.val[e];
+        else { gr = T.val[2 * e]; gi = T.val[2 * e + 1]; }
+        N<W, CP> x;
+        while (!n_poll<W, CP>(out, j, x)) {
+          const long long dt = clock64() - t0;
+          if (dt > kWaitCycles || ((++polls & 63) == 0 && ld_relaxed(M.ctl + CTL_ERR) != 0)) {
+            timeout = true;
+            break;
+          }
+          if (dt > kSpinCycles) __nanosleep(128);
+        }
+        if (!timeout) acc = n_sub<W, CP>(acc, n_mul_fp<W, CP>(x, gr, gi));
+      }
+      if (!timeout) {
+        if (!unit) acc = n_div_fp<W, CP>(acc, dr, di);
+        n_publish<W, CP>(out, i, acc);
+      }
+    }
+    if (__any_sync(FULL, timeout)) {
+      if (lane == 0) atomicCAS(M.ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
+      return;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -927,10 +1088,18 @@ struct Launch {
   }
   static int trsv_mp(const IluHandleView& M, bool lower, bool unit, const double* in, double* out, const int* done,
                      cudaStream_t s) {
-    static int blocks = persistent_blocks(k_trsv_mp<W, CP>);
+    // out starts as sentinels: completion is read from the values
+    {
+      count_launch();
+      const int64_t m = (int64_t)M.n * CP * W;
+      k_fill_sent<<<grid_for(M.n), kBlock, 0, s>>>(m, out, 0, nullptr, done);
+    }
+    // one block per SM, all co-resident: the static schedule of k_trsv_mp needs every warp running
+    void* args[] = {(void*)&M, (void*)&lower, (void*)&unit, (void*)&in, (void*)&out, (void*)&done};
     count_launch();
-    k_trsv_mp<W, CP><<<blocks, kBlock, 0, s>>>(M, lower, unit, in, out, done);
-    return cudaGetLastError() == cudaSuccess ? MPK_OK : MPK_CUDA_ERROR;
+    const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_trsv_mp<W, CP>, dim3(sm_count()),
+                                                      dim3(kTrsvWarps * 32), args, 0, s);
+    return e == cudaSuccess ? MPK_OK : MPK_CUDA_ERROR;
   }
   static int trsv32(const IluHandleView& M, bool lower, bool unit, const double* in, double* out, const int* done,
                     cudaStream_t s) {
