@@ -552,12 +552,14 @@ __global__ void k_sell_width(int nchunks, const int* __restrict__ perm, const in
 // Also records, per chunk, the dependency with the largest level-order position (rep): the
 // substitution polls that one value before checking all the others.  The 32 positions of a chunk
 // are the 32 lanes of one warp (blockDim and the stride are multiples of 32).
-template <int CP>
+__device__ __forceinline__ double one_of(double) { return 1.0; }
+__device__ __forceinline__ float one_of(float) { return 1.0f; }
+__device__ __forceinline__ uint16_t one_of(uint16_t) { return (uint16_t)0x3F80u; }  // bfloat16 1.0
+template <typename T, int CP>
 __global__ void k_sell_fill(int nchunks, const int* __restrict__ perm, const int* __restrict__ pos,
                             const int* __restrict__ rp, const int* __restrict__ ci, const int* __restrict__ diag,
-                            const double* __restrict__ fac, bool lower, const int* __restrict__ coff,
-                            int* __restrict__ col, double* __restrict__ val, double* __restrict__ dia,
-                            int* __restrict__ rep) {
+                            const T* __restrict__ fac, bool lower, const int* __restrict__ coff,
+                            int* __restrict__ col, T* __restrict__ val, T* __restrict__ dia, int* __restrict__ rep) {
   const int64_t P = (int64_t)nchunks * 32;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < P; q += (int64_t)gridDim.x * blockDim.x) {
     const int c = (int)(q >> 5), lane = (int)(q & 31);
@@ -574,19 +576,20 @@ __global__ void k_sell_fill(int nchunks, const int* __restrict__ perm, const int
       col[e] = k < len ? ci[p + k] : -1;
       if (k < len) last = max(last, pos[ci[p + k]]);
 #pragma unroll
-      for (int t = 0; t < CP; ++t) val[e * CP + t] = k < len ? fac[(int64_t)(p + k) * CP + t] : 0.0;
+      for (int t = 0; t < CP; ++t) val[e * CP + t] = k < len ? fac[(int64_t)(p + k) * CP + t] : T(0);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) last = max(last, __shfl_xor_sync(0xffffffffu, last, off));
     if (lane == 0) rep[c] = last >= 0 ? perm[last] : -1;
 #pragma unroll
-    for (int t = 0; t < CP; ++t) dia[q * CP + t] = i >= 0 ? fac[(int64_t)diag[i] * CP + t] : (t == 0 ? 1.0 : 0.0);
+    for (int t = 0; t < CP; ++t) dia[q * CP + t] = i >= 0 ? fac[(int64_t)diag[i] * CP + t] : (t == 0 ? one_of(T(0)) : T(0));
   }
 }
 
 // Repack one triangle of (rp, ci, diag, fac) in the positions of its level order into *buf
 // (allocated here) and describe it in *out.
-static int build_sell(int n, int cp, const int* rp, const int* ci, const int* diag, const double* fac, int* lvbuf,
+template <typename T>
+static int build_sell(int n, int cp, const int* rp, const int* ci, const int* diag, const T* fac, int* lvbuf,
                       int nlevels, bool lower, void** buf, SellTri* out, cudaStream_t s) {
   const LevelOrder lo = level_view(lvbuf, n, nlevels);
   int nch = 0;
@@ -604,23 +607,23 @@ static int build_sell(int n, int cp, const int* rp, const int* ci, const int* di
   const size_t slots = (size_t)total * 32;
   const size_t coff_b = ((sizeof(int) * ((size_t)nch + 1)) + 255) & ~(size_t)255;
   const size_t col_b = ((sizeof(int) * slots) + 255) & ~(size_t)255;
-  const size_t val_b = ((sizeof(double) * slots * cp) + 255) & ~(size_t)255;
-  const size_t dia_b = ((sizeof(double) * (size_t)nch * 32 * cp) + 255) & ~(size_t)255;
+  const size_t val_b = ((sizeof(T) * slots * cp) + 255) & ~(size_t)255;
+  const size_t dia_b = ((sizeof(T) * (size_t)nch * 32 * cp) + 255) & ~(size_t)255;
   const size_t rep_b = sizeof(int) * (size_t)nch;
   char* b = nullptr;
   MPK_CUDA(cudaMalloc((void**)&b, coff_b + col_b + val_b + dia_b + rep_b + 256));
   int* coff = (int*)b;
   int* col = (int*)(b + coff_b);
-  double* val = (double*)(b + coff_b + col_b);
-  double* dia = (double*)(b + coff_b + col_b + val_b);
+  T* val = (T*)(b + coff_b + col_b);
+  T* dia = (T*)(b + coff_b + col_b + val_b);
   int* rep = (int*)(b + coff_b + col_b + val_b + dia_b);
   MPK_CUDA(cudaMemcpyAsync(coff, coff_tmp, sizeof(int) * ((size_t)nch + 1), cudaMemcpyDeviceToDevice, s));
   count_launch();
   if (cp == 1)
-    k_sell_fill<1><<<grid_for(nch * 32), kBlock, 0, s>>>(nch, lo.perm, lo.pos, rp, ci, diag, fac, lower, coff, col,
+    k_sell_fill<T, 1><<<grid_for(nch * 32), kBlock, 0, s>>>(nch, lo.perm, lo.pos, rp, ci, diag, fac, lower, coff, col,
                                                           val, dia, rep);
   else
-    k_sell_fill<2><<<grid_for(nch * 32), kBlock, 0, s>>>(nch, lo.perm, lo.pos, rp, ci, diag, fac, lower, coff, col,
+    k_sell_fill<T, 2><<<grid_for(nch * 32), kBlock, 0, s>>>(nch, lo.perm, lo.pos, rp, ci, diag, fac, lower, coff, col,
                                                           val, dia, rep);
   MPK_CUDA(cudaGetLastError());
   MPK_CUDA(cudaFreeAsync(width, s));
@@ -632,6 +635,26 @@ static int build_sell(int n, int cp, const int* rp, const int* ci, const int* di
   out->dia = dia;
   out->rep = rep;
   out->nchunks = nch;
+  return MPK_OK;
+}
+
+// Repacked triangles t0, t0+1 of the handle (0: the factor, 2: its conjugate transpose).
+static int build_sells(mpk_ilu* M, int t0, const int* rp, const int* ci, const int* diag, const void* fac,
+                       cudaStream_t s) {
+  for (int t = t0; t < t0 + 2; ++t) {
+    const bool lower = (t == t0);
+    int st;
+    if (M->prec == MPK_ILU_FP64)
+      st = build_sell<double>(M->n, M->cp, rp, ci, diag, (const double*)fac, M->lvbuf[t], M->nlevels[t], lower,
+                              M->sellbuf + t, M->sell + t, s);
+    else if (M->prec == MPK_ILU_FP32)
+      st = build_sell<float>(M->n, M->cp, rp, ci, diag, (const float*)fac, M->lvbuf[t], M->nlevels[t], lower,
+                             M->sellbuf + t, M->sell + t, s);
+    else
+      st = build_sell<uint16_t>(M->n, M->cp, rp, ci, diag, (const uint16_t*)fac, M->lvbuf[t], M->nlevels[t], lower,
+                                M->sellbuf + t, M->sell + t, s);
+    if (st != MPK_OK) return st;
+  }
   return MPK_OK;
 }
 
@@ -667,14 +690,12 @@ static int build_transpose(mpk_ilu* M, cudaStream_t s) {
                                                M->ciT, (uint16_t*)M->facT, M->diagT, s);
   }
   if (st != MPK_OK) return st;
+  // pk also serves as the binary32 substitutions' result buffer: clear it before the epoch-stamped
+  // ordering passes read it
+  MPK_CUDA(cudaMemsetAsync(M->pk, 0, sizeof(unsigned long long) * (size_t)M->n * M->cp, s));
   st = build_levels(M->n, M->rpT, M->ciT, M->diagT, M->pk, M->ctl, 1, M->lvbuf + 2, M->nlevels + 2, s);
-  if (st != MPK_OK || M->prec != MPK_ILU_FP64) return st;
-  for (int t = 2; t < 4; ++t) {
-    st = build_sell(M->n, M->cp, M->rpT, M->ciT, M->diagT, (const double*)M->facT, M->lvbuf[t], M->nlevels[t], t == 2,
-                    M->sellbuf + t, M->sell + t, s);
-    if (st != MPK_OK) return st;
-  }
-  return MPK_OK;
+  if (st != MPK_OK) return st;
+  return build_sells(M, 2, M->rpT, M->ciT, M->diagT, M->facT, s);
 }
 
 int prepare_trans(mpk_ilu* M, cudaStream_t s) { return build_transpose(M, s); }
@@ -846,13 +867,12 @@ static int factor_impl(const mpk_csr* A, int prec, mpk_ilu** out, int* fail_row,
   }
   if (prec == MPK_ILU_FP64) {
     MPK_TRY(cudaMalloc((void**)&M->vmp, sizeof(double) * (size_t)n * cp * 4));
-    for (int t = 0; t < 2; ++t) {
-      int st = build_sell(n, cp, M->rp, M->ci, M->diag, (const double*)M->fac, M->lvbuf[t], M->nlevels[t], t == 0,
-                          M->sellbuf + t, M->sell + t, s);
-      if (st != MPK_OK) return bail(st);
-    }
   } else {
     MPK_TRY(cudaMalloc((void**)&M->v32, sizeof(float) * (size_t)n * cp));
+  }
+  {
+    int st = build_sells(M, 0, M->rp, M->ci, M->diag, M->fac, s);
+    if (st != MPK_OK) return bail(st);
   }
   MPK_TRY(cudaMemcpyAsync(M->ctl, ctl0, sizeof(int) * 4, cudaMemcpyHostToDevice, s));
   MPK_TRY(cudaStreamSynchronize(s));

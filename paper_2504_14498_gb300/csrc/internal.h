@@ -106,16 +106,17 @@ struct Ops {
 };
 const Ops* get_ops(int w, int cp);
 
-// One triangle of a binary64 factor repacked for the static chunk schedule of the substitution
+// One triangle of the factor repacked for the static chunk schedule of the substitutions
 // (SELL-32): positions are the level order's (32 rows per chunk, levels padded to whole chunks);
 // chunk c owns slot blocks coff[c] .. coff[c+1]-1, and slot k of the row at lane l of chunk c is
-// entry (coff[c] + k) * 32 + l of col / val, its entries in CSR order.
+// entry (coff[c] + k) * 32 + l of col / val, its entries in CSR order.  Values have the factor's
+// storage type (double, float or bfloat16 bits).
 struct SellTri {
   const int* perm = nullptr;    // 32 * nchunks: row at each position (-1: padding)
   const int* coff = nullptr;    // nchunks + 1
   const int* col = nullptr;     // 32 * coff[nchunks]: column of the slot (-1 past the row's end)
-  const double* val = nullptr;  // 32 * coff[nchunks] * cp: factor value of the slot
-  const double* dia = nullptr;  // 32 * nchunks * cp: the row's diagonal factor value (1 for padding)
+  const void* val = nullptr;    // 32 * coff[nchunks] * cp: factor value of the slot
+  const void* dia = nullptr;    // 32 * nchunks * cp: the row's diagonal factor value (1 for padding)
   const int* rep = nullptr;     // nchunks: the chunk's dependency latest in the level order (-1: none)
   int nchunks = 0;
 };
@@ -136,7 +137,7 @@ struct IluHandleView {
   unsigned long long* pk = nullptr;  // packed (epoch << 32 | 32 payload bits) words, 8*cp per row
   LevelOrder lv_lo, lv_up;           // level orders (chunk dataflow) of the two triangles
   Order ch_lo, ch_up;                // chunk orders (dependency-driven, row chains in warps)
-  SellTri sl_lo, sl_up;              // binary64 factor: repacked triangles of the substitution
+  SellTri sl_lo, sl_up;              // repacked triangles of the substitutions
 };
 enum CtlIdx : int { CTL_EPOCH = 0, CTL_TICKET_LO, CTL_TICKET_UP, CTL_ERR, CTL_FAIL_ROW, CTL_COUNT };
 
@@ -174,7 +175,7 @@ struct mpk_ilu {
   unsigned long long* pk = nullptr;
   int* lvbuf[4] = {nullptr, nullptr, nullptr, nullptr};  // level orders: lower, upper, transposed lower / upper
   int nlevels[4] = {0, 0, 0, 0};
-  void* sellbuf[4] = {nullptr, nullptr, nullptr, nullptr};  // binary64 factor: repacked triangles (same order)
+  void* sellbuf[4] = {nullptr, nullptr, nullptr, nullptr};  // repacked triangles (same order)
   mpk::SellTri sell[4];
   mpk::IluHandleView view(bool trans) const;
 };

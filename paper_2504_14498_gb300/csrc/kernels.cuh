@@ -819,6 +819,7 @@ __global__ void __launch_bounds__(kBlock) k_trsv_pk32(IluHandleView M, bool lowe
 // chunk's positions and slot block are fetched one chunk ahead.  Every wait is bounded by
 // kWaitCycles (then MPK_TIMEOUT in ctl[CTL_ERR] and all warps leave).
 constexpr int kTrsvWarps = 4;
+constexpr bool kRepFirst = true;
 constexpr long long kSpinCycles = 40000;  // ~20 us of polling without sleeping
 constexpr unsigned long long kSent = 0xFFFFFFFFFFFFFFFFull;
 
@@ -886,6 +887,8 @@ __global__ void __launch_bounds__(kTrsvWarps * 32, 1)
   constexpr int kPre = 4;  // slots held in registers (longer rows stream the rest)
   const unsigned FULL = 0xffffffffu;
   const SellTri T = lower ? M.sl_lo : M.sl_up;
+  const double* __restrict__ tval = (const double*)T.val;
+  const double* __restrict__ tdia = (const double*)T.dia;
   const int lane = threadIdx.x & 31;
   const int G = gridDim.x * (blockDim.x >> 5);
   const int g = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
@@ -910,8 +913,8 @@ __global__ void __launch_bounds__(kTrsvWarps * 32, 1)
       if (k < w) {
         const int64_t e = ((int64_t)(b0 + k) << 5) + lane;
         jj[k] = T.col[e];
-        if constexpr (CP == 1) fr[k] = T.val[e];
-        else { fr[k] = T.val[2 * e]; fi[k] = T.val[2 * e + 1]; }
+        if constexpr (CP == 1) fr[k] = tval[e];
+        else { fr[k] = tval[2 * e]; fi[k] = tval[2 * e + 1]; }
       }
     }
     N<W, CP> acc = n_zero<W, CP>();
@@ -920,8 +923,8 @@ __global__ void __launch_bounds__(kTrsvWarps * 32, 1)
       acc = n_load<W, CP>(in, i);
       if (!unit) {
         const int64_t q = ((int64_t)chunk << 5) + lane;
-        if constexpr (CP == 1) dr = T.dia[q];
-        else { dr = T.dia[2 * q]; di = T.dia[2 * q + 1]; }
+        if constexpr (CP == 1) dr = tdia[q];
+        else { dr = tdia[2 * q]; di = tdia[2 * q + 1]; }
       }
     }
     // fetch the next chunk's position and slot block while this one waits
@@ -943,9 +946,8 @@ __global__ void __launch_bounds__(kTrsvWarps * 32, 1)
     bool timeout = false;
     const long long t0 = clock64();
     int polls = 0;
-    // lane 0 alone polls the latest dependency (one address instead of every lane's): polling
-    // from many lanes loads the SM enough to slow the FP64 arithmetic of its other warps
-    if (lane == 0 && rep >= 0) {
+    // kRepFirst: lane 0 alone polls the chunk's latest dependency before all lanes check theirs
+    if (kRepFirst && lane == 0 && rep >= 0) {
       N<W, CP> r;
       while (!n_poll<W, CP>(out, rep, r)) {
         const long long dt = clock64() - t0;
@@ -986,8 +988,8 @@ __global__ void __launch_bounds__(kTrsvWarps * 32, 1)
         const int j = T.col[e];
         if (j < 0) break;
         double gr, gi = 0.0;
-        if constexpr (CP == 1) gr = T.val[e];
-        else { gr = T.val[2 * e]; gi = T.val[2 * e + 1]; }
+        if constexpr (CP == 1) gr = tval[e];
+        else { gr = tval[2 * e]; gi = tval[2 * e + 1]; }
         N<W, CP> x;
         while (!n_poll<W, CP>(out, j, x)) {
           const long long dt = clock64() - t0;
@@ -1002,6 +1004,201 @@ __global__ void __launch_bounds__(kTrsvWarps * 32, 1)
       if (!timeout) {
         if (!unit) acc = n_div_fp<W, CP>(acc, dr, di);
         n_publish<W, CP>(out, i, acc);
+      }
+    }
+    if (__any_sync(FULL, timeout)) {
+      if (lane == 0) atomicCAS(M.ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
+      return;
+    }
+  }
+}
+
+
+// Binary32 / bfloat16 factor (substitutions in binary32): the same static balanced schedule and
+// value-carried completion as k_trsv_mp, with binary32 values and the sentinel kSent32.  Row i:
+//   lower: a = fl32(2^-e in_i) (leading components), a -= f_ij v_j (fmaf, CSR order), v_i = a;
+//   upper: a = lower result of row i, a -= f_ij v_j, a /= f_ii, v_i = a, out_i = 2^e v_i,
+// e = frexp exponent of the largest leading component of the right-hand side (the scaling keeps
+// residuals far below binary32's range representable); complex steps in the fixed fmaf order
+// (see RowPk32).  Lower results go to M.v32, upper results to M.pk read as binary32.
+constexpr unsigned kSent32 = 0xFFFFFFFFu;
+__device__ __forceinline__ float ld_relaxed_f32(const float* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return __uint_as_float(v);
+}
+__device__ __forceinline__ void st_relaxed_f32(float* p, float x) {
+  unsigned v = __float_as_uint(x);
+  if (v == kSent32) v = 0x7FC00000u;  // never publish the sentinel
+  asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+static __global__ void __launch_bounds__(kBlock) k_fill_sent32(int64_t m, float* __restrict__ a,
+                                                              const int* __restrict__ done) {
+  if (is_done(done)) return;
+  const float s = __uint_as_float(kSent32);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) a[k] = s;
+}
+template <int CP>
+__device__ __forceinline__ bool f_poll(const float* __restrict__ v, int j, float& xr, float& xi) {
+  xr = ld_relaxed_f32(v + (int64_t)j * CP);
+  xi = CP == 2 ? ld_relaxed_f32(v + (int64_t)j * CP + 1) : 0.0f;
+  return __float_as_uint(xr) != kSent32 && (CP == 1 || __float_as_uint(xi) != kSent32);
+}
+
+template <int W, int CP, typename TS>
+__global__ void __launch_bounds__(kTrsvWarps * 32, 1)
+    k_trsv_lp(IluHandleView M, bool lower, bool unit, const double* __restrict__ in, double* __restrict__ out,
+              const int* __restrict__ done) {
+  if (is_done(done)) return;
+  constexpr int kPre = 4;
+  const unsigned FULL = 0xffffffffu;
+  const SellTri T = lower ? M.sl_lo : M.sl_up;
+  const TS* __restrict__ tval = (const TS*)T.val;
+  const TS* __restrict__ tdia = (const TS*)T.dia;
+  float* __restrict__ mine = lower ? M.v32 : reinterpret_cast<float*>(M.pk);
+  const int e = scale_exponent(M.absmax);
+  const int lane = threadIdx.x & 31;
+  const int G = gridDim.x * (blockDim.x >> 5);
+  const int g = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+  int nx_i = -1, nx_b0 = 0, nx_b1 = 0, nx_rep = -1;
+  if (g < T.nchunks) {
+    nx_i = T.perm[(g << 5) + lane];
+    nx_b0 = T.coff[g];
+    nx_b1 = T.coff[g + 1];
+    nx_rep = T.rep[g];
+  }
+  for (int chunk = g; chunk < T.nchunks; chunk += G) {
+    const int i = nx_i, b0 = nx_b0, w = nx_b1 - nx_b0, rep = nx_rep;
+    int jj[kPre];
+    float fr[kPre], fi[kPre];
+#pragma unroll
+    for (int k = 0; k < kPre; ++k) {
+      jj[k] = -1;
+      fr[k] = 0.0f;
+      fi[k] = 0.0f;
+      if (k < w) {
+        const int64_t s = ((int64_t)(b0 + k) << 5) + lane;
+        jj[k] = T.col[s];
+        if constexpr (CP == 1) fr[k] = ld_fac(tval, s);
+        else { fr[k] = ld_fac(tval, 2 * s); fi[k] = ld_fac(tval, 2 * s + 1); }
+      }
+    }
+    float ar = 0.0f, ai = 0.0f, dr = 1.0f, di = 0.0f;
+    if (i >= 0) {
+      if (lower) {
+        const double* q = in + (int64_t)i * CP * W;
+        ar = __double2float_rn(ldexp(q[0], -e));
+        ai = CP == 2 ? __double2float_rn(ldexp(q[W], -e)) : 0.0f;
+      } else {
+        ar = M.v32[(int64_t)i * CP];
+        ai = CP == 2 ? M.v32[(int64_t)i * CP + 1] : 0.0f;
+      }
+      if (!unit) {
+        const int64_t q = ((int64_t)chunk << 5) + lane;
+        if constexpr (CP == 1) dr = ld_fac(tdia, q);
+        else { dr = ld_fac(tdia, 2 * q); di = ld_fac(tdia, 2 * q + 1); }
+      }
+    }
+    const int nc = chunk + G;
+    if (nc < T.nchunks) {
+      nx_i = T.perm[(nc << 5) + lane];
+      nx_b0 = T.coff[nc];
+      nx_b1 = T.coff[nc + 1];
+      nx_rep = T.rep[nc];
+    }
+    float vr[kPre], vi[kPre];
+    unsigned need = 0u;
+#pragma unroll
+    for (int k = 0; k < kPre; ++k) {
+      vr[k] = 0.0f;
+      vi[k] = 0.0f;
+      if (jj[k] >= 0) need |= 1u << k;
+    }
+    bool timeout = false;
+    const long long t0 = clock64();
+    int polls = 0;
+    if (kRepFirst && lane == 0 && rep >= 0) {
+      float xr, xi;
+      while (!f_poll<CP>(mine, rep, xr, xi)) {
+        const long long dt = clock64() - t0;
+        if (dt > kWaitCycles || ((++polls & 63) == 0 && ld_relaxed(M.ctl + CTL_ERR) != 0)) {
+          timeout = true;
+          break;
+        }
+        if (dt > kSpinCycles) __nanosleep(128);
+      }
+    }
+    __syncwarp();
+    while (__any_sync(FULL, need != 0u && !timeout)) {
+      unsigned got = 0u;
+#pragma unroll
+      for (int k = 0; k < kPre; ++k)
+        if ((need >> k) & 1u) {
+          vr[k] = ld_relaxed_f32(mine + (int64_t)jj[k] * CP);
+          if constexpr (CP == 2) vi[k] = ld_relaxed_f32(mine + (int64_t)jj[k] * CP + 1);
+        }
+#pragma unroll
+      for (int k = 0; k < kPre; ++k)
+        if (((need >> k) & 1u) && __float_as_uint(vr[k]) != kSent32 && (CP == 1 || __float_as_uint(vi[k]) != kSent32))
+          got |= 1u << k;
+      need &= ~got;
+      if (need != 0u && !timeout) {
+        const long long dt = clock64() - t0;
+        if (dt > kWaitCycles || ((++polls & 63) == 0 && ld_relaxed(M.ctl + CTL_ERR) != 0)) timeout = true;
+      }
+      __nanosleep(64);
+    }
+    __syncwarp();
+    if (!timeout && i >= 0) {
+      auto consume = [&](float lr, float li, float xr, float xi) {
+        if constexpr (CP == 1) {
+          ar = fmaf(-lr, xr, ar);
+        } else {
+          ar = fmaf(-lr, xr, ar);
+          ar = fmaf(li, xi, ar);
+          ai = fmaf(-lr, xi, ai);
+          ai = fmaf(-li, xr, ai);
+        }
+      };
+#pragma unroll
+      for (int k = 0; k < kPre; ++k)
+        if (jj[k] >= 0) consume(fr[k], fi[k], vr[k], vi[k]);
+      for (int k = kPre; k < w && !timeout; ++k) {  // slots beyond the held ones, one at a time
+        const int64_t s = ((int64_t)(b0 + k) << 5) + lane;
+        const int j = T.col[s];
+        if (j < 0) break;
+        float gr, gi = 0.0f;
+        if constexpr (CP == 1) gr = ld_fac(tval, s);
+        else { gr = ld_fac(tval, 2 * s); gi = ld_fac(tval, 2 * s + 1); }
+        float xr, xi;
+        while (!f_poll<CP>(mine, j, xr, xi)) {
+          const long long dt = clock64() - t0;
+          if (dt > kWaitCycles || ((++polls & 63) == 0 && ld_relaxed(M.ctl + CTL_ERR) != 0)) {
+            timeout = true;
+            break;
+          }
+          if (dt > kSpinCycles) __nanosleep(128);
+        }
+        if (!timeout) consume(gr, gi, xr, xi);
+      }
+      if (!timeout) {
+        if (!unit) {
+          if constexpr (CP == 1) {
+            ar = ar / dr;
+          } else {
+            const float den = fmaf(dr, dr, di * di), nr = fmaf(ar, dr, ai * di), ni = fmaf(ai, dr, -(ar * di));
+            ar = nr / den;
+            ai = ni / den;
+          }
+        }
+        st_relaxed_f32(mine + (int64_t)i * CP, ar);
+        if constexpr (CP == 2) st_relaxed_f32(mine + (int64_t)i * CP + 1, ai);
+        if (!lower) {
+          N<W, CP> z = n_zero<W, CP>();
+          z.re.c[0] = ldexp((double)ar, e);
+          if constexpr (CP == 2) z.im.c[0] = ldexp((double)ai, e);
+          n_store<W, CP>(out, i, z);
+        }
       }
     }
     if (__any_sync(FULL, timeout)) {
@@ -1103,15 +1300,15 @@ struct Launch {
   }
   static int trsv32(const IluHandleView& M, bool lower, bool unit, const double* in, double* out, const int* done,
                     cudaStream_t s) {
-    count_launch();
-    if (M.prec == MPK_ILU_BF16) {
-      static int blocks = persistent_blocks(k_trsv_pk32<W, CP, uint16_t>);
-      k_trsv_pk32<W, CP, uint16_t><<<blocks, kBlock, 0, s>>>(M, lower, unit, in, out, done);
-    } else {
-      static int blocks = persistent_blocks(k_trsv_pk32<W, CP, float>);
-      k_trsv_pk32<W, CP, float><<<blocks, kBlock, 0, s>>>(M, lower, unit, in, out, done);
-    }
-    return cudaGetLastError() == cudaSuccess ? MPK_OK : MPK_CUDA_ERROR;
+    // this pass's binary32 results start as sentinels: completion is read from the values
+    count_launch(2);
+    float* mine = lower ? M.v32 : reinterpret_cast<float*>(M.pk);
+    k_fill_sent32<<<grid_for(M.n), kBlock, 0, s>>>((int64_t)M.n * CP, mine, done);
+    // one block per SM, all co-resident (static schedule)
+    void* args[] = {(void*)&M, (void*)&lower, (void*)&unit, (void*)&in, (void*)&out, (void*)&done};
+    const void* fn = M.prec == MPK_ILU_BF16 ? (const void*)k_trsv_lp<W, CP, uint16_t> : (const void*)k_trsv_lp<W, CP, float>;
+    const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(sm_count()), dim3(kTrsvWarps * 32), args, 0, s);
+    return e == cudaSuccess ? MPK_OK : MPK_CUDA_ERROR;
   }
   static Ops table() {
     Ops o;
