@@ -1,7 +1,8 @@
 #!/usr/bin/env python3
 """Benchmark of the hot path: time to relative residual 1e-25 of DD BiCGSTAB + ILU(0) on the
-128^3 convection-diffusion workload (N = 2,097,152, nnz = 14,581,760), plus the mixed SpMV's
-HBM roofline.
+128^3 convection-diffusion workload (N = 2,097,152, nnz = 14,581,760), plus the rooflines of the
+substitution (the dominant kernel) and the mixed SpMV: binary64 operation rate against the
+GB300's binary64 peak, and HBM bytes against the measured copy bandwidth.
 
 One step = one whole solve on inputs already resident in HBM: ILU(0) factorisation of A
 (binary64 by default, the paper's "_d" preconditioner) and DD BiCGSTAB from x0 = 0 until
@@ -35,6 +36,14 @@ TOL = 1e-25
 # by the CUDA path, whose iterations are identical to the CPU oracle's; used only to
 # extrapolate the CPU timings from a bounded sample.
 ITERS_128 = {"fp64": 17, "fp32": 18, "bf16": 18}
+# Peak binary64 operation rate of the GB300, from its unit counts and clock: 152 SMs x 4
+# sub-partitions x 0.5 binary64 lanes per clock x 2.07 GHz (a warp instruction holds a
+# sub-partition's FP64 unit 64 cycles; measured by a dependent-FMA probe).  In T op/s.
+FP64_PEAK_OPS = 152 * 4 * 0.5 * 2.07e9 / 1e12
+# DRAM bytes (read + write) of one k_trsv_mp launch pair (both triangles) on the 128^3 workload:
+# dram__bytes_read.sum + dram__bytes_write.sum from an ncu capture of the current kernel
+# (profiles/k_trsv_mp_convdiff3d_128.md); None once the kernel changes.
+TRSV_MP_TRAFFIC = 151913472 + 18082048 + 168578304 + 16981760
 
 
 def parse():
@@ -277,31 +286,43 @@ def run_mpk(args):
     x = torch.as_tensor(inputs.random_vector(n, w, 1, seed=3), device="cuda")
     y = torch.empty_like(x)
     t_spmv = time_launches(lambda: _lib.spmv_mp(A, x, w, y))
-    spmv_bytes = 12 * nnz + 4 * (n + 1) + 2 * 16 * n
-    spmv_gbs = spmv_bytes / t_spmv / 1e9
     M64 = _lib.ILU0(A, "fp64")
     M32 = _lib.ILU0(A, "fp32")
     z = torch.empty_like(x)
     t_pre64 = time_launches(lambda: M64.apply(x, w, False, z), reps=10, warm=3)
     t_pre32 = time_launches(lambda: M32.apply(x, w, False, z), reps=10, warm=3)
-    # algorithmic bytes of one M^-1 application: factor values + columns of both triangles, row
-    # pointers and diagonal index twice, DD right-hand side in and DD result out, intermediate
-    # written and read once (binary64: DD, binary32: 4 bytes)
-    pre64_bytes = (8 + 4) * nnz + 2 * 4 * (n + 1) + 2 * 4 * n + 16 * n + 16 * n + 2 * 16 * n
-    pre32_bytes = (4 + 4) * nnz + 2 * 4 * (n + 1) + 2 * 4 * n + 16 * n + 16 * n + 2 * 4 * n
     M64.close()
     M32.close()
     hbm = float(pk.get("hbm_gbs", 6800.0))
+    nod = nnz - n  # off-diagonal entries (both triangles)
+    # algorithmic HBM bytes per launch (values + int32 columns, row pointers, DD vectors in and out;
+    # M^-1: both triangles, intermediate written and read once, binary64 DD / binary32 4 bytes)
+    spmv_bytes = 12 * nnz + 4 * (n + 1) + 2 * 16 * n
+    pre64_bytes = (8 + 4) * nnz + 2 * 4 * (n + 1) + 2 * 4 * n + 16 * n + 16 * n + 2 * 16 * n
+    pre32_bytes = (4 + 4) * nnz + 2 * 4 * (n + 1) + 2 * 4 * n + 16 * n + 16 * n + 2 * 4 * n
+    # algorithmic binary64 operations (add, mul or fma) of the double-word algorithms as run:
+    # DW*FP 6 + DW+DW 14 (TwoSum as FastTwoSum on exponent-ordered operands) = 20 per multiply-add;
+    # DW/FP 10 (two divisions counted as one operation each)
+    spmv_ops = 20 * nnz
+    pre64_ops = 20 * nod + 10 * n
+    alu = FP64_PEAK_OPS
+    def rl(bound, work, t, peak, unit, per_unit):
+        a = work / t / (1e9 if unit == "GB/s" else 1e12)
+        return {"bound": bound, "achieved": a, "peak": peak, "unit": unit, "frac": a / peak, "traffic": None,
+                "work_per_launch": work, "s_per_launch": t, "unit_of_work": per_unit}
     rooflines = {
-        "spmv_dd": {"bound": "hbm", "achieved": spmv_gbs, "peak": hbm, "unit": "GB/s", "frac": spmv_gbs / hbm,
-                    "traffic": None, "bytes_per_launch": spmv_bytes, "s_per_launch": t_spmv, "peak_note": pk_note},
-        "precond_fp64_dd": {"bound": "hbm", "achieved": pre64_bytes / t_pre64 / 1e9, "peak": hbm, "unit": "GB/s",
-                            "frac": pre64_bytes / t_pre64 / 1e9 / hbm, "bytes_per_launch": pre64_bytes,
-                            "s_per_launch": t_pre64},
-        "precond_fp32": {"bound": "hbm", "achieved": pre32_bytes / t_pre32 / 1e9, "peak": hbm, "unit": "GB/s",
-                         "frac": pre32_bytes / t_pre32 / 1e9 / hbm, "bytes_per_launch": pre32_bytes,
-                         "s_per_launch": t_pre32},
+        "precond_fp64_dd": rl("alu", pre64_ops, t_pre64, alu, "T FP64 op/s",
+                              "binary64 operations of one M^-1 (both triangles; k_trsv_mp x2)"),
+        "spmv_dd": rl("alu", spmv_ops, t_spmv, alu, "T FP64 op/s", "binary64 operations of one SpMV (k_spmv)"),
+        "spmv_dd_hbm": rl("hbm", spmv_bytes, t_spmv, hbm, "GB/s", "HBM bytes of one SpMV"),
+        "precond_fp64_dd_hbm": rl("hbm", pre64_bytes, t_pre64, hbm, "GB/s", "HBM bytes of one M^-1"),
+        "precond_fp32_hbm": rl("hbm", pre32_bytes, t_pre32, hbm, "GB/s", "HBM bytes of one M^-1 (k_trsv_lp x2)"),
     }
+    for k in rooflines:
+        rooflines[k]["peak_note"] = "of derived nominal" if rooflines[k]["bound"] == "alu" else pk_note
+    # the dominant kernel of the timed solve is the binary64-factor substitution (latency-bound
+    # chain of levels; FP64 issue while a level computes); its counters, where taken, are in profiles/
+    rooflines["precond_fp64_dd"]["traffic"] = TRSV_MP_TRAFFIC
 
     # ---- end to end through the host-buffer C call --------------------------------------------
     e2e = None
@@ -328,7 +349,7 @@ def run_mpk(args):
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": dict(workload_config(args.m, args.prec), parallelism="replicas x%d" % world),
-                "roofline": rooflines["spmv_dd"], "rooflines": rooflines, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": rooflines["precond_fp64_dd"], "rooflines": rooflines, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "gpu_launches": int(launches), "solve": extra, "variants": variants,
                 "pe": meta["pe"]}
         print(json.dumps(line))

@@ -228,3 +228,12 @@ def random_vector(n, w, c=1, seed=SEED_BASE + 7, scale=1.0):
     for k in range(1, w):
         v[:, :, k] = v[:, :, k - 1] * (2.0 ** -53) * rng.uniform(-0.5, 0.5, size=(n, c))
     return v.reshape(-1)
+
+
+def normal_rhs(n, w, c=2, seed=SEED_BASE + 3):
+    """Right-hand side with N(0, 1) leading components (real and imaginary parts when c = 2) and
+    zero lower components: the Helmholtz workload's random b."""
+    rng = np.random.default_rng(seed)
+    v = np.zeros((n, c, w))
+    v[:, :, 0] = rng.standard_normal((n, c))
+    return v.reshape(-1)
