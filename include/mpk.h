@@ -172,6 +172,26 @@ int mpk_precond_apply(const mpk_ilu* M, int w, int trans, const double* r_dev, d
 int mpk_krylov_solve(int method, int w, const mpk_csr* A, const mpk_ilu* M, const double* b_dev, double* x_dev,
                      const mpk_opts* opts, mpk_info* info, void* stream);
 
+/* Batched solve of nsys independent systems (the benchmark spec's batching pattern; the paper
+ * solves one system at a time).  A is block-diagonal: system s owns rows and columns
+ * sys_rows[s] .. sys_rows[s+1]-1, and every stored column of a row lies in its system's block
+ * (checked; MPK_INVALID_ARG otherwise, nothing solved).  All systems advance together, each step
+ * of every system in the same kernel launches; each system follows exactly the operation
+ * sequence mpk_krylov_solve would perform on it alone (identical results), with its own scalars,
+ * stopping test, breakdown test and iteration count, and a finished system keeps its iterate and
+ * residual while the others go on.
+ *   M: ILU(0) handle of the whole block-diagonal matrix (it equals the block-diagonal of the
+ *      systems' ILU(0)s), or NULL.  With a binary32 / bfloat16 factor each system's right-hand
+ *      side is scaled by its own power of two.
+ *   sys_rows_host, sys_rows_dev: the same nsys+1 increasing row offsets (0 .. n) on host and device.
+ *   b_dev, x_dev: n*c*w doubles (x0 in, iterates out).  infos: HOST array of nsys records.
+ *   opts->hist_dev (nullable): nsys*(maxit+1) doubles, system s's history at s*(maxit+1).
+ * Returns MPK_OK when every system converged, else the first non-OK system status (or an error
+ * code of the call itself).  The call synchronises `stream`. */
+int mpk_krylov_solve_batched(int method, int w, const mpk_csr* A, int nsys, const int32_t* sys_rows_host,
+                             const int32_t* sys_rows_dev, const mpk_ilu* M, const double* b_dev, double* x_dev,
+                             const mpk_opts* opts, mpk_info* infos, void* stream);
+
 /* End-to-end convenience: host CSR, host b and x (x0 in, solution out).  Copies A and b to
  * the device, builds ILU(0) in `prec` (MPK_ILU_NONE: none), solves, copies x back and frees
  * everything.  info->ms_solve covers the whole call. */

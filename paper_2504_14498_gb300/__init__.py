@@ -11,7 +11,8 @@ holds the ctypes binding (_lib), the in-tree build (build) and the synthetic inp
 """
 import importlib
 
-__all__ = ["Matrix", "ILU0", "spmv_mp", "dot", "krylov_solve", "solve_host", "MpkError", "build", "inputs"]
+__all__ = ["Matrix", "ILU0", "spmv_mp", "dot", "krylov_solve", "krylov_solve_batched", "solve_host", "MpkError",
+           "build", "inputs"]
 
 
 def __getattr__(name):

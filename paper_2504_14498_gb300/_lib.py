@@ -61,6 +61,8 @@ SIGNATURES = [
                               ctypes.POINTER(Info), _VP]),
     ("mpk_solve_host", _I, [_I, _I, _I, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP,
                             ctypes.POINTER(Opts), ctypes.POINTER(Info)]),
+    ("mpk_krylov_solve_batched", _I, [_I, _I, ctypes.POINTER(CsrDesc), _I, _VP, _VP, _VP, _VP, _VP,
+                                      ctypes.POINTER(Opts), ctypes.POINTER(Info), _VP]),
 ]
 
 
@@ -196,6 +198,35 @@ def krylov_solve(method, w, A: Matrix, M: ILU0, b: torch.Tensor, x0: torch.Tenso
     h = hist[: info.iters + 1].cpu().numpy() if history else None
     return {"status": STATUS[info.status], "iters": info.iters, "x": x, "hist": h, "res0": info.res0,
             "relres_rec": info.relres_rec, "relres_true": info.relres_true, "ms": info.ms_solve}
+
+
+def krylov_solve_batched(method, w, A: Matrix, sys_rows, M: ILU0, b: torch.Tensor, x0: torch.Tensor = None,
+                         tol_rel=1e-25, tol_abs=0.0, maxit=1000, check_every=25, history=False):
+    """Solve the nsys independent systems of the block-diagonal A (system s: rows sys_rows[s] ..
+    sys_rows[s+1]-1) together; returns dict(status, x, per-system arrays: statuses, iters, res0,
+    relres_rec, relres_true, and hist (nsys x (maxit+1)) when asked)."""
+    rows = np.ascontiguousarray(np.asarray(sys_rows, dtype=np.int32))
+    nsys = len(rows) - 1
+    rows_dev = torch.as_tensor(rows, device=b.device)
+    x = torch.zeros_like(b) if x0 is None else x0.clone()
+    hist = torch.full((nsys, maxit + 1), float("nan"), dtype=torch.float64, device=b.device) if history else None
+    opts = Opts(float(tol_rel), float(tol_abs), int(maxit), int(check_every), 0, 0,
+                hist.data_ptr() if history else None)
+    infos = (Info * nsys)()
+    st = lib().mpk_krylov_solve_batched(METHODS[method], w, ctypes.byref(A.desc), nsys, rows.ctypes.data,
+                                        _ptr(rows_dev), M.handle if M is not None else None, _ptr(b), _ptr(x),
+                                        ctypes.byref(opts), infos, _stream())
+    if st not in (0, 1, 2, 5):
+        raise MpkError(st, lib().mpk_last_error().decode())
+    out = {"status": STATUS[st], "x": x,
+           "statuses": [STATUS[i.status] for i in infos],
+           "iters": np.array([i.iters for i in infos]), "res0": np.array([i.res0 for i in infos]),
+           "relres_rec": np.array([i.relres_rec for i in infos]),
+           "relres_true": np.array([i.relres_true for i in infos]), "ms": infos[0].ms_solve}
+    if history:
+        h = hist.cpu().numpy()
+        out["hist"] = [h[s_, : out["iters"][s_] + 1] for s_ in range(nsys)]
+    return out
 
 
 def solve_host(method, w, prec, A_tuple, b: np.ndarray, x0: np.ndarray = None, is_complex=False, tol_rel=1e-25,

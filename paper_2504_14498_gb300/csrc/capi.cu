@@ -72,7 +72,7 @@ extern "C" int mpk_spmv_mp(const mpk_csr* A, int w, const double* x_dev, double*
   if (w < 1 || w > 4) return fail(MPK_INVALID_ARG, "w must be 1..4");
   const Ops* o = get_ops(w, A->is_complex ? 2 : 1);
   Csr c{A->n, A->nnz, A->row_ptr, A->col_idx, A->val, A->is_complex};
-  o->spmv(c, x_dev, y_dev, nullptr, nullptr, (cudaStream_t)stream);
+  o->spmv(c, x_dev, y_dev, nullptr, nullptr, nullptr, (cudaStream_t)stream);
   MPK_CUDA(cudaGetLastError());
   return MPK_OK;
 }

@@ -701,10 +701,11 @@ static int build_transpose(mpk_ilu* M, cudaStream_t s) {
 int prepare_trans(mpk_ilu* M, cudaStream_t s) { return build_transpose(M, s); }
 
 // z = M^-1 r or M^-H r, stream-ordered; `done` may be null.
+// bt (nullable): a batch of systems, each with its own binary32 scaling (bt->absmax)
 int precond_apply(const mpk_ilu* M, const Ops* o, bool trans, const double* r, double* z, const int* done,
-                  cudaStream_t s) {
+                  const Batch* bt, cudaStream_t s) {
   if (trans && M->rpT == nullptr) return fail(MPK_INVALID_ARG, "M^H solve needs the transposed factor");
-  const IluHandleView v = M->view(trans);
+  IluHandleView v = M->view(trans);
   launch_trsv_prep(v, done, s);
   int st;
   // M: unit lower L~ then upper U~ with division; M^H: lower U~^H with division then unit upper L~^H
@@ -712,7 +713,12 @@ int precond_apply(const mpk_ilu* M, const Ops* o, bool trans, const double* r, d
     st = o->trsv_mp(v, true, !trans, r, M->vmp, done, s);
     if (st == MPK_OK) st = o->trsv_mp(v, false, trans, M->vmp, z, done, s);
   } else {
-    o->absmax(M->n, r, v.absmax, done, s);
+    if (bt != nullptr && bt->sysid != nullptr) {
+      v.sysid = bt->sysid;
+      v.absmax = bt->absmax;
+      MPK_CUDA(cudaMemsetAsync(bt->absmax, 0, sizeof(unsigned long long) * (size_t)bt->nsys, s));
+    }
+    o->absmax(M->n, r, v.absmax, done, bt, s);
     st = o->trsv32(v, true, !trans, r, nullptr, done, s);
     if (st == MPK_OK) st = o->trsv32(v, false, trans, nullptr, z, done, s);
   }
@@ -922,7 +928,7 @@ extern "C" int mpk_precond_apply(const mpk_ilu* M, int w, int trans, const doubl
     if (st != MPK_OK) return st;
   }
   const Ops* o = get_ops(w, M->cp);
-  int st = precond_apply(M, o, trans != 0, r_dev, z_dev, nullptr, s);
+  int st = precond_apply(M, o, trans != 0, r_dev, z_dev, nullptr, nullptr, s);
   if (st != MPK_OK) return st;
   MPK_CUDA(cudaGetLastError());
   return read_ctl_err(M, s);

@@ -59,10 +59,33 @@ struct DotWs {           // workspace of the fixed-order reduction
   unsigned* counter = nullptr;
 };
 constexpr int kMaxDots = 6;
+// Fixed summation order of the inner products: leaves of kDotLeaf consecutive products, one leaf
+// per thread of a kDotBlockLeaves-thread block; dot_blocks(n) blocks for n entries.
+constexpr int kDotLeaf = 16;
+constexpr int kDotBlockLeaves = 256;
+inline int dot_blocks(int n) {
+  const int m = (n + kDotLeaf - 1) / kDotLeaf;
+  return m < 1 ? 1 : (m + kDotBlockLeaves - 1) / kDotBlockLeaves;
+}
 // doubles of per-block partials needed by up to kMaxDots simultaneous inner products of length n
 inline size_t dot_partial_doubles(int n) { return ((size_t)(n > 0 ? n : 1) + 4095) / 4096 * kMaxDots * 8; }
 
 struct IluHandleView;  // forward
+
+// nsys independent systems stored as consecutive row blocks of one block-diagonal matrix.  Each
+// system has its own scalar slots (S + s * kSysDoubles) and integer state (st + s * ST_COUNT); a
+// system whose ST_DONE is set keeps its iterate and residual (its rows are skipped).
+constexpr int kSysDoubles = S_COUNT * kSlotDoubles;
+struct Batch {
+  int nsys = 1;
+  const int* sysid = nullptr;        // row -> system
+  const int* roff = nullptr;         // nsys + 1 row offsets
+  const int* boff = nullptr;         // nsys + 1: first inner-product block of each system
+  const int* bsys = nullptr;         // inner-product block -> system
+  int nblocks = 0;                   // boff[nsys]
+  const int* st = nullptr;           // per-system state (nullptr: skip no system)
+  unsigned long long* absmax = nullptr;  // nsys scale accumulators of the binary32 substitutions
+};
 
 // Level order of one triangle for the chunk dataflow (see chunk_rows).
 struct LevelOrder {
@@ -83,18 +106,28 @@ struct Order {
 // launch into a no-op once a solve has finished.
 struct Ops {
   int w, cp;
-  void (*spmv)(const Csr& A, const double* x, double* y, const double* b_or_null, const int* done, cudaStream_t s);
+  // bt (nullable): rows of systems whose ST_DONE is set are skipped
+  void (*spmv)(const Csr& A, const double* x, double* y, const double* b_or_null, const int* done, const Batch* bt,
+               cudaStream_t s);
   void (*dots)(int n, int k, const double* const* a, const double* const* b, double* const* out, const DotWs& ws,
                const int* done, cudaStream_t s);
+  // per-system inner products of a batch: system s's k-th result goes to its slot slot0 + k (same
+  // summation order as `dots` on the system alone); partial: nblocks * k entries, counters: nsys
+  void (*dots_seg)(const Batch& bt, int k, const double* const* a, const double* const* b, double* S, int slot0,
+                   double* partial, unsigned* counters, const int* done, cudaStream_t s);
   // y = sum_k coef_k * v_k evaluated left to right; coef == nullptr means exactly 1
   // copy_at_first (nullable, the solve's int state): y = v_0 when the iteration counter is 1
+  // bt (nullable): coefficients per system (coef_k + s * kSysDoubles), done systems skipped
   void (*lincomb)(int n, double* y, int nt, const double* const* coef, const double* const* v,
-                  const int* copy_at_first, const int* done, cudaStream_t s);
+                  const int* copy_at_first, const int* done, const Batch* bt, cudaStream_t s);
   // y = v0 + s2 * (v1 + s1 * v2)
   void (*nested)(int n, double* y, const double* v0, const double* v1, const double* v2, const double* s1,
-                 const double* s2, const int* copy_at_first, const int* done, cudaStream_t s);
+                 const double* s2, const int* copy_at_first, const int* done, const Batch* bt, cudaStream_t s);
   void (*copy)(int n, double* y, const double* x, const int* done, cudaStream_t s);
-  void (*scalar)(int method, int phase, double* S, int* st, double* hist, const int* done, cudaStream_t s);
+  // nsys systems (one thread each); fin (nsys > 1): count of finished systems, and *alldone set
+  // when it reaches nsys; hist: hist_stride doubles per system
+  void (*scalar)(int method, int phase, double* S, int* st, double* hist, const int* done, int nsys, int hist_stride,
+                 int* fin, int* alldone, cudaStream_t s);
   // Substitutions with a binary64 factor and w-component vectors (the paper's "_d").
   int (*trsv_mp)(const IluHandleView& M, bool lower, bool unit, const double* in, double* out, const int* done,
                  cudaStream_t s);
@@ -102,7 +135,8 @@ struct Ops {
   // binary32 vector), upper (in: that vector, out: w-component); scaling by a power of two.
   int (*trsv32)(const IluHandleView& M, bool lower, bool unit, const double* in, double* out, const int* done,
                 cudaStream_t s);
-  void (*absmax)(int n, const double* v, unsigned long long* out, const int* done, cudaStream_t s);
+  // bt (nullable): one accumulator per system (out + s)
+  void (*absmax)(int n, const double* v, unsigned long long* out, const int* done, const Batch* bt, cudaStream_t s);
 };
 const Ops* get_ops(int w, int cp);
 
@@ -138,6 +172,7 @@ struct IluHandleView {
   LevelOrder lv_lo, lv_up;           // level orders (chunk dataflow) of the two triangles
   Order ch_lo, ch_up;                // chunk orders (dependency-driven, row chains in warps)
   SellTri sl_lo, sl_up;              // repacked triangles of the substitutions
+  const int* sysid = nullptr;        // batch: row -> system (absmax holds one scale per system)
 };
 enum CtlIdx : int { CTL_EPOCH = 0, CTL_TICKET_LO, CTL_TICKET_UP, CTL_ERR, CTL_FAIL_ROW, CTL_COUNT };
 

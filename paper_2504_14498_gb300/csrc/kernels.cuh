@@ -52,14 +52,17 @@ __device__ __forceinline__ N<W, CP> warp_sum(N<W, CP> a) {  // fixed tree order
 // ---------------------------------------------------------------------------------------------
 // y = A x  (b != nullptr: y = b - A x), one thread per row, CSR order from 0.
 // ---------------------------------------------------------------------------------------------
+// A batch (sysid != nullptr) skips the rows of systems whose state sst has ST_DONE set.
 template <int W, int CP>
 __global__ void __launch_bounds__(kBlock) k_spmv(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                                  const double* __restrict__ val, const double* __restrict__ x,
                                                  double* __restrict__ y, const double* __restrict__ b,
-                                                 const int* __restrict__ done) {
+                                                 const int* __restrict__ done, const int* __restrict__ sysid,
+                                                 const int* __restrict__ sst) {
   if (is_done(done)) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  if (sysid != nullptr && sst != nullptr && sst[sysid[i] * ST_COUNT + ST_DONE] != 0) return;
   N<W, CP> acc = n_zero<W, CP>();
   const int p1 = rp[i + 1];
   for (int p = rp[i]; p < p1; ++p) {
@@ -86,12 +89,8 @@ __global__ void __launch_bounds__(kBlock) k_spmv(int n, const int* __restrict__ 
 // warp, d = 32..128 across the warps of a block, d >= 256 across blocks (the last block to
 // finish walks the per-block partials).  The result depends on n only, not on the hardware.
 // ---------------------------------------------------------------------------------------------
-constexpr int kDotLeaf = 16;
 constexpr int kLeavesPerBlock = kBlock;  // one leaf per thread
-inline int dot_blocks(int n) {
-  const int m = (n + kDotLeaf - 1) / kDotLeaf;
-  return m < 1 ? 1 : (m + kLeavesPerBlock - 1) / kLeavesPerBlock;
-}
+static_assert(kLeavesPerBlock == kDotBlockLeaves, "inner-product block layout");
 
 template <int K>
 struct DotArgs {
@@ -100,15 +99,18 @@ struct DotArgs {
   double* out[K];
 };
 
+// One block of the fixed-order reduction of K inner products of length n: block lb of G
+// (a, b already offset to the first entry), partials[0 .. G*K) and counter private to these n
+// entries.  The last block to finish reduces the partials and writes out[k].
 template <int W, int CP, int K>
-__global__ void __launch_bounds__(kBlock) k_dots(int n, DotArgs<K> args, double* __restrict__ partial,
-                                                 unsigned* __restrict__ counter, const int* __restrict__ done) {
-  if (is_done(done)) return;
+__device__ __forceinline__ void dots_block(int n, int lb, int G, const double* const* a, const double* const* b,
+                                           double* const* out, double* __restrict__ partial,
+                                           unsigned* __restrict__ counter) {
   __shared__ __align__(16) double sh[(kBlock / 32) * K * CP * W];
   __shared__ bool last;
   const int m = (n + kDotLeaf - 1) / kDotLeaf;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int block_leaf0 = blockIdx.x * kLeavesPerBlock;
+  const int block_leaf0 = lb * kLeavesPerBlock;
   const int leaf = block_leaf0 + threadIdx.x;
   N<W, CP> acc[K];
 #pragma unroll
@@ -116,11 +118,11 @@ __global__ void __launch_bounds__(kBlock) k_dots(int n, DotArgs<K> args, double*
   if (leaf < m) {
     const int i0 = leaf * kDotLeaf, i1 = min(n, i0 + kDotLeaf);
 #pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] = n_mul_conj<W, CP>(n_load<W, CP>(args.a[k], i0), n_load<W, CP>(args.b[k], i0));
+    for (int k = 0; k < K; ++k) acc[k] = n_mul_conj<W, CP>(n_load<W, CP>(a[k], i0), n_load<W, CP>(b[k], i0));
     for (int i = i0 + 1; i < i1; ++i) {
 #pragma unroll
       for (int k = 0; k < K; ++k)
-        acc[k] = n_add<W, CP>(acc[k], n_mul_conj<W, CP>(n_load<W, CP>(args.a[k], i), n_load<W, CP>(args.b[k], i)));
+        acc[k] = n_add<W, CP>(acc[k], n_mul_conj<W, CP>(n_load<W, CP>(a[k], i), n_load<W, CP>(b[k], i)));
     }
   }
   // levels d = 1..16 across lanes
@@ -153,33 +155,63 @@ __global__ void __launch_bounds__(kBlock) k_dots(int n, DotArgs<K> args, double*
     }
     if (lane == 0) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) n_store<W, CP>(partial, (int64_t)blockIdx.x * K + k, acc[k]);
+      for (int k = 0; k < K; ++k) n_store<W, CP>(partial, (int64_t)lb * K + k, acc[k]);
       __threadfence();
       const unsigned t = atomicAdd(counter, 1u);
-      last = (t == gridDim.x - 1);
+      last = (t == (unsigned)G - 1);
     }
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
   // levels d >= 256 across blocks, on the partials
-  const int G = gridDim.x;
   for (int e = 1; e < G; e <<= 1) {
-    for (int b = threadIdx.x * 2 * e; b + e < G; b += blockDim.x * 2 * e) {
+    for (int bb = threadIdx.x * 2 * e; bb + e < G; bb += blockDim.x * 2 * e) {
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        N<W, CP> x = n_load<W, CP>(partial, (int64_t)b * K + k);
-        N<W, CP> y = n_load<W, CP>(partial, (int64_t)(b + e) * K + k);
-        n_store<W, CP>(partial, (int64_t)b * K + k, n_add<W, CP>(x, y));
+        N<W, CP> x = n_load<W, CP>(partial, (int64_t)bb * K + k);
+        N<W, CP> y = n_load<W, CP>(partial, (int64_t)(bb + e) * K + k);
+        n_store<W, CP>(partial, (int64_t)bb * K + k, n_add<W, CP>(x, y));
       }
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) n_store<W, CP>(args.out[k], 0, n_load<W, CP>(partial, k));
+    for (int k = 0; k < K; ++k) n_store<W, CP>(out[k], 0, n_load<W, CP>(partial, k));
     *counter = 0u;
   }
+}
+
+template <int W, int CP, int K>
+__global__ void __launch_bounds__(kBlock) k_dots(int n, DotArgs<K> args, double* __restrict__ partial,
+                                                 unsigned* __restrict__ counter, const int* __restrict__ done) {
+  if (is_done(done)) return;
+  dots_block<W, CP, K>(n, blockIdx.x, gridDim.x, args.a, args.b, args.out, partial, counter);
+}
+
+// Segmented: block b belongs to system bsys[b] (blocks boff[s] .. boff[s+1]-1); every system is
+// reduced exactly as k_dots would reduce it alone.  Systems whose state has ST_DONE set are skipped
+// by all their blocks (the state does not change during the launch).
+template <int W, int CP, int K>
+__global__ void __launch_bounds__(kBlock) k_dots_seg(Batch bt, DotArgs<K> args, double* __restrict__ S, int slot0,
+                                                     double* __restrict__ partial, unsigned* __restrict__ counters,
+                                                     const int* __restrict__ done) {
+  if (is_done(done)) return;
+  const int sy = bt.bsys[blockIdx.x];
+  if (bt.st != nullptr && bt.st[sy * ST_COUNT + ST_DONE] != 0) return;
+  const int r0 = bt.roff[sy], n = bt.roff[sy + 1] - r0;
+  const int b0 = bt.boff[sy], G = bt.boff[sy + 1] - b0;
+  const double* a[K];
+  const double* b[K];
+  double* out[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    a[k] = args.a[k] + (int64_t)r0 * CP * W;
+    b[k] = args.b[k] + (int64_t)r0 * CP * W;
+    out[k] = S + (int64_t)sy * kSysDoubles + (slot0 + k) * kSlotDoubles;
+  }
+  dots_block<W, CP, K>(n, blockIdx.x - b0, G, a, b, out, partial + (int64_t)b0 * K * CP * W, counters + sy);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -192,9 +224,36 @@ struct LinArgs {
   int nt;
   const int* copy_at_first;  // non-null: at iteration 1 (st[ST_IT] == 1) y = v[0] instead
 };
+// Batch (sysid != nullptr): coefficients of system s at a.s[k] + s * kSysDoubles, its iteration
+// counter in sst, and the rows of finished systems left untouched.
 template <int W, int CP>
-__global__ void __launch_bounds__(kBlock) k_lincomb(int n, LinArgs a, const int* __restrict__ done) {
+__global__ void __launch_bounds__(kBlock) k_lincomb(int n, LinArgs a, const int* __restrict__ done,
+                                                    const int* __restrict__ sysid, const int* __restrict__ sst) {
   if (is_done(done)) return;
+  if (sysid != nullptr) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      const int sy = sysid[i];
+      const int* st = sst + sy * ST_COUNT;
+      if (st[ST_DONE] != 0) continue;
+      if (a.copy_at_first != nullptr && st[ST_IT] == 1) {
+        n_store<W, CP>(a.y, i, n_load<W, CP>(a.v[0], i));
+        continue;
+      }
+      const int64_t so = (int64_t)sy * kSysDoubles;
+      N<W, CP> acc = n_load<W, CP>(a.v[0], i);
+      if (a.s[0] != nullptr) acc = n_mul<W, CP>(n_load<W, CP>(a.s[0] + so, 0), acc);
+#pragma unroll
+      for (int k = 1; k < 3; ++k) {
+        if (k < a.nt) {
+          N<W, CP> t = n_load<W, CP>(a.v[k], i);
+          if (a.s[k] != nullptr) t = n_mul<W, CP>(n_load<W, CP>(a.s[k] + so, 0), t);
+          acc = n_add<W, CP>(acc, t);
+        }
+      }
+      n_store<W, CP>(a.y, i, acc);
+    }
+    return;
+  }
   if (a.copy_at_first != nullptr && a.copy_at_first[ST_IT] == 1) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
       n_store<W, CP>(a.y, i, n_load<W, CP>(a.v[0], i));
@@ -221,8 +280,25 @@ __global__ void __launch_bounds__(kBlock) k_lincomb(int n, LinArgs a, const int*
 template <int W, int CP>
 __global__ void __launch_bounds__(kBlock) k_nested(int n, double* y, const double* v0, const double* v1,
                                                    const double* v2, const double* s1p, const double* s2p,
-                                                   const int* copy_at_first, const int* __restrict__ done) {
+                                                   const int* copy_at_first, const int* __restrict__ done,
+                                                   const int* __restrict__ sysid, const int* __restrict__ sst) {
   if (is_done(done)) return;
+  if (sysid != nullptr) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      const int sy = sysid[i];
+      const int* st = sst + sy * ST_COUNT;
+      if (st[ST_DONE] != 0) continue;
+      if (copy_at_first != nullptr && st[ST_IT] == 1) {
+        n_store<W, CP>(y, i, n_load<W, CP>(v0, i));
+        continue;
+      }
+      const int64_t so = (int64_t)sy * kSysDoubles;
+      const N<W, CP> s1 = n_load<W, CP>(s1p + so, 0), s2 = n_load<W, CP>(s2p + so, 0);
+      N<W, CP> inner = n_add<W, CP>(n_load<W, CP>(v1, i), n_mul<W, CP>(s1, n_load<W, CP>(v2, i)));
+      n_store<W, CP>(y, i, n_add<W, CP>(n_load<W, CP>(v0, i), n_mul<W, CP>(s2, inner)));
+    }
+    return;
+  }
   if (copy_at_first != nullptr && copy_at_first[ST_IT] == 1) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
       n_store<W, CP>(y, i, n_load<W, CP>(v0, i));
@@ -244,11 +320,24 @@ __global__ void __launch_bounds__(kBlock) k_copy(int n, double* __restrict__ y, 
 
 // Largest |leading component| (real and imaginary parts) as the bit pattern of a nonnegative
 // double, combined with atomicMax (bit order equals numeric order for nonnegative doubles).
+// Batch (sysid != nullptr): one accumulator per system, out[sysid[i]].
 template <int W, int CP>
 __global__ void __launch_bounds__(kBlock) k_absmax(int n, const double* __restrict__ v,
                                                    unsigned long long* __restrict__ out,
-                                                   const int* __restrict__ done) {
+                                                   const int* __restrict__ done, const int* __restrict__ sysid) {
   if (is_done(done)) return;
+  if (sysid != nullptr) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      const double* p = v + (int64_t)i * CP * W;
+      unsigned long long a = (unsigned long long)__double_as_longlong(fabs(p[0]));
+      if constexpr (CP == 2) {
+        unsigned long long b = (unsigned long long)__double_as_longlong(fabs(p[W]));
+        a = b > a ? b : a;
+      }
+      if (a != 0ull) atomicMax(out + sysid[i], a);
+    }
+    return;
+  }
   unsigned long long m = 0ull;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const double* p = v + (int64_t)i * CP * W;
@@ -290,10 +379,27 @@ __device__ __forceinline__ void next_iter(int* st) {
   if (it > st[ST_MAXIT]) finish(st, MPK_MAXIT, st[ST_MAXIT]);
 }
 
+// One thread per system: system sy uses S + sy * kSysDoubles, st + sy * ST_COUNT and
+// hist + sy * hist_stride.  With done != nullptr a finished system is skipped; when a system
+// finishes in a batch (fin != nullptr) it is counted, and the last one sets *alldone.
+template <int W, int CP>
+__device__ void scalar_phase(int method, int phase, double* __restrict__ S, int* __restrict__ st,
+                             double* __restrict__ hist);
 template <int W, int CP>
 __global__ void k_scalar(int method, int phase, double* __restrict__ S, int* __restrict__ st,
-                         double* __restrict__ hist, const int* __restrict__ done) {
-  if (is_done(done) || threadIdx.x != 0 || blockIdx.x != 0) return;
+                         double* __restrict__ hist, const int* __restrict__ done, int nsys, int hist_stride,
+                         int* __restrict__ fin, int* __restrict__ alldone) {
+  const int sy = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sy >= nsys || is_done(done)) return;
+  int* sst = st + (int64_t)sy * ST_COUNT;
+  if (done != nullptr && sst[ST_DONE] != 0) return;
+  scalar_phase<W, CP>(method, phase, S + (int64_t)sy * kSysDoubles, sst,
+                      hist != nullptr ? hist + (int64_t)sy * hist_stride : nullptr);
+  if (fin != nullptr && sst[ST_DONE] != 0 && atomicAdd(fin, 1) == nsys - 1) *alldone = 1;
+}
+template <int W, int CP>
+__device__ void scalar_phase(int method, int phase, double* __restrict__ S, int* __restrict__ st,
+                             double* __restrict__ hist) {
   using Num = N<W, CP>;
   const int it = st[ST_IT];
   switch (phase) {
@@ -1056,7 +1162,7 @@ __global__ void __launch_bounds__(kTrsvWarps * 32, 1)
   const TS* __restrict__ tval = (const TS*)T.val;
   const TS* __restrict__ tdia = (const TS*)T.dia;
   float* __restrict__ mine = lower ? M.v32 : reinterpret_cast<float*>(M.pk);
-  const int e = scale_exponent(M.absmax);
+  const int e1 = M.sysid == nullptr ? scale_exponent(M.absmax) : 0;  // one system: one scale
   const int lane = threadIdx.x & 31;
   const int G = gridDim.x * (blockDim.x >> 5);
   const int g = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
@@ -1084,6 +1190,7 @@ __global__ void __launch_bounds__(kTrsvWarps * 32, 1)
       }
     }
     float ar = 0.0f, ai = 0.0f, dr = 1.0f, di = 0.0f;
+    const int e = (M.sysid != nullptr && i >= 0) ? scale_exponent(M.absmax + M.sysid[i]) : e1;
     if (i >= 0) {
       if (lower) {
         const double* q = in + (int64_t)i * CP * W;
@@ -1231,9 +1338,11 @@ inline int persistent_blocks(KernelT kernel) {
 
 template <int W, int CP>
 struct Launch {
-  static void spmv(const Csr& A, const double* x, double* y, const double* b, const int* done, cudaStream_t s) {
+  static void spmv(const Csr& A, const double* x, double* y, const double* b, const int* done, const Batch* bt,
+                   cudaStream_t s) {
     count_launch();
-    k_spmv<W, CP><<<(A.n + kBlock - 1) / kBlock, kBlock, 0, s>>>(A.n, A.rp, A.ci, A.val, x, y, b, done);
+    k_spmv<W, CP><<<(A.n + kBlock - 1) / kBlock, kBlock, 0, s>>>(A.n, A.rp, A.ci, A.val, x, y, b, done,
+                                                                  bt ? bt->sysid : nullptr, bt ? bt->st : nullptr);
   }
   template <int K>
   static void dotsK(int n, const double* const* a, const double* const* b, double* const* out, const DotWs& ws,
@@ -1253,8 +1362,26 @@ struct Launch {
     else if (k == 2) dotsK<2>(n, a, b, out, ws, done, s);
     else dotsK<6>(n, a, b, out, ws, done, s);
   }
+  template <int K>
+  static void dotsSegK(const Batch& bt, const double* const* a, const double* const* b, double* S, int slot0,
+                       double* partial, unsigned* counters, const int* done, cudaStream_t s) {
+    DotArgs<K> args;
+    for (int k = 0; k < K; ++k) {
+      args.a[k] = a[k];
+      args.b[k] = b[k];
+      args.out[k] = nullptr;
+    }
+    count_launch();
+    k_dots_seg<W, CP, K><<<bt.nblocks, kBlock, 0, s>>>(bt, args, S, slot0, partial, counters, done);
+  }
+  static void dots_seg(const Batch& bt, int k, const double* const* a, const double* const* b, double* S, int slot0,
+                       double* partial, unsigned* counters, const int* done, cudaStream_t s) {
+    if (k == 1) dotsSegK<1>(bt, a, b, S, slot0, partial, counters, done, s);
+    else if (k == 2) dotsSegK<2>(bt, a, b, S, slot0, partial, counters, done, s);
+    else dotsSegK<6>(bt, a, b, S, slot0, partial, counters, done, s);
+  }
   static void lincomb(int n, double* y, int nt, const double* const* coef, const double* const* v,
-                      const int* copy_at_first, const int* done, cudaStream_t s) {
+                      const int* copy_at_first, const int* done, const Batch* bt, cudaStream_t s) {
     LinArgs a;
     a.y = y;
     a.nt = nt;
@@ -1264,24 +1391,27 @@ struct Launch {
       a.s[k] = k < nt ? coef[k] : nullptr;
     }
     count_launch();
-    k_lincomb<W, CP><<<grid_for(n), kBlock, 0, s>>>(n, a, done);
+    k_lincomb<W, CP><<<grid_for(n), kBlock, 0, s>>>(n, a, done, bt ? bt->sysid : nullptr, bt ? bt->st : nullptr);
   }
   static void nested(int n, double* y, const double* v0, const double* v1, const double* v2, const double* s1,
-                     const double* s2, const int* copy_at_first, const int* done, cudaStream_t s) {
+                     const double* s2, const int* copy_at_first, const int* done, const Batch* bt, cudaStream_t s) {
     count_launch();
-    k_nested<W, CP><<<grid_for(n), kBlock, 0, s>>>(n, y, v0, v1, v2, s1, s2, copy_at_first, done);
+    k_nested<W, CP><<<grid_for(n), kBlock, 0, s>>>(n, y, v0, v1, v2, s1, s2, copy_at_first, done,
+                                                    bt ? bt->sysid : nullptr, bt ? bt->st : nullptr);
   }
   static void copy(int n, double* y, const double* x, const int* done, cudaStream_t s) {
     count_launch();
     k_copy<W, CP><<<grid_for(n), kBlock, 0, s>>>(n, y, x, done);
   }
-  static void scalar(int method, int phase, double* S, int* st, double* hist, const int* done, cudaStream_t s) {
+  static void scalar(int method, int phase, double* S, int* st, double* hist, const int* done, int nsys,
+                     int hist_stride, int* fin, int* alldone, cudaStream_t s) {
     count_launch();
-    k_scalar<W, CP><<<1, 32, 0, s>>>(method, phase, S, st, hist, done);
+    k_scalar<W, CP><<<(nsys + 63) / 64, 64, 0, s>>>(method, phase, S, st, hist, done, nsys, hist_stride, fin, alldone);
   }
-  static void absmax(int n, const double* v, unsigned long long* out, const int* done, cudaStream_t s) {
+  static void absmax(int n, const double* v, unsigned long long* out, const int* done, const Batch* bt,
+                     cudaStream_t s) {
     count_launch();
-    k_absmax<W, CP><<<grid_for(n), kBlock, 0, s>>>(n, v, out, done);
+    k_absmax<W, CP><<<grid_for(n), kBlock, 0, s>>>(n, v, out, done, bt ? bt->sysid : nullptr);
   }
   static int trsv_mp(const IluHandleView& M, bool lower, bool unit, const double* in, double* out, const int* done,
                      cudaStream_t s) {
@@ -1316,6 +1446,7 @@ struct Launch {
     o.cp = CP;
     o.spmv = &spmv;
     o.dots = &dots;
+    o.dots_seg = &dots_seg;
     o.lincomb = &lincomb;
     o.nested = &nested;
     o.copy = &copy;

@@ -9,13 +9,14 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "internal.h"
 
 namespace mpk {
 int precond_apply(const mpk_ilu* M, const Ops* o, bool trans, const double* r, double* z, const int* done,
-                  cudaStream_t s);
+                  const Batch* bt, cudaStream_t s);
 int prepare_trans(mpk_ilu* M, cudaStream_t s);
 int read_ctl_err(const mpk_ilu* M, cudaStream_t s);
 int transpose_matrix(const Csr& A, int* rpT, int* ciT, double* vT, cudaStream_t s);
@@ -25,6 +26,8 @@ using namespace mpk;
 
 namespace {
 
+// A solve of nsys systems (nsys == 1: the plain single-system solve; a batch otherwise, with
+// per-system scalars, segmented inner products and finished systems frozen).
 struct Ctx {
   const Ops* o;
   Csr A, AH;
@@ -33,19 +36,34 @@ struct Ctx {
   cudaStream_t s;
   double* S;
   int* st;
-  const int* done;
+  const int* done;  // single: st[ST_DONE]; batch: the "all systems finished" flag
   double* hist;
+  int hist_stride = 0;
   DotWs dws;
+  const Batch* bt = nullptr;  // nullptr for a single system
+  double* seg_partial = nullptr;
+  unsigned* seg_counters = nullptr;
+  int* fin = nullptr;
+  int* alldone = nullptr;
   int err = MPK_OK;
 
+  int nsys() const { return bt ? bt->nsys : 1; }
   double* slot(int k) const { return S + k * kSlotDoubles; }
   void dot(const double* a, const double* b, int out_slot) {
     const double* av[1] = {a};
     const double* bv[1] = {b};
+    if (bt) {
+      o->dots_seg(*bt, 1, av, bv, S, out_slot, seg_partial, seg_counters, done, s);
+      return;
+    }
     double* ov[1] = {slot(out_slot)};
     o->dots(n, 1, av, bv, ov, dws, done, s);
   }
   void dots(int k, const double* const* a, const double* const* b, int first_slot) {
+    if (bt) {
+      o->dots_seg(*bt, k, a, b, S, first_slot, seg_partial, seg_counters, done, s);
+      return;
+    }
     double* ov[kMaxDots];
     for (int q = 0; q < k; ++q) ov[q] = slot(first_slot + q);
     o->dots(n, k, a, b, ov, dws, done, s);
@@ -56,21 +74,21 @@ struct Ctx {
     const double* coef[3] = {c0 >= 0 ? slot(c0) : nullptr, c1 >= 0 ? slot(c1) : nullptr, c2 >= 0 ? slot(c2) : nullptr};
     const double* v[3] = {v0, v1, v2};
     const int nt = (c1 == -2) ? 1 : ((c2 == -2) ? 2 : 3);
-    o->lincomb(n, y, nt, coef, v, copy_at_first ? st : nullptr, done, s);
+    o->lincomb(n, y, nt, coef, v, copy_at_first ? st : nullptr, done, bt, s);
   }
   // y = v0 + s2 (v1 + s1 v2); copy_at_first: y = v0 at iteration 1
   void nested(double* y, const double* v0, const double* v1, const double* v2, int s1, int s2, bool copy_at_first) {
-    o->nested(n, y, v0, v1, v2, slot(s1), slot(s2), copy_at_first ? st : nullptr, done, s);
+    o->nested(n, y, v0, v1, v2, slot(s1), slot(s2), copy_at_first ? st : nullptr, done, bt, s);
   }
-  void scalar(int phase) { o->scalar(method, phase, S, st, hist, done, s); }
-  void mv(const double* x, double* y) { o->spmv(A, x, y, nullptr, done, s); }
-  void mvh(const double* x, double* y) { o->spmv(AH, x, y, nullptr, done, s); }
+  void scalar(int phase) { o->scalar(method, phase, S, st, hist, done, nsys(), hist_stride, fin, alldone, s); }
+  void mv(const double* x, double* y) { o->spmv(A, x, y, nullptr, done, bt, s); }
+  void mvh(const double* x, double* y) { o->spmv(AH, x, y, nullptr, done, bt, s); }
   void prec(bool trans, const double* r, double* z) {
     if (M == nullptr) {
       o->copy(n, z, r, done, s);
       return;
     }
-    int st_ = precond_apply(M, o, trans, r, z, done, s);
+    int st_ = precond_apply(M, o, trans, r, z, done, bt, s);
     if (st_ != MPK_OK && err == MPK_OK) err = st_;
   }
 };
@@ -205,8 +223,40 @@ static int validate_csr(const mpk_csr* A) {
   return MPK_OK;
 }
 
+// Rows -> system, and the segmented inner products' block layout, of a batch with row offsets roff.
+__global__ void k_batch_sysid(int n, int nsys, const int* __restrict__ roff, int* __restrict__ sysid,
+                              int* __restrict__ bad) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int lo = 0, hi = nsys;  // largest sy with roff[sy] <= i
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (roff[mid] <= i) lo = mid;
+      else hi = mid;
+    }
+    sysid[i] = lo;
+  }
+  (void)bad;
+}
+// Every stored column of row i lies in row i's system block (block-diagonal structure).
+__global__ void k_batch_check(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                              const int* __restrict__ roff, const int* __restrict__ sysid, int* __restrict__ bad) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int sy = sysid[i], lo = roff[sy], hi = roff[sy + 1];
+    for (int p = rp[i]; p < rp[i + 1]; ++p)
+      if (ci[p] < lo || ci[p] >= hi) atomicMin(bad, i);
+  }
+}
+__global__ void k_batch_bsys(int nsys, const int* __restrict__ boff, int* __restrict__ bsys) {
+  for (int sy = blockIdx.x; sy < nsys; sy += gridDim.x)
+    for (int b = boff[sy] + threadIdx.x; b < boff[sy + 1]; b += blockDim.x) bsys[b] = sy;
+}
+
+// nsys == 1 and roff_host == nullptr: one system.  Otherwise A is block-diagonal with the systems'
+// rows at roff_host[s] .. roff_host[s+1]-1 (host copy) / roff_dev (device copy); infos has nsys
+// entries; hist_dev (nullable) nsys * (maxit + 1) doubles.
 static int solve_impl(int method, int w, const mpk_csr* Ac, const mpk_ilu* Mc, const double* b, double* x,
-                      const mpk_opts* opts, mpk_info* info, cudaStream_t s) {
+                      const mpk_opts* opts, mpk_info* infos, cudaStream_t s, int nsys, const int* roff_host,
+                      const int* roff_dev) {
   const int n = Ac->n, cp = Ac->is_complex ? 2 : 1;
   const int64_t vlen = (int64_t)n * cp * w;
   mpk_ilu* M = const_cast<mpk_ilu*>(Mc);
@@ -214,6 +264,7 @@ static int solve_impl(int method, int w, const mpk_csr* Ac, const mpk_ilu* Mc, c
   if (o == nullptr) return fail(MPK_INVALID_ARG, "unsupported (w, complex)");
   const int check_every = opts->check_every > 0 ? opts->check_every : 25;
   const int maxit = opts->maxit;
+  const bool batched = roff_host != nullptr;
 
   Ctx c;
   c.o = o;
@@ -223,6 +274,7 @@ static int solve_impl(int method, int w, const mpk_csr* Ac, const mpk_ilu* Mc, c
   c.n = n;
   c.s = s;
   c.hist = opts->hist_dev;
+  c.hist_stride = maxit + 1;
 
   cudaEvent_t e0, e1;
   MPK_CUDA(cudaEventCreate(&e0));
@@ -233,24 +285,89 @@ static int solve_impl(int method, int w, const mpk_csr* Ac, const mpk_ilu* Mc, c
     int st = prepare_trans(M, s);
     if (st != MPK_OK) return st;
   }
+  // batch layout: inner-product blocks per system (host scan of the row offsets)
+  std::vector<int> boff_h;
+  int nblocks = 0;
+  if (batched) {
+    boff_h.resize((size_t)nsys + 1);
+    for (int sy = 0; sy < nsys; ++sy) {
+      boff_h[sy] = nblocks;
+      nblocks += dot_blocks(roff_host[sy + 1] - roff_host[sy]);
+    }
+    boff_h[nsys] = nblocks;
+  }
   const int nvec = 17;
   const size_t vec_bytes = (sizeof(double) * (size_t)vlen + 255) & ~(size_t)255;
-  const size_t small_bytes = sizeof(double) * (S_COUNT * kSlotDoubles + dot_partial_doubles(n)) + 64;
+  const size_t S_bytes = (sizeof(double) * (size_t)kSysDoubles * nsys + 255) & ~(size_t)255;
+  const size_t part_bytes = batched ? (sizeof(double) * (size_t)nblocks * kMaxDots * 8 + 255) & ~(size_t)255
+                                    : (sizeof(double) * dot_partial_doubles(n) + 255) & ~(size_t)255;
+  const size_t st_bytes = (sizeof(int) * ((size_t)ST_COUNT * nsys + 8) + 255) & ~(size_t)255;
+  const size_t cnt_bytes = (sizeof(unsigned) * ((size_t)nsys + 8) + 255) & ~(size_t)255;
+  const size_t batch_bytes = batched ? (sizeof(int) * ((size_t)n + 2 * ((size_t)nsys + 1) + nblocks) +
+                                        sizeof(unsigned long long) * (size_t)nsys + 1024)
+                                     : 0;
+  const size_t total = vec_bytes * nvec + S_bytes + part_bytes + st_bytes + cnt_bytes + batch_bytes + 256;
   char* base = nullptr;
-  MPK_CUDA(cudaMallocAsync((void**)&base, vec_bytes * nvec + small_bytes + 256, s));
-  MPK_CUDA(cudaMemsetAsync(base, 0, vec_bytes * nvec + small_bytes + 256, s));
+  MPK_CUDA(cudaMallocAsync((void**)&base, total, s));
+  MPK_CUDA(cudaMemsetAsync(base + vec_bytes * nvec, 0, total - vec_bytes * nvec, s));
+  MPK_CUDA(cudaMemsetAsync(base, 0, vec_bytes * nvec, s));
   std::vector<double*> V(nvec);
   for (int k = 0; k < nvec; ++k) V[k] = (double*)(base + vec_bytes * k);
   char* tail = base + vec_bytes * nvec;
   c.S = (double*)tail;
-  c.dws.partial = c.S + S_COUNT * kSlotDoubles;
-  char* ints = (char*)(c.dws.partial + dot_partial_doubles(n));
-  c.st = (int*)ints;
-  c.dws.counter = (unsigned*)(ints + 32);
-  c.done = c.st + ST_DONE;
+  tail += S_bytes;
+  double* partial = (double*)tail;
+  tail += part_bytes;
+  c.st = (int*)tail;
+  int* gstate = c.st + (size_t)ST_COUNT * nsys;  // [0] finished systems, [1] all finished
+  tail += st_bytes;
+  unsigned* counters = (unsigned*)tail;
+  tail += cnt_bytes;
+  c.dws.partial = partial;
+  c.dws.counter = counters;
+  Batch bt;
+  if (batched) {
+    unsigned long long* amax = (unsigned long long*)(((uintptr_t)tail + 15) & ~(uintptr_t)15);
+    int* sysid = (int*)(amax + nsys);
+    int* boff = sysid + n;
+    int* bsys = boff + nsys + 1;
+    int* bad = bsys + nblocks;
+    MPK_CUDA(cudaMemcpyAsync(boff, boff_h.data(), sizeof(int) * ((size_t)nsys + 1), cudaMemcpyHostToDevice, s));
+    int bad0 = INT_MAX;
+    MPK_CUDA(cudaMemcpyAsync(bad, &bad0, sizeof(int), cudaMemcpyHostToDevice, s));
+    count_launch(3);
+    k_batch_sysid<<<(n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096, 256, 0, s>>>(n, nsys, roff_dev, sysid, bad);
+    k_batch_check<<<(n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096, 256, 0, s>>>(n, Ac->row_ptr, Ac->col_idx,
+                                                                                   roff_dev, sysid, bad);
+    k_batch_bsys<<<nsys < 1024 ? nsys : 1024, 128, 0, s>>>(nsys, boff, bsys);
+    MPK_CUDA(cudaGetLastError());
+    int badh = INT_MAX;
+    MPK_CUDA(cudaMemcpyAsync(&badh, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MPK_CUDA(cudaStreamSynchronize(s));
+    if (badh != INT_MAX) {
+      cudaFreeAsync(base, s);
+      return fail(MPK_INVALID_ARG, "row " + std::to_string(badh) + " has a column outside its system's block");
+    }
+    bt.nsys = nsys;
+    bt.sysid = sysid;
+    bt.roff = roff_dev;
+    bt.boff = boff;
+    bt.bsys = bsys;
+    bt.nblocks = nblocks;
+    bt.st = c.st;
+    bt.absmax = amax;
+    c.bt = &bt;
+    c.seg_partial = partial;
+    c.seg_counters = counters;
+    c.fin = gstate;
+    c.alldone = gstate + 1;
+    c.done = gstate + 1;
+  } else {
+    c.done = c.st + ST_DONE;
+  }
 
   int* ahbuf = nullptr;
-  if (method == MPK_BICG) {  // A^H for q~ = A^H p~
+  if (method == MPK_BICG) {  // A^H for q~ = A^H p~ (block-diagonal stays block-diagonal)
     const size_t nnz = (size_t)Ac->nnz;
     MPK_CUDA(cudaMallocAsync((void**)&ahbuf, sizeof(int) * ((size_t)n + 1 + nnz) + sizeof(double) * nnz * cp + 16, s));
     int* rpT = ahbuf;
@@ -261,15 +378,32 @@ static int solve_impl(int method, int w, const mpk_csr* Ac, const mpk_ilu* Mc, c
     c.AH = Csr{n, Ac->nnz, rpT, ciT, vT, Ac->is_complex};
   }
 
-  int st_init[ST_COUNT] = {0, MPK_MAXIT, 0, 0, maxit, opts->flags};
-  MPK_CUDA(cudaMemcpyAsync(c.st, st_init, sizeof(st_init), cudaMemcpyHostToDevice, s));
-  double tolv[2] = {opts->tol_rel, opts->tol_abs};
-  MPK_CUDA(cudaMemcpyAsync(c.slot(S_TOL) + 1, tolv, sizeof(tolv), cudaMemcpyHostToDevice, s));
+  {
+    std::vector<int> st_init((size_t)ST_COUNT * nsys);
+    for (int sy = 0; sy < nsys; ++sy) {
+      int* q = st_init.data() + (size_t)sy * ST_COUNT;
+      q[ST_DONE] = 0;
+      q[ST_STATUS] = MPK_MAXIT;
+      q[ST_ITERS] = 0;
+      q[ST_IT] = 0;
+      q[ST_MAXIT] = maxit;
+      q[ST_FLAGS] = opts->flags;
+    }
+    MPK_CUDA(cudaMemcpyAsync(c.st, st_init.data(), sizeof(int) * st_init.size(), cudaMemcpyHostToDevice, s));
+    std::vector<double> tolv((size_t)2 * nsys);
+    for (int sy = 0; sy < nsys; ++sy) {
+      tolv[2 * sy] = opts->tol_rel;
+      tolv[2 * sy + 1] = opts->tol_abs;
+    }
+    MPK_CUDA(cudaMemcpy2DAsync(c.slot(S_TOL) + 1, sizeof(double) * kSysDoubles, tolv.data(), 2 * sizeof(double),
+                               2 * sizeof(double), nsys, cudaMemcpyHostToDevice, s));
+    MPK_CUDA(cudaStreamSynchronize(s));  // the host buffers above go out of scope
+  }
 
   double* r = V[0];
   double* rt = V[1];
   // r = b - A x0, r~ = r, ||r0||
-  o->spmv(c.A, x, r, b, c.done, s);
+  o->spmv(c.A, x, r, b, c.done, nullptr, s);
   o->copy(n, rt, r, c.done, s);
   c.dot(r, r, S_D0);
   c.scalar(PH_INIT);
@@ -283,7 +417,7 @@ static int solve_impl(int method, int w, const mpk_csr* Ac, const mpk_ilu* Mc, c
     case MPK_GPBICG: m_gp.init(c); break;
     default: break;
   }
-  int hst[ST_COUNT];
+  int hflag = 0;
   int queued = 0;
   for (;;) {
     for (int k = 0; k < check_every; ++k) {
@@ -297,9 +431,9 @@ static int solve_impl(int method, int w, const mpk_csr* Ac, const mpk_ilu* Mc, c
     queued += check_every;
     if (c.err != MPK_OK) break;
     MPK_CUDA(cudaGetLastError());
-    MPK_CUDA(cudaMemcpyAsync(hst, c.st, sizeof(hst), cudaMemcpyDeviceToHost, s));
+    MPK_CUDA(cudaMemcpyAsync(&hflag, c.done, sizeof(int), cudaMemcpyDeviceToHost, s));
     MPK_CUDA(cudaStreamSynchronize(s));
-    if (hst[ST_DONE] || queued > maxit + check_every) break;
+    if (hflag || queued > maxit + check_every) break;
   }
   if (c.err != MPK_OK) {
     cudaFreeAsync(base, s);
@@ -309,21 +443,26 @@ static int solve_impl(int method, int w, const mpk_csr* Ac, const mpk_ilu* Mc, c
   int dev_err = MPK_OK;
   if (M != nullptr) dev_err = read_ctl_err(M, s);
 
-  // true residual b - A x with the final x (no done-gating)
-  o->spmv(c.A, x, V[16], b, nullptr, s);
+  // true residual b - A x with the final x (no done-gating: every system)
+  o->spmv(c.A, x, V[16], b, nullptr, nullptr, s);
   {
     const double* av[1] = {V[16]};
     const double* bv[1] = {V[16]};
-    double* ov[1] = {c.slot(S_D5)};
-    o->dots(n, 1, av, bv, ov, c.dws, nullptr, s);
-    o->scalar(method, PH_TRUE, c.S, c.st, nullptr, nullptr, s);
+    if (batched) {
+      Batch all = bt;
+      all.st = nullptr;
+      o->dots_seg(all, 1, av, bv, c.S, S_D5, partial, counters, nullptr, s);
+    } else {
+      double* ov[1] = {c.slot(S_D5)};
+      o->dots(n, 1, av, bv, ov, c.dws, nullptr, s);
+    }
+    o->scalar(method, PH_TRUE, c.S, c.st, nullptr, nullptr, nsys, 0, nullptr, nullptr, s);
   }
   MPK_CUDA(cudaEventRecord(e1, s));
-  double sl[3][kSlotDoubles];
-  MPK_CUDA(cudaMemcpyAsync(hst, c.st, sizeof(hst), cudaMemcpyDeviceToHost, s));
-  MPK_CUDA(cudaMemcpyAsync(sl[0], c.slot(S_R0N), sizeof(double) * kSlotDoubles, cudaMemcpyDeviceToHost, s));
-  MPK_CUDA(cudaMemcpyAsync(sl[1], c.slot(S_NORM), sizeof(double) * kSlotDoubles, cudaMemcpyDeviceToHost, s));
-  MPK_CUDA(cudaMemcpyAsync(sl[2], c.slot(S_D4), sizeof(double) * kSlotDoubles, cudaMemcpyDeviceToHost, s));
+  std::vector<int> hst((size_t)ST_COUNT * nsys);
+  std::vector<double> hS((size_t)kSysDoubles * nsys);
+  MPK_CUDA(cudaMemcpyAsync(hst.data(), c.st, sizeof(int) * hst.size(), cudaMemcpyDeviceToHost, s));
+  MPK_CUDA(cudaMemcpyAsync(hS.data(), c.S, sizeof(double) * hS.size(), cudaMemcpyDeviceToHost, s));
   MPK_CUDA(cudaStreamSynchronize(s));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
@@ -332,18 +471,30 @@ static int solve_impl(int method, int w, const mpk_csr* Ac, const mpk_ilu* Mc, c
   MPK_CUDA(cudaFreeAsync(base, s));
   if (ahbuf) MPK_CUDA(cudaFreeAsync(ahbuf, s));
 
-  const double r0n = sl[0][0];
-  info->status = hst[ST_DONE] ? hst[ST_STATUS] : MPK_MAXIT;
-  info->iters = hst[ST_DONE] ? hst[ST_ITERS] : maxit;
-  if (dev_err != MPK_OK) info->status = dev_err;
-  info->res0 = r0n;
-  info->relres_rec = r0n > 0 ? sl[1][0] / r0n : 0.0;
-  info->relres_true = r0n > 0 ? sl[2][0] / r0n : 0.0;
-  info->ms_solve = ms;
-  if (info->status != MPK_OK && info->status != MPK_MAXIT && info->status != MPK_BREAKDOWN &&
-      info->status != MPK_NAN)
-    return fail(info->status, "solve failed on the device");
-  return info->status;
+  int worst = MPK_OK;
+  for (int sy = 0; sy < nsys; ++sy) {
+    const int* q = hst.data() + (size_t)sy * ST_COUNT;
+    const double* Sy = hS.data() + (size_t)sy * kSysDoubles;
+    mpk_info& info = infos[sy];
+    const double r0n = Sy[S_R0N * kSlotDoubles];
+    info.status = q[ST_DONE] ? q[ST_STATUS] : MPK_MAXIT;
+    info.iters = q[ST_DONE] ? q[ST_ITERS] : maxit;
+    if (dev_err != MPK_OK) info.status = dev_err;
+    info.fail_row = -1;
+    info.res0 = r0n;
+    info.relres_rec = r0n > 0 ? Sy[S_NORM * kSlotDoubles] / r0n : 0.0;
+    info.relres_true = r0n > 0 ? Sy[S_D4 * kSlotDoubles] / r0n : 0.0;
+    info.ms_solve = ms;
+    if (info.status != MPK_OK && worst == MPK_OK) worst = info.status;
+  }
+  if (dev_err != MPK_OK) return fail(dev_err, "solve failed on the device");
+  if (!batched) {
+    const int st = infos[0].status;
+    if (st != MPK_OK && st != MPK_MAXIT && st != MPK_BREAKDOWN && st != MPK_NAN)
+      return fail(st, "solve failed on the device");
+    return st;
+  }
+  return worst;
 }
 
 extern "C" int mpk_krylov_solve(int method, int w, const mpk_csr* A, const mpk_ilu* M, const double* b_dev,
@@ -362,9 +513,36 @@ extern "C" int mpk_krylov_solve(int method, int w, const mpk_csr* A, const mpk_i
   if (opts->maxit < 0) return fail(MPK_INVALID_ARG, "maxit must be >= 0");
   if (M != nullptr && (M->n != A->n || M->cp != (A->is_complex ? 2 : 1)))
     return fail(MPK_INVALID_ARG, "preconditioner does not match the matrix");
-  int st = solve_impl(method, w, A, M, b_dev, x_dev, opts, info, (cudaStream_t)stream);
+  int st = solve_impl(method, w, A, M, b_dev, x_dev, opts, info, (cudaStream_t)stream, 1, nullptr, nullptr);
   info->status = st;
   return st;
+}
+
+extern "C" int mpk_krylov_solve_batched(int method, int w, const mpk_csr* A, int nsys, const int32_t* sys_rows_host,
+                                        const int32_t* sys_rows_dev, const mpk_ilu* M, const double* b_dev,
+                                        double* x_dev, const mpk_opts* opts, mpk_info* infos, void* stream) {
+  if (infos == nullptr || nsys < 1) return fail(MPK_INVALID_ARG, "null infos or nsys < 1");
+  for (int sy = 0; sy < nsys; ++sy) {
+    std::memset(infos + sy, 0, sizeof(mpk_info));
+    infos[sy].fail_row = -1;
+    infos[sy].status = MPK_INVALID_ARG;
+  }
+  int v = validate_csr(A);
+  if (v != MPK_OK) return v;
+  if (method < MPK_BICG || method > MPK_GPBICG) return fail(MPK_INVALID_ARG, "unknown method");
+  if (w < 1 || w > 4) return fail(MPK_INVALID_ARG, "w must be 1..4");
+  if (b_dev == nullptr || x_dev == nullptr || opts == nullptr || b_dev == x_dev)
+    return fail(MPK_INVALID_ARG, "null or aliased vector / options");
+  if (sys_rows_host == nullptr || sys_rows_dev == nullptr) return fail(MPK_INVALID_ARG, "null system row offsets");
+  if (sys_rows_host[0] != 0 || sys_rows_host[nsys] != A->n)
+    return fail(MPK_INVALID_ARG, "system row offsets must start at 0 and end at n");
+  for (int sy = 0; sy < nsys; ++sy)
+    if (sys_rows_host[sy + 1] <= sys_rows_host[sy]) return fail(MPK_INVALID_ARG, "empty or decreasing system");
+  if (opts->maxit < 0) return fail(MPK_INVALID_ARG, "maxit must be >= 0");
+  if (M != nullptr && (M->n != A->n || M->cp != (A->is_complex ? 2 : 1)))
+    return fail(MPK_INVALID_ARG, "preconditioner does not match the matrix");
+  return solve_impl(method, w, A, M, b_dev, x_dev, opts, infos, (cudaStream_t)stream, nsys, sys_rows_host,
+                    sys_rows_dev);
 }
 
 extern "C" int mpk_solve_host(int method, int w, int prec, int32_t n, int32_t is_complex, const int32_t* rp_h,

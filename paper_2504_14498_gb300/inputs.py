@@ -237,3 +237,81 @@ def normal_rhs(n, w, c=2, seed=SEED_BASE + 3):
     v = np.zeros((n, c, w))
     v[:, :, 0] = rng.standard_normal((n, c))
     return v.reshape(-1)
+
+
+def random_system(n, seed, kmin=5, kmax=40, weak_frac=0.05, weak_factor=0.6):
+    """One system of the batched workload (vectorised recipe of random_sparse): n x n, K ~
+    U{kmin..kmax} entries per row including the diagonal, off-diagonal columns distinct and
+    uniform among the other n-1, off-diagonals N(0,1), diagonal = (sum |off|)(1 + U(0, 0.2)),
+    weakened by weak_factor in a weak_frac share of the rows.  Returns (n, row_ptr, col, val)."""
+    rng = np.random.default_rng(seed)
+    kmax = min(kmax, n)
+    kmin = min(kmin, kmax)
+    k = rng.integers(kmin, kmax + 1, size=n)
+    rows = np.repeat(np.arange(n, dtype=np.int64), k - 1)
+    cols = rng.integers(0, n - 1, size=len(rows), dtype=np.int64)
+    cols += cols >= rows
+    for _ in range(64):  # redraw duplicated columns of a row until all are distinct
+        key = rows * n + cols
+        order = np.argsort(key, kind="stable")
+        rows, cols = rows[order], cols[order]
+        dup = np.zeros(len(rows), dtype=bool)
+        dup[1:] = (rows[1:] == rows[:-1]) & (cols[1:] == cols[:-1])
+        nd = int(dup.sum())
+        if nd == 0:
+            break
+        c = rng.integers(0, n - 1, size=nd, dtype=np.int64)
+        cols[dup] = c + (c >= rows[dup])
+    off = rng.standard_normal(len(rows))
+    weak = rng.random(n) < weak_frac
+    grow = rng.uniform(0.0, 0.2, size=n)
+    rsum = np.bincount(rows, weights=np.abs(off), minlength=n)
+    diag = rsum * (1.0 + grow) * np.where(weak, weak_factor, 1.0)
+    rows_all = np.concatenate([rows, np.arange(n, dtype=np.int64)])
+    cols_all = np.concatenate([cols, np.arange(n, dtype=np.int64)])
+    vals_all = np.concatenate([off, diag])
+    order = np.argsort(rows_all * n + cols_all, kind="stable")
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(k, out=rp[1:])
+    return (n, rp.astype(np.int32), cols_all[order].astype(np.int32), vals_all[order].astype(np.float64))
+
+
+def batch_sizes(nsys=512, nmin=1000, nmax=200000, seed=SEED_BASE + 4):
+    """System sizes of the batched workload: N log-uniform in [nmin, nmax]."""
+    rng = np.random.default_rng(seed)
+    return np.exp(rng.uniform(math.log(nmin), math.log(nmax), size=nsys)).astype(np.int64)
+
+
+def batch_system(s, sizes, seed=SEED_BASE + 4000):
+    """System s of the batch (its own seed, so any one system can be rebuilt alone)."""
+    return random_system(int(sizes[s]), seed + int(s))
+
+
+def batch_xstar(n, w, seed):
+    """Exact solution of one batch system: leading components U(-1, 1)."""
+    rng = np.random.default_rng(seed)
+    x = np.zeros((n, w))
+    x[:, 0] = rng.uniform(-1.0, 1.0, size=n)
+    return x.reshape(-1)
+
+
+def block_diagonal(systems):
+    """Concatenate CSR systems into one block-diagonal CSR (global column indices) and the row
+    offsets of the systems (int64 for the total entry count; the library takes int32)."""
+    ns = np.array([A[0] for A in systems], dtype=np.int64)
+    roff = np.zeros(len(systems) + 1, dtype=np.int64)
+    np.cumsum(ns, out=roff[1:])
+    nnzs = np.array([len(A[2]) for A in systems], dtype=np.int64)
+    eoff = np.zeros(len(systems) + 1, dtype=np.int64)
+    np.cumsum(nnzs, out=eoff[1:])
+    rp = np.empty(int(roff[-1]) + 1, dtype=np.int64)
+    ci = np.empty(int(eoff[-1]), dtype=np.int32)
+    val = np.empty(int(eoff[-1]) * (len(systems[0][3]) // max(1, len(systems[0][2]))), dtype=np.float64)
+    c = len(systems[0][3]) // max(1, len(systems[0][2]))
+    for s, A in enumerate(systems):
+        n, r, cc, v = A
+        rp[roff[s]:roff[s] + n] = r[:-1].astype(np.int64) + eoff[s]
+        ci[eoff[s]:eoff[s + 1]] = cc + roff[s]
+        val[eoff[s] * c:eoff[s + 1] * c] = v
+    rp[-1] = eoff[-1]
+    return (int(roff[-1]), rp, ci, val), roff
