@@ -96,7 +96,7 @@ typedef struct {
   int32_t status;          /* mpk_status of the solve                                           */
   int32_t iters;           /* iterations performed                                              */
   int32_t fail_row;        /* ILU failures: the row; otherwise -1                               */
-  int32_t reserved;
+  int32_t graph;           /* 1: the iterations ran as replays of one captured CUDA graph         */
   double res0;             /* ||b - A x0|| (leading component)                                  */
   double relres_rec;       /* ||r_k|| / ||r0|| of the recursively updated residual               */
   double relres_true;      /* ||b - A x_k|| / ||r0|| recomputed at the end in the vector format */

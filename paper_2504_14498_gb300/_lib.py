@@ -37,7 +37,7 @@ class Opts(ctypes.Structure):
 
 class Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("fail_row", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("res0", ctypes.c_double), ("relres_rec", ctypes.c_double),
+                ("graph", ctypes.c_int32), ("res0", ctypes.c_double), ("relres_rec", ctypes.c_double),
                 ("relres_true", ctypes.c_double), ("ms_solve", ctypes.c_float), ("reserved2", ctypes.c_float)]
 
 
@@ -197,7 +197,8 @@ def krylov_solve(method, w, A: Matrix, M: ILU0, b: torch.Tensor, x0: torch.Tenso
         raise MpkError(st, lib().mpk_last_error().decode())
     h = hist[: info.iters + 1].cpu().numpy() if history else None
     return {"status": STATUS[info.status], "iters": info.iters, "x": x, "hist": h, "res0": info.res0,
-            "relres_rec": info.relres_rec, "relres_true": info.relres_true, "ms": info.ms_solve}
+            "relres_rec": info.relres_rec, "relres_true": info.relres_true, "ms": info.ms_solve,
+            "graph": bool(info.graph)}
 
 
 def krylov_solve_batched(method, w, A: Matrix, sys_rows, M: ILU0, b: torch.Tensor, x0: torch.Tensor = None,
@@ -222,7 +223,8 @@ def krylov_solve_batched(method, w, A: Matrix, sys_rows, M: ILU0, b: torch.Tenso
            "statuses": [STATUS[i.status] for i in infos],
            "iters": np.array([i.iters for i in infos]), "res0": np.array([i.res0 for i in infos]),
            "relres_rec": np.array([i.relres_rec for i in infos]),
-           "relres_true": np.array([i.relres_true for i in infos]), "ms": infos[0].ms_solve}
+           "relres_true": np.array([i.relres_true for i in infos]), "ms": infos[0].ms_solve,
+           "graph": bool(infos[0].graph)}
     if history:
         h = hist.cpu().numpy()
         out["hist"] = [h[s_, : out["iters"][s_] + 1] for s_ in range(nsys)]

@@ -17,6 +17,8 @@ int fail(int status, const std::string& msg) {
 
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch(unsigned k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void uncount_launch(unsigned long long k) { g_launches.fetch_sub(k, std::memory_order_relaxed); }
 
 int resident_warps_per_sm() {
   static int w = [] {

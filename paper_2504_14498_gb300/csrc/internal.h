@@ -25,6 +25,7 @@ struct Csr {  // device CSR view
   const int* ci = nullptr;
   const double* val = nullptr;  // c doubles per entry
   int cplx = 0;
+  const int* order = nullptr;   // SpMV: thread t computes row order[t] (nullptr: row t)
 };
 
 // Scalar slots of a solve: each slot holds one number (up to 8 doubles).
@@ -180,6 +181,8 @@ enum CtlIdx : int { CTL_EPOCH = 0, CTL_TICKET_LO, CTL_TICKET_UP, CTL_ERR, CTL_FA
 int sm_count();
 int resident_warps_per_sm();        // MPK_RESIDENT_WARPS (default 32): dependency-driven kernels
 void count_launch(unsigned k = 1);  // every kernel launch of the library is counted
+unsigned long long launch_count();
+void uncount_launch(unsigned long long k);  // launches recorded into a graph run only when it is launched
 void launch_trsv_prep(const IluHandleView& M, const int* done, cudaStream_t s);
 // ints of the order buffer of one triangle with n rows and `nlevels` levels:
 // level perm (P = n + 32*nlevels) | level pos (n) | chunk flags (P/32 + 1) | nchunks (1) |

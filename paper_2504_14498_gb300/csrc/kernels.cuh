@@ -58,10 +58,13 @@ __global__ void __launch_bounds__(kBlock) k_spmv(int n, const int* __restrict__ 
                                                  const double* __restrict__ val, const double* __restrict__ x,
                                                  double* __restrict__ y, const double* __restrict__ b,
                                                  const int* __restrict__ done, const int* __restrict__ sysid,
-                                                 const int* __restrict__ sst) {
+                                                 const int* __restrict__ sst, const int* __restrict__ order) {
   if (is_done(done)) return;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  // order (nullable): rows grouped by length so that the lanes of a warp do equal work (every
+  // binary64 warp instruction costs its full pipe time however many lanes are active)
+  const int i = order != nullptr ? order[t] : t;
   if (sysid != nullptr && sst != nullptr && sst[sysid[i] * ST_COUNT + ST_DONE] != 0) return;
   N<W, CP> acc = n_zero<W, CP>();
   const int p1 = rp[i + 1];
@@ -1342,7 +1345,8 @@ struct Launch {
                    cudaStream_t s) {
     count_launch();
     k_spmv<W, CP><<<(A.n + kBlock - 1) / kBlock, kBlock, 0, s>>>(A.n, A.rp, A.ci, A.val, x, y, b, done,
-                                                                  bt ? bt->sysid : nullptr, bt ? bt->st : nullptr);
+                                                                  bt ? bt->sysid : nullptr, bt ? bt->st : nullptr,
+                                                                  A.order);
   }
   template <int K>
   static void dotsK(int n, const double* const* a, const double* const* b, double* const* out, const DotWs& ws,

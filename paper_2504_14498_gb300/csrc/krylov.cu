@@ -8,7 +8,9 @@
 // sequence of w-component operations as the CPU restatement of the method.
 #include <climits>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -223,6 +225,109 @@ static int validate_csr(const mpk_csr* A) {
   return MPK_OK;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Autotuner of the SpMV row order.  Candidates: natural order, and rows grouped by length
+// (longest first; counting sort on the row lengths).  Both compute every row in CSR order, so the
+// choice changes timing only.  The decision (and the order) is cached per matrix pattern
+// (row_ptr address, n, nnz, w, c) for the process; any permutation of the rows is a valid order,
+// so a stale entry can only cost speed.
+// ---------------------------------------------------------------------------------------------
+constexpr int kLenBuckets = 1024;
+__global__ void k_len_hist(int n, const int* __restrict__ rp, int* __restrict__ cnt) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int len = min(rp[i + 1] - rp[i], kLenBuckets - 1);
+    atomicAdd(cnt + (kLenBuckets - 1 - len), 1);
+  }
+}
+__global__ void k_len_scan(int* __restrict__ cnt) {  // one thread: exclusive scan in place
+  int run = 0;
+  for (int b = 0; b < kLenBuckets; ++b) {
+    const int v = cnt[b];
+    cnt[b] = run;
+    run += v;
+  }
+}
+__global__ void k_len_scatter(int n, const int* __restrict__ rp, int* __restrict__ off, int* __restrict__ order) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int len = min(rp[i + 1] - rp[i], kLenBuckets - 1);
+    order[atomicAdd(off + (kLenBuckets - 1 - len), 1)] = i;
+  }
+}
+struct SpmvTune {
+  const int* rp;
+  int n, nnz, w, cp;
+  int* order;  // nullptr: natural order wins
+};
+static std::mutex g_tune_mu;
+static std::vector<SpmvTune> g_tune;
+
+static const int* spmv_order(const Ops* o, const Csr& A, int w, int cp, double* x, double* y, cudaStream_t s) {
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const SpmvTune& t : g_tune)
+      if (t.rp == A.rp && t.n == A.n && t.nnz == A.nnz && t.w == w && t.cp == cp) return t.order;
+  }
+  int* order = nullptr;
+  int* cnt = nullptr;
+  if (cudaMalloc((void**)&order, sizeof(int) * (size_t)A.n) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (cudaMallocAsync((void**)&cnt, sizeof(int) * kLenBuckets, s) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(order);
+    return nullptr;
+  }
+  cudaMemsetAsync(cnt, 0, sizeof(int) * kLenBuckets, s);
+  const int g = (A.n + 255) / 256 < 4096 ? (A.n + 255) / 256 : 4096;
+  count_launch(3);
+  k_len_hist<<<g, 256, 0, s>>>(A.n, A.rp, cnt);
+  k_len_scan<<<1, 1, 0, s>>>(cnt);
+  k_len_scatter<<<g, 256, 0, s>>>(A.n, A.rp, cnt, order);
+  cudaFreeAsync(cnt, s);
+  // time both candidates (x, y: scratch vectors; the cost does not depend on the values)
+  cudaEvent_t ev[4];
+  for (auto& e : ev) cudaEventCreate(&e);
+  Csr nat = A, srt = A;
+  nat.order = nullptr;
+  srt.order = order;
+  float t[2] = {0.f, 0.f};
+  for (int rep = 0; rep < 2; ++rep) {
+    for (int v = 0; v < 2; ++v) {
+      const Csr& M = v == 0 ? nat : srt;
+      o->spmv(M, x, y, nullptr, nullptr, nullptr, s);  // warm
+      cudaEventRecord(ev[2 * v], s);
+      o->spmv(M, x, y, nullptr, nullptr, nullptr, s);
+      o->spmv(M, x, y, nullptr, nullptr, nullptr, s);
+      cudaEventRecord(ev[2 * v + 1], s);
+    }
+    cudaEventSynchronize(ev[3]);
+    for (int v = 0; v < 2; ++v) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[2 * v], ev[2 * v + 1]);
+      t[v] += ms;
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (cudaGetLastError() != cudaSuccess) {
+    cudaFree(order);
+    return nullptr;
+  }
+  const bool use = t[1] < 0.97f * t[0];
+  if (!use) {
+    cudaFree(order);
+    order = nullptr;
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (g_tune.size() < 64) g_tune.push_back(SpmvTune{A.rp, A.n, A.nnz, w, cp, order});
+  else if (order != nullptr) {
+    // cache full: keep this solve untuned rather than grow without bound
+    cudaFree(order);
+    order = nullptr;
+  }
+  return order;
+}
+
 // Rows -> system, and the segmented inner products' block layout, of a batch with row offsets roff.
 __global__ void k_batch_sysid(int n, int nsys, const int* __restrict__ roff, int* __restrict__ sysid,
                               int* __restrict__ bad) {
@@ -254,9 +359,39 @@ __global__ void k_batch_bsys(int nsys, const int* __restrict__ boff, int* __rest
 // nsys == 1 and roff_host == nullptr: one system.  Otherwise A is block-diagonal with the systems'
 // rows at roff_host[s] .. roff_host[s+1]-1 (host copy) / roff_dev (device copy); infos has nsys
 // entries; hist_dev (nullable) nsys * (maxit + 1) doubles.
+// The solve runs on a private stream joined to the caller's stream at both ends (stream capture
+// into a CUDA graph is not possible on the legacy default stream).
+struct StreamJoin {
+  cudaStream_t caller = nullptr, own = nullptr;
+  cudaEvent_t ev = nullptr;
+  bool ok = false;
+  explicit StreamJoin(cudaStream_t c) : caller(c) {
+    ok = cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventRecord(ev, caller) == cudaSuccess && cudaStreamWaitEvent(own, ev, 0) == cudaSuccess;
+  }
+  ~StreamJoin() {
+    if (own != nullptr) {
+      if (ev != nullptr && cudaEventRecord(ev, own) == cudaSuccess) cudaStreamWaitEvent(caller, ev, 0);
+      cudaStreamDestroy(own);
+    }
+    if (ev != nullptr) cudaEventDestroy(ev);
+  }
+};
+static bool graphs_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("MPK_NO_GRAPH");
+    return !(e != nullptr && e[0] == '1');
+  }();
+  return on;
+}
+
 static int solve_impl(int method, int w, const mpk_csr* Ac, const mpk_ilu* Mc, const double* b, double* x,
-                      const mpk_opts* opts, mpk_info* infos, cudaStream_t s, int nsys, const int* roff_host,
+                      const mpk_opts* opts, mpk_info* infos, cudaStream_t caller, int nsys, const int* roff_host,
                       const int* roff_dev) {
+  StreamJoin join(caller);
+  if (!join.ok) return fail(MPK_CUDA_ERROR, "could not create the solve's stream");
+  cudaStream_t s = join.own;
   const int n = Ac->n, cp = Ac->is_complex ? 2 : 1;
   const int64_t vlen = (int64_t)n * cp * w;
   mpk_ilu* M = const_cast<mpk_ilu*>(Mc);
@@ -400,6 +535,9 @@ static int solve_impl(int method, int w, const mpk_csr* Ac, const mpk_ilu* Mc, c
     MPK_CUDA(cudaStreamSynchronize(s));  // the host buffers above go out of scope
   }
 
+  // SpMV row order of this matrix (autotuned once per pattern; V[15], V[16] serve as scratch)
+  c.A.order = spmv_order(o, c.A, w, cp, V[15], V[16], s);
+
   double* r = V[0];
   double* rt = V[1];
   // r = b - A x0, r~ = r, ||r0||
@@ -417,15 +555,48 @@ static int solve_impl(int method, int w, const mpk_csr* Ac, const mpk_ilu* Mc, c
     case MPK_GPBICG: m_gp.init(c); break;
     default: break;
   }
+  auto one_iter = [&]() {
+    switch (method) {
+      case MPK_BICG: m_bicg.iter(c); break;
+      case MPK_CGS: m_cgs.iter(c); break;
+      case MPK_BICGSTAB: m_stab.iter(c); break;
+      default: m_gp.iter(c); break;
+    }
+  };
+  // One iteration captured into a CUDA graph and replayed; every kernel reads its state from device
+  // memory, so the replays are the iterations.  If capture is not possible the launches go direct.
+  cudaGraphExec_t gexec = nullptr;
+  unsigned long long per_iter = 0;
+  if (graphs_enabled() && c.err == MPK_OK) {
+    const unsigned long long l0 = launch_count();
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      one_iter();
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamEndCapture(s, &g);
+      if (e == cudaSuccess && c.err == MPK_OK) e = cudaGraphInstantiate(&gexec, g, 0);
+      if (g != nullptr) cudaGraphDestroy(g);
+      if (e != cudaSuccess || c.err != MPK_OK) {
+        if (gexec != nullptr) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+        c.err = MPK_OK;
+      }
+    }
+    cudaGetLastError();  // a failed capture leaves no error behind: the launches then go direct
+    per_iter = launch_count() - l0;
+    uncount_launch(per_iter);
+  }
   int hflag = 0;
   int queued = 0;
   for (;;) {
     for (int k = 0; k < check_every; ++k) {
-      switch (method) {
-        case MPK_BICG: m_bicg.iter(c); break;
-        case MPK_CGS: m_cgs.iter(c); break;
-        case MPK_BICGSTAB: m_stab.iter(c); break;
-        default: m_gp.iter(c); break;
+      if (gexec != nullptr) {
+        if (cudaGraphLaunch(gexec, s) != cudaSuccess) {
+          c.err = fail(MPK_CUDA_ERROR, "graph launch failed");
+          break;
+        }
+        count_launch((unsigned)per_iter);
+      } else {
+        one_iter();
       }
     }
     queued += check_every;
@@ -435,6 +606,8 @@ static int solve_impl(int method, int w, const mpk_csr* Ac, const mpk_ilu* Mc, c
     MPK_CUDA(cudaStreamSynchronize(s));
     if (hflag || queued > maxit + check_every) break;
   }
+  const bool gexec_used = gexec != nullptr;
+  if (gexec != nullptr) cudaGraphExecDestroy(gexec);
   if (c.err != MPK_OK) {
     cudaFreeAsync(base, s);
     if (ahbuf) cudaFreeAsync(ahbuf, s);
@@ -481,6 +654,7 @@ static int solve_impl(int method, int w, const mpk_csr* Ac, const mpk_ilu* Mc, c
     info.iters = q[ST_DONE] ? q[ST_ITERS] : maxit;
     if (dev_err != MPK_OK) info.status = dev_err;
     info.fail_row = -1;
+    info.graph = gexec_used ? 1 : 0;
     info.res0 = r0n;
     info.relres_rec = r0n > 0 ? Sy[S_NORM * kSlotDoubles] / r0n : 0.0;
     info.relres_true = r0n > 0 ? Sy[S_D4 * kSlotDoubles] / r0n : 0.0;

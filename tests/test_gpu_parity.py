@@ -160,6 +160,7 @@ def _compare_solve(method, A_t, c, w, ilu, tol, maxit=600, x_star=None):
     assert np.array_equal(out["hist"], ref["hist"])
     assert out["relres_true"] == ref["relres_true"]
     assert np.array_equal(host(out["x"]), ref["x"])
+    assert out["graph"]  # the iterations ran as replays of one captured CUDA graph
     return out, ref
 
 
