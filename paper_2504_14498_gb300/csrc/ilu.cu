@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
+#include <vector>
 
 #include "kernels.cuh"
 
@@ -148,60 +150,8 @@ __global__ void k_trsv_prep(int* ctl, unsigned long long* absmax, const int* don
   *absmax = 0ull;
 }
 
-// ---------------------------------------------------------------------------------------------
-// Chunk order of one triangle.  Order position k is row k (lower) or row n-1-k (upper); chunk c
-// holds positions [32c, 32c+32).  depth(c) = 0 if no row of c depends on a row of another chunk,
-// else 1 + the largest depth among those chunks.  Chunks depend only on earlier chunks, so the
-// depths are computed in chunk order with (epoch << 32 | depth) words and bounded waits; a
-// counting sort by depth then gives the order in which the substitution kernels take chunks.
-// ---------------------------------------------------------------------------------------------
-constexpr unsigned kDepthEpoch0 = 0x40000000u;  // distinct from the substitution epochs
+constexpr unsigned kDepthEpoch0 = 0x40000000u;  // epochs of the ordering passes, distinct from others
 
-__global__ void __launch_bounds__(kBlock) k_chunk_depth(int n, bool lower, const int* __restrict__ rp,
-                                                        const int* __restrict__ diag, const int* __restrict__ ci,
-                                                        unsigned long long* pk, unsigned epoch, int* __restrict__ depth,
-                                                        int* ticket, int* ctl) {
-  const unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  const int nchunks = (n + 31) >> 5;
-  for (;;) {
-    int chunk = 0;
-    if (lane == 0) chunk = atomicAdd(ticket, 1);
-    chunk = __shfl_sync(FULL, chunk, 0);
-    if (chunk >= nchunks) return;
-    const int k = (chunk << 5) + lane;
-    int d = -1;
-    bool timeout = false;
-    if (k < n) {
-      const int i = lower ? k : n - 1 - k;
-      const int p0 = lower ? rp[i] : diag[i] + 1, p1 = lower ? diag[i] : rp[i + 1];
-      for (int p = p0; p < p1 && !timeout; ++p) {
-        const int j = ci[p];
-        const int cj = (lower ? j : n - 1 - j) >> 5;
-        if (cj == chunk) continue;
-        const long long t0 = clock64();
-        unsigned long long wv;
-        for (;;) {
-          wv = ld_relaxed_u64(pk + cj);
-          if ((unsigned)(wv >> 32) == epoch) break;
-          if (clock64() - t0 > kWaitCycles || ld_relaxed(ctl + CTL_ERR) != 0) { timeout = true; break; }
-          __nanosleep(64);
-        }
-        if (!timeout) d = max(d, (int)(unsigned)wv);
-      }
-    }
-    if (__any_sync(FULL, timeout)) {
-      if (lane == 0) atomicCAS(ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
-      return;
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) d = max(d, __shfl_xor_sync(FULL, d, off));
-    if (lane == 0) {
-      depth[chunk] = d + 1;
-      st_relaxed_u64(pk + chunk, ((unsigned long long)epoch << 32) | (unsigned)(d + 1));
-    }
-  }
-}
 // counts per depth; cnt[L] (L = array length - 1, passed as maxslot) collects the largest depth
 __global__ void k_depth_count(int m, const int* __restrict__ depth, int* __restrict__ cnt, int* __restrict__ maxd) {
   int mx = 0;
@@ -212,32 +162,6 @@ __global__ void k_depth_count(int m, const int* __restrict__ depth, int* __restr
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
   if ((threadIdx.x & 31) == 0) atomicMax(maxd, mx);
-}
-// exclusive scan of cnt[0 .. *maxd] into off (one block of 1024 threads)
-__global__ void k_scan_depths(const int* __restrict__ maxd, const int* __restrict__ cnt, int* __restrict__ out) {
-  __shared__ int part[1024];
-  const int n = *maxd + 1;
-  const int t = threadIdx.x, T_ = blockDim.x;
-  const int per = (n + T_ - 1) / T_;
-  const int lo = min(n, t * per), hi = min(n, lo + per);
-  int s = 0;
-  for (int k = lo; k < hi; ++k) s += cnt[k];
-  part[t] = s;
-  __syncthreads();
-  if (t == 0) {
-    int run = 0;
-    for (int k = 0; k < T_; ++k) { int v = part[k]; part[k] = run; run += v; }
-  }
-  __syncthreads();
-  int run = part[t];
-  for (int k = lo; k < hi; ++k) { out[k] = run; run += cnt[k]; }
-}
-__global__ void k_depth_scatter(int m, const int* __restrict__ depth, const int* __restrict__ off,
-                                int* __restrict__ fill, int* __restrict__ order) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
-    const int d = depth[c];
-    order[off[d] + atomicAdd(fill + d, 1)] = c;
-  }
 }
 __global__ void k_scan_single(int n, const int* __restrict__ cnt, int* __restrict__ out);
 
@@ -378,14 +302,11 @@ __global__ void __launch_bounds__(kBlock) k_row_depth(Order ord, const int* __re
   row.depth = depth;
   syncfree_rows(ord, ci, ticket, ctl, row);
 }
-// positions of the chunk order: chunk_order[q / 32] * 32 + q % 32 (order index -> row)
-__global__ void k_perm_from_chunks(int n, bool lower, int nchunks, const int* __restrict__ chunk_order,
-                                   int* __restrict__ perm, int* __restrict__ pos) {
-  const int P = nchunks * 32;
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < P; q += gridDim.x * blockDim.x) {
-    const int idx = chunk_order[q >> 5] * 32 + (q & 31);
-    if (idx < n) {
-      const int row = lower ? idx : n - 1 - idx;
+// Natural row order of a triangle as an Order: position q holds row q (lower) or n-1-q (upper).
+__global__ void k_natural_order(int n, bool lower, int npos, int* __restrict__ perm, int* __restrict__ pos) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < npos; q += gridDim.x * blockDim.x) {
+    if (q < n) {
+      const int row = lower ? q : n - 1 - q;
       perm[q] = row;
       pos[row] = q;
     } else {
@@ -399,15 +320,7 @@ __global__ void k_inverse(int n, const int* __restrict__ perm, int* __restrict__
 
 size_t level_buf_ints(int n, int nlevels) {
   const size_t P = (size_t)n + 32 * (size_t)nlevels;
-  return P + (size_t)n + (P / 32 + 1) + 1 + (size_t)((n + 31) >> 5) * 32 + (size_t)n;
-}
-Order chunk_view(int* buf, int n, int nlevels) {
-  const size_t P = (size_t)n + 32 * (size_t)nlevels;
-  Order o;
-  o.perm = buf + P + (size_t)n + (P / 32 + 1) + 1;
-  o.pos = o.perm + (size_t)((n + 31) >> 5) * 32;
-  o.npos = ((n + 31) >> 5) * 32;
-  return o;
+  return P + (size_t)n + (P / 32 + 1) + 1;
 }
 LevelOrder level_view(int* buf, int n, int nlevels) {
   const size_t P = (size_t)n + 32 * (size_t)nlevels;
@@ -442,62 +355,66 @@ __global__ void k_level_layout(int nlevels, const int* __restrict__ cnt, int* __
     run += (cnt[k] + 31) & ~31;
   }
 }
-__global__ void k_level_scatter(int n, const int* __restrict__ depth, const int* __restrict__ off,
-                                int* __restrict__ fill, int* __restrict__ perm, int* __restrict__ pos) {
+// Within a level the rows are sorted by their length in the triangle (longest first, lengths
+// bucketed by kLenB): the 32 rows of a chunk then have similar lengths and the repacked chunk few
+// padding slots.  key = level * kLenB + (kLenB - 1 - min(len, kLenB - 1)).
+constexpr int kLenB = 32;
+__device__ __forceinline__ int tri_len(const int* rp, const int* diag, bool lower, int i) {
+  return lower ? diag[i] - rp[i] : rp[i + 1] - diag[i] - 1;
+}
+__global__ void k_key_count(int n, const int* __restrict__ depth, const int* __restrict__ rp,
+                            const int* __restrict__ diag, bool lower, int* __restrict__ cnt2) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    atomicAdd(cnt2 + depth[i] * kLenB + (kLenB - 1 - min(tri_len(rp, diag, lower, i), kLenB - 1)), 1);
+}
+__global__ void k_key_offsets(int nlevels, const int* __restrict__ off, const int* __restrict__ cnt2,
+                              int* __restrict__ sub) {
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < nlevels; d += gridDim.x * blockDim.x) {
+    int run = off[d];
+    for (int b = 0; b < kLenB; ++b) {
+      sub[d * kLenB + b] = run;
+      run += cnt2[d * kLenB + b];
+    }
+  }
+}
+__global__ void k_level_scatter(int n, const int* __restrict__ depth, const int* __restrict__ rp,
+                                const int* __restrict__ diag, bool lower, int* __restrict__ sub,
+                                int* __restrict__ perm, int* __restrict__ pos) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int d = depth[i];
-    const int q = off[d] + atomicAdd(fill + d, 1);
+    const int key = depth[i] * kLenB + (kLenB - 1 - min(tri_len(rp, diag, lower, i), kLenB - 1));
+    const int q = atomicAdd(sub + key, 1);
     perm[q] = i;
     pos[i] = q;
   }
 }
 
 // Level orders of the two triangles of (rp, ci, diag) into bufs[0] (lower) and bufs[1] (upper),
-// allocated here.  Row levels come from the dependency-driven pass over the chunk order
-// (chunks of 32 consecutive rows sorted by chunk depth).
+// allocated here.  Row levels come from the dependency-driven pass over the natural row order
+// (every row depends on earlier rows only: a valid order for it), then a counting sort by
+// (level, length) places them, every level padded to whole 32-row chunks.
 static int build_levels(int n, const int* rp, const int* ci, const int* diag, unsigned long long* pk, int* ctl,
                         int which, int** bufs, int* nlev, cudaStream_t s) {
   const int m = (n + 31) >> 5;
-  const size_t L = (size_t)(n > m ? n : m) + 1;
+  const size_t L = (size_t)n + 1;
   int* tmp = nullptr;
-  MPK_CUDA(cudaMallocAsync((void**)&tmp, sizeof(int) * (4 * L + (size_t)m * 33 + (size_t)n + 16), s));
+  MPK_CUDA(cudaMallocAsync((void**)&tmp, sizeof(int) * (2 * L + (size_t)m * 32 + (size_t)n + 16), s));
   int* depth = tmp;                      // L
   int* cnt = depth + L;                  // L
-  int* off = cnt + L;                    // L
-  int* fill = off + L;                   // L
-  int* corder = fill + L;                // m
-  int* perm_c = corder + m;              // 32 m
+  int* perm_c = cnt + L;                 // 32 m
   int* pos_c = perm_c + (size_t)m * 32;  // n
   int* maxd = pos_c + n;                 // 1
-  static int blocks_cd = [] {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chunk_depth, kBlock, 0) != cudaSuccess || per_sm < 1)
-      per_sm = 1;
-    return per_sm * sm_count();
-  }();
   static int blocks_rd = persistent_blocks(k_row_depth);
   for (int tri = 0; tri < 2; ++tri) {
     const bool lower = tri == 0;
-    // chunk depths -> chunk order -> permutation of chunk positions
     MPK_CUDA(cudaMemsetAsync(ctl + CTL_TICKET_LO, 0, sizeof(int), s));
-    MPK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * 3 * L, s));
-    MPK_CUDA(cudaMemsetAsync(maxd, 0, sizeof(int), s));
-    count_launch(5);
-    k_chunk_depth<<<blocks_cd, kBlock, 0, s>>>(n, lower, rp, diag, ci, pk, kDepthEpoch0 + 4u * which + tri, depth,
-                                               ctl + CTL_TICKET_LO, ctl);
-    k_depth_count<<<grid_for(m), kBlock, 0, s>>>(m, depth, cnt, maxd);
-    k_scan_depths<<<1, 1024, 0, s>>>(maxd, cnt, off);
-    k_depth_scatter<<<grid_for(m), kBlock, 0, s>>>(m, depth, off, fill, corder);
-    k_perm_from_chunks<<<grid_for(m * 32), kBlock, 0, s>>>(n, lower, m, corder, perm_c, pos_c);
-    // row levels
-    MPK_CUDA(cudaMemsetAsync(ctl + CTL_TICKET_LO, 0, sizeof(int), s));
-    MPK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * 3 * L, s));
+    MPK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * L, s));
     MPK_CUDA(cudaMemsetAsync(maxd, 0, sizeof(int), s));
     Order oc;
     oc.perm = perm_c;
     oc.pos = pos_c;
     oc.npos = m * 32;
-    count_launch(2);
+    count_launch(3);
+    k_natural_order<<<grid_for(m * 32), kBlock, 0, s>>>(n, lower, m * 32, perm_c, pos_c);
     k_row_depth<<<blocks_rd, kBlock, 0, s>>>(oc, ci, rp, diag, lower, pk, kDepthEpoch0 + 4u * which + 2u + tri, depth,
                                              ctl + CTL_TICKET_LO, ctl);
     k_depth_count<<<grid_for(n), kBlock, 0, s>>>(n, depth, cnt, maxd);
@@ -516,12 +433,18 @@ static int build_levels(int n, const int* rp, const int* ci, const int* diag, un
     const size_t P = (size_t)n + 32 * (size_t)nl;
     MPK_CUDA(cudaMemsetAsync(buf, 0xff, sizeof(int) * P, s));  // padding positions: -1
     MPK_CUDA(cudaMemsetAsync(lo.flags, 0, sizeof(int) * (P / 32 + 1), s));
-    count_launch(2);
+    int* keys = nullptr;  // off[nl] | cnt2[nl*kLenB] | sub[nl*kLenB]
+    MPK_CUDA(cudaMallocAsync((void**)&keys, sizeof(int) * ((size_t)nl * (2 * kLenB + 1)), s));
+    int* off = keys;
+    int* cnt2 = off + nl;
+    int* sub = cnt2 + (size_t)nl * kLenB;
+    MPK_CUDA(cudaMemsetAsync(cnt2, 0, sizeof(int) * (size_t)nl * kLenB, s));
+    count_launch(4);
     k_level_layout<<<1, 1024, 0, s>>>(nl, cnt, off, lo);
-    k_level_scatter<<<grid_for(n), kBlock, 0, s>>>(n, depth, off, fill, buf, const_cast<int*>(lo.pos));
-    const Order co = chunk_view(buf, n, nl);
-    MPK_CUDA(cudaMemcpyAsync(const_cast<int*>(co.perm), perm_c, sizeof(int) * (size_t)m * 32, cudaMemcpyDeviceToDevice, s));
-    MPK_CUDA(cudaMemcpyAsync(const_cast<int*>(co.pos), pos_c, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    k_key_count<<<grid_for(n), kBlock, 0, s>>>(n, depth, rp, diag, lower, cnt2);
+    k_key_offsets<<<(nl + 255) / 256, 256, 0, s>>>(nl, off, cnt2, sub);
+    k_level_scatter<<<grid_for(n), kBlock, 0, s>>>(n, depth, rp, diag, lower, sub, buf, const_cast<int*>(lo.pos));
+    MPK_CUDA(cudaFreeAsync(keys, s));
     bufs[tri] = buf;
     nlev[tri] = nl;
   }
@@ -726,6 +649,59 @@ int precond_apply(const mpk_ilu* M, const Ops* o, bool trans, const double* r, d
   return MPK_OK;
 }
 
+// ---- substitution autotuner ---------------------------------------------------------------------
+int read_ctl_err(const mpk_ilu* M, cudaStream_t s);
+struct TrsvTune {
+  const void* rp;
+  int n, nnz, prec, w, cp, wpb;
+};
+static std::mutex g_trsv_mu;
+static std::vector<TrsvTune> g_trsv;
+static int cached_wpb(const mpk_ilu* M, int w) {
+  std::lock_guard<std::mutex> lk(g_trsv_mu);
+  for (const TrsvTune& t : g_trsv)
+    if (t.rp == M->src_rp && t.n == M->n && t.nnz == M->nnz && t.prec == M->prec && t.w == w && t.cp == M->cp)
+      return t.wpb;
+  return 0;
+}
+int tune_substitution(mpk_ilu* M, const Ops* o, int w, double* r, double* z, cudaStream_t s) {
+  const int known = cached_wpb(M, w);
+  if (known > 0) {
+    M->wpb = known;
+    return MPK_OK;
+  }
+  static const int cands[4] = {4, 8, 16, 32};
+  cudaEvent_t e0, e1;
+  MPK_CUDA(cudaEventCreate(&e0));
+  MPK_CUDA(cudaEventCreate(&e1));
+  float best = 0.f;
+  int best_wpb = 4;
+  for (int wpb : cands) {
+    if (!o->trsv_fits(M->prec, wpb)) continue;
+    M->wpb = wpb;
+    int st = precond_apply(M, o, false, r, z, nullptr, nullptr, s);  // warm
+    if (st != MPK_OK) continue;
+    cudaEventRecord(e0, s);
+    for (int k = 0; k < 2; ++k) precond_apply(M, o, false, r, z, nullptr, nullptr, s);
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (best == 0.f || ms < best) {
+      best = ms;
+      best_wpb = wpb;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  M->wpb = best_wpb;
+  const int err = read_ctl_err(M, s);
+  if (err != MPK_OK) return err;
+  std::lock_guard<std::mutex> lk(g_trsv_mu);
+  if (g_trsv.size() < 256) g_trsv.push_back(TrsvTune{M->src_rp, M->n, M->nnz, M->prec, w, M->cp, best_wpb});
+  return MPK_OK;
+}
+
 int read_ctl_err(const mpk_ilu* M, cudaStream_t s) {
   int err = 0;
   MPK_CUDA(cudaMemcpyAsync(&err, M->ctl + CTL_ERR, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -767,10 +743,9 @@ IluHandleView mpk_ilu::view(bool trans) const {
   const int t = trans ? 2 : 0;
   v.lv_lo = level_view(lvbuf[t], n, nlevels[t]);
   v.lv_up = level_view(lvbuf[t + 1], n, nlevels[t + 1]);
-  v.ch_lo = chunk_view(lvbuf[t], n, nlevels[t]);
-  v.ch_up = chunk_view(lvbuf[t + 1], n, nlevels[t + 1]);
   v.sl_lo = sell[t];
   v.sl_up = sell[t + 1];
+  v.wpb = wpb;
   return v;
 }
 
@@ -783,6 +758,7 @@ static int factor_impl(const mpk_csr* A, int prec, mpk_ilu** out, int* fail_row,
   if (head[0] != 0 || head[1] != nnz) return fail(MPK_INVALID_ARG, "row_ptr[0] must be 0 and row_ptr[n] == nnz");
 
   mpk_ilu* M = new mpk_ilu();
+  M->src_rp = A->row_ptr;
   M->n = n;
   M->nnz = nnz;
   M->cp = cp;
@@ -928,6 +904,10 @@ extern "C" int mpk_precond_apply(const mpk_ilu* M, int w, int trans, const doubl
     if (st != MPK_OK) return st;
   }
   const Ops* o = get_ops(w, M->cp);
+  {
+    const int known = cached_wpb(M, w);
+    if (known > 0) const_cast<mpk_ilu*>(M)->wpb = known;
+  }
   int st = precond_apply(M, o, trans != 0, r_dev, z_dev, nullptr, nullptr, s);
   if (st != MPK_OK) return st;
   MPK_CUDA(cudaGetLastError());

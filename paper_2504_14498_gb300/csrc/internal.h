@@ -72,6 +72,9 @@ inline int dot_blocks(int n) {
 inline size_t dot_partial_doubles(int n) { return ((size_t)(n > 0 ? n : 1) + 4095) / 4096 * kMaxDots * 8; }
 
 struct IluHandleView;  // forward
+}  // namespace mpk
+struct mpk_ilu;
+namespace mpk {
 
 // nsys independent systems stored as consecutive row blocks of one block-diagonal matrix.  Each
 // system has its own scalar slots (S + s * kSysDoubles) and integer state (st + s * ST_COUNT); a
@@ -138,6 +141,8 @@ struct Ops {
                 cudaStream_t s);
   // bt (nullable): one accumulator per system (out + s)
   void (*absmax)(int n, const double* v, unsigned long long* out, const int* done, const Batch* bt, cudaStream_t s);
+  // 1 if the substitution kernel for factor precision prec fits one block of wpb warps per SM
+  int (*trsv_fits)(int prec, int wpb);
 };
 const Ops* get_ops(int w, int cp);
 
@@ -170,10 +175,10 @@ struct IluHandleView {
   double* vmp = nullptr;       // n*cp*w multi-component intermediate (capacity for w = 4)
   unsigned long long* absmax = nullptr;
   unsigned long long* pk = nullptr;  // packed (epoch << 32 | 32 payload bits) words, 8*cp per row
-  LevelOrder lv_lo, lv_up;           // level orders (chunk dataflow) of the two triangles
-  Order ch_lo, ch_up;                // chunk orders (dependency-driven, row chains in warps)
+  LevelOrder lv_lo, lv_up;           // level orders of the two triangles
   SellTri sl_lo, sl_up;              // repacked triangles of the substitutions
   const int* sysid = nullptr;        // batch: row -> system (absmax holds one scale per system)
+  int wpb = 4;                       // warps per block (per SM) of the substitution kernels
 };
 enum CtlIdx : int { CTL_EPOCH = 0, CTL_TICKET_LO, CTL_TICKET_UP, CTL_ERR, CTL_FAIL_ROW, CTL_COUNT };
 
@@ -184,12 +189,13 @@ void count_launch(unsigned k = 1);  // every kernel launch of the library is cou
 unsigned long long launch_count();
 void uncount_launch(unsigned long long k);  // launches recorded into a graph run only when it is launched
 void launch_trsv_prep(const IluHandleView& M, const int* done, cudaStream_t s);
+// Pick the substitution kernels' warps per SM for this handle and w by timing the candidates
+// (r, z: scratch vectors of n*c*w doubles); cached per (matrix pattern, factor precision, w, c).
+int tune_substitution(mpk_ilu* M, const Ops* o, int w, double* r, double* z, cudaStream_t s);
 // ints of the order buffer of one triangle with n rows and `nlevels` levels:
-// level perm (P = n + 32*nlevels) | level pos (n) | chunk flags (P/32 + 1) | nchunks (1) |
-// chunk-order perm (32*ceil(n/32)) | chunk-order pos (n)
+// level perm (P = n + 32*nlevels) | level pos (n) | chunk flags (P/32 + 1) | nchunks (1)
 size_t level_buf_ints(int n, int nlevels);
 LevelOrder level_view(int* buf, int n, int nlevels);
-Order chunk_view(int* buf, int n, int nlevels);
 
 }  // namespace mpk
 
@@ -215,5 +221,7 @@ struct mpk_ilu {
   int nlevels[4] = {0, 0, 0, 0};
   void* sellbuf[4] = {nullptr, nullptr, nullptr, nullptr};  // repacked triangles (same order)
   mpk::SellTri sell[4];
+  int wpb = 4;                   // warps per SM of the substitution kernels (autotuned per pattern)
+  const void* src_rp = nullptr;  // the factored matrix's row_ptr address: the tuning cache's key
   mpk::IluHandleView view(bool trans) const;
 };

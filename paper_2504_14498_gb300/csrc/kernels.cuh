@@ -329,15 +329,33 @@ __global__ void __launch_bounds__(kBlock) k_absmax(int n, const double* __restri
                                                    unsigned long long* __restrict__ out,
                                                    const int* __restrict__ done, const int* __restrict__ sysid) {
   if (is_done(done)) return;
-  if (sysid != nullptr) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-      const double* p = v + (int64_t)i * CP * W;
-      unsigned long long a = (unsigned long long)__double_as_longlong(fabs(p[0]));
-      if constexpr (CP == 2) {
-        unsigned long long b = (unsigned long long)__double_as_longlong(fabs(p[W]));
-        a = b > a ? b : a;
+  if (sysid != nullptr) {  // warp-uniform loop: a warp whose rows share one system reduces first
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += gridDim.x * blockDim.x) {
+      const int i = base + lane;
+      unsigned long long a = 0ull;
+      int sy = -1;
+      if (i < n) {
+        const double* p = v + (int64_t)i * CP * W;
+        a = (unsigned long long)__double_as_longlong(fabs(p[0]));
+        if constexpr (CP == 2) {
+          unsigned long long b = (unsigned long long)__double_as_longlong(fabs(p[W]));
+          a = b > a ? b : a;
+        }
+        sy = sysid[i];
       }
-      if (a != 0ull) atomicMax(out + sysid[i], a);
+      const int sy0 = __shfl_sync(FULL, sy, 0);
+      if (__all_sync(FULL, sy < 0 || sy == sy0)) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          const unsigned long long o = __shfl_down_sync(FULL, a, off);
+          a = o > a ? o : a;
+        }
+        if (lane == 0 && a != 0ull) atomicMax(out + sy0, a);
+      } else if (sy >= 0 && a != 0ull) {
+        atomicMax(out + sy, a);
+      }
     }
     return;
   }
@@ -786,150 +804,37 @@ __device__ __forceinline__ void chunk_rows(const LevelOrder lo, const int* __res
   }
 }
 
-// Triangles with a binary32 / bfloat16 factor, dependency-driven over the chunk order (chunks of
-// 32 consecutive rows sorted by chunk depth, so a warp holds a run of a row chain and passes it
-// along by shuffle).  Rows are published to other warps as (epoch << 32 | value bits) 64-bit
-// words: one single-copy-atomic store, read back with relaxed loads and no fence.
-template <int W, int CP, typename TS>
-struct RowPk32 {
-  using Val = typename std::conditional<CP == 1, float, float2>::type;
-  static constexpr int kLook = 4;
-  static constexpr int kBatch = 0;
-  struct Raw { unsigned long long w[CP]; };
-  const int* rp;
-  const int* diag;
-  const TS* f;
-  float* v32;
-  unsigned long long* pk;
-  const double* in;  // lower: multi-component right-hand side
-  double* out;       // upper: multi-component result
-  unsigned epoch;
-  bool lower, unit;
-  int e;
-  int i;
-  float ar, ai;
-  __device__ void begin(int i_, int& p, int& pend) {
-    i = i_;
-    if (lower) {
-      p = rp[i_];
-      pend = diag[i_];
-      const double* q = in + (int64_t)i_ * CP * W;
-      ar = __double2float_rn(ldexp(q[0], -e));
-      ai = CP == 2 ? __double2float_rn(ldexp(q[W], -e)) : 0.0f;
-    } else {
-      p = diag[i_] + 1;
-      pend = rp[i_ + 1];
-      if constexpr (CP == 1) { ar = v32[i_]; ai = 0.0f; }
-      else { ar = v32[2 * (int64_t)i_]; ai = v32[2 * (int64_t)i_ + 1]; }
-    }
-  }
-  __device__ void issue(int j, Raw& r) {
-#pragma unroll
-    for (int c = 0; c < CP; ++c) r.w[c] = ld_relaxed_u64(pk + (int64_t)j * CP + c);
-  }
-  __device__ bool check(int, const Raw& r, Val& v) {
-#pragma unroll
-    for (int c = 0; c < CP; ++c)
-      if ((unsigned)(r.w[c] >> 32) != epoch) return false;
-    if constexpr (CP == 1) v = __uint_as_float((unsigned)r.w[0]);
-    else v = make_float2(__uint_as_float((unsigned)r.w[0]), __uint_as_float((unsigned)r.w[1]));
-    return true;
-  }
-  __device__ void consume(int p, int, const Val& v) {
-    if constexpr (CP == 1) {
-      ar = fmaf(-ld_fac(f, p), v, ar);
-    } else {
-      const float lr = ld_fac(f, 2 * (int64_t)p), li = ld_fac(f, 2 * (int64_t)p + 1);
-      ar = fmaf(-lr, v.x, ar);
-      ar = fmaf(li, v.y, ar);
-      ai = fmaf(-lr, v.y, ai);
-      ai = fmaf(-li, v.x, ai);
-    }
-  }
-  __device__ Val finish() {
-    if (!unit) {
-      const int d = diag[i];
-      if constexpr (CP == 1) {
-        ar = ar / ld_fac(f, d);
-      } else {
-        const float yr = ld_fac(f, 2 * (int64_t)d), yi = ld_fac(f, 2 * (int64_t)d + 1);
-        const float den = fmaf(yr, yr, yi * yi), nr = fmaf(ar, yr, ai * yi), ni = fmaf(ai, yr, -(ar * yi));
-        ar = nr / den;
-        ai = ni / den;
-      }
-    }
-    if constexpr (CP == 1) return ar;
-    else return make_float2(ar, ai);
-  }
-  __device__ void publish(const Val& v) {
-    const unsigned long long hi = (unsigned long long)epoch << 32;
-    if constexpr (CP == 1) {
-      v32[i] = v;
-      st_relaxed_u64(pk + i, hi | __float_as_uint(v));
-    } else {
-      v32[2 * (int64_t)i] = v.x;
-      v32[2 * (int64_t)i + 1] = v.y;
-      st_relaxed_u64(pk + 2 * (int64_t)i, hi | __float_as_uint(v.x));
-      st_relaxed_u64(pk + 2 * (int64_t)i + 1, hi | __float_as_uint(v.y));
-    }
-    if (!lower) {
-      N<W, CP> z = n_zero<W, CP>();
-      if constexpr (CP == 1) {
-        z.re.c[0] = ldexp((double)v, e);
-      } else {
-        z.re.c[0] = ldexp((double)v.x, e);
-        z.im.c[0] = ldexp((double)v.y, e);
-      }
-      n_store<W, CP>(out, i, z);
-    }
-  }
-};
-template <int W, int CP, typename TS>
-__global__ void __launch_bounds__(kBlock) k_trsv_pk32(IluHandleView M, bool lower, bool unit,
-                                                      const double* __restrict__ in, double* __restrict__ out,
-                                                      const int* __restrict__ done) {
-  if (is_done(done)) return;
-  RowPk32<W, CP, TS> row;
-  row.rp = M.rp;
-  row.diag = M.diag;
-  row.f = (const TS*)M.fac;
-  row.v32 = M.v32;
-  row.pk = M.pk;
-  row.in = in;
-  row.out = out;
-  row.epoch = (unsigned)M.ctl[CTL_EPOCH] + (lower ? 0u : 1u);
-  row.lower = lower;
-  row.unit = unit;
-  row.e = scale_exponent(M.absmax);
-  syncfree_rows(lower ? M.ch_lo : M.ch_up, M.ci, M.ctl + (lower ? CTL_TICKET_LO : CTL_TICKET_UP), M.ctl, row);
-}
-
 // Binary64 factor, w-component vectors (paper's "_d" substitutions): row i computes
 //   acc = in_i;  acc -= f_ij * out_j  for the row's entries of the triangle in CSR order;
 //   upper triangle: acc /= f_ii;  out_i = acc,
 // every product and difference in w-component arithmetic (the sequential order of Algorithm 2).
 //
 // Schedule (static, balanced): the rows come in their triangle's level order, every level
-// padded to whole 32-row chunks, from the repacked triangle (SellTri: coalesced columns and
-// values per chunk).  The grid has one block per SM and kTrsvWarps warps per block, all
-// co-resident (cooperative launch); chunk c belongs to warp c mod G (G = warps in the grid),
-// numbered so that consecutive chunks of a level fall on different SMs and, once every SM has
-// one, on the next sub-partition.  A level of up to G chunks thus puts at most one chunk on each
-// FP64 unit: on this GPU an FP64 warp instruction holds its sub-partition's unit for 64 cycles
-// whatever the number of active lanes, so a level costs one chunk's instruction count, not a
-// multiple of it.  Each warp walks its chunks in increasing order; every dependency of a chunk
-// lies in an earlier level, i.e. in a smaller chunk, so the smallest unfinished chunk can always
-// proceed (no deadlock).
+// padded to whole 32-row chunks and sorted by row length within the level, from the repacked
+// triangle (SellTri: coalesced columns and values per chunk).  The grid has one block per SM and
+// WPB warps per block, all co-resident (cooperative launch); chunk c belongs to warp c mod G
+// (G = warps in the grid), numbered so that consecutive chunks of a level fall on different SMs
+// and, once every SM has one, on the next sub-partition.  A level of up to 4 x 152 chunks thus
+// puts at most one chunk on each FP64 unit: on this GPU an FP64 warp instruction holds its
+// sub-partition's unit for 64 cycles whatever the number of active lanes, so a level costs one
+// chunk's instruction count, not a multiple of it.  Wide, shallow level structures (many chunks
+// per level) want more warps per SM to overlap their memory latency: WPB is chosen per matrix
+// pattern by the autotuner.  Each warp walks its chunks in increasing order; every dependency of
+// a chunk lies in an earlier level, i.e. in a smaller chunk, so the smallest unfinished chunk can
+// always proceed (no deadlock).
 // Completion is carried by the values themselves: before the pass, `out` is filled with the
 // sentinel bit pattern kSent (k_fill_sent), a finished row stores its w-component value with
 // strong relaxed 64-bit stores (a computed value equal to kSent is stored as another NaN), and a
 // dependent row polls those words with strong relaxed loads until none is kSent.  Each word is
-// written once per pass, so a word that is not kSent is final: no flag, no fence.  The next
-// chunk's positions and slot block are fetched one chunk ahead.  Every wait is bounded by
-// kWaitCycles (then MPK_TIMEOUT in ctl[CTL_ERR] and all warps leave).
-constexpr int kTrsvWarps = 4;
-constexpr bool kRepFirst = true;
-constexpr long long kSpinCycles = 40000;  // ~20 us of polling without sleeping
+// written once per pass, so a word that is not kSent is final: no flag, no fence.  Entries are
+// handled in groups of KG: the group's columns and values are loaded together, all its
+// dependencies polled together (warp-uniform loop: lanes that are ready early do not run the
+// FP64 arithmetic as a separate divergent group), then consumed in CSR order.  The first group
+// of a chunk and the next chunk's position are fetched ahead; lane 0 first polls the chunk's
+// latest dependency alone.  Every wait is bounded by kWaitCycles (then MPK_TIMEOUT in
+// ctl[CTL_ERR] and all warps leave).
+constexpr int kTrsvWpbChoices[4] = {4, 8, 16, 32};  // candidate warps per block (per SM)
+constexpr long long kSpinCycles = 40000;            // ~20 us of polling without sleeping
 constexpr unsigned long long kSent = 0xFFFFFFFFFFFFFFFFull;
 
 __device__ __forceinline__ double ld_relaxed_f64(const double* p) {
@@ -979,7 +884,7 @@ __device__ __forceinline__ void n_publish(double* __restrict__ v, int64_t i, con
   }
 }
 static __global__ void __launch_bounds__(kBlock) k_fill_sent(int64_t m, double* __restrict__ a, int64_t mb,
-                                                      double* __restrict__ b, const int* __restrict__ done) {
+                                                             double* __restrict__ b, const int* __restrict__ done) {
   if (is_done(done)) return;
   const double s = __longlong_as_double((long long)kSent);
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m + mb; k += (int64_t)gridDim.x * blockDim.x) {
@@ -988,12 +893,21 @@ static __global__ void __launch_bounds__(kBlock) k_fill_sent(int64_t m, double* 
   }
 }
 
-template <int W, int CP>
-__global__ void __launch_bounds__(kTrsvWarps * 32, 1)
+// Bounded wait bookkeeping shared by the substitution kernels: true once the wait must end.
+__device__ __forceinline__ bool wait_expired(long long t0, int& polls, const int* ctl) {
+  const long long dt = clock64() - t0;
+  return dt > kWaitCycles || ((++polls & 63) == 0 && ld_relaxed(ctl + CTL_ERR) != 0);
+}
+__device__ __forceinline__ void wait_pause(long long t0, int ns) {
+  if (clock64() - t0 > kSpinCycles) __nanosleep(ns);
+}
+
+template <int W, int CP, int WPB>
+__global__ void __launch_bounds__(WPB * 32, 1)
     k_trsv_mp(IluHandleView M, bool lower, bool unit, const double* __restrict__ in, double* __restrict__ out,
               const int* __restrict__ done) {
   if (is_done(done)) return;
-  constexpr int kPre = 4;  // slots held in registers (longer rows stream the rest)
+  constexpr int KG = 4;  // entries per group
   const unsigned FULL = 0xffffffffu;
   const SellTri T = lower ? M.sl_lo : M.sl_up;
   const double* __restrict__ tval = (const double*)T.val;
@@ -1001,7 +915,6 @@ __global__ void __launch_bounds__(kTrsvWarps * 32, 1)
   const int lane = threadIdx.x & 31;
   const int G = gridDim.x * (blockDim.x >> 5);
   const int g = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
-  // one chunk ahead: position's row, the chunk's slot block and its latest dependency
   int nx_i = -1, nx_b0 = 0, nx_b1 = 0, nx_rep = -1;
   if (g < T.nchunks) {
     nx_i = T.perm[(g << 5) + lane];
@@ -1011,21 +924,23 @@ __global__ void __launch_bounds__(kTrsvWarps * 32, 1)
   }
   for (int chunk = g; chunk < T.nchunks; chunk += G) {
     const int i = nx_i, b0 = nx_b0, w = nx_b1 - nx_b0, rep = nx_rep;
-    // this chunk's slots, right-hand side and diagonal
-    int jj[kPre];
-    double fr[kPre], fi[kPre];
+    int jj[KG];
+    double fr[KG], fi[KG];
+    auto load_group = [&](int k0) {
 #pragma unroll
-    for (int k = 0; k < kPre; ++k) {
-      jj[k] = -1;
-      fr[k] = 0.0;
-      fi[k] = 0.0;
-      if (k < w) {
-        const int64_t e = ((int64_t)(b0 + k) << 5) + lane;
-        jj[k] = T.col[e];
-        if constexpr (CP == 1) fr[k] = tval[e];
-        else { fr[k] = tval[2 * e]; fi[k] = tval[2 * e + 1]; }
+      for (int k = 0; k < KG; ++k) {
+        jj[k] = -1;
+        fr[k] = 0.0;
+        fi[k] = 0.0;
+        if (k0 + k < w) {
+          const int64_t e = ((int64_t)(b0 + k0 + k) << 5) + lane;
+          jj[k] = T.col[e];
+          if constexpr (CP == 1) fr[k] = tval[e];
+          else { fr[k] = tval[2 * e]; fi[k] = tval[2 * e + 1]; }
+        }
       }
-    }
+    };
+    load_group(0);
     N<W, CP> acc = n_zero<W, CP>();
     double dr = 1.0, di = 0.0;
     if (i >= 0) {
@@ -1036,7 +951,6 @@ __global__ void __launch_bounds__(kTrsvWarps * 32, 1)
         else { dr = tdia[2 * q]; di = tdia[2 * q + 1]; }
       }
     }
-    // fetch the next chunk's position and slot block while this one waits
     const int nc = chunk + G;
     if (nc < T.nchunks) {
       nx_i = T.perm[(nc << 5) + lane];
@@ -1044,76 +958,49 @@ __global__ void __launch_bounds__(kTrsvWarps * 32, 1)
       nx_b1 = T.coff[nc + 1];
       nx_rep = T.rep[nc];
     }
-    // wait for the held dependencies: poll their values until no word is the sentinel
-    N<W, CP> v[kPre];
-    unsigned need = 0u;
-#pragma unroll
-    for (int k = 0; k < kPre; ++k) {
-      v[k] = n_zero<W, CP>();
-      if (jj[k] >= 0) need |= 1u << k;
-    }
     bool timeout = false;
     const long long t0 = clock64();
     int polls = 0;
-    // kRepFirst: lane 0 alone polls the chunk's latest dependency before all lanes check theirs
-    if (kRepFirst && lane == 0 && rep >= 0) {
+    if (lane == 0 && rep >= 0) {  // the chunk's latest dependency, polled by one lane
       N<W, CP> r;
       while (!n_poll<W, CP>(out, rep, r)) {
-        const long long dt = clock64() - t0;
-        if (dt > kWaitCycles || ((++polls & 63) == 0 && ld_relaxed(M.ctl + CTL_ERR) != 0)) {
-          timeout = true;
-          break;
-        }
-        if (dt > kSpinCycles) __nanosleep(128);
+        if (wait_expired(t0, polls, M.ctl)) { timeout = true; break; }
+        wait_pause(t0, 128);
       }
     }
     __syncwarp();
-    // the loop and the arithmetic after it are warp-uniform: lanes that leave the polling loop
-    // early must not run the FP64 arithmetic as a separate divergent group (every FP64 warp
-    // instruction costs the same pipe time however few lanes are active)
-    while (__any_sync(FULL, need != 0u && !timeout)) {
-      // every outstanding load of the round is issued before any is checked
+    for (int k0 = 0; k0 < w; k0 += KG) {
+      if (k0 > 0) load_group(k0);
+      N<W, CP> v[KG];
+      unsigned need = 0u;
 #pragma unroll
-      for (int k = 0; k < kPre; ++k)
-        if ((need >> k) & 1u) n_fetch<W, CP>(out, jj[k], v[k]);
-      unsigned got = 0u;
-#pragma unroll
-      for (int k = 0; k < kPre; ++k)
-        if (((need >> k) & 1u) && n_ready<W, CP>(v[k])) got |= 1u << k;
-      need &= ~got;
-      if (need != 0u && !timeout) {
-        const long long dt = clock64() - t0;
-        if (dt > kWaitCycles || ((++polls & 63) == 0 && ld_relaxed(M.ctl + CTL_ERR) != 0)) timeout = true;
+      for (int k = 0; k < KG; ++k) {
+        v[k] = n_zero<W, CP>();
+        if (jj[k] >= 0) need |= 1u << k;
       }
-      __nanosleep(64);
+      while (__any_sync(FULL, need != 0u && !timeout)) {
+        // every outstanding load of the round is issued before any is checked
+#pragma unroll
+        for (int k = 0; k < KG; ++k)
+          if ((need >> k) & 1u) n_fetch<W, CP>(out, jj[k], v[k]);
+        unsigned got = 0u;
+#pragma unroll
+        for (int k = 0; k < KG; ++k)
+          if (((need >> k) & 1u) && n_ready<W, CP>(v[k])) got |= 1u << k;
+        need &= ~got;
+        if (need != 0u && !timeout && wait_expired(t0, polls, M.ctl)) timeout = true;
+        if (__any_sync(FULL, need != 0u)) __nanosleep(64);
+      }
+      __syncwarp();
+      if (!timeout && i >= 0) {
+#pragma unroll
+        for (int k = 0; k < KG; ++k)
+          if (jj[k] >= 0) acc = n_sub<W, CP>(acc, n_mul_fp<W, CP>(v[k], fr[k], fi[k]));
+      }
     }
-    __syncwarp();
     if (!timeout && i >= 0) {
-#pragma unroll
-      for (int k = 0; k < kPre; ++k)
-        if (jj[k] >= 0) acc = n_sub<W, CP>(acc, n_mul_fp<W, CP>(v[k], fr[k], fi[k]));
-      for (int k = kPre; k < w && !timeout; ++k) {  // slots beyond the held ones, one at a time
-        const int64_t e = ((int64_t)(b0 + k) << 5) + lane;
-        const int j = T.col[e];
-        if (j < 0) break;
-        double gr, gi = 0.0;
-        if constexpr (CP == 1) gr = tval[e];
-        else { gr = tval[2 * e]; gi = tval[2 * e + 1]; }
-        N<W, CP> x;
-        while (!n_poll<W, CP>(out, j, x)) {
-          const long long dt = clock64() - t0;
-          if (dt > kWaitCycles || ((++polls & 63) == 0 && ld_relaxed(M.ctl + CTL_ERR) != 0)) {
-            timeout = true;
-            break;
-          }
-          if (dt > kSpinCycles) __nanosleep(128);
-        }
-        if (!timeout) acc = n_sub<W, CP>(acc, n_mul_fp<W, CP>(x, gr, gi));
-      }
-      if (!timeout) {
-        if (!unit) acc = n_div_fp<W, CP>(acc, dr, di);
-        n_publish<W, CP>(out, i, acc);
-      }
+      if (!unit) acc = n_div_fp<W, CP>(acc, dr, di);
+      n_publish<W, CP>(out, i, acc);
     }
     if (__any_sync(FULL, timeout)) {
       if (lane == 0) atomicCAS(M.ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
@@ -1122,14 +1009,15 @@ __global__ void __launch_bounds__(kTrsvWarps * 32, 1)
   }
 }
 
-
 // Binary32 / bfloat16 factor (substitutions in binary32): the same static balanced schedule and
 // value-carried completion as k_trsv_mp, with binary32 values and the sentinel kSent32.  Row i:
 //   lower: a = fl32(2^-e in_i) (leading components), a -= f_ij v_j (fmaf, CSR order), v_i = a;
 //   upper: a = lower result of row i, a -= f_ij v_j, a /= f_ii, v_i = a, out_i = 2^e v_i,
-// e = frexp exponent of the largest leading component of the right-hand side (the scaling keeps
-// residuals far below binary32's range representable); complex steps in the fixed fmaf order
-// (see RowPk32).  Lower results go to M.v32, upper results to M.pk read as binary32.
+// e = frexp exponent of the largest leading component of the right-hand side (of the row's
+// system in a batch): the scaling keeps residuals far below binary32's range representable.
+// Complex steps: a -= l*v as re = fmaf(-lr, vr, re), re = fmaf(li, vi, re), im = fmaf(-lr, vi, im),
+// im = fmaf(-li, vr, im); a / d as den = fmaf(dr, dr, di*di), (fmaf(ar, dr, ai*di), fmaf(ai, dr,
+// -(ar*di))) / den.  Lower results go to M.v32, upper results to M.pk read as binary32.
 constexpr unsigned kSent32 = 0xFFFFFFFFu;
 __device__ __forceinline__ float ld_relaxed_f32(const float* p) {
   unsigned v;
@@ -1154,12 +1042,12 @@ __device__ __forceinline__ bool f_poll(const float* __restrict__ v, int j, float
   return __float_as_uint(xr) != kSent32 && (CP == 1 || __float_as_uint(xi) != kSent32);
 }
 
-template <int W, int CP, typename TS>
-__global__ void __launch_bounds__(kTrsvWarps * 32, 1)
+template <int W, int CP, typename TS, int WPB>
+__global__ void __launch_bounds__(WPB * 32, 1)
     k_trsv_lp(IluHandleView M, bool lower, bool unit, const double* __restrict__ in, double* __restrict__ out,
               const int* __restrict__ done) {
   if (is_done(done)) return;
-  constexpr int kPre = 4;
+  constexpr int KG = 8;  // entries per group
   const unsigned FULL = 0xffffffffu;
   const SellTri T = lower ? M.sl_lo : M.sl_up;
   const TS* __restrict__ tval = (const TS*)T.val;
@@ -1178,20 +1066,23 @@ __global__ void __launch_bounds__(kTrsvWarps * 32, 1)
   }
   for (int chunk = g; chunk < T.nchunks; chunk += G) {
     const int i = nx_i, b0 = nx_b0, w = nx_b1 - nx_b0, rep = nx_rep;
-    int jj[kPre];
-    float fr[kPre], fi[kPre];
+    int jj[KG];
+    float fr[KG], fi[KG];
+    auto load_group = [&](int k0) {
 #pragma unroll
-    for (int k = 0; k < kPre; ++k) {
-      jj[k] = -1;
-      fr[k] = 0.0f;
-      fi[k] = 0.0f;
-      if (k < w) {
-        const int64_t s = ((int64_t)(b0 + k) << 5) + lane;
-        jj[k] = T.col[s];
-        if constexpr (CP == 1) fr[k] = ld_fac(tval, s);
-        else { fr[k] = ld_fac(tval, 2 * s); fi[k] = ld_fac(tval, 2 * s + 1); }
+      for (int k = 0; k < KG; ++k) {
+        jj[k] = -1;
+        fr[k] = 0.0f;
+        fi[k] = 0.0f;
+        if (k0 + k < w) {
+          const int64_t s = ((int64_t)(b0 + k0 + k) << 5) + lane;
+          jj[k] = T.col[s];
+          if constexpr (CP == 1) fr[k] = ld_fac(tval, s);
+          else { fr[k] = ld_fac(tval, 2 * s); fi[k] = ld_fac(tval, 2 * s + 1); }
+        }
       }
-    }
+    };
+    load_group(0);
     float ar = 0.0f, ai = 0.0f, dr = 1.0f, di = 0.0f;
     const int e = (M.sysid != nullptr && i >= 0) ? scale_exponent(M.absmax + M.sysid[i]) : e1;
     if (i >= 0) {
@@ -1216,99 +1107,77 @@ __global__ void __launch_bounds__(kTrsvWarps * 32, 1)
       nx_b1 = T.coff[nc + 1];
       nx_rep = T.rep[nc];
     }
-    float vr[kPre], vi[kPre];
-    unsigned need = 0u;
-#pragma unroll
-    for (int k = 0; k < kPre; ++k) {
-      vr[k] = 0.0f;
-      vi[k] = 0.0f;
-      if (jj[k] >= 0) need |= 1u << k;
-    }
     bool timeout = false;
     const long long t0 = clock64();
     int polls = 0;
-    if (kRepFirst && lane == 0 && rep >= 0) {
+    if (lane == 0 && rep >= 0) {  // the chunk's latest dependency, polled by one lane
       float xr, xi;
       while (!f_poll<CP>(mine, rep, xr, xi)) {
-        const long long dt = clock64() - t0;
-        if (dt > kWaitCycles || ((++polls & 63) == 0 && ld_relaxed(M.ctl + CTL_ERR) != 0)) {
-          timeout = true;
-          break;
-        }
-        if (dt > kSpinCycles) __nanosleep(128);
+        if (wait_expired(t0, polls, M.ctl)) { timeout = true; break; }
+        wait_pause(t0, 128);
       }
     }
     __syncwarp();
-    while (__any_sync(FULL, need != 0u && !timeout)) {
-      unsigned got = 0u;
+    for (int k0 = 0; k0 < w; k0 += KG) {
+      if (k0 > 0) load_group(k0);
+      float vr[KG], vi[KG];
+      unsigned need = 0u;
 #pragma unroll
-      for (int k = 0; k < kPre; ++k)
-        if ((need >> k) & 1u) {
-          vr[k] = ld_relaxed_f32(mine + (int64_t)jj[k] * CP);
-          if constexpr (CP == 2) vi[k] = ld_relaxed_f32(mine + (int64_t)jj[k] * CP + 1);
-        }
-#pragma unroll
-      for (int k = 0; k < kPre; ++k)
-        if (((need >> k) & 1u) && __float_as_uint(vr[k]) != kSent32 && (CP == 1 || __float_as_uint(vi[k]) != kSent32))
-          got |= 1u << k;
-      need &= ~got;
-      if (need != 0u && !timeout) {
-        const long long dt = clock64() - t0;
-        if (dt > kWaitCycles || ((++polls & 63) == 0 && ld_relaxed(M.ctl + CTL_ERR) != 0)) timeout = true;
+      for (int k = 0; k < KG; ++k) {
+        vr[k] = 0.0f;
+        vi[k] = 0.0f;
+        if (jj[k] >= 0) need |= 1u << k;
       }
-      __nanosleep(64);
-    }
-    __syncwarp();
-    if (!timeout && i >= 0) {
-      auto consume = [&](float lr, float li, float xr, float xi) {
-        if constexpr (CP == 1) {
-          ar = fmaf(-lr, xr, ar);
-        } else {
-          ar = fmaf(-lr, xr, ar);
-          ar = fmaf(li, xi, ar);
-          ai = fmaf(-lr, xi, ai);
-          ai = fmaf(-li, xr, ai);
-        }
-      };
+      while (__any_sync(FULL, need != 0u && !timeout)) {
 #pragma unroll
-      for (int k = 0; k < kPre; ++k)
-        if (jj[k] >= 0) consume(fr[k], fi[k], vr[k], vi[k]);
-      for (int k = kPre; k < w && !timeout; ++k) {  // slots beyond the held ones, one at a time
-        const int64_t s = ((int64_t)(b0 + k) << 5) + lane;
-        const int j = T.col[s];
-        if (j < 0) break;
-        float gr, gi = 0.0f;
-        if constexpr (CP == 1) gr = ld_fac(tval, s);
-        else { gr = ld_fac(tval, 2 * s); gi = ld_fac(tval, 2 * s + 1); }
-        float xr, xi;
-        while (!f_poll<CP>(mine, j, xr, xi)) {
-          const long long dt = clock64() - t0;
-          if (dt > kWaitCycles || ((++polls & 63) == 0 && ld_relaxed(M.ctl + CTL_ERR) != 0)) {
-            timeout = true;
-            break;
+        for (int k = 0; k < KG; ++k)
+          if ((need >> k) & 1u) {
+            vr[k] = ld_relaxed_f32(mine + (int64_t)jj[k] * CP);
+            if constexpr (CP == 2) vi[k] = ld_relaxed_f32(mine + (int64_t)jj[k] * CP + 1);
           }
-          if (dt > kSpinCycles) __nanosleep(128);
-        }
-        if (!timeout) consume(gr, gi, xr, xi);
+        unsigned got = 0u;
+#pragma unroll
+        for (int k = 0; k < KG; ++k)
+          if (((need >> k) & 1u) && __float_as_uint(vr[k]) != kSent32 &&
+              (CP == 1 || __float_as_uint(vi[k]) != kSent32))
+            got |= 1u << k;
+        need &= ~got;
+        if (need != 0u && !timeout && wait_expired(t0, polls, M.ctl)) timeout = true;
+        if (__any_sync(FULL, need != 0u)) __nanosleep(64);
       }
-      if (!timeout) {
-        if (!unit) {
+      __syncwarp();
+      if (!timeout && i >= 0) {
+#pragma unroll
+        for (int k = 0; k < KG; ++k) {
+          if (jj[k] < 0) continue;
           if constexpr (CP == 1) {
-            ar = ar / dr;
+            ar = fmaf(-fr[k], vr[k], ar);
           } else {
-            const float den = fmaf(dr, dr, di * di), nr = fmaf(ar, dr, ai * di), ni = fmaf(ai, dr, -(ar * di));
-            ar = nr / den;
-            ai = ni / den;
+            ar = fmaf(-fr[k], vr[k], ar);
+            ar = fmaf(fi[k], vi[k], ar);
+            ai = fmaf(-fr[k], vi[k], ai);
+            ai = fmaf(-fi[k], vr[k], ai);
           }
         }
-        st_relaxed_f32(mine + (int64_t)i * CP, ar);
-        if constexpr (CP == 2) st_relaxed_f32(mine + (int64_t)i * CP + 1, ai);
-        if (!lower) {
-          N<W, CP> z = n_zero<W, CP>();
-          z.re.c[0] = ldexp((double)ar, e);
-          if constexpr (CP == 2) z.im.c[0] = ldexp((double)ai, e);
-          n_store<W, CP>(out, i, z);
+      }
+    }
+    if (!timeout && i >= 0) {
+      if (!unit) {
+        if constexpr (CP == 1) {
+          ar = ar / dr;
+        } else {
+          const float den = fmaf(dr, dr, di * di), nr = fmaf(ar, dr, ai * di), ni = fmaf(ai, dr, -(ar * di));
+          ar = nr / den;
+          ai = ni / den;
         }
+      }
+      st_relaxed_f32(mine + (int64_t)i * CP, ar);
+      if constexpr (CP == 2) st_relaxed_f32(mine + (int64_t)i * CP + 1, ai);
+      if (!lower) {
+        N<W, CP> z = n_zero<W, CP>();
+        z.re.c[0] = ldexp((double)ar, e);
+        if constexpr (CP == 2) z.im.c[0] = ldexp((double)ai, e);
+        n_store<W, CP>(out, i, z);
       }
     }
     if (__any_sync(FULL, timeout)) {
@@ -1417,32 +1286,57 @@ struct Launch {
     count_launch();
     k_absmax<W, CP><<<grid_for(n), kBlock, 0, s>>>(n, v, out, done, bt ? bt->sysid : nullptr);
   }
+  // Launch of a static-schedule substitution with wpb warps per block (one block per SM, all
+  // co-resident: cooperative launch)
+  static int coop(const void* fn, int wpb, const IluHandleView& M, bool lower, bool unit, const double* in,
+                  double* out, const int* done, cudaStream_t s) {
+    void* args[] = {(void*)&M, (void*)&lower, (void*)&unit, (void*)&in, (void*)&out, (void*)&done};
+    count_launch();
+    const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(sm_count()), dim3(wpb * 32), args, 0, s);
+    return e == cudaSuccess ? MPK_OK : MPK_CUDA_ERROR;
+  }
+  static const void* mp_fn(int wpb) {
+    switch (wpb) {
+      case 8: return (const void*)k_trsv_mp<W, CP, 8>;
+      case 16: return (const void*)k_trsv_mp<W, CP, 16>;
+      case 32: return (const void*)k_trsv_mp<W, CP, 32>;
+      default: return (const void*)k_trsv_mp<W, CP, 4>;
+    }
+  }
+  template <typename TS>
+  static const void* lp_fn(int wpb) {
+    switch (wpb) {
+      case 8: return (const void*)k_trsv_lp<W, CP, TS, 8>;
+      case 16: return (const void*)k_trsv_lp<W, CP, TS, 16>;
+      case 32: return (const void*)k_trsv_lp<W, CP, TS, 32>;
+      default: return (const void*)k_trsv_lp<W, CP, TS, 4>;
+    }
+  }
   static int trsv_mp(const IluHandleView& M, bool lower, bool unit, const double* in, double* out, const int* done,
                      cudaStream_t s) {
     // out starts as sentinels: completion is read from the values
-    {
-      count_launch();
-      const int64_t m = (int64_t)M.n * CP * W;
-      k_fill_sent<<<grid_for(M.n), kBlock, 0, s>>>(m, out, 0, nullptr, done);
-    }
-    // one block per SM, all co-resident: the static schedule of k_trsv_mp needs every warp running
-    void* args[] = {(void*)&M, (void*)&lower, (void*)&unit, (void*)&in, (void*)&out, (void*)&done};
     count_launch();
-    const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_trsv_mp<W, CP>, dim3(sm_count()),
-                                                      dim3(kTrsvWarps * 32), args, 0, s);
-    return e == cudaSuccess ? MPK_OK : MPK_CUDA_ERROR;
+    k_fill_sent<<<grid_for(M.n), kBlock, 0, s>>>((int64_t)M.n * CP * W, out, 0, nullptr, done);
+    return coop(mp_fn(M.wpb), M.wpb, M, lower, unit, in, out, done, s);
   }
   static int trsv32(const IluHandleView& M, bool lower, bool unit, const double* in, double* out, const int* done,
                     cudaStream_t s) {
     // this pass's binary32 results start as sentinels: completion is read from the values
-    count_launch(2);
+    count_launch();
     float* mine = lower ? M.v32 : reinterpret_cast<float*>(M.pk);
     k_fill_sent32<<<grid_for(M.n), kBlock, 0, s>>>((int64_t)M.n * CP, mine, done);
-    // one block per SM, all co-resident (static schedule)
-    void* args[] = {(void*)&M, (void*)&lower, (void*)&unit, (void*)&in, (void*)&out, (void*)&done};
-    const void* fn = M.prec == MPK_ILU_BF16 ? (const void*)k_trsv_lp<W, CP, uint16_t> : (const void*)k_trsv_lp<W, CP, float>;
-    const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(sm_count()), dim3(kTrsvWarps * 32), args, 0, s);
-    return e == cudaSuccess ? MPK_OK : MPK_CUDA_ERROR;
+    const void* fn = M.prec == MPK_ILU_BF16 ? lp_fn<uint16_t>(M.wpb) : lp_fn<float>(M.wpb);
+    return coop(fn, M.wpb, M, lower, unit, in, out, done, s);
+  }
+  // largest per-SM warp count whose block fits one SM, for each candidate (0: does not fit)
+  static int trsv_fits(int prec, int wpb) {
+    const void* fn = prec == MPK_ILU_FP64 ? mp_fn(wpb) : (prec == MPK_ILU_BF16 ? lp_fn<uint16_t>(wpb) : lp_fn<float>(wpb));
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, wpb * 32, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return per_sm >= 1 ? 1 : 0;
   }
   static Ops table() {
     Ops o;
@@ -1458,6 +1352,7 @@ struct Launch {
     o.trsv_mp = &trsv_mp;
     o.trsv32 = &trsv32;
     o.absmax = &absmax;
+    o.trsv_fits = &trsv_fits;
     return o;
   }
 };

@@ -535,8 +535,16 @@ static int solve_impl(int method, int w, const mpk_csr* Ac, const mpk_ilu* Mc, c
     MPK_CUDA(cudaStreamSynchronize(s));  // the host buffers above go out of scope
   }
 
-  // SpMV row order of this matrix (autotuned once per pattern; V[15], V[16] serve as scratch)
+  // SpMV row order and substitution warps per SM for this matrix pattern (autotuned once per
+  // pattern and cached; V[15], V[16] serve as scratch: zero in, zero out)
   c.A.order = spmv_order(o, c.A, w, cp, V[15], V[16], s);
+  if (M != nullptr) {
+    const int st = tune_substitution(M, o, w, V[15], V[16], s);
+    if (st != MPK_OK) {
+      cudaFreeAsync(base, s);
+      return st;
+    }
+  }
 
   double* r = V[0];
   double* rt = V[1];
