@@ -31,6 +31,7 @@
 #ifndef MPK_H
 #define MPK_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -191,6 +192,48 @@ int mpk_krylov_solve(int method, int w, const mpk_csr* A, const mpk_ilu* M, cons
 int mpk_krylov_solve_batched(int method, int w, const mpk_csr* A, int nsys, const int32_t* sys_rows_host,
                              const int32_t* sys_rows_dev, const mpk_ilu* M, const double* b_dev, double* x_dev,
                              const mpk_opts* opts, mpk_info* infos, void* stream);
+
+/* ---- Learned correction of the ILU(0) factor (the benchmark spec's learned-preconditioner pattern;
+ * the paper has no counterpart) -----------------------------------------------------------------
+ * A graph network on A's pattern (3 message-passing layers, hidden width 32, binary32 weights,
+ * bfloat16-stored activations; the exact network is documented in csrc/gnn.cu) predicts one value
+ * o_p per stored entry p; the corrected factor is f'_p = f_p (1 + 0.5 tanh o_p), so o = 0 is the
+ * plain ILU(0) factor.  Real matrices only.  Parameters: MPK_GNN_NPARAMS binary32 values in one
+ * device array.  work_dev: caller-owned device scratch of at least mpk_gnn_workspace_bytes(n, nnz,
+ * nprobe, nsys) bytes; mpk_gnn_forward leaves in it the activations that mpk_gnn_backward reads,
+ * so the three calls of a training step share one workspace and one (A, M). */
+#define MPK_GNN_NPARAMS 12193
+int mpk_gnn_nparams(void);
+size_t mpk_gnn_workspace_bytes(int n, int nnz, int nprobe, int nsys);
+/* o_dev[nnz] = network output for A and the factor M (its features read A's values and M's). */
+int mpk_gnn_forward(const mpk_csr* A, const mpk_ilu* M, const float* params_dev, float* o_dev, void* work_dev,
+                    size_t work_bytes, void* stream);
+/* Training loss of the corrected factor and its gradient with respect to o:
+ *   loss = mean over systems s of  sum_{i in s} ||((L'U' - A) W)_i||^2 / sum_{i in s} ||(A W)_i||^2
+ * W: nprobe (1..16) probe vectors, n x nprobe row-major binary32 (device); L' unit lower, U' upper,
+ * both from f'.  nsys > 1: A is a block-diagonal batch with row offsets sys_rows_dev[nsys+1].
+ * loss_dev: one float; g_o_dev: nnz floats. */
+int mpk_gnn_loss(const mpk_csr* A, const mpk_ilu* M, const float* o_dev, int nprobe, const float* probes_dev,
+                 int nsys, const int32_t* sys_rows_dev, float* loss_dev, float* g_o_dev, void* work_dev,
+                 size_t work_bytes, void* stream);
+/* Training loss of the preconditioned operator and its gradient with respect to o:
+ *   loss = mean over systems s of  sum_{i in s} ||(M'^-1 A W - W)_i||^2 / sum_{i in s} ||W_i||^2
+ * with M' = L'U' from f' (binary32 arithmetic; four level-scheduled triangular solves per call,
+ * two of them with the transposed factors).  nprobe 1..4; the pattern must be structurally
+ * symmetric (MPK_INVALID_ARG otherwise).  Other arguments as mpk_gnn_loss. */
+int mpk_gnn_loss_precond(const mpk_csr* A, const mpk_ilu* M, const float* o_dev, int nprobe,
+                         const float* probes_dev, int nsys, const int32_t* sys_rows_dev, float* loss_dev,
+                         float* g_o_dev, void* work_dev, size_t work_bytes, void* stream);
+/* g_params_dev = d loss / d params by back-propagating g_o_dev through the network (after
+ * mpk_gnn_forward with the same A, M, params and workspace). */
+int mpk_gnn_backward(const mpk_csr* A, const mpk_ilu* M, const float* params_dev, const float* g_o_dev,
+                     float* g_params_dev, void* work_dev, size_t work_bytes, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected; step counts from 1). */
+int mpk_gnn_adam(int nparams, float* params_dev, const float* grad_dev, float* m_dev, float* v_dev, float lr,
+                 int step, void* stream);
+/* Replace M's factor by f' = f (1 + 0.5 tanh o) in M's precision (repacks the triangles; the
+ * conjugate transpose is rebuilt on its next use). */
+int mpk_ilu0_correct(mpk_ilu* M, const float* o_dev, void* stream);
 
 /* End-to-end convenience: host CSR, host b and x (x0 in, solution out).  Copies A and b to
  * the device, builds ILU(0) in `prec` (MPK_ILU_NONE: none), solves, copies x back and frees

@@ -63,6 +63,15 @@ SIGNATURES = [
                             ctypes.POINTER(Opts), ctypes.POINTER(Info)]),
     ("mpk_krylov_solve_batched", _I, [_I, _I, ctypes.POINTER(CsrDesc), _I, _VP, _VP, _VP, _VP, _VP,
                                       ctypes.POINTER(Opts), ctypes.POINTER(Info), _VP]),
+    ("mpk_gnn_nparams", _I, []),
+    ("mpk_gnn_workspace_bytes", ctypes.c_size_t, [_I, _I, _I, _I]),
+    ("mpk_gnn_forward", _I, [ctypes.POINTER(CsrDesc), _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
+    ("mpk_gnn_loss", _I, [ctypes.POINTER(CsrDesc), _VP, _VP, _I, _VP, _I, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
+    ("mpk_gnn_loss_precond", _I, [ctypes.POINTER(CsrDesc), _VP, _VP, _I, _VP, _I, _VP, _VP, _VP, _VP,
+                                  ctypes.c_size_t, _VP]),
+    ("mpk_gnn_backward", _I, [ctypes.POINTER(CsrDesc), _VP, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
+    ("mpk_gnn_adam", _I, [_I, _VP, _VP, _VP, _VP, ctypes.c_float, _I, _VP]),
+    ("mpk_ilu0_correct", _I, [_VP, _VP, _VP]),
 ]
 
 

@@ -1,0 +1,919 @@
+// gnn.cu -- learned correction of the ILU(0) factor (the benchmark spec's learned-preconditioner
+// pattern; the paper has no counterpart): a graph network on A's pattern predicts, per stored
+// entry, o_ij, and the corrected factor is f'_ij = f_ij (1 + 0.5 tanh o_ij).  o = 0 gives the
+// plain ILU(0) factor exactly, which stays the fallback.
+//
+// Network (hidden width H = 32, binary32 weights, activations stored as bfloat16 and computed in
+// binary32):
+//   node input  x_i = (1, sum_{j!=i} |a_ij| / a_ii, sum_j a_ij / a_ii, f_ii / a_ii)
+//   edge input  e_ij = (a_ij / a_ii, a_ji / a_jj (1 on the diagonal, 0 if a_ji is not stored),
+//                       f_ij / a_ii, sign(j - i))
+//   encoder     h0_i = bf16(relu(W0^T x_i + b0))
+//   3 layers    m_ij = relu(Wm^T [h_j, e_ij] + bm) for the stored off-diagonal entries of row i
+//               a_i = bf16(sum_j m_ij)           (CSR order)
+//               h'_i = bf16(h_i + relu(Wu^T [h_i, a_i] + bu))
+//   decoder     o_ij = wo . relu(Wd^T [h_i, h_j, e_ij] + bd) + bo for every stored entry (i, j)
+// Training loss (probe estimate of the factorisation error, per system of a batch):
+//   loss = mean_s  sum_{i in s} ||(L'U' W - A W)_i||^2 / sum_{i in s} ||(A W)_i||^2
+// over nprobe probe vectors W (L' unit lower with the corrected strict lower part, U' the
+// corrected upper part).  Forward, loss gradient and backward are hand-written; parameters live
+// in one binary32 array (layout below, weight matrices stored input-major [in][out]).
+#include <cuda_bf16.h>
+
+#include <climits>
+#include <cstdint>
+
+#include "internal.h"
+
+namespace mpk {
+namespace gnn {
+
+constexpr int H = 32, FN = 4, FE = 4, NL = 3;
+constexpr int P_W0 = 0, P_B0 = FN * H;
+constexpr int L_WM = 0, L_BM = (H + FE) * H, L_WU = L_BM + H, L_BU = L_WU + 2 * H * H, L_SIZE = L_BU + H;
+constexpr int P_L0 = P_B0 + H;
+constexpr int P_DEC = P_L0 + NL * L_SIZE;
+constexpr int D_WD = 0, D_BD = (2 * H + FE) * H, D_WO = D_BD + H, D_BO = D_WO + H;
+constexpr int NPARAMS = P_DEC + D_BO + 1;
+static_assert(NPARAMS == MPK_GNN_NPARAMS, "parameter layout");
+constexpr int kThreads = 256;
+constexpr int kBlock = 256;
+constexpr int kStride = H + 1;  // shared-memory row stride: conflict-free by row and by column
+
+__device__ __forceinline__ float bf(const __nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ __nv_bfloat16 tobf(float x) { return __float2bfloat16_rn(x); }
+__device__ __forceinline__ float shfl(float v, int l) { return __shfl_sync(0xffffffffu, v, l); }
+
+// rows x H block of weights (global, input-major) into shared memory with row stride kStride
+__device__ __forceinline__ void load_w(float* sw, const float* w, int rows) {
+  for (int t = threadIdx.x; t < rows * H; t += blockDim.x) sw[(t / H) * kStride + (t % H)] = w[t];
+}
+__device__ __forceinline__ void flush_w(float* gw, const float* sw, int rows) {
+  for (int t = threadIdx.x; t < rows * H; t += blockDim.x) atomicAdd(gw + t, sw[(t / H) * kStride + (t % H)]);
+}
+__device__ __forceinline__ void zero_s(float* s, int count) {
+  for (int t = threadIdx.x; t < count; t += blockDim.x) s[t] = 0.0f;
+}
+__device__ __forceinline__ int warp_id_global() { return (blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
+__device__ __forceinline__ int warps_total() { return (gridDim.x * blockDim.x) >> 5; }
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+// corrected factor value
+__device__ __forceinline__ float corrected(float f, float o) { return f * (1.0f + 0.5f * tanhf(o)); }
+
+// ---- factor values of the handle as binary32 ------------------------------------------------
+__device__ __forceinline__ float fac_at(const void* fac, int prec, int64_t p) {
+  if (prec == MPK_ILU_FP64) return (float)((const double*)fac)[p];
+  if (prec == MPK_ILU_FP32) return ((const float*)fac)[p];
+  return __uint_as_float(((unsigned)((const uint16_t*)fac)[p]) << 16);
+}
+
+// position of (j, i) for every stored (i, j) (-1 if absent): binary search in row j
+__global__ void k_tpos(int n, const int* __restrict__ rp, const int* __restrict__ ci, int* __restrict__ tpos) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      const int j = ci[p];
+      int lo = rp[j], hi = rp[j + 1] - 1, found = -1;
+      while (lo <= hi) {
+        const int mid = (lo + hi) >> 1;
+        if (ci[mid] == i) { found = mid; break; }
+        if (ci[mid] < i) lo = mid + 1;
+        else hi = mid - 1;
+      }
+      tpos[p] = found;
+    }
+  }
+}
+
+__global__ void k_features(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                           const double* __restrict__ a, const void* fac, int prec, const int* __restrict__ tpos,
+                           const int* __restrict__ diag, float4* __restrict__ xn, float4* __restrict__ xe) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int d = diag[i];
+    const double aii = a[d];
+    const double inv = aii != 0.0 ? 1.0 / aii : 0.0;
+    double sabs = 0.0, ssum = 0.0;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      const int j = ci[p];
+      ssum += a[p];
+      if (j != i) sabs += fabs(a[p]);
+      const int q = tpos[p];
+      double aji = 0.0;
+      if (j == i) aji = 1.0;
+      else if (q >= 0) {
+        const double ajj = a[diag[j]];
+        aji = ajj != 0.0 ? a[q] / ajj : 0.0;
+      }
+      xe[p] = make_float4((float)(a[p] * inv), (float)aji, (float)(fac_at(fac, prec, p) * inv),
+                          j < i ? 1.0f : (j > i ? -1.0f : 0.0f));
+    }
+    xn[i] = make_float4(1.0f, (float)(sabs * fabs(inv)), (float)(ssum * inv), (float)(fac_at(fac, prec, d) * inv));
+  }
+}
+
+// ---- forward ----------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_encode(int n, const float4* __restrict__ xn, const float* __restrict__ P,
+                                                     __nv_bfloat16* __restrict__ h0) {
+  const int k = threadIdx.x & 31;
+  const float w0 = P[P_W0 + 0 * H + k], w1 = P[P_W0 + 1 * H + k], w2 = P[P_W0 + 2 * H + k],
+              w3 = P[P_W0 + 3 * H + k], b = P[P_B0 + k];
+  for (int i = warp_id_global(); i < n; i += warps_total()) {
+    const float4 x = xn[i];
+    float pre = b;
+    pre = fmaf(w0, x.x, pre);
+    pre = fmaf(w1, x.y, pre);
+    pre = fmaf(w2, x.z, pre);
+    pre = fmaf(w3, x.w, pre);
+    h0[(int64_t)i * H + k] = tobf(fmaxf(pre, 0.0f));
+  }
+}
+
+// message pre-activation of entry p (neighbour value hj held by lane k)
+__device__ __forceinline__ float msg_pre(const float* sWm, const float* sbm, float hj, float4 e, int k) {
+  float pre = sbm[k];
+#pragma unroll
+  for (int l = 0; l < H; ++l) pre = fmaf(sWm[l * kStride + k], shfl(hj, l), pre);
+  pre = fmaf(sWm[(H + 0) * kStride + k], e.x, pre);
+  pre = fmaf(sWm[(H + 1) * kStride + k], e.y, pre);
+  pre = fmaf(sWm[(H + 2) * kStride + k], e.z, pre);
+  pre = fmaf(sWm[(H + 3) * kStride + k], e.w, pre);
+  return pre;
+}
+__device__ __forceinline__ float upd_pre(const float* sWu, const float* sbu, float hi, float a, int k) {
+  float q = sbu[k];
+#pragma unroll
+  for (int l = 0; l < H; ++l) q = fmaf(sWu[l * kStride + k], shfl(hi, l), q);
+#pragma unroll
+  for (int l = 0; l < H; ++l) q = fmaf(sWu[(H + l) * kStride + k], shfl(a, l), q);
+  return q;
+}
+
+__global__ void __launch_bounds__(kThreads) k_layer(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                    const float4* __restrict__ xe, const float* __restrict__ PL,
+                                                    const __nv_bfloat16* __restrict__ hin,
+                                                    __nv_bfloat16* __restrict__ aout, __nv_bfloat16* __restrict__ hout) {
+  __shared__ float sWm[(H + FE) * kStride], sbm[H], sWu[2 * H * kStride], sbu[H];
+  load_w(sWm, PL + L_WM, H + FE);
+  load_w(sWu, PL + L_WU, 2 * H);
+  for (int t = threadIdx.x; t < H; t += blockDim.x) {
+    sbm[t] = PL[L_BM + t];
+    sbu[t] = PL[L_BU + t];
+  }
+  __syncthreads();
+  const int k = threadIdx.x & 31;
+  for (int i = warp_id_global(); i < n; i += warps_total()) {
+    float acc = 0.0f;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      const int j = ci[p];
+      if (j == i) continue;
+      acc += fmaxf(msg_pre(sWm, sbm, bf(hin[(int64_t)j * H + k]), xe[p], k), 0.0f);
+    }
+    const __nv_bfloat16 ab = tobf(acc);
+    aout[(int64_t)i * H + k] = ab;
+    const float hi = bf(hin[(int64_t)i * H + k]);
+    const float q = upd_pre(sWu, sbu, hi, bf(ab), k);
+    hout[(int64_t)i * H + k] = tobf(hi + fmaxf(q, 0.0f));
+  }
+}
+
+__device__ __forceinline__ float dec_pre(const float* sWd, const float* sbd, float hi, float hj, float4 e, int k) {
+  float pre = sbd[k];
+#pragma unroll
+  for (int l = 0; l < H; ++l) pre = fmaf(sWd[l * kStride + k], shfl(hi, l), pre);
+#pragma unroll
+  for (int l = 0; l < H; ++l) pre = fmaf(sWd[(H + l) * kStride + k], shfl(hj, l), pre);
+  pre = fmaf(sWd[(2 * H + 0) * kStride + k], e.x, pre);
+  pre = fmaf(sWd[(2 * H + 1) * kStride + k], e.y, pre);
+  pre = fmaf(sWd[(2 * H + 2) * kStride + k], e.z, pre);
+  pre = fmaf(sWd[(2 * H + 3) * kStride + k], e.w, pre);
+  return pre;
+}
+
+__global__ void __launch_bounds__(kThreads) k_decode(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                     const float4* __restrict__ xe, const float* __restrict__ PD,
+                                                     const __nv_bfloat16* __restrict__ h, float* __restrict__ o) {
+  __shared__ float sWd[(2 * H + FE) * kStride], sbd[H];
+  load_w(sWd, PD + D_WD, 2 * H + FE);
+  for (int t = threadIdx.x; t < H; t += blockDim.x) sbd[t] = PD[D_BD + t];
+  __syncthreads();
+  const int k = threadIdx.x & 31;
+  const float wo = PD[D_WO + k], bo = PD[D_BO];
+  for (int i = warp_id_global(); i < n; i += warps_total()) {
+    const float hi = bf(h[(int64_t)i * H + k]);
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      const int j = ci[p];
+      const float pre = dec_pre(sWd, sbd, hi, bf(h[(int64_t)j * H + k]), xe[p], k);
+      const float out = warp_sum(wo * fmaxf(pre, 0.0f)) + bo;
+      if (k == 0) o[p] = out;
+    }
+  }
+}
+
+// ---- loss and its gradient with respect to o --------------------------------------------------
+// pass 1: u = U' W, aw = A W (row i, nprobe columns)
+__global__ void k_loss_u(int n, int K, const int* __restrict__ rp, const int* __restrict__ ci,
+                         const double* __restrict__ a, const void* fac, int prec, const int* __restrict__ diag,
+                         const float* __restrict__ o, const float* __restrict__ W, float* __restrict__ u,
+                         float* __restrict__ aw) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)n * K; t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / K), c = (int)(t % K);
+    float su = 0.0f, sa = 0.0f;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      const int j = ci[p];
+      const float wj = W[(int64_t)j * K + c];
+      sa = fmaf((float)a[p], wj, sa);
+      if (p >= diag[i]) su = fmaf(corrected(fac_at(fac, prec, p), o[p]), wj, su);
+    }
+    u[t] = su;
+    aw[t] = sa;
+  }
+}
+// pass 2: r = L' u - aw; per-system sums R_s = sum r^2, D_s = sum aw^2
+__global__ void k_loss_r(int n, int K, const int* __restrict__ rp, const int* __restrict__ ci,
+                         const void* fac, int prec, const int* __restrict__ diag, const float* __restrict__ o,
+                         const float* __restrict__ u, const float* __restrict__ aw, float* __restrict__ r,
+                         const int* __restrict__ sysid, float* __restrict__ sums) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)n * K; t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / K), c = (int)(t % K);
+    float v = u[t];
+    for (int p = rp[i]; p < diag[i]; ++p) v = fmaf(corrected(fac_at(fac, prec, p), o[p]), u[(int64_t)ci[p] * K + c], v);
+    const float rr = v - aw[t];
+    r[t] = rr;
+    const int s = sysid ? sysid[i] : 0;
+    atomicAdd(sums + 2 * s, rr * rr);
+    atomicAdd(sums + 2 * s + 1, aw[t] * aw[t]);
+  }
+}
+__global__ void k_loss_total(int nsys, const float* __restrict__ sums, float* __restrict__ loss) {
+  float tot = 0.0f;
+  for (int s = threadIdx.x; s < nsys; s += blockDim.x) tot += sums[2 * s + 1] > 0.0f ? sums[2 * s] / sums[2 * s + 1] : 0.0f;
+  tot = warp_sum(tot);
+  __shared__ float part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = tot;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float z = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) z += part[w];
+    *loss = z / (float)nsys;
+  }
+}
+// pass 3: g_r = 2 r / (nsys D_s); lower entries: g_f = sum_c g_r_i u_j, g_o; g_u = L'^T g_r (atomic)
+__global__ void k_loss_grad_lower(int n, int K, int nsys, const int* __restrict__ rp, const int* __restrict__ ci,
+                                  const void* fac, int prec, const int* __restrict__ diag, const float* __restrict__ o,
+                                  const float* __restrict__ u, const float* __restrict__ r, const int* __restrict__ sysid,
+                                  const float* __restrict__ sums, float* __restrict__ gu, float* __restrict__ go) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int s = sysid ? sysid[i] : 0;
+    const float coef = sums[2 * s + 1] > 0.0f ? 2.0f / ((float)nsys * sums[2 * s + 1]) : 0.0f;
+    for (int c = 0; c < K; ++c) atomicAdd(gu + (int64_t)i * K + c, coef * r[(int64_t)i * K + c]);
+    for (int p = rp[i]; p < diag[i]; ++p) {
+      const int j = ci[p];
+      const float f = fac_at(fac, prec, p), th = tanhf(o[p]), fp = f * (1.0f + 0.5f * th);
+      float gf = 0.0f;
+      for (int c = 0; c < K; ++c) {
+        const float gr = coef * r[(int64_t)i * K + c];
+        gf = fmaf(gr, u[(int64_t)j * K + c], gf);
+        atomicAdd(gu + (int64_t)j * K + c, fp * gr);
+      }
+      go[p] = gf * f * 0.5f * (1.0f - th * th);
+    }
+  }
+}
+// pass 4: upper entries (diagonal included): g_f = sum_c g_u_i w_j
+__global__ void k_loss_grad_upper(int n, int K, const int* __restrict__ rp, const int* __restrict__ ci,
+                                  const void* fac, int prec, const int* __restrict__ diag, const float* __restrict__ o,
+                                  const float* __restrict__ W, const float* __restrict__ gu, float* __restrict__ go) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int p = diag[i]; p < rp[i + 1]; ++p) {
+      const int j = ci[p];
+      const float f = fac_at(fac, prec, p), th = tanhf(o[p]);
+      float gf = 0.0f;
+      for (int c = 0; c < K; ++c) gf = fmaf(gu[(int64_t)i * K + c], W[(int64_t)j * K + c], gf);
+      go[p] = gf * f * 0.5f * (1.0f - th * th);
+    }
+  }
+}
+
+// ---- backward ---------------------------------------------------------------------------------
+// decoder: g_params (decoder part) and g_h (w.r.t. the last node states, atomic)
+__global__ void __launch_bounds__(kThreads) k_decode_bwd(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                         const float4* __restrict__ xe, const float* __restrict__ PD,
+                                                         const __nv_bfloat16* __restrict__ h, const float* __restrict__ go,
+                                                         float* __restrict__ gPD, float* __restrict__ gh) {
+  __shared__ float sWd[(2 * H + FE) * kStride], sbd[H], gWd[(2 * H + FE) * kStride], gbd[H], gwo[H], gbo;
+  load_w(sWd, PD + D_WD, 2 * H + FE);
+  zero_s(gWd, (2 * H + FE) * kStride);
+  for (int t = threadIdx.x; t < H; t += blockDim.x) {
+    sbd[t] = PD[D_BD + t];
+    gbd[t] = 0.0f;
+    gwo[t] = 0.0f;
+  }
+  if (threadIdx.x == 0) gbo = 0.0f;
+  __syncthreads();
+  const int k = threadIdx.x & 31;
+  const float wo = PD[D_WO + k];
+  float r_gbd = 0.0f, r_gwo = 0.0f, r_gbo = 0.0f;
+  for (int i = warp_id_global(); i < n; i += warps_total()) {
+    const float hi = bf(h[(int64_t)i * H + k]);
+    float ghi = 0.0f;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      const int j = ci[p];
+      const float hj = bf(h[(int64_t)j * H + k]);
+      const float4 e = xe[p];
+      const float pre = dec_pre(sWd, sbd, hi, hj, e, k);
+      const float g = go[p];
+      const float gpre = pre > 0.0f ? g * wo : 0.0f;
+      r_gwo = fmaf(g, fmaxf(pre, 0.0f), r_gwo);
+      r_gbo += g;
+      r_gbd += gpre;
+#pragma unroll
+      for (int l = 0; l < H; ++l) atomicAdd(&gWd[l * kStride + k], shfl(hi, l) * gpre);
+#pragma unroll
+      for (int l = 0; l < H; ++l) atomicAdd(&gWd[(H + l) * kStride + k], shfl(hj, l) * gpre);
+      atomicAdd(&gWd[(2 * H + 0) * kStride + k], e.x * gpre);
+      atomicAdd(&gWd[(2 * H + 1) * kStride + k], e.y * gpre);
+      atomicAdd(&gWd[(2 * H + 2) * kStride + k], e.z * gpre);
+      atomicAdd(&gWd[(2 * H + 3) * kStride + k], e.w * gpre);
+      // input gradients: lane m gets sum_k Wd[m][k] gpre_k (h_i part) and Wd[H+m][k] gpre_k (h_j)
+      float gi = 0.0f, gj = 0.0f;
+#pragma unroll
+      for (int kk = 0; kk < H; ++kk) {
+        const float gk = shfl(gpre, kk);
+        gi = fmaf(sWd[k * kStride + kk], gk, gi);
+        gj = fmaf(sWd[(H + k) * kStride + kk], gk, gj);
+      }
+      ghi += gi;
+      atomicAdd(gh + (int64_t)j * H + k, gj);
+    }
+    atomicAdd(gh + (int64_t)i * H + k, ghi);
+  }
+  r_gbo = k == 0 ? r_gbo : 0.0f;  // every lane saw the same g; count it once
+  atomicAdd(&gbd[k], r_gbd);
+  atomicAdd(&gwo[k], r_gwo);
+  if (k == 0) atomicAdd(&gbo, r_gbo);
+  __syncthreads();
+  flush_w(gPD + D_WD, gWd, 2 * H + FE);
+  for (int t = threadIdx.x; t < H; t += blockDim.x) {
+    atomicAdd(gPD + D_BD + t, gbd[t]);
+    atomicAdd(gPD + D_WO + t, gwo[t]);
+  }
+  if (threadIdx.x == 0) atomicAdd(gPD + D_BO, gbo);
+}
+
+// one message-passing layer backwards: from gout (w.r.t. hout) to gin (w.r.t. hin, atomic)
+__global__ void __launch_bounds__(kThreads) k_layer_bwd(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                        const float4* __restrict__ xe, const float* __restrict__ PL,
+                                                        const __nv_bfloat16* __restrict__ hin,
+                                                        const __nv_bfloat16* __restrict__ ain,
+                                                        const float* __restrict__ gout, float* __restrict__ gPL,
+                                                        float* __restrict__ gin) {
+  __shared__ float sWm[(H + FE) * kStride], sbm[H], sWu[2 * H * kStride], sbu[H];
+  __shared__ float gWm[(H + FE) * kStride], gWu[2 * H * kStride], gbm[H], gbu[H];
+  load_w(sWm, PL + L_WM, H + FE);
+  load_w(sWu, PL + L_WU, 2 * H);
+  zero_s(gWm, (H + FE) * kStride);
+  zero_s(gWu, 2 * H * kStride);
+  for (int t = threadIdx.x; t < H; t += blockDim.x) {
+    sbm[t] = PL[L_BM + t];
+    sbu[t] = PL[L_BU + t];
+    gbm[t] = 0.0f;
+    gbu[t] = 0.0f;
+  }
+  __syncthreads();
+  const int k = threadIdx.x & 31;
+  float r_gbm = 0.0f, r_gbu = 0.0f;
+  for (int i = warp_id_global(); i < n; i += warps_total()) {
+    const float g = gout[(int64_t)i * H + k];
+    const float hi = bf(hin[(int64_t)i * H + k]);
+    const float a = bf(ain[(int64_t)i * H + k]);
+    const float q = upd_pre(sWu, sbu, hi, a, k);
+    const float gq = q > 0.0f ? g : 0.0f;
+    r_gbu += gq;
+#pragma unroll
+    for (int l = 0; l < H; ++l) atomicAdd(&gWu[l * kStride + k], shfl(hi, l) * gq);
+#pragma unroll
+    for (int l = 0; l < H; ++l) atomicAdd(&gWu[(H + l) * kStride + k], shfl(a, l) * gq);
+    float ghi = g, ga = 0.0f;  // residual path, then the update's input gradients
+#pragma unroll
+    for (int kk = 0; kk < H; ++kk) {
+      const float gk = shfl(gq, kk);
+      ghi = fmaf(sWu[k * kStride + kk], gk, ghi);
+      ga = fmaf(sWu[(H + k) * kStride + kk], gk, ga);
+    }
+    // messages: d a_i / d m_ij = 1
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      const int j = ci[p];
+      if (j == i) continue;
+      const float hj = bf(hin[(int64_t)j * H + k]);
+      const float4 e = xe[p];
+      const float pre = msg_pre(sWm, sbm, hj, e, k);
+      const float gp = pre > 0.0f ? ga : 0.0f;
+      r_gbm += gp;
+#pragma unroll
+      for (int l = 0; l < H; ++l) atomicAdd(&gWm[l * kStride + k], shfl(hj, l) * gp);
+      atomicAdd(&gWm[(H + 0) * kStride + k], e.x * gp);
+      atomicAdd(&gWm[(H + 1) * kStride + k], e.y * gp);
+      atomicAdd(&gWm[(H + 2) * kStride + k], e.z * gp);
+      atomicAdd(&gWm[(H + 3) * kStride + k], e.w * gp);
+      float gj = 0.0f;
+#pragma unroll
+      for (int kk = 0; kk < H; ++kk) gj = fmaf(sWm[k * kStride + kk], shfl(gp, kk), gj);
+      atomicAdd(gin + (int64_t)j * H + k, gj);
+    }
+    atomicAdd(gin + (int64_t)i * H + k, ghi);
+  }
+  atomicAdd(&gbm[k], r_gbm);
+  atomicAdd(&gbu[k], r_gbu);
+  __syncthreads();
+  flush_w(gPL + L_WM, gWm, H + FE);
+  flush_w(gPL + L_WU, gWu, 2 * H);
+  for (int t = threadIdx.x; t < H; t += blockDim.x) {
+    atomicAdd(gPL + L_BM + t, gbm[t]);
+    atomicAdd(gPL + L_BU + t, gbu[t]);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_encode_bwd(int n, const float4* __restrict__ xn, const float* __restrict__ P,
+                                                         const float* __restrict__ g0, float* __restrict__ gP) {
+  __shared__ float gW[FN * H], gb[H];
+  for (int t = threadIdx.x; t < FN * H; t += blockDim.x) gW[t] = 0.0f;
+  for (int t = threadIdx.x; t < H; t += blockDim.x) gb[t] = 0.0f;
+  __syncthreads();
+  const int k = threadIdx.x & 31;
+  const float w0 = P[P_W0 + 0 * H + k], w1 = P[P_W0 + 1 * H + k], w2 = P[P_W0 + 2 * H + k],
+              w3 = P[P_W0 + 3 * H + k], b = P[P_B0 + k];
+  float r[FN + 1] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  for (int i = warp_id_global(); i < n; i += warps_total()) {
+    const float4 x = xn[i];
+    float pre = b;
+    pre = fmaf(w0, x.x, pre);
+    pre = fmaf(w1, x.y, pre);
+    pre = fmaf(w2, x.z, pre);
+    pre = fmaf(w3, x.w, pre);
+    const float gp = pre > 0.0f ? g0[(int64_t)i * H + k] : 0.0f;
+    r[0] = fmaf(x.x, gp, r[0]);
+    r[1] = fmaf(x.y, gp, r[1]);
+    r[2] = fmaf(x.z, gp, r[2]);
+    r[3] = fmaf(x.w, gp, r[3]);
+    r[4] += gp;
+  }
+#pragma unroll
+  for (int l = 0; l < FN; ++l) atomicAdd(&gW[l * H + k], r[l]);
+  atomicAdd(&gb[k], r[4]);
+  __syncthreads();
+  for (int t = threadIdx.x; t < FN * H; t += blockDim.x) atomicAdd(gP + P_W0 + t, gW[t]);
+  for (int t = threadIdx.x; t < H; t += blockDim.x) atomicAdd(gP + P_B0 + t, gb[t]);
+}
+
+// ---- loss of the preconditioned operator ------------------------------------------------------
+//   loss = mean_s  sum_{i in s} ||(M'^-1 A W - W)_i||^2 / sum_{i in s} ||W_i||^2,  M' = L'U'
+// with its gradient: t = L'^-1 A W, z = U'^-1 t, g = 2 (z - W) / (nsys ||W_s||^2),
+// lambda = U'^-T g, mu = L'^-T lambda, d loss / d U'_ij = -lambda_i . z_j (j >= i),
+// d loss / d L'_ij = -mu_i . t_j (j < i).  The four solves run on the factor's level orders
+// (the transposed solves read U'_ji, L'_ji through the position of (j, i): the pattern must be
+// structurally symmetric), K <= 4 right-hand sides per row, binary32, completion carried by the
+// values (sentinel fill, strong relaxed stores and polls), static schedule over co-resident warps.
+constexpr unsigned kSentF = 0xFFFFFFFFu;
+constexpr long long kWaitCyclesG = 1ll << 31;  // ~1 s: bound of every wait
+__device__ __forceinline__ float ldr(const float* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return __uint_as_float(v);
+}
+__device__ __forceinline__ void str(float* p, float x) {
+  unsigned v = __float_as_uint(x);
+  if (v == kSentF) v = 0x7FC00000u;
+  asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__global__ void k_fillf(int64_t m, float* __restrict__ a) {
+  const float s = __uint_as_float(kSentF);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) a[k] = s;
+}
+// mode 0: L' x = b (unit lower)        entries j < i, value f'_p
+// mode 1: U' x = b                     entries j > i, value f'_p, divided by f'_ii
+// mode 2: U'^T x = b                   entries j < i, value f'_(j,i), divided by f'_ii
+// mode 3: L'^T x = b (unit upper)      entries j > i, value f'_(j,i)
+template <int K>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tri(int n, const int* __restrict__ rp, const int* __restrict__ ci, const int* __restrict__ diag,
+          const int* __restrict__ tpos, const void* fac, int prec, const float* __restrict__ o,
+          const int* __restrict__ perm, const int* __restrict__ nchunks, int mode, const float* __restrict__ b,
+          float* __restrict__ x, int* __restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  const int G = gridDim.x * (blockDim.x >> 5);
+  const int g = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+  const int nch = *nchunks;
+  for (int chunk = g; chunk < nch; chunk += G) {
+    const int i = perm[(chunk << 5) + lane];
+    bool timeout = false;
+    if (i >= 0) {
+      float acc[K];
+#pragma unroll
+      for (int c = 0; c < K; ++c) acc[c] = b[(int64_t)i * K + c];
+      const bool low = (mode == 0 || mode == 2);
+      const int p0 = low ? rp[i] : diag[i] + 1, p1 = low ? diag[i] : rp[i + 1];
+      const long long t0 = clock64();
+      for (int p = p0; p < p1 && !timeout; ++p) {
+        const int j = ci[p];
+        const int q = mode >= 2 ? tpos[p] : p;
+        const float v = corrected(fac_at(fac, prec, q), o[q]);
+        float xj[K];
+        for (;;) {
+          bool ok = true;
+#pragma unroll
+          for (int c = 0; c < K; ++c) {
+            xj[c] = ldr(x + (int64_t)j * K + c);
+            ok = ok && __float_as_uint(xj[c]) != kSentF;
+          }
+          if (ok) break;
+          if (clock64() - t0 > kWaitCyclesG || ldr((const float*)err) != 0.0f) { timeout = true; break; }
+        }
+#pragma unroll
+        for (int c = 0; c < K; ++c) acc[c] = fmaf(-v, xj[c], acc[c]);
+      }
+      if (!timeout) {
+        if (mode == 1 || mode == 2) {
+          const int d = diag[i];
+          const float dv = corrected(fac_at(fac, prec, d), o[d]);
+#pragma unroll
+          for (int c = 0; c < K; ++c) acc[c] = acc[c] / dv;
+        }
+#pragma unroll
+        for (int c = 0; c < K; ++c) str(x + (int64_t)i * K + c, acc[c]);
+      }
+    }
+    if (__any_sync(0xffffffffu, timeout)) {
+      if (lane == 0) atomicExch(err, 1);
+      return;
+    }
+  }
+}
+__global__ void k_mirror_check(int nnz, const int* __restrict__ tpos, int* __restrict__ miss) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += gridDim.x * blockDim.x)
+    if (tpos[p] < 0) atomicExch(miss, 1);
+}
+// y = A W (binary32, K columns)
+__global__ void k_spmm_f(int n, int K, const int* __restrict__ rp, const int* __restrict__ ci,
+                         const double* __restrict__ a, const float* __restrict__ W, float* __restrict__ y) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)n * K; t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / K), c = (int)(t % K);
+    float s = 0.0f;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) s = fmaf((float)a[p], W[(int64_t)ci[p] * K + c], s);
+    y[t] = s;
+  }
+}
+// residual r = z - W, per-system sums (sum r^2, sum W^2), and g = 2 r / (nsys ||W_s||^2) after
+__global__ void k_pres(int n, int K, const float* __restrict__ z, const float* __restrict__ W,
+                       const int* __restrict__ sysid, float* __restrict__ sums) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)n * K; t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / K);
+    const float r = z[t] - W[t];
+    const int s = sysid ? sysid[i] : 0;
+    atomicAdd(sums + 2 * s, r * r);
+    atomicAdd(sums + 2 * s + 1, W[t] * W[t]);
+  }
+}
+__global__ void k_pgrad_in(int n, int K, int nsys, const float* __restrict__ z, const float* __restrict__ W,
+                           const int* __restrict__ sysid, const float* __restrict__ sums, float* __restrict__ gz) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)n * K; t += (int64_t)gridDim.x * blockDim.x) {
+    const int s = sysid ? sysid[(int)(t / K)] : 0;
+    const float den = sums[2 * s + 1];
+    gz[t] = den > 0.0f ? 2.0f * (z[t] - W[t]) / ((float)nsys * den) : 0.0f;
+  }
+}
+// d loss / d o for every stored entry
+__global__ void k_pgrad_o(int n, int K, const int* __restrict__ rp, const int* __restrict__ ci,
+                          const int* __restrict__ diag, const void* fac, int prec, const float* __restrict__ o,
+                          const float* __restrict__ t, const float* __restrict__ z, const float* __restrict__ lam,
+                          const float* __restrict__ mu, float* __restrict__ go) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      const int j = ci[p];
+      const bool low = p < diag[i];
+      const float* lhs = low ? mu : lam;
+      const float* rhs = low ? t : z;
+      float gf = 0.0f;
+      for (int c = 0; c < K; ++c) gf = fmaf(lhs[(int64_t)i * K + c], rhs[(int64_t)j * K + c], gf);
+      const float f = fac_at(fac, prec, p), th = tanhf(o[p]);
+      go[p] = -gf * f * 0.5f * (1.0f - th * th);
+    }
+  }
+}
+
+__global__ void k_adam(int m, float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m1,
+                       float* __restrict__ m2, float lr, float b1, float b2, float eps, float c1, float c2) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x) {
+    const float gt = g[t];
+    const float a = b1 * m1[t] + (1.0f - b1) * gt;
+    const float b = b2 * m2[t] + (1.0f - b2) * gt * gt;
+    m1[t] = a;
+    m2[t] = b;
+    p[t] -= lr * (a / c1) / (sqrtf(b / c2) + eps);
+  }
+}
+
+template <typename T>
+__global__ void k_correct(int64_t nnz, T* __restrict__ fac, const float* __restrict__ o);
+template <>
+__global__ void k_correct<double>(int64_t nnz, double* __restrict__ fac, const float* __restrict__ o) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
+    fac[p] = fac[p] * (1.0 + 0.5 * (double)tanhf(o[p]));
+}
+template <>
+__global__ void k_correct<float>(int64_t nnz, float* __restrict__ fac, const float* __restrict__ o) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
+    fac[p] = corrected(fac[p], o[p]);
+}
+template <>
+__global__ void k_correct<uint16_t>(int64_t nnz, uint16_t* __restrict__ fac, const float* __restrict__ o) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+    const float v = corrected(__uint_as_float(((unsigned)fac[p]) << 16), o[p]);
+    fac[p] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+  }
+}
+
+}  // namespace gnn
+}  // namespace mpk
+
+// ---------------------------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------------------------
+namespace mpk {
+int refresh_factor(mpk_ilu* M, cudaStream_t s);  // ilu.cu: repack the triangles after new values
+namespace gnn {
+
+struct Work {  // views into the caller's workspace
+  int* tpos;
+  float4* xn;
+  float4* xe;
+  __nv_bfloat16* h;  // (NL + 1) * n * H
+  __nv_bfloat16* a;  // NL * n * H
+  float* gh;         // 2 * n * H
+  float* u;          // n * K (and aw, r, gu after it)
+  float* aw;
+  float* r;
+  float* gu;
+  float* e5;         // n * K (preconditioned loss)
+  float* e6;         // n * K
+  float* sums;       // 2 * nsys
+  int* sysid;        // n
+  int* flags;        // 4 ints: [0] wait ran out, [1] an entry without its mirror
+};
+static size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
+static size_t work_bytes(int n, int nnz, int K, int nsys) {
+  return al(sizeof(int) * (size_t)nnz) + al(sizeof(float4) * (size_t)n) + al(sizeof(float4) * (size_t)nnz) +
+         al(sizeof(__nv_bfloat16) * (size_t)(NL + 1) * n * H) + al(sizeof(__nv_bfloat16) * (size_t)NL * n * H) +
+         al(sizeof(float) * 2 * (size_t)n * H) + 6 * al(sizeof(float) * (size_t)n * K) + al(sizeof(float) * 2 * (size_t)nsys) +
+         al(sizeof(int) * (size_t)n) + al(sizeof(int) * 4) + 256;
+}
+static Work carve(void* base, int n, int nnz, int K, int nsys) {
+  char* p = (char*)(((uintptr_t)base + 255) & ~(uintptr_t)255);
+  Work w;
+  w.tpos = (int*)p; p += al(sizeof(int) * (size_t)nnz);
+  w.xn = (float4*)p; p += al(sizeof(float4) * (size_t)n);
+  w.xe = (float4*)p; p += al(sizeof(float4) * (size_t)nnz);
+  w.h = (__nv_bfloat16*)p; p += al(sizeof(__nv_bfloat16) * (size_t)(NL + 1) * n * H);
+  w.a = (__nv_bfloat16*)p; p += al(sizeof(__nv_bfloat16) * (size_t)NL * n * H);
+  w.gh = (float*)p; p += al(sizeof(float) * 2 * (size_t)n * H);
+  w.u = (float*)p; p += al(sizeof(float) * (size_t)n * K);
+  w.aw = (float*)p; p += al(sizeof(float) * (size_t)n * K);
+  w.r = (float*)p; p += al(sizeof(float) * (size_t)n * K);
+  w.gu = (float*)p; p += al(sizeof(float) * (size_t)n * K);
+  w.e5 = (float*)p; p += al(sizeof(float) * (size_t)n * K);
+  w.e6 = (float*)p; p += al(sizeof(float) * (size_t)n * K);
+  w.sums = (float*)p; p += al(sizeof(float) * 2 * (size_t)nsys);
+  w.sysid = (int*)p; p += al(sizeof(int) * (size_t)n);
+  w.flags = (int*)p;
+  return w;
+}
+constexpr int kMaxProbes = 16;
+
+static int check(const mpk_csr* A, const mpk_ilu* M, const void* work, size_t bytes, int K, int nsys) {
+  if (A == nullptr || M == nullptr || work == nullptr) return fail(MPK_INVALID_ARG, "null argument");
+  if (A->is_complex) return fail(MPK_INVALID_ARG, "the learned correction is defined for real matrices");
+  if (M->n != A->n || M->nnz != A->nnz || M->cp != 1) return fail(MPK_INVALID_ARG, "factor does not match the matrix");
+  if (K < 1 || K > kMaxProbes || nsys < 1) return fail(MPK_INVALID_ARG, "nprobe must be 1..16, nsys >= 1");
+  if (bytes < work_bytes(A->n, A->nnz, K, nsys)) return fail(MPK_INVALID_ARG, "workspace too small");
+  return MPK_OK;
+}
+static int grid_for(int n) {
+  const int g = (n + kBlock - 1) / kBlock, cap = sm_count() * 8;
+  return g < 1 ? 1 : (g > cap ? cap : g);
+}
+static int blocks_for(int warps_needed) {
+  const int b = (warps_needed + kThreads / 32 - 1) / (kThreads / 32);
+  const int cap = sm_count() * 8;
+  return b < 1 ? 1 : (b > cap ? cap : b);
+}
+__global__ void k_sysid(int n, int nsys, const int* __restrict__ roff, int* __restrict__ sysid) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int lo = 0, hi = nsys;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (roff[mid] <= i) lo = mid;
+      else hi = mid;
+    }
+    sysid[i] = lo;
+  }
+}
+
+}  // namespace gnn
+}  // namespace mpk
+
+using namespace mpk;
+using namespace mpk::gnn;
+
+extern "C" int mpk_gnn_nparams(void) { return NPARAMS; }
+
+extern "C" size_t mpk_gnn_workspace_bytes(int n, int nnz, int nprobe, int nsys) {
+  if (n < 1 || nnz < 0 || nprobe < 1 || nsys < 1) return 0;
+  return work_bytes(n, nnz, nprobe, nsys);
+}
+
+extern "C" int mpk_gnn_forward(const mpk_csr* A, const mpk_ilu* M, const float* params, float* o, void* work,
+                               size_t work_bytes_, void* stream) {
+  int st = check(A, M, work, work_bytes_, 1, 1);
+  if (st != MPK_OK) return st;
+  if (params == nullptr || o == nullptr) return fail(MPK_INVALID_ARG, "null parameters or output");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = A->n;
+  Work w = carve(work, n, A->nnz, 1, 1);
+  count_launch(3 + NL);
+  k_tpos<<<grid_for(n), kBlock, 0, s>>>(n, M->rp, M->ci, w.tpos);
+  k_features<<<grid_for(n), kBlock, 0, s>>>(n, M->rp, M->ci, A->val, M->fac, M->prec, w.tpos, M->diag, w.xn, w.xe);
+  k_encode<<<blocks_for(n), kThreads, 0, s>>>(n, w.xn, params, w.h);
+  for (int L = 0; L < NL; ++L)
+    k_layer<<<blocks_for(n), kThreads, 0, s>>>(n, M->rp, M->ci, w.xe, params + P_L0 + L * L_SIZE,
+                                               w.h + (size_t)L * n * H, w.a + (size_t)L * n * H,
+                                               w.h + (size_t)(L + 1) * n * H);
+  count_launch();
+  k_decode<<<blocks_for(n), kThreads, 0, s>>>(n, M->rp, M->ci, w.xe, params + P_DEC, w.h + (size_t)NL * n * H, o);
+  MPK_CUDA(cudaGetLastError());
+  return MPK_OK;
+}
+
+extern "C" int mpk_gnn_loss(const mpk_csr* A, const mpk_ilu* M, const float* o, int nprobe, const float* probes,
+                            int nsys, const int32_t* sys_rows_dev, float* loss, float* g_o, void* work,
+                            size_t work_bytes_, void* stream) {
+  int st = check(A, M, work, work_bytes_, nprobe, nsys);
+  if (st != MPK_OK) return st;
+  if (o == nullptr || probes == nullptr || loss == nullptr || g_o == nullptr || (nsys > 1 && sys_rows_dev == nullptr))
+    return fail(MPK_INVALID_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = A->n, K = nprobe;
+  Work w = carve(work, n, A->nnz, K, nsys);
+  const int* sysid = nullptr;
+  if (nsys > 1) {
+    count_launch();
+    k_sysid<<<grid_for(n), kBlock, 0, s>>>(n, nsys, sys_rows_dev, w.sysid);
+    sysid = w.sysid;
+  }
+  MPK_CUDA(cudaMemsetAsync(w.sums, 0, sizeof(float) * 2 * (size_t)nsys, s));
+  MPK_CUDA(cudaMemsetAsync(w.gu, 0, sizeof(float) * (size_t)n * K, s));
+  const int gk = grid_for((int)((int64_t)n * K < INT_MAX ? (int64_t)n * K : INT_MAX));
+  count_launch(5);
+  k_loss_u<<<gk, kBlock, 0, s>>>(n, K, M->rp, M->ci, A->val, M->fac, M->prec, M->diag, o, probes, w.u, w.aw);
+  k_loss_r<<<gk, kBlock, 0, s>>>(n, K, M->rp, M->ci, M->fac, M->prec, M->diag, o, w.u, w.aw, w.r, sysid, w.sums);
+  k_loss_total<<<1, 1024, 0, s>>>(nsys, w.sums, loss);
+  k_loss_grad_lower<<<grid_for(n), kBlock, 0, s>>>(n, K, nsys, M->rp, M->ci, M->fac, M->prec, M->diag, o, w.u, w.r,
+                                                   sysid, w.sums, w.gu, g_o);
+  k_loss_grad_upper<<<grid_for(n), kBlock, 0, s>>>(n, K, M->rp, M->ci, M->fac, M->prec, M->diag, o, probes, w.gu, g_o);
+  MPK_CUDA(cudaGetLastError());
+  return MPK_OK;
+}
+
+extern "C" int mpk_gnn_backward(const mpk_csr* A, const mpk_ilu* M, const float* params, const float* g_o,
+                                float* g_params, void* work, size_t work_bytes_, void* stream) {
+  int st = check(A, M, work, work_bytes_, 1, 1);
+  if (st != MPK_OK) return st;
+  if (params == nullptr || g_o == nullptr || g_params == nullptr) return fail(MPK_INVALID_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = A->n;
+  Work w = carve(work, n, A->nnz, 1, 1);
+  const size_t nh = (size_t)n * H;
+  MPK_CUDA(cudaMemsetAsync(g_params, 0, sizeof(float) * NPARAMS, s));
+  float* g_cur = w.gh;
+  float* g_nxt = w.gh + nh;
+  MPK_CUDA(cudaMemsetAsync(g_cur, 0, sizeof(float) * nh, s));
+  count_launch();
+  k_decode_bwd<<<blocks_for(n), kThreads, 0, s>>>(n, M->rp, M->ci, w.xe, params + P_DEC, w.h + (size_t)NL * nh, g_o,
+                                                  g_params + P_DEC, g_cur);
+  for (int L = NL - 1; L >= 0; --L) {
+    MPK_CUDA(cudaMemsetAsync(g_nxt, 0, sizeof(float) * nh, s));
+    count_launch();
+    k_layer_bwd<<<blocks_for(n), kThreads, 0, s>>>(n, M->rp, M->ci, w.xe, params + P_L0 + L * L_SIZE, w.h + (size_t)L * nh,
+                                                   w.a + (size_t)L * nh, g_cur, g_params + P_L0 + L * L_SIZE, g_nxt);
+    float* t = g_cur;
+    g_cur = g_nxt;
+    g_nxt = t;
+  }
+  count_launch();
+  k_encode_bwd<<<blocks_for(n), kThreads, 0, s>>>(n, w.xn, params, g_cur, g_params);
+  MPK_CUDA(cudaGetLastError());
+  return MPK_OK;
+}
+
+extern "C" int mpk_gnn_adam(int nparams, float* params, const float* grad, float* m, float* v, float lr, int step,
+                            void* stream) {
+  if (nparams < 1 || params == nullptr || grad == nullptr || m == nullptr || v == nullptr || step < 1)
+    return fail(MPK_INVALID_ARG, "bad argument");
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
+  count_launch();
+  k_adam<<<grid_for(nparams), kBlock, 0, (cudaStream_t)stream>>>(nparams, params, grad, m, v, lr, b1, b2, eps, c1, c2);
+  MPK_CUDA(cudaGetLastError());
+  return MPK_OK;
+}
+
+extern "C" int mpk_ilu0_correct(mpk_ilu* M, const float* o, void* stream) {
+  if (M == nullptr || o == nullptr) return fail(MPK_INVALID_ARG, "null argument");
+  if (M->cp != 1) return fail(MPK_INVALID_ARG, "the learned correction is defined for real matrices");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t nnz = M->nnz;
+  count_launch();
+  if (M->prec == MPK_ILU_FP64) k_correct<double><<<grid_for(M->n), kBlock, 0, s>>>(nnz, (double*)M->fac, o);
+  else if (M->prec == MPK_ILU_FP32) k_correct<float><<<grid_for(M->n), kBlock, 0, s>>>(nnz, (float*)M->fac, o);
+  else k_correct<uint16_t><<<grid_for(M->n), kBlock, 0, s>>>(nnz, (uint16_t*)M->fac, o);
+  MPK_CUDA(cudaGetLastError());
+  return refresh_factor(M, s);
+}
+
+extern "C" int mpk_gnn_loss_precond(const mpk_csr* A, const mpk_ilu* M, const float* o, int nprobe,
+                                    const float* probes, int nsys, const int32_t* sys_rows_dev, float* loss, float* g_o,
+                                    void* work, size_t work_bytes_, void* stream) {
+  int st = check(A, M, work, work_bytes_, nprobe, nsys);
+  if (st != MPK_OK) return st;
+  if (nprobe > 4) return fail(MPK_INVALID_ARG, "the preconditioned loss takes at most 4 probes");
+  if (o == nullptr || probes == nullptr || loss == nullptr || g_o == nullptr || (nsys > 1 && sys_rows_dev == nullptr))
+    return fail(MPK_INVALID_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = A->n, K = nprobe, nnz = A->nnz;
+  Work w = carve(work, n, nnz, K, nsys);
+  const int64_t nk = (int64_t)n * K;
+  const int gk = grid_for((int)(nk < INT_MAX ? nk : INT_MAX));
+  // transpose positions; every off-diagonal entry must have its mirror (checked before any solve)
+  int* err = w.flags;
+  MPK_CUDA(cudaMemsetAsync(w.flags, 0, sizeof(int) * 2, s));
+  count_launch(2);
+  k_tpos<<<grid_for(n), kBlock, 0, s>>>(n, M->rp, M->ci, w.tpos);
+  k_mirror_check<<<grid_for(nnz), kBlock, 0, s>>>(nnz, w.tpos, w.flags + 1);
+  {
+    int miss = 0;
+    MPK_CUDA(cudaMemcpyAsync(&miss, w.flags + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MPK_CUDA(cudaStreamSynchronize(s));
+    if (miss != 0) return fail(MPK_INVALID_ARG, "the preconditioned loss needs a structurally symmetric pattern");
+  }
+  const int* sysid = nullptr;
+  if (nsys > 1) {
+    count_launch();
+    k_sysid<<<grid_for(n), kBlock, 0, s>>>(n, nsys, sys_rows_dev, w.sysid);
+    sysid = w.sysid;
+  }
+  float* y = w.u;
+  float* t = w.aw;
+  float* z = w.r;
+  float* gz = w.gu;
+  float* lam = w.e5;
+  float* mu = w.e6;
+  MPK_CUDA(cudaMemsetAsync(w.sums, 0, sizeof(float) * 2 * (size_t)nsys, s));
+  const LevelOrder lo = level_view(M->lvbuf[0], n, M->nlevels[0]);
+  const LevelOrder up = level_view(M->lvbuf[1], n, M->nlevels[1]);
+  auto tri = [&](int mode, const LevelOrder& L, const float* b, float* x) -> int {
+    count_launch(2);
+    k_fillf<<<gk, kBlock, 0, s>>>(nk, x);
+    const int* tp = w.tpos;
+    const void* fac = M->fac;
+    int prec = M->prec;
+    const int* rp = M->rp;
+    const int* ci = M->ci;
+    const int* dg = M->diag;
+    int nn = n;
+    void* args[] = {(void*)&nn, (void*)&rp, (void*)&ci, (void*)&dg, (void*)&tp, (void*)&fac, (void*)&prec,
+                    (void*)&o, (void*)&L.perm, (void*)&L.nchunks, (void*)&mode, (void*)&b, (void*)&x, (void*)&err};
+    const void* fn = K == 1 ? (const void*)k_tri<1> : K == 2 ? (const void*)k_tri<2> : K == 3 ? (const void*)k_tri<3>
+                                                                                          : (const void*)k_tri<4>;
+    return cudaLaunchCooperativeKernel(fn, dim3(sm_count()), dim3(kThreads), args, 0, s) == cudaSuccess ? MPK_OK
+                                                                                                       : MPK_CUDA_ERROR;
+  };
+  count_launch();
+  k_spmm_f<<<gk, kBlock, 0, s>>>(n, K, M->rp, M->ci, A->val, probes, y);
+  if ((st = tri(0, lo, y, t)) != MPK_OK) return fail(st, "triangular solve launch failed");
+  if ((st = tri(1, up, t, z)) != MPK_OK) return fail(st, "triangular solve launch failed");
+  count_launch(3);
+  k_pres<<<gk, kBlock, 0, s>>>(n, K, z, probes, sysid, w.sums);
+  k_loss_total<<<1, 1024, 0, s>>>(nsys, w.sums, loss);
+  k_pgrad_in<<<gk, kBlock, 0, s>>>(n, K, nsys, z, probes, sysid, w.sums, gz);
+  if ((st = tri(2, lo, gz, lam)) != MPK_OK) return fail(st, "triangular solve launch failed");
+  if ((st = tri(3, up, lam, mu)) != MPK_OK) return fail(st, "triangular solve launch failed");
+  count_launch();
+  k_pgrad_o<<<grid_for(n), kBlock, 0, s>>>(n, K, M->rp, M->ci, M->diag, M->fac, M->prec, o, t, z, lam, mu, g_o);
+  MPK_CUDA(cudaGetLastError());
+  int herr = 0;
+  MPK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MPK_CUDA(cudaStreamSynchronize(s));
+  if (herr != 0) return fail(MPK_TIMEOUT, "a bounded wait ran out in a training solve (pattern not symmetric?)");
+  return MPK_OK;
+}

@@ -649,6 +649,25 @@ int precond_apply(const mpk_ilu* M, const Ops* o, bool trans, const double* r, d
   return MPK_OK;
 }
 
+// New factor values on the same pattern (after a learned correction): repack the triangles and
+// drop the conjugate transpose (rebuilt on its next use).
+int refresh_factor(mpk_ilu* M, cudaStream_t s) {
+  MPK_CUDA(cudaStreamSynchronize(s));
+  for (int t = 0; t < 4; ++t) {
+    if (M->sellbuf[t] != nullptr) cudaFree(M->sellbuf[t]);
+    M->sellbuf[t] = nullptr;
+    M->sell[t] = SellTri();
+  }
+  void* tp[] = {M->rpT, M->ciT, M->diagT, M->facT, M->lvbuf[2], M->lvbuf[3]};
+  for (void* p : tp)
+    if (p != nullptr) cudaFree(p);
+  M->rpT = M->ciT = M->diagT = nullptr;
+  M->facT = nullptr;
+  M->lvbuf[2] = M->lvbuf[3] = nullptr;
+  M->nlevels[2] = M->nlevels[3] = 0;
+  return build_sells(M, 0, M->rp, M->ci, M->diag, M->fac, s);
+}
+
 // ---- substitution autotuner ---------------------------------------------------------------------
 int read_ctl_err(const mpk_ilu* M, cudaStream_t s);
 struct TrsvTune {

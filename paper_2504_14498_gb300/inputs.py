@@ -315,3 +315,125 @@ def block_diagonal(systems):
         val[eoff[s] * c:eoff[s + 1] * c] = v
     rp[-1] = eoff[-1]
     return (int(roff[-1]), rp, ci, val), roff
+
+
+_PATTERN_2D = {}
+
+
+def _pattern2d(m):
+    """5-point pattern of an m x m grid (natural ordering) and, per slot (-m, -1, centre, +1, +m),
+    the CSR position of each row's entry (-1 where the neighbour does not exist)."""
+    if m not in _PATTERN_2D:
+        n = m * m
+        idx = np.arange(n)
+        ix, iy = idx % m, idx // m
+        cols = np.full((n, 5), -1, dtype=np.int64)
+        cols[iy > 0, 0] = idx[iy > 0] - m
+        cols[ix > 0, 1] = idx[ix > 0] - 1
+        cols[:, 2] = idx
+        cols[ix < m - 1, 3] = idx[ix < m - 1] + 1
+        cols[iy < m - 1, 4] = idx[iy < m - 1] + m
+        mask = cols >= 0
+        rp = np.zeros(n + 1, dtype=np.int64)
+        np.cumsum(mask.sum(axis=1), out=rp[1:])
+        slotpos = np.full((n, 5), -1, dtype=np.int64)
+        slotpos[mask] = np.arange(int(rp[-1]))
+        _PATTERN_2D[m] = (rp.astype(np.int32), cols[mask].astype(np.int32), slotpos)
+    return _PATTERN_2D[m]
+
+
+def convdiff2d_random(m, seed, sigma=1.0, pe_range=(1.0, 100.0)):
+    """Learned-preconditioner workload: 5-point first-order upwind convection-diffusion on an
+    m x m grid with a node-wise log-normal diffusivity k = exp(sigma g), g ~ N(0,1) (face value =
+    harmonic mean of the two nodes, the node's own value at a boundary face), a random flow
+    direction theta ~ U(0, 2 pi) and one cell Peclet number Pe ~ U(pe_lo, pe_hi) measured against
+    k = 1 (h v_d = 2 Pe (cos theta, sin theta)_d); upwind side chosen by the sign of v_d; scaled by
+    h^2, natural ordering.  Returns (n, row_ptr, col, val)."""
+    rng = np.random.default_rng(seed)
+    n = m * m
+    kap = np.exp(sigma * rng.standard_normal(n))
+    theta = float(rng.uniform(0.0, 2.0 * math.pi))
+    pe = float(rng.uniform(*pe_range))
+    hv = (2.0 * pe * math.cos(theta), 2.0 * pe * math.sin(theta))
+    rp, ci, slotpos = _pattern2d(m)
+    kg = kap.reshape(m, m)  # [y, x]
+    val = np.zeros(len(ci))
+    diag = np.zeros((m, m))
+    # axis 0: x (stride 1, slots 1 / 3), axis 1: y (stride m, slots 0 / 4)
+    for axis, (slot_lo, slot_hi) in enumerate(((1, 3), (0, 4))):
+        k = kg if axis == 0 else kg.T  # k[.., c] runs along the axis
+        face = 2.0 / (1.0 / k[:, 1:] + 1.0 / k[:, :-1])  # between c and c+1
+        k_lo = k.copy()
+        k_lo[:, 1:] = face
+        k_hi = k.copy()
+        k_hi[:, :-1] = face
+        if axis == 1:
+            k_lo, k_hi = k_lo.T, k_hi.T
+        up_lo, up_hi = max(hv[axis], 0.0), max(-hv[axis], 0.0)
+        diag += k_lo + k_hi + up_lo + up_hi
+        lo = slotpos[:, slot_lo]
+        hi = slotpos[:, slot_hi]
+        klo, khi = k_lo.reshape(-1), k_hi.reshape(-1)
+        val[lo[lo >= 0]] = -klo[lo >= 0] - up_lo
+        val[hi[hi >= 0]] = -khi[hi >= 0] - up_hi
+    val[slotpos[:, 2]] = diag.reshape(-1)
+    return (n, rp.copy(), ci.copy(), val)
+
+
+def probe_vectors(n, k, seed):
+    """k random probe vectors with N(0,1) entries (binary32), n x k row-major: the learned
+    preconditioner's training losses are estimated over such vectors."""
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((n, k)).astype(np.float32)
+
+
+def smooth_probes(m, nsys, k, seed, modes=4):
+    """k smooth probe vectors per m x m grid system, for nsys stacked systems (binary32,
+    (nsys m^2) x k row-major): sums of the grid's lowest sine modes sin(a pi x) sin(b pi y),
+    a, b = 1..modes, with N(0,1) / (a b) coefficients."""
+    rng = np.random.default_rng(seed)
+    x = (np.arange(m) + 1.0) / (m + 1.0)
+    S = np.stack([np.sin(a * np.pi * x) for a in range(1, modes + 1)])  # [modes, m]
+    out = np.empty((nsys, m * m, k), dtype=np.float32)
+    w = 1.0 / np.outer(np.arange(1, modes + 1), np.arange(1, modes + 1))
+    for s_ in range(nsys):
+        for c in range(k):
+            C = rng.standard_normal((modes, modes)) * w  # C[b, a]: y mode b, x mode a
+            out[s_, :, c] = (S.T @ C @ S).reshape(-1)  # [y, x], natural ordering y * m + x
+    return out.reshape(nsys * m * m, k)
+
+
+def training_probes(m, nsys, k, seed):
+    """Probe vectors of the learned correction's training: half smooth (smooth_probes), half
+    N(0,1) (probe_vectors)."""
+    ks = k // 2
+    sm = smooth_probes(m, nsys, ks, seed)
+    rn = probe_vectors(nsys * m * m, k - ks, seed + 1)
+    return np.ascontiguousarray(np.concatenate([sm, rn], axis=1), dtype=np.float32)
+
+
+GNN_NPARAMS = 12193  # parameter count of the learned correction's network (layout in csrc/gnn.cu)
+
+
+def gnn_init_params(seed, hidden=32, node_in=4, edge_in=4, layers=3):
+    """Seeded initial parameters of the learned-correction network, in its parameter layout
+    (encoder W0 [node_in][hidden], b0; per layer Wm [hidden+edge_in][hidden], bm, Wu [2 hidden]
+    [hidden], bu; decoder Wd [2 hidden+edge_in][hidden], bd, wo, bo): weights uniform in
+    +-1/sqrt(fan_in), biases zero, output layer (wo, bo) zero so that the untrained network's
+    output is zero (the plain ILU(0) factor)."""
+    H = hidden
+    rng = np.random.default_rng(seed)
+    P = np.zeros(GNN_NPARAMS, dtype=np.float32)
+
+    def fill(off, fan_in, cnt):
+        P[off:off + cnt] = rng.uniform(-1.0, 1.0, cnt) / np.sqrt(fan_in)
+
+    fill(0, node_in, node_in * H)
+    base = node_in * H + H
+    lsize = (H + edge_in) * H + H + 2 * H * H + H
+    for L in range(layers):
+        b = base + L * lsize
+        fill(b, H + edge_in, (H + edge_in) * H)
+        fill(b + (H + edge_in) * H + H, 2 * H, 2 * H * H)
+    fill(base + layers * lsize, 2 * H + edge_in, (2 * H + edge_in) * H)
+    return P
