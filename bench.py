@@ -134,6 +134,16 @@ def dist_setup():
     return world, rank, local
 
 
+def reduce_max(x, device):
+    """Largest value over the ranks (the job's time is its slowest replica's)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload_config(m, prec):
     n = m ** 3
     nnz = 7 * n - 6 * m * m
@@ -248,11 +258,7 @@ def run_mpk(args):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
     if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = reduce_max(ms, "cuda")
     last = outs[-1]
 
     extra = {"iters": last["iters"], "status": last["status"], "relres_true": last["relres_true"],

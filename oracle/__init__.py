@@ -23,10 +23,10 @@ from . import build as _build
 
 _lib = None
 
-ILU_NONE, ILU_FP64, ILU_FP32, ILU_BF16 = -1, 0, 1, 2
+ILU_NONE, ILU_FP64, ILU_FP32, ILU_BF16, ILU_MP = -1, 0, 1, 2, 3
 BICG, CGS, BICGSTAB, GPBICG = 0, 1, 2, 3
 METHODS = {"bicg": BICG, "cgs": CGS, "bicgstab": BICGSTAB, "gpbicg": GPBICG}
-ILUS = {"none": ILU_NONE, "fp64": ILU_FP64, "fp32": ILU_FP32, "bf16": ILU_BF16}
+ILUS = {"none": ILU_NONE, "fp64": ILU_FP64, "fp32": ILU_FP32, "bf16": ILU_BF16, "mp": ILU_MP}
 STATUS = {0: "OK", 1: "MAXIT", 2: "BREAKDOWN", 3: "ZERO_PIVOT", 4: "MISSING_DIAG", 5: "NAN", 6: "INVALID_ARG"}
 
 _i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
@@ -51,6 +51,8 @@ def lib():
         L.orc_check_pattern.restype = _I
         L.orc_ilu0.argtypes = [_I, _i32p, _i32p, _f64p, _I, _I, _f64p, _IP]
         L.orc_ilu0.restype = _I
+        L.orc_ilu0_mp.argtypes = [_I, _i32p, _i32p, _f64p, _I, _I, _f64p, _IP]
+        L.orc_ilu0_mp.restype = _I
         L.orc_precond.argtypes = [_I, _i32p, _i32p, _f64p, _I, _I, _I, _I, _f64p, _f64p]
         L.orc_krylov.argtypes = [_I, _I, _i32p, _i32p, _f64p, _I, _I, _I, ctypes.c_void_p, _f64p, _f64p,
                                  _D, _D, _I, _I, _f64p, _IP, _DP]
@@ -110,11 +112,17 @@ def check_pattern(A):
     return st, fr.value
 
 
-def ilu0(A, prec="fp64", c=1):
-    """ILU(0) factor on A's pattern (Algorithm 1); returns (status, factor values, fail_row)."""
+def ilu0(A, prec="fp64", c=1, w=1):
+    """ILU(0) factor on A's pattern (Algorithm 1); returns (status, factor values, fail_row).
+    prec 'mp': the factor in w-component arithmetic (nnz * c * w values)."""
     n, rp, ci, val = A
-    fac = np.zeros(len(ci) * c)
     fr = ctypes.c_int(-1)
+    if prec == "mp":
+        fac = np.zeros(len(ci) * c * w)
+        st = lib().orc_ilu0_mp(n, _c(rp, np.int32), _c(ci, np.int32), _c(val, np.float64), c, w, fac,
+                               ctypes.byref(fr))
+        return st, fac, fr.value
+    fac = np.zeros(len(ci) * c)
     st = lib().orc_ilu0(n, _c(rp, np.int32), _c(ci, np.int32), _c(val, np.float64), c, ILUS[prec], fac, ctypes.byref(fr))
     return st, fac, fr.value
 
@@ -139,7 +147,7 @@ def krylov(method, A, b, w, c=1, ilu="none", fac=None, x0=None, tol_rel=1e-25, t
     facp = None
     if ILUS[ilu] >= 0:
         if fac is None:
-            st, fac, fr = ilu0(A, ilu, c)
+            st, fac, fr = ilu0(A, ilu, c, w)
             if st != 0:
                 return {"status": STATUS[st], "iters": 0, "x": x, "hist": hist[:1], "relres_true": float("nan"),
                         "fail_row": fr}

@@ -601,6 +601,58 @@ done:
   return st;
 }
 
+/* ILU(0) in the working multi-component precision w (the paper's rows without "_d": factor
+ * entries are w-component numbers).  Algorithm 1 in the same KIJ order as orc_ilu0, every step
+ * in w-component arithmetic: L_ik := A_ik / U_kk, then A_ij := A_ij - L_ik * U_kj (the product
+ * with L_ik as its first operand).  The pivot test reads the leading components.  fac receives
+ * nnz * c * w doubles (entry p: real components, then imaginary components). */
+int orc_ilu0_mp(int n, const int *rp, const int *ci, const double *val, int c, int w, double *fac, int *fail_row) {
+  int nnz = rp[n], i, k, p, q, st;
+  ctx t = {w, c};
+  int s = c * w;
+  int *diag = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+  int *cnt = (int *)calloc((size_t)n + 1, sizeof(int));
+  int *cptr = (int *)calloc((size_t)n + 1, sizeof(int));
+  int *crow = (int *)malloc(sizeof(int) * (size_t)(nnz > 0 ? nnz : 1));
+  int *cpos = (int *)malloc(sizeof(int) * (size_t)(nnz > 0 ? nnz : 1));
+  *fail_row = -1;
+  st = orc_check_pattern(n, rp, ci, diag, fail_row);
+  if (st != ORC_OK) goto done;
+  for (i = 0; i < n; ++i)
+    for (p = rp[i]; p < rp[i + 1]; ++p)
+      if (ci[p] < i) cnt[ci[p]]++;
+  for (k = 0; k < n; ++k) cptr[k + 1] = cptr[k] + cnt[k];
+  memset(cnt, 0, sizeof(int) * (size_t)n);
+  for (i = 0; i < n; ++i)
+    for (p = rp[i]; p < rp[i + 1]; ++p)
+      if (ci[p] < i) { int k2 = ci[p]; crow[cptr[k2] + cnt[k2]] = i; cpos[cptr[k2] + cnt[k2]] = p; cnt[k2]++; }
+  memset(fac, 0, sizeof(double) * (size_t)nnz * s);
+  for (p = 0; p < nnz; ++p) {
+    fac[(size_t)p * s] = c == 2 ? val[2 * (size_t)p] : val[p];
+    if (c == 2) fac[(size_t)p * s + w] = val[2 * (size_t)p + 1];
+  }
+  for (k = 0; k < n; ++k) {
+    int dk = diag[k], e;
+    num ukk = n_load(fac + (size_t)dk * s, t);
+    if (n_is_zero(ukk)) { *fail_row = k; st = ORC_ZERO_PIVOT; goto done; }
+    for (e = cptr[k]; e < cptr[k + 1]; ++e) {
+      int ii = crow[e], pik = cpos[e];
+      num l = n_div(n_load(fac + (size_t)pik * s, t), ukk, t);
+      n_store(fac + (size_t)pik * s, l, t);
+      for (q = dk + 1; q < rp[k + 1]; ++q) {
+        int j = ci[q];
+        int pij = find_col(ci, rp[ii], rp[ii + 1], j);
+        if (pij >= rp[ii + 1] || ci[pij] != j) continue;
+        n_store(fac + (size_t)pij * s,
+                n_sub(n_load(fac + (size_t)pij * s, t), n_mul(l, n_load(fac + (size_t)q * s, t), t), t), t);
+      }
+    }
+  }
+done:
+  free(diag); free(cnt); free(cptr); free(crow); free(cpos);
+  return st;
+}
+
 /* ------------------------------------------------------------------------------------------
  * Substitutions, Algorithm 2, on CSR patterns (column order ascending within a row).
  * Factor layout as returned by orc_ilu0.  M z = r: forward with unit L~, backward with U~.
@@ -608,6 +660,8 @@ done:
  * both evaluated row-wise on the explicitly conjugate-transposed factor.
  *
  * prec 0 ("_d"): binary64 factor entries times MP vector entries, subtracted in MP, divided in MP.
+ * prec 3 (full MP, the rows without "_d"): w-component factor entries (orc_ilu0_mp) times MP
+ *   vector entries, factor first in every product, divided in MP.
  * prec 1, 2: the MP right-hand side is scaled by 2^-e, e = frexp exponent of the largest
  *   |leading component| (real and imaginary parts), each scaled leading component is rounded
  *   to binary32, both triangles are solved in binary32 (y := fma(-l, y_j, y); division
@@ -615,6 +669,27 @@ done:
  * ---------------------------------------------------------------------------------------- */
 typedef struct { int n; int *rp, *ci; double *v; } csr_t; /* v: c doubles per entry */
 
+/* entries of s doubles; the last nneg of them (imaginary components) change sign */
+static csr_t csr_conj_transpose_s(int n, const int *rp, const int *ci, const double *v, int s, int nneg) {
+  csr_t t;
+  int nnz = rp[n], i, p, k;
+  int *cnt = (int *)calloc((size_t)n + 1, sizeof(int));
+  t.n = n;
+  t.rp = (int *)calloc((size_t)n + 1, sizeof(int));
+  t.ci = (int *)malloc(sizeof(int) * (size_t)(nnz > 0 ? nnz : 1));
+  t.v = (double *)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1) * s);
+  for (p = 0; p < nnz; ++p) cnt[ci[p]]++;
+  for (i = 0; i < n; ++i) t.rp[i + 1] = t.rp[i] + cnt[i];
+  memset(cnt, 0, sizeof(int) * (size_t)n);
+  for (i = 0; i < n; ++i)
+    for (p = rp[i]; p < rp[i + 1]; ++p) {
+      int j = ci[p], dst = t.rp[j] + cnt[j]++;
+      t.ci[dst] = i;
+      for (k = 0; k < s; ++k) t.v[(size_t)dst * s + k] = k >= s - nneg ? -v[(size_t)p * s + k] : v[(size_t)p * s + k];
+    }
+  free(cnt);
+  return t;
+}
 static csr_t csr_conj_transpose(int n, const int *rp, const int *ci, const double *v, int c) {
   csr_t t;
   int nnz = rp[n], i, p;
@@ -658,6 +733,22 @@ static void tri_mp(int n, const int *rp, const int *ci, const double *f, ctx t, 
     n_store(z + (size_t)i * s, acc, t);
   }
 }
+/* The same with w-component factor entries (stride c * w): acc -= f_p * z_j (factor first). */
+static void tri_mpf(int n, const int *rp, const int *ci, const double *f, ctx t, int lower, int unit, const double *r, double *z) {
+  int s = t.c * t.w, ii, p;
+  for (ii = 0; ii < n; ++ii) {
+    int i = lower ? ii : n - 1 - ii, pd = -1;
+    num acc = n_load(r + (size_t)i * s, t);
+    for (p = rp[i]; p < rp[i + 1]; ++p) {
+      int j = ci[p];
+      if (j == i) { pd = p; continue; }
+      if ((lower && j < i) || (!lower && j > i))
+        acc = n_sub(acc, n_mul(n_load(f + (size_t)p * s, t), n_load(z + (size_t)j * s, t), t), t);
+    }
+    if (!unit && pd >= 0) acc = n_div(acc, n_load(f + (size_t)pd * s, t), t);
+    n_store(z + (size_t)i * s, acc, t);
+  }
+}
 static void tri_f32(int n, const int *rp, const int *ci, const double *f, int c, int lower, int unit, const float *r, float *z) {
   int ii, p;
   for (ii = 0; ii < n; ++ii) {
@@ -695,9 +786,17 @@ static void precond_apply(int n, const int *rp, const int *ci, const double *fac
   const double *fv = fac;
   csr_t tr;
   int have_tr = 0;
-  if (trans) { tr = csr_conj_transpose(n, rp, ci, fac, t.c); have_tr = 1; frp = tr.rp; fci = tr.ci; fv = tr.v; }
+  if (trans) {
+    tr = prec == 3 ? csr_conj_transpose_s(n, rp, ci, fac, s, t.c == 2 ? t.w : 0) : csr_conj_transpose(n, rp, ci, fac, t.c);
+    have_tr = 1; frp = tr.rp; fci = tr.ci; fv = tr.v;
+  }
   /* M: lower unit then upper with division.  M^H: lower with division then upper unit. */
-  if (prec == 0) {
+  if (prec == 3) {
+    double *y = (double *)malloc(sizeof(double) * (size_t)n * s + 1);
+    tri_mpf(n, frp, fci, fv, t, 1, trans ? 0 : 1, r, y);
+    tri_mpf(n, frp, fci, fv, t, 0, trans ? 1 : 0, y, z);
+    free(y);
+  } else if (prec == 0) {
     double *y = (double *)malloc(sizeof(double) * (size_t)n * s + 1);
     tri_mp(n, frp, fci, fv, t, 1, trans ? 0 : 1, r, y);
     tri_mp(n, frp, fci, fv, t, 0, trans ? 1 : 0, y, z);
