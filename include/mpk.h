@@ -59,8 +59,11 @@ typedef enum {
   MPK_ILU_FP32 = 1,  /* A rounded to binary32, factor and substitutions in binary32: the
                         right-hand side is scaled by 2^-e (e = exponent of its largest entry),
                         rounded to binary32, solved, widened and scaled back                 */
-  MPK_ILU_BF16 = 2   /* binary32 factorisation, factor stored as bfloat16 (round to nearest
+  MPK_ILU_BF16 = 2,  /* binary32 factorisation, factor stored as bfloat16 (round to nearest
                         even); substitutions as MPK_ILU_FP32                                 */
+  MPK_ILU_MP = 3     /* factor entries in the solve's w-component arithmetic (the paper's rows
+                        without "_d"): factorisation, products and divisions of the
+                        substitutions all in w components; made by mpk_ilu0_factor_mp       */
 } mpk_ilu_prec;
 
 /* Product-type Krylov methods (Sec. 3): BiCG is Algorithm 3; CGS, BiCGSTAB and GPBiCG are the
@@ -82,12 +85,20 @@ typedef struct {
  * dependency-driven substitutions.  One solve at a time per handle. */
 typedef struct mpk_ilu mpk_ilu;
 
+/* mpk_opts.flags bits. */
+#define MPK_FLAG_ETA0 1      /* GPBiCG with eta forced to 0 (it then reduces to BiCGSTAB)            */
+#define MPK_FLAG_MP_MATRIX 2 /* every SpMV (A x, A^H p~, the final b - A x) promotes the binary64
+                                entry a to the w-component number (a, 0, ..., 0) -- the same value --
+                                and multiplies in full w-component arithmetic, matrix entry first:
+                                the SpMV of the paper's rows without "_d" (Sec. 4); default (0) is
+                                the mixed-precision SpMV of the "_d" rows                           */
+
 typedef struct {
   double tol_rel;          /* eps_r of the stopping rule ||r|| < eps_r ||r0|| + eps_a (Alg. 3) */
   double tol_abs;          /* eps_a                                                            */
   int32_t maxit;           /* iteration limit (Sec. 4 uses 3n)                                  */
   int32_t check_every;     /* iterations queued between host checks of the device "done" flag */
-  int32_t flags;           /* bit 0: GPBiCG with eta forced to 0 (reduces to BiCGSTAB)          */
+  int32_t flags;           /* MPK_FLAG_* bits                                                   */
   int32_t reserved;
   double* hist_dev;        /* nullable device array of maxit+1 doubles: leading component of
                               ||r_k||_2, k = 0..iters                                            */
@@ -102,7 +113,8 @@ typedef struct {
   double relres_rec;       /* ||r_k|| / ||r0|| of the recursively updated residual               */
   double relres_true;      /* ||b - A x_k|| / ||r0|| recomputed at the end in the vector format */
   float ms_solve;          /* device time of the solve (CUDA events on `stream`)                */
-  float reserved2;
+  int32_t hermitian;       /* BiCG: 1 if A was found equal to A^H (entries compared as numbers),
+                              so that q~ = A^H p~ used A's own rows and no transpose was built     */
 } mpk_info;
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -120,6 +132,14 @@ uint64_t mpk_kernel_launches(void);
  * product and sum in w-component arithmetic.  x_dev, y_dev: n*c*w doubles (c from A), must
  * not overlap. */
 int mpk_spmv_mp(const mpk_csr* A, int w, const double* x_dev, double* y_dev, void* stream);
+
+/* y = A x with A held in the vectors' w-component type (the SpMV of the paper's rows without
+ * "_d", Sec. 4): each binary64 entry a is promoted to (a, 0, ..., 0) -- the same value -- and
+ * multiplied as a full w-component number, matrix entry first; accumulation as mpk_spmv_mp.
+ * For w = 1, 3, 4 the result equals mpk_spmv_mp's (exactly rounded products and sums); for
+ * w = 2 the double-word product of two double words differs from the double word times binary64
+ * product in rounding.  Arguments and errors as mpk_spmv_mp. */
+int mpk_spmv_mp_matrix(const mpk_csr* A, int w, const double* x_dev, double* y_dev, void* stream);
 
 /* out_dev[0 .. c*w) = <a, b> = sum_i conj(a_i) b_i in w-component arithmetic (Alg. 3 inner
  * products), reduced in a fixed order (deterministic for a given n). */
@@ -152,13 +172,27 @@ int mpk_dot_noalloc(int n, int is_complex, int w, const double* a_dev, const dou
  * The call synchronises `stream` to read the device status. */
 int mpk_ilu0_factor(const mpk_csr* A, int prec, mpk_ilu** out, int* fail_row, void* stream);
 
+/* ILU(0) of A in w-component arithmetic (w = 1..4; Algorithm 1 with every step in the
+ * multi-component format of Sec. 2, the factor of the paper's rows without "_d").  Entry
+ * values start as A's binary64 values (lower components 0); the KIJ updates
+ * L_ik := A_ik / U_kk and A_ij := A_ij - L_ik * U_kj are the format's division, product (L_ik
+ * first) and subtraction, each rounded to w components, in the sequential order.  The zero
+ * pivot test reads the leading components.  The handle (prec MPK_ILU_MP) serves solves and
+ * mpk_precond_apply with the same w only (MPK_INVALID_ARG otherwise); it holds nnz*c*w
+ * doubles of factor.  Status, ownership and synchronisation as mpk_ilu0_factor. */
+int mpk_ilu0_factor_mp(const mpk_csr* A, int w, mpk_ilu** out, int* fail_row, void* stream);
+
 /* Copy the factor values (nnz*c doubles on A's pattern: strict lower part = L~ without its
  * unit diagonal, upper part with diagonal = U~; binary32/bfloat16 values widened) to
- * out_dev. */
+ * out_dev.  A MPK_ILU_MP handle copies nnz*c*w doubles (entry p: its w real components, then
+ * its w imaginary components). */
 int mpk_ilu0_values(const mpk_ilu* M, double* out_dev, void* stream);
 
 /* Precision the handle was built with (mpk_ilu_prec), or -2 for a NULL handle. */
 int mpk_ilu0_prec(const mpk_ilu* M);
+
+/* Components per factor value: w for a MPK_ILU_MP handle, 1 otherwise; -2 for NULL. */
+int mpk_ilu0_width(const mpk_ilu* M);
 
 void mpk_ilu0_destroy(mpk_ilu* M);
 
@@ -232,12 +266,13 @@ int mpk_gnn_backward(const mpk_csr* A, const mpk_ilu* M, const float* params_dev
 int mpk_gnn_adam(int nparams, float* params_dev, const float* grad_dev, float* m_dev, float* v_dev, float lr,
                  int step, void* stream);
 /* Replace M's factor by f' = f (1 + 0.5 tanh o) in M's precision (repacks the triangles; the
- * conjugate transpose is rebuilt on its next use). */
+ * conjugate transpose is rebuilt on its next use).  MPK_ILU_MP handles: MPK_INVALID_ARG (the
+ * network reads binary64, binary32 and bfloat16 factors). */
 int mpk_ilu0_correct(mpk_ilu* M, const float* o_dev, void* stream);
 
 /* End-to-end convenience: host CSR, host b and x (x0 in, solution out).  Copies A and b to
- * the device, builds ILU(0) in `prec` (MPK_ILU_NONE: none), solves, copies x back and frees
- * everything.  info->ms_solve covers the whole call. */
+ * the device, builds ILU(0) in `prec` (MPK_ILU_NONE: none; MPK_ILU_MP: in w components),
+ * solves, copies x back and frees everything.  info->ms_solve covers the whole call. */
 int mpk_solve_host(int method, int w, int prec, int32_t n, int32_t is_complex, const int32_t* row_ptr_host,
                    const int32_t* col_idx_host, const double* val_host, const double* b_host, double* x_host,
                    const mpk_opts* opts, mpk_info* info);

@@ -46,6 +46,7 @@ def lib():
         L.orc_two_prod.argtypes = [_D, _D, _f64p]
         L.orc_mp_op.argtypes = [_I, _I, _f64p, _f64p, _f64p]
         L.orc_spmv.argtypes = [_I, _i32p, _i32p, _f64p, _I, _I, _f64p, _f64p]
+        L.orc_spmv_mm.argtypes = [_I, _i32p, _i32p, _f64p, _I, _I, _f64p, _f64p]
         L.orc_dot.argtypes = [_I, _I, _I, _f64p, _f64p, _f64p]
         L.orc_check_pattern.argtypes = [_I, _i32p, _i32p, ctypes.c_void_p, _IP]
         L.orc_check_pattern.restype = _I
@@ -90,11 +91,13 @@ def mp_op(op, w, a, b=None):
     return out[:w]
 
 
-def spmv(A, x, w, c=1):
-    """y = A x; A = (n, row_ptr, col, val) with val interleaved re,im when c == 2."""
+def spmv(A, x, w, c=1, mp_matrix=False):
+    """y = A x; A = (n, row_ptr, col, val) with val interleaved re,im when c == 2.
+    mp_matrix: the matrix entries promoted to w components (the rows without "_d")."""
     n, rp, ci, val = A
     y = np.zeros(n * c * w)
-    lib().orc_spmv(n, _c(rp, np.int32), _c(ci, np.int32), _c(val, np.float64), c, w, _c(x, np.float64), y)
+    f = lib().orc_spmv_mm if mp_matrix else lib().orc_spmv
+    f(n, _c(rp, np.int32), _c(ci, np.int32), _c(val, np.float64), c, w, _c(x, np.float64), y)
     return y
 
 
@@ -137,8 +140,9 @@ def precond(A, fac, r, w, prec="fp64", c=1, trans=False):
 
 
 def krylov(method, A, b, w, c=1, ilu="none", fac=None, x0=None, tol_rel=1e-25, tol_abs=0.0, maxit=1000,
-           force_eta0=False):
-    """Run one solve; returns dict(status, iters, x, hist, relres_true)."""
+           force_eta0=False, mp_matrix=False):
+    """Run one solve; returns dict(status, iters, x, hist, relres_true).
+    mp_matrix: every SpMV with the matrix promoted to w components (the rows without "_d")."""
     n, rp, ci, val = A
     x = np.zeros(n * c * w) if x0 is None else _c(x0, np.float64).copy()
     hist = np.zeros(maxit + 2)
@@ -155,6 +159,7 @@ def krylov(method, A, b, w, c=1, ilu="none", fac=None, x0=None, tol_rel=1e-25, t
         facp = fac.ctypes.data_as(ctypes.c_void_p)
     st = lib().orc_krylov(METHODS[method], n, _c(rp, np.int32), _c(ci, np.int32), _c(val, np.float64), c, w,
                           ILUS[ilu], facp, _c(b, np.float64), x, float(tol_rel), float(tol_abs), int(maxit),
-                          1 if force_eta0 else 0, hist, ctypes.byref(it), ctypes.byref(rr))
+                          (1 if force_eta0 else 0) | (2 if mp_matrix else 0), hist, ctypes.byref(it),
+                          ctypes.byref(rr))
     return {"status": STATUS[st], "iters": it.value, "x": x, "hist": hist[: it.value + 1].copy(),
             "relres_true": rr.value}

@@ -11,6 +11,10 @@
  * What follows which passage:
  *   number formats D / DD / TD / QD ........ Sec. 2 (binary64 with 1, 2, 3, 4 components)
  *   mixed SpMV (binary64 matrix, MP vector) Sec. 3, last paragraph; Sec. 4 ("_d" variants)
+ *   MP-matrix SpMV (matrix promoted to MP) . Sec. 4 (the rows without "_d": matrix in the same
+ *                                             multi-component type as the vectors)
+ *   ILU(0) in MP (orc_ilu0_mp) .............. Algorithm 1 in the working precision (Sec. 4, the
+ *                                             rows without "_d")
  *   ILU(0) .................................. Algorithm 1 (KIJ form, no fill)
  *   forward / backward substitution ......... Algorithm 2
  *   preconditioned BiCG ..................... Algorithm 3
@@ -325,7 +329,7 @@ void orc_mp_op(int op, int w, const double *a, const double *b, double *out) {
  *                       power of two 2^-e that brings max(|c|,|d|) (leading parts) into [0.5, 1)
  * ---------------------------------------------------------------------------------------- */
 typedef struct { mp re, im; } num;
-typedef struct { int w, c; } ctx;
+typedef struct { int w, c, mm; } ctx; /* mm: matrix entries promoted to w components */
 
 static num n_zero(void) { num z; z.re = mp_zero(); z.im = mp_zero(); return z; }
 static num n_load(const double *p, ctx t) {
@@ -413,6 +417,9 @@ static int n_is_zero(num a) { return a.re.c[0] == 0.0 && a.im.c[0] == 0.0; }
 /* ------------------------------------------------------------------------------------------
  * Vector kernels: mixed SpMV y = A x (binary64 matrix, MP vector; CSR order, starting from 0),
  * inner product <a,b> = sum conj(a_i) b_i (sequential), 2-norm = sqrt(Re <r,r>).
+ * With t.mm the matrix entry is first promoted to a w-component number (a, 0, ..., 0) -- the
+ * value is unchanged, the paper's matrices being binary64 -- and the product is the format's
+ * full multiplication with the matrix entry first: the SpMV of the rows without "_d".
  * ---------------------------------------------------------------------------------------- */
 static void spmv(int n, const int *rp, const int *ci, const double *val, ctx t, const double *x, double *y) {
   int s = t.c * t.w, i, p;
@@ -422,13 +429,24 @@ static void spmv(int n, const int *rp, const int *ci, const double *val, ctx t, 
       num xj = n_load(x + (size_t)ci[p] * s, t);
       double ar = t.c == 2 ? val[2 * (size_t)p] : val[p];
       double ai = t.c == 2 ? val[2 * (size_t)p + 1] : 0.0;
-      acc = n_add(acc, n_mul_d(xj, ar, ai, t), t);
+      if (t.mm) {
+        num a = n_zero();
+        a.re.c[0] = ar;
+        a.im.c[0] = ai;
+        acc = n_add(acc, n_mul(a, xj, t), t);
+      } else {
+        acc = n_add(acc, n_mul_d(xj, ar, ai, t), t);
+      }
     }
     n_store(y + (size_t)i * s, acc, t);
   }
 }
 void orc_spmv(int n, const int *rp, const int *ci, const double *val, int c, int w, const double *x, double *y) {
-  ctx t = {w, c};
+  ctx t = {w, c, 0};
+  spmv(n, rp, ci, val, t, x, y);
+}
+void orc_spmv_mm(int n, const int *rp, const int *ci, const double *val, int c, int w, const double *x, double *y) {
+  ctx t = {w, c, 1};
   spmv(n, rp, ci, val, t, x, y);
 }
 /* The summation order of an inner product is fixed (the paper leaves it open): the products
@@ -455,7 +473,7 @@ static num dot(int n, ctx t, const double *a, const double *b) {
   return res;
 }
 void orc_dot(int n, int c, int w, const double *a, const double *b, double *out) {
-  ctx t = {w, c};
+  ctx t = {w, c, 0};
   n_store(out, dot(n, t, a, b), t);
 }
 static mp nrm2(int n, ctx t, const double *a) { return mp_sqrt(dot(n, t, a, a).re, t.w); }
@@ -608,7 +626,7 @@ done:
  * nnz * c * w doubles (entry p: real components, then imaginary components). */
 int orc_ilu0_mp(int n, const int *rp, const int *ci, const double *val, int c, int w, double *fac, int *fail_row) {
   int nnz = rp[n], i, k, p, q, st;
-  ctx t = {w, c};
+  ctx t = {w, c, 0};
   int s = c * w;
   int *diag = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
   int *cnt = (int *)calloc((size_t)n + 1, sizeof(int));
@@ -826,7 +844,7 @@ static void precond_apply(int n, const int *rp, const int *ci, const double *fac
   if (have_tr) csr_free(&tr);
 }
 void orc_precond(int n, const int *rp, const int *ci, const double *fac, int c, int w, int prec, int trans, const double *r, double *z) {
-  ctx t = {w, c};
+  ctx t = {w, c, 0};
   precond_apply(n, rp, ci, fac, t, prec, trans, r, z);
 }
 
@@ -864,7 +882,7 @@ int orc_krylov(int method, int n, const int *rp, const int *ci, const double *va
                const double *fac, const double *b, double *x, double tol_rel, double tol_abs, int maxit, int flags,
                double *hist, int *iters_out, double *relres_true) {
   sys_t S;
-  ctx t = {w, c};
+  ctx t = {w, c, (flags >> 1) & 1}; /* flags bit 1: every SpMV with the matrix promoted to MP */
   int s = c * w, it = 0, st = ORC_MAXIT, i;
   double r0n, tol;
   double *r, *rt, *tmp;

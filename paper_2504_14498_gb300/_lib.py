@@ -15,7 +15,8 @@ LIB_PATH = os.path.join(HERE, "libmpk.so")
 STATUS = {0: "OK", 1: "MAXIT", 2: "BREAKDOWN", 3: "ZERO_PIVOT", 4: "MISSING_DIAG", 5: "NAN", 6: "INVALID_ARG",
           7: "CUDA_ERROR", 8: "TIMEOUT", 9: "NOT_IMPLEMENTED"}
 METHODS = {"bicg": 0, "cgs": 1, "bicgstab": 2, "gpbicg": 3}
-ILUS = {"none": -1, "fp64": 0, "fp32": 1, "bf16": 2}
+ILUS = {"none": -1, "fp64": 0, "fp32": 1, "bf16": 2, "mp": 3}
+FLAG_ETA0, FLAG_MP_MATRIX = 1, 2  # mpk_opts.flags bits
 
 
 class MpkError(RuntimeError):
@@ -38,7 +39,7 @@ class Opts(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("fail_row", ctypes.c_int32),
                 ("graph", ctypes.c_int32), ("res0", ctypes.c_double), ("relres_rec", ctypes.c_double),
-                ("relres_true", ctypes.c_double), ("ms_solve", ctypes.c_float), ("reserved2", ctypes.c_float)]
+                ("relres_true", ctypes.c_double), ("ms_solve", ctypes.c_float), ("hermitian", ctypes.c_int32)]
 
 
 _lib = None
@@ -50,11 +51,14 @@ SIGNATURES = [
     ("mpk_last_error", ctypes.c_char_p, []),
     ("mpk_kernel_launches", ctypes.c_uint64, []),
     ("mpk_spmv_mp", _I, [ctypes.POINTER(CsrDesc), _I, _VP, _VP, _VP]),
+    ("mpk_spmv_mp_matrix", _I, [ctypes.POINTER(CsrDesc), _I, _VP, _VP, _VP]),
     ("mpk_dot", _I, [_I, _I, _I, _VP, _VP, _VP, _VP]),
     ("mpk_dot_noalloc", _I, [_I, _I, _I, _VP, _VP, _VP, _VP]),
     ("mpk_ilu0_factor", _I, [ctypes.POINTER(CsrDesc), _I, ctypes.POINTER(_VP), ctypes.POINTER(_I), _VP]),
+    ("mpk_ilu0_factor_mp", _I, [ctypes.POINTER(CsrDesc), _I, ctypes.POINTER(_VP), ctypes.POINTER(_I), _VP]),
     ("mpk_ilu0_values", _I, [_VP, _VP, _VP]),
     ("mpk_ilu0_prec", _I, [_VP]),
+    ("mpk_ilu0_width", _I, [_VP]),
     ("mpk_ilu0_destroy", None, [_VP]),
     ("mpk_precond_apply", _I, [_VP, _I, _I, _VP, _VP, _VP]),
     ("mpk_krylov_solve", _I, [_I, _I, ctypes.POINTER(CsrDesc), _VP, _VP, _VP, ctypes.POINTER(Opts),
@@ -130,11 +134,13 @@ class Matrix:
         return cls(n, rp, ci, val, is_complex, device)
 
 
-def spmv_mp(A: Matrix, x: torch.Tensor, w: int, y: torch.Tensor = None) -> torch.Tensor:
-    """y = A x with w-component vectors (n*c*w doubles)."""
+def spmv_mp(A: Matrix, x: torch.Tensor, w: int, y: torch.Tensor = None, mp_matrix=False) -> torch.Tensor:
+    """y = A x with w-component vectors (n*c*w doubles); mp_matrix: A's entries promoted to w
+    components (the rows without "_d")."""
     if y is None:
         y = torch.empty(A.n * A.cp * w, dtype=torch.float64, device=x.device)
-    _check(lib().mpk_spmv_mp(ctypes.byref(A.desc), w, _ptr(x), _ptr(y), _stream()))
+    f = lib().mpk_spmv_mp_matrix if mp_matrix else lib().mpk_spmv_mp
+    _check(f(ctypes.byref(A.desc), w, _ptr(x), _ptr(y), _stream()))
     return y
 
 
@@ -156,21 +162,28 @@ def dot_noalloc(a: torch.Tensor, b: torch.Tensor, n: int, w: int, is_complex=Fal
 
 
 class ILU0:
-    """ILU(0) handle (Algorithm 1) in 'fp64', 'fp32' or 'bf16'."""
+    """ILU(0) handle (Algorithm 1) in 'fp64', 'fp32' or 'bf16', or in w-component arithmetic
+    ('mp', with w: the factor of the rows without "_d", serving solves with the same w)."""
 
-    def __init__(self, A: Matrix, prec="fp64"):
+    def __init__(self, A: Matrix, prec="fp64", w: int = None):
         self.A = A
         self.prec = prec
+        self.w = w if prec == "mp" else 1
         h = ctypes.c_void_p()
         fr = ctypes.c_int(-1)
-        st = lib().mpk_ilu0_factor(ctypes.byref(A.desc), ILUS[prec], ctypes.byref(h), ctypes.byref(fr), _stream())
+        if prec == "mp":
+            if w is None:
+                raise ValueError("prec 'mp' needs the component count w")
+            st = lib().mpk_ilu0_factor_mp(ctypes.byref(A.desc), int(w), ctypes.byref(h), ctypes.byref(fr), _stream())
+        else:
+            st = lib().mpk_ilu0_factor(ctypes.byref(A.desc), ILUS[prec], ctypes.byref(h), ctypes.byref(fr), _stream())
         self.fail_row = fr.value
         if st != 0:
             raise MpkError(st, lib().mpk_last_error().decode() + " (row %d)" % fr.value)
         self.handle = h
 
     def values(self) -> torch.Tensor:
-        out = torch.empty(self.A.nnz * self.A.cp, dtype=torch.float64, device="cuda")
+        out = torch.empty(self.A.nnz * self.A.cp * self.w, dtype=torch.float64, device="cuda")
         _check(lib().mpk_ilu0_values(self.handle, _ptr(out), _stream()))
         return out
 
@@ -193,11 +206,13 @@ class ILU0:
 
 
 def krylov_solve(method, w, A: Matrix, M: ILU0, b: torch.Tensor, x0: torch.Tensor = None, tol_rel=1e-25,
-                 tol_abs=0.0, maxit=1000, check_every=25, history=True, force_eta0=False):
-    """Solve A x = b; returns dict(status, iters, x, hist, res0, relres_rec, relres_true, ms)."""
+                 tol_abs=0.0, maxit=1000, check_every=25, history=True, force_eta0=False, mp_matrix=False):
+    """Solve A x = b; returns dict(status, iters, x, hist, res0, relres_rec, relres_true, ms, graph,
+    hermitian).  mp_matrix: every SpMV with A's entries promoted to w components."""
     x = torch.zeros_like(b) if x0 is None else x0.clone()
     hist = torch.full((maxit + 1,), float("nan"), dtype=torch.float64, device=b.device) if history else None
-    opts = Opts(float(tol_rel), float(tol_abs), int(maxit), int(check_every), 1 if force_eta0 else 0, 0,
+    flags = (FLAG_ETA0 if force_eta0 else 0) | (FLAG_MP_MATRIX if mp_matrix else 0)
+    opts = Opts(float(tol_rel), float(tol_abs), int(maxit), int(check_every), flags, 0,
                 hist.data_ptr() if history else None)
     info = Info()
     st = lib().mpk_krylov_solve(METHODS[method], w, ctypes.byref(A.desc), M.handle if M is not None else None,
@@ -207,11 +222,11 @@ def krylov_solve(method, w, A: Matrix, M: ILU0, b: torch.Tensor, x0: torch.Tenso
     h = hist[: info.iters + 1].cpu().numpy() if history else None
     return {"status": STATUS[info.status], "iters": info.iters, "x": x, "hist": h, "res0": info.res0,
             "relres_rec": info.relres_rec, "relres_true": info.relres_true, "ms": info.ms_solve,
-            "graph": bool(info.graph)}
+            "graph": bool(info.graph), "hermitian": bool(info.hermitian)}
 
 
 def krylov_solve_batched(method, w, A: Matrix, sys_rows, M: ILU0, b: torch.Tensor, x0: torch.Tensor = None,
-                         tol_rel=1e-25, tol_abs=0.0, maxit=1000, check_every=25, history=False):
+                         tol_rel=1e-25, tol_abs=0.0, maxit=1000, check_every=25, history=False, mp_matrix=False):
     """Solve the nsys independent systems of the block-diagonal A (system s: rows sys_rows[s] ..
     sys_rows[s+1]-1) together; returns dict(status, x, per-system arrays: statuses, iters, res0,
     relres_rec, relres_true, and hist (nsys x (maxit+1)) when asked)."""
@@ -220,7 +235,7 @@ def krylov_solve_batched(method, w, A: Matrix, sys_rows, M: ILU0, b: torch.Tenso
     rows_dev = torch.as_tensor(rows, device=b.device)
     x = torch.zeros_like(b) if x0 is None else x0.clone()
     hist = torch.full((nsys, maxit + 1), float("nan"), dtype=torch.float64, device=b.device) if history else None
-    opts = Opts(float(tol_rel), float(tol_abs), int(maxit), int(check_every), 0, 0,
+    opts = Opts(float(tol_rel), float(tol_abs), int(maxit), int(check_every), FLAG_MP_MATRIX if mp_matrix else 0, 0,
                 hist.data_ptr() if history else None)
     infos = (Info * nsys)()
     st = lib().mpk_krylov_solve_batched(METHODS[method], w, ctypes.byref(A.desc), nsys, rows.ctypes.data,

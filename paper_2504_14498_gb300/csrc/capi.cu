@@ -65,7 +65,7 @@ extern "C" const char* mpk_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" uint64_t mpk_kernel_launches(void) { return (uint64_t)g_launches.load(); }
 
-extern "C" int mpk_spmv_mp(const mpk_csr* A, int w, const double* x_dev, double* y_dev, void* stream) {
+static int spmv_entry(const mpk_csr* A, int w, const double* x_dev, double* y_dev, bool mm, void* stream) {
   if (A == nullptr || x_dev == nullptr || y_dev == nullptr || x_dev == y_dev)
     return fail(MPK_INVALID_ARG, "null or aliased argument");
   if (A->n < 1 || A->nnz < 0 || A->row_ptr == nullptr || (A->nnz > 0 && (A->col_idx == nullptr || A->val == nullptr)))
@@ -74,9 +74,18 @@ extern "C" int mpk_spmv_mp(const mpk_csr* A, int w, const double* x_dev, double*
   if (w < 1 || w > 4) return fail(MPK_INVALID_ARG, "w must be 1..4");
   const Ops* o = get_ops(w, A->is_complex ? 2 : 1);
   Csr c{A->n, A->nnz, A->row_ptr, A->col_idx, A->val, A->is_complex};
+  c.mm = mm;
   o->spmv(c, x_dev, y_dev, nullptr, nullptr, nullptr, (cudaStream_t)stream);
   MPK_CUDA(cudaGetLastError());
   return MPK_OK;
+}
+
+extern "C" int mpk_spmv_mp(const mpk_csr* A, int w, const double* x_dev, double* y_dev, void* stream) {
+  return spmv_entry(A, w, x_dev, y_dev, false, stream);
+}
+
+extern "C" int mpk_spmv_mp_matrix(const mpk_csr* A, int w, const double* x_dev, double* y_dev, void* stream) {
+  return spmv_entry(A, w, x_dev, y_dev, true, stream);
 }
 
 extern "C" int mpk_dot(int n, int is_complex, int w, const double* a_dev, const double* b_dev, double* out_dev,

@@ -695,6 +695,7 @@ static int check(const mpk_csr* A, const mpk_ilu* M, const void* work, size_t by
   if (A == nullptr || M == nullptr || work == nullptr) return fail(MPK_INVALID_ARG, "null argument");
   if (A->is_complex) return fail(MPK_INVALID_ARG, "the learned correction is defined for real matrices");
   if (M->n != A->n || M->nnz != A->nnz || M->cp != 1) return fail(MPK_INVALID_ARG, "factor does not match the matrix");
+  if (M->prec == MPK_ILU_MP) return fail(MPK_INVALID_ARG, "the network reads binary64, binary32 or bfloat16 factors");
   if (K < 1 || K > kMaxProbes || nsys < 1) return fail(MPK_INVALID_ARG, "nprobe must be 1..16, nsys >= 1");
   if (bytes < work_bytes(A->n, A->nnz, K, nsys)) return fail(MPK_INVALID_ARG, "workspace too small");
   return MPK_OK;
@@ -831,6 +832,7 @@ extern "C" int mpk_gnn_adam(int nparams, float* params, const float* grad, float
 extern "C" int mpk_ilu0_correct(mpk_ilu* M, const float* o, void* stream) {
   if (M == nullptr || o == nullptr) return fail(MPK_INVALID_ARG, "null argument");
   if (M->cp != 1) return fail(MPK_INVALID_ARG, "the learned correction is defined for real matrices");
+  if (M->prec == MPK_ILU_MP) return fail(MPK_INVALID_ARG, "the correction applies to binary64, binary32 or bfloat16 factors");
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t nnz = M->nnz;
   count_launch();

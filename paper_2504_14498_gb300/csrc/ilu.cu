@@ -141,6 +141,91 @@ __global__ void __launch_bounds__(kBlock) k_ilu(int n, const int* __restrict__ r
   chunk_rows(lo, ci, kIluEpoch, ctl + CTL_TICKET_LO, ctl, row);
 }
 
+// ILU(0) in w-component arithmetic (MPK_ILU_MP): the same row-IKJ dataflow, entries of CP * W
+// doubles; for each k < i in row i, ascending: a_ik := a_ik / a_kk (the format's division), then
+// a_ij := a_ij - a_ik * a_kj for every j > k of row k also in row i (product with a_ik first,
+// then the subtraction, each rounded to W components).  Every entry receives the updates of the
+// KIJ listing in its order, so the result is the sequential one bit for bit.
+template <int W, int CP>
+struct RowIluMp {
+  using Val = Empty;
+  const int* rp;
+  const int* ci;
+  const int* diag;
+  double* a;
+  int* ctl;
+  int i;
+  __device__ void begin(int i_, int& p, int& pend) {
+    i = i_;
+    p = rp[i_];
+    pend = diag[i_];
+  }
+  __device__ Val load(int) { return Val{}; }
+  __device__ void consume(int p, int k, const Val&) {
+    const int dk = diag[k], ek = rp[k + 1], ei = rp[i + 1];
+    const N<W, CP> l = n_div<W, CP>(n_load<W, CP>(a, p), n_load<W, CP>(a, dk));
+    n_store<W, CP>(a, p, l);
+    int r = p + 1;
+    for (int q = dk + 1; q < ek; ++q) {
+      const int j = ci[q];
+      while (r < ei && ci[r] < j) ++r;
+      if (r >= ei) break;
+      if (ci[r] != j) continue;
+      n_store<W, CP>(a, r, n_sub<W, CP>(n_load<W, CP>(a, r), n_mul<W, CP>(l, n_load<W, CP>(a, q))));
+    }
+  }
+  __device__ Val finish() {
+    if (n_is_zero<W, CP>(n_load<W, CP>(a, diag[i]))) atomicMin(ctl + CTL_FAIL_ROW, i);
+    return Val{};
+  }
+  __device__ void store(const Val&) {}
+};
+
+template <int W, int CP>
+__global__ void __launch_bounds__(kBlock) k_ilu_mp(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                   const int* __restrict__ diag, const LevelOrder lo, double* a,
+                                                   int* ctl) {
+  RowIluMp<W, CP> row;
+  row.rp = rp;
+  row.ci = ci;
+  row.diag = diag;
+  row.a = a;
+  row.ctl = ctl;
+  chunk_rows(lo, ci, kIluEpoch, ctl + CTL_TICKET_LO, ctl, row);
+}
+
+// A's binary64 values as w-component numbers: entry p, value t of CP (real, imaginary) goes to
+// component 0 of its part, the other components are 0.
+__global__ void k_to_mp(int64_t nnz, int cp, int w, const double* __restrict__ v, double* __restrict__ out) {
+  const int64_t m = nnz * cp * w;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = k / (cp * w);
+    const int r = (int)(k - p * cp * w), t = r / w, c = r - t * w;
+    out[k] = c == 0 ? v[p * cp + t] : 0.0;
+  }
+}
+
+template <int W, int CP>
+static void launch_ilu_mp_wc(int n, const int* rp, const int* ci, const int* diag, const LevelOrder& lo, double* a,
+                             int* ctl, cudaStream_t s) {
+  static const int blocks = persistent_blocks(k_ilu_mp<W, CP>);
+  k_ilu_mp<W, CP><<<blocks, kBlock, 0, s>>>(n, rp, ci, diag, lo, a, ctl);
+}
+static void launch_ilu_mp(int w, int cp, int n, const int* rp, const int* ci, const int* diag, const LevelOrder& lo,
+                          double* a, int* ctl, cudaStream_t s) {
+  count_launch();
+  switch (w * 2 + cp - 1) {
+    case 2: launch_ilu_mp_wc<1, 1>(n, rp, ci, diag, lo, a, ctl, s); break;
+    case 3: launch_ilu_mp_wc<1, 2>(n, rp, ci, diag, lo, a, ctl, s); break;
+    case 4: launch_ilu_mp_wc<2, 1>(n, rp, ci, diag, lo, a, ctl, s); break;
+    case 5: launch_ilu_mp_wc<2, 2>(n, rp, ci, diag, lo, a, ctl, s); break;
+    case 6: launch_ilu_mp_wc<3, 1>(n, rp, ci, diag, lo, a, ctl, s); break;
+    case 7: launch_ilu_mp_wc<3, 2>(n, rp, ci, diag, lo, a, ctl, s); break;
+    case 8: launch_ilu_mp_wc<4, 1>(n, rp, ci, diag, lo, a, ctl, s); break;
+    default: launch_ilu_mp_wc<4, 2>(n, rp, ci, diag, lo, a, ctl, s); break;
+  }
+}
+
 // New epoch pair (lower: even, upper: odd) and reset tickets and the scale accumulator.
 __global__ void k_trsv_prep(int* ctl, unsigned long long* absmax, const int* done) {
   if (is_done(done)) return;
@@ -193,7 +278,8 @@ __global__ void k_scan_single(int n, const int* __restrict__ cnt, int* __restric
 __device__ __forceinline__ double conj_part(double x) { return -x; }
 __device__ __forceinline__ float conj_part(float x) { return -x; }
 __device__ __forceinline__ uint16_t conj_part(uint16_t x) { return (uint16_t)(x ^ 0x8000u); }
-template <typename T, int CP>
+// Entries of S values each; the last NNEG of them (the imaginary components) change sign.
+template <typename T, int S, int NNEG>
 __global__ void k_scatter_t(int n, const int* __restrict__ rp, const int* __restrict__ ci, const T* __restrict__ v,
                             const int* __restrict__ rpT, int* __restrict__ fill, int* __restrict__ ciT,
                             T* __restrict__ vT) {
@@ -203,11 +289,14 @@ __global__ void k_scatter_t(int n, const int* __restrict__ rp, const int* __rest
     const int j = ci[p];
     const int dst = rpT[j] + atomicAdd(fill + j, 1);
     ciT[dst] = i;
-    vT[(int64_t)dst * CP] = v[(int64_t)p * CP];
-    if constexpr (CP == 2) vT[(int64_t)dst * CP + 1] = conj_part(v[(int64_t)p * CP + 1]);
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+      const T x = v[(int64_t)p * S + t];
+      vT[(int64_t)dst * S + t] = t >= S - NNEG ? conj_part(x) : x;
+    }
   }
 }
-template <typename T, int CP>
+template <typename T, int S>
 __global__ void k_sort_rows(int n, const int* __restrict__ rp, int* __restrict__ ci, T* __restrict__ v,
                             int* __restrict__ diag) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -215,17 +304,19 @@ __global__ void k_sort_rows(int n, const int* __restrict__ rp, int* __restrict__
   const int a = rp[i], b = rp[i + 1];
   for (int p = a + 1; p < b; ++p) {
     const int c = ci[p];
-    T x0 = v[(int64_t)p * CP], x1 = CP == 2 ? v[(int64_t)p * CP + 1] : T(0);
+    T x[S];
+#pragma unroll
+    for (int t = 0; t < S; ++t) x[t] = v[(int64_t)p * S + t];
     int q = p - 1;
     while (q >= a && ci[q] > c) {
       ci[q + 1] = ci[q];
-      v[(int64_t)(q + 1) * CP] = v[(int64_t)q * CP];
-      if constexpr (CP == 2) v[(int64_t)(q + 1) * CP + 1] = v[(int64_t)q * CP + 1];
+#pragma unroll
+      for (int t = 0; t < S; ++t) v[(int64_t)(q + 1) * S + t] = v[(int64_t)q * S + t];
       --q;
     }
     ci[q + 1] = c;
-    v[(int64_t)(q + 1) * CP] = x0;
-    if constexpr (CP == 2) v[(int64_t)(q + 1) * CP + 1] = x1;
+#pragma unroll
+    for (int t = 0; t < S; ++t) v[(int64_t)(q + 1) * S + t] = x[t];
   }
   if (diag != nullptr) {
     int d = -1;
@@ -235,7 +326,8 @@ __global__ void k_sort_rows(int n, const int* __restrict__ rp, int* __restrict__
   }
 }
 
-template <typename T, int CP>
+// Conjugate transpose of a CSR matrix whose entries hold S values, the last NNEG negated.
+template <typename T, int S, int NNEG>
 static int transpose_t(int n, int nnz, const int* rp, const int* ci, const T* v, int* rpT, int* ciT, T* vT, int* diagT,
                        cudaStream_t s) {
   int* cnt = nullptr;
@@ -245,16 +337,16 @@ static int transpose_t(int n, int nnz, const int* rp, const int* ci, const T* v,
   count_launch(4);  // count, scan, scatter, sort
   k_count_cols<<<grid_for(nnz), kBlock, 0, s>>>(nnz, ci, cnt);
   k_scan_single<<<1, 1024, 0, s>>>(n, cnt, rpT);
-  k_scatter_t<T, CP><<<(n + kBlock - 1) / kBlock, kBlock, 0, s>>>(n, rp, ci, v, rpT, fill, ciT, vT);
-  k_sort_rows<T, CP><<<(n + kBlock - 1) / kBlock, kBlock, 0, s>>>(n, rpT, ciT, vT, diagT);
+  k_scatter_t<T, S, NNEG><<<(n + kBlock - 1) / kBlock, kBlock, 0, s>>>(n, rp, ci, v, rpT, fill, ciT, vT);
+  k_sort_rows<T, S><<<(n + kBlock - 1) / kBlock, kBlock, 0, s>>>(n, rpT, ciT, vT, diagT);
   MPK_CUDA(cudaFreeAsync(cnt, s));
   MPK_CUDA(cudaGetLastError());
   return MPK_OK;
 }
 
 int transpose_matrix(const Csr& A, int* rpT, int* ciT, double* vT, cudaStream_t s) {
-  if (A.cplx) return transpose_t<double, 2>(A.n, A.nnz, A.rp, A.ci, A.val, rpT, ciT, vT, nullptr, s);
-  return transpose_t<double, 1>(A.n, A.nnz, A.rp, A.ci, A.val, rpT, ciT, vT, nullptr, s);
+  if (A.cplx) return transpose_t<double, 2, 1>(A.n, A.nnz, A.rp, A.ci, A.val, rpT, ciT, vT, nullptr, s);
+  return transpose_t<double, 1, 0>(A.n, A.nnz, A.rp, A.ci, A.val, rpT, ciT, vT, nullptr, s);
 }
 
 // Level of every row of one triangle: 0 without dependencies, else 1 + the largest level of the
@@ -510,7 +602,7 @@ __global__ void k_sell_fill(int nchunks, const int* __restrict__ perm, const int
 }
 
 // Repack one triangle of (rp, ci, diag, fac) in the positions of its level order into *buf
-// (allocated here) and describe it in *out.
+// (allocated here) and describe it in *out; cp values of type T per entry.
 template <typename T>
 static int build_sell(int n, int cp, const int* rp, const int* ci, const int* diag, const T* fac, int* lvbuf,
                       int nlevels, bool lower, void** buf, SellTri* out, cudaStream_t s) {
@@ -542,12 +634,19 @@ static int build_sell(int n, int cp, const int* rp, const int* ci, const int* di
   int* rep = (int*)(b + coff_b + col_b + val_b + dia_b);
   MPK_CUDA(cudaMemcpyAsync(coff, coff_tmp, sizeof(int) * ((size_t)nch + 1), cudaMemcpyDeviceToDevice, s));
   count_launch();
-  if (cp == 1)
-    k_sell_fill<T, 1><<<grid_for(nch * 32), kBlock, 0, s>>>(nch, lo.perm, lo.pos, rp, ci, diag, fac, lower, coff, col,
-                                                          val, dia, rep);
-  else
-    k_sell_fill<T, 2><<<grid_for(nch * 32), kBlock, 0, s>>>(nch, lo.perm, lo.pos, rp, ci, diag, fac, lower, coff, col,
-                                                          val, dia, rep);
+  const int g = grid_for(nch * 32);
+#define MPK_SELL_FILL(CPX) \
+  k_sell_fill<T, CPX><<<g, kBlock, 0, s>>>(nch, lo.perm, lo.pos, rp, ci, diag, fac, lower, coff, col, val, dia, rep)
+  switch (cp) {  // values per entry: c, or c * w for a w-component factor
+    case 1: MPK_SELL_FILL(1); break;
+    case 2: MPK_SELL_FILL(2); break;
+    case 3: MPK_SELL_FILL(3); break;
+    case 4: MPK_SELL_FILL(4); break;
+    case 6: MPK_SELL_FILL(6); break;
+    case 8: MPK_SELL_FILL(8); break;
+    default: cudaFree(b); cudaFreeAsync(width, s); return fail(MPK_INVALID_ARG, "unsupported values per entry");
+  }
+#undef MPK_SELL_FILL
   MPK_CUDA(cudaGetLastError());
   MPK_CUDA(cudaFreeAsync(width, s));
   *buf = b;
@@ -567,9 +666,9 @@ static int build_sells(mpk_ilu* M, int t0, const int* rp, const int* ci, const i
   for (int t = t0; t < t0 + 2; ++t) {
     const bool lower = (t == t0);
     int st;
-    if (M->prec == MPK_ILU_FP64)
-      st = build_sell<double>(M->n, M->cp, rp, ci, diag, (const double*)fac, M->lvbuf[t], M->nlevels[t], lower,
-                              M->sellbuf + t, M->sell + t, s);
+    if (M->prec == MPK_ILU_FP64 || M->prec == MPK_ILU_MP)
+      st = build_sell<double>(M->n, M->vals_per_entry(), rp, ci, diag, (const double*)fac, M->lvbuf[t], M->nlevels[t],
+                              lower, M->sellbuf + t, M->sell + t, s);
     else if (M->prec == MPK_ILU_FP32)
       st = build_sell<float>(M->n, M->cp, rp, ci, diag, (const float*)fac, M->lvbuf[t], M->nlevels[t], lower,
                              M->sellbuf + t, M->sell + t, s);
@@ -586,7 +685,9 @@ void launch_trsv_prep(const IluHandleView& M, const int* done, cudaStream_t s) {
   k_trsv_prep<<<1, 1, 0, s>>>(M.ctl, M.absmax, done);
 }
 
-static size_t fac_elem_size(int prec) { return prec == MPK_ILU_FP64 ? 8 : (prec == MPK_ILU_FP32 ? 4 : 2); }
+static size_t fac_elem_size(int prec) {
+  return (prec == MPK_ILU_FP64 || prec == MPK_ILU_MP) ? 8 : (prec == MPK_ILU_FP32 ? 4 : 2);
+}
 
 static int build_transpose(mpk_ilu* M, cudaStream_t s) {
   if (M->rpT != nullptr) return MPK_OK;
@@ -594,24 +695,30 @@ static int build_transpose(mpk_ilu* M, cudaStream_t s) {
   MPK_CUDA(cudaMalloc((void**)&M->rpT, sizeof(int) * ((size_t)M->n + 1)));
   MPK_CUDA(cudaMalloc((void**)&M->ciT, sizeof(int) * (size_t)M->nnz));
   MPK_CUDA(cudaMalloc((void**)&M->diagT, sizeof(int) * (size_t)M->n));
-  MPK_CUDA(cudaMalloc(&M->facT, es * (size_t)M->nnz * M->cp));
+  MPK_CUDA(cudaMalloc(&M->facT, es * (size_t)M->nnz * M->vals_per_entry()));
   int st;
-  if (M->prec == MPK_ILU_FP64) {
-    st = M->cp == 2 ? transpose_t<double, 2>(M->n, M->nnz, M->rp, M->ci, (const double*)M->fac, M->rpT, M->ciT,
-                                             (double*)M->facT, M->diagT, s)
-                    : transpose_t<double, 1>(M->n, M->nnz, M->rp, M->ci, (const double*)M->fac, M->rpT, M->ciT,
-                                             (double*)M->facT, M->diagT, s);
+#define MPK_TRANSPOSE(T, S, NNEG)                                                                            \
+  transpose_t<T, S, NNEG>(M->n, M->nnz, M->rp, M->ci, (const T*)M->fac, M->rpT, M->ciT, (T*)M->facT, M->diagT, s)
+  if (M->prec == MPK_ILU_MP) {
+    // w-component entries: the w imaginary components change sign
+    switch (M->wf * 2 + M->cp - 1) {
+      case 2: st = MPK_TRANSPOSE(double, 1, 0); break;
+      case 3: st = MPK_TRANSPOSE(double, 2, 1); break;
+      case 4: st = MPK_TRANSPOSE(double, 2, 0); break;
+      case 5: st = MPK_TRANSPOSE(double, 4, 2); break;
+      case 6: st = MPK_TRANSPOSE(double, 3, 0); break;
+      case 7: st = MPK_TRANSPOSE(double, 6, 3); break;
+      case 8: st = MPK_TRANSPOSE(double, 4, 0); break;
+      default: st = MPK_TRANSPOSE(double, 8, 4); break;
+    }
+  } else if (M->prec == MPK_ILU_FP64) {
+    st = M->cp == 2 ? MPK_TRANSPOSE(double, 2, 1) : MPK_TRANSPOSE(double, 1, 0);
   } else if (M->prec == MPK_ILU_FP32) {
-    st = M->cp == 2 ? transpose_t<float, 2>(M->n, M->nnz, M->rp, M->ci, (const float*)M->fac, M->rpT, M->ciT,
-                                            (float*)M->facT, M->diagT, s)
-                    : transpose_t<float, 1>(M->n, M->nnz, M->rp, M->ci, (const float*)M->fac, M->rpT, M->ciT,
-                                            (float*)M->facT, M->diagT, s);
+    st = M->cp == 2 ? MPK_TRANSPOSE(float, 2, 1) : MPK_TRANSPOSE(float, 1, 0);
   } else {
-    st = M->cp == 2 ? transpose_t<uint16_t, 2>(M->n, M->nnz, M->rp, M->ci, (const uint16_t*)M->fac, M->rpT,
-                                               M->ciT, (uint16_t*)M->facT, M->diagT, s)
-                    : transpose_t<uint16_t, 1>(M->n, M->nnz, M->rp, M->ci, (const uint16_t*)M->fac, M->rpT,
-                                               M->ciT, (uint16_t*)M->facT, M->diagT, s);
+    st = M->cp == 2 ? MPK_TRANSPOSE(uint16_t, 2, 1) : MPK_TRANSPOSE(uint16_t, 1, 0);
   }
+#undef MPK_TRANSPOSE
   if (st != MPK_OK) return st;
   // pk also serves as the binary32 substitutions' result buffer: clear it before the epoch-stamped
   // ordering passes read it
@@ -632,7 +739,8 @@ int precond_apply(const mpk_ilu* M, const Ops* o, bool trans, const double* r, d
   launch_trsv_prep(v, done, s);
   int st;
   // M: unit lower L~ then upper U~ with division; M^H: lower U~^H with division then unit upper L~^H
-  if (M->prec == MPK_ILU_FP64) {
+  if (M->prec == MPK_ILU_MP && M->wf != o->w) return fail(MPK_INVALID_ARG, "a w-component factor needs the same w");
+  if (M->prec == MPK_ILU_FP64 || M->prec == MPK_ILU_MP) {
     st = o->trsv_mp(v, true, !trans, r, M->vmp, done, s);
     if (st == MPK_OK) st = o->trsv_mp(v, false, trans, M->vmp, z, done, s);
   } else {
@@ -768,7 +876,7 @@ IluHandleView mpk_ilu::view(bool trans) const {
   return v;
 }
 
-static int factor_impl(const mpk_csr* A, int prec, mpk_ilu** out, int* fail_row, cudaStream_t s) {
+static int factor_impl(const mpk_csr* A, int prec, int w, mpk_ilu** out, int* fail_row, cudaStream_t s) {
   const int n = A->n, nnz = A->nnz, cp = A->is_complex ? 2 : 1;
   int head[2] = {-1, -1};
   MPK_CUDA(cudaMemcpyAsync(&head[0], A->row_ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -782,6 +890,7 @@ static int factor_impl(const mpk_csr* A, int prec, mpk_ilu** out, int* fail_row,
   M->nnz = nnz;
   M->cp = cp;
   M->prec = prec;
+  M->wf = prec == MPK_ILU_MP ? w : 1;
   auto bail = [&](int st) {
     free_handle(M);
     return st;
@@ -827,7 +936,12 @@ static int factor_impl(const mpk_csr* A, int prec, mpk_ilu** out, int* fail_row,
 
   const int64_t m = (int64_t)nnz * cp;
   void* work = nullptr;  // factor in its computation type
-  if (prec == MPK_ILU_FP64) {
+  if (prec == MPK_ILU_MP) {
+    const int64_t mw = m * w;
+    MPK_TRY(cudaMalloc(&work, sizeof(double) * (size_t)(mw > 0 ? mw : 1)));
+    count_launch();
+    k_to_mp<<<grid_for((int)((mw + 3) / 4)), kBlock, 0, s>>>(nnz, cp, w, A->val, (double*)work);
+  } else if (prec == MPK_ILU_FP64) {
     MPK_TRY(cudaMalloc(&work, sizeof(double) * (size_t)(m > 0 ? m : 1)));
     MPK_TRY(cudaMemcpyAsync(work, A->val, sizeof(double) * (size_t)m, cudaMemcpyDeviceToDevice, s));
   } else {
@@ -839,11 +953,14 @@ static int factor_impl(const mpk_csr* A, int prec, mpk_ilu** out, int* fail_row,
   MPK_TRY(cudaMemsetAsync(M->ctl + CTL_TICKET_LO, 0, sizeof(int), s));
   static int blocks_d1 = persistent_blocks(k_ilu<double, 1>), blocks_d2 = persistent_blocks(k_ilu<double, 2>);
   static int blocks_f1 = persistent_blocks(k_ilu<float, 1>), blocks_f2 = persistent_blocks(k_ilu<float, 2>);
-  count_launch();
-  if (prec == MPK_ILU_FP64) {
+  if (prec == MPK_ILU_MP) {
+    launch_ilu_mp(w, cp, n, M->rp, M->ci, M->diag, M->view(false).lv_lo, (double*)work, M->ctl, s);
+  } else if (prec == MPK_ILU_FP64) {
+    count_launch();
     if (cp == 1) k_ilu<double, 1><<<blocks_d1, kBlock, 0, s>>>(n, M->rp, M->ci, M->diag, M->view(false).lv_lo, (double*)work, M->ctl);
     else k_ilu<double, 2><<<blocks_d2, kBlock, 0, s>>>(n, M->rp, M->ci, M->diag, M->view(false).lv_lo, (double*)work, M->ctl);
   } else {
+    count_launch();
     if (cp == 1) k_ilu<float, 1><<<blocks_f1, kBlock, 0, s>>>(n, M->rp, M->ci, M->diag, M->view(false).lv_lo, (float*)work, M->ctl);
     else k_ilu<float, 2><<<blocks_f2, kBlock, 0, s>>>(n, M->rp, M->ci, M->diag, M->view(false).lv_lo, (float*)work, M->ctl);
   }
@@ -866,7 +983,7 @@ static int factor_impl(const mpk_csr* A, int prec, mpk_ilu** out, int* fail_row,
     cudaFree(work);
     M->fac = h;
   }
-  if (prec == MPK_ILU_FP64) {
+  if (prec == MPK_ILU_FP64 || prec == MPK_ILU_MP) {
     MPK_TRY(cudaMalloc((void**)&M->vmp, sizeof(double) * (size_t)n * cp * 4));
   } else {
     MPK_TRY(cudaMalloc((void**)&M->v32, sizeof(float) * (size_t)n * cp));
@@ -891,7 +1008,18 @@ extern "C" int mpk_ilu0_factor(const mpk_csr* A, int prec, mpk_ilu** out, int* f
   if (A->is_complex != 0 && A->is_complex != 1) return fail(MPK_INVALID_ARG, "is_complex must be 0 or 1");
   if (prec != MPK_ILU_FP64 && prec != MPK_ILU_FP32 && prec != MPK_ILU_BF16)
     return fail(MPK_INVALID_ARG, "prec must be MPK_ILU_FP64, MPK_ILU_FP32 or MPK_ILU_BF16");
-  return factor_impl(A, prec, out, fail_row, (cudaStream_t)stream);
+  return factor_impl(A, prec, 1, out, fail_row, (cudaStream_t)stream);
+}
+
+extern "C" int mpk_ilu0_factor_mp(const mpk_csr* A, int w, mpk_ilu** out, int* fail_row, void* stream) {
+  if (fail_row) *fail_row = -1;
+  if (out) *out = nullptr;
+  if (A == nullptr || out == nullptr) return fail(MPK_INVALID_ARG, "null argument");
+  if (A->n < 1 || A->nnz < 0 || A->row_ptr == nullptr || (A->nnz > 0 && (A->col_idx == nullptr || A->val == nullptr)))
+    return fail(MPK_INVALID_ARG, "invalid CSR descriptor");
+  if (A->is_complex != 0 && A->is_complex != 1) return fail(MPK_INVALID_ARG, "is_complex must be 0 or 1");
+  if (w < 1 || w > 4) return fail(MPK_INVALID_ARG, "w must be 1..4");
+  return factor_impl(A, MPK_ILU_MP, w, out, fail_row, (cudaStream_t)stream);
 }
 
 extern "C" int mpk_ilu0_values(const mpk_ilu* M, double* out_dev, void* stream) {
@@ -899,6 +1027,10 @@ extern "C" int mpk_ilu0_values(const mpk_ilu* M, double* out_dev, void* stream) 
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t m = (int64_t)M->nnz * M->cp;
   if (m == 0) return MPK_OK;
+  if (M->prec == MPK_ILU_MP) {
+    MPK_CUDA(cudaMemcpyAsync(out_dev, M->fac, sizeof(double) * (size_t)m * M->wf, cudaMemcpyDeviceToDevice, s));
+    return MPK_OK;
+  }
   const int g = grid_for((int)((m + 3) / 4));
   count_launch();
   if (M->prec == MPK_ILU_FP64) k_widen<double><<<g, kBlock, 0, s>>>(m, (const double*)M->fac, out_dev);
@@ -909,6 +1041,8 @@ extern "C" int mpk_ilu0_values(const mpk_ilu* M, double* out_dev, void* stream) 
 }
 
 extern "C" int mpk_ilu0_prec(const mpk_ilu* M) { return M == nullptr ? -2 : M->prec; }
+
+extern "C" int mpk_ilu0_width(const mpk_ilu* M) { return M == nullptr ? -2 : M->wf; }
 
 extern "C" void mpk_ilu0_destroy(mpk_ilu* M) { free_handle(M); }
 

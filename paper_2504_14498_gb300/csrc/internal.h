@@ -26,6 +26,7 @@ struct Csr {  // device CSR view
   const double* val = nullptr;  // c doubles per entry
   int cplx = 0;
   const int* order = nullptr;   // SpMV: thread t computes row order[t] (nullptr: row t)
+  bool mm = false;              // SpMV with the entries promoted to the vectors' w components
 };
 
 // Scalar slots of a solve: each slot holds one number (up to 8 doubles).
@@ -132,7 +133,8 @@ struct Ops {
   // when it reaches nsys; hist: hist_stride doubles per system
   void (*scalar)(int method, int phase, double* S, int* st, double* hist, const int* done, int nsys, int hist_stride,
                  int* fin, int* alldone, cudaStream_t s);
-  // Substitutions with a binary64 factor and w-component vectors (the paper's "_d").
+  // Substitutions with a binary64 factor and w-component vectors (the paper's "_d"), or, for a
+  // MPK_ILU_MP handle, with a w-component factor.
   int (*trsv_mp)(const IluHandleView& M, bool lower, bool unit, const double* in, double* out, const int* done,
                  cudaStream_t s);
   // Substitutions with a binary32 / bfloat16 factor: lower (in: w-component, out: the handle's
@@ -168,7 +170,8 @@ struct IluHandleView {
   const int* rp = nullptr;
   const int* ci = nullptr;
   const int* diag = nullptr;
-  const void* fac = nullptr;   // double / float / uint16 (bfloat16), cp values per entry
+  const void* fac = nullptr;   // double / float / uint16 (bfloat16), cp values per entry;
+                               // MPK_ILU_MP: cp * w doubles (w real components, then imaginary)
   int* flags = nullptr;        // n: epoch stamps of finished rows
   int* ctl = nullptr;          // device control words, see CtlIdx
   float* v32 = nullptr;        // n*cp binary32 intermediate
@@ -202,6 +205,7 @@ LevelOrder level_view(int* buf, int n, int nlevels);
 // The opaque handle.
 struct mpk_ilu {
   int n = 0, nnz = 0, cp = 1, prec = 0;
+  int wf = 1;  // components per factor value (MPK_ILU_MP: the w it was built for)
   int* rp = nullptr;
   int* ci = nullptr;
   int* diag = nullptr;
@@ -224,4 +228,5 @@ struct mpk_ilu {
   int wpb = 4;                   // warps per SM of the substitution kernels (autotuned per pattern)
   const void* src_rp = nullptr;  // the factored matrix's row_ptr address: the tuning cache's key
   mpk::IluHandleView view(bool trans) const;
+  int vals_per_entry() const { return cp * wf; }  // doubles (or narrower values) per factor entry
 };

@@ -53,7 +53,10 @@ __device__ __forceinline__ N<W, CP> warp_sum(N<W, CP> a) {  // fixed tree order
 // y = A x  (b != nullptr: y = b - A x), one thread per row, CSR order from 0.
 // ---------------------------------------------------------------------------------------------
 // A batch (sysid != nullptr) skips the rows of systems whose state sst has ST_DONE set.
-template <int W, int CP>
+// MM: the matrix entry is promoted to a W-component number (a, 0, ..., 0), same value, and the
+// product is the format's full multiplication with the matrix entry first (the paper's rows
+// without "_d", whose matrices are held in the vectors' type).
+template <int W, int CP, bool MM>
 __global__ void __launch_bounds__(kBlock) k_spmv(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                                  const double* __restrict__ val, const double* __restrict__ x,
                                                  double* __restrict__ y, const double* __restrict__ b,
@@ -78,7 +81,14 @@ __global__ void __launch_bounds__(kBlock) k_spmv(int n, const int* __restrict__ 
       ar = v.x;
       ai = v.y;
     }
-    acc = n_add<W, CP>(acc, n_mul_fp<W, CP>(n_load<W, CP>(x, j), ar, ai));
+    if constexpr (MM) {
+      N<W, CP> a = n_zero<W, CP>();
+      a.re.c[0] = ar;
+      a.im.c[0] = ai;
+      acc = n_add<W, CP>(acc, n_mul<W, CP>(a, n_load<W, CP>(x, j)));
+    } else {
+      acc = n_add<W, CP>(acc, n_mul_fp<W, CP>(n_load<W, CP>(x, j), ar, ai));
+    }
   }
   if (b != nullptr) acc = n_add<W, CP>(n_load<W, CP>(b, i), n_mul<W, CP>(n_real<W, CP>(-1.0), acc));
   n_store<W, CP>(y, i, acc);
@@ -902,12 +912,16 @@ __device__ __forceinline__ void wait_pause(long long t0, int ns) {
   if (clock64() - t0 > kSpinCycles) __nanosleep(ns);
 }
 
-template <int W, int CP, int WPB>
+// MF (MPK_ILU_MP handle): the factor values are w-component numbers (CP * W doubles per slot)
+// and row i computes acc -= f_ij * out_j with the factor first in the product, then
+// acc /= f_ii, both in w-component arithmetic; fewer entries per group keep the values in
+// registers.
+template <int W, int CP, int WPB, bool MF>
 __global__ void __launch_bounds__(WPB * 32, 1)
     k_trsv_mp(IluHandleView M, bool lower, bool unit, const double* __restrict__ in, double* __restrict__ out,
               const int* __restrict__ done) {
   if (is_done(done)) return;
-  constexpr int KG = 4;  // entries per group
+  constexpr int KG = (MF && W * CP >= 4) ? 2 : 4;  // entries per group
   const unsigned FULL = 0xffffffffu;
   const SellTri T = lower ? M.sl_lo : M.sl_up;
   const double* __restrict__ tval = (const double*)T.val;
@@ -926,16 +940,19 @@ __global__ void __launch_bounds__(WPB * 32, 1)
     const int i = nx_i, b0 = nx_b0, w = nx_b1 - nx_b0, rep = nx_rep;
     int jj[KG];
     double fr[KG], fi[KG];
+    N<W, CP> fv[MF ? KG : 1];
     auto load_group = [&](int k0) {
 #pragma unroll
       for (int k = 0; k < KG; ++k) {
         jj[k] = -1;
         fr[k] = 0.0;
         fi[k] = 0.0;
+        if constexpr (MF) fv[k] = n_zero<W, CP>();
         if (k0 + k < w) {
           const int64_t e = ((int64_t)(b0 + k0 + k) << 5) + lane;
           jj[k] = T.col[e];
-          if constexpr (CP == 1) fr[k] = tval[e];
+          if constexpr (MF) fv[k] = n_load<W, CP>(tval, e);
+          else if constexpr (CP == 1) fr[k] = tval[e];
           else { fr[k] = tval[2 * e]; fi[k] = tval[2 * e + 1]; }
         }
       }
@@ -943,11 +960,13 @@ __global__ void __launch_bounds__(WPB * 32, 1)
     load_group(0);
     N<W, CP> acc = n_zero<W, CP>();
     double dr = 1.0, di = 0.0;
+    N<W, CP> dv = n_real<W, CP>(1.0);
     if (i >= 0) {
       acc = n_load<W, CP>(in, i);
       if (!unit) {
         const int64_t q = ((int64_t)chunk << 5) + lane;
-        if constexpr (CP == 1) dr = tdia[q];
+        if constexpr (MF) dv = n_load<W, CP>(tdia, q);
+        else if constexpr (CP == 1) dr = tdia[q];
         else { dr = tdia[2 * q]; di = tdia[2 * q + 1]; }
       }
     }
@@ -994,12 +1013,18 @@ __global__ void __launch_bounds__(WPB * 32, 1)
       __syncwarp();
       if (!timeout && i >= 0) {
 #pragma unroll
-        for (int k = 0; k < KG; ++k)
-          if (jj[k] >= 0) acc = n_sub<W, CP>(acc, n_mul_fp<W, CP>(v[k], fr[k], fi[k]));
+        for (int k = 0; k < KG; ++k) {
+          if (jj[k] < 0) continue;
+          if constexpr (MF) acc = n_sub<W, CP>(acc, n_mul<W, CP>(fv[k], v[k]));
+          else acc = n_sub<W, CP>(acc, n_mul_fp<W, CP>(v[k], fr[k], fi[k]));
+        }
       }
     }
     if (!timeout && i >= 0) {
-      if (!unit) acc = n_div_fp<W, CP>(acc, dr, di);
+      if (!unit) {
+        if constexpr (MF) acc = n_div<W, CP>(acc, dv);
+        else acc = n_div_fp<W, CP>(acc, dr, di);
+      }
       n_publish<W, CP>(out, i, acc);
     }
     if (__any_sync(FULL, timeout)) {
@@ -1213,9 +1238,9 @@ struct Launch {
   static void spmv(const Csr& A, const double* x, double* y, const double* b, const int* done, const Batch* bt,
                    cudaStream_t s) {
     count_launch();
-    k_spmv<W, CP><<<(A.n + kBlock - 1) / kBlock, kBlock, 0, s>>>(A.n, A.rp, A.ci, A.val, x, y, b, done,
-                                                                  bt ? bt->sysid : nullptr, bt ? bt->st : nullptr,
-                                                                  A.order);
+    auto fn = A.mm ? k_spmv<W, CP, true> : k_spmv<W, CP, false>;
+    fn<<<(A.n + kBlock - 1) / kBlock, kBlock, 0, s>>>(A.n, A.rp, A.ci, A.val, x, y, b, done, bt ? bt->sysid : nullptr,
+                                                       bt ? bt->st : nullptr, A.order);
   }
   template <int K>
   static void dotsK(int n, const double* const* a, const double* const* b, double* const* out, const DotWs& ws,
@@ -1295,12 +1320,13 @@ struct Launch {
     const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(sm_count()), dim3(wpb * 32), args, 0, s);
     return e == cudaSuccess ? MPK_OK : MPK_CUDA_ERROR;
   }
+  template <bool MF>
   static const void* mp_fn(int wpb) {
     switch (wpb) {
-      case 8: return (const void*)k_trsv_mp<W, CP, 8>;
-      case 16: return (const void*)k_trsv_mp<W, CP, 16>;
-      case 32: return (const void*)k_trsv_mp<W, CP, 32>;
-      default: return (const void*)k_trsv_mp<W, CP, 4>;
+      case 8: return (const void*)k_trsv_mp<W, CP, 8, MF>;
+      case 16: return (const void*)k_trsv_mp<W, CP, 16, MF>;
+      case 32: return (const void*)k_trsv_mp<W, CP, 32, MF>;
+      default: return (const void*)k_trsv_mp<W, CP, 4, MF>;
     }
   }
   template <typename TS>
@@ -1317,7 +1343,8 @@ struct Launch {
     // out starts as sentinels: completion is read from the values
     count_launch();
     k_fill_sent<<<grid_for(M.n), kBlock, 0, s>>>((int64_t)M.n * CP * W, out, 0, nullptr, done);
-    return coop(mp_fn(M.wpb), M.wpb, M, lower, unit, in, out, done, s);
+    const void* fn = M.prec == MPK_ILU_MP ? mp_fn<true>(M.wpb) : mp_fn<false>(M.wpb);
+    return coop(fn, M.wpb, M, lower, unit, in, out, done, s);
   }
   static int trsv32(const IluHandleView& M, bool lower, bool unit, const double* in, double* out, const int* done,
                     cudaStream_t s) {
@@ -1330,7 +1357,9 @@ struct Launch {
   }
   // largest per-SM warp count whose block fits one SM, for each candidate (0: does not fit)
   static int trsv_fits(int prec, int wpb) {
-    const void* fn = prec == MPK_ILU_FP64 ? mp_fn(wpb) : (prec == MPK_ILU_BF16 ? lp_fn<uint16_t>(wpb) : lp_fn<float>(wpb));
+    const void* fn = prec == MPK_ILU_FP64 ? mp_fn<false>(wpb)
+                     : prec == MPK_ILU_MP ? mp_fn<true>(wpb)
+                     : (prec == MPK_ILU_BF16 ? lp_fn<uint16_t>(wpb) : lp_fn<float>(wpb));
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, wpb * 32, 0) != cudaSuccess) {
       cudaGetLastError();

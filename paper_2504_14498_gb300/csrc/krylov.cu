@@ -356,6 +356,35 @@ __global__ void k_batch_bsys(int nsys, const int* __restrict__ boff, int* __rest
     for (int b = boff[sy] + threadIdx.x; b < boff[sy + 1]; b += blockDim.x) bsys[b] = sy;
 }
 
+// Whether A equals its conjugate transpose: every entry (i, j) has its mirror (j, i) with the
+// conjugate value (compared as numbers).  Columns are sorted within rows (validated), so the
+// mirror is found by bisection.  *not_h is set to 1 on the first mismatch.
+__global__ void k_hermitian(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                            const double* __restrict__ val, int cplx, int* __restrict__ not_h) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      const int j = ci[p];
+      if (j < 0 || j >= n) {
+        atomicOr(not_h, 1);
+        return;
+      }
+      int lo = rp[j], hi = rp[j + 1];  // first position in row j with column >= i
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (ci[mid] < i) lo = mid + 1;
+        else hi = mid;
+      }
+      bool ok = lo < rp[j + 1] && ci[lo] == i;
+      if (ok) ok = cplx ? (val[2 * (int64_t)lo] == val[2 * (int64_t)p] && val[2 * (int64_t)lo + 1] == -val[2 * (int64_t)p + 1])
+                        : val[lo] == val[p];
+      if (!ok) {
+        atomicOr(not_h, 1);
+        return;
+      }
+    }
+  }
+}
+
 // nsys == 1 and roff_host == nullptr: one system.  Otherwise A is block-diagonal with the systems'
 // rows at roff_host[s] .. roff_host[s+1]-1 (host copy) / roff_dev (device copy); infos has nsys
 // entries; hist_dev (nullable) nsys * (maxit + 1) doubles.
@@ -404,6 +433,7 @@ static int solve_impl(int method, int w, const mpk_csr* Ac, const mpk_ilu* Mc, c
   Ctx c;
   c.o = o;
   c.A = Csr{n, Ac->nnz, Ac->row_ptr, Ac->col_idx, Ac->val, Ac->is_complex};
+  c.A.mm = (opts->flags & MPK_FLAG_MP_MATRIX) != 0;
   c.M = M;
   c.method = method;
   c.n = n;
@@ -502,7 +532,21 @@ static int solve_impl(int method, int w, const mpk_csr* Ac, const mpk_ilu* Mc, c
   }
 
   int* ahbuf = nullptr;
-  if (method == MPK_BICG) {  // A^H for q~ = A^H p~ (block-diagonal stays block-diagonal)
+  int hermitian = 0;
+  if (method == MPK_BICG) {  // A = A^H: q~ = A^H p~ multiplies by A itself (its rows are A^H's)
+    int* flag = nullptr;
+    MPK_CUDA(cudaMallocAsync((void**)&flag, sizeof(int), s));
+    MPK_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    count_launch();
+    k_hermitian<<<(n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096, 256, 0, s>>>(n, Ac->row_ptr, Ac->col_idx, Ac->val, Ac->is_complex, flag);
+    int not_h = 1;
+    MPK_CUDA(cudaMemcpyAsync(&not_h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MPK_CUDA(cudaFreeAsync(flag, s));
+    MPK_CUDA(cudaStreamSynchronize(s));
+    hermitian = not_h == 0;
+    if (hermitian) c.AH = c.A;
+  }
+  if (method == MPK_BICG && !hermitian) {  // A^H for q~ = A^H p~ (block-diagonal stays block-diagonal)
     const size_t nnz = (size_t)Ac->nnz;
     MPK_CUDA(cudaMallocAsync((void**)&ahbuf, sizeof(int) * ((size_t)n + 1 + nnz) + sizeof(double) * nnz * cp + 16, s));
     int* rpT = ahbuf;
@@ -511,6 +555,7 @@ static int solve_impl(int method, int w, const mpk_csr* Ac, const mpk_ilu* Mc, c
     int st = transpose_matrix(c.A, rpT, ciT, vT, s);
     if (st != MPK_OK) return st;
     c.AH = Csr{n, Ac->nnz, rpT, ciT, vT, Ac->is_complex};
+    c.AH.mm = c.A.mm;
   }
 
   {
@@ -663,6 +708,7 @@ static int solve_impl(int method, int w, const mpk_csr* Ac, const mpk_ilu* Mc, c
     if (dev_err != MPK_OK) info.status = dev_err;
     info.fail_row = -1;
     info.graph = gexec_used ? 1 : 0;
+    info.hermitian = hermitian;
     info.res0 = r0n;
     info.relres_rec = r0n > 0 ? Sy[S_NORM * kSlotDoubles] / r0n : 0.0;
     info.relres_true = r0n > 0 ? Sy[S_D4 * kSlotDoubles] / r0n : 0.0;
@@ -695,6 +741,8 @@ extern "C" int mpk_krylov_solve(int method, int w, const mpk_csr* A, const mpk_i
   if (opts->maxit < 0) return fail(MPK_INVALID_ARG, "maxit must be >= 0");
   if (M != nullptr && (M->n != A->n || M->cp != (A->is_complex ? 2 : 1)))
     return fail(MPK_INVALID_ARG, "preconditioner does not match the matrix");
+  if (M != nullptr && M->prec == MPK_ILU_MP && M->wf != w)
+    return fail(MPK_INVALID_ARG, "a w-component factor serves solves with the same w");
   int st = solve_impl(method, w, A, M, b_dev, x_dev, opts, info, (cudaStream_t)stream, 1, nullptr, nullptr);
   info->status = st;
   return st;
@@ -723,6 +771,8 @@ extern "C" int mpk_krylov_solve_batched(int method, int w, const mpk_csr* A, int
   if (opts->maxit < 0) return fail(MPK_INVALID_ARG, "maxit must be >= 0");
   if (M != nullptr && (M->n != A->n || M->cp != (A->is_complex ? 2 : 1)))
     return fail(MPK_INVALID_ARG, "preconditioner does not match the matrix");
+  if (M != nullptr && M->prec == MPK_ILU_MP && M->wf != w)
+    return fail(MPK_INVALID_ARG, "a w-component factor serves solves with the same w");
   return solve_impl(method, w, A, M, b_dev, x_dev, opts, infos, (cudaStream_t)stream, nsys, sys_rows_host,
                     sys_rows_dev);
 }
@@ -763,7 +813,8 @@ extern "C" int mpk_solve_host(int method, int w, int prec, int32_t n, int32_t is
   mpk_csr A{n, nnz, rp, ci, val, is_complex};
   mpk_ilu* M = nullptr;
   int st = MPK_OK;
-  if (prec != MPK_ILU_NONE) st = mpk_ilu0_factor(&A, prec, &M, &info->fail_row, s);
+  if (prec == MPK_ILU_MP) st = mpk_ilu0_factor_mp(&A, w, &M, &info->fail_row, s);
+  else if (prec != MPK_ILU_NONE) st = mpk_ilu0_factor(&A, prec, &M, &info->fail_row, s);
   if (st == MPK_OK) st = mpk_krylov_solve(method, w, &A, M, b, x, opts, info, s);
   if (M) mpk_ilu0_destroy(M);
   int fr = info->fail_row;

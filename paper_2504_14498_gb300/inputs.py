@@ -134,6 +134,35 @@ def helmholtz2d(m=1024, k=20 * math.pi, damping=0.5):
     return (n, rp, ci, va)
 
 
+def magnetic_laplacian2d(m, seed=SEED_BASE + 11, shift=-0.5, flux=1.0):
+    """Hermitian test system: the 5-point Laplacian of a charged particle in a random magnetic
+    field (a gauge Laplacian), h^2-scaled: diagonal 4 + shift, edge (i, j) couples with
+    -exp(i theta_ij) and its mirror with the exact conjugate -exp(-i theta_ij); theta ~
+    U(-pi flux, pi flux) per edge, seeded.  A = A^H exactly (the imaginary parts of mirrors are
+    exact negations); the random gauge lifts the spectrum's lower edge above the shifted 0."""
+    rng = np.random.default_rng(seed)
+    n = m * m
+    idx = np.arange(n)
+    ix, iy = idx % m, idx // m
+    th_e = rng.uniform(-math.pi * flux, math.pi * flux, size=n)  # edge to the east neighbour
+    th_n = rng.uniform(-math.pi * flux, math.pi * flux, size=n)  # edge to the north neighbour
+    ce, se = -np.cos(th_e), -np.sin(th_e)
+    cn, sn = -np.cos(th_n), -np.sin(th_n)
+    cols = np.full((n, 5), -1, dtype=np.int64)
+    vals = np.zeros((n, 5, 2))
+    s = iy > 0  # south neighbour: mirror of its north edge
+    cols[s, 0] = idx[s] - m; vals[s, 0, 0] = cn[idx[s] - m]; vals[s, 0, 1] = -sn[idx[s] - m]
+    w_ = ix > 0  # west neighbour: mirror of its east edge
+    cols[w_, 1] = idx[w_] - 1; vals[w_, 1, 0] = ce[idx[w_] - 1]; vals[w_, 1, 1] = -se[idx[w_] - 1]
+    cols[:, 2] = idx; vals[:, 2, 0] = 4.0 + shift
+    e = ix < m - 1
+    cols[e, 3] = idx[e] + 1; vals[e, 3, 0] = ce[idx[e]]; vals[e, 3, 1] = se[idx[e]]
+    nn = iy < m - 1
+    cols[nn, 4] = idx[nn] + m; vals[nn, 4, 0] = cn[idx[nn]]; vals[nn, 4, 1] = sn[idx[nn]]
+    rp, ci, va = _csr_from_rows(n, cols, vals)
+    return (n, rp, ci, va)
+
+
 def random_sparse(n, kmin=5, kmax=40, weak_frac=0.05, weak_factor=0.6, seed=SEED_BASE + 3, complex_=False):
     """Nonsymmetric random sparse system (diagonally dominant except the weakened rows)."""
     rng = np.random.default_rng(seed)
