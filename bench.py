@@ -58,12 +58,16 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=1, help="oracle iterations in the CPU sample")
-    ap.add_argument("--only", default=None, choices=["spmv", "precond_fp64", "precond_fp32", "precond_bf16", "ilu_fp64"],
+    ap.add_argument("--only", default=None, choices=["spmv", "spmv_mm", "precond_fp64", "precond_fp32", "precond_bf16",
+                                                     "precond_mp", "ilu_fp64", "ilu_mp"],
                     help="run just this kernel --reps times on the workload (for profiling) and exit")
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--workload", default="convdiff3d", choices=["convdiff3d", "batch512", "learned"],
+    ap.add_argument("--workload", default="convdiff3d", choices=["convdiff3d", "batch512", "learned", "plainrows"],
                     help="batch512: the batched workload (512 systems, binary32 ILU(0), DD BiCGSTAB); "
-                         "learned: train the learned ILU(0) correction, evaluate on held-out instances")
+                         "learned: train the learned ILU(0) correction, evaluate on held-out instances; "
+                         "plainrows: the paper's rows without \"_d\" against the \"_d\" rows (Table 4)")
+    ap.add_argument("--m-complex", type=int, default=1024, help="plainrows: Helmholtz grid points per axis")
+    ap.add_argument("--complex-iters", type=int, default=20, help="plainrows: Helmholtz iterations per solve")
     ap.add_argument("--train-instances", type=int, default=20000)
     ap.add_argument("--eval-instances", type=int, default=200)
     return ap.parse_args()
@@ -383,12 +387,15 @@ def run_only(args):
     A = _lib.Matrix.from_tuple(A_t)
     x = torch.as_tensor(inputs.random_vector(n, w, 1, seed=3), device="cuda")
     y = torch.empty_like(x)
-    if args.only == "spmv":
-        fn = lambda: _lib.spmv_mp(A, x, w, y)
+    if args.only in ("spmv", "spmv_mm"):
+        fn = lambda: _lib.spmv_mp(A, x, w, y, mp_matrix=args.only == "spmv_mm")
     elif args.only == "ilu_fp64":
         fn = lambda: _lib.ILU0(A, "fp64").close()
+    elif args.only == "ilu_mp":
+        fn = lambda: _lib.ILU0(A, "mp", w).close()
     else:
-        M = _lib.ILU0(A, args.only.split("_")[1])
+        prec = args.only.split("_")[1]
+        M = _lib.ILU0(A, prec, w) if prec == "mp" else _lib.ILU0(A, prec)
         fn = lambda: M.apply(x, w, False, y)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -458,6 +465,112 @@ def run_batch(args):
             "iters": {"min": int(its.min()), "median": float(np.median(its)), "max": int(its.max())},
             "relres_true_max": float(out["relres_true"].max()), "graph": out["graph"],
             "clocks": clk, "gpu_launches": int(launches), "s_generate_inputs": t_gen}
+    print(json.dumps(line))
+    return 0
+
+
+def _median_launch_s(fn, reps=10, warm=3):
+    """Median duration of fn() on the current stream (CUDA events), seconds."""
+    import torch
+
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, c in evs:
+        a.record()
+        fn()
+        c.record()
+    torch.cuda.synchronize()
+    return statistics.median(a.elapsed_time(c) for a, c in evs) / 1e3
+
+
+def run_plainrows(args):
+    """Table 4 on the GPU: the paper's plain rows ("ILU(0)": every SpMV with the matrix promoted to
+    w components, factor and substitutions in w components) against its "_d" rows ("ILU(0)_d":
+    mixed SpMV, binary64 factor), BiCGSTAB.  Real: the 128^3 convection-diffusion workload, DD
+    solved to 1e-25 (complete solves), TD / QD for a fixed number of iterations.  Complex: the
+    1024^2 shifted-Laplacian Helmholtz workload (thousands of iterations to converge), a fixed
+    number of iterations.  Reported per case: factorisation time, solve time, iterations, time per
+    iteration; value = the per-iteration time ratio ILU(0) / ILU(0)_d of the real DD solve (the
+    paper's Table 4 ratios are per-iteration ratios)."""
+    import torch
+
+    from paper_2504_14498_gb300 import _lib, inputs
+
+    torch.cuda.set_device(0)
+    cases = []
+
+    def run_case(name, A, A_t, c, w, row, tol, maxit):
+        n = A_t[0]
+        b = _lib.spmv_mp(A, torch.as_tensor(inputs.ones(n, w, c), device="cuda"), w)
+
+        def once():
+            f0, f1, s1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            f0.record()
+            M = _lib.ILU0(A, "fp64") if row == "d" else _lib.ILU0(A, "mp", w)
+            f1.record()
+            out = _lib.krylov_solve("bicgstab", w, A, M, b, tol_rel=tol, maxit=maxit, check_every=10,
+                                    history=False, mp_matrix=(row == "plain"))
+            s1.record()
+            torch.cuda.synchronize()
+            M.close()
+            return out, f0.elapsed_time(f1) / 1e3, f1.elapsed_time(s1) / 1e3
+
+        once()  # graph capture, autotuners
+        res = [once() for _ in range(max(1, args.steps))]
+        out = res[-1][0]
+        t_fac = statistics.median(r[1] for r in res)
+        t_sol = statistics.median(r[2] for r in res)
+        cases.append({"case": name, "row": "ILU(0)" if row == "plain" else "ILU(0)_d", "w": w, "c": c,
+                      "status": out["status"], "iters": out["iters"], "relres_true": out["relres_true"],
+                      "s_factor": t_fac, "s_solve": t_sol, "ms_per_iter": 1e3 * t_sol / max(1, out["iters"])})
+
+    A_t, meta = inputs.convdiff3d(args.m)
+    A = _lib.Matrix.from_tuple(A_t)
+    for w, tol, maxit in ((2, TOL, 20000), (3, 0.0, 5), (4, 0.0, 3)):
+        for row in ("d", "plain"):
+            run_case("convdiff3d_%d" % args.m, A, A_t, 1, w, row, tol, maxit)
+    # kernel roofline of the multi-component-factor substitution (DD, both triangles)
+    n, nnz = A_t[0], len(A_t[2])
+    nod = nnz - n
+    x = torch.as_tensor(inputs.random_vector(n, 2, 1, seed=3), device="cuda")
+    z = torch.empty_like(x)
+    Mmp = _lib.ILU0(A, "mp", 2)
+    M64 = _lib.ILU0(A, "fp64")
+    t_mp = _median_launch_s(lambda: Mmp.apply(x, 2, False, z))
+    t_64 = _median_launch_s(lambda: M64.apply(x, 2, False, z))
+    Mmp.close()
+    M64.close()
+    del A
+    # DW*DW 9 + DW+DW 14 per off-diagonal entry, DW/DW 18 per row (divisions counted as one op)
+    ops_mp = 23 * nod + 18 * n
+    ops_64 = 20 * nod + 10 * n
+    alu = FP64_PEAK_OPS
+    rl_mp = {"bound": "alu", "achieved": ops_mp / t_mp / 1e12, "peak": alu, "unit": "T FP64 op/s",
+             "frac": ops_mp / t_mp / 1e12 / alu, "traffic": None, "peak_note": "of derived nominal",
+             "work_per_launch": ops_mp, "s_per_launch": t_mp,
+             "unit_of_work": "binary64 operations of one M^-1 with the DD factor (k_trsv_mp, MF, x2)"}
+    H_t = inputs.helmholtz2d(args.m_complex, k=20 * np.pi * args.m_complex / 1024)
+    H = _lib.Matrix.from_tuple(H_t, is_complex=True)
+    for w, its in ((2, args.complex_iters), (4, 2)):
+        for row in ("d", "plain"):
+            run_case("helmholtz2d_%d" % args.m_complex, H, H_t, 2, w, row, 0.0, its)
+
+    def ratio(case, w):
+        d = [c_ for c_ in cases if c_["case"] == case and c_["w"] == w and c_["row"] == "ILU(0)_d"][0]
+        p = [c_ for c_ in cases if c_["case"] == case and c_["w"] == w and c_["row"] == "ILU(0)"][0]
+        return p["ms_per_iter"] / d["ms_per_iter"]
+
+    ratios = {"%s_w%d" % (c_["case"], c_["w"]): ratio(c_["case"], c_["w"]) for c_ in cases if c_["row"] == "ILU(0)"}
+    line = {"metric": "per-iteration time ratio ILU(0) / ILU(0)_d (paper's Table 4), DD BiCGSTAB on 128^3",
+            "value": ratios["convdiff3d_%d_w2" % args.m], "unit": "ratio", "higher_is_better": False,
+            "n_gpus": 1, "steps": args.steps, "data": "synthetic", "dtype": "f64",
+            "config": {"workload": "plain rows (matrix and factor in w components) vs _d rows (binary64 matrix "
+                                   "and factor): 128^3 convection-diffusion (DD complete solves to 1e-25; TD, QD "
+                                   "fixed iterations) and %d^2 complex Helmholtz (fixed iterations)" % args.m_complex},
+            "ratios": ratios, "cases": cases, "roofline_trsv_mp_factor": rl_mp,
+            "precond_s": {"mp_factor_dd": t_mp, "binary64_factor_dd": t_64}}
     print(json.dumps(line))
     return 0
 
@@ -574,6 +687,8 @@ def main():
         return run_learned(args)
     if args.workload == "batch512" and args.impl == "mpk":
         return run_batch(args)
+    if args.workload == "plainrows" and args.impl == "mpk":
+        return run_plainrows(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_mpk(args)

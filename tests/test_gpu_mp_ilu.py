@@ -1,5 +1,6 @@
-"""GPU parity of the multi-component ILU(0) (the paper's rows without "_d": factor entries,
-products and divisions in the solve's w-component arithmetic) against the oracle.
+"""GPU parity of the paper's plain rows (without "_d") against the oracle: the multi-component
+ILU(0) (factor entries, products and divisions in the solve's w-component arithmetic), the SpMV
+with the matrix promoted to w components, and the Hermitian case of BiCG.
 Bars:
   * factor: identical for w <= 2 (the kernel applies the KIJ updates in their sequential order,
     every step the same double-word algorithm); w = 3, 4 within 2^-150 / 2^-200 of the entry's
@@ -7,7 +8,11 @@ Bars:
   * substitutions M z = r and M^H z = r: identical for w <= 2, w = 3, 4 within 2^-190 of max |z|;
   * Krylov with the factor: identical runs for w = 2 (same operations in the same order),
     iteration counts within 5 % for w = 3, 4;
-  * a factor built for one w is refused by a solve with another w, and by the learned correction.
+  * a factor built for one w is refused by a solve with another w, and by the learned correction;
+  * SpMV with the matrix promoted to w components: identical for w <= 2, within 2^-150 / 2^-200
+    for w = 3, 4; whole solves of the plain rows (promoted matrix + multi-component factor),
+    single and batched, identical to the oracle's;
+  * Hermitian A: BiCG multiplies A^H p~ by A's own rows (reported), with identical results.
 Sizes span several 32-row chunks and 256-row tiles and end in a ragged tail.
 """
 import numpy as np
@@ -161,3 +166,90 @@ def test_mp_solve_host_end_to_end():
     assert out["status"] == ref["status"] == "OK"
     assert out["iters"] == ref["iters"]
     assert np.array_equal(out["x"], ref["x"])
+
+
+# ---- SpMV with the matrix promoted to w components (the rows without "_d") ----------------------
+
+@pytest.mark.parametrize("c", [1, 2])
+@pytest.mark.parametrize("w", [1, 2, 3, 4])
+def test_mp_matrix_spmv_parity(w, c):
+    A_t = inputs.random_sparse(3001, 3, 20, seed=91) if c == 1 else inputs.random_sparse(2003, 3, 12, seed=92,
+                                                                                        complex_=True)
+    n = A_t[0]
+    x = inputs.random_vector(n, w, c, seed=27 + w)
+    A = _lib.Matrix.from_tuple(A_t, is_complex=(c == 2))
+    y = host(_lib.spmv_mp(A, dev(x), w, mp_matrix=True))
+    ref = oracle.spmv(A_t, x, w, c, mp_matrix=True)
+    if w <= 2:
+        assert np.array_equal(y, ref)
+    else:
+        lead = np.abs(ref.reshape(n, c, w)[:, :, 0])
+        err = np.abs((y - ref).reshape(n, c, w)).sum(axis=2)
+        assert np.all(err <= TOL[w] * 64 * np.maximum(lead, np.max(lead) * 2.0 ** -30))
+
+
+@pytest.mark.parametrize("method", ["bicg", "cgs", "bicgstab", "gpbicg"])
+def test_plain_rows_identical(method):
+    """The paper's plain rows ("BiCG_ILU(0)" etc.): promoted matrix and multi-component factor."""
+    A_t = inputs.convdiff2d(33, pe=10.0)
+    n, w = A_t[0], 2
+    A = _lib.Matrix.from_tuple(A_t)
+    b_ref = oracle.spmv(A_t, inputs.ones(n, w), w)
+    out = _lib.krylov_solve(method, w, A, _lib.ILU0(A, "mp", w), dev(b_ref), tol_rel=1e-25, maxit=600, mp_matrix=True)
+    ref = oracle.krylov(method, A_t, b_ref, w, ilu="mp", tol_rel=1e-25, maxit=600, mp_matrix=True)
+    assert out["status"] == ref["status"] == "OK"
+    assert out["iters"] == ref["iters"]
+    assert np.array_equal(out["hist"], ref["hist"])
+    assert np.array_equal(host(out["x"]), ref["x"])
+    assert out["relres_true"] == ref["relres_true"]
+
+
+def test_plain_rows_batched_identical():
+    sys_ = [inputs.convdiff2d_random(m, 300 + m) for m in (12, 17, 23)]
+    B_t, roff = inputs.block_diagonal(sys_)
+    B_t = (B_t[0], B_t[1].astype(np.int32), B_t[2], B_t[3])
+    w = 2
+    B = _lib.Matrix.from_tuple(B_t)
+    b = np.concatenate([oracle.spmv(S, inputs.ones(S[0], w), w) for S in sys_])
+    out = _lib.krylov_solve_batched("bicgstab", w, B, roff, _lib.ILU0(B, "mp", w), dev(b), tol_rel=1e-25, maxit=400,
+                                    mp_matrix=True)
+    x = host(out["x"])
+    for k, S in enumerate(sys_):
+        ref = oracle.krylov("bicgstab", S, b[roff[k] * w:roff[k + 1] * w], w, ilu="mp", tol_rel=1e-25, maxit=400,
+                            mp_matrix=True)
+        assert out["statuses"][k] == ref["status"] == "OK"
+        assert out["iters"][k] == ref["iters"]
+        assert np.array_equal(x[roff[k] * w:roff[k + 1] * w], ref["x"])
+
+
+# ---- Hermitian systems ------------------------------------------------------------------------
+
+@pytest.mark.parametrize("ilu", ["fp64", "mp"])
+def test_hermitian_bicg_reuses_A(ilu):
+    A_t = inputs.magnetic_laplacian2d(31)
+    n, w, c = A_t[0], 2, 2
+    A = _lib.Matrix.from_tuple(A_t, is_complex=True)
+    b_ref = oracle.spmv(A_t, inputs.ones(n, w, c), w, c)
+    M = _lib.ILU0(A, ilu, w) if ilu == "mp" else _lib.ILU0(A, ilu)
+    out = _lib.krylov_solve("bicg", w, A, M, dev(b_ref), tol_rel=1e-25, maxit=600)
+    ref = oracle.krylov("bicg", A_t, b_ref, w, c, ilu=ilu, tol_rel=1e-25, maxit=600)
+    assert out["hermitian"]  # q~ = A^H p~ multiplied by A's own rows: no transpose built
+    assert out["status"] == ref["status"] == "OK"
+    assert out["iters"] == ref["iters"]
+    assert np.array_equal(out["hist"], ref["hist"])
+    assert np.array_equal(host(out["x"]), ref["x"])
+
+
+def test_non_hermitian_bicg_builds_transpose():
+    A_t = inputs.helmholtz2d(23, k=10.0)  # complex symmetric, not Hermitian
+    n, w = A_t[0], 2
+    A = _lib.Matrix.from_tuple(A_t, is_complex=True)
+    b = _lib.spmv_mp(A, dev(inputs.ones(n, w, 2)), w)
+    out = _lib.krylov_solve("bicg", w, A, _lib.ILU0(A, "fp64"), b, tol_rel=1e-20, maxit=300)
+    assert not out["hermitian"] and out["status"] == "OK"
+    # a real symmetric matrix is Hermitian
+    S_t = inputs.tridiag(300, -1.0, 2.5, -1.0)
+    S = _lib.Matrix.from_tuple(S_t)
+    bs = _lib.spmv_mp(S, dev(inputs.ones(300, w)), w)
+    o2 = _lib.krylov_solve("bicg", w, S, _lib.ILU0(S, "fp64"), bs, tol_rel=1e-25, maxit=300)
+    assert o2["hermitian"] and o2["status"] == "OK"
