@@ -1,0 +1,55 @@
+"""The paper-scale stand-ins on the GPU (Tables 1-2 shape), identical to the oracle's runs:
+unpreconditioned DD BiCGSTAB stops at 3n (same residual history), the "_d_ILU(0)" and plain
+"ILU(0)" rows converge in the oracle's iteration counts with the oracle's iterates."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2504_14498_gb300 import _lib, inputs
+
+pytestmark = pytest.mark.gpu
+
+KW = dict(tol_rel=1e-13, tol_abs=1e-100)
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def _pair(A_t, c, w, method, ilu, mm):
+    n = A_t[0]
+    A = _lib.Matrix.from_tuple(A_t, is_complex=(c == 2))
+    b = oracle.spmv(A_t, inputs.ones(n, w, c), w, c)
+    M = None
+    if ilu is not None:
+        M = _lib.ILU0(A, "mp", w) if ilu == "mp" else _lib.ILU0(A, ilu)
+    out = _lib.krylov_solve(method, w, A, M, dev(b), maxit=3 * n, mp_matrix=mm, **KW)
+    ref = oracle.krylov(method, A_t, b, w, c, ilu=ilu or "none", maxit=3 * n, mp_matrix=mm, **KW)
+    return out, ref
+
+
+@pytest.mark.parametrize("c", [1, 2])
+def test_unpreconditioned_stops_at_3n(c):
+    A_t = inputs.scaled_random_sparse() if c == 1 else inputs.scaled_helmholtz2d()
+    out, ref = _pair(A_t, c, 2, "bicgstab", None, False)
+    assert out["status"] == ref["status"] == "MAXIT" and out["iters"] == 3 * A_t[0]
+    assert np.array_equal(out["hist"], ref["hist"])
+
+
+@pytest.mark.parametrize("method", ["bicg", "cgs", "bicgstab", "gpbicg"])
+@pytest.mark.parametrize("row", ["d_ilu", "plain_ilu"])
+def test_real_standin_ilu_rows(method, row):
+    ilu, mm = ("fp64", False) if row == "d_ilu" else ("mp", True)
+    out, ref = _pair(inputs.scaled_random_sparse(), 1, 2, method, ilu, mm)
+    assert out["status"] == ref["status"] == "OK"
+    assert out["iters"] == ref["iters"]
+    assert np.array_equal(out["x"].cpu().numpy(), ref["x"])
+
+
+def test_complex_standin_bicg_ilu():
+    out, ref = _pair(inputs.scaled_helmholtz2d(), 2, 2, "bicg", "fp64", False)
+    assert out["status"] == ref["status"] == "OK"
+    assert out["iters"] == ref["iters"]
+    assert not out["hermitian"]
+    assert np.array_equal(out["x"].cpu().numpy(), ref["x"])
