@@ -69,6 +69,7 @@ def parse():
                          "plainrows: the paper's rows without \"_d\" against the \"_d\" rows (Table 4); "
                          "tables: Tables 1-2 at the paper's scale on stand-in matrices")
     ap.add_argument("--m-complex", type=int, default=1024, help="plainrows: Helmholtz grid points per axis")
+    ap.add_argument("--formats", default="DD", help="tables: comma-separated formats among DD,TD,QD")
     ap.add_argument("--complex-iters", type=int, default=20, help="plainrows: Helmholtz iterations per solve")
     ap.add_argument("--train-instances", type=int, default=20000)
     ap.add_argument("--eval-instances", type=int, default=200)
@@ -237,6 +238,7 @@ def run_mpk(args):
     def solve(prec):
         M = _lib.ILU0(A, prec)
         out = _lib.krylov_solve("bicgstab", w, A, M, b, tol_rel=TOL, maxit=20000, check_every=10, history=False)
+        out["schedule"] = M.schedule()
         M.close()
         return out
 
@@ -268,7 +270,8 @@ def run_mpk(args):
     last = outs[-1]
 
     extra = {"iters": last["iters"], "status": last["status"], "relres_true": last["relres_true"],
-             "relres_rec": last["relres_rec"]}
+             "relres_rec": last["relres_rec"],
+             "substitution_schedule": {"schedule": last["schedule"][0], "warps_per_sm": last["schedule"][1]}}
     # ---- variants: other factor precisions at equal final accuracy ----------------------------
     variants = {}
     if not args.no_variants:
@@ -285,7 +288,7 @@ def run_mpk(args):
             v1.record()
             torch.cuda.synchronize()
             variants[prec] = {"s": v0.elapsed_time(v1) / reps / 1e3, "iters": o["iters"], "status": o["status"],
-                              "relres_true": o["relres_true"]}
+                              "relres_true": o["relres_true"], "substitution_schedule": list(o["schedule"])}
 
     # ---- kernel rooflines (CUDA events on the launching stream) -------------------------------
     def time_launches(fn, reps=20, warm=5):
@@ -579,7 +582,8 @@ def run_plainrows(args):
 
 def run_tables(args):
     """Tables 1 and 2 at the paper's scale on the GPU: the real stand-in (n = 765) and the complex
-    stand-in (n = 961) solved by BiCG, CGS, BiCGSTAB and GPBiCG in DD, TD and QD, for the rows
+    stand-in (n = 961) solved by BiCG, CGS, BiCGSTAB and GPBiCG in the formats of --formats (DD by
+    default; TD and QD take minutes: exact expansion arithmetic over 3n iterations), for the rows
     "_d" (mixed SpMV, no preconditioner), "_d_ILU(0)" (binary64 factor), plain (matrix in the
     vectors' format, no preconditioner) and "ILU(0)" (matrix and factor in the vectors' format);
     eps_r = 1e-13, eps_a = 1e-100, maxit = 3n, x* = ones.  Columns as the paper's: [1] iterations,
@@ -595,7 +599,7 @@ def run_tables(args):
                          ("complex n=961", inputs.scaled_helmholtz2d(), 2)):
         A = _lib.Matrix.from_tuple(A_t, is_complex=(c == 2))
         n = A_t[0]
-        for w in (2, 3, 4):
+        for w in [{"DD": 2, "TD": 3, "QD": 4}[f] for f in args.formats.split(",")]:
             b = _lib.spmv_mp(A, torch.as_tensor(inputs.ones(n, w, c), device="cuda"), w)
             for method in ("bicg", "cgs", "bicgstab", "gpbicg"):
                 for row, ilu, mm in (("_d", None, False), ("_d_ILU(0)", "fp64", False), ("", None, True),
@@ -614,8 +618,11 @@ def run_tables(args):
                             M.close()
                         return out, e0.elapsed_time(e1) / 1e3
 
-                    once()
+                    if w == 2:
+                        once()  # untimed: graph capture and tuning (DD; TD / QD runs are long enough)
                     out, t = once()
+                    print("%s %s %s%s: %s %d it %.3f s" % (name, w, method, row, out["status"], out["iters"], t),
+                          file=sys.stderr, flush=True)
                     rows_out.append({"matrix": name, "format": {2: "DD", 3: "TD", 4: "QD"}[w],
                                      "algorithm": {"bicg": "BiCG", "cgs": "CGS", "bicgstab": "BiCGSTAB",
                                                    "gpbicg": "GPBiCG"}[method] + row,
@@ -627,7 +634,7 @@ def run_tables(args):
             "value": float(sum(r["status"] == "OK" for r in conv)) / len(conv), "unit": "fraction of ILU(0) rows converged",
             "higher_is_better": True, "n_gpus": 1, "data": "synthetic", "dtype": "f64",
             "config": {"workload": "stand-ins for the paper's real (n 765) and complex (n 961) matrices; BiCG, CGS, "
-                                   "BiCGSTAB, GPBiCG in DD/TD/QD; eps_r 1e-13, eps_a 1e-100, maxit 3n"},
+                                   "BiCGSTAB, GPBiCG in %s; eps_r 1e-13, eps_a 1e-100, maxit 3n" % args.formats},
             "unpreconditioned_at_maxit": int(sum(r["status"] == "MAXIT" for r in rows_out if "ILU" not in r["algorithm"])),
             "unpreconditioned_rows": int(sum("ILU" not in r["algorithm"] for r in rows_out)),
             "rows": rows_out}

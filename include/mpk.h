@@ -194,6 +194,14 @@ int mpk_ilu0_prec(const mpk_ilu* M);
 /* Components per factor value: w for a MPK_ILU_MP handle, 1 otherwise; -2 for NULL. */
 int mpk_ilu0_width(const mpk_ilu* M);
 
+/* Substitution schedule the handle last used or was tuned to: 0 = static chunk schedule (every
+ * level's chunks dealt over all SMs), 1 = owner-block schedule (contiguous row blocks per SM,
+ * levels separated by block barriers, shared-memory values for dependencies inside a block);
+ * *wpb_out (if not NULL): warps per SM.  -2 for NULL.  Both give identical results; a solve
+ * times both once per matrix pattern and keeps the faster (environment MPK_SUBST_SCHEDULE=
+ * static|owner restricts the choice). */
+int mpk_ilu0_schedule(const mpk_ilu* M, int* wpb_out);
+
 void mpk_ilu0_destroy(mpk_ilu* M);
 
 /* z = M^-1 r (trans = 0) or z = M^-H r (trans = 1) with M = L~U~ (Algorithm 2; the M^H solve

@@ -59,6 +59,7 @@ SIGNATURES = [
     ("mpk_ilu0_values", _I, [_VP, _VP, _VP]),
     ("mpk_ilu0_prec", _I, [_VP]),
     ("mpk_ilu0_width", _I, [_VP]),
+    ("mpk_ilu0_schedule", _I, [_VP, ctypes.POINTER(_I)]),
     ("mpk_ilu0_destroy", None, [_VP]),
     ("mpk_precond_apply", _I, [_VP, _I, _I, _VP, _VP, _VP]),
     ("mpk_krylov_solve", _I, [_I, _I, ctypes.POINTER(CsrDesc), _VP, _VP, _VP, ctypes.POINTER(Opts),
@@ -181,6 +182,12 @@ class ILU0:
         if st != 0:
             raise MpkError(st, lib().mpk_last_error().decode() + " (row %d)" % fr.value)
         self.handle = h
+
+    def schedule(self):
+        """(schedule, warps per SM) of the substitutions: 'static' or 'owner'."""
+        wpb = ctypes.c_int(0)
+        sc = lib().mpk_ilu0_schedule(self.handle, ctypes.byref(wpb))
+        return ("static", "owner")[sc], wpb.value
 
     def values(self) -> torch.Tensor:
         out = torch.empty(self.A.nnz * self.A.cp * self.w, dtype=torch.float64, device="cuda")

@@ -485,19 +485,21 @@ __global__ void k_level_scatter(int n, const int* __restrict__ depth, const int*
 // (every row depends on earlier rows only: a valid order for it), then a counting sort by
 // (level, length) places them, every level padded to whole 32-row chunks.
 static int build_levels(int n, const int* rp, const int* ci, const int* diag, unsigned long long* pk, int* ctl,
-                        int which, int** bufs, int* nlev, cudaStream_t s) {
+                        int which, int** bufs, int* nlev, int** depths, cudaStream_t s) {
   const int m = (n + 31) >> 5;
   const size_t L = (size_t)n + 1;
   int* tmp = nullptr;
   MPK_CUDA(cudaMallocAsync((void**)&tmp, sizeof(int) * (2 * L + (size_t)m * 32 + (size_t)n + 16), s));
-  int* depth = tmp;                      // L
-  int* cnt = depth + L;                  // L
+  int* cnt = tmp + L;                    // L
   int* perm_c = cnt + L;                 // 32 m
   int* pos_c = perm_c + (size_t)m * 32;  // n
   int* maxd = pos_c + n;                 // 1
   static int blocks_rd = persistent_blocks(k_row_depth);
   for (int tri = 0; tri < 2; ++tri) {
     const bool lower = tri == 0;
+    int* depth = nullptr;  // kept: the owner-block layout groups rows by level
+    MPK_CUDA(cudaMalloc((void**)&depth, sizeof(int) * L));
+    depths[tri] = depth;
     MPK_CUDA(cudaMemsetAsync(ctl + CTL_TICKET_LO, 0, sizeof(int), s));
     MPK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * L, s));
     MPK_CUDA(cudaMemsetAsync(maxd, 0, sizeof(int), s));
@@ -567,13 +569,21 @@ __global__ void k_sell_width(int nchunks, const int* __restrict__ perm, const in
 // Also records, per chunk, the dependency with the largest level-order position (rep): the
 // substitution polls that one value before checking all the others.  The 32 positions of a chunk
 // are the 32 lanes of one warp (blockDim and the stride are multiples of 32).
+// Owner-block layout (enc.blk != nullptr): a dependency on a row of the same block whose value
+// is still in the block's ring when this row's group runs (its position + kRing reaches the end
+// of the group, enc.cgend of the chunk) is encoded as -2 - ring slot and left out of rep.
+struct ObEnc {
+  const int* blk = nullptr;     // row -> owner block
+  const int* bstart = nullptr;  // block -> first position
+  const int* cgend = nullptr;   // chunk -> end position of its group
+};
 __device__ __forceinline__ double one_of(double) { return 1.0; }
 __device__ __forceinline__ float one_of(float) { return 1.0f; }
 __device__ __forceinline__ uint16_t one_of(uint16_t) { return (uint16_t)0x3F80u; }  // bfloat16 1.0
 template <typename T, int CP>
 __global__ void k_sell_fill(int nchunks, const int* __restrict__ perm, const int* __restrict__ pos,
                             const int* __restrict__ rp, const int* __restrict__ ci, const int* __restrict__ diag,
-                            const T* __restrict__ fac, bool lower, const int* __restrict__ coff,
+                            const T* __restrict__ fac, bool lower, const int* __restrict__ coff, ObEnc enc,
                             int* __restrict__ col, T* __restrict__ val, T* __restrict__ dia, int* __restrict__ rep) {
   const int64_t P = (int64_t)nchunks * 32;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < P; q += (int64_t)gridDim.x * blockDim.x) {
@@ -585,11 +595,22 @@ __global__ void k_sell_fill(int nchunks, const int* __restrict__ perm, const int
       len = lower ? diag[i] - rp[i] : rp[i + 1] - diag[i] - 1;
     }
     const int b0 = coff[c], w = coff[c + 1] - b0;
+    const int bi = (enc.blk != nullptr && i >= 0) ? enc.blk[i] : -1;
+    const int gend = enc.blk != nullptr ? enc.cgend[c] : 0;
     int last = -1;
     for (int k = 0; k < w; ++k) {
       const int64_t e = ((int64_t)(b0 + k) << 5) + lane;
-      col[e] = k < len ? ci[p + k] : -1;
-      if (k < len) last = max(last, pos[ci[p + k]]);
+      int cv = -1;
+      if (k < len) {
+        const int j = ci[p + k], qj = pos[j];
+        if (bi >= 0 && enc.blk[j] == bi && qj + kRing >= gend) {
+          cv = -2 - (qj - enc.bstart[bi]) % kRing;
+        } else {
+          cv = j;
+          last = max(last, qj);
+        }
+      }
+      col[e] = cv;
 #pragma unroll
       for (int t = 0; t < CP; ++t) val[e * CP + t] = k < len ? fac[(int64_t)(p + k) * CP + t] : T(0);
     }
@@ -601,20 +622,18 @@ __global__ void k_sell_fill(int nchunks, const int* __restrict__ perm, const int
   }
 }
 
-// Repack one triangle of (rp, ci, diag, fac) in the positions of its level order into *buf
-// (allocated here) and describe it in *out; cp values of type T per entry.
+// Repack one triangle of (rp, ci, diag, fac) in the positions of the order (perm, pos, nch
+// chunks) into *buf (allocated here) and describe it in *out; cp values of type T per entry.
 template <typename T>
-static int build_sell(int n, int cp, const int* rp, const int* ci, const int* diag, const T* fac, int* lvbuf,
-                      int nlevels, bool lower, void** buf, SellTri* out, cudaStream_t s) {
-  const LevelOrder lo = level_view(lvbuf, n, nlevels);
-  int nch = 0;
-  MPK_CUDA(cudaMemcpyAsync(&nch, lo.nchunks, sizeof(int), cudaMemcpyDeviceToHost, s));
-  MPK_CUDA(cudaStreamSynchronize(s));
+static int build_sell(int n, int cp, const int* rp, const int* ci, const int* diag, const T* fac, const int* perm,
+                      const int* pos, int nch, bool lower, const ObEnc& enc, void** buf, SellTri* out,
+                      cudaStream_t s) {
+  (void)n;
   int* width = nullptr;
   MPK_CUDA(cudaMallocAsync((void**)&width, sizeof(int) * ((size_t)nch + 1) * 2, s));
   int* coff_tmp = width + nch + 1;
   count_launch(2);
-  k_sell_width<<<grid_for(nch * 32), kBlock, 0, s>>>(nch, lo.perm, rp, diag, lower, width);
+  k_sell_width<<<grid_for(nch * 32), kBlock, 0, s>>>(nch, perm, rp, diag, lower, width);
   k_scan_single<<<1, 1024, 0, s>>>(nch, width, coff_tmp);
   int total = 0;
   MPK_CUDA(cudaMemcpyAsync(&total, coff_tmp + nch, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -636,7 +655,7 @@ static int build_sell(int n, int cp, const int* rp, const int* ci, const int* di
   count_launch();
   const int g = grid_for(nch * 32);
 #define MPK_SELL_FILL(CPX) \
-  k_sell_fill<T, CPX><<<g, kBlock, 0, s>>>(nch, lo.perm, lo.pos, rp, ci, diag, fac, lower, coff, col, val, dia, rep)
+  k_sell_fill<T, CPX><<<g, kBlock, 0, s>>>(nch, perm, pos, rp, ci, diag, fac, lower, coff, enc, col, val, dia, rep)
   switch (cp) {  // values per entry: c, or c * w for a w-component factor
     case 1: MPK_SELL_FILL(1); break;
     case 2: MPK_SELL_FILL(2); break;
@@ -650,7 +669,7 @@ static int build_sell(int n, int cp, const int* rp, const int* ci, const int* di
   MPK_CUDA(cudaGetLastError());
   MPK_CUDA(cudaFreeAsync(width, s));
   *buf = b;
-  out->perm = lo.perm;
+  out->perm = perm;
   out->coff = coff;
   out->col = col;
   out->val = val;
@@ -660,21 +679,180 @@ static int build_sell(int n, int cp, const int* rp, const int* ci, const int* di
   return MPK_OK;
 }
 
-// Repacked triangles t0, t0+1 of the handle (0: the factor, 2: its conjugate transpose).
-static int build_sells(mpk_ilu* M, int t0, const int* rp, const int* ci, const int* diag, const void* fac,
-                       cudaStream_t s) {
+// ---------------------------------------------------------------------------------------------
+// Owner-block order of one triangle (see SellTri): rows are dealt to the B blocks of the
+// substitution grid in contiguous ranges of equal work (row length + 1), then grouped by
+// (block, level), each group padded to whole chunks; inside a group rows keep no particular
+// order.  Keys k = block * nlevels + level; counts, padded offsets and group numbers by scans.
+// ---------------------------------------------------------------------------------------------
+__global__ void k_ob_work(int n, const int* __restrict__ rp, const int* __restrict__ diag, bool lower,
+                          int* __restrict__ work) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    work[i] = (lower ? diag[i] - rp[i] : rp[i + 1] - diag[i] - 1) + 1;
+}
+__global__ void k_ob_keys(int n, int B, int nl, const int* __restrict__ wcum, const int* __restrict__ depth,
+                          int* __restrict__ blk, int* __restrict__ cnt) {
+  const long long W = wcum[n];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int b = min(B - 1, (int)((long long)wcum[i] * B / (W > 0 ? W : 1)));
+    blk[i] = b;
+    atomicAdd(cnt + (int64_t)b * nl + depth[i], 1);
+  }
+}
+__global__ void k_ob_pad(int K, const int* __restrict__ cnt, int* __restrict__ pc, int* __restrict__ fl) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+    pc[k] = (cnt[k] + 31) & ~31;
+    fl[k] = cnt[k] > 0 ? 1 : 0;
+  }
+}
+// off: K + 1 padded position offsets; gid: K + 1 group numbers (exclusive scans)
+__global__ void k_ob_groups(int K, int B, int nl, const int* __restrict__ cnt, const int* __restrict__ off,
+                            const int* __restrict__ gid, int* __restrict__ goff, int* __restrict__ bgrp,
+                            int* __restrict__ bstart, int* __restrict__ cgend) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= K; k += gridDim.x * blockDim.x) {
+    if (k == K) {
+      goff[gid[K]] = off[K] >> 5;
+      bgrp[B] = gid[K];
+      bstart[B] = off[K];
+      continue;
+    }
+    if (k % nl == 0) {
+      bgrp[k / nl] = gid[k];
+      bstart[k / nl] = off[k];
+    }
+    if (cnt[k] > 0) {
+      goff[gid[k]] = off[k] >> 5;
+      for (int c = off[k] >> 5; c < (off[k + 1] >> 5); ++c) cgend[c] = off[k + 1];
+    }
+  }
+}
+__global__ void k_ob_scatter(int n, int nl, const int* __restrict__ blk, const int* __restrict__ depth,
+                             int* __restrict__ sub, int* __restrict__ perm, int* __restrict__ pos) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int q = atomicAdd(sub + (int64_t)blk[i] * nl + depth[i], 1);
+    perm[q] = i;
+    pos[i] = q;
+  }
+}
+
+// Orientation t of the handle: 0, 1 the factor's lower / upper triangle, 2, 3 the conjugate
+// transpose's.
+struct Orient {
+  const int *rp, *ci, *diag;
+  const void* fac;
+};
+static Orient orient(const mpk_ilu* M, int t) {
+  if (t < 2) return Orient{M->rp, M->ci, M->diag, M->fac};
+  return Orient{M->rpT, M->ciT, M->diagT, M->facT};
+}
+
+template <typename T>
+static int build_ob_t(mpk_ilu* M, int t, cudaStream_t s) {
+  const Orient o = orient(M, t);
+  const bool lower = (t % 2) == 0;
+  const int n = M->n, nl = M->nlevels[t], B = sm_count();
+  const int64_t K64 = (int64_t)B * nl;
+  if (K64 > (1 << 28)) return fail(MPK_INVALID_ARG, "too many levels for the owner-block layout");
+  const int K = (int)K64;
+  // temporaries: work/wcum (n + 1), blk (n), cnt, pc, fl (K each), off, gid (K + 1 each)
+  int* tmp = nullptr;
+  const size_t tmp_ints = 2 * ((size_t)n + 1) + (size_t)n + 3 * (size_t)K + 2 * ((size_t)K + 1);
+  MPK_CUDA(cudaMallocAsync((void**)&tmp, sizeof(int) * tmp_ints, s));
+  int* work = tmp;
+  int* wcum = work + n + 1;
+  int* blk = wcum + n + 1;
+  int* cnt = blk + n;
+  int* pc = cnt + K;
+  int* fl = pc + K;
+  int* off = fl + K;
+  int* gid = off + K + 1;
+  MPK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)K, s));
+  count_launch(6);
+  k_ob_work<<<grid_for(n), kBlock, 0, s>>>(n, o.rp, o.diag, lower, work);
+  k_scan_single<<<1, 1024, 0, s>>>(n, work, wcum);
+  k_ob_keys<<<grid_for(n), kBlock, 0, s>>>(n, B, nl, wcum, M->depth[t], blk, cnt);
+  k_ob_pad<<<grid_for(K), kBlock, 0, s>>>(K, cnt, pc, fl);
+  k_scan_single<<<1, 1024, 0, s>>>(K, pc, off);
+  k_scan_single<<<1, 1024, 0, s>>>(K, fl, gid);
+  int tot[2] = {0, 0};
+  MPK_CUDA(cudaMemcpyAsync(&tot[0], off + K, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MPK_CUDA(cudaMemcpyAsync(&tot[1], gid + K, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MPK_CUDA(cudaStreamSynchronize(s));
+  const int P = tot[0], G = tot[1], nch = P / 32;
+  // persistent order buffer: perm (P) | pos (n) | goff (G + 1) | bgrp (B + 1) | bstart (B + 1) |
+  // cgend (nch; needed only while repacking)
+  int* ob = nullptr;
+  const size_t ob_ints = (size_t)P + n + (size_t)G + 1 + 2 * ((size_t)B + 1) + (size_t)nch;
+  MPK_CUDA(cudaMalloc((void**)&ob, sizeof(int) * ob_ints));
+  int* perm = ob;
+  int* pos = perm + P;
+  int* goff = pos + n;
+  int* bgrp = goff + G + 1;
+  int* bstart = bgrp + B + 1;
+  int* cgend = bstart + B + 1;
+  MPK_CUDA(cudaMemsetAsync(perm, 0xff, sizeof(int) * (size_t)P, s));  // padding positions: -1
+  count_launch(2);
+  k_ob_groups<<<grid_for(K + 1), kBlock, 0, s>>>(K, B, nl, cnt, off, gid, goff, bgrp, bstart, cgend);
+  k_ob_scatter<<<grid_for(n), kBlock, 0, s>>>(n, nl, blk, M->depth[t], off, perm, pos);  // off becomes ends
+  MPK_CUDA(cudaGetLastError());
+  ObEnc enc;
+  enc.blk = blk;
+  enc.bstart = bstart;
+  enc.cgend = cgend;
+  M->obbuf[t] = ob;
+  int st = build_sell<T>(n, M->vals_per_entry(), o.rp, o.ci, o.diag, (const T*)o.fac, perm, pos, nch, lower, enc,
+                         M->obsellbuf + t, M->sellob + t, s);
+  MPK_CUDA(cudaFreeAsync(tmp, s));
+  if (st != MPK_OK) return st;
+  SellTri& L = M->sellob[t];
+  L.ob = 1;
+  L.goff = goff;
+  L.bgrp = bgrp;
+  L.bstart = bstart;
+  L.nblocks = B;
+  return MPK_OK;
+}
+
+// Classic (static chunk schedule) repack of orientation t from its level order.
+template <typename T>
+static int build_classic_t(mpk_ilu* M, int t, cudaStream_t s) {
+  const Orient o = orient(M, t);
+  const LevelOrder lo = level_view(M->lvbuf[t], M->n, M->nlevels[t]);
+  int nch = 0;
+  MPK_CUDA(cudaMemcpyAsync(&nch, lo.nchunks, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MPK_CUDA(cudaStreamSynchronize(s));
+  return build_sell<T>(M->n, M->vals_per_entry(), o.rp, o.ci, o.diag, (const T*)o.fac, lo.perm, lo.pos, nch,
+                       (t % 2) == 0, ObEnc(), M->sellbuf + t, M->sell + t, s);
+}
+
+template <typename T>
+static int build_layout_t(mpk_ilu* M, int t, int sched, cudaStream_t s) {
+  return sched == 1 ? build_ob_t<T>(M, t, s) : build_classic_t<T>(M, t, s);
+}
+
+static void drop_layout(mpk_ilu* M, int t, int sched) {
+  if (sched == 1) {
+    if (M->obsellbuf[t] != nullptr) cudaFree(M->obsellbuf[t]);
+    if (M->obbuf[t] != nullptr) cudaFree(M->obbuf[t]);
+    M->obsellbuf[t] = nullptr;
+    M->obbuf[t] = nullptr;
+    M->sellob[t] = SellTri();
+  } else {
+    if (M->sellbuf[t] != nullptr) cudaFree(M->sellbuf[t]);
+    M->sellbuf[t] = nullptr;
+    M->sell[t] = SellTri();
+  }
+}
+
+int ensure_layout(mpk_ilu* M, int t0, int sched, cudaStream_t s) {
   for (int t = t0; t < t0 + 2; ++t) {
-    const bool lower = (t == t0);
+    const bool have = sched == 1 ? M->obsellbuf[t] != nullptr : M->sellbuf[t] != nullptr;
+    if (have) continue;
+    if (t >= 2 && M->rpT == nullptr) return fail(MPK_INVALID_ARG, "the conjugate transpose is not built");
     int st;
-    if (M->prec == MPK_ILU_FP64 || M->prec == MPK_ILU_MP)
-      st = build_sell<double>(M->n, M->vals_per_entry(), rp, ci, diag, (const double*)fac, M->lvbuf[t], M->nlevels[t],
-                              lower, M->sellbuf + t, M->sell + t, s);
-    else if (M->prec == MPK_ILU_FP32)
-      st = build_sell<float>(M->n, M->cp, rp, ci, diag, (const float*)fac, M->lvbuf[t], M->nlevels[t], lower,
-                             M->sellbuf + t, M->sell + t, s);
-    else
-      st = build_sell<uint16_t>(M->n, M->cp, rp, ci, diag, (const uint16_t*)fac, M->lvbuf[t], M->nlevels[t], lower,
-                                M->sellbuf + t, M->sell + t, s);
+    if (M->prec == MPK_ILU_FP64 || M->prec == MPK_ILU_MP) st = build_layout_t<double>(M, t, sched, s);
+    else if (M->prec == MPK_ILU_FP32) st = build_layout_t<float>(M, t, sched, s);
+    else st = build_layout_t<uint16_t>(M, t, sched, s);
     if (st != MPK_OK) return st;
   }
   return MPK_OK;
@@ -723,9 +901,7 @@ static int build_transpose(mpk_ilu* M, cudaStream_t s) {
   // pk also serves as the binary32 substitutions' result buffer: clear it before the epoch-stamped
   // ordering passes read it
   MPK_CUDA(cudaMemsetAsync(M->pk, 0, sizeof(unsigned long long) * (size_t)M->n * M->cp, s));
-  st = build_levels(M->n, M->rpT, M->ciT, M->diagT, M->pk, M->ctl, 1, M->lvbuf + 2, M->nlevels + 2, s);
-  if (st != MPK_OK) return st;
-  return build_sells(M, 2, M->rpT, M->ciT, M->diagT, M->facT, s);
+  return build_levels(M->n, M->rpT, M->ciT, M->diagT, M->pk, M->ctl, 1, M->lvbuf + 2, M->nlevels + 2, M->depth + 2, s);
 }
 
 int prepare_trans(mpk_ilu* M, cudaStream_t s) { return build_transpose(M, s); }
@@ -736,6 +912,8 @@ int precond_apply(const mpk_ilu* M, const Ops* o, bool trans, const double* r, d
                   const Batch* bt, cudaStream_t s) {
   if (trans && M->rpT == nullptr) return fail(MPK_INVALID_ARG, "M^H solve needs the transposed factor");
   IluHandleView v = M->view(trans);
+  if (v.sl_lo.coff == nullptr || v.sl_up.coff == nullptr)
+    return fail(MPK_INVALID_ARG, "the substitution layout of this schedule is not built");
   launch_trsv_prep(v, done, s);
   int st;
   // M: unit lower L~ then upper U~ with division; M^H: lower U~^H with division then unit upper L~^H
@@ -757,76 +935,110 @@ int precond_apply(const mpk_ilu* M, const Ops* o, bool trans, const double* r, d
   return MPK_OK;
 }
 
-// New factor values on the same pattern (after a learned correction): repack the triangles and
-// drop the conjugate transpose (rebuilt on its next use).
+// New factor values on the same pattern (after a learned correction): drop every repacked
+// triangle and the conjugate transpose (all rebuilt on their next use).
 int refresh_factor(mpk_ilu* M, cudaStream_t s) {
   MPK_CUDA(cudaStreamSynchronize(s));
   for (int t = 0; t < 4; ++t) {
-    if (M->sellbuf[t] != nullptr) cudaFree(M->sellbuf[t]);
-    M->sellbuf[t] = nullptr;
-    M->sell[t] = SellTri();
+    drop_layout(M, t, 0);
+    drop_layout(M, t, 1);
   }
-  void* tp[] = {M->rpT, M->ciT, M->diagT, M->facT, M->lvbuf[2], M->lvbuf[3]};
+  void* tp[] = {M->rpT, M->ciT, M->diagT, M->facT, M->lvbuf[2], M->lvbuf[3], M->depth[2], M->depth[3]};
   for (void* p : tp)
     if (p != nullptr) cudaFree(p);
   M->rpT = M->ciT = M->diagT = nullptr;
   M->facT = nullptr;
   M->lvbuf[2] = M->lvbuf[3] = nullptr;
+  M->depth[2] = M->depth[3] = nullptr;
   M->nlevels[2] = M->nlevels[3] = 0;
-  return build_sells(M, 0, M->rp, M->ci, M->diag, M->fac, s);
+  return MPK_OK;
 }
 
 // ---- substitution autotuner ---------------------------------------------------------------------
+// Candidates: both schedules (static chunk schedule, owner-block schedule) x warps per SM
+// {4, 8, 16, 32}, each timed on two applications of M^-1; the choice is cached per (matrix
+// pattern, factor precision, w, c).  MPK_SUBST_SCHEDULE=static|owner restricts the candidates to
+// one schedule (tests use it to cover both).
 int read_ctl_err(const mpk_ilu* M, cudaStream_t s);
 struct TrsvTune {
   const void* rp;
-  int n, nnz, prec, w, cp, wpb;
+  int n, nnz, prec, w, cp, forced, wpb, sched;
 };
 static std::mutex g_trsv_mu;
 static std::vector<TrsvTune> g_trsv;
-static int cached_wpb(const mpk_ilu* M, int w) {
+static int forced_schedule() {
+  const char* e = std::getenv("MPK_SUBST_SCHEDULE");
+  if (e == nullptr) return -1;
+  if (std::strcmp(e, "static") == 0) return 0;
+  if (std::strcmp(e, "owner") == 0) return 1;
+  return -1;
+}
+static bool cached_choice(const mpk_ilu* M, int w, int forced, int* wpb, int* sched) {
   std::lock_guard<std::mutex> lk(g_trsv_mu);
   for (const TrsvTune& t : g_trsv)
-    if (t.rp == M->src_rp && t.n == M->n && t.nnz == M->nnz && t.prec == M->prec && t.w == w && t.cp == M->cp)
-      return t.wpb;
-  return 0;
+    if (t.rp == M->src_rp && t.n == M->n && t.nnz == M->nnz && t.prec == M->prec && t.w == w && t.cp == M->cp &&
+        t.forced == forced) {
+      *wpb = t.wpb;
+      *sched = t.sched;
+      return true;
+    }
+  return false;
+}
+// the handle's layouts for its current schedule (factor, and the conjugate transpose if built)
+static int ensure_current(mpk_ilu* M, cudaStream_t s) {
+  int st = ensure_layout(M, 0, M->sched, s);
+  if (st == MPK_OK && M->rpT != nullptr) st = ensure_layout(M, 2, M->sched, s);
+  return st;
 }
 int tune_substitution(mpk_ilu* M, const Ops* o, int w, double* r, double* z, cudaStream_t s) {
-  const int known = cached_wpb(M, w);
-  if (known > 0) {
-    M->wpb = known;
-    return MPK_OK;
+  const int forced = forced_schedule();
+  int wpb = 0, sched = 0;
+  if (cached_choice(M, w, forced, &wpb, &sched)) {
+    M->wpb = wpb;
+    M->sched = sched;
+    return ensure_current(M, s);
   }
   static const int cands[4] = {4, 8, 16, 32};
   cudaEvent_t e0, e1;
   MPK_CUDA(cudaEventCreate(&e0));
   MPK_CUDA(cudaEventCreate(&e1));
   float best = 0.f;
-  int best_wpb = 4;
-  for (int wpb : cands) {
-    if (!o->trsv_fits(M->prec, wpb)) continue;
-    M->wpb = wpb;
-    int st = precond_apply(M, o, false, r, z, nullptr, nullptr, s);  // warm
-    if (st != MPK_OK) continue;
-    cudaEventRecord(e0, s);
-    for (int k = 0; k < 2; ++k) precond_apply(M, o, false, r, z, nullptr, nullptr, s);
-    cudaEventRecord(e1, s);
-    if (cudaEventSynchronize(e1) != cudaSuccess) break;
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (best == 0.f || ms < best) {
-      best = ms;
-      best_wpb = wpb;
+  int best_wpb = 4, best_sched = forced >= 0 ? forced : 0;
+  for (int sc = 0; sc < 2; ++sc) {
+    if (forced >= 0 && sc != forced) continue;
+    if (ensure_layout(M, 0, sc, s) != MPK_OK) continue;
+    M->sched = sc;
+    for (int wp : cands) {
+      if (!o->trsv_fits(M->prec, wp, sc)) continue;
+      M->wpb = wp;
+      int st = precond_apply(M, o, false, r, z, nullptr, nullptr, s);  // warm
+      if (st != MPK_OK) continue;
+      cudaEventRecord(e0, s);
+      for (int k = 0; k < 2; ++k) precond_apply(M, o, false, r, z, nullptr, nullptr, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (best == 0.f || ms < best) {
+        best = ms;
+        best_wpb = wp;
+        best_sched = sc;
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   M->wpb = best_wpb;
+  M->sched = best_sched;
   const int err = read_ctl_err(M, s);
   if (err != MPK_OK) return err;
-  std::lock_guard<std::mutex> lk(g_trsv_mu);
-  if (g_trsv.size() < 256) g_trsv.push_back(TrsvTune{M->src_rp, M->n, M->nnz, M->prec, w, M->cp, best_wpb});
-  return MPK_OK;
+  for (int t = 0; t < 4; ++t) drop_layout(M, t, 1 - best_sched);  // keep the chosen repack only
+  {
+    std::lock_guard<std::mutex> lk(g_trsv_mu);
+    if (g_trsv.size() < 256)
+      g_trsv.push_back(TrsvTune{M->src_rp, M->n, M->nnz, M->prec, w, M->cp, forced, best_wpb, best_sched});
+  }
+  return ensure_current(M, s);
 }
 
 int read_ctl_err(const mpk_ilu* M, cudaStream_t s) {
@@ -841,7 +1053,10 @@ static void free_handle(mpk_ilu* M) {
   if (M == nullptr) return;
   void* ptrs[] = {M->rp, M->ci, M->diag, M->fac, M->rpT, M->ciT, M->diagT, M->facT, M->flags, M->ctl, M->v32, M->vmp,
                   M->absmax, M->pk, M->lvbuf[0], M->lvbuf[1], M->lvbuf[2], M->lvbuf[3],
-                  M->sellbuf[0], M->sellbuf[1], M->sellbuf[2], M->sellbuf[3]};
+                  M->sellbuf[0], M->sellbuf[1], M->sellbuf[2], M->sellbuf[3],
+                  M->obbuf[0], M->obbuf[1], M->obbuf[2], M->obbuf[3],
+                  M->obsellbuf[0], M->obsellbuf[1], M->obsellbuf[2], M->obsellbuf[3],
+                  M->depth[0], M->depth[1], M->depth[2], M->depth[3]};
   for (void* p : ptrs)
     if (p != nullptr) cudaFree(p);
   delete M;
@@ -870,9 +1085,10 @@ IluHandleView mpk_ilu::view(bool trans) const {
   const int t = trans ? 2 : 0;
   v.lv_lo = level_view(lvbuf[t], n, nlevels[t]);
   v.lv_up = level_view(lvbuf[t + 1], n, nlevels[t + 1]);
-  v.sl_lo = sell[t];
-  v.sl_up = sell[t + 1];
+  v.sl_lo = sched == 1 ? sellob[t] : sell[t];
+  v.sl_up = sched == 1 ? sellob[t + 1] : sell[t + 1];
   v.wpb = wpb;
+  v.sched = sched;
   return v;
 }
 
@@ -930,7 +1146,7 @@ static int factor_impl(const mpk_csr* A, int prec, int w, mpk_ilu** out, int* fa
     MPK_TRY(cudaMalloc((void**)&M->pk, sizeof(unsigned long long) * (size_t)n * cp));
     MPK_TRY(cudaMemsetAsync(M->pk, 0, sizeof(unsigned long long) * (size_t)n * cp, s));
     (void)nch;
-    int st = build_levels(n, M->rp, M->ci, M->diag, M->pk, M->ctl, 0, M->lvbuf, M->nlevels, s);
+    int st = build_levels(n, M->rp, M->ci, M->diag, M->pk, M->ctl, 0, M->lvbuf, M->nlevels, M->depth, s);
     if (st != MPK_OK) return bail(st);
   }
 
@@ -988,10 +1204,7 @@ static int factor_impl(const mpk_csr* A, int prec, int w, mpk_ilu** out, int* fa
   } else {
     MPK_TRY(cudaMalloc((void**)&M->v32, sizeof(float) * (size_t)n * cp));
   }
-  {
-    int st = build_sells(M, 0, M->rp, M->ci, M->diag, M->fac, s);
-    if (st != MPK_OK) return bail(st);
-  }
+  // the repacked triangles are built on first use, for the schedule the tuner picks
   MPK_TRY(cudaMemcpyAsync(M->ctl, ctl0, sizeof(int) * 4, cudaMemcpyHostToDevice, s));
   MPK_TRY(cudaStreamSynchronize(s));
 #undef MPK_TRY
@@ -1044,6 +1257,12 @@ extern "C" int mpk_ilu0_prec(const mpk_ilu* M) { return M == nullptr ? -2 : M->p
 
 extern "C" int mpk_ilu0_width(const mpk_ilu* M) { return M == nullptr ? -2 : M->wf; }
 
+extern "C" int mpk_ilu0_schedule(const mpk_ilu* M, int* wpb_out) {
+  if (M == nullptr) return -2;
+  if (wpb_out != nullptr) *wpb_out = M->wpb;
+  return M->sched;
+}
+
 extern "C" void mpk_ilu0_destroy(mpk_ilu* M) { free_handle(M); }
 
 extern "C" int mpk_precond_apply(const mpk_ilu* M, int w, int trans, const double* r_dev, double* z_dev,
@@ -1057,9 +1276,18 @@ extern "C" int mpk_precond_apply(const mpk_ilu* M, int w, int trans, const doubl
     if (st != MPK_OK) return st;
   }
   const Ops* o = get_ops(w, M->cp);
+  mpk_ilu* Mm = const_cast<mpk_ilu*>(M);
   {
-    const int known = cached_wpb(M, w);
-    if (known > 0) const_cast<mpk_ilu*>(M)->wpb = known;
+    const int forced = forced_schedule();
+    int wpb = 0, sched = 0;
+    if (cached_choice(M, w, forced, &wpb, &sched)) {
+      Mm->wpb = wpb;
+      Mm->sched = sched;
+    } else if (forced >= 0) {
+      Mm->sched = forced;
+    }
+    int st = ensure_layout(Mm, trans ? 2 : 0, M->sched, s);
+    if (st != MPK_OK) return st;
   }
   int st = precond_apply(M, o, trans != 0, r_dev, z_dev, nullptr, nullptr, s);
   if (st != MPK_OK) return st;

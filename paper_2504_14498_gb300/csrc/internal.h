@@ -144,7 +144,8 @@ struct Ops {
   // bt (nullable): one accumulator per system (out + s)
   void (*absmax)(int n, const double* v, unsigned long long* out, const int* done, const Batch* bt, cudaStream_t s);
   // 1 if the substitution kernel for factor precision prec fits one block of wpb warps per SM
-  int (*trsv_fits)(int prec, int wpb);
+  // (sched 1: the owner-block kernel with its shared-memory ring)
+  int (*trsv_fits)(int prec, int wpb, int sched);
 };
 const Ops* get_ops(int w, int cp);
 
@@ -153,6 +154,16 @@ const Ops* get_ops(int w, int cp);
 // chunk c owns slot blocks coff[c] .. coff[c+1]-1, and slot k of the row at lane l of chunk c is
 // entry (coff[c] + k) * 32 + l of col / val, its entries in CSR order.  Values have the factor's
 // storage type (double, float or bfloat16 bits).
+//
+// Owner-block variant (ob != 0): the positions are grouped by owner block first (block b of the
+// cooperative grid owns a contiguous range of rows, balanced by work), then by level, each
+// (block, level) group padded to whole chunks.  Block b runs its groups goff[bgrp[b]] ..
+// goff[bgrp[b+1]] in order, its warps sharing a group's chunks, with a block barrier between
+// groups.  A dependency computed earlier by the same block and still held in the block's
+// shared-memory ring of kRing values is encoded as col = -2 - slot (slot = its position minus
+// bstart[b], modulo kRing); the others keep their column and are polled in global memory; rep
+// then names the latest of those (-1: none).
+constexpr int kRing = 2048;  // values kept per block in shared memory (owner-block schedule)
 struct SellTri {
   const int* perm = nullptr;    // 32 * nchunks: row at each position (-1: padding)
   const int* coff = nullptr;    // nchunks + 1
@@ -161,6 +172,11 @@ struct SellTri {
   const void* dia = nullptr;    // 32 * nchunks * cp: the row's diagonal factor value (1 for padding)
   const int* rep = nullptr;     // nchunks: the chunk's dependency latest in the level order (-1: none)
   int nchunks = 0;
+  int ob = 0;                   // 1: owner-block layout (fields below)
+  const int* goff = nullptr;    // groups + 1: first chunk of each (block, level) group
+  const int* bgrp = nullptr;    // blocks + 1: first group of each block
+  const int* bstart = nullptr;  // blocks + 1: first position of each block
+  int nblocks = 0;              // the grid the layout was built for
 };
 
 // Device-side view of an ILU(0) handle used by the substitution kernels (one triangle pair:
@@ -182,6 +198,7 @@ struct IluHandleView {
   SellTri sl_lo, sl_up;              // repacked triangles of the substitutions
   const int* sysid = nullptr;        // batch: row -> system (absmax holds one scale per system)
   int wpb = 4;                       // warps per block (per SM) of the substitution kernels
+  int sched = 0;                     // 0: static chunk schedule, 1: owner-block schedule
 };
 enum CtlIdx : int { CTL_EPOCH = 0, CTL_TICKET_LO, CTL_TICKET_UP, CTL_ERR, CTL_FAIL_ROW, CTL_COUNT };
 
@@ -195,6 +212,9 @@ void launch_trsv_prep(const IluHandleView& M, const int* done, cudaStream_t s);
 // Pick the substitution kernels' warps per SM for this handle and w by timing the candidates
 // (r, z: scratch vectors of n*c*w doubles); cached per (matrix pattern, factor precision, w, c).
 int tune_substitution(mpk_ilu* M, const Ops* o, int w, double* r, double* z, cudaStream_t s);
+// Repacked triangles t0, t0 + 1 (0: the factor, 2: its conjugate transpose) for schedule `sched`,
+// built if missing (not inside a graph capture).
+int ensure_layout(mpk_ilu* M, int t0, int sched, cudaStream_t s);
 // ints of the order buffer of one triangle with n rows and `nlevels` levels:
 // level perm (P = n + 32*nlevels) | level pos (n) | chunk flags (P/32 + 1) | nchunks (1)
 size_t level_buf_ints(int n, int nlevels);
@@ -225,7 +245,12 @@ struct mpk_ilu {
   int nlevels[4] = {0, 0, 0, 0};
   void* sellbuf[4] = {nullptr, nullptr, nullptr, nullptr};  // repacked triangles (same order)
   mpk::SellTri sell[4];
+  void* obbuf[4] = {nullptr, nullptr, nullptr, nullptr};    // owner-block orders (same order)
+  void* obsellbuf[4] = {nullptr, nullptr, nullptr, nullptr};  // owner-block repacks
+  mpk::SellTri sellob[4];
+  int* depth[4] = {nullptr, nullptr, nullptr, nullptr};      // level of every row, per triangle
   int wpb = 4;                   // warps per SM of the substitution kernels (autotuned per pattern)
+  int sched = 0;                 // 0: static chunk schedule, 1: owner-block schedule (autotuned)
   const void* src_rp = nullptr;  // the factored matrix's row_ptr address: the tuning cache's key
   mpk::IluHandleView view(bool trans) const;
   int vals_per_entry() const { return cp * wf; }  // doubles (or narrower values) per factor entry

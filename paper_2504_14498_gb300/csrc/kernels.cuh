@@ -6,6 +6,7 @@
 
 #include <climits>
 #include <cstdint>
+#include <mutex>
 #include <type_traits>
 
 #include "internal.h"
@@ -916,16 +917,112 @@ __device__ __forceinline__ void wait_pause(long long t0, int ns) {
 // and row i computes acc -= f_ij * out_j with the factor first in the product, then
 // acc /= f_ii, both in w-component arithmetic; fewer entries per group keep the values in
 // registers.
+//
+// One chunk (32 rows) of the substitution, shared by both schedules.  ring (owner-block
+// schedule; nullptr otherwise): the block's shared-memory values, read for the entries encoded
+// as local (col <= -2) and written at own_slot.  Returns the warp-uniform timeout flag.
+template <int W, int CP, bool MF>
+__device__ __forceinline__ bool trsv_mp_chunk(const SellTri& T, const IluHandleView& M, bool unit,
+                                              const double* __restrict__ in, double* __restrict__ out, int chunk,
+                                              int i, int b0, int w, int rep, double* ring, int own_slot) {
+  constexpr int KG = (MF && W * CP >= 4) ? 2 : 4;  // entries per group
+  const unsigned FULL = 0xffffffffu;
+  const double* __restrict__ tval = (const double*)T.val;
+  const double* __restrict__ tdia = (const double*)T.dia;
+  const int lane = threadIdx.x & 31;
+  int jj[KG];
+  double fr[KG], fi[KG];
+  N<W, CP> fv[MF ? KG : 1];
+  auto load_group = [&](int k0) {
+#pragma unroll
+    for (int k = 0; k < KG; ++k) {
+      jj[k] = -1;
+      fr[k] = 0.0;
+      fi[k] = 0.0;
+      if constexpr (MF) fv[k] = n_zero<W, CP>();
+      if (k0 + k < w) {
+        const int64_t e = ((int64_t)(b0 + k0 + k) << 5) + lane;
+        jj[k] = T.col[e];
+        if constexpr (MF) fv[k] = n_load<W, CP>(tval, e);
+        else if constexpr (CP == 1) fr[k] = tval[e];
+        else { fr[k] = tval[2 * e]; fi[k] = tval[2 * e + 1]; }
+      }
+    }
+  };
+  load_group(0);
+  N<W, CP> acc = n_zero<W, CP>();
+  double dr = 1.0, di = 0.0;
+  N<W, CP> dv = n_real<W, CP>(1.0);
+  if (i >= 0) {
+    acc = n_load<W, CP>(in, i);
+    if (!unit) {
+      const int64_t q = ((int64_t)chunk << 5) + lane;
+      if constexpr (MF) dv = n_load<W, CP>(tdia, q);
+      else if constexpr (CP == 1) dr = tdia[q];
+      else { dr = tdia[2 * q]; di = tdia[2 * q + 1]; }
+    }
+  }
+  bool timeout = false;
+  const long long t0 = clock64();
+  int polls = 0;
+  if (lane == 0 && rep >= 0) {  // the chunk's latest dependency, polled by one lane
+    N<W, CP> r;
+    while (!n_poll<W, CP>(out, rep, r)) {
+      if (wait_expired(t0, polls, M.ctl)) { timeout = true; break; }
+      wait_pause(t0, 128);
+    }
+  }
+  __syncwarp();
+  for (int k0 = 0; k0 < w; k0 += KG) {
+    if (k0 > 0) load_group(k0);
+    N<W, CP> v[KG];
+    unsigned need = 0u;
+#pragma unroll
+    for (int k = 0; k < KG; ++k) {
+      v[k] = n_zero<W, CP>();
+      if (jj[k] >= 0) need |= 1u << k;
+      else if (jj[k] <= -2) v[k] = n_load<W, CP>(ring, -2 - jj[k]);  // computed by this block
+    }
+    while (__any_sync(FULL, need != 0u && !timeout)) {
+      // every outstanding load of the round is issued before any is checked
+#pragma unroll
+      for (int k = 0; k < KG; ++k)
+        if ((need >> k) & 1u) n_fetch<W, CP>(out, jj[k], v[k]);
+      unsigned got = 0u;
+#pragma unroll
+      for (int k = 0; k < KG; ++k)
+        if (((need >> k) & 1u) && n_ready<W, CP>(v[k])) got |= 1u << k;
+      need &= ~got;
+      if (need != 0u && !timeout && wait_expired(t0, polls, M.ctl)) timeout = true;
+      if (__any_sync(FULL, need != 0u)) __nanosleep(64);
+    }
+    __syncwarp();
+    if (!timeout && i >= 0) {
+#pragma unroll
+      for (int k = 0; k < KG; ++k) {
+        if (jj[k] == -1) continue;
+        if constexpr (MF) acc = n_sub<W, CP>(acc, n_mul<W, CP>(fv[k], v[k]));
+        else acc = n_sub<W, CP>(acc, n_mul_fp<W, CP>(v[k], fr[k], fi[k]));
+      }
+    }
+  }
+  if (!timeout && i >= 0) {
+    if (!unit) {
+      if constexpr (MF) acc = n_div<W, CP>(acc, dv);
+      else acc = n_div_fp<W, CP>(acc, dr, di);
+    }
+    n_publish<W, CP>(out, i, acc);
+    if (ring != nullptr) n_store<W, CP>(ring, own_slot, acc);
+  }
+  return __any_sync(FULL, timeout);
+}
+
 template <int W, int CP, int WPB, bool MF>
 __global__ void __launch_bounds__(WPB * 32, 1)
     k_trsv_mp(IluHandleView M, bool lower, bool unit, const double* __restrict__ in, double* __restrict__ out,
               const int* __restrict__ done) {
   if (is_done(done)) return;
-  constexpr int KG = (MF && W * CP >= 4) ? 2 : 4;  // entries per group
-  const unsigned FULL = 0xffffffffu;
   const SellTri T = lower ? M.sl_lo : M.sl_up;
-  const double* __restrict__ tval = (const double*)T.val;
-  const double* __restrict__ tdia = (const double*)T.dia;
   const int lane = threadIdx.x & 31;
   const int G = gridDim.x * (blockDim.x >> 5);
   const int g = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
@@ -938,99 +1035,60 @@ __global__ void __launch_bounds__(WPB * 32, 1)
   }
   for (int chunk = g; chunk < T.nchunks; chunk += G) {
     const int i = nx_i, b0 = nx_b0, w = nx_b1 - nx_b0, rep = nx_rep;
-    int jj[KG];
-    double fr[KG], fi[KG];
-    N<W, CP> fv[MF ? KG : 1];
-    auto load_group = [&](int k0) {
-#pragma unroll
-      for (int k = 0; k < KG; ++k) {
-        jj[k] = -1;
-        fr[k] = 0.0;
-        fi[k] = 0.0;
-        if constexpr (MF) fv[k] = n_zero<W, CP>();
-        if (k0 + k < w) {
-          const int64_t e = ((int64_t)(b0 + k0 + k) << 5) + lane;
-          jj[k] = T.col[e];
-          if constexpr (MF) fv[k] = n_load<W, CP>(tval, e);
-          else if constexpr (CP == 1) fr[k] = tval[e];
-          else { fr[k] = tval[2 * e]; fi[k] = tval[2 * e + 1]; }
-        }
-      }
-    };
-    load_group(0);
-    N<W, CP> acc = n_zero<W, CP>();
-    double dr = 1.0, di = 0.0;
-    N<W, CP> dv = n_real<W, CP>(1.0);
-    if (i >= 0) {
-      acc = n_load<W, CP>(in, i);
-      if (!unit) {
-        const int64_t q = ((int64_t)chunk << 5) + lane;
-        if constexpr (MF) dv = n_load<W, CP>(tdia, q);
-        else if constexpr (CP == 1) dr = tdia[q];
-        else { dr = tdia[2 * q]; di = tdia[2 * q + 1]; }
-      }
-    }
-    const int nc = chunk + G;
+    const int nc = chunk + G;  // the next chunk's row and slot range, fetched ahead
     if (nc < T.nchunks) {
       nx_i = T.perm[(nc << 5) + lane];
       nx_b0 = T.coff[nc];
       nx_b1 = T.coff[nc + 1];
       nx_rep = T.rep[nc];
     }
-    bool timeout = false;
-    const long long t0 = clock64();
-    int polls = 0;
-    if (lane == 0 && rep >= 0) {  // the chunk's latest dependency, polled by one lane
-      N<W, CP> r;
-      while (!n_poll<W, CP>(out, rep, r)) {
-        if (wait_expired(t0, polls, M.ctl)) { timeout = true; break; }
-        wait_pause(t0, 128);
-      }
-    }
-    __syncwarp();
-    for (int k0 = 0; k0 < w; k0 += KG) {
-      if (k0 > 0) load_group(k0);
-      N<W, CP> v[KG];
-      unsigned need = 0u;
-#pragma unroll
-      for (int k = 0; k < KG; ++k) {
-        v[k] = n_zero<W, CP>();
-        if (jj[k] >= 0) need |= 1u << k;
-      }
-      while (__any_sync(FULL, need != 0u && !timeout)) {
-        // every outstanding load of the round is issued before any is checked
-#pragma unroll
-        for (int k = 0; k < KG; ++k)
-          if ((need >> k) & 1u) n_fetch<W, CP>(out, jj[k], v[k]);
-        unsigned got = 0u;
-#pragma unroll
-        for (int k = 0; k < KG; ++k)
-          if (((need >> k) & 1u) && n_ready<W, CP>(v[k])) got |= 1u << k;
-        need &= ~got;
-        if (need != 0u && !timeout && wait_expired(t0, polls, M.ctl)) timeout = true;
-        if (__any_sync(FULL, need != 0u)) __nanosleep(64);
-      }
-      __syncwarp();
-      if (!timeout && i >= 0) {
-#pragma unroll
-        for (int k = 0; k < KG; ++k) {
-          if (jj[k] < 0) continue;
-          if constexpr (MF) acc = n_sub<W, CP>(acc, n_mul<W, CP>(fv[k], v[k]));
-          else acc = n_sub<W, CP>(acc, n_mul_fp<W, CP>(v[k], fr[k], fi[k]));
-        }
-      }
-    }
-    if (!timeout && i >= 0) {
-      if (!unit) {
-        if constexpr (MF) acc = n_div<W, CP>(acc, dv);
-        else acc = n_div_fp<W, CP>(acc, dr, di);
-      }
-      n_publish<W, CP>(out, i, acc);
-    }
-    if (__any_sync(FULL, timeout)) {
+    if (trsv_mp_chunk<W, CP, MF>(T, M, unit, in, out, chunk, i, b0, w, rep, nullptr, 0)) {
       if (lane == 0) atomicCAS(M.ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
       return;
     }
+  }
+}
+
+// Owner-block schedule (SellTri::ob): block b runs its (block, level) groups in order; the
+// block's warps share a group's chunks (chunk goff[g] + k for warp k mod WPB), then meet at a
+// block barrier, after which the group's values are in the block's shared-memory ring.  Only
+// dependencies on other blocks' rows (or on own rows that left the ring) are polled in global
+// memory: on a mesh in natural order with contiguous row blocks those are the rows of the
+// neighbouring block, so most levels cost a barrier instead of a cross-SM notification.
+// Deadlock-free with all blocks resident (cooperative launch): a block waits only for rows of
+// lower levels, and the block with the lowest current level waits for nothing unfinished.  A
+// timed-out wait sets MPK_TIMEOUT and a block flag; every warp still reaches the barrier, then
+// the block leaves.
+template <int W, int CP, int WPB, bool MF>
+__global__ void __launch_bounds__(WPB * 32, 1)
+    k_trsv_mp_ob(IluHandleView M, bool lower, bool unit, const double* __restrict__ in, double* __restrict__ out,
+                 const int* __restrict__ done) {
+  if (is_done(done)) return;
+  extern __shared__ double ring_mp[];
+  __shared__ int abort_blk;
+  const SellTri T = lower ? M.sl_lo : M.sl_up;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int b = blockIdx.x;
+  if (threadIdx.x == 0) abort_blk = 0;
+  __syncthreads();
+  if (b >= T.nblocks) return;
+  const int bs = T.bstart[b], g1 = T.bgrp[b + 1];
+  for (int g = T.bgrp[b]; g < g1; ++g) {
+    const int c1 = T.goff[g + 1];
+    for (int chunk = T.goff[g] + warp; chunk < c1; chunk += WPB) {
+      const int i = T.perm[(chunk << 5) + lane];
+      const int b0 = T.coff[chunk], w = T.coff[chunk + 1] - b0, rep = T.rep[chunk];
+      const int own = ((chunk << 5) + lane - bs) % kRing;
+      if (trsv_mp_chunk<W, CP, MF>(T, M, unit, in, out, chunk, i, b0, w, rep, ring_mp, own)) {
+        if (lane == 0) {
+          atomicCAS(M.ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
+          abort_blk = 1;
+        }
+        break;
+      }
+    }
+    __syncthreads();
+    if (abort_blk) return;
   }
 }
 
@@ -1067,17 +1125,142 @@ __device__ __forceinline__ bool f_poll(const float* __restrict__ v, int j, float
   return __float_as_uint(xr) != kSent32 && (CP == 1 || __float_as_uint(xi) != kSent32);
 }
 
+// One chunk of the binary32 substitution, shared by both schedules (ring: see trsv_mp_chunk).
+template <int W, int CP, typename TS>
+__device__ __forceinline__ bool trsv_lp_chunk(const SellTri& T, const IluHandleView& M, bool lower, bool unit,
+                                              const double* __restrict__ in, double* __restrict__ out, int chunk,
+                                              int i, int b0, int w, int rep, int e1, float* ring, int own_slot) {
+  constexpr int KG = 8;  // entries per group
+  const unsigned FULL = 0xffffffffu;
+  const TS* __restrict__ tval = (const TS*)T.val;
+  const TS* __restrict__ tdia = (const TS*)T.dia;
+  float* __restrict__ mine = lower ? M.v32 : reinterpret_cast<float*>(M.pk);
+  const int lane = threadIdx.x & 31;
+  int jj[KG];
+  float fr[KG], fi[KG];
+  auto load_group = [&](int k0) {
+#pragma unroll
+    for (int k = 0; k < KG; ++k) {
+      jj[k] = -1;
+      fr[k] = 0.0f;
+      fi[k] = 0.0f;
+      if (k0 + k < w) {
+        const int64_t s = ((int64_t)(b0 + k0 + k) << 5) + lane;
+        jj[k] = T.col[s];
+        if constexpr (CP == 1) fr[k] = ld_fac(tval, s);
+        else { fr[k] = ld_fac(tval, 2 * s); fi[k] = ld_fac(tval, 2 * s + 1); }
+      }
+    }
+  };
+  load_group(0);
+  float ar = 0.0f, ai = 0.0f, dr = 1.0f, di = 0.0f;
+  const int e = (M.sysid != nullptr && i >= 0) ? scale_exponent(M.absmax + M.sysid[i]) : e1;
+  if (i >= 0) {
+    if (lower) {
+      const double* q = in + (int64_t)i * CP * W;
+      ar = __double2float_rn(ldexp(q[0], -e));
+      ai = CP == 2 ? __double2float_rn(ldexp(q[W], -e)) : 0.0f;
+    } else {
+      ar = M.v32[(int64_t)i * CP];
+      ai = CP == 2 ? M.v32[(int64_t)i * CP + 1] : 0.0f;
+    }
+    if (!unit) {
+      const int64_t q = ((int64_t)chunk << 5) + lane;
+      if constexpr (CP == 1) dr = ld_fac(tdia, q);
+      else { dr = ld_fac(tdia, 2 * q); di = ld_fac(tdia, 2 * q + 1); }
+    }
+  }
+  bool timeout = false;
+  const long long t0 = clock64();
+  int polls = 0;
+  if (lane == 0 && rep >= 0) {  // the chunk's latest dependency, polled by one lane
+    float xr, xi;
+    while (!f_poll<CP>(mine, rep, xr, xi)) {
+      if (wait_expired(t0, polls, M.ctl)) { timeout = true; break; }
+      wait_pause(t0, 128);
+    }
+  }
+  __syncwarp();
+  for (int k0 = 0; k0 < w; k0 += KG) {
+    if (k0 > 0) load_group(k0);
+    float vr[KG], vi[KG];
+    unsigned need = 0u;
+#pragma unroll
+    for (int k = 0; k < KG; ++k) {
+      vr[k] = 0.0f;
+      vi[k] = 0.0f;
+      if (jj[k] >= 0) {
+        need |= 1u << k;
+      } else if (jj[k] <= -2) {  // computed by this block
+        vr[k] = ring[(-2 - jj[k]) * CP];
+        if constexpr (CP == 2) vi[k] = ring[(-2 - jj[k]) * CP + 1];
+      }
+    }
+    while (__any_sync(FULL, need != 0u && !timeout)) {
+#pragma unroll
+      for (int k = 0; k < KG; ++k)
+        if ((need >> k) & 1u) {
+          vr[k] = ld_relaxed_f32(mine + (int64_t)jj[k] * CP);
+          if constexpr (CP == 2) vi[k] = ld_relaxed_f32(mine + (int64_t)jj[k] * CP + 1);
+        }
+      unsigned got = 0u;
+#pragma unroll
+      for (int k = 0; k < KG; ++k)
+        if (((need >> k) & 1u) && __float_as_uint(vr[k]) != kSent32 &&
+            (CP == 1 || __float_as_uint(vi[k]) != kSent32))
+          got |= 1u << k;
+      need &= ~got;
+      if (need != 0u && !timeout && wait_expired(t0, polls, M.ctl)) timeout = true;
+      if (__any_sync(FULL, need != 0u)) __nanosleep(64);
+    }
+    __syncwarp();
+    if (!timeout && i >= 0) {
+#pragma unroll
+      for (int k = 0; k < KG; ++k) {
+        if (jj[k] == -1) continue;
+        if constexpr (CP == 1) {
+          ar = fmaf(-fr[k], vr[k], ar);
+        } else {
+          ar = fmaf(-fr[k], vr[k], ar);
+          ar = fmaf(fi[k], vi[k], ar);
+          ai = fmaf(-fr[k], vi[k], ai);
+          ai = fmaf(-fi[k], vr[k], ai);
+        }
+      }
+    }
+  }
+  if (!timeout && i >= 0) {
+    if (!unit) {
+      if constexpr (CP == 1) {
+        ar = ar / dr;
+      } else {
+        const float den = fmaf(dr, dr, di * di), nr = fmaf(ar, dr, ai * di), ni = fmaf(ai, dr, -(ar * di));
+        ar = nr / den;
+        ai = ni / den;
+      }
+    }
+    st_relaxed_f32(mine + (int64_t)i * CP, ar);
+    if constexpr (CP == 2) st_relaxed_f32(mine + (int64_t)i * CP + 1, ai);
+    if (ring != nullptr) {
+      ring[own_slot * CP] = ar;
+      if constexpr (CP == 2) ring[own_slot * CP + 1] = ai;
+    }
+    if (!lower) {
+      N<W, CP> z = n_zero<W, CP>();
+      z.re.c[0] = ldexp((double)ar, e);
+      if constexpr (CP == 2) z.im.c[0] = ldexp((double)ai, e);
+      n_store<W, CP>(out, i, z);
+    }
+  }
+  return __any_sync(FULL, timeout);
+}
+
 template <int W, int CP, typename TS, int WPB>
 __global__ void __launch_bounds__(WPB * 32, 1)
     k_trsv_lp(IluHandleView M, bool lower, bool unit, const double* __restrict__ in, double* __restrict__ out,
               const int* __restrict__ done) {
   if (is_done(done)) return;
-  constexpr int KG = 8;  // entries per group
-  const unsigned FULL = 0xffffffffu;
   const SellTri T = lower ? M.sl_lo : M.sl_up;
-  const TS* __restrict__ tval = (const TS*)T.val;
-  const TS* __restrict__ tdia = (const TS*)T.dia;
-  float* __restrict__ mine = lower ? M.v32 : reinterpret_cast<float*>(M.pk);
   const int e1 = M.sysid == nullptr ? scale_exponent(M.absmax) : 0;  // one system: one scale
   const int lane = threadIdx.x & 31;
   const int G = gridDim.x * (blockDim.x >> 5);
@@ -1091,40 +1274,6 @@ __global__ void __launch_bounds__(WPB * 32, 1)
   }
   for (int chunk = g; chunk < T.nchunks; chunk += G) {
     const int i = nx_i, b0 = nx_b0, w = nx_b1 - nx_b0, rep = nx_rep;
-    int jj[KG];
-    float fr[KG], fi[KG];
-    auto load_group = [&](int k0) {
-#pragma unroll
-      for (int k = 0; k < KG; ++k) {
-        jj[k] = -1;
-        fr[k] = 0.0f;
-        fi[k] = 0.0f;
-        if (k0 + k < w) {
-          const int64_t s = ((int64_t)(b0 + k0 + k) << 5) + lane;
-          jj[k] = T.col[s];
-          if constexpr (CP == 1) fr[k] = ld_fac(tval, s);
-          else { fr[k] = ld_fac(tval, 2 * s); fi[k] = ld_fac(tval, 2 * s + 1); }
-        }
-      }
-    };
-    load_group(0);
-    float ar = 0.0f, ai = 0.0f, dr = 1.0f, di = 0.0f;
-    const int e = (M.sysid != nullptr && i >= 0) ? scale_exponent(M.absmax + M.sysid[i]) : e1;
-    if (i >= 0) {
-      if (lower) {
-        const double* q = in + (int64_t)i * CP * W;
-        ar = __double2float_rn(ldexp(q[0], -e));
-        ai = CP == 2 ? __double2float_rn(ldexp(q[W], -e)) : 0.0f;
-      } else {
-        ar = M.v32[(int64_t)i * CP];
-        ai = CP == 2 ? M.v32[(int64_t)i * CP + 1] : 0.0f;
-      }
-      if (!unit) {
-        const int64_t q = ((int64_t)chunk << 5) + lane;
-        if constexpr (CP == 1) dr = ld_fac(tdia, q);
-        else { dr = ld_fac(tdia, 2 * q); di = ld_fac(tdia, 2 * q + 1); }
-      }
-    }
     const int nc = chunk + G;
     if (nc < T.nchunks) {
       nx_i = T.perm[(nc << 5) + lane];
@@ -1132,83 +1281,45 @@ __global__ void __launch_bounds__(WPB * 32, 1)
       nx_b1 = T.coff[nc + 1];
       nx_rep = T.rep[nc];
     }
-    bool timeout = false;
-    const long long t0 = clock64();
-    int polls = 0;
-    if (lane == 0 && rep >= 0) {  // the chunk's latest dependency, polled by one lane
-      float xr, xi;
-      while (!f_poll<CP>(mine, rep, xr, xi)) {
-        if (wait_expired(t0, polls, M.ctl)) { timeout = true; break; }
-        wait_pause(t0, 128);
-      }
-    }
-    __syncwarp();
-    for (int k0 = 0; k0 < w; k0 += KG) {
-      if (k0 > 0) load_group(k0);
-      float vr[KG], vi[KG];
-      unsigned need = 0u;
-#pragma unroll
-      for (int k = 0; k < KG; ++k) {
-        vr[k] = 0.0f;
-        vi[k] = 0.0f;
-        if (jj[k] >= 0) need |= 1u << k;
-      }
-      while (__any_sync(FULL, need != 0u && !timeout)) {
-#pragma unroll
-        for (int k = 0; k < KG; ++k)
-          if ((need >> k) & 1u) {
-            vr[k] = ld_relaxed_f32(mine + (int64_t)jj[k] * CP);
-            if constexpr (CP == 2) vi[k] = ld_relaxed_f32(mine + (int64_t)jj[k] * CP + 1);
-          }
-        unsigned got = 0u;
-#pragma unroll
-        for (int k = 0; k < KG; ++k)
-          if (((need >> k) & 1u) && __float_as_uint(vr[k]) != kSent32 &&
-              (CP == 1 || __float_as_uint(vi[k]) != kSent32))
-            got |= 1u << k;
-        need &= ~got;
-        if (need != 0u && !timeout && wait_expired(t0, polls, M.ctl)) timeout = true;
-        if (__any_sync(FULL, need != 0u)) __nanosleep(64);
-      }
-      __syncwarp();
-      if (!timeout && i >= 0) {
-#pragma unroll
-        for (int k = 0; k < KG; ++k) {
-          if (jj[k] < 0) continue;
-          if constexpr (CP == 1) {
-            ar = fmaf(-fr[k], vr[k], ar);
-          } else {
-            ar = fmaf(-fr[k], vr[k], ar);
-            ar = fmaf(fi[k], vi[k], ar);
-            ai = fmaf(-fr[k], vi[k], ai);
-            ai = fmaf(-fi[k], vr[k], ai);
-          }
-        }
-      }
-    }
-    if (!timeout && i >= 0) {
-      if (!unit) {
-        if constexpr (CP == 1) {
-          ar = ar / dr;
-        } else {
-          const float den = fmaf(dr, dr, di * di), nr = fmaf(ar, dr, ai * di), ni = fmaf(ai, dr, -(ar * di));
-          ar = nr / den;
-          ai = ni / den;
-        }
-      }
-      st_relaxed_f32(mine + (int64_t)i * CP, ar);
-      if constexpr (CP == 2) st_relaxed_f32(mine + (int64_t)i * CP + 1, ai);
-      if (!lower) {
-        N<W, CP> z = n_zero<W, CP>();
-        z.re.c[0] = ldexp((double)ar, e);
-        if constexpr (CP == 2) z.im.c[0] = ldexp((double)ai, e);
-        n_store<W, CP>(out, i, z);
-      }
-    }
-    if (__any_sync(FULL, timeout)) {
+    if (trsv_lp_chunk<W, CP, TS>(T, M, lower, unit, in, out, chunk, i, b0, w, rep, e1, nullptr, 0)) {
       if (lane == 0) atomicCAS(M.ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
       return;
     }
+  }
+}
+
+// Owner-block schedule of the binary32 substitution (see k_trsv_mp_ob).
+template <int W, int CP, typename TS, int WPB>
+__global__ void __launch_bounds__(WPB * 32, 1)
+    k_trsv_lp_ob(IluHandleView M, bool lower, bool unit, const double* __restrict__ in, double* __restrict__ out,
+                 const int* __restrict__ done) {
+  if (is_done(done)) return;
+  extern __shared__ float ring_lp[];
+  __shared__ int abort_blk;
+  const SellTri T = lower ? M.sl_lo : M.sl_up;
+  const int e1 = M.sysid == nullptr ? scale_exponent(M.absmax) : 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int b = blockIdx.x;
+  if (threadIdx.x == 0) abort_blk = 0;
+  __syncthreads();
+  if (b >= T.nblocks) return;
+  const int bs = T.bstart[b], g1 = T.bgrp[b + 1];
+  for (int g = T.bgrp[b]; g < g1; ++g) {
+    const int c1 = T.goff[g + 1];
+    for (int chunk = T.goff[g] + warp; chunk < c1; chunk += WPB) {
+      const int i = T.perm[(chunk << 5) + lane];
+      const int b0 = T.coff[chunk], w = T.coff[chunk + 1] - b0, rep = T.rep[chunk];
+      const int own = ((chunk << 5) + lane - bs) % kRing;
+      if (trsv_lp_chunk<W, CP, TS>(T, M, lower, unit, in, out, chunk, i, b0, w, rep, e1, ring_lp, own)) {
+        if (lane == 0) {
+          atomicCAS(M.ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
+          abort_blk = 1;
+        }
+        break;
+      }
+    }
+    __syncthreads();
+    if (abort_blk) return;
   }
 }
 
@@ -1311,40 +1422,88 @@ struct Launch {
     count_launch();
     k_absmax<W, CP><<<grid_for(n), kBlock, 0, s>>>(n, v, out, done, bt ? bt->sysid : nullptr);
   }
-  // Launch of a static-schedule substitution with wpb warps per block (one block per SM, all
-  // co-resident: cooperative launch)
-  static int coop(const void* fn, int wpb, const IluHandleView& M, bool lower, bool unit, const double* in,
-                  double* out, const int* done, cudaStream_t s) {
+  // Launch of a substitution kernel with wpb warps per block, one block per SM, all co-resident
+  // (cooperative launch); smem: dynamic shared memory (the owner-block ring)
+  static int coop(const void* fn, int wpb, size_t smem, const IluHandleView& M, bool lower, bool unit,
+                  const double* in, double* out, const int* done, cudaStream_t s) {
     void* args[] = {(void*)&M, (void*)&lower, (void*)&unit, (void*)&in, (void*)&out, (void*)&done};
     count_launch();
-    const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(sm_count()), dim3(wpb * 32), args, 0, s);
+    const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(sm_count()), dim3(wpb * 32), args, smem, s);
     return e == cudaSuccess ? MPK_OK : MPK_CUDA_ERROR;
   }
-  template <bool MF>
-  static const void* mp_fn(int wpb) {
-    switch (wpb) {
-      case 8: return (const void*)k_trsv_mp<W, CP, 8, MF>;
-      case 16: return (const void*)k_trsv_mp<W, CP, 16, MF>;
-      case 32: return (const void*)k_trsv_mp<W, CP, 32, MF>;
-      default: return (const void*)k_trsv_mp<W, CP, 4, MF>;
+  static size_t ring_bytes(int prec) {  // the owner-block kernels' shared-memory ring
+    return (size_t)kRing * CP * ((prec == MPK_ILU_FP64 || prec == MPK_ILU_MP) ? W * sizeof(double) : sizeof(float));
+  }
+  template <bool MF, bool OB>
+  static const void* mp_fn_t(int wpb) {
+    if constexpr (OB) {
+      switch (wpb) {
+        case 8: return (const void*)k_trsv_mp_ob<W, CP, 8, MF>;
+        case 16: return (const void*)k_trsv_mp_ob<W, CP, 16, MF>;
+        case 32: return (const void*)k_trsv_mp_ob<W, CP, 32, MF>;
+        default: return (const void*)k_trsv_mp_ob<W, CP, 4, MF>;
+      }
+    } else {
+      switch (wpb) {
+        case 8: return (const void*)k_trsv_mp<W, CP, 8, MF>;
+        case 16: return (const void*)k_trsv_mp<W, CP, 16, MF>;
+        case 32: return (const void*)k_trsv_mp<W, CP, 32, MF>;
+        default: return (const void*)k_trsv_mp<W, CP, 4, MF>;
+      }
     }
   }
-  template <typename TS>
-  static const void* lp_fn(int wpb) {
-    switch (wpb) {
-      case 8: return (const void*)k_trsv_lp<W, CP, TS, 8>;
-      case 16: return (const void*)k_trsv_lp<W, CP, TS, 16>;
-      case 32: return (const void*)k_trsv_lp<W, CP, TS, 32>;
-      default: return (const void*)k_trsv_lp<W, CP, TS, 4>;
+  template <typename TS, bool OB>
+  static const void* lp_fn_t(int wpb) {
+    if constexpr (OB) {
+      switch (wpb) {
+        case 8: return (const void*)k_trsv_lp_ob<W, CP, TS, 8>;
+        case 16: return (const void*)k_trsv_lp_ob<W, CP, TS, 16>;
+        case 32: return (const void*)k_trsv_lp_ob<W, CP, TS, 32>;
+        default: return (const void*)k_trsv_lp_ob<W, CP, TS, 4>;
+      }
+    } else {
+      switch (wpb) {
+        case 8: return (const void*)k_trsv_lp<W, CP, TS, 8>;
+        case 16: return (const void*)k_trsv_lp<W, CP, TS, 16>;
+        case 32: return (const void*)k_trsv_lp<W, CP, TS, 32>;
+        default: return (const void*)k_trsv_lp<W, CP, TS, 4>;
+      }
     }
+  }
+  // the substitution kernel of a factor precision, schedule and block size
+  static const void* trsv_fn(int prec, int sched, int wpb) {
+    const bool ob = sched == 1;
+    if (prec == MPK_ILU_FP64) return ob ? mp_fn_t<false, true>(wpb) : mp_fn_t<false, false>(wpb);
+    if (prec == MPK_ILU_MP) return ob ? mp_fn_t<true, true>(wpb) : mp_fn_t<true, false>(wpb);
+    if (prec == MPK_ILU_BF16) return ob ? lp_fn_t<uint16_t, true>(wpb) : lp_fn_t<uint16_t, false>(wpb);
+    return ob ? lp_fn_t<float, true>(wpb) : lp_fn_t<float, false>(wpb);
+  }
+  // the owner-block ring may exceed the default 48 KB of dynamic shared memory: opt in, once per
+  // kernel (the first call comes from the tuner, outside any graph capture)
+  static size_t prepare_fn(const void* fn, int prec, int sched) {
+    if (sched != 1) return 0;
+    const size_t rb = ring_bytes(prec);
+    if (rb > 48 * 1024) {
+      static std::mutex mu;
+      static const void* seen[64];
+      static int nseen = 0;
+      std::lock_guard<std::mutex> lk(mu);
+      bool found = false;
+      for (int k = 0; k < nseen; ++k) found = found || seen[k] == fn;
+      if (!found) {
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rb);
+        if (nseen < 64) seen[nseen++] = fn;
+      }
+    }
+    return rb;
   }
   static int trsv_mp(const IluHandleView& M, bool lower, bool unit, const double* in, double* out, const int* done,
                      cudaStream_t s) {
     // out starts as sentinels: completion is read from the values
     count_launch();
     k_fill_sent<<<grid_for(M.n), kBlock, 0, s>>>((int64_t)M.n * CP * W, out, 0, nullptr, done);
-    const void* fn = M.prec == MPK_ILU_MP ? mp_fn<true>(M.wpb) : mp_fn<false>(M.wpb);
-    return coop(fn, M.wpb, M, lower, unit, in, out, done, s);
+    const void* fn = trsv_fn(M.prec, M.sched, M.wpb);
+    return coop(fn, M.wpb, prepare_fn(fn, M.prec, M.sched), M, lower, unit, in, out, done, s);
   }
   static int trsv32(const IluHandleView& M, bool lower, bool unit, const double* in, double* out, const int* done,
                     cudaStream_t s) {
@@ -1352,16 +1511,15 @@ struct Launch {
     count_launch();
     float* mine = lower ? M.v32 : reinterpret_cast<float*>(M.pk);
     k_fill_sent32<<<grid_for(M.n), kBlock, 0, s>>>((int64_t)M.n * CP, mine, done);
-    const void* fn = M.prec == MPK_ILU_BF16 ? lp_fn<uint16_t>(M.wpb) : lp_fn<float>(M.wpb);
-    return coop(fn, M.wpb, M, lower, unit, in, out, done, s);
+    const void* fn = trsv_fn(M.prec, M.sched, M.wpb);
+    return coop(fn, M.wpb, prepare_fn(fn, M.prec, M.sched), M, lower, unit, in, out, done, s);
   }
-  // largest per-SM warp count whose block fits one SM, for each candidate (0: does not fit)
-  static int trsv_fits(int prec, int wpb) {
-    const void* fn = prec == MPK_ILU_FP64 ? mp_fn<false>(wpb)
-                     : prec == MPK_ILU_MP ? mp_fn<true>(wpb)
-                     : (prec == MPK_ILU_BF16 ? lp_fn<uint16_t>(wpb) : lp_fn<float>(wpb));
+  // 1 if one block of wpb warps (and, owner-block schedule, its ring) fits one SM
+  static int trsv_fits(int prec, int wpb, int sched) {
+    const void* fn = trsv_fn(prec, sched, wpb);
+    const size_t smem = prepare_fn(fn, prec, sched);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, wpb * 32, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, wpb * 32, smem) != cudaSuccess) {
       cudaGetLastError();
       return 0;
     }
