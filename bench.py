@@ -40,10 +40,10 @@ ITERS_128 = {"fp64": 17, "fp32": 18, "bf16": 18}
 # sub-partitions x 0.5 binary64 lanes per clock x 2.07 GHz (a warp instruction holds a
 # sub-partition's FP64 unit 64 cycles; measured by a dependent-FMA probe).  In T op/s.
 FP64_PEAK_OPS = 152 * 4 * 0.5 * 2.07e9 / 1e12
-# DRAM bytes (read + write) of one k_trsv_mp launch pair (both triangles) on the 128^3 workload:
-# dram__bytes_read.sum + dram__bytes_write.sum from an ncu capture of the current kernel
-# (profiles/k_trsv_mp_convdiff3d_128.md); None once the kernel changes.
-TRSV_MP_TRAFFIC = 151913472 + 18082048 + 168578304 + 16981760
+# DRAM bytes (read + write) of one k_trsv_mp launch pair (both triangles, static schedule) on the
+# 128^3 workload: dram__bytes_read.sum + dram__bytes_write.sum from an ncu capture of the current
+# kernel (its summary is under profiles/); None once the kernel changes.
+TRSV_MP_TRAFFIC = 151218176 + 18590976 + 168678912 + 16925184
 
 
 def parse():
@@ -62,6 +62,8 @@ def parse():
                                                      "precond_mp", "ilu_fp64", "ilu_mp"],
                     help="run just this kernel --reps times on the workload (for profiling) and exit")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--only-on", default="convdiff3d", choices=["convdiff3d", "helmholtz2d", "batch512"],
+                    help="the matrix of --only")
     ap.add_argument("--workload", default="convdiff3d",
                     choices=["convdiff3d", "batch512", "learned", "plainrows", "tables"],
                     help="batch512: the batched workload (512 systems, binary32 ILU(0), DD BiCGSTAB); "
@@ -342,7 +344,9 @@ def run_mpk(args):
         rooflines[k]["peak_note"] = "of derived nominal" if rooflines[k]["bound"] == "alu" else pk_note
     # the dominant kernel of the timed solve is the binary64-factor substitution (latency-bound
     # chain of levels; FP64 issue while a level computes); its counters, where taken, are in profiles/
-    rooflines["precond_fp64_dd"]["traffic"] = TRSV_MP_TRAFFIC
+    # (counters of the static-schedule kernel: reported only when the tuner chose that schedule)
+    if extra["substitution_schedule"]["schedule"] == "static":
+        rooflines["precond_fp64_dd"]["traffic"] = TRSV_MP_TRAFFIC
 
     # ---- end to end through the host-buffer C call --------------------------------------------
     e2e = None
@@ -387,10 +391,18 @@ def run_only(args):
     from paper_2504_14498_gb300 import _lib, inputs
 
     torch.cuda.set_device(0)
-    A_t, _ = inputs.convdiff3d(args.m)
+    c = 1
+    if args.only_on == "helmholtz2d":
+        A_t, c = inputs.helmholtz2d(args.m_complex, k=20 * np.pi * args.m_complex / 1024), 2
+    elif args.only_on == "batch512":
+        sizes = inputs.batch_sizes()
+        A_t, _ = inputs.block_diagonal([inputs.batch_system(s_, sizes) for s_ in range(len(sizes))])
+        A_t = (A_t[0], A_t[1].astype(np.int32), A_t[2], A_t[3])
+    else:
+        A_t, _ = inputs.convdiff3d(args.m)
     n, w = A_t[0], 2
-    A = _lib.Matrix.from_tuple(A_t)
-    x = torch.as_tensor(inputs.random_vector(n, w, 1, seed=3), device="cuda")
+    A = _lib.Matrix.from_tuple(A_t, is_complex=(c == 2))
+    x = torch.as_tensor(inputs.random_vector(n, w, c, seed=3), device="cuda")
     y = torch.empty_like(x)
     if args.only in ("spmv", "spmv_mm"):
         fn = lambda: _lib.spmv_mp(A, x, w, y, mp_matrix=args.only == "spmv_mm")
@@ -402,6 +414,8 @@ def run_only(args):
         prec = args.only.split("_")[1]
         M = _lib.ILU0(A, prec, w) if prec == "mp" else _lib.ILU0(A, prec)
         fn = lambda: M.apply(x, w, False, y)
+    if args.only.startswith("precond") or args.only.startswith("spmv"):
+        fn()  # untimed: builds the repacked triangles on first use
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record()
@@ -409,7 +423,9 @@ def run_only(args):
         fn()
     e1.record()
     torch.cuda.synchronize()
-    print(json.dumps({"only": args.only, "m": args.m, "reps": args.reps, "ms_per_rep": e0.elapsed_time(e1) / args.reps}))
+    sched = M.schedule() if args.only.startswith("precond") else None
+    print(json.dumps({"only": args.only, "on": args.only_on, "m": args.m, "reps": args.reps,
+                      "ms_per_rep": e0.elapsed_time(e1) / args.reps, "schedule": sched}))
     return 0
 
 

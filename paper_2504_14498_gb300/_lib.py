@@ -184,10 +184,11 @@ class ILU0:
         self.handle = h
 
     def schedule(self):
-        """(schedule, warps per SM) of the substitutions: 'static' or 'owner'."""
+        """(schedule, warps per SM) of the substitutions: 'static', 'owner', 'cluster8' or
+        'cluster16'."""
         wpb = ctypes.c_int(0)
         sc = lib().mpk_ilu0_schedule(self.handle, ctypes.byref(wpb))
-        return ("static", "owner")[sc], wpb.value
+        return ("static", "owner", "cluster8", "cluster16")[sc], wpb.value
 
     def values(self) -> torch.Tensor:
         out = torch.empty(self.A.nnz * self.A.cp * self.w, dtype=torch.float64, device="cuda")

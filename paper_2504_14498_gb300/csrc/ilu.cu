@@ -573,9 +573,11 @@ __global__ void k_sell_width(int nchunks, const int* __restrict__ perm, const in
 // is still in the block's ring when this row's group runs (its position + kRing reaches the end
 // of the group, enc.cgend of the chunk) is encoded as -2 - ring slot and left out of rep.
 struct ObEnc {
-  const int* blk = nullptr;     // row -> owner block
-  const int* bstart = nullptr;  // block -> first position
-  const int* cgend = nullptr;   // chunk -> end position of its group
+  const int* blk = nullptr;      // row -> owner block
+  const int* bstart = nullptr;   // block -> first position
+  const int* cgend = nullptr;    // chunk -> end position of its group
+  const int* cgstart = nullptr;  // chunk -> first chunk of its group (the CTA of a chunk in a cluster)
+  int csize = 1;                 // CTAs per block
 };
 __device__ __forceinline__ double one_of(double) { return 1.0; }
 __device__ __forceinline__ float one_of(float) { return 1.0f; }
@@ -604,7 +606,8 @@ __global__ void k_sell_fill(int nchunks, const int* __restrict__ perm, const int
       if (k < len) {
         const int j = ci[p + k], qj = pos[j];
         if (bi >= 0 && enc.blk[j] == bi && qj + kRing >= gend) {
-          cv = -2 - (qj - enc.bstart[bi]) % kRing;
+          const int rank = ((qj >> 5) - enc.cgstart[qj >> 5]) % enc.csize;
+          cv = -2 - (rank * kRing + (qj - enc.bstart[bi]) % kRing);
         } else {
           cv = j;
           last = max(last, qj);
@@ -708,7 +711,7 @@ __global__ void k_ob_pad(int K, const int* __restrict__ cnt, int* __restrict__ p
 // off: K + 1 padded position offsets; gid: K + 1 group numbers (exclusive scans)
 __global__ void k_ob_groups(int K, int B, int nl, const int* __restrict__ cnt, const int* __restrict__ off,
                             const int* __restrict__ gid, int* __restrict__ goff, int* __restrict__ bgrp,
-                            int* __restrict__ bstart, int* __restrict__ cgend) {
+                            int* __restrict__ bstart, int* __restrict__ cgend, int* __restrict__ cgstart) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= K; k += gridDim.x * blockDim.x) {
     if (k == K) {
       goff[gid[K]] = off[K] >> 5;
@@ -722,7 +725,10 @@ __global__ void k_ob_groups(int K, int B, int nl, const int* __restrict__ cnt, c
     }
     if (cnt[k] > 0) {
       goff[gid[k]] = off[k] >> 5;
-      for (int c = off[k] >> 5; c < (off[k + 1] >> 5); ++c) cgend[c] = off[k + 1];
+      for (int c = off[k] >> 5; c < (off[k + 1] >> 5); ++c) {
+        cgend[c] = off[k + 1];
+        cgstart[c] = off[k] >> 5;
+      }
     }
   }
 }
@@ -746,11 +752,43 @@ static Orient orient(const mpk_ilu* M, int t) {
   return Orient{M->rpT, M->ciT, M->diagT, M->facT};
 }
 
+// Empty kernel whose launch configuration (one CTA per SM through its shared memory, clusters
+// of csize) gives the number of clusters that can be co-resident.
+__global__ void k_cluster_slot() {}
+static int cluster_count(int csize) {
+  static std::mutex mu;
+  static int known[17] = {0};
+  std::lock_guard<std::mutex> lk(mu);
+  if (known[csize] != 0) return known[csize];
+  int n = -1;
+  cudaFuncSetAttribute(k_cluster_slot, cudaFuncAttributeMaxDynamicSharedMemorySize, kClusterSmem);
+  if (csize > 8) cudaFuncSetAttribute(k_cluster_slot, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = csize;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(csize);
+  cfg.blockDim = dim3(128);
+  cfg.dynamicSmemBytes = kClusterSmem;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int active = 0;
+  if (cudaOccupancyMaxActiveClusters(&active, k_cluster_slot, &cfg) == cudaSuccess && active > 0)
+    n = active < sm_count() / csize ? active : sm_count() / csize;
+  cudaGetLastError();
+  known[csize] = n;
+  return n;
+}
+
 template <typename T>
-static int build_ob_t(mpk_ilu* M, int t, cudaStream_t s) {
+static int build_ob_t(mpk_ilu* M, int t, int sched, cudaStream_t s) {
   const Orient o = orient(M, t);
   const bool lower = (t % 2) == 0;
-  const int n = M->n, nl = M->nlevels[t], B = sm_count();
+  const int csize = sched_csize(sched);
+  const int n = M->n, nl = M->nlevels[t], B = sched == 1 ? sm_count() : cluster_count(csize);
+  if (B < 1) return fail(MPK_INVALID_ARG, "no co-resident clusters of this size");
   const int64_t K64 = (int64_t)B * nl;
   if (K64 > (1 << 28)) return fail(MPK_INVALID_ARG, "too many levels for the owner-block layout");
   const int K = (int)K64;
@@ -780,9 +818,9 @@ static int build_ob_t(mpk_ilu* M, int t, cudaStream_t s) {
   MPK_CUDA(cudaStreamSynchronize(s));
   const int P = tot[0], G = tot[1], nch = P / 32;
   // persistent order buffer: perm (P) | pos (n) | goff (G + 1) | bgrp (B + 1) | bstart (B + 1) |
-  // cgend (nch; needed only while repacking)
+  // cgend, cgstart (nch each; needed only while repacking)
   int* ob = nullptr;
-  const size_t ob_ints = (size_t)P + n + (size_t)G + 1 + 2 * ((size_t)B + 1) + (size_t)nch;
+  const size_t ob_ints = (size_t)P + n + (size_t)G + 1 + 2 * ((size_t)B + 1) + 2 * (size_t)nch;
   MPK_CUDA(cudaMalloc((void**)&ob, sizeof(int) * ob_ints));
   int* perm = ob;
   int* pos = perm + P;
@@ -790,26 +828,30 @@ static int build_ob_t(mpk_ilu* M, int t, cudaStream_t s) {
   int* bgrp = goff + G + 1;
   int* bstart = bgrp + B + 1;
   int* cgend = bstart + B + 1;
+  int* cgstart = cgend + nch;
   MPK_CUDA(cudaMemsetAsync(perm, 0xff, sizeof(int) * (size_t)P, s));  // padding positions: -1
   count_launch(2);
-  k_ob_groups<<<grid_for(K + 1), kBlock, 0, s>>>(K, B, nl, cnt, off, gid, goff, bgrp, bstart, cgend);
+  k_ob_groups<<<grid_for(K + 1), kBlock, 0, s>>>(K, B, nl, cnt, off, gid, goff, bgrp, bstart, cgend, cgstart);
   k_ob_scatter<<<grid_for(n), kBlock, 0, s>>>(n, nl, blk, M->depth[t], off, perm, pos);  // off becomes ends
   MPK_CUDA(cudaGetLastError());
   ObEnc enc;
   enc.blk = blk;
   enc.bstart = bstart;
   enc.cgend = cgend;
-  M->obbuf[t] = ob;
+  enc.cgstart = cgstart;
+  enc.csize = csize;
+  M->ordbuf[sched][t] = ob;
   int st = build_sell<T>(n, M->vals_per_entry(), o.rp, o.ci, o.diag, (const T*)o.fac, perm, pos, nch, lower, enc,
-                         M->obsellbuf + t, M->sellob + t, s);
+                         &M->laybuf[sched][t], &M->lay[sched][t], s);
   MPK_CUDA(cudaFreeAsync(tmp, s));
   if (st != MPK_OK) return st;
-  SellTri& L = M->sellob[t];
+  SellTri& L = M->lay[sched][t];
   L.ob = 1;
   L.goff = goff;
   L.bgrp = bgrp;
   L.bstart = bstart;
   L.nblocks = B;
+  L.csize = csize;
   return MPK_OK;
 }
 
@@ -822,32 +864,25 @@ static int build_classic_t(mpk_ilu* M, int t, cudaStream_t s) {
   MPK_CUDA(cudaMemcpyAsync(&nch, lo.nchunks, sizeof(int), cudaMemcpyDeviceToHost, s));
   MPK_CUDA(cudaStreamSynchronize(s));
   return build_sell<T>(M->n, M->vals_per_entry(), o.rp, o.ci, o.diag, (const T*)o.fac, lo.perm, lo.pos, nch,
-                       (t % 2) == 0, ObEnc(), M->sellbuf + t, M->sell + t, s);
+                       (t % 2) == 0, ObEnc(), &M->laybuf[0][t], &M->lay[0][t], s);
 }
 
 template <typename T>
 static int build_layout_t(mpk_ilu* M, int t, int sched, cudaStream_t s) {
-  return sched == 1 ? build_ob_t<T>(M, t, s) : build_classic_t<T>(M, t, s);
+  return sched >= 1 ? build_ob_t<T>(M, t, sched, s) : build_classic_t<T>(M, t, s);
 }
 
 static void drop_layout(mpk_ilu* M, int t, int sched) {
-  if (sched == 1) {
-    if (M->obsellbuf[t] != nullptr) cudaFree(M->obsellbuf[t]);
-    if (M->obbuf[t] != nullptr) cudaFree(M->obbuf[t]);
-    M->obsellbuf[t] = nullptr;
-    M->obbuf[t] = nullptr;
-    M->sellob[t] = SellTri();
-  } else {
-    if (M->sellbuf[t] != nullptr) cudaFree(M->sellbuf[t]);
-    M->sellbuf[t] = nullptr;
-    M->sell[t] = SellTri();
-  }
+  if (M->laybuf[sched][t] != nullptr) cudaFree(M->laybuf[sched][t]);
+  if (M->ordbuf[sched][t] != nullptr) cudaFree(M->ordbuf[sched][t]);
+  M->laybuf[sched][t] = nullptr;
+  M->ordbuf[sched][t] = nullptr;
+  M->lay[sched][t] = SellTri();
 }
 
 int ensure_layout(mpk_ilu* M, int t0, int sched, cudaStream_t s) {
   for (int t = t0; t < t0 + 2; ++t) {
-    const bool have = sched == 1 ? M->obsellbuf[t] != nullptr : M->sellbuf[t] != nullptr;
-    if (have) continue;
+    if (M->laybuf[sched][t] != nullptr) continue;
     if (t >= 2 && M->rpT == nullptr) return fail(MPK_INVALID_ARG, "the conjugate transpose is not built");
     int st;
     if (M->prec == MPK_ILU_FP64 || M->prec == MPK_ILU_MP) st = build_layout_t<double>(M, t, sched, s);
@@ -939,10 +974,8 @@ int precond_apply(const mpk_ilu* M, const Ops* o, bool trans, const double* r, d
 // triangle and the conjugate transpose (all rebuilt on their next use).
 int refresh_factor(mpk_ilu* M, cudaStream_t s) {
   MPK_CUDA(cudaStreamSynchronize(s));
-  for (int t = 0; t < 4; ++t) {
-    drop_layout(M, t, 0);
-    drop_layout(M, t, 1);
-  }
+  for (int t = 0; t < 4; ++t)
+    for (int sc = 0; sc < kScheds; ++sc) drop_layout(M, t, sc);
   void* tp[] = {M->rpT, M->ciT, M->diagT, M->facT, M->lvbuf[2], M->lvbuf[3], M->depth[2], M->depth[3]};
   for (void* p : tp)
     if (p != nullptr) cudaFree(p);
@@ -955,10 +988,11 @@ int refresh_factor(mpk_ilu* M, cudaStream_t s) {
 }
 
 // ---- substitution autotuner ---------------------------------------------------------------------
-// Candidates: both schedules (static chunk schedule, owner-block schedule) x warps per SM
-// {4, 8, 16, 32}, each timed on two applications of M^-1; the choice is cached per (matrix
-// pattern, factor precision, w, c).  MPK_SUBST_SCHEDULE=static|owner restricts the candidates to
-// one schedule (tests use it to cover both).
+// Candidates: the static chunk schedule and the owner-block schedule per SM with 4, 8, 16 or 32
+// warps per SM, the owner-block schedule per cluster of 8 or 16 SMs with 4 or 8 warps per SM,
+// each timed on two applications of M^-1; the choice is cached per (matrix pattern, factor
+// precision, w, c).  MPK_SUBST_SCHEDULE=static|owner|cluster8|cluster16 restricts the
+// candidates to one schedule (tests use it to cover each).
 int read_ctl_err(const mpk_ilu* M, cudaStream_t s);
 struct TrsvTune {
   const void* rp;
@@ -971,6 +1005,8 @@ static int forced_schedule() {
   if (e == nullptr) return -1;
   if (std::strcmp(e, "static") == 0) return 0;
   if (std::strcmp(e, "owner") == 0) return 1;
+  if (std::strcmp(e, "cluster8") == 0) return 2;
+  if (std::strcmp(e, "cluster16") == 0) return 3;
   return -1;
 }
 static bool cached_choice(const mpk_ilu* M, int w, int forced, int* wpb, int* sched) {
@@ -1004,12 +1040,18 @@ int tune_substitution(mpk_ilu* M, const Ops* o, int w, double* r, double* z, cud
   MPK_CUDA(cudaEventCreate(&e1));
   float best = 0.f;
   int best_wpb = 4, best_sched = forced >= 0 ? forced : 0;
-  for (int sc = 0; sc < 2; ++sc) {
+  for (int sc = 0; sc < kScheds; ++sc) {
     if (forced >= 0 && sc != forced) continue;
-    if (ensure_layout(M, 0, sc, s) != MPK_OK) continue;
+    if (ensure_layout(M, 0, sc, s) != MPK_OK) {
+      cudaGetLastError();
+      drop_layout(M, 0, sc);
+      drop_layout(M, 1, sc);
+      continue;
+    }
     M->sched = sc;
     for (int wp : cands) {
-      if (!o->trsv_fits(M->prec, wp, sc)) continue;
+      if (sc >= 2 && wp > 8) continue;  // cluster CTAs: one per SM, 4 or 8 warps
+      if (!o->trsv_fits(M->prec, wp, sc, M->lay[sc][0].nblocks)) continue;
       M->wpb = wp;
       int st = precond_apply(M, o, false, r, z, nullptr, nullptr, s);  // warm
       if (st != MPK_OK) continue;
@@ -1032,7 +1074,9 @@ int tune_substitution(mpk_ilu* M, const Ops* o, int w, double* r, double* z, cud
   M->sched = best_sched;
   const int err = read_ctl_err(M, s);
   if (err != MPK_OK) return err;
-  for (int t = 0; t < 4; ++t) drop_layout(M, t, 1 - best_sched);  // keep the chosen repack only
+  for (int sc = 0; sc < kScheds; ++sc)  // keep the chosen repack only
+    if (sc != best_sched)
+      for (int t = 0; t < 4; ++t) drop_layout(M, t, sc);
   {
     std::lock_guard<std::mutex> lk(g_trsv_mu);
     if (g_trsv.size() < 256)
@@ -1053,12 +1097,11 @@ static void free_handle(mpk_ilu* M) {
   if (M == nullptr) return;
   void* ptrs[] = {M->rp, M->ci, M->diag, M->fac, M->rpT, M->ciT, M->diagT, M->facT, M->flags, M->ctl, M->v32, M->vmp,
                   M->absmax, M->pk, M->lvbuf[0], M->lvbuf[1], M->lvbuf[2], M->lvbuf[3],
-                  M->sellbuf[0], M->sellbuf[1], M->sellbuf[2], M->sellbuf[3],
-                  M->obbuf[0], M->obbuf[1], M->obbuf[2], M->obbuf[3],
-                  M->obsellbuf[0], M->obsellbuf[1], M->obsellbuf[2], M->obsellbuf[3],
                   M->depth[0], M->depth[1], M->depth[2], M->depth[3]};
   for (void* p : ptrs)
     if (p != nullptr) cudaFree(p);
+  for (int sc = 0; sc < kScheds; ++sc)
+    for (int t = 0; t < 4; ++t) drop_layout(M, t, sc);
   delete M;
 }
 
@@ -1085,8 +1128,8 @@ IluHandleView mpk_ilu::view(bool trans) const {
   const int t = trans ? 2 : 0;
   v.lv_lo = level_view(lvbuf[t], n, nlevels[t]);
   v.lv_up = level_view(lvbuf[t + 1], n, nlevels[t + 1]);
-  v.sl_lo = sched == 1 ? sellob[t] : sell[t];
-  v.sl_up = sched == 1 ? sellob[t + 1] : sell[t + 1];
+  v.sl_lo = lay[sched][t];
+  v.sl_up = lay[sched][t + 1];
   v.wpb = wpb;
   v.sched = sched;
   return v;

@@ -143,9 +143,9 @@ struct Ops {
                 cudaStream_t s);
   // bt (nullable): one accumulator per system (out + s)
   void (*absmax)(int n, const double* v, unsigned long long* out, const int* done, const Batch* bt, cudaStream_t s);
-  // 1 if the substitution kernel for factor precision prec fits one block of wpb warps per SM
-  // (sched 1: the owner-block kernel with its shared-memory ring)
-  int (*trsv_fits)(int prec, int wpb, int sched);
+  // 1 if the substitution kernel for factor precision prec, block size wpb warps and schedule
+  // sched can be launched with all its blocks co-resident
+  int (*trsv_fits)(int prec, int wpb, int sched, int nblocks);
 };
 const Ops* get_ops(int w, int cp);
 
@@ -163,7 +163,15 @@ const Ops* get_ops(int w, int cp);
 // shared-memory ring of kRing values is encoded as col = -2 - slot (slot = its position minus
 // bstart[b], modulo kRing); the others keep their column and are polled in global memory; rep
 // then names the latest of those (-1: none).
-constexpr int kRing = 2048;  // values kept per block in shared memory (owner-block schedule)
+// Cluster variants (schedules 2, 3): a block is a thread-block cluster of csize CTAs (one per
+// SM) sharing the group's chunks (chunk m of a group goes to CTA m mod csize); every CTA keeps
+// the values it computed in its own ring, and a local dependency is encoded as
+// -2 - (rank * kRing + slot), read from CTA `rank`'s ring through distributed shared memory
+// after the cluster barrier that ends the producing group.
+constexpr int kRing = 2048;  // values kept per CTA in shared memory (owner-block schedules)
+constexpr int kScheds = 4;   // 0 static, 1 owner-block per SM, 2 / 3 owner-block per cluster of 8 / 16
+constexpr int kClusterSmem = 116 * 1024;  // dynamic shared memory of a cluster CTA: one CTA per SM
+inline int sched_csize(int sched) { return sched == 2 ? 8 : (sched == 3 ? 16 : 1); }
 struct SellTri {
   const int* perm = nullptr;    // 32 * nchunks: row at each position (-1: padding)
   const int* coff = nullptr;    // nchunks + 1
@@ -176,7 +184,8 @@ struct SellTri {
   const int* goff = nullptr;    // groups + 1: first chunk of each (block, level) group
   const int* bgrp = nullptr;    // blocks + 1: first group of each block
   const int* bstart = nullptr;  // blocks + 1: first position of each block
-  int nblocks = 0;              // the grid the layout was built for
+  int nblocks = 0;              // the grid the layout was built for (blocks or clusters)
+  int csize = 1;                // CTAs per block (cluster schedules: 8 or 16)
 };
 
 // Device-side view of an ILU(0) handle used by the substitution kernels (one triangle pair:
@@ -198,7 +207,7 @@ struct IluHandleView {
   SellTri sl_lo, sl_up;              // repacked triangles of the substitutions
   const int* sysid = nullptr;        // batch: row -> system (absmax holds one scale per system)
   int wpb = 4;                       // warps per block (per SM) of the substitution kernels
-  int sched = 0;                     // 0: static chunk schedule, 1: owner-block schedule
+  int sched = 0;                     // see kScheds
 };
 enum CtlIdx : int { CTL_EPOCH = 0, CTL_TICKET_LO, CTL_TICKET_UP, CTL_ERR, CTL_FAIL_ROW, CTL_COUNT };
 
@@ -243,14 +252,14 @@ struct mpk_ilu {
   unsigned long long* pk = nullptr;
   int* lvbuf[4] = {nullptr, nullptr, nullptr, nullptr};  // level orders: lower, upper, transposed lower / upper
   int nlevels[4] = {0, 0, 0, 0};
-  void* sellbuf[4] = {nullptr, nullptr, nullptr, nullptr};  // repacked triangles (same order)
-  mpk::SellTri sell[4];
-  void* obbuf[4] = {nullptr, nullptr, nullptr, nullptr};    // owner-block orders (same order)
-  void* obsellbuf[4] = {nullptr, nullptr, nullptr, nullptr};  // owner-block repacks
-  mpk::SellTri sellob[4];
+  // repacked triangles per schedule (see mpk::kScheds) and orientation (lower, upper, transposed
+  // lower / upper): the repack buffer and, owner-block schedules, the order buffer
+  void* laybuf[mpk::kScheds][4] = {};
+  void* ordbuf[mpk::kScheds][4] = {};
+  mpk::SellTri lay[mpk::kScheds][4];
   int* depth[4] = {nullptr, nullptr, nullptr, nullptr};      // level of every row, per triangle
   int wpb = 4;                   // warps per SM of the substitution kernels (autotuned per pattern)
-  int sched = 0;                 // 0: static chunk schedule, 1: owner-block schedule (autotuned)
+  int sched = 0;                 // substitution schedule (autotuned per pattern)
   const void* src_rp = nullptr;  // the factored matrix's row_ptr address: the tuning cache's key
   mpk::IluHandleView view(bool trans) const;
   int vals_per_entry() const { return cp * wf; }  // doubles (or narrower values) per factor entry

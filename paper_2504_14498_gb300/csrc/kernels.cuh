@@ -918,76 +918,172 @@ __device__ __forceinline__ void wait_pause(long long t0, int ns) {
 // acc /= f_ii, both in w-component arithmetic; fewer entries per group keep the values in
 // registers.
 //
-// One chunk (32 rows) of the substitution, shared by both schedules.  ring (owner-block
-// schedule; nullptr otherwise): the block's shared-memory values, read for the entries encoded
-// as local (col <= -2) and written at own_slot.  Returns the warp-uniform timeout flag.
+// One chunk (32 rows) of the substitution, shared by both schedules, in three steps so that a
+// schedule can load a chunk's operands ahead of its dependencies: mp_meta (the row and slot
+// range), mp_operands (the first group of entries, the right-hand side, the diagonal) and
+// mp_finish (dependency waits, arithmetic, publication).  ring (owner-block schedule; nullptr
+// otherwise): the block's shared-memory values, read for the entries encoded as local
+// (col <= -2) and written at own_slot.  mp_finish returns the warp-uniform timeout flag.
+// Shared-memory ring of an owner-block schedule as seen by one CTA: its own ring (base, and its
+// 32-bit shared address sa) and its rank in the cluster; a local dependency code
+// rank * kRing + slot names a slot of CTA `rank` (rank 0 and csize 1 without clusters).
+struct RingRef {
+  void* base = nullptr;  // nullptr: static schedule, no ring
+  unsigned sa = 0;
+  unsigned rank = 0;
+};
+__device__ __forceinline__ unsigned cta_rank_in_cluster() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_index() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_barrier() {  // release / acquire: orders shared-memory values
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ unsigned cluster_addr(unsigned sa, unsigned rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(sa), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ double ld_cluster_f64(unsigned a) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ float ld_cluster_f32(unsigned a) {
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_cluster_s32(unsigned a, int v) {
+  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+template <int W, int CP>
+__device__ __forceinline__ N<W, CP> ring_read(const RingRef& R, int code) {
+  const unsigned rank = (unsigned)(code / kRing);
+  const int slot = code - (int)rank * kRing;
+  if (rank == R.rank) return n_load<W, CP>((const double*)R.base, slot);
+  N<W, CP> z = n_zero<W, CP>();
+  const unsigned a = cluster_addr(R.sa + (unsigned)slot * (CP * W * 8), rank);
+#pragma unroll
+  for (int k = 0; k < W; ++k) z.re.c[k] = ld_cluster_f64(a + 8u * k);
+  if constexpr (CP == 2) {
+#pragma unroll
+    for (int k = 0; k < W; ++k) z.im.c[k] = ld_cluster_f64(a + 8u * (W + k));
+  }
+  return z;
+}
+template <int CP>
+__device__ __forceinline__ void ring_read32(const RingRef& R, int code, float& xr, float& xi) {
+  const unsigned rank = (unsigned)(code / kRing);
+  const int slot = code - (int)rank * kRing;
+  if (rank == R.rank) {
+    const float* b = (const float*)R.base;
+    xr = b[slot * CP];
+    xi = CP == 2 ? b[slot * CP + 1] : 0.0f;
+    return;
+  }
+  const unsigned a = cluster_addr(R.sa + (unsigned)slot * (CP * 4), rank);
+  xr = ld_cluster_f32(a);
+  xi = CP == 2 ? ld_cluster_f32(a + 4u) : 0.0f;
+}
+
 template <int W, int CP, bool MF>
-__device__ __forceinline__ bool trsv_mp_chunk(const SellTri& T, const IluHandleView& M, bool unit,
-                                              const double* __restrict__ in, double* __restrict__ out, int chunk,
-                                              int i, int b0, int w, int rep, double* ring, int own_slot) {
-  constexpr int KG = (MF && W * CP >= 4) ? 2 : 4;  // entries per group
-  const unsigned FULL = 0xffffffffu;
-  const double* __restrict__ tval = (const double*)T.val;
-  const double* __restrict__ tdia = (const double*)T.dia;
-  const int lane = threadIdx.x & 31;
+struct MpChunk {
+  static constexpr int KG = (MF && W * CP >= 4) ? 2 : 4;  // entries per group
+  int i, b0, w, rep;
   int jj[KG];
   double fr[KG], fi[KG];
   N<W, CP> fv[MF ? KG : 1];
-  auto load_group = [&](int k0) {
+  N<W, CP> acc, dv;
+  double dr, di;
+};
+template <int W, int CP, bool MF>
+__device__ __forceinline__ void mp_meta(const SellTri& T, int chunk, MpChunk<W, CP, MF>& c) {
+  const int lane = threadIdx.x & 31;
+  c.i = T.perm[(chunk << 5) + lane];
+  c.b0 = T.coff[chunk];
+  c.w = T.coff[chunk + 1] - c.b0;
+  c.rep = T.rep[chunk];
+}
+template <int W, int CP, bool MF>
+__device__ __forceinline__ void mp_group(const SellTri& T, int k0, MpChunk<W, CP, MF>& c) {
+  const double* __restrict__ tval = (const double*)T.val;
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int k = 0; k < KG; ++k) {
-      jj[k] = -1;
-      fr[k] = 0.0;
-      fi[k] = 0.0;
-      if constexpr (MF) fv[k] = n_zero<W, CP>();
-      if (k0 + k < w) {
-        const int64_t e = ((int64_t)(b0 + k0 + k) << 5) + lane;
-        jj[k] = T.col[e];
-        if constexpr (MF) fv[k] = n_load<W, CP>(tval, e);
-        else if constexpr (CP == 1) fr[k] = tval[e];
-        else { fr[k] = tval[2 * e]; fi[k] = tval[2 * e + 1]; }
-      }
-    }
-  };
-  load_group(0);
-  N<W, CP> acc = n_zero<W, CP>();
-  double dr = 1.0, di = 0.0;
-  N<W, CP> dv = n_real<W, CP>(1.0);
-  if (i >= 0) {
-    acc = n_load<W, CP>(in, i);
-    if (!unit) {
-      const int64_t q = ((int64_t)chunk << 5) + lane;
-      if constexpr (MF) dv = n_load<W, CP>(tdia, q);
-      else if constexpr (CP == 1) dr = tdia[q];
-      else { dr = tdia[2 * q]; di = tdia[2 * q + 1]; }
+  for (int k = 0; k < MpChunk<W, CP, MF>::KG; ++k) {
+    c.jj[k] = -1;
+    c.fr[k] = 0.0;
+    c.fi[k] = 0.0;
+    if constexpr (MF) c.fv[k] = n_zero<W, CP>();
+    if (k0 + k < c.w) {
+      const int64_t e = ((int64_t)(c.b0 + k0 + k) << 5) + lane;
+      c.jj[k] = T.col[e];
+      if constexpr (MF) c.fv[k] = n_load<W, CP>(tval, e);
+      else if constexpr (CP == 1) c.fr[k] = tval[e];
+      else { c.fr[k] = tval[2 * e]; c.fi[k] = tval[2 * e + 1]; }
     }
   }
+}
+template <int W, int CP, bool MF>
+__device__ __forceinline__ void mp_operands(const SellTri& T, bool unit, const double* __restrict__ in, int chunk,
+                                            MpChunk<W, CP, MF>& c) {
+  const double* __restrict__ tdia = (const double*)T.dia;
+  const int lane = threadIdx.x & 31;
+  mp_group<W, CP, MF>(T, 0, c);
+  c.acc = n_zero<W, CP>();
+  c.dr = 1.0;
+  c.di = 0.0;
+  c.dv = n_real<W, CP>(1.0);
+  if (c.i >= 0) {
+    c.acc = n_load<W, CP>(in, c.i);
+    if (!unit) {
+      const int64_t q = ((int64_t)chunk << 5) + lane;
+      if constexpr (MF) c.dv = n_load<W, CP>(tdia, q);
+      else if constexpr (CP == 1) c.dr = tdia[q];
+      else { c.dr = tdia[2 * q]; c.di = tdia[2 * q + 1]; }
+    }
+  }
+}
+template <int W, int CP, bool MF>
+__device__ __forceinline__ bool mp_finish(const SellTri& T, const IluHandleView& M, bool unit,
+                                          double* __restrict__ out, MpChunk<W, CP, MF>& c, const RingRef& R,
+                                          int own_slot) {
+  constexpr int KG = MpChunk<W, CP, MF>::KG;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
   bool timeout = false;
   const long long t0 = clock64();
   int polls = 0;
-  if (lane == 0 && rep >= 0) {  // the chunk's latest dependency, polled by one lane
+  if (lane == 0 && c.rep >= 0) {  // the chunk's latest dependency, polled by one lane
     N<W, CP> r;
-    while (!n_poll<W, CP>(out, rep, r)) {
+    while (!n_poll<W, CP>(out, c.rep, r)) {
       if (wait_expired(t0, polls, M.ctl)) { timeout = true; break; }
       wait_pause(t0, 128);
     }
   }
   __syncwarp();
-  for (int k0 = 0; k0 < w; k0 += KG) {
-    if (k0 > 0) load_group(k0);
+  N<W, CP> acc = c.acc;
+  for (int k0 = 0; k0 < c.w; k0 += KG) {
+    if (k0 > 0) mp_group<W, CP, MF>(T, k0, c);
     N<W, CP> v[KG];
     unsigned need = 0u;
 #pragma unroll
     for (int k = 0; k < KG; ++k) {
       v[k] = n_zero<W, CP>();
-      if (jj[k] >= 0) need |= 1u << k;
-      else if (jj[k] <= -2) v[k] = n_load<W, CP>(ring, -2 - jj[k]);  // computed by this block
+      if (c.jj[k] >= 0) need |= 1u << k;
+      else if (c.jj[k] <= -2) v[k] = ring_read<W, CP>(R, -2 - c.jj[k]);  // computed by this block
     }
     while (__any_sync(FULL, need != 0u && !timeout)) {
       // every outstanding load of the round is issued before any is checked
 #pragma unroll
       for (int k = 0; k < KG; ++k)
-        if ((need >> k) & 1u) n_fetch<W, CP>(out, jj[k], v[k]);
+        if ((need >> k) & 1u) n_fetch<W, CP>(out, c.jj[k], v[k]);
       unsigned got = 0u;
 #pragma unroll
       for (int k = 0; k < KG; ++k)
@@ -997,22 +1093,22 @@ __device__ __forceinline__ bool trsv_mp_chunk(const SellTri& T, const IluHandleV
       if (__any_sync(FULL, need != 0u)) __nanosleep(64);
     }
     __syncwarp();
-    if (!timeout && i >= 0) {
+    if (!timeout && c.i >= 0) {
 #pragma unroll
       for (int k = 0; k < KG; ++k) {
-        if (jj[k] == -1) continue;
-        if constexpr (MF) acc = n_sub<W, CP>(acc, n_mul<W, CP>(fv[k], v[k]));
-        else acc = n_sub<W, CP>(acc, n_mul_fp<W, CP>(v[k], fr[k], fi[k]));
+        if (c.jj[k] == -1) continue;
+        if constexpr (MF) acc = n_sub<W, CP>(acc, n_mul<W, CP>(c.fv[k], v[k]));
+        else acc = n_sub<W, CP>(acc, n_mul_fp<W, CP>(v[k], c.fr[k], c.fi[k]));
       }
     }
   }
-  if (!timeout && i >= 0) {
+  if (!timeout && c.i >= 0) {
     if (!unit) {
-      if constexpr (MF) acc = n_div<W, CP>(acc, dv);
-      else acc = n_div_fp<W, CP>(acc, dr, di);
+      if constexpr (MF) acc = n_div<W, CP>(acc, c.dv);
+      else acc = n_div_fp<W, CP>(acc, c.dr, c.di);
     }
-    n_publish<W, CP>(out, i, acc);
-    if (ring != nullptr) n_store<W, CP>(ring, own_slot, acc);
+    n_publish<W, CP>(out, c.i, acc);
+    if (R.base != nullptr) n_store<W, CP>((double*)R.base, own_slot, acc);
   }
   return __any_sync(FULL, timeout);
 }
@@ -1026,23 +1122,16 @@ __global__ void __launch_bounds__(WPB * 32, 1)
   const int lane = threadIdx.x & 31;
   const int G = gridDim.x * (blockDim.x >> 5);
   const int g = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
-  int nx_i = -1, nx_b0 = 0, nx_b1 = 0, nx_rep = -1;
-  if (g < T.nchunks) {
-    nx_i = T.perm[(g << 5) + lane];
-    nx_b0 = T.coff[g];
-    nx_b1 = T.coff[g + 1];
-    nx_rep = T.rep[g];
-  }
+  MpChunk<W, CP, MF> c, nx;
+  if (g < T.nchunks) mp_meta<W, CP, MF>(T, g, nx);
   for (int chunk = g; chunk < T.nchunks; chunk += G) {
-    const int i = nx_i, b0 = nx_b0, w = nx_b1 - nx_b0, rep = nx_rep;
-    const int nc = chunk + G;  // the next chunk's row and slot range, fetched ahead
-    if (nc < T.nchunks) {
-      nx_i = T.perm[(nc << 5) + lane];
-      nx_b0 = T.coff[nc];
-      nx_b1 = T.coff[nc + 1];
-      nx_rep = T.rep[nc];
-    }
-    if (trsv_mp_chunk<W, CP, MF>(T, M, unit, in, out, chunk, i, b0, w, rep, nullptr, 0)) {
+    c.i = nx.i;
+    c.b0 = nx.b0;
+    c.w = nx.w;
+    c.rep = nx.rep;
+    mp_operands<W, CP, MF>(T, unit, in, chunk, c);
+    if (chunk + G < T.nchunks) mp_meta<W, CP, MF>(T, chunk + G, nx);  // the next chunk's rows, ahead
+    if (mp_finish<W, CP, MF>(T, M, unit, out, c, RingRef(), 0)) {
       if (lane == 0) atomicCAS(M.ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
       return;
     }
@@ -1054,11 +1143,13 @@ __global__ void __launch_bounds__(WPB * 32, 1)
 // block barrier, after which the group's values are in the block's shared-memory ring.  Only
 // dependencies on other blocks' rows (or on own rows that left the ring) are polled in global
 // memory: on a mesh in natural order with contiguous row blocks those are the rows of the
-// neighbouring block, so most levels cost a barrier instead of a cross-SM notification.
-// Deadlock-free with all blocks resident (cooperative launch): a block waits only for rows of
-// lower levels, and the block with the lowest current level waits for nothing unfinished.  A
-// timed-out wait sets MPK_TIMEOUT and a block flag; every warp still reaches the barrier, then
-// the block leaves.
+// neighbouring block, so such levels cost a barrier instead of a cross-SM notification.  A
+// warp loads its next chunk's rows before computing the current one and that chunk's operands
+// right after (they do not depend on the current values), so no load latency sits between a
+// barrier and the arithmetic.  Deadlock-free with all blocks resident (cooperative launch): a
+// block waits only for rows of lower levels, and the block with the lowest current level waits
+// for nothing unfinished.  A timed-out wait sets MPK_TIMEOUT and a block flag; every warp still
+// reaches the barrier, then the block leaves.
 template <int W, int CP, int WPB, bool MF>
 __global__ void __launch_bounds__(WPB * 32, 1)
     k_trsv_mp_ob(IluHandleView M, bool lower, bool unit, const double* __restrict__ in, double* __restrict__ out,
@@ -1072,23 +1163,116 @@ __global__ void __launch_bounds__(WPB * 32, 1)
   if (threadIdx.x == 0) abort_blk = 0;
   __syncthreads();
   if (b >= T.nblocks) return;
-  const int bs = T.bstart[b], g1 = T.bgrp[b + 1];
-  for (int g = T.bgrp[b]; g < g1; ++g) {
-    const int c1 = T.goff[g + 1];
-    for (int chunk = T.goff[g] + warp; chunk < c1; chunk += WPB) {
-      const int i = T.perm[(chunk << 5) + lane];
-      const int b0 = T.coff[chunk], w = T.coff[chunk + 1] - b0, rep = T.rep[chunk];
+  RingRef R;
+  R.base = ring_mp;
+  const int bs = T.bstart[b], gbeg = T.bgrp[b], gend = T.bgrp[b + 1];
+  // chunk bounds of the current group and the next one: [cg0, cg1), [cg1, cg2)
+  int cg0 = 0, cg1 = 0, cg2 = 0;
+  if (gbeg < gend) {
+    cg0 = T.goff[gbeg];
+    cg1 = T.goff[gbeg + 1];
+    cg2 = gbeg + 1 < gend ? T.goff[gbeg + 2] : cg1;
+  }
+  MpChunk<W, CP, MF> c, nx;
+  bool ahead = false;  // c holds the operands of this warp's next chunk
+  for (int g = gbeg; g < gend; ++g) {
+    const int cg3 = g + 2 < gend ? T.goff[g + 3] : cg2;
+    for (int chunk = cg0 + warp; chunk < cg1; chunk += WPB) {
+      if (!ahead) {
+        mp_meta<W, CP, MF>(T, chunk, c);
+        mp_operands<W, CP, MF>(T, unit, in, chunk, c);
+      }
+      int nxt = chunk + WPB;  // this warp's next chunk: in this group, else its chunk of the next group
+      if (nxt >= cg1) nxt = (g + 1 < gend && cg1 + warp < cg2) ? cg1 + warp : -1;
+      if (nxt >= 0) mp_meta<W, CP, MF>(T, nxt, nx);
       const int own = ((chunk << 5) + lane - bs) % kRing;
-      if (trsv_mp_chunk<W, CP, MF>(T, M, unit, in, out, chunk, i, b0, w, rep, ring_mp, own)) {
+      if (mp_finish<W, CP, MF>(T, M, unit, out, c, R, own)) {
         if (lane == 0) {
           atomicCAS(M.ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
           abort_blk = 1;
         }
+        ahead = false;
         break;
+      }
+      ahead = nxt >= 0;
+      if (ahead) {
+        mp_operands<W, CP, MF>(T, unit, in, nxt, nx);
+        c = nx;
       }
     }
     __syncthreads();
     if (abort_blk) return;
+    cg0 = cg1;
+    cg1 = cg2;
+    cg2 = cg3;
+  }
+}
+
+// Owner-block schedule per thread-block cluster of CS CTAs (one per SM): cluster b runs its
+// groups in order; chunk m of a group goes to CTA m mod CS, warp (m / CS) mod WPB; a CTA keeps
+// its values in its own ring, and a dependency computed by another CTA of the cluster is read
+// through distributed shared memory.  Groups are separated by cluster barriers (release /
+// acquire).  A timed-out wait sets MPK_TIMEOUT and writes the abort flag of every CTA of the
+// cluster before the barrier, so all of them leave after it; no CTA touches another's shared
+// memory after the last barrier it passes.
+template <int W, int CP, int WPB, bool MF, int CS>
+__global__ void __launch_bounds__(WPB * 32, 1)
+    k_trsv_mp_cl(IluHandleView M, bool lower, bool unit, const double* __restrict__ in, double* __restrict__ out,
+                 const int* __restrict__ done) {
+  if (is_done(done)) return;  // the same for every CTA: no barrier is left waiting
+  extern __shared__ double ring_mc[];
+  __shared__ int abort_blk;
+  const SellTri T = lower ? M.sl_lo : M.sl_up;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  RingRef R;
+  R.base = ring_mc;
+  R.sa = (unsigned)__cvta_generic_to_shared(ring_mc);
+  R.rank = cta_rank_in_cluster();
+  const int b = (int)cluster_index();
+  if (threadIdx.x == 0) abort_blk = 0;
+  cluster_barrier();  // every CTA's flag is set before any CTA may write it
+  if (b >= T.nblocks) return;  // the whole cluster
+  const unsigned abort_sa = (unsigned)__cvta_generic_to_shared(&abort_blk);
+  const int bs = T.bstart[b], gbeg = T.bgrp[b], gend = T.bgrp[b + 1];
+  int cg0 = 0, cg1 = 0, cg2 = 0;
+  if (gbeg < gend) {
+    cg0 = T.goff[gbeg];
+    cg1 = T.goff[gbeg + 1];
+    cg2 = gbeg + 1 < gend ? T.goff[gbeg + 2] : cg1;
+  }
+  const int first = (int)R.rank + CS * warp, stride = CS * WPB;
+  MpChunk<W, CP, MF> c, nx;
+  bool ahead = false;
+  for (int g = gbeg; g < gend; ++g) {
+    const int cg3 = g + 2 < gend ? T.goff[g + 3] : cg2;
+    for (int chunk = cg0 + first; chunk < cg1; chunk += stride) {
+      if (!ahead) {
+        mp_meta<W, CP, MF>(T, chunk, c);
+        mp_operands<W, CP, MF>(T, unit, in, chunk, c);
+      }
+      int nxt = chunk + stride;
+      if (nxt >= cg1) nxt = (g + 1 < gend && cg1 + first < cg2) ? cg1 + first : -1;
+      if (nxt >= 0) mp_meta<W, CP, MF>(T, nxt, nx);
+      const int own = ((chunk << 5) + lane - bs) % kRing;
+      if (mp_finish<W, CP, MF>(T, M, unit, out, c, R, own)) {
+        if (lane == 0) {
+          atomicCAS(M.ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
+          for (int r = 0; r < CS; ++r) st_cluster_s32(cluster_addr(abort_sa, (unsigned)r), 1);
+        }
+        ahead = false;
+        break;
+      }
+      ahead = nxt >= 0;
+      if (ahead) {
+        mp_operands<W, CP, MF>(T, unit, in, nxt, nx);
+        c = nx;
+      }
+    }
+    cluster_barrier();
+    if (abort_blk) return;
+    cg0 = cg1;
+    cg1 = cg2;
+    cg2 = cg3;
   }
 }
 
@@ -1125,83 +1309,109 @@ __device__ __forceinline__ bool f_poll(const float* __restrict__ v, int j, float
   return __float_as_uint(xr) != kSent32 && (CP == 1 || __float_as_uint(xi) != kSent32);
 }
 
-// One chunk of the binary32 substitution, shared by both schedules (ring: see trsv_mp_chunk).
-template <int W, int CP, typename TS>
-__device__ __forceinline__ bool trsv_lp_chunk(const SellTri& T, const IluHandleView& M, bool lower, bool unit,
-                                              const double* __restrict__ in, double* __restrict__ out, int chunk,
-                                              int i, int b0, int w, int rep, int e1, float* ring, int own_slot) {
-  constexpr int KG = 8;  // entries per group
-  const unsigned FULL = 0xffffffffu;
-  const TS* __restrict__ tval = (const TS*)T.val;
-  const TS* __restrict__ tdia = (const TS*)T.dia;
-  float* __restrict__ mine = lower ? M.v32 : reinterpret_cast<float*>(M.pk);
-  const int lane = threadIdx.x & 31;
+// One chunk of the binary32 substitution, shared by both schedules, in the three steps of the
+// binary64 one (lp_meta, lp_operands, lp_finish; ring: see mp_finish).  e1: the scale exponent
+// of a single system (a batch reads each row's system's).
+template <typename TS>
+struct LpChunk {
+  static constexpr int KG = 8;  // entries per group
+  int i, b0, w, rep, e;
   int jj[KG];
   float fr[KG], fi[KG];
-  auto load_group = [&](int k0) {
+  float ar, ai, dr, di;
+};
+template <typename TS>
+__device__ __forceinline__ void lp_meta(const SellTri& T, int chunk, LpChunk<TS>& c) {
+  const int lane = threadIdx.x & 31;
+  c.i = T.perm[(chunk << 5) + lane];
+  c.b0 = T.coff[chunk];
+  c.w = T.coff[chunk + 1] - c.b0;
+  c.rep = T.rep[chunk];
+}
+template <int CP, typename TS>
+__device__ __forceinline__ void lp_group(const SellTri& T, int k0, LpChunk<TS>& c) {
+  const TS* __restrict__ tval = (const TS*)T.val;
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int k = 0; k < KG; ++k) {
-      jj[k] = -1;
-      fr[k] = 0.0f;
-      fi[k] = 0.0f;
-      if (k0 + k < w) {
-        const int64_t s = ((int64_t)(b0 + k0 + k) << 5) + lane;
-        jj[k] = T.col[s];
-        if constexpr (CP == 1) fr[k] = ld_fac(tval, s);
-        else { fr[k] = ld_fac(tval, 2 * s); fi[k] = ld_fac(tval, 2 * s + 1); }
-      }
+  for (int k = 0; k < LpChunk<TS>::KG; ++k) {
+    c.jj[k] = -1;
+    c.fr[k] = 0.0f;
+    c.fi[k] = 0.0f;
+    if (k0 + k < c.w) {
+      const int64_t s = ((int64_t)(c.b0 + k0 + k) << 5) + lane;
+      c.jj[k] = T.col[s];
+      if constexpr (CP == 1) c.fr[k] = ld_fac(tval, s);
+      else { c.fr[k] = ld_fac(tval, 2 * s); c.fi[k] = ld_fac(tval, 2 * s + 1); }
     }
-  };
-  load_group(0);
-  float ar = 0.0f, ai = 0.0f, dr = 1.0f, di = 0.0f;
-  const int e = (M.sysid != nullptr && i >= 0) ? scale_exponent(M.absmax + M.sysid[i]) : e1;
-  if (i >= 0) {
+  }
+}
+template <int W, int CP, typename TS>
+__device__ __forceinline__ void lp_operands(const SellTri& T, const IluHandleView& M, bool lower, bool unit,
+                                            const double* __restrict__ in, int chunk, int e1, LpChunk<TS>& c) {
+  const TS* __restrict__ tdia = (const TS*)T.dia;
+  const int lane = threadIdx.x & 31;
+  lp_group<CP, TS>(T, 0, c);
+  c.ar = 0.0f;
+  c.ai = 0.0f;
+  c.dr = 1.0f;
+  c.di = 0.0f;
+  c.e = (M.sysid != nullptr && c.i >= 0) ? scale_exponent(M.absmax + M.sysid[c.i]) : e1;
+  if (c.i >= 0) {
     if (lower) {
-      const double* q = in + (int64_t)i * CP * W;
-      ar = __double2float_rn(ldexp(q[0], -e));
-      ai = CP == 2 ? __double2float_rn(ldexp(q[W], -e)) : 0.0f;
+      const double* q = in + (int64_t)c.i * CP * W;
+      c.ar = __double2float_rn(ldexp(q[0], -c.e));
+      c.ai = CP == 2 ? __double2float_rn(ldexp(q[W], -c.e)) : 0.0f;
     } else {
-      ar = M.v32[(int64_t)i * CP];
-      ai = CP == 2 ? M.v32[(int64_t)i * CP + 1] : 0.0f;
+      c.ar = M.v32[(int64_t)c.i * CP];
+      c.ai = CP == 2 ? M.v32[(int64_t)c.i * CP + 1] : 0.0f;
     }
     if (!unit) {
       const int64_t q = ((int64_t)chunk << 5) + lane;
-      if constexpr (CP == 1) dr = ld_fac(tdia, q);
-      else { dr = ld_fac(tdia, 2 * q); di = ld_fac(tdia, 2 * q + 1); }
+      if constexpr (CP == 1) c.dr = ld_fac(tdia, q);
+      else { c.dr = ld_fac(tdia, 2 * q); c.di = ld_fac(tdia, 2 * q + 1); }
     }
   }
+}
+template <int W, int CP, typename TS>
+__device__ __forceinline__ bool lp_finish(const SellTri& T, const IluHandleView& M, bool lower, bool unit,
+                                          double* __restrict__ out, LpChunk<TS>& c, const RingRef& R,
+                                          int own_slot) {
+  constexpr int KG = LpChunk<TS>::KG;
+  const unsigned FULL = 0xffffffffu;
+  float* __restrict__ mine = lower ? M.v32 : reinterpret_cast<float*>(M.pk);
+  const int lane = threadIdx.x & 31;
   bool timeout = false;
   const long long t0 = clock64();
   int polls = 0;
-  if (lane == 0 && rep >= 0) {  // the chunk's latest dependency, polled by one lane
+  if (lane == 0 && c.rep >= 0) {  // the chunk's latest dependency, polled by one lane
     float xr, xi;
-    while (!f_poll<CP>(mine, rep, xr, xi)) {
+    while (!f_poll<CP>(mine, c.rep, xr, xi)) {
       if (wait_expired(t0, polls, M.ctl)) { timeout = true; break; }
       wait_pause(t0, 128);
     }
   }
   __syncwarp();
-  for (int k0 = 0; k0 < w; k0 += KG) {
-    if (k0 > 0) load_group(k0);
+  float ar = c.ar, ai = c.ai;
+  for (int k0 = 0; k0 < c.w; k0 += KG) {
+    if (k0 > 0) lp_group<CP, TS>(T, k0, c);
     float vr[KG], vi[KG];
     unsigned need = 0u;
 #pragma unroll
     for (int k = 0; k < KG; ++k) {
       vr[k] = 0.0f;
       vi[k] = 0.0f;
-      if (jj[k] >= 0) {
+      if (c.jj[k] >= 0) {
         need |= 1u << k;
-      } else if (jj[k] <= -2) {  // computed by this block
-        vr[k] = ring[(-2 - jj[k]) * CP];
-        if constexpr (CP == 2) vi[k] = ring[(-2 - jj[k]) * CP + 1];
+      } else if (c.jj[k] <= -2) {  // computed by this block
+        ring_read32<CP>(R, -2 - c.jj[k], vr[k], vi[k]);
       }
     }
     while (__any_sync(FULL, need != 0u && !timeout)) {
 #pragma unroll
       for (int k = 0; k < KG; ++k)
         if ((need >> k) & 1u) {
-          vr[k] = ld_relaxed_f32(mine + (int64_t)jj[k] * CP);
-          if constexpr (CP == 2) vi[k] = ld_relaxed_f32(mine + (int64_t)jj[k] * CP + 1);
+          vr[k] = ld_relaxed_f32(mine + (int64_t)c.jj[k] * CP);
+          if constexpr (CP == 2) vi[k] = ld_relaxed_f32(mine + (int64_t)c.jj[k] * CP + 1);
         }
       unsigned got = 0u;
 #pragma unroll
@@ -1214,42 +1424,44 @@ __device__ __forceinline__ bool trsv_lp_chunk(const SellTri& T, const IluHandleV
       if (__any_sync(FULL, need != 0u)) __nanosleep(64);
     }
     __syncwarp();
-    if (!timeout && i >= 0) {
+    if (!timeout && c.i >= 0) {
 #pragma unroll
       for (int k = 0; k < KG; ++k) {
-        if (jj[k] == -1) continue;
+        if (c.jj[k] == -1) continue;
         if constexpr (CP == 1) {
-          ar = fmaf(-fr[k], vr[k], ar);
+          ar = fmaf(-c.fr[k], vr[k], ar);
         } else {
-          ar = fmaf(-fr[k], vr[k], ar);
-          ar = fmaf(fi[k], vi[k], ar);
-          ai = fmaf(-fr[k], vi[k], ai);
-          ai = fmaf(-fi[k], vr[k], ai);
+          ar = fmaf(-c.fr[k], vr[k], ar);
+          ar = fmaf(c.fi[k], vi[k], ar);
+          ai = fmaf(-c.fr[k], vi[k], ai);
+          ai = fmaf(-c.fi[k], vr[k], ai);
         }
       }
     }
   }
-  if (!timeout && i >= 0) {
+  if (!timeout && c.i >= 0) {
     if (!unit) {
       if constexpr (CP == 1) {
-        ar = ar / dr;
+        ar = ar / c.dr;
       } else {
-        const float den = fmaf(dr, dr, di * di), nr = fmaf(ar, dr, ai * di), ni = fmaf(ai, dr, -(ar * di));
+        const float den = fmaf(c.dr, c.dr, c.di * c.di), nr = fmaf(ar, c.dr, ai * c.di);
+        const float ni = fmaf(ai, c.dr, -(ar * c.di));
         ar = nr / den;
         ai = ni / den;
       }
     }
-    st_relaxed_f32(mine + (int64_t)i * CP, ar);
-    if constexpr (CP == 2) st_relaxed_f32(mine + (int64_t)i * CP + 1, ai);
-    if (ring != nullptr) {
+    st_relaxed_f32(mine + (int64_t)c.i * CP, ar);
+    if constexpr (CP == 2) st_relaxed_f32(mine + (int64_t)c.i * CP + 1, ai);
+    if (R.base != nullptr) {
+      float* ring = (float*)R.base;
       ring[own_slot * CP] = ar;
       if constexpr (CP == 2) ring[own_slot * CP + 1] = ai;
     }
     if (!lower) {
       N<W, CP> z = n_zero<W, CP>();
-      z.re.c[0] = ldexp((double)ar, e);
-      if constexpr (CP == 2) z.im.c[0] = ldexp((double)ai, e);
-      n_store<W, CP>(out, i, z);
+      z.re.c[0] = ldexp((double)ar, c.e);
+      if constexpr (CP == 2) z.im.c[0] = ldexp((double)ai, c.e);
+      n_store<W, CP>(out, c.i, z);
     }
   }
   return __any_sync(FULL, timeout);
@@ -1265,23 +1477,16 @@ __global__ void __launch_bounds__(WPB * 32, 1)
   const int lane = threadIdx.x & 31;
   const int G = gridDim.x * (blockDim.x >> 5);
   const int g = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
-  int nx_i = -1, nx_b0 = 0, nx_b1 = 0, nx_rep = -1;
-  if (g < T.nchunks) {
-    nx_i = T.perm[(g << 5) + lane];
-    nx_b0 = T.coff[g];
-    nx_b1 = T.coff[g + 1];
-    nx_rep = T.rep[g];
-  }
+  LpChunk<TS> c, nx;
+  if (g < T.nchunks) lp_meta<TS>(T, g, nx);
   for (int chunk = g; chunk < T.nchunks; chunk += G) {
-    const int i = nx_i, b0 = nx_b0, w = nx_b1 - nx_b0, rep = nx_rep;
-    const int nc = chunk + G;
-    if (nc < T.nchunks) {
-      nx_i = T.perm[(nc << 5) + lane];
-      nx_b0 = T.coff[nc];
-      nx_b1 = T.coff[nc + 1];
-      nx_rep = T.rep[nc];
-    }
-    if (trsv_lp_chunk<W, CP, TS>(T, M, lower, unit, in, out, chunk, i, b0, w, rep, e1, nullptr, 0)) {
+    c.i = nx.i;
+    c.b0 = nx.b0;
+    c.w = nx.w;
+    c.rep = nx.rep;
+    lp_operands<W, CP, TS>(T, M, lower, unit, in, chunk, e1, c);
+    if (chunk + G < T.nchunks) lp_meta<TS>(T, chunk + G, nx);  // the next chunk's rows, ahead
+    if (lp_finish<W, CP, TS>(T, M, lower, unit, out, c, RingRef(), 0)) {
       if (lane == 0) atomicCAS(M.ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
       return;
     }
@@ -1303,23 +1508,110 @@ __global__ void __launch_bounds__(WPB * 32, 1)
   if (threadIdx.x == 0) abort_blk = 0;
   __syncthreads();
   if (b >= T.nblocks) return;
-  const int bs = T.bstart[b], g1 = T.bgrp[b + 1];
-  for (int g = T.bgrp[b]; g < g1; ++g) {
-    const int c1 = T.goff[g + 1];
-    for (int chunk = T.goff[g] + warp; chunk < c1; chunk += WPB) {
-      const int i = T.perm[(chunk << 5) + lane];
-      const int b0 = T.coff[chunk], w = T.coff[chunk + 1] - b0, rep = T.rep[chunk];
+  RingRef R;
+  R.base = ring_lp;
+  const int bs = T.bstart[b], gbeg = T.bgrp[b], gend = T.bgrp[b + 1];
+  int cg0 = 0, cg1 = 0, cg2 = 0;
+  if (gbeg < gend) {
+    cg0 = T.goff[gbeg];
+    cg1 = T.goff[gbeg + 1];
+    cg2 = gbeg + 1 < gend ? T.goff[gbeg + 2] : cg1;
+  }
+  LpChunk<TS> c, nx;
+  bool ahead = false;
+  for (int g = gbeg; g < gend; ++g) {
+    const int cg3 = g + 2 < gend ? T.goff[g + 3] : cg2;
+    for (int chunk = cg0 + warp; chunk < cg1; chunk += WPB) {
+      if (!ahead) {
+        lp_meta<TS>(T, chunk, c);
+        lp_operands<W, CP, TS>(T, M, lower, unit, in, chunk, e1, c);
+      }
+      int nxt = chunk + WPB;
+      if (nxt >= cg1) nxt = (g + 1 < gend && cg1 + warp < cg2) ? cg1 + warp : -1;
+      if (nxt >= 0) lp_meta<TS>(T, nxt, nx);
       const int own = ((chunk << 5) + lane - bs) % kRing;
-      if (trsv_lp_chunk<W, CP, TS>(T, M, lower, unit, in, out, chunk, i, b0, w, rep, e1, ring_lp, own)) {
+      if (lp_finish<W, CP, TS>(T, M, lower, unit, out, c, R, own)) {
         if (lane == 0) {
           atomicCAS(M.ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
           abort_blk = 1;
         }
+        ahead = false;
         break;
+      }
+      ahead = nxt >= 0;
+      if (ahead) {
+        lp_operands<W, CP, TS>(T, M, lower, unit, in, nxt, e1, nx);
+        c = nx;
       }
     }
     __syncthreads();
     if (abort_blk) return;
+    cg0 = cg1;
+    cg1 = cg2;
+    cg2 = cg3;
+  }
+}
+
+// Owner-block schedule per cluster of the binary32 substitution (see k_trsv_mp_cl).
+template <int W, int CP, typename TS, int WPB, int CS>
+__global__ void __launch_bounds__(WPB * 32, 1)
+    k_trsv_lp_cl(IluHandleView M, bool lower, bool unit, const double* __restrict__ in, double* __restrict__ out,
+                 const int* __restrict__ done) {
+  if (is_done(done)) return;
+  extern __shared__ float ring_lc[];
+  __shared__ int abort_blk;
+  const SellTri T = lower ? M.sl_lo : M.sl_up;
+  const int e1 = M.sysid == nullptr ? scale_exponent(M.absmax) : 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  RingRef R;
+  R.base = ring_lc;
+  R.sa = (unsigned)__cvta_generic_to_shared(ring_lc);
+  R.rank = cta_rank_in_cluster();
+  const int b = (int)cluster_index();
+  if (threadIdx.x == 0) abort_blk = 0;
+  cluster_barrier();
+  if (b >= T.nblocks) return;
+  const unsigned abort_sa = (unsigned)__cvta_generic_to_shared(&abort_blk);
+  const int bs = T.bstart[b], gbeg = T.bgrp[b], gend = T.bgrp[b + 1];
+  int cg0 = 0, cg1 = 0, cg2 = 0;
+  if (gbeg < gend) {
+    cg0 = T.goff[gbeg];
+    cg1 = T.goff[gbeg + 1];
+    cg2 = gbeg + 1 < gend ? T.goff[gbeg + 2] : cg1;
+  }
+  const int first = (int)R.rank + CS * warp, stride = CS * WPB;
+  LpChunk<TS> c, nx;
+  bool ahead = false;
+  for (int g = gbeg; g < gend; ++g) {
+    const int cg3 = g + 2 < gend ? T.goff[g + 3] : cg2;
+    for (int chunk = cg0 + first; chunk < cg1; chunk += stride) {
+      if (!ahead) {
+        lp_meta<TS>(T, chunk, c);
+        lp_operands<W, CP, TS>(T, M, lower, unit, in, chunk, e1, c);
+      }
+      int nxt = chunk + stride;
+      if (nxt >= cg1) nxt = (g + 1 < gend && cg1 + first < cg2) ? cg1 + first : -1;
+      if (nxt >= 0) lp_meta<TS>(T, nxt, nx);
+      const int own = ((chunk << 5) + lane - bs) % kRing;
+      if (lp_finish<W, CP, TS>(T, M, lower, unit, out, c, R, own)) {
+        if (lane == 0) {
+          atomicCAS(M.ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
+          for (int r = 0; r < CS; ++r) st_cluster_s32(cluster_addr(abort_sa, (unsigned)r), 1);
+        }
+        ahead = false;
+        break;
+      }
+      ahead = nxt >= 0;
+      if (ahead) {
+        lp_operands<W, CP, TS>(T, M, lower, unit, in, nxt, e1, nx);
+        c = nx;
+      }
+    }
+    cluster_barrier();
+    if (abort_blk) return;
+    cg0 = cg1;
+    cg1 = cg2;
+    cg2 = cg3;
   }
 }
 
@@ -1422,21 +1714,44 @@ struct Launch {
     count_launch();
     k_absmax<W, CP><<<grid_for(n), kBlock, 0, s>>>(n, v, out, done, bt ? bt->sysid : nullptr);
   }
-  // Launch of a substitution kernel with wpb warps per block, one block per SM, all co-resident
-  // (cooperative launch); smem: dynamic shared memory (the owner-block ring)
-  static int coop(const void* fn, int wpb, size_t smem, const IluHandleView& M, bool lower, bool unit,
-                  const double* in, double* out, const int* done, cudaStream_t s) {
+  // Launch of a substitution kernel with wpb warps per block, all blocks co-resident (cooperative
+  // launch): one block per SM, or (cluster schedules) nblocks clusters of csize CTAs, one CTA per
+  // SM; smem: dynamic shared memory (the owner-block ring)
+  static int coop(const void* fn, int wpb, size_t smem, int sched, int nblocks, const IluHandleView& M, bool lower,
+                  bool unit, const double* in, double* out, const int* done, cudaStream_t s) {
     void* args[] = {(void*)&M, (void*)&lower, (void*)&unit, (void*)&in, (void*)&out, (void*)&done};
     count_launch();
-    const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(sm_count()), dim3(wpb * 32), args, smem, s);
+    if (sched < 2) {
+      const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(sm_count()), dim3(wpb * 32), args, smem, s);
+      return e == cudaSuccess ? MPK_OK : MPK_CUDA_ERROR;
+    }
+    const int cs = sched_csize(sched);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeCooperative;
+    at[1].val.cooperative = 1;
+    cfg.gridDim = dim3(nblocks * cs);
+    cfg.blockDim = dim3(wpb * 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 2;
+    const cudaError_t e = cudaLaunchKernelExC(&cfg, fn, args);
     return e == cudaSuccess ? MPK_OK : MPK_CUDA_ERROR;
   }
   static size_t ring_bytes(int prec) {  // the owner-block kernels' shared-memory ring
     return (size_t)kRing * CP * ((prec == MPK_ILU_FP64 || prec == MPK_ILU_MP) ? W * sizeof(double) : sizeof(float));
   }
-  template <bool MF, bool OB>
+  template <bool MF, int S>
   static const void* mp_fn_t(int wpb) {
-    if constexpr (OB) {
+    if constexpr (S == 2 || S == 3) {
+      constexpr int C = S == 2 ? 8 : 16;
+      return wpb == 8 ? (const void*)k_trsv_mp_cl<W, CP, 8, MF, C> : (const void*)k_trsv_mp_cl<W, CP, 4, MF, C>;
+    } else if constexpr (S == 1) {
       switch (wpb) {
         case 8: return (const void*)k_trsv_mp_ob<W, CP, 8, MF>;
         case 16: return (const void*)k_trsv_mp_ob<W, CP, 16, MF>;
@@ -1452,9 +1767,12 @@ struct Launch {
       }
     }
   }
-  template <typename TS, bool OB>
+  template <typename TS, int S>
   static const void* lp_fn_t(int wpb) {
-    if constexpr (OB) {
+    if constexpr (S == 2 || S == 3) {
+      constexpr int C = S == 2 ? 8 : 16;
+      return wpb == 8 ? (const void*)k_trsv_lp_cl<W, CP, TS, 8, C> : (const void*)k_trsv_lp_cl<W, CP, TS, 4, C>;
+    } else if constexpr (S == 1) {
       switch (wpb) {
         case 8: return (const void*)k_trsv_lp_ob<W, CP, TS, 8>;
         case 16: return (const void*)k_trsv_lp_ob<W, CP, TS, 16>;
@@ -1470,29 +1788,41 @@ struct Launch {
       }
     }
   }
-  // the substitution kernel of a factor precision, schedule and block size
-  static const void* trsv_fn(int prec, int sched, int wpb) {
-    const bool ob = sched == 1;
-    if (prec == MPK_ILU_FP64) return ob ? mp_fn_t<false, true>(wpb) : mp_fn_t<false, false>(wpb);
-    if (prec == MPK_ILU_MP) return ob ? mp_fn_t<true, true>(wpb) : mp_fn_t<true, false>(wpb);
-    if (prec == MPK_ILU_BF16) return ob ? lp_fn_t<uint16_t, true>(wpb) : lp_fn_t<uint16_t, false>(wpb);
-    return ob ? lp_fn_t<float, true>(wpb) : lp_fn_t<float, false>(wpb);
+  template <int S>
+  static const void* trsv_fn_s(int prec, int wpb) {
+    if (prec == MPK_ILU_FP64) return mp_fn_t<false, S>(wpb);
+    if (prec == MPK_ILU_MP) return mp_fn_t<true, S>(wpb);
+    if (prec == MPK_ILU_BF16) return lp_fn_t<uint16_t, S>(wpb);
+    return lp_fn_t<float, S>(wpb);
   }
-  // the owner-block ring may exceed the default 48 KB of dynamic shared memory: opt in, once per
-  // kernel (the first call comes from the tuner, outside any graph capture)
+  // the substitution kernel of a factor precision, schedule and block size (cluster schedules:
+  // 4 or 8 warps; launch_wpb gives the block size to launch with)
+  static int launch_wpb(int sched, int wpb) { return sched >= 2 ? (wpb == 8 ? 8 : 4) : wpb; }
+  static const void* trsv_fn(int prec, int sched, int wpb) {
+    switch (sched) {
+      case 1: return trsv_fn_s<1>(prec, wpb);
+      case 2: return trsv_fn_s<2>(prec, wpb);
+      case 3: return trsv_fn_s<3>(prec, wpb);
+      default: return trsv_fn_s<0>(prec, wpb);
+    }
+  }
+  // dynamic shared memory of a schedule's kernel; above the default 48 KB the kernel opts in,
+  // once (the first call comes from the tuner, outside any graph capture)
   static size_t prepare_fn(const void* fn, int prec, int sched) {
-    if (sched != 1) return 0;
-    const size_t rb = ring_bytes(prec);
-    if (rb > 48 * 1024) {
+    if (sched == 0) return 0;
+    size_t rb = ring_bytes(prec);
+    if (sched >= 2 && rb < (size_t)kClusterSmem) rb = kClusterSmem;  // one CTA per SM
+    if (rb > 48 * 1024 || sched == 3) {
       static std::mutex mu;
-      static const void* seen[64];
+      static const void* seen[128];
       static int nseen = 0;
       std::lock_guard<std::mutex> lk(mu);
       bool found = false;
       for (int k = 0; k < nseen; ++k) found = found || seen[k] == fn;
       if (!found) {
-        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rb);
-        if (nseen < 64) seen[nseen++] = fn;
+        if (rb > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rb);
+        if (sched == 3) cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (nseen < 128) seen[nseen++] = fn;
       }
     }
     return rb;
@@ -1502,8 +1832,10 @@ struct Launch {
     // out starts as sentinels: completion is read from the values
     count_launch();
     k_fill_sent<<<grid_for(M.n), kBlock, 0, s>>>((int64_t)M.n * CP * W, out, 0, nullptr, done);
-    const void* fn = trsv_fn(M.prec, M.sched, M.wpb);
-    return coop(fn, M.wpb, prepare_fn(fn, M.prec, M.sched), M, lower, unit, in, out, done, s);
+    const int wpb = launch_wpb(M.sched, M.wpb);
+    const void* fn = trsv_fn(M.prec, M.sched, wpb);
+    return coop(fn, wpb, prepare_fn(fn, M.prec, M.sched), M.sched, M.sl_lo.nblocks, M, lower, unit, in, out, done,
+                s);
   }
   static int trsv32(const IluHandleView& M, bool lower, bool unit, const double* in, double* out, const int* done,
                     cudaStream_t s) {
@@ -1511,19 +1843,42 @@ struct Launch {
     count_launch();
     float* mine = lower ? M.v32 : reinterpret_cast<float*>(M.pk);
     k_fill_sent32<<<grid_for(M.n), kBlock, 0, s>>>((int64_t)M.n * CP, mine, done);
-    const void* fn = trsv_fn(M.prec, M.sched, M.wpb);
-    return coop(fn, M.wpb, prepare_fn(fn, M.prec, M.sched), M, lower, unit, in, out, done, s);
+    const int wpb = launch_wpb(M.sched, M.wpb);
+    const void* fn = trsv_fn(M.prec, M.sched, wpb);
+    return coop(fn, wpb, prepare_fn(fn, M.prec, M.sched), M.sched, M.sl_lo.nblocks, M, lower, unit, in, out, done,
+                s);
   }
-  // 1 if one block of wpb warps (and, owner-block schedule, its ring) fits one SM
-  static int trsv_fits(int prec, int wpb, int sched) {
+  // 1 if the kernel of (prec, wpb, sched) can run all its blocks co-resident: one block per SM,
+  // or (cluster schedules) nblocks clusters
+  static int trsv_fits(int prec, int wpb, int sched, int nblocks) {
+    wpb = launch_wpb(sched, wpb);
     const void* fn = trsv_fn(prec, sched, wpb);
     const size_t smem = prepare_fn(fn, prec, sched);
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, wpb * 32, smem) != cudaSuccess) {
+    if (sched < 2) {
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, wpb * 32, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+      }
+      return per_sm >= 1 ? 1 : 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = sched_csize(sched);
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(sched_csize(sched));
+    cfg.blockDim = dim3(wpb * 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int active = 0;
+    if (cudaOccupancyMaxActiveClusters(&active, fn, &cfg) != cudaSuccess) {
       cudaGetLastError();
       return 0;
     }
-    return per_sm >= 1 ? 1 : 0;
+    return (nblocks >= 1 && active >= nblocks) ? 1 : 0;
   }
   static Ops table() {
     Ops o;

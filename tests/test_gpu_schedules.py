@@ -1,7 +1,8 @@
-"""Both substitution schedules on the GPU against the oracle: the static chunk schedule and the
-owner-block schedule (contiguous row blocks per SM, block barriers between levels, shared-memory
-values for dependencies inside a block) must give the same bits as the oracle for every factor
-precision, both orientations (M and M^H), real and complex, whole solves and batches.  The
+"""Every substitution schedule on the GPU against the oracle: the static chunk schedule, the
+owner-block schedule per SM (contiguous row blocks, block barriers between levels, shared-memory
+values for dependencies inside a block) and per cluster of 8 or 16 SMs (distributed shared memory
+between the CTAs of a cluster, cluster barriers) must give the same bits as the oracle for every
+factor precision, both orientations (M and M^H), real and complex, whole solves and batches.  The
 schedule is forced through MPK_SUBST_SCHEDULE, which the library reads at each call."""
 import numpy as np
 import pytest
@@ -30,7 +31,7 @@ def host(t):
     return t.cpu().numpy()
 
 
-@pytest.fixture(params=["static", "owner"])
+@pytest.fixture(params=["static", "owner", "cluster8", "cluster16"])
 def schedule(request, monkeypatch):
     monkeypatch.setenv("MPK_SUBST_SCHEDULE", request.param)
     return request.param
