@@ -291,6 +291,25 @@ def run_mpk(args):
             torch.cuda.synchronize()
             variants[prec] = {"s": v0.elapsed_time(v1) / reps / 1e3, "iters": o["iters"], "status": o["status"],
                               "relres_true": o["relres_true"], "substitution_schedule": list(o["schedule"])}
+        # QD (w = 4) BiCGSTAB to 1e-55 with the binary64 factor, one timed solve after one untimed
+        b4 = _lib.spmv_mp(A, torch.as_tensor(inputs.ones(n, 4), device="cuda"), 4)
+
+        def solve_qd():
+            M = _lib.ILU0(A, "fp64")
+            o = _lib.krylov_solve("bicgstab", 4, A, M, b4, tol_rel=1e-55, maxit=2000, check_every=10, history=False)
+            M.close()
+            return o
+
+        solve_qd()
+        torch.cuda.synchronize()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record()
+        o = solve_qd()
+        q1.record()
+        torch.cuda.synchronize()
+        variants["qd_fp64"] = {"s": q0.elapsed_time(q1) / 1e3, "iters": o["iters"], "status": o["status"],
+                               "relres_true": o["relres_true"], "tol_rel": 1e-55, "vectors": "QD (w=4)"}
+        del b4
 
     # ---- kernel rooflines (CUDA events on the launching stream) -------------------------------
     def time_launches(fn, reps=20, warm=5):
