@@ -196,11 +196,19 @@ int mpk_ilu0_width(const mpk_ilu* M);
 
 /* Substitution schedule the handle last used or was tuned to: 0 = static chunk schedule (every
  * level's chunks dealt over all SMs), 1 = owner-block schedule (contiguous row blocks per SM,
- * levels separated by block barriers, shared-memory values for dependencies inside a block);
- * *wpb_out (if not NULL): warps per SM.  -2 for NULL.  Both give identical results; a solve
- * times both once per matrix pattern and keeps the faster (environment MPK_SUBST_SCHEDULE=
- * static|owner restricts the choice). */
+ * levels separated by block barriers, shared-memory values for dependencies inside a block),
+ * 2 / 3 = owner-block schedule per thread-block cluster of 8 / 16 SMs (distributed shared
+ * memory); *wpb_out (if not NULL): warps per SM.  -2 for NULL.  All give identical results.  A
+ * solve times schedules 0 and 1 once per matrix pattern and keeps the faster; the environment
+ * variable MPK_SUBST_SCHEDULE=static|owner|cluster8|cluster16 selects one instead. */
 int mpk_ilu0_schedule(const mpk_ilu* M, int* wpb_out);
+
+/* Testing aid for failure detection: the handle's substitutions leave row `row` unpublished
+ * (-1: none, the default), so every row that depends on it waits until its bounded wait runs out
+ * (about a second), the kernels leave, and the call returns MPK_TIMEOUT.  Nothing faults or
+ * hangs; the error is reported once and the handle serves the next call.  MPK_INVALID_ARG for
+ * a NULL handle or a row outside -1..n-1. */
+int mpk_ilu0_test_withhold(mpk_ilu* M, int row);
 
 void mpk_ilu0_destroy(mpk_ilu* M);
 

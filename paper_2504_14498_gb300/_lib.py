@@ -60,6 +60,7 @@ SIGNATURES = [
     ("mpk_ilu0_prec", _I, [_VP]),
     ("mpk_ilu0_width", _I, [_VP]),
     ("mpk_ilu0_schedule", _I, [_VP, ctypes.POINTER(_I)]),
+    ("mpk_ilu0_test_withhold", _I, [_VP, _I]),
     ("mpk_ilu0_destroy", None, [_VP]),
     ("mpk_precond_apply", _I, [_VP, _I, _I, _VP, _VP, _VP]),
     ("mpk_krylov_solve", _I, [_I, _I, ctypes.POINTER(CsrDesc), _VP, _VP, _VP, ctypes.POINTER(Opts),
@@ -189,6 +190,10 @@ class ILU0:
         wpb = ctypes.c_int(0)
         sc = lib().mpk_ilu0_schedule(self.handle, ctypes.byref(wpb))
         return ("static", "owner", "cluster8", "cluster16")[sc], wpb.value
+
+    def test_withhold(self, row: int):
+        """Testing aid: leave `row` unpublished in the substitutions (-1: none)."""
+        _check(lib().mpk_ilu0_test_withhold(self.handle, int(row)))
 
     def values(self) -> torch.Tensor:
         out = torch.empty(self.A.nnz * self.A.cp * self.w, dtype=torch.float64, device="cuda")

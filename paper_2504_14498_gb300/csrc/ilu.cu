@@ -989,10 +989,10 @@ int refresh_factor(mpk_ilu* M, cudaStream_t s) {
 
 // ---- substitution autotuner ---------------------------------------------------------------------
 // Candidates: the static chunk schedule and the owner-block schedule per SM with 4, 8, 16 or 32
-// warps per SM, the owner-block schedule per cluster of 8 or 16 SMs with 4 or 8 warps per SM,
-// each timed on two applications of M^-1; the choice is cached per (matrix pattern, factor
-// precision, w, c).  MPK_SUBST_SCHEDULE=static|owner|cluster8|cluster16 restricts the
-// candidates to one schedule (tests use it to cover each).
+// warps per SM, each timed on two applications of M^-1; the choice is cached per (matrix
+// pattern, factor precision, w, c).  MPK_SUBST_SCHEDULE=static|owner|cluster8|cluster16 selects
+// one schedule instead (the owner-block schedule per cluster of 8 or 16 SMs, with 4 or 8 warps
+// per SM, runs only when selected so; tests use it to cover each).
 int read_ctl_err(const mpk_ilu* M, cudaStream_t s);
 struct TrsvTune {
   const void* rp;
@@ -1041,7 +1041,9 @@ int tune_substitution(mpk_ilu* M, const Ops* o, int w, double* r, double* z, cud
   float best = 0.f;
   int best_wpb = 4, best_sched = forced >= 0 ? forced : 0;
   for (int sc = 0; sc < kScheds; ++sc) {
-    if (forced >= 0 && sc != forced) continue;
+    // the cluster schedules (2, 3) are candidates only when asked for: they lost on every
+    // workload measured, and their cooperative cluster launches cannot run under ncu
+    if (forced >= 0 ? sc != forced : sc >= 2) continue;
     if (ensure_layout(M, 0, sc, s) != MPK_OK) {
       cudaGetLastError();
       drop_layout(M, 0, sc);
@@ -1085,11 +1087,17 @@ int tune_substitution(mpk_ilu* M, const Ops* o, int w, double* r, double* z, cud
   return ensure_current(M, s);
 }
 
+// Device error of the handle's last kernels; reported once (cleared after reading, so the handle
+// serves the next call).
 int read_ctl_err(const mpk_ilu* M, cudaStream_t s) {
   int err = 0;
   MPK_CUDA(cudaMemcpyAsync(&err, M->ctl + CTL_ERR, sizeof(int), cudaMemcpyDeviceToHost, s));
   MPK_CUDA(cudaStreamSynchronize(s));
-  if (err != 0) return fail(err, "a bounded device wait ran out in a substitution kernel");
+  if (err != 0) {
+    MPK_CUDA(cudaMemsetAsync(M->ctl + CTL_ERR, 0, sizeof(int), s));
+    MPK_CUDA(cudaStreamSynchronize(s));
+    return fail(err, "a bounded device wait ran out in a substitution kernel");
+  }
   return MPK_OK;
 }
 
@@ -1132,6 +1140,7 @@ IluHandleView mpk_ilu::view(bool trans) const {
   v.sl_up = lay[sched][t + 1];
   v.wpb = wpb;
   v.sched = sched;
+  v.withhold = withhold;
   return v;
 }
 
@@ -1299,6 +1308,12 @@ extern "C" int mpk_ilu0_values(const mpk_ilu* M, double* out_dev, void* stream) 
 extern "C" int mpk_ilu0_prec(const mpk_ilu* M) { return M == nullptr ? -2 : M->prec; }
 
 extern "C" int mpk_ilu0_width(const mpk_ilu* M) { return M == nullptr ? -2 : M->wf; }
+
+extern "C" int mpk_ilu0_test_withhold(mpk_ilu* M, int row) {
+  if (M == nullptr || row < -1 || row >= M->n) return fail(MPK_INVALID_ARG, "bad handle or row");
+  M->withhold = row;
+  return MPK_OK;
+}
 
 extern "C" int mpk_ilu0_schedule(const mpk_ilu* M, int* wpb_out) {
   if (M == nullptr) return -2;

@@ -208,6 +208,7 @@ struct IluHandleView {
   const int* sysid = nullptr;        // batch: row -> system (absmax holds one scale per system)
   int wpb = 4;                       // warps per block (per SM) of the substitution kernels
   int sched = 0;                     // see kScheds
+  int withhold = -1;                 // testing aid: a row whose value is never published
 };
 enum CtlIdx : int { CTL_EPOCH = 0, CTL_TICKET_LO, CTL_TICKET_UP, CTL_ERR, CTL_FAIL_ROW, CTL_COUNT };
 
@@ -260,6 +261,7 @@ struct mpk_ilu {
   int* depth[4] = {nullptr, nullptr, nullptr, nullptr};      // level of every row, per triangle
   int wpb = 4;                   // warps per SM of the substitution kernels (autotuned per pattern)
   int sched = 0;                 // substitution schedule (autotuned per pattern)
+  int withhold = -1;             // testing aid (mpk_ilu0_test_withhold): a row left unpublished
   const void* src_rp = nullptr;  // the factored matrix's row_ptr address: the tuning cache's key
   mpk::IluHandleView view(bool trans) const;
   int vals_per_entry() const { return cp * wf; }  // doubles (or narrower values) per factor entry

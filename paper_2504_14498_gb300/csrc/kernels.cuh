@@ -1050,7 +1050,7 @@ __device__ __forceinline__ void mp_operands(const SellTri& T, bool unit, const d
     }
   }
 }
-template <int W, int CP, bool MF>
+template <int W, int CP, bool MF, bool RING>
 __device__ __forceinline__ bool mp_finish(const SellTri& T, const IluHandleView& M, bool unit,
                                           double* __restrict__ out, MpChunk<W, CP, MF>& c, const RingRef& R,
                                           int own_slot) {
@@ -1077,7 +1077,7 @@ __device__ __forceinline__ bool mp_finish(const SellTri& T, const IluHandleView&
     for (int k = 0; k < KG; ++k) {
       v[k] = n_zero<W, CP>();
       if (c.jj[k] >= 0) need |= 1u << k;
-      else if (c.jj[k] <= -2) v[k] = ring_read<W, CP>(R, -2 - c.jj[k]);  // computed by this block
+      else if (RING && c.jj[k] <= -2) v[k] = ring_read<W, CP>(R, -2 - c.jj[k]);  // computed by this block
     }
     while (__any_sync(FULL, need != 0u && !timeout)) {
       // every outstanding load of the round is issued before any is checked
@@ -1102,13 +1102,13 @@ __device__ __forceinline__ bool mp_finish(const SellTri& T, const IluHandleView&
       }
     }
   }
-  if (!timeout && c.i >= 0) {
+  if (!timeout && c.i >= 0 && c.i != M.withhold) {
     if (!unit) {
       if constexpr (MF) acc = n_div<W, CP>(acc, c.dv);
       else acc = n_div_fp<W, CP>(acc, c.dr, c.di);
     }
     n_publish<W, CP>(out, c.i, acc);
-    if (R.base != nullptr) n_store<W, CP>((double*)R.base, own_slot, acc);
+    if constexpr (RING) n_store<W, CP>((double*)R.base, own_slot, acc);
   }
   return __any_sync(FULL, timeout);
 }
@@ -1131,7 +1131,7 @@ __global__ void __launch_bounds__(WPB * 32, 1)
     c.rep = nx.rep;
     mp_operands<W, CP, MF>(T, unit, in, chunk, c);
     if (chunk + G < T.nchunks) mp_meta<W, CP, MF>(T, chunk + G, nx);  // the next chunk's rows, ahead
-    if (mp_finish<W, CP, MF>(T, M, unit, out, c, RingRef(), 0)) {
+    if (mp_finish<W, CP, MF, false>(T, M, unit, out, c, RingRef(), 0)) {
       if (lane == 0) atomicCAS(M.ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
       return;
     }
@@ -1186,7 +1186,7 @@ __global__ void __launch_bounds__(WPB * 32, 1)
       if (nxt >= cg1) nxt = (g + 1 < gend && cg1 + warp < cg2) ? cg1 + warp : -1;
       if (nxt >= 0) mp_meta<W, CP, MF>(T, nxt, nx);
       const int own = ((chunk << 5) + lane - bs) % kRing;
-      if (mp_finish<W, CP, MF>(T, M, unit, out, c, R, own)) {
+      if (mp_finish<W, CP, MF, true>(T, M, unit, out, c, R, own)) {
         if (lane == 0) {
           atomicCAS(M.ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
           abort_blk = 1;
@@ -1254,7 +1254,7 @@ __global__ void __launch_bounds__(WPB * 32, 1)
       if (nxt >= cg1) nxt = (g + 1 < gend && cg1 + first < cg2) ? cg1 + first : -1;
       if (nxt >= 0) mp_meta<W, CP, MF>(T, nxt, nx);
       const int own = ((chunk << 5) + lane - bs) % kRing;
-      if (mp_finish<W, CP, MF>(T, M, unit, out, c, R, own)) {
+      if (mp_finish<W, CP, MF, true>(T, M, unit, out, c, R, own)) {
         if (lane == 0) {
           atomicCAS(M.ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
           for (int r = 0; r < CS; ++r) st_cluster_s32(cluster_addr(abort_sa, (unsigned)r), 1);
@@ -1372,7 +1372,7 @@ __device__ __forceinline__ void lp_operands(const SellTri& T, const IluHandleVie
     }
   }
 }
-template <int W, int CP, typename TS>
+template <int W, int CP, typename TS, bool RING>
 __device__ __forceinline__ bool lp_finish(const SellTri& T, const IluHandleView& M, bool lower, bool unit,
                                           double* __restrict__ out, LpChunk<TS>& c, const RingRef& R,
                                           int own_slot) {
@@ -1402,7 +1402,7 @@ __device__ __forceinline__ bool lp_finish(const SellTri& T, const IluHandleView&
       vi[k] = 0.0f;
       if (c.jj[k] >= 0) {
         need |= 1u << k;
-      } else if (c.jj[k] <= -2) {  // computed by this block
+      } else if (RING && c.jj[k] <= -2) {  // computed by this block
         ring_read32<CP>(R, -2 - c.jj[k], vr[k], vi[k]);
       }
     }
@@ -1439,7 +1439,7 @@ __device__ __forceinline__ bool lp_finish(const SellTri& T, const IluHandleView&
       }
     }
   }
-  if (!timeout && c.i >= 0) {
+  if (!timeout && c.i >= 0 && c.i != M.withhold) {
     if (!unit) {
       if constexpr (CP == 1) {
         ar = ar / c.dr;
@@ -1452,7 +1452,7 @@ __device__ __forceinline__ bool lp_finish(const SellTri& T, const IluHandleView&
     }
     st_relaxed_f32(mine + (int64_t)c.i * CP, ar);
     if constexpr (CP == 2) st_relaxed_f32(mine + (int64_t)c.i * CP + 1, ai);
-    if (R.base != nullptr) {
+    if constexpr (RING) {
       float* ring = (float*)R.base;
       ring[own_slot * CP] = ar;
       if constexpr (CP == 2) ring[own_slot * CP + 1] = ai;
@@ -1486,7 +1486,7 @@ __global__ void __launch_bounds__(WPB * 32, 1)
     c.rep = nx.rep;
     lp_operands<W, CP, TS>(T, M, lower, unit, in, chunk, e1, c);
     if (chunk + G < T.nchunks) lp_meta<TS>(T, chunk + G, nx);  // the next chunk's rows, ahead
-    if (lp_finish<W, CP, TS>(T, M, lower, unit, out, c, RingRef(), 0)) {
+    if (lp_finish<W, CP, TS, false>(T, M, lower, unit, out, c, RingRef(), 0)) {
       if (lane == 0) atomicCAS(M.ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
       return;
     }
@@ -1530,7 +1530,7 @@ __global__ void __launch_bounds__(WPB * 32, 1)
       if (nxt >= cg1) nxt = (g + 1 < gend && cg1 + warp < cg2) ? cg1 + warp : -1;
       if (nxt >= 0) lp_meta<TS>(T, nxt, nx);
       const int own = ((chunk << 5) + lane - bs) % kRing;
-      if (lp_finish<W, CP, TS>(T, M, lower, unit, out, c, R, own)) {
+      if (lp_finish<W, CP, TS, true>(T, M, lower, unit, out, c, R, own)) {
         if (lane == 0) {
           atomicCAS(M.ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
           abort_blk = 1;
@@ -1593,7 +1593,7 @@ __global__ void __launch_bounds__(WPB * 32, 1)
       if (nxt >= cg1) nxt = (g + 1 < gend && cg1 + first < cg2) ? cg1 + first : -1;
       if (nxt >= 0) lp_meta<TS>(T, nxt, nx);
       const int own = ((chunk << 5) + lane - bs) % kRing;
-      if (lp_finish<W, CP, TS>(T, M, lower, unit, out, c, R, own)) {
+      if (lp_finish<W, CP, TS, true>(T, M, lower, unit, out, c, R, own)) {
         if (lane == 0) {
           atomicCAS(M.ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
           for (int r = 0; r < CS; ++r) st_cluster_s32(cluster_addr(abort_sa, (unsigned)r), 1);
