@@ -70,7 +70,10 @@ __device__ __forceinline__ double fm(double a, double b, double c) { return fma(
 
 template <typename T, int CP>
 struct RowIlu {
-  using Val = Empty;  // rows of earlier levels are read from memory (ordered by the level chain)
+  // row k's diagonal position and end, fetched ahead of consume (row k is finished)
+  struct Val {
+    int dk, ek;
+  };
   const int* rp;
   const int* ci;
   const int* diag;
@@ -82,9 +85,9 @@ struct RowIlu {
     p = rp[i_];
     pend = diag[i_];
   }
-  __device__ Val load(int) { return Val{}; }
-  __device__ void consume(int p, int k, const Val&) {
-    const int dk = diag[k], ek = rp[k + 1], ei = rp[i + 1];
+  __device__ Val load(int k) { return Val{diag[k], rp[k + 1]}; }
+  __device__ void consume(int p, int k, const Val& vk) {
+    const int dk = vk.dk, ek = vk.ek, ei = rp[i + 1];
     T lr, li = T(0);
     if constexpr (CP == 1) {
       lr = a[p] / a[dk];

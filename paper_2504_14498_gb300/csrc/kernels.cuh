@@ -782,15 +782,33 @@ __device__ __forceinline__ void chunk_rows(const LevelOrder lo, const int* __res
     const int i = lo.perm[(chunk << 5) + lane];
     int p = 0, pend = 0;
     if (i >= 0) row.begin(i, p, pend);
-    // wait for the chunks this row depends on
+    // wait for the chunks this row depends on, kDepBatch dependencies at a time: their columns,
+    // positions and flags are each loaded together (one memory round trip per step, not per
+    // dependency)
+    constexpr int kDepBatch = 4;
     bool timeout = false;
     {
       const long long t0 = clock64();
       unsigned backoff = 0u;
       int rounds = 0;
-      for (int q = p; q < pend && !timeout; ++q) {
-        const int c = lo.pos[ci[q]] >> 5;
-        while (ld_relaxed(lo.flags + c) != epoch) {
+      for (int q0 = p; q0 < pend && !timeout; q0 += kDepBatch) {
+        int cc[kDepBatch];
+#pragma unroll
+        for (int k = 0; k < kDepBatch; ++k) cc[k] = q0 + k < pend ? ci[q0 + k] : -1;
+#pragma unroll
+        for (int k = 0; k < kDepBatch; ++k) cc[k] = cc[k] >= 0 ? (lo.pos[cc[k]] >> 5) : -1;
+        unsigned need = 0u;
+#pragma unroll
+        for (int k = 0; k < kDepBatch; ++k)
+          if (cc[k] >= 0) need |= 1u << k;
+        while (need != 0u) {
+          int f[kDepBatch];
+#pragma unroll
+          for (int k = 0; k < kDepBatch; ++k) f[k] = ((need >> k) & 1u) ? ld_relaxed(lo.flags + cc[k]) : epoch;
+#pragma unroll
+          for (int k = 0; k < kDepBatch; ++k)
+            if (f[k] == epoch) need &= ~(1u << k);
+          if (need == 0u) break;
           if (clock64() - t0 > kWaitCycles) { timeout = true; break; }
           if ((++rounds & 31) == 0 && ld_relaxed(ctl + CTL_ERR) != 0) { timeout = true; break; }
           backoff = backoff == 0u ? 32u : (backoff < 512u ? 2u * backoff : 512u);
@@ -804,9 +822,19 @@ __device__ __forceinline__ void chunk_rows(const LevelOrder lo, const int* __res
     }
     fence_acq_rel();
     if (i >= 0) {
-      for (int q = p; q < pend; ++q) {
-        const int j = ci[q];
-        row.consume(q, j, row.load(j));
+      // the rows' finished data (Row::load) is fetched for a batch of dependencies before the
+      // batch is consumed in order
+      for (int q0 = p; q0 < pend; q0 += kDepBatch) {
+        int jj[kDepBatch];
+        typename Row::Val v[kDepBatch];
+#pragma unroll
+        for (int k = 0; k < kDepBatch; ++k) jj[k] = q0 + k < pend ? ci[q0 + k] : -1;
+#pragma unroll
+        for (int k = 0; k < kDepBatch; ++k)
+          if (jj[k] >= 0) v[k] = row.load(jj[k]);
+#pragma unroll
+        for (int k = 0; k < kDepBatch; ++k)
+          if (jj[k] >= 0) row.consume(q0 + k, jj[k], v[k]);
       }
       row.store(row.finish());
     }
