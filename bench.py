@@ -43,7 +43,7 @@ FP64_PEAK_OPS = 152 * 4 * 0.5 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one k_trsv_mp launch pair (both triangles, static schedule) on the
 # 128^3 workload: dram__bytes_read.sum + dram__bytes_write.sum from an ncu capture of the current
 # kernel (its summary is under profiles/); None once the kernel changes.
-TRSV_MP_TRAFFIC = 151218176 + 18590976 + 168678912 + 16925184
+TRSV_MP_TRAFFIC = 151249152 + 18557952 + 168018688 + 17200128
 
 
 def parse():
