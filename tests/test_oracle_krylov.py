@@ -160,3 +160,31 @@ def test_ilu_needed_paper_setting():
         non = oracle.krylov(m, A, b, w, ilu="none", tol_rel=1e-13, tol_abs=1e-100, maxit=3 * n)
         assert pre["status"] == "OK"
         assert 3 * pre["iters"] < non["iters"], (m, pre["iters"], non["iters"])
+
+
+@pytest.mark.parametrize("method", ["cgs", "bicgstab", "gpbicg"])
+def test_hat_form_equals_definitional_form(method):
+    """The right-preconditioned forms run on A with M^-1 applied inside (the "hat" vectors) equal
+    the unpreconditioned method on the explicit operator A~ = A M^-1 (dense, each entry rounded to
+    binary64 once), residual norm for residual norm: r = b - A x = b - A~ y with x = M^-1 y.  A
+    mis-stated recurrence in any of these forms separates the two histories immediately.  (BiCG
+    of Algorithm 3 is the two-sided form, M z = r and M^H z~ = r~: it equals BiCG on A~ started
+    from the shadow M^-H r0 instead of r0, so it is pinned by the M = A and CG reductions.)"""
+    n, w = 8, 4
+    A = inputs.random_sparse(n, 3, 5, seed=61, weak_frac=0.0)
+    _, rp, ci, val = A
+    st, fac, _ = oracle.ilu0(A, "fp64")
+    assert st == 0
+    F = np.zeros((n, n))
+    F[np.repeat(np.arange(n), np.diff(rp)), ci] = fac
+    Mm = (np.tril(F, -1) + np.eye(n)) @ np.triu(F)
+    D = np.zeros((n, n))
+    D[np.repeat(np.arange(n), np.diff(rp)), ci] = val
+    At = D @ np.linalg.inv(Mm)
+    At_csr = (n, np.arange(0, n * n + 1, n, dtype=np.int32), np.tile(np.arange(n, dtype=np.int32), n), At.reshape(-1))
+    b = inputs.random_vector(n, w, 1, seed=8)
+    hat = oracle.krylov(method, A, b, w, ilu="fp64", tol_rel=1e-40, maxit=n)
+    defn = oracle.krylov(method, At_csr, b, w, ilu="none", tol_rel=1e-40, maxit=n)
+    k = min(len(hat["hist"]), len(defn["hist"]), 5)
+    assert k >= 4
+    np.testing.assert_allclose(hat["hist"][:k], defn["hist"][:k], rtol=1e-9)
