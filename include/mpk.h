@@ -223,9 +223,9 @@ int mpk_precond_apply(const mpk_ilu* M, int w, int trans, const double* r_dev, d
 int mpk_krylov_solve(int method, int w, const mpk_csr* A, const mpk_ilu* M, const double* b_dev, double* x_dev,
                      const mpk_opts* opts, mpk_info* info, void* stream);
 
-/* Batched solve of nsys independent systems (the benchmark spec's batching pattern; the paper
- * solves one system at a time).  A is block-diagonal: system s owns rows and columns
- * sys_rows[s] .. sys_rows[s+1]-1, and every stored column of a row lies in its system's block
+/* Batched solve of nsys independent systems (the paper solves one system at a time).  A is
+ * block-diagonal: system s owns rows and columns sys_rows[s] .. sys_rows[s+1]-1, and every
+ * stored column of a row lies in its system's block
  * (checked; MPK_INVALID_ARG otherwise, nothing solved).  All systems advance together, each step
  * of every system in the same kernel launches; each system follows exactly the operation
  * sequence mpk_krylov_solve would perform on it alone (identical results), with its own scalars,
@@ -243,7 +243,7 @@ int mpk_krylov_solve_batched(int method, int w, const mpk_csr* A, int nsys, cons
                              const int32_t* sys_rows_dev, const mpk_ilu* M, const double* b_dev, double* x_dev,
                              const mpk_opts* opts, mpk_info* infos, void* stream);
 
-/* ---- Learned correction of the ILU(0) factor (the benchmark spec's learned-preconditioner pattern;
+/* ---- Learned correction of the ILU(0) factor (a learned preconditioner;
  * the paper has no counterpart) -----------------------------------------------------------------
  * A graph network on A's pattern (3 message-passing layers, hidden width 32, binary32 weights,
  * bfloat16-stored activations; the exact network is documented in csrc/gnn.cu) predicts one value

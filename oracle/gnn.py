@@ -2,7 +2,7 @@
 use it).  Plain numpy in binary64: the graph network's forward pass, the training loss
 ||(L'U' - A) W||^2 / ||A W||^2 per system, and the gradients by hand-written reverse mode.
 
-The paper has no learned preconditioner; this restates the network that the benchmark spec asks for
+The paper has no learned preconditioner; this restates the learned correction of the library
 (3 message-passing layers, hidden width 32, binary32 weights, bfloat16 activations) exactly as the
 library defines it:
   node input  x_i = (1, sum_{j!=i} |a_ij| / a_ii, sum_j a_ij / a_ii, f_ii / a_ii)

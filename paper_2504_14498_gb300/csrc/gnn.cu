@@ -1,7 +1,7 @@
-// gnn.cu -- learned correction of the ILU(0) factor (the benchmark spec's learned-preconditioner
-// pattern; the paper has no counterpart): a graph network on A's pattern predicts, per stored
-// entry, o_ij, and the corrected factor is f'_ij = f_ij (1 + 0.5 tanh o_ij).  o = 0 gives the
-// plain ILU(0) factor exactly, which stays the fallback.
+// gnn.cu -- learned correction of the ILU(0) factor (the paper has no counterpart): a graph
+// network on A's pattern predicts, per stored entry, o_ij, and the corrected factor is
+// f'_ij = f_ij (1 + 0.5 tanh o_ij).  o = 0 gives the plain ILU(0) factor exactly, which stays
+// the fallback.
 //
 // Network (hidden width H = 32, binary32 weights, activations stored as bfloat16 and computed in
 // binary32):

@@ -3,7 +3,7 @@
 Argument marshalling and the training loop's control flow only: the network's forward and
 backward passes, the loss and its gradient, the optimiser step and the correction of the factor
 all run in libmpk's CUDA kernels (csrc/gnn.cu).  The network and loss are documented there.
-Plain ILU(0) is the fallback (an untrained network returns the plain factor) and the judge: see
+Plain ILU(0) is the fallback (an untrained network returns the plain factor) and the arbiter: see
 `solve_with_fallback`.
 """
 import ctypes

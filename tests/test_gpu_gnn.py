@@ -146,7 +146,7 @@ def _batch_of(ms, seeds):
 def test_training_reduces_loss_and_iterations_are_judged():
     """Train on 48 seeded 32x32 instances (6 batches of 8, 25 epochs, loss of the preconditioned
     operator over half smooth, half random probes) and evaluate on 6 held-out 48x48 instances with
-    DD BiCGSTAB + binary64 ILU(0): the loss must fall, and the judged result (learned factor kept
+    DD BiCGSTAB + binary64 ILU(0): the loss must fall, and the arbitrated result (learned factor kept
     only when it needs no more iterations) never needs more than plain.  The training at the
     workload's scale is bench.py --workload learned."""
     net = learned.LearnedILU(seed=11)
