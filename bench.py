@@ -65,13 +65,16 @@ def parse():
     ap.add_argument("--only-on", default="convdiff3d", choices=["convdiff3d", "helmholtz2d", "batch512"],
                     help="the matrix of --only")
     ap.add_argument("--workload", default="convdiff3d",
-                    choices=["convdiff3d", "batch512", "learned", "plainrows", "tables"],
+                    choices=["convdiff3d", "batch512", "learned", "plainrows", "tables", "helmholtz"],
                     help="batch512: the batched workload (512 systems, binary32 ILU(0), DD BiCGSTAB); "
                          "learned: train the learned ILU(0) correction, evaluate on held-out instances; "
                          "plainrows: the paper's rows without \"_d\" against the \"_d\" rows (Table 4); "
-                         "tables: Tables 1-2 at the paper's scale on stand-in matrices")
+                         "tables: Tables 1-2 at the paper's scale on stand-in matrices; "
+                         "helmholtz: the complex 1024^2 workload solved to 1e-25")
     ap.add_argument("--m-complex", type=int, default=1024, help="plainrows: Helmholtz grid points per axis")
     ap.add_argument("--formats", default="DD", help="tables: comma-separated formats among DD,TD,QD")
+    ap.add_argument("--helm-maxit32", type=int, default=20000, help="helmholtz: iteration limit, binary32 factor")
+    ap.add_argument("--helm-maxit64", type=int, default=2000, help="helmholtz: iteration limit, binary64 factor")
     ap.add_argument("--complex-iters", type=int, default=20, help="plainrows: Helmholtz iterations per solve")
     ap.add_argument("--train-instances", type=int, default=20000)
     ap.add_argument("--eval-instances", type=int, default=200)
@@ -637,6 +640,46 @@ def run_plainrows(args):
     return 0
 
 
+def run_helmholtz(args):
+    """The complex workload: shifted-Laplacian Helmholtz h^2(-Lap - k^2 (1 - 0.5 i)) on a 1024^2
+    grid, k = 20 pi, b with N(0, 1) real and imaginary parts; complex DD BiCGSTAB to 1e-25 with the
+    complex binary32 factor (maxit --helm-maxit32) and with the complex binary64 factor (maxit
+    --helm-maxit64: at about 84 ms per iteration a complete run takes minutes).  Reports
+    iterations, seconds (factorisation + solve, CUDA events), ms per iteration and the true
+    relative residual of each."""
+    import torch
+
+    from paper_2504_14498_gb300 import _lib, inputs
+
+    torch.cuda.set_device(0)
+    A_t = inputs.helmholtz2d(1024, k=20 * np.pi)
+    n, w = A_t[0], 2
+    A = _lib.Matrix.from_tuple(A_t, is_complex=True)
+    b = torch.as_tensor(inputs.normal_rhs(n, w), device="cuda")
+    rows = {}
+    for prec, maxit in (("fp32", args.helm_maxit32), ("fp64", args.helm_maxit64)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        M = _lib.ILU0(A, prec)
+        out = _lib.krylov_solve("bicgstab", w, A, M, b, tol_rel=TOL, maxit=maxit, check_every=50, history=True)
+        e1.record()
+        torch.cuda.synchronize()
+        M.close()
+        t = e0.elapsed_time(e1) / 1e3
+        h = out["hist"]
+        rows[prec] = {"status": out["status"], "iters": out["iters"], "maxit": maxit, "s": t,
+                      "ms_per_iter": 1e3 * t / max(1, out["iters"]), "relres_true": out["relres_true"],
+                      "relres_rec_by_1000": [float(h[k] / h[0]) for k in range(0, len(h), 1000)]}
+        print("%s: %s %d it %.1f s" % (prec, out["status"], out["iters"], t), file=sys.stderr, flush=True)
+    line = {"metric": "complex DD BiCGSTAB + ILU(0) on 1024^2 shifted-Laplacian Helmholtz (k = 20 pi) to 1e-25",
+            "value": rows["fp32"]["s"], "unit": "s (binary32 factor)", "higher_is_better": False, "n_gpus": 1,
+            "data": "synthetic", "dtype": "f64",
+            "config": {"workload": "helmholtz2d 1024^2 (N=1048576, nnz=5238784), complex DD vectors, b ~ N(0,1)"},
+            "solves": rows}
+    print(json.dumps(line))
+    return 0
+
+
 def run_tables(args):
     """Tables 1 and 2 at the paper's scale on the GPU: the real stand-in (n = 765) and the complex
     stand-in (n = 961) solved by BiCG, CGS, BiCGSTAB and GPBiCG in the formats of --formats (DD by
@@ -815,6 +858,8 @@ def main():
         return run_plainrows(args)
     if args.workload == "tables" and args.impl == "mpk":
         return run_tables(args)
+    if args.workload == "helmholtz" and args.impl == "mpk":
+        return run_helmholtz(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_mpk(args)
