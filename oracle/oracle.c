@@ -878,6 +878,20 @@ static void vaxpy(const sys_t *S, double *y, const double *a, num alpha, const d
 }
 static int nan_mp(mp a) { return a.c[0] != a.c[0]; }
 
+/* Test hooks (set by orc_krylov_hooks around one call, NULL otherwise):
+ *   g_shadow: the initial shadow residual r~0 instead of r0 (n*c*w doubles);
+ *   g_trace:  per iteration k (1-based), two leading components of normalised inner products
+ *             that exact arithmetic makes zero: BiCGSTAB <t, r_k> / (|t| |r_k|) and 0;
+ *             GPBiCG <c, r_k> / (|c| |r_k|) and <y, r_k> / (|y| |r_k|) (y from the second step);
+ *             real parts for complex systems.  2 * (maxit + 1) doubles. */
+static const double *g_shadow = NULL;
+static double *g_trace = NULL;
+static double ortho(int n, ctx t, const double *a, const double *b) {
+  mp ab = dot(n, t, a, b).re, aa = nrm2(n, t, a), bb = nrm2(n, t, b);
+  double den = aa.c[0] * bb.c[0];
+  return den > 0.0 ? ab.c[0] / den : 0.0;
+}
+
 int orc_krylov(int method, int n, const int *rp, const int *ci, const double *val, int c, int w, int ilu,
                const double *fac, const double *b, double *x, double tol_rel, double tol_abs, int maxit, int flags,
                double *hist, int *iters_out, double *relres_true) {
@@ -892,7 +906,8 @@ int orc_krylov(int method, int n, const int *rp, const int *ci, const double *va
   r = vnew(&S); rt = vnew(&S); tmp = vnew(&S);
   spmv(n, rp, ci, val, t, x, tmp);
   vaxpy(&S, r, b, n_neg((num){mp_from_d(1.0), mp_zero()}), tmp); /* r = b - A x */
-  vcopy(&S, rt, r);
+  if (g_shadow) vcopy(&S, rt, g_shadow);
+  else vcopy(&S, rt, r);
   nr = nrm2(n, t, r);
   r0n = nr.c[0];
   if (hist) hist[0] = r0n;
@@ -987,6 +1002,7 @@ int orc_krylov(int method, int n, const int *rp, const int *ci, const double *va
       vaxpy(&S, x, x, alpha, ph);
       vaxpy(&S, x, x, omega, sh);
       vaxpy(&S, r, sv, n_neg(omega), tv);      /* r = s - omega t */
+      if (g_trace) g_trace[2 * it] = ortho(n, t, tv, r);
       nr = nrm2(n, t, r);
       if (hist) hist[it] = nr.c[0];
       if (nan_mp(nr)) { st = ORC_NAN; break; }
@@ -1058,6 +1074,10 @@ int orc_krylov(int method, int n, const int *rp, const int *ci, const double *va
       vaxpy(&S, x, x, one, zh);               /*    + z^ */
       vaxpy(&S, tmp, tv, n_neg(eta), y);      /* t - eta y */
       vaxpy(&S, r, tmp, n_neg(zeta), cv);     /* r = t - eta y - zeta c */
+      if (g_trace) {
+        g_trace[2 * it] = ortho(n, t, cv, r);
+        g_trace[2 * it + 1] = it > 1 ? ortho(n, t, y, r) : 0.0;
+      }
       nr = nrm2(n, t, r);
       if (hist) hist[it] = nr.c[0];
       if (nan_mp(nr)) { st = ORC_NAN; break; }
@@ -1085,5 +1105,20 @@ finish:
   }
   if (S.have_ah) csr_free(&S.ah);
   free(r); free(rt); free(tmp);
+  return st;
+}
+
+/* orc_krylov with the test hooks above (shadow and trace may be NULL). */
+int orc_krylov_hooks(int method, int n, const int *rp, const int *ci, const double *val, int c, int w, int ilu,
+                     const double *fac, const double *b, double *x, double tol_rel, double tol_abs, int maxit,
+                     int flags, double *hist, int *iters_out, double *relres_true, const double *shadow,
+                     double *trace) {
+  int st;
+  g_shadow = shadow;
+  g_trace = trace;
+  st = orc_krylov(method, n, rp, ci, val, c, w, ilu, fac, b, x, tol_rel, tol_abs, maxit, flags, hist, iters_out,
+                  relres_true);
+  g_shadow = NULL;
+  g_trace = NULL;
   return st;
 }

@@ -188,3 +188,45 @@ def test_hat_form_equals_definitional_form(method):
     k = min(len(hat["hist"]), len(defn["hist"]), 5)
     assert k >= 4
     np.testing.assert_allclose(hat["hist"][:k], defn["hist"][:k], rtol=1e-9)
+
+
+def test_bicg_two_sided_equals_bicg_on_explicit_operator():
+    """Algorithm 3 (M z = r, M^H z~ = r~) equals unpreconditioned BiCG on A~ = A M^-1 started from
+    the shadow M^-H r0, residual for residual (the derivation: z~ = M^-H r~ carries the shadow of
+    the explicit form)."""
+    n, w = 8, 4
+    A = inputs.random_sparse(n, 3, 5, seed=63, weak_frac=0.0)
+    _, rp, ci, val = A
+    st, fac, _ = oracle.ilu0(A, "fp64")
+    F = np.zeros((n, n))
+    F[np.repeat(np.arange(n), np.diff(rp)), ci] = fac
+    Mm = (np.tril(F, -1) + np.eye(n)) @ np.triu(F)
+    D = np.zeros((n, n))
+    D[np.repeat(np.arange(n), np.diff(rp)), ci] = val
+    At = D @ np.linalg.inv(Mm)
+    At_csr = (n, np.arange(0, n * n + 1, n, dtype=np.int32), np.tile(np.arange(n, dtype=np.int32), n), At.reshape(-1))
+    b = inputs.random_vector(n, w, 1, seed=9)
+    shadow = oracle.precond(A, fac, b, w, "fp64", 1, True)  # M^-H r0 (x0 = 0)
+    two_sided = oracle.krylov("bicg", A, b, w, ilu="fp64", tol_rel=1e-40, maxit=n)
+    explicit = oracle.krylov("bicg", At_csr, b, w, tol_rel=1e-40, maxit=n, shadow=shadow)
+    k = min(len(two_sided["hist"]), len(explicit["hist"]), 6)
+    assert k >= 4
+    np.testing.assert_allclose(two_sided["hist"][:k], explicit["hist"][:k], rtol=1e-9)
+    plain_shadow = oracle.krylov("bicg", At_csr, b, w, tol_rel=1e-40, maxit=n)
+    assert not np.allclose(two_sided["hist"][1:k], plain_shadow["hist"][1:k], rtol=1e-6)  # the shadow matters
+
+
+@pytest.mark.parametrize("c", [1, 2])
+def test_step_invariants(c):
+    """Exact-arithmetic invariants of every step, here in QD (rounding ~1e-60): BiCGSTAB's new
+    residual is orthogonal to t = A s^ (omega minimises ||s - omega t||), GPBiCG's to c = A t^ and
+    to y (the two-term minimisation)."""
+    n, w = 40, 4
+    A = inputs.random_sparse(n, 3, 8, seed=70 + c, complex_=(c == 2), weak_frac=0.0)
+    b = inputs.random_vector(n, w, c, seed=10)
+    st = oracle.krylov("bicgstab", A, b, w, c, ilu="fp64", tol_rel=1e-50, maxit=60, trace=True)
+    assert st["iters"] >= 5
+    assert np.max(np.abs(st["trace"][:, 0])) < 1e-50
+    gp = oracle.krylov("gpbicg", A, b, w, c, ilu="fp64", tol_rel=1e-50, maxit=60, trace=True)
+    assert gp["iters"] >= 5
+    assert np.max(np.abs(gp["trace"])) < 1e-50
