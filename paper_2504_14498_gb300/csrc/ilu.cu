@@ -70,36 +70,127 @@ __device__ __forceinline__ double fm(double a, double b, double c) { return fma(
 
 template <typename T, int CP>
 struct RowIlu {
-  // row k's diagonal position and end, fetched ahead of consume (row k is finished)
+  // Rows of up to RI entries are held in registers while they are factored, and a finished row
+  // k's pivot and first RK upper entries are fetched ahead of consume (Val), so that the
+  // eliminations need no memory round trip per entry; longer rows take the memory path, with
+  // the same operations in the same order.
+  static constexpr int RI = 8, RK = 4;
   struct Val {
     int dk, ek;
+    int uc[RK];       // columns of row k's upper entries dk+1 .. (-1 past its end)
+    T uv[RK * CP];    // their values
+    T piv[CP];        // U_kk
   };
   const int* rp;
   const int* ci;
   const int* diag;
   T* a;
   int* ctl;
-  int i;
+  int i, p0, len;
+  bool reg;          // row i is held in rc / rv
+  int rc[RI];
+  T rv[RI * CP];
   __device__ void begin(int i_, int& p, int& pend) {
     i = i_;
-    p = rp[i_];
+    p0 = rp[i_];
+    len = rp[i_ + 1] - p0;
+    reg = len <= RI;
+#pragma unroll
+    for (int t = 0; t < RI; ++t) {
+      rc[t] = -1;
+#pragma unroll
+      for (int h = 0; h < CP; ++h) rv[t * CP + h] = T(0);
+      if (reg && t < len) {
+        rc[t] = ci[p0 + t];
+#pragma unroll
+        for (int h = 0; h < CP; ++h) rv[t * CP + h] = a[(int64_t)(p0 + t) * CP + h];
+      }
+    }
+    p = p0;
     pend = diag[i_];
   }
-  __device__ Val load(int k) { return Val{diag[k], rp[k + 1]}; }
-  __device__ void consume(int p, int k, const Val& vk) {
-    const int dk = vk.dk, ek = vk.ek, ei = rp[i + 1];
-    T lr, li = T(0);
+  __device__ Val load(int k) {
+    Val v;
+    v.dk = diag[k];
+    v.ek = rp[k + 1];
+#pragma unroll
+    for (int h = 0; h < CP; ++h) v.piv[h] = a[(int64_t)v.dk * CP + h];
+#pragma unroll
+    for (int u = 0; u < RK; ++u) {
+      const int q = v.dk + 1 + u;
+      v.uc[u] = q < v.ek ? ci[q] : -1;
+#pragma unroll
+      for (int h = 0; h < CP; ++h) v.uv[u * CP + h] = q < v.ek ? a[(int64_t)q * CP + h] : T(0);
+    }
+    return v;
+  }
+  // l = x / y in the factor's type, complex steps as documented above
+  __device__ static void divide(const T* x, const T* y, T& lr, T& li) {
     if constexpr (CP == 1) {
-      lr = a[p] / a[dk];
-      a[p] = lr;
+      lr = x[0] / y[0];
+      li = T(0);
     } else {
-      const T xr = a[2 * (int64_t)p], xi = a[2 * (int64_t)p + 1];
-      const T yr = a[2 * (int64_t)dk], yi = a[2 * (int64_t)dk + 1];
-      const T den = fm(yr, yr, yi * yi), nr = fm(xr, yr, xi * yi), ni = fm(xi, yr, -(xr * yi));
+      const T den = fm(y[0], y[0], y[1] * y[1]), nr = fm(x[0], y[0], x[1] * y[1]), ni = fm(x[1], y[0], -(x[0] * y[1]));
       lr = nr / den;
       li = ni / den;
-      a[2 * (int64_t)p] = lr;
-      a[2 * (int64_t)p + 1] = li;
+    }
+  }
+  // a := a - l * u
+  __device__ static void update(T lr, T li, const T* u, T* av) {
+    if constexpr (CP == 1) {
+      av[0] = fm(-lr, u[0], av[0]);
+    } else {
+      T re = fm(-lr, u[0], av[0]), im = fm(-lr, u[1], av[1]);
+      re = fm(li, u[1], re);
+      im = fm(-li, u[0], im);
+      av[0] = re;
+      av[1] = im;
+    }
+  }
+  __device__ void spill() {  // row i back to memory; the memory path continues from there
+#pragma unroll
+    for (int t = 0; t < RI; ++t)
+      if (t < len)
+#pragma unroll
+        for (int h = 0; h < CP; ++h) a[(int64_t)(p0 + t) * CP + h] = rv[t * CP + h];
+    reg = false;
+  }
+  __device__ void consume(int p, int k, const Val& vk) {
+    if (reg && vk.ek - vk.dk - 1 > RK) spill();
+    if (reg) {
+      const int tk = p - p0;  // position of (i, k) in row i
+      T x[CP];
+#pragma unroll
+      for (int t = 0; t < RI; ++t)
+        if (t == tk)
+#pragma unroll
+          for (int h = 0; h < CP; ++h) x[h] = rv[t * CP + h];
+      T lr, li;
+      divide(x, vk.piv, lr, li);
+#pragma unroll
+      for (int t = 0; t < RI; ++t)
+        if (t == tk) {
+          rv[t * CP] = lr;
+          if constexpr (CP == 2) rv[t * CP + 1] = li;
+        }
+#pragma unroll
+      for (int u = 0; u < RK; ++u) {
+        if (vk.uc[u] < 0) continue;
+#pragma unroll
+        for (int t = 0; t < RI; ++t)
+          if (t > tk && t < len && rc[t] == vk.uc[u]) update(lr, li, vk.uv + u * CP, rv + t * CP);
+      }
+      return;
+    }
+    const int dk = vk.dk, ek = vk.ek, ei = rp[i + 1];
+    T lr, li;
+    {
+      T x[CP];
+#pragma unroll
+      for (int h = 0; h < CP; ++h) x[h] = a[(int64_t)p * CP + h];
+      divide(x, vk.piv, lr, li);
+      a[(int64_t)p * CP] = lr;
+      if constexpr (CP == 2) a[(int64_t)p * CP + 1] = li;
     }
     int r = p + 1;
     for (int q = dk + 1; q < ek; ++q) {
@@ -107,19 +198,19 @@ struct RowIlu {
       while (r < ei && ci[r] < j) ++r;
       if (r >= ei) break;
       if (ci[r] != j) continue;
-      if constexpr (CP == 1) {
-        a[r] = fm(-lr, a[q], a[r]);
-      } else {
-        const T ur = a[2 * (int64_t)q], ui = a[2 * (int64_t)q + 1];
-        T re = fm(-lr, ur, a[2 * (int64_t)r]), im = fm(-lr, ui, a[2 * (int64_t)r + 1]);
-        re = fm(li, ui, re);
-        im = fm(-li, ur, im);
-        a[2 * (int64_t)r] = re;
-        a[2 * (int64_t)r + 1] = im;
+      T u[CP], av[CP];
+#pragma unroll
+      for (int h = 0; h < CP; ++h) {
+        u[h] = a[(int64_t)q * CP + h];
+        av[h] = a[(int64_t)r * CP + h];
       }
+      update(lr, li, u, av);
+#pragma unroll
+      for (int h = 0; h < CP; ++h) a[(int64_t)r * CP + h] = av[h];
     }
   }
   __device__ Val finish() {
+    if (reg) spill();
     const int d = diag[i];
     bool zero;
     if constexpr (CP == 1) zero = a[d] == T(0);
