@@ -476,17 +476,29 @@ struct RowDepth {
     st_relaxed_u64(pk + i, ((unsigned long long)epoch << 32) | (unsigned)v);
   }
 };
-__global__ void __launch_bounds__(kBlock) k_row_depth(Order ord, const int* __restrict__ ci, const int* __restrict__ rp,
-                                                      const int* __restrict__ diag, bool lower, unsigned long long* pk,
-                                                      unsigned epoch, int* depth, int* ticket, int* ctl) {
+// Both triangles at once: the first half of the blocks runs the lower triangle's pass, the second
+// half the upper one's, each with its own order, ticket, packed words and result (the two passes
+// are independent; each half's warps are resident, so each pass progresses as alone).
+struct DepthPass {
+  Order ord;
+  unsigned long long* pk;
+  unsigned epoch;
+  int* depth;
+  int* ticket;
+};
+__global__ void __launch_bounds__(kBlock) k_row_depth(DepthPass lo_pass, DepthPass up_pass, const int* __restrict__ ci,
+                                                      const int* __restrict__ rp, const int* __restrict__ diag,
+                                                      int* ctl) {
+  const bool lower = blockIdx.x < (gridDim.x >> 1);
+  const DepthPass& P = lower ? lo_pass : up_pass;
   RowDepth row;
   row.rp = rp;
   row.diag = diag;
   row.lower = lower;
-  row.pk = pk;
-  row.epoch = epoch;
-  row.depth = depth;
-  syncfree_rows(ord, ci, ticket, ctl, row);
+  row.pk = P.pk;
+  row.epoch = P.epoch;
+  row.depth = P.depth;
+  syncfree_rows(P.ord, ci, P.ticket, ctl, row);
 }
 // Natural row order of a triangle as an Order: position q holds row q (lower) or n-1-q (upper).
 __global__ void k_natural_order(int n, bool lower, int npos, int* __restrict__ perm, int* __restrict__ pos) {
@@ -582,39 +594,58 @@ static int build_levels(int n, const int* rp, const int* ci, const int* diag, un
                         int which, int** bufs, int* nlev, int** depths, cudaStream_t s) {
   const int m = (n + 31) >> 5;
   const size_t L = (size_t)n + 1;
+  // per triangle: level counts (L), natural order perm (32 m) and pos (n), largest level (1);
+  // packed words of the upper pass (the lower pass uses pk)
   int* tmp = nullptr;
-  MPK_CUDA(cudaMallocAsync((void**)&tmp, sizeof(int) * (2 * L + (size_t)m * 32 + (size_t)n + 16), s));
-  int* cnt = tmp + L;                    // L
-  int* perm_c = cnt + L;                 // 32 m
-  int* pos_c = perm_c + (size_t)m * 32;  // n
-  int* maxd = pos_c + n;                 // 1
-  static int blocks_rd = persistent_blocks(k_row_depth);
+  const size_t per = L + (size_t)m * 32 + (size_t)n + 1;
+  MPK_CUDA(cudaMallocAsync((void**)&tmp, sizeof(int) * (2 * per + 16) + sizeof(unsigned long long) * L, s));
+  int* cnt[2];
+  int* perm_c[2];
+  int* pos_c[2];
+  int* maxd[2];
   for (int tri = 0; tri < 2; ++tri) {
-    const bool lower = tri == 0;
+    int* base = tmp + tri * per;
+    cnt[tri] = base;
+    perm_c[tri] = base + L;
+    pos_c[tri] = perm_c[tri] + (size_t)m * 32;
+    maxd[tri] = pos_c[tri] + n;
+  }
+  unsigned long long* pk_up = (unsigned long long*)(((uintptr_t)(tmp + 2 * per + 8)) & ~(uintptr_t)7);
+  MPK_CUDA(cudaMemsetAsync(tmp, 0, sizeof(int) * 2 * per, s));
+  MPK_CUDA(cudaMemsetAsync(pk_up, 0, sizeof(unsigned long long) * L, s));
+  MPK_CUDA(cudaMemsetAsync(ctl + CTL_TICKET_LO, 0, sizeof(int) * 2, s));  // CTL_TICKET_LO, CTL_TICKET_UP
+  DepthPass pass[2];
+  for (int tri = 0; tri < 2; ++tri) {
     int* depth = nullptr;  // kept: the owner-block layout groups rows by level
     MPK_CUDA(cudaMalloc((void**)&depth, sizeof(int) * L));
     depths[tri] = depth;
-    MPK_CUDA(cudaMemsetAsync(ctl + CTL_TICKET_LO, 0, sizeof(int), s));
-    MPK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * L, s));
-    MPK_CUDA(cudaMemsetAsync(maxd, 0, sizeof(int), s));
-    Order oc;
-    oc.perm = perm_c;
-    oc.pos = pos_c;
-    oc.npos = m * 32;
-    count_launch(3);
-    k_natural_order<<<grid_for(m * 32), kBlock, 0, s>>>(n, lower, m * 32, perm_c, pos_c);
-    k_row_depth<<<blocks_rd, kBlock, 0, s>>>(oc, ci, rp, diag, lower, pk, kDepthEpoch0 + 4u * which + 2u + tri, depth,
-                                             ctl + CTL_TICKET_LO, ctl);
-    k_depth_count<<<grid_for(n), kBlock, 0, s>>>(n, depth, cnt, maxd);
-    int hmax = 0, herr = 0;
-    MPK_CUDA(cudaMemcpyAsync(&hmax, maxd, sizeof(int), cudaMemcpyDeviceToHost, s));
-    MPK_CUDA(cudaMemcpyAsync(&herr, ctl + CTL_ERR, sizeof(int), cudaMemcpyDeviceToHost, s));
-    MPK_CUDA(cudaStreamSynchronize(s));
-    if (herr != 0) {
-      cudaFreeAsync(tmp, s);
-      return fail(MPK_TIMEOUT, "a bounded device wait ran out while ordering the triangles");
-    }
-    const int nl = hmax + 1;
+    count_launch();
+    k_natural_order<<<grid_for(m * 32), kBlock, 0, s>>>(n, tri == 0, m * 32, perm_c[tri], pos_c[tri]);
+    pass[tri].ord.perm = perm_c[tri];
+    pass[tri].ord.pos = pos_c[tri];
+    pass[tri].ord.npos = m * 32;
+    pass[tri].pk = tri == 0 ? pk : pk_up;
+    pass[tri].epoch = kDepthEpoch0 + 4u * which + 2u + tri;
+    pass[tri].depth = depth;
+    pass[tri].ticket = ctl + (tri == 0 ? CTL_TICKET_LO : CTL_TICKET_UP);
+  }
+  static int blocks_rd = (persistent_blocks(k_row_depth) + 1) & ~1;  // even: two halves
+  count_launch(3);
+  k_row_depth<<<blocks_rd, kBlock, 0, s>>>(pass[0], pass[1], ci, rp, diag, ctl);
+  for (int tri = 0; tri < 2; ++tri) k_depth_count<<<grid_for(n), kBlock, 0, s>>>(n, depths[tri], cnt[tri], maxd[tri]);
+  int hmax[2] = {0, 0}, herr = 0;
+  MPK_CUDA(cudaMemcpyAsync(&hmax[0], maxd[0], sizeof(int), cudaMemcpyDeviceToHost, s));
+  MPK_CUDA(cudaMemcpyAsync(&hmax[1], maxd[1], sizeof(int), cudaMemcpyDeviceToHost, s));
+  MPK_CUDA(cudaMemcpyAsync(&herr, ctl + CTL_ERR, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MPK_CUDA(cudaStreamSynchronize(s));
+  if (herr != 0) {
+    cudaFreeAsync(tmp, s);
+    return fail(MPK_TIMEOUT, "a bounded device wait ran out while ordering the triangles");
+  }
+  for (int tri = 0; tri < 2; ++tri) {
+    const bool lower = tri == 0;
+    const int nl = hmax[tri] + 1;
+    int* depth = depths[tri];
     int* buf = nullptr;
     MPK_CUDA(cudaMalloc((void**)&buf, sizeof(int) * level_buf_ints(n, nl)));
     const LevelOrder lo = level_view(buf, n, nl);
@@ -628,7 +659,7 @@ static int build_levels(int n, const int* rp, const int* ci, const int* diag, un
     int* sub = cnt2 + (size_t)nl * kLenB;
     MPK_CUDA(cudaMemsetAsync(cnt2, 0, sizeof(int) * (size_t)nl * kLenB, s));
     count_launch(4);
-    k_level_layout<<<1, 1024, 0, s>>>(nl, cnt, off, lo);
+    k_level_layout<<<1, 1024, 0, s>>>(nl, cnt[tri], off, lo);
     k_key_count<<<grid_for(n), kBlock, 0, s>>>(n, depth, rp, diag, lower, cnt2);
     k_key_offsets<<<(nl + 255) / 256, 256, 0, s>>>(nl, off, cnt2, sub);
     k_level_scatter<<<grid_for(n), kBlock, 0, s>>>(n, depth, rp, diag, lower, sub, buf, const_cast<int*>(lo.pos));
@@ -636,7 +667,7 @@ static int build_levels(int n, const int* rp, const int* ci, const int* diag, un
     bufs[tri] = buf;
     nlev[tri] = nl;
   }
-  MPK_CUDA(cudaMemsetAsync(ctl + CTL_TICKET_LO, 0, sizeof(int), s));
+  MPK_CUDA(cudaMemsetAsync(ctl + CTL_TICKET_LO, 0, sizeof(int) * 2, s));
   MPK_CUDA(cudaGetLastError());
   MPK_CUDA(cudaFreeAsync(tmp, s));
   return MPK_OK;
