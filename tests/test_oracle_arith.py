@@ -165,3 +165,4 @@ def test_exact_results_are_exact():
     for w in (1, 2, 3, 4):
         x = rand_mp(random.Random(w), w)
         assert all(c == 0 for c in oracle.mp_op("sub", w, x, x))
+
