@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=1, help="oracle iterations in the CPU sample")
     ap.add_argument("--only", default=None, choices=["spmv", "spmv_mm", "precond_fp64", "precond_fp32", "precond_bf16",
-                                                     "precond_mp", "ilu_fp64", "ilu_mp"],
+                                                     "precond_mp", "ilu_fp64", "ilu_fp32", "ilu_mp"],
                     help="run just this kernel --reps times on the workload (for profiling) and exit")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--only-on", default="convdiff3d", choices=["convdiff3d", "helmholtz2d", "batch512"],
@@ -450,8 +450,8 @@ def run_only(args):
     y = torch.empty_like(x)
     if args.only in ("spmv", "spmv_mm"):
         fn = lambda: _lib.spmv_mp(A, x, w, y, mp_matrix=args.only == "spmv_mm")
-    elif args.only == "ilu_fp64":
-        fn = lambda: _lib.ILU0(A, "fp64").close()
+    elif args.only in ("ilu_fp64", "ilu_fp32"):
+        fn = lambda: _lib.ILU0(A, args.only.split("_")[1]).close()
     elif args.only == "ilu_mp":
         fn = lambda: _lib.ILU0(A, "mp", w).close()
     else:

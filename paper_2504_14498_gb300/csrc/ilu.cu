@@ -235,6 +235,19 @@ __global__ void __launch_bounds__(kBlock) k_ilu(int n, const int* __restrict__ r
   chunk_rows(lo, ci, kIluEpoch, ctl + CTL_TICKET_LO, ctl, row);
 }
 
+// The same rows level by level (level_rows): a cooperative launch, grid barriers between levels.
+template <typename T, int CP>
+__global__ void __launch_bounds__(kBlock) k_ilu_lv(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                   const int* __restrict__ diag, const LevelOrder lo, T* a, int* ctl) {
+  RowIlu<T, CP> row;
+  row.rp = rp;
+  row.ci = ci;
+  row.diag = diag;
+  row.a = a;
+  row.ctl = ctl;
+  level_rows(lo, ci, ctl, row);
+}
+
 // ILU(0) in w-component arithmetic (MPK_ILU_MP): the same row-IKJ dataflow, entries of CP * W
 // doubles; for each k < i in row i, ascending: a_ik := a_ik / a_kk (the format's division), then
 // a_ij := a_ij - a_ik * a_kj for every j > k of row k also in row i (product with a_ik first,
@@ -300,23 +313,73 @@ __global__ void k_to_mp(int64_t nnz, int cp, int w, const double* __restrict__ v
 }
 
 template <int W, int CP>
-static void launch_ilu_mp_wc(int n, const int* rp, const int* ci, const int* diag, const LevelOrder& lo, double* a,
-                             int* ctl, cudaStream_t s) {
-  static const int blocks = persistent_blocks(k_ilu_mp<W, CP>);
-  k_ilu_mp<W, CP><<<blocks, kBlock, 0, s>>>(n, rp, ci, diag, lo, a, ctl);
+__global__ void __launch_bounds__(kBlock) k_ilu_mp_lv(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                      const int* __restrict__ diag, const LevelOrder lo, double* a,
+                                                      int* ctl) {
+  RowIluMp<W, CP> row;
+  row.rp = rp;
+  row.ci = ci;
+  row.diag = diag;
+  row.a = a;
+  row.ctl = ctl;
+  level_rows(lo, ci, ctl, row);
 }
-static void launch_ilu_mp(int w, int cp, int n, const int* rp, const int* ci, const int* diag, const LevelOrder& lo,
-                          double* a, int* ctl, cudaStream_t s) {
+
+// Schedule of the ILU(0) kernels: level-synchronous (level_rows) or the dataflow over chunk flags
+// (chunk_rows).  Both compute every row with the same operations in the same order: identical
+// factors.  Measured on GB300: levels of a few hundred chunks (the 128^3 mesh: 382 levels of 172
+// chunks on average) factor faster level by level (12.1 against 12.8 ms for the whole
+// factorisation), while wide levels (the 512-system batch: 61 levels of ~10,000 chunks) want the
+// dataflow, which overlaps consecutive levels (133 against 153 ms).  So the levels schedule is
+// taken when a level averages no more chunks than the grid has warps; MPK_ILU_SCHEDULE=levels|
+// dataflow, read at every factorisation, forces one.
+static bool ilu_levels(int n, int nlev, int warps) {
+  const char* e = std::getenv("MPK_ILU_SCHEDULE");
+  if (e != nullptr && std::strcmp(e, "dataflow") == 0) return false;
+  if (e != nullptr && std::strcmp(e, "levels") == 0) return true;
+  return (double)n / (32.0 * (nlev > 0 ? nlev : 1)) <= (double)warps;
+}
+// One launch of the level-synchronous kernel `lv` (cooperative: its grid barriers need every
+// block resident) or of the dataflow kernel `df`, over the lower level order.
+template <typename T>
+static int launch_ilu_kernel(const void* lv, const void* df, int blocks_lv, int blocks_df, int n, const int* rp,
+                             const int* ci, const int* diag, LevelOrder lo, T* a, int* ctl, cudaStream_t s) {
+  void* args[] = {(void*)&n, (void*)&rp, (void*)&ci, (void*)&diag, (void*)&lo, (void*)&a, (void*)&ctl};
   count_launch();
+  if (ilu_levels(n, lo.nlev, blocks_lv * (kBlock / 32))) {
+    MPK_CUDA(cudaMemsetAsync(ctl + CTL_BAR_COUNT, 0, sizeof(int), s));
+    MPK_CUDA(cudaLaunchCooperativeKernel(lv, dim3(blocks_lv), dim3(kBlock), args, 0, s));
+  } else {
+    MPK_CUDA(cudaMemsetAsync(ctl + CTL_TICKET_LO, 0, sizeof(int), s));
+    MPK_CUDA(cudaLaunchKernel(df, dim3(blocks_df), dim3(kBlock), args, 0, s));
+  }
+  return MPK_OK;
+}
+template <typename T, int CP>
+static int launch_ilu(int n, const int* rp, const int* ci, const int* diag, const LevelOrder& lo, T* a, int* ctl,
+                      cudaStream_t s) {
+  static const int blv = persistent_blocks(k_ilu_lv<T, CP>), bdf = persistent_blocks(k_ilu<T, CP>);
+  return launch_ilu_kernel<T>((const void*)k_ilu_lv<T, CP>, (const void*)k_ilu<T, CP>, blv, bdf, n, rp, ci, diag, lo,
+                              a, ctl, s);
+}
+template <int W, int CP>
+static int launch_ilu_mp_wc(int n, const int* rp, const int* ci, const int* diag, const LevelOrder& lo, double* a,
+                            int* ctl, cudaStream_t s) {
+  static const int blv = persistent_blocks(k_ilu_mp_lv<W, CP>), bdf = persistent_blocks(k_ilu_mp<W, CP>);
+  return launch_ilu_kernel<double>((const void*)k_ilu_mp_lv<W, CP>, (const void*)k_ilu_mp<W, CP>, blv, bdf, n, rp,
+                                   ci, diag, lo, a, ctl, s);
+}
+static int launch_ilu_mp(int w, int cp, int n, const int* rp, const int* ci, const int* diag, const LevelOrder& lo,
+                         double* a, int* ctl, cudaStream_t s) {
   switch (w * 2 + cp - 1) {
-    case 2: launch_ilu_mp_wc<1, 1>(n, rp, ci, diag, lo, a, ctl, s); break;
-    case 3: launch_ilu_mp_wc<1, 2>(n, rp, ci, diag, lo, a, ctl, s); break;
-    case 4: launch_ilu_mp_wc<2, 1>(n, rp, ci, diag, lo, a, ctl, s); break;
-    case 5: launch_ilu_mp_wc<2, 2>(n, rp, ci, diag, lo, a, ctl, s); break;
-    case 6: launch_ilu_mp_wc<3, 1>(n, rp, ci, diag, lo, a, ctl, s); break;
-    case 7: launch_ilu_mp_wc<3, 2>(n, rp, ci, diag, lo, a, ctl, s); break;
-    case 8: launch_ilu_mp_wc<4, 1>(n, rp, ci, diag, lo, a, ctl, s); break;
-    default: launch_ilu_mp_wc<4, 2>(n, rp, ci, diag, lo, a, ctl, s); break;
+    case 2: return launch_ilu_mp_wc<1, 1>(n, rp, ci, diag, lo, a, ctl, s);
+    case 3: return launch_ilu_mp_wc<1, 2>(n, rp, ci, diag, lo, a, ctl, s);
+    case 4: return launch_ilu_mp_wc<2, 1>(n, rp, ci, diag, lo, a, ctl, s);
+    case 5: return launch_ilu_mp_wc<2, 2>(n, rp, ci, diag, lo, a, ctl, s);
+    case 6: return launch_ilu_mp_wc<3, 1>(n, rp, ci, diag, lo, a, ctl, s);
+    case 7: return launch_ilu_mp_wc<3, 2>(n, rp, ci, diag, lo, a, ctl, s);
+    case 8: return launch_ilu_mp_wc<4, 1>(n, rp, ci, diag, lo, a, ctl, s);
+    default: return launch_ilu_mp_wc<4, 2>(n, rp, ci, diag, lo, a, ctl, s);
   }
 }
 
@@ -518,7 +581,7 @@ __global__ void k_inverse(int n, const int* __restrict__ perm, int* __restrict__
 
 size_t level_buf_ints(int n, int nlevels) {
   const size_t P = (size_t)n + 32 * (size_t)nlevels;
-  return P + (size_t)n + (P / 32 + 1) + 1;
+  return P + (size_t)n + (P / 32 + 1) + 1 + (size_t)nlevels + 1;
 }
 LevelOrder level_view(int* buf, int n, int nlevels) {
   const size_t P = (size_t)n + 32 * (size_t)nlevels;
@@ -527,11 +590,13 @@ LevelOrder level_view(int* buf, int n, int nlevels) {
   o.pos = buf + P;
   o.flags = buf + P + n;
   o.nchunks = buf + P + n + (P / 32 + 1);
+  o.lstart = o.nchunks + 1;
+  o.nlev = nlevels;
   return o;
 }
 
 // Level layout: level_size = cnt, padded starts (exclusive scan of 32-rounded sizes, in `off`),
-// nchunks; one block of 1024 threads.
+// each level's first chunk (lstart) and nchunks; one block of 1024 threads.
 __global__ void k_level_layout(int nlevels, const int* __restrict__ cnt, int* __restrict__ off, LevelOrder lo) {
   __shared__ int part[1024];
   const int t = threadIdx.x, T_ = blockDim.x;
@@ -545,11 +610,13 @@ __global__ void k_level_layout(int nlevels, const int* __restrict__ cnt, int* __
     int run = 0;
     for (int k = 0; k < T_; ++k) { int v = part[k]; part[k] = run; run += v; }
     *const_cast<int*>(lo.nchunks) = run / 32;
+    const_cast<int*>(lo.lstart)[nlevels] = run / 32;
   }
   __syncthreads();
   int run = part[t];
   for (int k = lo_; k < hi; ++k) {
     off[k] = run;
+    const_cast<int*>(lo.lstart)[k] = run / 32;
     run += (cnt[k] + 31) & ~31;
   }
 }
@@ -1343,20 +1410,18 @@ static int factor_impl(const mpk_csr* A, int prec, int w, mpk_ilu** out, int* fa
     k_narrow<float><<<grid_for((int)((m + 3) / 4)), kBlock, 0, s>>>(m, A->val, (float*)work);
   }
   M->fac = work;
-  MPK_TRY(cudaMemsetAsync(M->ctl + CTL_TICKET_LO, 0, sizeof(int), s));
-  static int blocks_d1 = persistent_blocks(k_ilu<double, 1>), blocks_d2 = persistent_blocks(k_ilu<double, 2>);
-  static int blocks_f1 = persistent_blocks(k_ilu<float, 1>), blocks_f2 = persistent_blocks(k_ilu<float, 2>);
+  const LevelOrder lv_lo = M->view(false).lv_lo;
+  int lst = MPK_OK;
   if (prec == MPK_ILU_MP) {
-    launch_ilu_mp(w, cp, n, M->rp, M->ci, M->diag, M->view(false).lv_lo, (double*)work, M->ctl, s);
+    lst = launch_ilu_mp(w, cp, n, M->rp, M->ci, M->diag, lv_lo, (double*)work, M->ctl, s);
   } else if (prec == MPK_ILU_FP64) {
-    count_launch();
-    if (cp == 1) k_ilu<double, 1><<<blocks_d1, kBlock, 0, s>>>(n, M->rp, M->ci, M->diag, M->view(false).lv_lo, (double*)work, M->ctl);
-    else k_ilu<double, 2><<<blocks_d2, kBlock, 0, s>>>(n, M->rp, M->ci, M->diag, M->view(false).lv_lo, (double*)work, M->ctl);
+    if (cp == 1) lst = launch_ilu<double, 1>(n, M->rp, M->ci, M->diag, lv_lo, (double*)work, M->ctl, s);
+    else lst = launch_ilu<double, 2>(n, M->rp, M->ci, M->diag, lv_lo, (double*)work, M->ctl, s);
   } else {
-    count_launch();
-    if (cp == 1) k_ilu<float, 1><<<blocks_f1, kBlock, 0, s>>>(n, M->rp, M->ci, M->diag, M->view(false).lv_lo, (float*)work, M->ctl);
-    else k_ilu<float, 2><<<blocks_f2, kBlock, 0, s>>>(n, M->rp, M->ci, M->diag, M->view(false).lv_lo, (float*)work, M->ctl);
+    if (cp == 1) lst = launch_ilu<float, 1>(n, M->rp, M->ci, M->diag, lv_lo, (float*)work, M->ctl, s);
+    else lst = launch_ilu<float, 2>(n, M->rp, M->ci, M->diag, lv_lo, (float*)work, M->ctl, s);
   }
+  if (lst != MPK_OK) return bail(lst);
   MPK_TRY(cudaGetLastError());
   int ctl1[CTL_COUNT];
   MPK_TRY(cudaMemcpyAsync(ctl1, M->ctl, sizeof(ctl1), cudaMemcpyDeviceToHost, s));

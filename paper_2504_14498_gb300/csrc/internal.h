@@ -98,6 +98,8 @@ struct LevelOrder {
   const int* pos = nullptr;      // row -> position
   int* flags = nullptr;          // per chunk: epoch of the last pass that finished it
   const int* nchunks = nullptr;  // device int: number of chunks
+  const int* lstart = nullptr;   // nlev + 1: first chunk of every level (the last: nchunks)
+  int nlev = 0;
 };
 
 // A dependency-respecting row order of one triangle (see syncfree_rows).
@@ -210,7 +212,16 @@ struct IluHandleView {
   int sched = 0;                     // see kScheds
   int withhold = -1;                 // testing aid: a row whose value is never published
 };
-enum CtlIdx : int { CTL_EPOCH = 0, CTL_TICKET_LO, CTL_TICKET_UP, CTL_ERR, CTL_FAIL_ROW, CTL_COUNT };
+enum CtlIdx : int {
+  CTL_EPOCH = 0,
+  CTL_TICKET_LO,
+  CTL_TICKET_UP,
+  CTL_ERR,
+  CTL_FAIL_ROW,
+  CTL_BAR_COUNT,  // grid barrier of the level-synchronous kernels: arrivals
+  CTL_BAR_GEN,    // and generation
+  CTL_COUNT
+};
 
 // Launch helpers shared by the instantiation units.
 int sm_count();

@@ -843,6 +843,83 @@ __device__ __forceinline__ void chunk_rows(const LevelOrder lo, const int* __res
   }
 }
 
+// Grid-wide barrier of a co-resident (cooperative) grid on the control words CTL_BAR_COUNT
+// (arrivals) and CTL_BAR_GEN (generation).  Thread 0 of every block reads the generation, makes
+// the block's writes visible (fence after the block barrier) and arrives; the last arrival
+// resets the count and publishes the next generation, the others wait for it.  Every wait is
+// bounded by kWaitCycles (then MPK_TIMEOUT) and ends early once a block has reported an error.
+// Returns false when the grid must stop.
+__device__ __forceinline__ bool grid_barrier(int* ctl) {
+  __shared__ int s_go;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int go = 1;
+    unsigned* cnt = (unsigned*)(ctl + CTL_BAR_COUNT);
+    const int gen = ld_acquire(ctl + CTL_BAR_GEN);
+    __threadfence();
+    if (atomicAdd(cnt, 1u) == gridDim.x - 1) {
+      atomicExch(cnt, 0u);
+      __threadfence();
+      st_release(ctl + CTL_BAR_GEN, gen + 1);
+    } else {
+      const long long t0 = clock64();
+      int rounds = 0;
+      while (ld_acquire(ctl + CTL_BAR_GEN) == gen) {
+        if (clock64() - t0 > kWaitCycles) {
+          atomicCAS(ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
+          go = 0;
+          break;
+        }
+        if ((++rounds & 15) == 0 && ld_relaxed(ctl + CTL_ERR) != 0) {
+          go = 0;
+          break;
+        }
+        if (rounds > 64) __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_go = go;
+  }
+  __syncthreads();
+  return s_go != 0;
+}
+
+// Level-synchronous form of chunk_rows for a co-resident (cooperative) grid: the chunks of level
+// l (lo.lstart[l] .. lo.lstart[l + 1]) are dealt over all warps, warp g taking lstart[l] + g,
+// + G, ... (g numbered so that consecutive chunks fall on different SMs), and a grid barrier
+// separates the levels.  A row depends on rows of earlier levels only, which are final after the
+// barrier: no flags, no polling, no fences per chunk.  The Row calls are those of chunk_rows.
+template <class Row>
+__device__ __forceinline__ void level_rows(const LevelOrder lo, const int* __restrict__ ci, int* ctl, Row& row) {
+  const int lane = threadIdx.x & 31;
+  const int G = gridDim.x * (blockDim.x >> 5);
+  const int g = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+  constexpr int kDepBatch = 4;
+  for (int l = 0; l < lo.nlev; ++l) {
+    const int c1 = lo.lstart[l + 1];
+    for (int c = lo.lstart[l] + g; c < c1; c += G) {
+      const int i = lo.perm[(c << 5) + lane];
+      if (i < 0) continue;
+      int p = 0, pend = 0;
+      row.begin(i, p, pend);
+      for (int q0 = p; q0 < pend; q0 += kDepBatch) {
+        int jj[kDepBatch];
+        typename Row::Val v[kDepBatch];
+#pragma unroll
+        for (int k = 0; k < kDepBatch; ++k) jj[k] = q0 + k < pend ? ci[q0 + k] : -1;
+#pragma unroll
+        for (int k = 0; k < kDepBatch; ++k)
+          if (jj[k] >= 0) v[k] = row.load(jj[k]);
+#pragma unroll
+        for (int k = 0; k < kDepBatch; ++k)
+          if (jj[k] >= 0) row.consume(q0 + k, jj[k], v[k]);
+      }
+      row.store(row.finish());
+    }
+    if (l + 1 < lo.nlev && !grid_barrier(ctl)) return;
+  }
+}
+
 // Binary64 factor, w-component vectors (paper's "_d" substitutions): row i computes
 //   acc = in_i;  acc -= f_ij * out_j  for the row's entries of the triangle in CSR order;
 //   upper triangle: acc /= f_ii;  out_i = acc,
