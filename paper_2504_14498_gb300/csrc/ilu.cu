@@ -523,7 +523,7 @@ struct RowDepth {
     if (lower) { p = rp[i_]; pend = diag[i_]; }
     else { p = diag[i_] + 1; pend = rp[i_ + 1]; }
   }
-  static constexpr int kLook = 4;
+  static constexpr int kLook = 3;  // a 7-point row's 3 entries per triangle; 32 registers in all
   static constexpr int kBatch = 0;
   struct Raw { unsigned long long w; };
   __device__ void issue(int j, Raw& r) { r.w = ld_relaxed_u64(pk + j); }
@@ -549,7 +549,7 @@ struct DepthPass {
   int* depth;
   int* ticket;
 };
-__global__ void __launch_bounds__(kBlock) k_row_depth(DepthPass lo_pass, DepthPass up_pass, const int* __restrict__ ci,
+__global__ void __launch_bounds__(kBlock, 8) k_row_depth(DepthPass lo_pass, DepthPass up_pass, const int* __restrict__ ci,
                                                       const int* __restrict__ rp, const int* __restrict__ diag,
                                                       int* ctl) {
   const bool lower = blockIdx.x < (gridDim.x >> 1);
@@ -696,7 +696,15 @@ static int build_levels(int n, const int* rp, const int* ci, const int* diag, un
     pass[tri].depth = depth;
     pass[tri].ticket = ctl + (tri == 0 ? CTL_TICKET_LO : CTL_TICKET_UP);
   }
-  static int blocks_rd = (persistent_blocks(k_row_depth) + 1) & ~1;  // even: two halves
+  // The pass is bound by its window of rows in flight (it follows the natural row order, in which
+  // the rows that are ready at any moment are spread over the whole matrix), so it runs as many
+  // warps as fit: 32 registers a thread, 64 warps per SM.  Even: two halves.
+  static int blocks_rd = [] {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_row_depth, kBlock, 0) != cudaSuccess || per_sm < 1)
+      per_sm = 1;
+    return (per_sm * sm_count() + 1) & ~1;
+  }();
   count_launch(3);
   k_row_depth<<<blocks_rd, kBlock, 0, s>>>(pass[0], pass[1], ci, rp, diag, ctl);
   for (int tri = 0; tri < 2; ++tri) k_depth_count<<<grid_for(n), kBlock, 0, s>>>(n, depths[tri], cnt[tri], maxd[tri]);
