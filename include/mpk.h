@@ -166,8 +166,11 @@ int mpk_dot_noalloc(int n, int is_complex, int w, const double* a_dev, const dou
 
 /* ILU(0) of A (Algorithm 1; the "!= 0" tests read as membership in A's stored pattern; the
  * update A_ij -= L_ik U_kj is one fused multiply-add; a zero pivot is an error instead of
- * being skipped).  Rows are factored by a dependency-driven device kernel; the result equals
- * the sequential KIJ order bit for bit.  On success *out receives a new handle (free with
+ * being skipped).  Rows are factored in the level order of the lower triangle, either level by
+ * level (a cooperative grid with a grid barrier between levels; taken when the levels are
+ * narrow) or as a dataflow over chunk flags (wide levels); the environment variable
+ * MPK_ILU_SCHEDULE=levels|dataflow forces one.  Either way the result equals the sequential KIJ
+ * order bit for bit.  On success *out receives a new handle (free with
  * mpk_ilu0_destroy); on failure *out is NULL and *fail_row (if not NULL) the failing row.
  * The call synchronises `stream` to read the device status. */
 int mpk_ilu0_factor(const mpk_csr* A, int prec, mpk_ilu** out, int* fail_row, void* stream);
