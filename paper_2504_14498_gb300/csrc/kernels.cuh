@@ -731,7 +731,7 @@ __device__ __forceinline__ void syncfree_rows(const Order ord, const int* __rest
           }
         }
         if (__shfl_sync(FULL, stop, 0)) return;
-        backoff = backoff == 0u ? 32u : (backoff < 256u ? 2u * backoff : 256u);
+        backoff = backoff == 0u ? 32u : (backoff < 1024u ? 2u * backoff : 1024u);
         __nanosleep(backoff);
       }
     }
