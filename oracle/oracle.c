@@ -880,16 +880,18 @@ static int nan_mp(mp a) { return a.c[0] != a.c[0]; }
 
 /* Test hooks (set by orc_krylov_hooks around one call, NULL otherwise):
  *   g_shadow: the initial shadow residual r~0 instead of r0 (n*c*w doubles);
- *   g_trace:  per iteration k (1-based), two leading components of normalised inner products
- *             that exact arithmetic makes zero: BiCGSTAB <t, r_k> / (|t| |r_k|) and 0;
- *             GPBiCG <c, r_k> / (|c| |r_k|) and <y, r_k> / (|y| |r_k|) (y from the second step);
- *             real parts for complex systems.  2 * (maxit + 1) doubles. */
+ *   g_trace:  per iteration k (1-based), the moduli of normalised inner products that exact
+ *             arithmetic makes zero (leading components): BiCGSTAB |<t, r_k>| / (|t| |r_k|) and
+ *             0; GPBiCG |<c, r_k>| / (|c| |r_k|) and |<y, r_k>| / (|y| |r_k|) (y from the second
+ *             step).  For complex systems the modulus covers the imaginary part as well.
+ *             2 * (maxit + 1) doubles. */
 static const double *g_shadow = NULL;
 static double *g_trace = NULL;
 static double ortho(int n, ctx t, const double *a, const double *b) {
-  mp ab = dot(n, t, a, b).re, aa = nrm2(n, t, a), bb = nrm2(n, t, b);
+  num ab = dot(n, t, a, b);
+  mp aa = nrm2(n, t, a), bb = nrm2(n, t, b);
   double den = aa.c[0] * bb.c[0];
-  return den > 0.0 ? ab.c[0] / den : 0.0;
+  return den > 0.0 ? hypot(ab.re.c[0], ab.im.c[0]) / den : 0.0;
 }
 
 int orc_krylov(int method, int n, const int *rp, const int *ci, const double *val, int c, int w, int ilu,

@@ -220,7 +220,9 @@ def test_bicg_two_sided_equals_bicg_on_explicit_operator():
 def test_step_invariants(c):
     """Exact-arithmetic invariants of every step, here in QD (rounding ~1e-60): BiCGSTAB's new
     residual is orthogonal to t = A s^ (omega minimises ||s - omega t||), GPBiCG's to c = A t^ and
-    to y (the two-term minimisation)."""
+    to y (the two-term minimisation).  The trace holds the moduli of the normalised inner
+    products, so for complex systems a slip in a conjugation (omega from <s, t> instead of
+    <t, s>, whose residual is off by a purely imaginary multiple of |t|^2) fails too."""
     n, w = 40, 4
     A = inputs.random_sparse(n, 3, 8, seed=70 + c, complex_=(c == 2), weak_frac=0.0)
     b = inputs.random_vector(n, w, c, seed=10)
