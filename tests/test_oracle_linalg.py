@@ -298,3 +298,44 @@ def test_fp32_path_power_of_two_invariance(shift):
     z1 = oracle.precond(A, fac, np.ldexp(r, shift), 2, "fp32")
     assert np.array_equal(np.ldexp(z0, shift), z1)
     assert np.any(z1 != 0)
+
+
+@pytest.mark.parametrize("prec,u", [("fp64", Fraction(1, 2 ** 53)), ("fp32", Fraction(1, 2 ** 24))])
+def test_ilu0_complex_pattern_invariant(prec, u):
+    """(L~ U~)_ij == a_ij on the pattern for a complex matrix whose off-diagonal entries are
+    complex too (every update l_ik u_kj has four nonzero real products; on a mesh with real
+    couplings the imaginary parts of u_kj stay 0 and the cross terms are never exercised), within
+    (terms + 4) * 4u * sum_k |l_ik| |u_kj| per component."""
+    A = inputs.random_sparse(40, 3, 9, seed=21, complex_=True, weak_frac=0.0)
+    n, rp, ci, val = A
+    st, fac, _ = oracle.ilu0(A, prec, c=2)
+    assert st == 0
+    L, Uu = _dense_LU(A, fac, c=2)
+    one = (Fraction(1), Fraction(0))
+    for i in range(n):
+        L[i][i] = one
+    src = val.astype(np.float32).astype(np.float64) if prec == "fp32" else val
+    updates = 0
+    for i in range(n):
+        for p in range(rp[i], rp[i + 1]):
+            j = ci[p]
+            sr = si = Fraction(0)
+            mag = Fraction(0)
+            terms = 0
+            for k in range(min(i, j) + 1):
+                lk, uk = L[i][k], Uu[k][j]
+                if not isinstance(lk, tuple) or not isinstance(uk, tuple):
+                    continue
+                tr = lk[0] * uk[0] - lk[1] * uk[1]
+                ti = lk[0] * uk[1] + lk[1] * uk[0]
+                if tr != 0 or ti != 0:
+                    terms += 1
+                    if k != min(i, j) and lk[1] != 0 and uk[1] != 0:
+                        updates += 1
+                sr += tr
+                si += ti
+                mag += (abs(lk[0]) + abs(lk[1])) * (abs(uk[0]) + abs(uk[1]))
+            bound = (terms + 4) * 4 * u * mag
+            assert abs(sr - Fraction(src[2 * p])) <= bound, (i, j, "re")
+            assert abs(si - Fraction(src[2 * p + 1])) <= bound, (i, j, "im")
+    assert updates > 0  # the cross terms of complex updates were exercised
