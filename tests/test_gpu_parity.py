@@ -165,6 +165,25 @@ def _compare_solve(method, A_t, c, w, ilu, tol, maxit=600, x_star=None):
 
 
 @pytest.mark.parametrize("method", ["bicg", "cgs", "bicgstab", "gpbicg"])
+def test_stopping_rule_absolute_term(method):
+    """||r_k|| < eps_r ||r_0|| + eps_a with the absolute term deciding (eps_r = 0, and both
+    terms): the GPU stops at the same iteration as the oracle, with the same iterates."""
+    A_t = inputs.convdiff2d(10, pe=10.0)
+    n, w = A_t[0], 2
+    A = _lib.Matrix.from_tuple(A_t)
+    b_ref = oracle.spmv(A_t, inputs.ones(n, w), w)
+    M = _lib.ILU0(A, "fp64")
+    r0 = oracle.krylov(method, A_t, b_ref, w, ilu="fp64", maxit=1)["hist"][0]
+    for tol_rel, tol_abs in ((0.0, 1e-6 * r0), (1e-9, 1e-6 * r0)):
+        out = _lib.krylov_solve(method, w, A, M, dev(b_ref), tol_rel=tol_rel, tol_abs=tol_abs, maxit=200)
+        ref = oracle.krylov(method, A_t, b_ref, w, ilu="fp64", tol_rel=tol_rel, tol_abs=tol_abs, maxit=200)
+        assert out["status"] == ref["status"] == "OK"
+        assert out["iters"] == ref["iters"]
+        assert np.array_equal(out["hist"], ref["hist"])
+        assert np.array_equal(host(out["x"]), ref["x"])
+
+
+@pytest.mark.parametrize("method", ["bicg", "cgs", "bicgstab", "gpbicg"])
 @pytest.mark.parametrize("ilu", ["fp64", "fp32", "bf16", "none"])
 def test_krylov_real_dd(method, ilu):
     A_t = inputs.convdiff2d(33, pe=10.0)

@@ -149,6 +149,27 @@ def test_nan_and_maxit():
     assert out["status"] == "MAXIT" and out["iters"] == 3
 
 
+@pytest.mark.parametrize("method", METHODS)
+def test_stopping_rule_both_terms(method):
+    """Algorithm 3's test ||r_k|| < eps_r ||r_0|| + eps_a, both terms: with eps_r = 0 the run stops
+    at the first k whose recorded norm is below eps_a (and not before), with eps_a = 0 at the
+    first below eps_r ||r_0||; a larger eps_a stops earlier."""
+    A = inputs.convdiff2d(10, pe=10.0)
+    n, w = A[0], 2
+    b = _rhs(A, inputs.ones(n, w), w)
+    ref = oracle.krylov(method, A, b, w, ilu="fp64", tol_rel=1e-28, maxit=200)
+    r0 = ref["hist"][0]
+    for tol_rel, tol_abs in ((0.0, 1e-6 * r0), (1e-6, 0.0), (1e-9, 1e-6 * r0)):
+        out = oracle.krylov(method, A, b, w, ilu="fp64", tol_rel=tol_rel, tol_abs=tol_abs, maxit=200)
+        tol = tol_rel * r0 + tol_abs
+        h = out["hist"]
+        assert out["status"] == "OK"
+        assert h[-1] < tol and np.all(h[:-1] >= tol), (tol_rel, tol_abs, h)
+        assert np.array_equal(h, ref["hist"][: len(h)])  # the same iterates until it stops
+    early = oracle.krylov(method, A, b, w, ilu="fp64", tol_rel=1e-12, tol_abs=1e-3 * r0, maxit=200)
+    assert early["iters"] < oracle.krylov(method, A, b, w, ilu="fp64", tol_rel=1e-12, maxit=200)["iters"]
+
+
 def test_ilu_needed_paper_setting():
     """Sec. 4 setting (eps_r = 1e-13, eps_a = 1e-100, maxit = 3n) on the config-1 stand-in:
     with ILU(0) each method converges, and needs far fewer iterations than without it."""
