@@ -138,6 +138,26 @@ def test_breakdown_status():
         assert out["status"] == "BREAKDOWN", m
 
 
+@pytest.mark.parametrize("w", [1, 2, 3, 4])
+def test_bicgstab_omega_zero_is_breakdown(w):
+    """omega = <t, s> / <t, t> = 0 makes the next beta = (rho_new / rho)(alpha / omega) divide
+    by zero, so it is a breakdown.  A = [[0, -1], [1, 0]] (skew), b = e1, shadow (1, 49): alpha =
+    1/49 rounded, s = (1, -alpha), t = A s = (alpha, 1), and <t, s> = alpha - alpha = 0 exactly,
+    while rho_new = <r~, s> = 1 - 49 alpha is not 0 after rounding in D, TD and QD (in exact
+    arithmetic it would be, and the rho test would catch it; in DD the product rounds back to 1
+    and the rho test fires on the same iteration).  Expected: BREAKDOWN after 1 iteration,
+    x = alpha b."""
+    A = (2, np.array([0, 1, 2], np.int32), np.array([1, 0], np.int32), np.array([-1.0, 1.0]))
+    b = np.zeros(2 * w)
+    b[0] = 1.0
+    shadow = np.zeros(2 * w)
+    shadow[0], shadow[w] = 1.0, 49.0
+    out = oracle.krylov("bicgstab", A, b, w, shadow=shadow, maxit=10)
+    assert out["status"] == "BREAKDOWN" and out["iters"] == 1
+    alpha = oracle.mp_op("div", w, [1.0] + [0.0] * (w - 1), [49.0] + [0.0] * (w - 1))
+    assert np.array_equal(out["x"][:w], alpha) and not np.any(out["x"][w:])
+
+
 def test_nan_and_maxit():
     A = inputs.convdiff2d(8, pe=10.0)
     n, w = A[0], 2
