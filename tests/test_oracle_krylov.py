@@ -158,6 +158,63 @@ def test_bicgstab_omega_zero_is_breakdown(w):
     assert np.array_equal(out["x"][:w], alpha) and not np.any(out["x"][w:])
 
 
+def test_gpbicg_zeta_zero_is_breakdown():
+    """GPBiCG's first step is BiCGSTAB's (eta = 0, zeta = <c, t> / <c, c>), so on the skew system
+    above zeta is exactly 0; the next beta = (alpha / zeta)(...) would divide by it: BREAKDOWN
+    after 1 iteration in every format where the rho test does not fire first."""
+    A = (2, np.array([0, 1, 2], np.int32), np.array([1, 0], np.int32), np.array([-1.0, 1.0]))
+    for w in (1, 3, 4):
+        b = np.zeros(2 * w)
+        b[0] = 1.0
+        shadow = np.zeros(2 * w)
+        shadow[0], shadow[w] = 1.0, 49.0
+        out = oracle.krylov("gpbicg", A, b, w, shadow=shadow, maxit=10)
+        assert out["status"] == "BREAKDOWN" and out["iters"] == 1, w
+
+
+@pytest.mark.parametrize("w", [1, 2, 4])
+def test_gpbicg_singular_least_squares_is_breakdown(w):
+    """GPBiCG's two-term minimisation ||t - eta y - zeta c|| has a singular 2x2 system when y and c
+    are parallel (det = <c,c><y,y> - <c,y><y,c> = 0).  On this 3x3 integer system with a shadow
+    residual every scalar of the first two steps is a dyadic rational, so each format computes
+    them exactly (alpha = 1/4, zeta = 1/4, beta = -3/8, then alpha = -2), and at the second step
+    c = (0, 0, -9) and y = (0, 0, -9/2) = c/2 (found by an exact rational search): BREAKDOWN after
+    1 completed iteration."""
+    D = [[2, 1, 0], [2, 0, 0], [-2, -2, 2]]
+    rp, ci, v = [0], [], []
+    for row in D:
+        for j, a in enumerate(row):
+            if a:
+                ci.append(j)
+                v.append(float(a))
+        rp.append(len(ci))
+    A = (3, np.array(rp, np.int32), np.array(ci, np.int32), np.array(v))
+    b = np.zeros(3 * w)
+    b[::w] = [-2.0, 0.0, -1.0]
+    shadow = np.zeros(3 * w)
+    shadow[::w] = [-1.0, -1.0, 0.0]
+    out = oracle.krylov("gpbicg", A, b, w, shadow=shadow, maxit=10)
+    assert out["status"] == "BREAKDOWN" and out["iters"] == 1
+
+
+@pytest.mark.parametrize("method", METHODS)
+@pytest.mark.parametrize("w", [1, 2])
+def test_breakdown_rho_zero(method, w):
+    """rho = <r~, r> = 0 with r != 0 (a shadow residual orthogonal to r0) is a breakdown before
+    the first step: BREAKDOWN after 0 iterations and x = x0 (otherwise alpha = 0 and the
+    iteration would stall until maxit)."""
+    A = inputs.convdiff2d(4, pe=3.0)
+    n = A[0]
+    b = _rhs(A, inputs.ones(n, w), w)
+    bh = b.reshape(n, w)[:, 0]
+    assert not np.any(b.reshape(n, w)[:, 1:])  # integer row sums: exact leading parts
+    shadow = np.zeros(n * w)
+    shadow[0], shadow[w] = bh[1], -bh[0]
+    out = oracle.krylov(method, A, b, w, shadow=shadow, maxit=20)
+    assert out["status"] == "BREAKDOWN" and out["iters"] == 0
+    assert not np.any(out["x"])
+
+
 def test_nan_and_maxit():
     A = inputs.convdiff2d(8, pe=10.0)
     n, w = A[0], 2
