@@ -1,7 +1,7 @@
 """Pins of the learned-correction oracle (oracle/gnn.py) to things other than itself:
 finite differences of its forward pass and loss (the gradients), an explicit dense evaluation of
 the factorisation-error loss, the exactness of ILU(0) on A's pattern when the correction is zero,
-and the batch loss as the mean of the systems' losses."""
+the batch loss as the mean of the systems' losses, and closed forms of the Adam step."""
 import numpy as np
 import pytest
 
@@ -146,3 +146,23 @@ def test_precond_loss_equals_dense_evaluation():
     T = inputs.tridiag(9, -1.0, 2.5, -0.7)
     _, ft, _ = oracle.ilu0(T, "fp64")
     assert gnn.loss_precond(T, ft, np.zeros(len(T[2])), inputs.probe_vectors(9, 2, 1))[0] < 1e-28
+
+
+def test_adam_closed_forms():
+    """Adam (Kingma and Ba, 2015) with its bias corrections: under a constant gradient g the
+    corrected moments are exactly g and g^2 at every step, so step k leaves P = -k lr g / (|g| +
+    eps); the first step of any gradient moves by lr g / (|g| + eps); and when the gradient flips
+    to -g at step 2 the corrected moments are -g (1 - b1) / (1 + b1) and g^2."""
+    lr, b1, b2, eps = 1e-2, 0.9, 0.999, 1e-8
+    g = np.array([3.0, -0.5, 1e-3, 2.0])
+    P, m, v = np.zeros(4), np.zeros(4), np.zeros(4)
+    for step in range(1, 6):
+        P, m, v = gnn.adam(P, g, m, v, lr, step)
+        np.testing.assert_allclose(P, -step * lr * g / (np.abs(g) + eps), rtol=1e-12)
+    P1, _, _ = gnn.adam(np.ones(4), -g, np.zeros(4), np.zeros(4), lr, 1)
+    np.testing.assert_allclose(P1, 1.0 + lr * g / (np.abs(g) + eps), rtol=1e-12)
+    P, m, v = gnn.adam(np.zeros(4), g, np.zeros(4), np.zeros(4), lr, 1)
+    P, m, v = gnn.adam(P, -g, m, v, lr, 2)
+    m_hat = -g * (1 - b1) / (1 + b1)
+    step2 = -lr * m_hat / (np.abs(g) + eps)
+    np.testing.assert_allclose(P, -lr * g / (np.abs(g) + eps) + step2, rtol=1e-10)
