@@ -112,8 +112,26 @@ def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def _ptr(t):
+def _ptr(t, numel=None, dtype=None, name="buffer"):
+    """Device pointer of a tensor the library reads or writes.  The C functions take raw pointers
+    and sizes, so a host tensor, a strided view, a narrower dtype or a short buffer is refused
+    here, before any call (MPK_INVALID_ARG semantics, as ValueError)."""
+    if not isinstance(t, torch.Tensor):
+        raise ValueError("%s: expected a torch tensor, got %s" % (name, type(t).__name__))
+    if t.device.type != "cuda":
+        raise ValueError("%s: the library needs device memory (a CUDA tensor), got %s" % (name, t.device))
+    if not t.is_contiguous():
+        raise ValueError("%s: must be contiguous" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError("%s: expected %s, got %s" % (name, dtype, t.dtype))
+    if numel is not None and t.numel() < numel:
+        raise ValueError("%s: needs at least %d elements, has %d" % (name, numel, t.numel()))
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _vec(t, numel, name):
+    """A multi-component vector argument: float64, on the device, contiguous, numel doubles."""
+    return _ptr(t, numel, torch.float64, name)
 
 
 class Matrix:
@@ -139,17 +157,22 @@ class Matrix:
 def spmv_mp(A: Matrix, x: torch.Tensor, w: int, y: torch.Tensor = None, mp_matrix=False) -> torch.Tensor:
     """y = A x with w-component vectors (n*c*w doubles); mp_matrix: A's entries promoted to w
     components (the rows without "_d")."""
+    m = A.n * A.cp * w
     if y is None:
-        y = torch.empty(A.n * A.cp * w, dtype=torch.float64, device=x.device)
+        y = torch.empty(m, dtype=torch.float64, device=x.device)
+    px, py = _vec(x, m, "x"), _vec(y, m, "y")
     f = lib().mpk_spmv_mp_matrix if mp_matrix else lib().mpk_spmv_mp
-    _check(f(ctypes.byref(A.desc), w, _ptr(x), _ptr(y), _stream()))
+    _check(f(ctypes.byref(A.desc), w, px, py, _stream()))
     return y
 
 
 def dot(a: torch.Tensor, b: torch.Tensor, n: int, w: int, is_complex=False) -> torch.Tensor:
     """<a, b> = sum conj(a_i) b_i; returns a device tensor of c*w doubles."""
-    out = torch.empty((2 if is_complex else 1) * w, dtype=torch.float64, device=a.device)
-    _check(lib().mpk_dot(n, int(is_complex), w, _ptr(a), _ptr(b), _ptr(out), _stream()))
+    c = 2 if is_complex else 1
+    out = torch.empty(c * w, dtype=torch.float64, device=a.device)
+    m = n * c * w
+    _check(lib().mpk_dot(n, int(is_complex), w, _vec(a, m, "a"), _vec(b, m, "b"), _vec(out, c * w, "out"),
+                         _stream()))
     return out
 
 
@@ -157,9 +180,12 @@ def dot_noalloc(a: torch.Tensor, b: torch.Tensor, n: int, w: int, is_complex=Fal
     """Same as dot(), for callers that must not let the library allocate device memory: the
     reduction scratch is a fixed array inside the library (n <= MPK_DOT_NOALLOC_MAX_N).  `out`
     may be preallocated by the caller (c*w doubles)."""
+    c = 2 if is_complex else 1
     if out is None:
-        out = torch.empty((2 if is_complex else 1) * w, dtype=torch.float64, device=a.device)
-    _check(lib().mpk_dot_noalloc(n, int(is_complex), w, _ptr(a), _ptr(b), _ptr(out), _stream()))
+        out = torch.empty(c * w, dtype=torch.float64, device=a.device)
+    m = n * c * w
+    _check(lib().mpk_dot_noalloc(n, int(is_complex), w, _vec(a, m, "a"), _vec(b, m, "b"), _vec(out, c * w, "out"),
+                                 _stream()))
     return out
 
 
@@ -203,7 +229,8 @@ class ILU0:
     def apply(self, r: torch.Tensor, w: int, trans=False, z: torch.Tensor = None) -> torch.Tensor:
         if z is None:
             z = torch.empty_like(r)
-        _check(lib().mpk_precond_apply(self.handle, w, int(trans), _ptr(r), _ptr(z), _stream()))
+        m = self.A.n * self.A.cp * w
+        _check(lib().mpk_precond_apply(self.handle, w, int(trans), _vec(r, m, "r"), _vec(z, m, "z"), _stream()))
         return z
 
     def close(self):
@@ -228,8 +255,10 @@ def krylov_solve(method, w, A: Matrix, M: ILU0, b: torch.Tensor, x0: torch.Tenso
     opts = Opts(float(tol_rel), float(tol_abs), int(maxit), int(check_every), flags, 0,
                 hist.data_ptr() if history else None)
     info = Info()
+    m = A.n * A.cp * w
+    pb, px = _vec(b, m, "b"), _vec(x, m, "x0")
     st = lib().mpk_krylov_solve(METHODS[method], w, ctypes.byref(A.desc), M.handle if M is not None else None,
-                                _ptr(b), _ptr(x), ctypes.byref(opts), ctypes.byref(info), _stream())
+                                pb, px, ctypes.byref(opts), ctypes.byref(info), _stream())
     if st not in (0, 1, 2, 5):
         raise MpkError(st, lib().mpk_last_error().decode())
     h = hist[: info.iters + 1].cpu().numpy() if history else None
@@ -251,8 +280,10 @@ def krylov_solve_batched(method, w, A: Matrix, sys_rows, M: ILU0, b: torch.Tenso
     opts = Opts(float(tol_rel), float(tol_abs), int(maxit), int(check_every), FLAG_MP_MATRIX if mp_matrix else 0, 0,
                 hist.data_ptr() if history else None)
     infos = (Info * nsys)()
+    m = A.n * A.cp * w
+    pb, px = _vec(b, m, "b"), _vec(x, m, "x0")
     st = lib().mpk_krylov_solve_batched(METHODS[method], w, ctypes.byref(A.desc), nsys, rows.ctypes.data,
-                                        _ptr(rows_dev), M.handle if M is not None else None, _ptr(b), _ptr(x),
+                                        _ptr(rows_dev), M.handle if M is not None else None, pb, px,
                                         ctypes.byref(opts), infos, _stream())
     if st not in (0, 1, 2, 5):
         raise MpkError(st, lib().mpk_last_error().decode())

@@ -71,3 +71,24 @@ def test_oracle_and_library_share_no_code():
         assert "oracle" not in txt.lower(), f
     otxt = open(os.path.join(ROOT, "oracle", "oracle.c")).read()
     assert "mp.cuh" not in otxt and "mpk.h" not in otxt
+
+
+def test_binding_refuses_host_and_malformed_tensors():
+    """The binding passes raw device pointers: a host tensor, a strided view, a non-tensor or a
+    short or narrower buffer is refused with ValueError before any call reaches the library."""
+    import torch
+
+    from paper_2504_14498_gb300 import _lib
+
+    with pytest.raises(ValueError, match="device memory"):
+        _lib._ptr(torch.zeros(4))
+    with pytest.raises(ValueError, match="torch tensor"):
+        _lib._ptr([0.0, 1.0])
+
+    class FakeA:  # only what spmv_mp reads before marshalling
+        n, cp, desc = 3, 1, None
+
+    with pytest.raises(ValueError, match="device memory"):
+        _lib.spmv_mp(FakeA(), torch.zeros(6, dtype=torch.float64), 2)
+    with pytest.raises(ValueError, match="device memory"):
+        _lib.dot(torch.zeros(6, dtype=torch.float64), torch.zeros(6, dtype=torch.float64), 3, 2)
