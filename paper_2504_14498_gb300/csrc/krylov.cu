@@ -99,7 +99,6 @@ constexpr int ONE = -1;  // coefficient "exactly one"
 // ---- BiCGSTAB (van der Vorst), right-preconditioned, r = b - A x -----------------------------
 struct BiCGSTAB {
   double *r, *rt, *p, *v, *ph, *sv, *sh, *tv;
-  void init(Ctx&) {}
   void iter(Ctx& c) {
     c.dot(rt, r, S_D0);                       // rho = <r~, r>
     c.scalar(PH_RHO);                         // beta = (rho/rho_old)(alpha/omega); 0 at it = 1
@@ -126,7 +125,6 @@ struct BiCGSTAB {
 // ---- CGS (Sonneveld), right-preconditioned ---------------------------------------------------
 struct CGS {
   double *r, *rt, *u, *p, *q, *ph, *v, *uh, *uq, *tmp, *xptr;
-  void init(Ctx&) {}
   void iter(Ctx& c) {
     c.dot(rt, r, S_D0);                       // rho = <r~, r>
     c.scalar(PH_RHO);                         // beta = rho / rho_old; 0 at it = 1
@@ -818,8 +816,6 @@ extern "C" int mpk_solve_host(int method, int w, int prec, int32_t n, int32_t is
   if (st == MPK_OK) st = mpk_krylov_solve(method, w, &A, M, b, x, opts, info, s);
   if (M) mpk_ilu0_destroy(M);
   int fr = info->fail_row;
-  float ms_inner = info->ms_solve;
-  (void)ms_inner;
   MPK_CUDA(cudaMemcpyAsync(x_h, x, vb, cudaMemcpyDeviceToHost, s));
   MPK_CUDA(cudaFreeAsync(buf, s));
   MPK_CUDA(cudaEventRecord(e1, s));
