@@ -27,6 +27,18 @@
  *
  * Arithmetic: see paper_2504_14498_gb300/csrc/mp.cuh (DD: Joldes-Muller-Popescu double-word
  * algorithms; TD/QD: exact evaluation then greedy rounding to w components).
+ *
+ * Environment variables (none changes a result; all choose how the same operations run):
+ *   MPK_SUBST_SCHEDULE=static|owner|cluster8|cluster16  substitution schedule (mpk_ilu0_schedule);
+ *                                                        read at every call; default: tuned.
+ *   MPK_ILU_SCHEDULE=levels|dataflow                     ILU(0) schedule (mpk_ilu0_factor); read
+ *                                                        at every factorisation; default: by the
+ *                                                        width of the levels.
+ *   MPK_RESIDENT_WARPS=k                                 warps per SM of the dependency-driven
+ *                                                        kernels (default 32); read once.
+ *   MPK_NO_GRAPH=1                                       run a solve's iterations as plain
+ *                                                        launches instead of replays of one
+ *                                                        captured CUDA graph; read once.
  */
 #ifndef MPK_H
 #define MPK_H
