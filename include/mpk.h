@@ -218,6 +218,14 @@ int mpk_ilu0_width(const mpk_ilu* M);
  * variable MPK_SUBST_SCHEDULE=static|owner|cluster8|cluster16 selects one instead. */
 int mpk_ilu0_schedule(const mpk_ilu* M, int* wpb_out);
 
+/* Level structure of the factor's triangles (the substitutions of Algorithm 2 and the ILU(0)
+ * kernels run in this order): tri = 0 for L~, 1 for U~.  *nlevels_out (if not NULL) receives the
+ * number of levels; depth_dev (if not NULL: n ints of device memory, the caller's) receives the
+ * level of every row, 0 for a row with no dependency in that triangle, else 1 + the largest level
+ * among the rows it depends on (the columns of its entries left of the diagonal for L~, right of
+ * it for U~), ordered on `stream`.  MPK_INVALID_ARG for a NULL handle or another tri. */
+int mpk_ilu0_levels(const mpk_ilu* M, int tri, int* nlevels_out, int* depth_dev, void* stream);
+
 /* Testing aid for failure detection: the handle's substitutions leave row `row` unpublished
  * (-1: none, the default), so every row that depends on it waits until its bounded wait runs out
  * (about a second), the kernels leave, and the call returns MPK_TIMEOUT.  Nothing faults or

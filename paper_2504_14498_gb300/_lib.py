@@ -60,6 +60,7 @@ SIGNATURES = [
     ("mpk_ilu0_prec", _I, [_VP]),
     ("mpk_ilu0_width", _I, [_VP]),
     ("mpk_ilu0_schedule", _I, [_VP, ctypes.POINTER(_I)]),
+    ("mpk_ilu0_levels", _I, [_VP, _I, ctypes.POINTER(_I), _VP, _VP]),
     ("mpk_ilu0_test_withhold", _I, [_VP, _I]),
     ("mpk_ilu0_destroy", None, [_VP]),
     ("mpk_precond_apply", _I, [_VP, _I, _I, _VP, _VP, _VP]),
@@ -216,6 +217,15 @@ class ILU0:
         wpb = ctypes.c_int(0)
         sc = lib().mpk_ilu0_schedule(self.handle, ctypes.byref(wpb))
         return ("static", "owner", "cluster8", "cluster16")[sc], wpb.value
+
+    def levels(self, tri: int):
+        """(number of levels, level of every row as a device int32 tensor) of L~ (tri 0) or U~
+        (tri 1)."""
+        nl = ctypes.c_int(0)
+        depth = torch.empty(self.A.n, dtype=torch.int32, device="cuda")
+        _check(lib().mpk_ilu0_levels(self.handle, int(tri), ctypes.byref(nl), _ptr(depth, self.A.n, torch.int32,
+                                                                                 "depth"), _stream()))
+        return nl.value, depth
 
     def test_withhold(self, row: int):
         """Testing aid: leave `row` unpublished in the substitutions (-1: none)."""

@@ -1507,6 +1507,17 @@ extern "C" int mpk_ilu0_prec(const mpk_ilu* M) { return M == nullptr ? -2 : M->p
 
 extern "C" int mpk_ilu0_width(const mpk_ilu* M) { return M == nullptr ? -2 : M->wf; }
 
+extern "C" int mpk_ilu0_levels(const mpk_ilu* M, int tri, int* nlevels_out, int* depth_dev, void* stream) {
+  if (M == nullptr || tri < 0 || tri > 1) return fail(MPK_INVALID_ARG, "bad handle or triangle");
+  if (nlevels_out != nullptr) *nlevels_out = M->nlevels[tri];
+  if (depth_dev != nullptr && M->n > 0) {
+    if (M->depth[tri] == nullptr) return fail(MPK_INVALID_ARG, "the handle holds no level record");
+    MPK_CUDA(cudaMemcpyAsync(depth_dev, M->depth[tri], sizeof(int) * (size_t)M->n, cudaMemcpyDeviceToDevice,
+                             (cudaStream_t)stream));
+  }
+  return MPK_OK;
+}
+
 extern "C" int mpk_ilu0_test_withhold(mpk_ilu* M, int row) {
   if (M == nullptr || row < -1 || row >= M->n) return fail(MPK_INVALID_ARG, "bad handle or row");
   M->withhold = row;

@@ -61,6 +61,7 @@ def test_invalid_arguments_rejected_on_host(libmpk):
     h = ctypes.c_void_p()
     assert L.mpk_ilu0_factor(ctypes.byref(d), 0, ctypes.byref(h), None, None) == 6
     assert L.mpk_krylov_solve(7, 2, ctypes.byref(d), None, None, None, None, None, None) == 6
+    assert L.mpk_ilu0_levels(None, 0, None, None, None) == 6
 
 
 def test_oracle_and_library_share_no_code():
