@@ -56,9 +56,10 @@ def lib():
         L.orc_ilu0_mp.restype = _I
         L.orc_precond.argtypes = [_I, _i32p, _i32p, _f64p, _I, _I, _I, _I, _f64p, _f64p]
         L.orc_krylov.argtypes = [_I, _I, _i32p, _i32p, _f64p, _I, _I, _I, ctypes.c_void_p, _f64p, _f64p,
-                                 _D, _D, _I, _I, _f64p, _IP, _DP]
+                                 _D, _D, _I, _I, _f64p, _IP, _DP, _I, ctypes.c_void_p, _IP]
         L.orc_krylov_hooks.argtypes = [_I, _I, _i32p, _i32p, _f64p, _I, _I, _I, ctypes.c_void_p, _f64p, _f64p,
-                                       _D, _D, _I, _I, _f64p, _IP, _DP, ctypes.c_void_p, ctypes.c_void_p]
+                                       _D, _D, _I, _I, _f64p, _IP, _DP, ctypes.c_void_p, ctypes.c_void_p,
+                                       _I, _f64p, _IP]
         L.orc_krylov.restype = _I
         _lib = L
     return _lib
@@ -141,10 +142,16 @@ def precond(A, fac, r, w, prec="fp64", c=1, trans=False):
     return z
 
 
+TRUE_RES_PERIOD = 50  # default period of the true-residual check (0: none)
+
+
 def krylov(method, A, b, w, c=1, ilu="none", fac=None, x0=None, tol_rel=1e-25, tol_abs=0.0, maxit=1000,
-           force_eta0=False, mp_matrix=False, shadow=None, trace=False):
-    """Run one solve; returns dict(status, iters, x, hist, relres_true).
+           force_eta0=False, mp_matrix=False, shadow=None, trace=False, true_res_period=TRUE_RES_PERIOD):
+    """Run one solve; returns dict(status, iters, x, hist, relres_true, hist_true, replacements).
     mp_matrix: every SpMV with the matrix promoted to w components (the rows without "_d").
+    true_res_period: P > 0 recomputes b - A x every P iterations and when the recursive residual
+    passes the stopping test, replacing r when the true norm is above 10x the target (then a
+    passed test is withdrawn); hist_true[k] is that norm at the checked iterations, NaN elsewhere.
     Test hooks: shadow, the initial shadow residual instead of r0; trace, also return "trace"
     (per iteration the normalised inner products that exact arithmetic makes zero)."""
     n, rp, ci, val = A
@@ -163,13 +170,16 @@ def krylov(method, A, b, w, c=1, ilu="none", fac=None, x0=None, tol_rel=1e-25, t
         facp = fac.ctypes.data_as(ctypes.c_void_p)
     sh = None if shadow is None else _c(shadow, np.float64)
     tr = np.zeros(2 * (maxit + 2)) if trace else None
+    htrue = np.full(maxit + 2, np.nan)
+    nrep = ctypes.c_int(0)
     st = lib().orc_krylov_hooks(METHODS[method], n, _c(rp, np.int32), _c(ci, np.int32), _c(val, np.float64), c, w,
                                 ILUS[ilu], facp, _c(b, np.float64), x, float(tol_rel), float(tol_abs), int(maxit),
                                 (1 if force_eta0 else 0) | (2 if mp_matrix else 0), hist, ctypes.byref(it),
                                 ctypes.byref(rr), None if sh is None else sh.ctypes.data_as(ctypes.c_void_p),
-                                None if tr is None else tr.ctypes.data_as(ctypes.c_void_p))
+                                None if tr is None else tr.ctypes.data_as(ctypes.c_void_p), int(true_res_period),
+                                htrue, ctypes.byref(nrep))
     out = {"status": STATUS[st], "iters": it.value, "x": x, "hist": hist[: it.value + 1].copy(),
-           "relres_true": rr.value}
+           "relres_true": rr.value, "hist_true": htrue[: it.value + 1].copy(), "replacements": nrep.value}
     if trace:
         out["trace"] = tr.reshape(-1, 2)[1: it.value + 1].copy()
     return out

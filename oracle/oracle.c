@@ -22,8 +22,8 @@
  *                                             standard right-preconditioned forms (Sonneveld
  *                                             1989; van der Vorst 1992; Zhang 1997)
  *   stopping rule ||r|| < eps_r ||r0|| + eps_a  Algorithm 3 and Sec. 4
- *   inner products <a,b> = sum conj(a_i) b_i  Algorithm 3; the summation order (not given in the
- *                                             paper) is fixed below: leaves of 16, pairwise tree
+ *   inner products <a,b> = sum conj(a_i) b_i  Algorithm 3, summed left to right (the paper gives
+ *                                             no order; this is the plain definition)
  *
  * Arithmetic definitions used here (the paper does not say which variants its library uses):
  *   DD  : Joldes, Muller, Popescu, "Tight and rigorous error bounds for basic building blocks
@@ -449,28 +449,14 @@ void orc_spmv_mm(int n, const int *rp, const int *ci, const double *val, int c, 
   ctx t = {w, c, 1};
   spmv(n, rp, ci, val, t, x, y);
 }
-/* The summation order of an inner product is fixed (the paper leaves it open): the products
- * p_i = conj(a_i) b_i are grouped in leaves of DOT_LEAF consecutive indices, each leaf summed
- * left to right starting from its first product, and the leaf sums s_0..s_{m-1} combined by a
- * stride-doubling pairwise tree: for d = 1, 2, 4, ...: s_j := s_j + s_{j+d} for every j that is
- * a multiple of 2d with j + d < m.  The result is s_0 (0 for n = 0). */
-#define DOT_LEAF 16
+/* Inner product <a,b> = sum_i conj(a_i) b_i (Algorithm 3), accumulated left to right from 0
+ * in the working format: acc := acc + conj(a_i) b_i for i = 0, 1, ..., n-1.  The paper gives
+ * no summation order; this is the plain definition. */
 static num dot(int n, ctx t, const double *a, const double *b) {
-  int s = t.c * t.w, i, j, d, m = (n + DOT_LEAF - 1) / DOT_LEAF;
-  num *leaf, res;
-  if (n <= 0) return n_zero();
-  leaf = (num *)malloc(sizeof(num) * (size_t)m);
-  for (j = 0; j < m; ++j) {
-    int i0 = j * DOT_LEAF, i1 = i0 + DOT_LEAF < n ? i0 + DOT_LEAF : n;
-    num acc = n_mul_conj(n_load(a + (size_t)i0 * s, t), n_load(b + (size_t)i0 * s, t), t);
-    for (i = i0 + 1; i < i1; ++i) acc = n_add(acc, n_mul_conj(n_load(a + (size_t)i * s, t), n_load(b + (size_t)i * s, t), t), t);
-    leaf[j] = acc;
-  }
-  for (d = 1; d < m; d *= 2)
-    for (j = 0; j + d < m; j += 2 * d) leaf[j] = n_add(leaf[j], leaf[j + d], t);
-  res = leaf[0];
-  free(leaf);
-  return res;
+  int s = t.c * t.w, i;
+  num acc = n_zero();
+  for (i = 0; i < n; ++i) acc = n_add(acc, n_mul_conj(n_load(a + (size_t)i * s, t), n_load(b + (size_t)i * s, t), t), t);
+  return acc;
 }
 void orc_dot(int n, int c, int w, const double *a, const double *b, double *out) {
   ctx t = {w, c, 0};
@@ -854,6 +840,15 @@ void orc_precond(int n, const int *rp, const int *ci, const double *fac, int c, 
  * leading components: ||r||_0 < eps_r ||r0||_0 + eps_a.  The shadow residual is r~ = r0.
  * Breakdown: an exactly zero denominator (rho, <r~,v>, <t,t> with t != 0, LS determinant, zeta).
  * hist[k] = leading component of ||r_k||, k = 0..iters.
+ *
+ * Residual replacement (the paper recomputes nothing; this is the periodic true residual that the
+ * stated method adds).  With a period P > 0, after the stopping test of iteration k, whenever k is
+ * a multiple of P or the recursive norm passed the test, the true residual b - A x_k is formed in
+ * the working format exactly as r0 was (SpMV, then b + (-1) * (A x)) and its norm taken.  If that
+ * norm is above 10 (eps_r ||r0|| + eps_a), r is replaced by the true residual and a passed test is
+ * withdrawn (the iteration goes on from the replaced r); otherwise nothing changes and a passed
+ * test stands.  hist_true[k] (if given) receives the leading component of ||b - A x_k|| at every
+ * such check; *nrep counts the replacements.  P = 0: no check, the test on the recursive r alone.
  * ---------------------------------------------------------------------------------------- */
 enum { M_BICG = 0, M_CGS = 1, M_BICGSTAB = 2, M_GPBICG = 3 };
 
@@ -878,6 +873,27 @@ static void vaxpy(const sys_t *S, double *y, const double *a, num alpha, const d
 }
 static int nan_mp(mp a) { return a.c[0] != a.c[0]; }
 
+/* The stopping decision of iteration it with the residual replacement described above; returns
+ * 1 when the solve stops with OK.  rtrue: scratch vector. */
+typedef struct { int period; double *hist_true; int nrep; } repl_t;
+static int stop_check(const sys_t *S, repl_t *R, const double *b, const double *x, double *r, double *rtrue,
+                      double nrec, double tol, int it) {
+  int cand = nrec < tol;
+  mp nt;
+  if (R->period <= 0) return cand;
+  if (!cand && it % R->period != 0) return 0;
+  spmv(S->n, S->rp, S->ci, S->val, S->t, x, rtrue);
+  vaxpy(S, rtrue, b, n_neg((num){mp_from_d(1.0), mp_zero()}), rtrue); /* b - A x */
+  nt = nrm2(S->n, S->t, rtrue);
+  if (R->hist_true) R->hist_true[it] = nt.c[0];
+  if (nt.c[0] > 10.0 * tol) {
+    vcopy(S, r, rtrue);
+    R->nrep++;
+    return 0;
+  }
+  return cand;
+}
+
 /* Test hooks (set by orc_krylov_hooks around one call, NULL otherwise):
  *   g_shadow: the initial shadow residual r~0 instead of r0 (n*c*w doubles);
  *   g_trace:  per iteration k (1-based), the moduli of normalised inner products that exact
@@ -896,16 +912,19 @@ static double ortho(int n, ctx t, const double *a, const double *b) {
 
 int orc_krylov(int method, int n, const int *rp, const int *ci, const double *val, int c, int w, int ilu,
                const double *fac, const double *b, double *x, double tol_rel, double tol_abs, int maxit, int flags,
-               double *hist, int *iters_out, double *relres_true) {
+               double *hist, int *iters_out, double *relres_true, int true_res_period, double *hist_true,
+               int *nrep_out) {
   sys_t S;
+  repl_t R;
   ctx t = {w, c, (flags >> 1) & 1}; /* flags bit 1: every SpMV with the matrix promoted to MP */
   int s = c * w, it = 0, st = ORC_MAXIT, i;
   double r0n, tol;
-  double *r, *rt, *tmp;
+  double *r, *rt, *tmp, *rtrue;
   mp nr;
   memset(&S, 0, sizeof(S));
   S.n = n; S.rp = rp; S.ci = ci; S.val = val; S.t = t; S.ilu = ilu; S.fac = fac;
-  r = vnew(&S); rt = vnew(&S); tmp = vnew(&S);
+  R.period = true_res_period; R.hist_true = hist_true; R.nrep = 0;
+  r = vnew(&S); rt = vnew(&S); tmp = vnew(&S); rtrue = vnew(&S);
   spmv(n, rp, ci, val, t, x, tmp);
   vaxpy(&S, r, b, n_neg((num){mp_from_d(1.0), mp_zero()}), tmp); /* r = b - A x */
   if (g_shadow) vcopy(&S, rt, g_shadow);
@@ -937,7 +956,7 @@ int orc_krylov(int method, int n, const int *rp, const int *ci, const double *va
       nr = nrm2(n, t, r);
       if (hist) hist[it] = nr.c[0];
       if (nan_mp(nr)) { st = ORC_NAN; break; }
-      if (nr.c[0] < tol) { st = ORC_OK; break; }
+      if (stop_check(&S, &R, b, x, r, rtrue, nr.c[0], tol, it)) { st = ORC_OK; break; }
       apply_m(&S, 0, r, z);
       apply_m(&S, 1, rt, zt);
       rhon = dot(n, t, zt, r);
@@ -974,7 +993,7 @@ int orc_krylov(int method, int n, const int *rp, const int *ci, const double *va
       nr = nrm2(n, t, r);
       if (hist) hist[it] = nr.c[0];
       if (nan_mp(nr)) { st = ORC_NAN; break; }
-      if (nr.c[0] < tol) { st = ORC_OK; break; }
+      if (stop_check(&S, &R, b, x, r, rtrue, nr.c[0], tol, it)) { st = ORC_OK; break; }
       rho_old = rho;
     }
     free(u); free(p); free(q); free(ph); free(v); free(uh); free(uq);
@@ -1008,7 +1027,7 @@ int orc_krylov(int method, int n, const int *rp, const int *ci, const double *va
       nr = nrm2(n, t, r);
       if (hist) hist[it] = nr.c[0];
       if (nan_mp(nr)) { st = ORC_NAN; break; }
-      if (nr.c[0] < tol) { st = ORC_OK; break; }
+      if (stop_check(&S, &R, b, x, r, rtrue, nr.c[0], tol, it)) { st = ORC_OK; break; }
       if (n_is_zero(omega)) { st = ORC_BREAKDOWN; break; }
       rho_old = rho;
     }
@@ -1083,7 +1102,7 @@ int orc_krylov(int method, int n, const int *rp, const int *ci, const double *va
       nr = nrm2(n, t, r);
       if (hist) hist[it] = nr.c[0];
       if (nan_mp(nr)) { st = ORC_NAN; break; }
-      if (nr.c[0] < tol) { st = ORC_OK; break; }
+      if (stop_check(&S, &R, b, x, r, rtrue, nr.c[0], tol, it)) { st = ORC_OK; break; }
       if (n_is_zero(zeta)) { st = ORC_BREAKDOWN; break; }
       rhon = dot(n, t, rt, r);
       beta = n_mul(n_div(alpha, zeta, t), n_div(rhon, rho, t), t);
@@ -1105,8 +1124,9 @@ finish:
     vaxpy(&S, tmp, b, n_neg((num){mp_from_d(1.0), mp_zero()}), tmp);
     *relres_true = r0n > 0.0 ? nrm2(n, t, tmp).c[0] / r0n : 0.0;
   }
+  if (nrep_out) *nrep_out = R.nrep;
   if (S.have_ah) csr_free(&S.ah);
-  free(r); free(rt); free(tmp);
+  free(r); free(rt); free(tmp); free(rtrue);
   return st;
 }
 
@@ -1114,12 +1134,12 @@ finish:
 int orc_krylov_hooks(int method, int n, const int *rp, const int *ci, const double *val, int c, int w, int ilu,
                      const double *fac, const double *b, double *x, double tol_rel, double tol_abs, int maxit,
                      int flags, double *hist, int *iters_out, double *relres_true, const double *shadow,
-                     double *trace) {
+                     double *trace, int true_res_period, double *hist_true, int *nrep_out) {
   int st;
   g_shadow = shadow;
   g_trace = trace;
   st = orc_krylov(method, n, rp, ci, val, c, w, ilu, fac, b, x, tol_rel, tol_abs, maxit, flags, hist, iters_out,
-                  relres_true);
+                  relres_true, true_res_period, hist_true, nrep_out);
   g_shadow = NULL;
   g_trace = NULL;
   return st;
