@@ -111,9 +111,18 @@ typedef struct {
   int32_t maxit;           /* iteration limit (Sec. 4 uses 3n)                                  */
   int32_t check_every;     /* iterations queued between host checks of the device "done" flag */
   int32_t flags;           /* MPK_FLAG_* bits                                                   */
-  int32_t reserved;
+  int32_t true_res_period; /* P > 0: residual replacement.  After the stopping test of iteration
+                              k, whenever k is a multiple of P or the recursive ||r_k|| passed the
+                              test, the true residual b - A x_k is formed in the vector format
+                              (the SpMV of r0) and its norm taken; above 10 (eps_r ||r0|| + eps_a)
+                              it replaces r and a passed test is withdrawn (the iteration goes
+                              on), else a passed test stands.  0: the test reads the recursive r
+                              alone and b - A x is formed once, after the last iteration        */
   double* hist_dev;        /* nullable device array of maxit+1 doubles: leading component of
                               ||r_k||_2, k = 0..iters                                            */
+  double* hist_true_dev;   /* nullable device array of maxit+1 doubles: leading component of
+                              ||b - A x_k||_2 at every iteration k checked by the replacement
+                              rule (entries of unchecked iterations are left as they were)      */
 } mpk_opts;
 
 typedef struct {
@@ -127,6 +136,7 @@ typedef struct {
   float ms_solve;          /* device time of the solve (CUDA events on `stream`)                */
   int32_t hermitian;       /* BiCG: 1 if A was found equal to A^H (entries compared as numbers),
                               so that q~ = A^H p~ used A's own rows and no transpose was built     */
+  int32_t replacements;    /* residual replacements performed (see true_res_period)              */
 } mpk_info;
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -259,7 +269,8 @@ int mpk_krylov_solve(int method, int w, const mpk_csr* A, const mpk_ilu* M, cons
  *      side is scaled by its own power of two.
  *   sys_rows_host, sys_rows_dev: the same nsys+1 increasing row offsets (0 .. n) on host and device.
  *   b_dev, x_dev: n*c*w doubles (x0 in, iterates out).  infos: HOST array of nsys records.
- *   opts->hist_dev (nullable): nsys*(maxit+1) doubles, system s's history at s*(maxit+1).
+ *   opts->hist_dev, opts->hist_true_dev (nullable): nsys*(maxit+1) doubles each, system s's
+ *   history at s*(maxit+1).  The replacement rule (true_res_period) applies per system.
  * Returns MPK_OK when every system converged, else the first non-OK system status (or an error
  * code of the call itself).  The call synchronises `stream`. */
 int mpk_krylov_solve_batched(int method, int w, const mpk_csr* A, int nsys, const int32_t* sys_rows_host,

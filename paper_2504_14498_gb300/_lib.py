@@ -32,14 +32,15 @@ class CsrDesc(ctypes.Structure):
 
 class Opts(ctypes.Structure):
     _fields_ = [("tol_rel", ctypes.c_double), ("tol_abs", ctypes.c_double), ("maxit", ctypes.c_int32),
-                ("check_every", ctypes.c_int32), ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("hist_dev", ctypes.c_void_p)]
+                ("check_every", ctypes.c_int32), ("flags", ctypes.c_int32), ("true_res_period", ctypes.c_int32),
+                ("hist_dev", ctypes.c_void_p), ("hist_true_dev", ctypes.c_void_p)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("fail_row", ctypes.c_int32),
                 ("graph", ctypes.c_int32), ("res0", ctypes.c_double), ("relres_rec", ctypes.c_double),
-                ("relres_true", ctypes.c_double), ("ms_solve", ctypes.c_float), ("hermitian", ctypes.c_int32)]
+                ("relres_true", ctypes.c_double), ("ms_solve", ctypes.c_float), ("hermitian", ctypes.c_int32),
+                ("replacements", ctypes.c_int32)]
 
 
 _lib = None
@@ -255,15 +256,22 @@ class ILU0:
             pass
 
 
+TRUE_RES_PERIOD = 50  # default period of the true-residual check (mpk_opts.true_res_period)
+
+
 def krylov_solve(method, w, A: Matrix, M: ILU0, b: torch.Tensor, x0: torch.Tensor = None, tol_rel=1e-25,
-                 tol_abs=0.0, maxit=1000, check_every=25, history=True, force_eta0=False, mp_matrix=False):
-    """Solve A x = b; returns dict(status, iters, x, hist, res0, relres_rec, relres_true, ms, graph,
-    hermitian).  mp_matrix: every SpMV with A's entries promoted to w components."""
+                 tol_abs=0.0, maxit=1000, check_every=25, history=True, force_eta0=False, mp_matrix=False,
+                 true_res_period=TRUE_RES_PERIOD):
+    """Solve A x = b; returns dict(status, iters, x, hist, hist_true, replacements, res0, relres_rec,
+    relres_true, ms, graph, hermitian).  mp_matrix: every SpMV with A's entries promoted to w
+    components.  true_res_period: residual replacement period (0: off); hist_true holds
+    ||b - A x_k|| at the checked iterations and NaN elsewhere."""
     x = torch.zeros_like(b) if x0 is None else x0.clone()
     hist = torch.full((maxit + 1,), float("nan"), dtype=torch.float64, device=b.device) if history else None
+    htrue = torch.full((maxit + 1,), float("nan"), dtype=torch.float64, device=b.device) if history else None
     flags = (FLAG_ETA0 if force_eta0 else 0) | (FLAG_MP_MATRIX if mp_matrix else 0)
-    opts = Opts(float(tol_rel), float(tol_abs), int(maxit), int(check_every), flags, 0,
-                hist.data_ptr() if history else None)
+    opts = Opts(float(tol_rel), float(tol_abs), int(maxit), int(check_every), flags, int(true_res_period),
+                hist.data_ptr() if history else None, htrue.data_ptr() if history else None)
     info = Info()
     m = A.n * A.cp * w
     pb, px = _vec(b, m, "b"), _vec(x, m, "x0")
@@ -272,23 +280,27 @@ def krylov_solve(method, w, A: Matrix, M: ILU0, b: torch.Tensor, x0: torch.Tenso
     if st not in (0, 1, 2, 5):
         raise MpkError(st, lib().mpk_last_error().decode())
     h = hist[: info.iters + 1].cpu().numpy() if history else None
-    return {"status": STATUS[info.status], "iters": info.iters, "x": x, "hist": h, "res0": info.res0,
-            "relres_rec": info.relres_rec, "relres_true": info.relres_true, "ms": info.ms_solve,
-            "graph": bool(info.graph), "hermitian": bool(info.hermitian)}
+    ht = htrue[: info.iters + 1].cpu().numpy() if history else None
+    return {"status": STATUS[info.status], "iters": info.iters, "x": x, "hist": h, "hist_true": ht,
+            "replacements": info.replacements, "res0": info.res0, "relres_rec": info.relres_rec,
+            "relres_true": info.relres_true, "ms": info.ms_solve, "graph": bool(info.graph),
+            "hermitian": bool(info.hermitian)}
 
 
 def krylov_solve_batched(method, w, A: Matrix, sys_rows, M: ILU0, b: torch.Tensor, x0: torch.Tensor = None,
-                         tol_rel=1e-25, tol_abs=0.0, maxit=1000, check_every=25, history=False, mp_matrix=False):
+                         tol_rel=1e-25, tol_abs=0.0, maxit=1000, check_every=25, history=False, mp_matrix=False,
+                         true_res_period=TRUE_RES_PERIOD):
     """Solve the nsys independent systems of the block-diagonal A (system s: rows sys_rows[s] ..
     sys_rows[s+1]-1) together; returns dict(status, x, per-system arrays: statuses, iters, res0,
-    relres_rec, relres_true, and hist (nsys x (maxit+1)) when asked)."""
+    relres_rec, relres_true, replacements, and hist, hist_true (nsys x (maxit+1)) when asked)."""
     rows = np.ascontiguousarray(np.asarray(sys_rows, dtype=np.int32))
     nsys = len(rows) - 1
     rows_dev = torch.as_tensor(rows, device=b.device)
     x = torch.zeros_like(b) if x0 is None else x0.clone()
     hist = torch.full((nsys, maxit + 1), float("nan"), dtype=torch.float64, device=b.device) if history else None
-    opts = Opts(float(tol_rel), float(tol_abs), int(maxit), int(check_every), FLAG_MP_MATRIX if mp_matrix else 0, 0,
-                hist.data_ptr() if history else None)
+    htrue = torch.full((nsys, maxit + 1), float("nan"), dtype=torch.float64, device=b.device) if history else None
+    opts = Opts(float(tol_rel), float(tol_abs), int(maxit), int(check_every), FLAG_MP_MATRIX if mp_matrix else 0,
+                int(true_res_period), hist.data_ptr() if history else None, htrue.data_ptr() if history else None)
     infos = (Info * nsys)()
     m = A.n * A.cp * w
     pb, px = _vec(b, m, "b"), _vec(x, m, "x0")
@@ -302,15 +314,17 @@ def krylov_solve_batched(method, w, A: Matrix, sys_rows, M: ILU0, b: torch.Tenso
            "iters": np.array([i.iters for i in infos]), "res0": np.array([i.res0 for i in infos]),
            "relres_rec": np.array([i.relres_rec for i in infos]),
            "relres_true": np.array([i.relres_true for i in infos]), "ms": infos[0].ms_solve,
-           "graph": bool(infos[0].graph)}
+           "replacements": np.array([i.replacements for i in infos]), "graph": bool(infos[0].graph)}
     if history:
         h = hist.cpu().numpy()
         out["hist"] = [h[s_, : out["iters"][s_] + 1] for s_ in range(nsys)]
+        ht = htrue.cpu().numpy()
+        out["hist_true"] = [ht[s_, : out["iters"][s_] + 1] for s_ in range(nsys)]
     return out
 
 
 def solve_host(method, w, prec, A_tuple, b: np.ndarray, x0: np.ndarray = None, is_complex=False, tol_rel=1e-25,
-               tol_abs=0.0, maxit=1000, check_every=25):
+               tol_abs=0.0, maxit=1000, check_every=25, true_res_period=TRUE_RES_PERIOD):
     """End to end from host arrays: H2D copies, ILU(0), solve, D2H of x inside one C call."""
     n, rp, ci, val = A_tuple
     rp = np.ascontiguousarray(rp, dtype=np.int32)
@@ -318,11 +332,11 @@ def solve_host(method, w, prec, A_tuple, b: np.ndarray, x0: np.ndarray = None, i
     val = np.ascontiguousarray(val, dtype=np.float64)
     b = np.ascontiguousarray(b, dtype=np.float64)
     x = np.zeros_like(b) if x0 is None else np.ascontiguousarray(x0, dtype=np.float64).copy()
-    opts = Opts(float(tol_rel), float(tol_abs), int(maxit), int(check_every), 0, 0, None)
+    opts = Opts(float(tol_rel), float(tol_abs), int(maxit), int(check_every), 0, int(true_res_period), None, None)
     info = Info()
     st = lib().mpk_solve_host(METHODS[method], w, ILUS[prec], n, int(is_complex), rp.ctypes.data, ci.ctypes.data,
                               val.ctypes.data, b.ctypes.data, x.ctypes.data, ctypes.byref(opts), ctypes.byref(info))
     if st not in (0, 1, 2, 5):
         raise MpkError(st, lib().mpk_last_error().decode())
     return {"status": STATUS[info.status], "iters": info.iters, "x": x, "relres_true": info.relres_true,
-            "ms": info.ms_solve}
+            "replacements": info.replacements, "ms": info.ms_solve}

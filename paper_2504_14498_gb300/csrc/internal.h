@@ -41,7 +41,15 @@ enum Slot : int {
 };
 constexpr int kSlotDoubles = 8;
 // Integer state of a solve on the device.
-enum StateIdx : int { ST_DONE = 0, ST_STATUS, ST_ITERS, ST_IT, ST_MAXIT, ST_FLAGS, ST_COUNT };
+// ST_PERIOD: the replacement period (0: off).  ST_NOCHK / ST_NOREPL: 0 while the true-residual
+// check / the replacement copy of the current iteration is to run (the gates of those launches),
+// else 1.  ST_CHECK: 1 periodic check, 2 the recursive norm passed the test; ST_CHK_IT: the
+// iteration checked; ST_NREP: replacements so far.
+enum StateIdx : int {
+  ST_DONE = 0, ST_STATUS, ST_ITERS, ST_IT, ST_MAXIT, ST_FLAGS,
+  ST_PERIOD, ST_NOCHK, ST_NOREPL, ST_CHECK, ST_CHK_IT, ST_NREP,
+  ST_COUNT
+};
 
 // Phases of the single-thread scalar kernel.
 enum Phase : int {
@@ -53,7 +61,8 @@ enum Phase : int {
   PH_NORM,        // after ||r||^2 in S_D0: history, convergence, breakdown checks
   PH_BETA,        // BiCG / GPBiCG: after the new rho in S_D0
   PH_STORE_RHO,   // store S_D0 as rho (BiCG / GPBiCG initialisation)
-  PH_TRUE         // ||b - A x|| from S_D5 (final true residual)
+  PH_TRUE,        // ||b - A x|| from S_D5 (final true residual)
+  PH_TRUECHK      // replacement rule: ||b - A x_k||^2 in S_D5 (true_res_period)
 };
 
 struct DotWs {           // workspace of the fixed-order reduction
@@ -89,6 +98,7 @@ struct Batch {
   const int* bsys = nullptr;         // inner-product block -> system
   int nblocks = 0;                   // boff[nsys]
   const int* st = nullptr;           // per-system state (nullptr: skip no system)
+  int gate = -1;                     // >= 0: also skip systems whose st[gate] is nonzero
   unsigned long long* absmax = nullptr;  // nsys scale accumulators of the binary32 substitutions
 };
 

@@ -53,7 +53,8 @@ __device__ __forceinline__ N<W, CP> warp_sum(N<W, CP> a) {  // fixed tree order
 // ---------------------------------------------------------------------------------------------
 // y = A x  (b != nullptr: y = b - A x), one thread per row, CSR order from 0.
 // ---------------------------------------------------------------------------------------------
-// A batch (sysid != nullptr) skips the rows of systems whose state sst has ST_DONE set.
+// A batch (sysid != nullptr) skips the rows of systems whose state sst has ST_DONE set, or, with
+// gate >= 0, a nonzero sst[gate].
 // MM: the matrix entry is promoted to a W-component number (a, 0, ..., 0), same value, and the
 // product is the format's full multiplication with the matrix entry first (the paper's rows
 // without "_d", whose matrices are held in the vectors' type).
@@ -62,14 +63,18 @@ __global__ void __launch_bounds__(kBlock) k_spmv(int n, const int* __restrict__ 
                                                  const double* __restrict__ val, const double* __restrict__ x,
                                                  double* __restrict__ y, const double* __restrict__ b,
                                                  const int* __restrict__ done, const int* __restrict__ sysid,
-                                                 const int* __restrict__ sst, const int* __restrict__ order) {
+                                                 const int* __restrict__ sst, const int* __restrict__ order,
+                                                 int gate) {
   if (is_done(done)) return;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   // order (nullable): rows grouped by length so that the lanes of a warp do equal work (every
   // binary64 warp instruction costs its full pipe time however many lanes are active)
   const int i = order != nullptr ? order[t] : t;
-  if (sysid != nullptr && sst != nullptr && sst[sysid[i] * ST_COUNT + ST_DONE] != 0) return;
+  if (sysid != nullptr && sst != nullptr) {
+    const int* q = sst + sysid[i] * ST_COUNT;
+    if (q[ST_DONE] != 0 || (gate >= 0 && q[gate] != 0)) return;
+  }
   N<W, CP> acc = n_zero<W, CP>();
   const int p1 = rp[i + 1];
   for (int p = rp[i]; p < p1; ++p) {
@@ -213,7 +218,9 @@ __global__ void __launch_bounds__(kBlock) k_dots_seg(Batch bt, DotArgs<K> args, 
                                                      const int* __restrict__ done) {
   if (is_done(done)) return;
   const int sy = bt.bsys[blockIdx.x];
-  if (bt.st != nullptr && bt.st[sy * ST_COUNT + ST_DONE] != 0) return;
+  if (bt.st != nullptr &&
+      (bt.st[sy * ST_COUNT + ST_DONE] != 0 || (bt.gate >= 0 && bt.st[sy * ST_COUNT + bt.gate] != 0)))
+    return;
   const int r0 = bt.roff[sy], n = bt.roff[sy + 1] - r0;
   const int b0 = bt.boff[sy], G = bt.boff[sy + 1] - b0;
   const double* a[K];
@@ -239,16 +246,18 @@ struct LinArgs {
   const int* copy_at_first;  // non-null: at iteration 1 (st[ST_IT] == 1) y = v[0] instead
 };
 // Batch (sysid != nullptr): coefficients of system s at a.s[k] + s * kSysDoubles, its iteration
-// counter in sst, and the rows of finished systems left untouched.
+// counter in sst, and the rows of finished systems (or, gate >= 0, of systems whose sst[gate] is
+// nonzero) left untouched.
 template <int W, int CP>
 __global__ void __launch_bounds__(kBlock) k_lincomb(int n, LinArgs a, const int* __restrict__ done,
-                                                    const int* __restrict__ sysid, const int* __restrict__ sst) {
+                                                    const int* __restrict__ sysid, const int* __restrict__ sst,
+                                                    int gate) {
   if (is_done(done)) return;
   if (sysid != nullptr) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
       const int sy = sysid[i];
       const int* st = sst + sy * ST_COUNT;
-      if (st[ST_DONE] != 0) continue;
+      if (st[ST_DONE] != 0 || (gate >= 0 && st[gate] != 0)) continue;
       if (a.copy_at_first != nullptr && st[ST_IT] == 1) {
         n_store<W, CP>(a.y, i, n_load<W, CP>(a.v[0], i));
         continue;
@@ -410,6 +419,21 @@ __device__ __forceinline__ void next_iter(int* st) {
   st[ST_IT] = it;
   if (it > st[ST_MAXIT]) finish(st, MPK_MAXIT, st[ST_MAXIT]);
 }
+// What follows a stopping test that did not stop iteration `it`: BiCGSTAB's omega = 0 and
+// GPBiCG's zeta = 0 breakdowns, rho_old, and (BiCGSTAB, CGS) the next iteration.
+template <int W, int CP>
+__device__ __forceinline__ void after_norm(int method, double* __restrict__ S, int* __restrict__ st, int it) {
+  if (method == MPK_BICGSTAB) {
+    if (n_is_zero<W, CP>(n_load<W, CP>(S + S_OMEGA * kSlotDoubles, 0))) { finish(st, MPK_BREAKDOWN, it); return; }
+    n_store<W, CP>(S + S_RHO_OLD * kSlotDoubles, 0, n_load<W, CP>(S + S_RHO * kSlotDoubles, 0));
+    next_iter(st);
+  } else if (method == MPK_CGS) {
+    n_store<W, CP>(S + S_RHO_OLD * kSlotDoubles, 0, n_load<W, CP>(S + S_RHO * kSlotDoubles, 0));
+    next_iter(st);
+  } else if (method == MPK_GPBICG) {
+    if (n_is_zero<W, CP>(n_load<W, CP>(S + S_ZETA * kSlotDoubles, 0))) finish(st, MPK_BREAKDOWN, it);
+  }
+}
 
 // One thread per system: system sy uses S + sy * kSysDoubles, st + sy * ST_COUNT and
 // hist + sy * hist_stride.  With done != nullptr a finished system is skipped; when a system
@@ -531,17 +555,39 @@ __device__ void scalar_phase(int method, int phase, double* __restrict__ S, int*
       nn.re = nr;
       set_slot<W, CP>(S, S_NORM, nn);
       if (hist) hist[it] = nr.c[0];
+      st[ST_NOCHK] = 1;
+      st[ST_NOREPL] = 1;
       if (nr.c[0] != nr.c[0]) { finish(st, MPK_NAN, it); break; }
-      if (nr.c[0] < S[S_TOL * kSlotDoubles]) { finish(st, MPK_OK, it); break; }
-      if (method == MPK_BICGSTAB) {
-        if (n_is_zero<W, CP>(slot<W, CP>(S, S_OMEGA))) { finish(st, MPK_BREAKDOWN, it); break; }
-        set_slot<W, CP>(S, S_RHO_OLD, slot<W, CP>(S, S_RHO));
-        next_iter(st);
-      } else if (method == MPK_CGS) {
-        set_slot<W, CP>(S, S_RHO_OLD, slot<W, CP>(S, S_RHO));
-        next_iter(st);
-      } else if (method == MPK_GPBICG) {
-        if (n_is_zero<W, CP>(slot<W, CP>(S, S_ZETA))) { finish(st, MPK_BREAKDOWN, it); break; }
+      const int period = st[ST_PERIOD];
+      if (nr.c[0] < S[S_TOL * kSlotDoubles]) {
+        if (period <= 0) { finish(st, MPK_OK, it); break; }
+        st[ST_CHECK] = 2;  // the test passed: it stands only if the true residual agrees
+        st[ST_CHK_IT] = it;
+        st[ST_NOCHK] = 0;
+        break;
+      }
+      if (period > 0 && it % period == 0) {
+        st[ST_CHECK] = 1;
+        st[ST_CHK_IT] = it;
+        st[ST_NOCHK] = 0;
+      }
+      after_norm<W, CP>(method, S, st, it);
+      break;
+    }
+    case PH_TRUECHK: {  // ||b - A x_k||^2 in S_D5; hist: the true-residual history
+      if (st[ST_NOCHK] != 0) break;
+      st[ST_NOCHK] = 1;
+      const int k = st[ST_CHK_IT];
+      const bool passed = st[ST_CHECK] == 2;
+      st[ST_CHECK] = 0;
+      R<W> nt = rsqrt_mp<W>(slot<W, CP>(S, S_D5).re);
+      if (hist) hist[k] = nt.c[0];
+      if (nt.c[0] > 10.0 * S[S_TOL * kSlotDoubles]) {
+        st[ST_NOREPL] = 0;  // r := b - A x_k (the launch after this one)
+        st[ST_NREP] += 1;
+        if (passed) after_norm<W, CP>(method, S, st, k);
+      } else if (passed) {
+        finish(st, MPK_OK, k);
       }
       break;
     }
@@ -1748,7 +1794,7 @@ struct Launch {
     count_launch();
     auto fn = A.mm ? k_spmv<W, CP, true> : k_spmv<W, CP, false>;
     fn<<<(A.n + kBlock - 1) / kBlock, kBlock, 0, s>>>(A.n, A.rp, A.ci, A.val, x, y, b, done, bt ? bt->sysid : nullptr,
-                                                       bt ? bt->st : nullptr, A.order);
+                                                       bt ? bt->st : nullptr, A.order, bt ? bt->gate : -1);
   }
   template <int K>
   static void dotsK(int n, const double* const* a, const double* const* b, double* const* out, const DotWs& ws,
@@ -1797,7 +1843,8 @@ struct Launch {
       a.s[k] = k < nt ? coef[k] : nullptr;
     }
     count_launch();
-    k_lincomb<W, CP><<<grid_for(n), kBlock, 0, s>>>(n, a, done, bt ? bt->sysid : nullptr, bt ? bt->st : nullptr);
+    k_lincomb<W, CP><<<grid_for(n), kBlock, 0, s>>>(n, a, done, bt ? bt->sysid : nullptr, bt ? bt->st : nullptr,
+                                                     bt ? bt->gate : -1);
   }
   static void nested(int n, double* y, const double* v0, const double* v1, const double* v2, const double* s1,
                      const double* s2, const int* copy_at_first, const int* done, const Batch* bt, cudaStream_t s) {

@@ -48,6 +48,13 @@ struct Ctx {
   int* fin = nullptr;
   int* alldone = nullptr;
   int err = MPK_OK;
+  // residual replacement (true_res_period > 0): b, the iterate, scratch for b - A x, the
+  // true-residual history
+  int period = 0;
+  const double* b = nullptr;
+  double* x = nullptr;
+  double* rtrue = nullptr;
+  double* hist_true = nullptr;
 
   int nsys() const { return bt ? bt->nsys : 1; }
   double* slot(int k) const { return S + k * kSlotDoubles; }
@@ -83,6 +90,32 @@ struct Ctx {
     o->nested(n, y, v0, v1, v2, slot(s1), slot(s2), copy_at_first ? st : nullptr, done, bt, s);
   }
   void scalar(int phase) { o->scalar(method, phase, S, st, hist, done, nsys(), hist_stride, fin, alldone, s); }
+  // The replacement rule after PH_NORM: when the iteration is checked (a multiple of the period,
+  // or the recursive norm passed the test), rtrue = b - A x and its norm decide whether r becomes
+  // rtrue.  The launches are gated on the state words ST_NOCHK / ST_NOREPL (per system in a batch).
+  void truechk(double* r) {
+    if (period <= 0) return;
+    const double* av[1] = {rtrue};
+    if (bt) {
+      Batch g = *bt;
+      g.gate = ST_NOCHK;
+      o->spmv(A, x, rtrue, b, done, &g, s);
+      o->dots_seg(g, 1, av, av, S, S_D5, seg_partial, seg_counters, done, s);
+      o->scalar(method, PH_TRUECHK, S, st, hist_true, done, nsys(), hist_stride, fin, alldone, s);
+      Batch gr = *bt;
+      gr.gate = ST_NOREPL;
+      const double* coef[1] = {nullptr};
+      const double* v[1] = {rtrue};
+      o->lincomb(n, r, 1, coef, v, nullptr, done, &gr, s);
+      return;
+    }
+    const int* g1 = st + ST_NOCHK;
+    o->spmv(A, x, rtrue, b, g1, nullptr, s);
+    double* ov[1] = {slot(S_D5)};
+    o->dots(n, 1, av, av, ov, dws, g1, s);
+    o->scalar(method, PH_TRUECHK, S, st, hist_true, g1, 1, hist_stride, nullptr, nullptr, s);
+    o->copy(n, r, rtrue, st + ST_NOREPL, s);
+  }
   void mv(const double* x, double* y) { o->spmv(A, x, y, nullptr, done, bt, s); }
   void mvh(const double* x, double* y) { o->spmv(AH, x, y, nullptr, done, bt, s); }
   void prec(bool trans, const double* r, double* z) {
@@ -118,6 +151,7 @@ struct BiCGSTAB {
     c.lin(r, ONE, sv, S_NOMEGA, tv);          // r = s + (-omega) t
     c.dot(r, r, S_D0);
     c.scalar(PH_NORM);                        // ||r||, stopping rule, omega = 0 breakdown
+    c.truechk(r);                             // replacement rule (true_res_period)
   }
   double* xptr;
 };
@@ -142,6 +176,7 @@ struct CGS {
     c.lin(r, ONE, r, S_NALPHA, tmp);          // r = r + (-alpha) A u^
     c.dot(r, r, S_D0);
     c.scalar(PH_NORM);
+    c.truechk(r);                             // replacement rule (true_res_period)
   }
 };
 
@@ -166,6 +201,7 @@ struct BiCG {
     c.lin(rt, ONE, rt, S_NCALPHA, qt);        // r~ = r~ + (-conj(alpha)) q~
     c.dot(r, r, S_D0);
     c.scalar(PH_NORM);
+    c.truechk(r);                             // replacement rule (true_res_period)
     c.prec(false, r, z);
     c.prec(true, rt, zt);
     c.dot(zt, r, S_D0);                       // rho_new = <z~, r>
@@ -205,6 +241,7 @@ struct GPBiCG {
     c.lin(r, ONE, tv, S_NETA, y, S_NZETA, cv);       // r = (t + (-eta) y) + (-zeta) c
     c.dot(r, r, S_D0);
     c.scalar(PH_NORM);
+    c.truechk(r);                             // replacement rule (true_res_period)
     c.dot(rt, r, S_D0);
     c.scalar(PH_BETA);                        // beta = (alpha/zeta) <r~,r_new>/<r~,r>
     c.lin(wv, ONE, cv, S_BETA, q);            // w = c + beta q
@@ -566,6 +603,12 @@ static int solve_impl(int method, int w, const mpk_csr* Ac, const mpk_ilu* Mc, c
       q[ST_IT] = 0;
       q[ST_MAXIT] = maxit;
       q[ST_FLAGS] = opts->flags;
+      q[ST_PERIOD] = opts->true_res_period > 0 ? opts->true_res_period : 0;
+      q[ST_NOCHK] = 1;
+      q[ST_NOREPL] = 1;
+      q[ST_CHECK] = 0;
+      q[ST_CHK_IT] = 0;
+      q[ST_NREP] = 0;
     }
     MPK_CUDA(cudaMemcpyAsync(c.st, st_init.data(), sizeof(int) * st_init.size(), cudaMemcpyHostToDevice, s));
     std::vector<double> tolv((size_t)2 * nsys);
@@ -591,6 +634,11 @@ static int solve_impl(int method, int w, const mpk_csr* Ac, const mpk_ilu* Mc, c
 
   double* r = V[0];
   double* rt = V[1];
+  c.period = opts->true_res_period > 0 ? opts->true_res_period : 0;
+  c.b = b;
+  c.x = x;
+  c.rtrue = V[16];  // free during the iterations (tuner scratch before, final residual after)
+  c.hist_true = opts->hist_true_dev;
   // r = b - A x0, r~ = r, ||r0||
   o->spmv(c.A, x, r, b, c.done, nullptr, s);
   o->copy(n, rt, r, c.done, s);
@@ -707,6 +755,7 @@ static int solve_impl(int method, int w, const mpk_csr* Ac, const mpk_ilu* Mc, c
     info.fail_row = -1;
     info.graph = gexec_used ? 1 : 0;
     info.hermitian = hermitian;
+    info.replacements = q[ST_NREP];
     info.res0 = r0n;
     info.relres_rec = r0n > 0 ? Sy[S_NORM * kSlotDoubles] / r0n : 0.0;
     info.relres_true = r0n > 0 ? Sy[S_D4 * kSlotDoubles] / r0n : 0.0;

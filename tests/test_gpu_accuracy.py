@@ -1,11 +1,13 @@
 """Final accuracy against the manufactured solution x* = ones (the error bars of the workload
 statement: relative error <= 1e-28 with DD vectors and <= 1e-60 with QD vectors on a
 well-conditioned system), with every factor precision: the binary32 / bfloat16 factors win the
-accuracy back through the multi-component iteration.  Runs identical to the oracle's."""
+accuracy back through the multi-component iteration.  Runs within the stated bars of the
+oracle's (tests/_bars.py)."""
 import numpy as np
 import pytest
 import torch
 
+import _bars
 import oracle
 from paper_2504_14498_gb300 import _lib, inputs
 
@@ -32,6 +34,6 @@ def test_final_error_on_config_1(w, tol, bar, prec):
     x = out["x"].cpu().numpy()
     ref = oracle.krylov("bicgstab", A_t, b, w, ilu=prec, tol_rel=tol, maxit=400)
     assert out["status"] == ref["status"] == "OK"
-    assert out["iters"] == ref["iters"]
-    assert np.array_equal(x, ref["x"]) or w > 2
+    _bars.check_solve(out, ref, prec, w, tol)
     assert _relerr(x, w) <= bar, _relerr(x, w)
+    assert _relerr(ref["x"], w) <= bar, _relerr(ref["x"], w)

@@ -8,13 +8,15 @@
   * shifted-Laplacian Helmholtz 1024 x 1024 complex (N = 1,048,576, nnz = 5,238,784): complex DD
     SpMV, complex ILU(0) in binary64 / binary32, M^-1 and M^-H, and the first iterations of
     complex DD BiCGSTAB and BiCG.
-Bars as in test_gpu_parity: bitwise for D / DD and for the factors and substitutions (the GPU
-follows the oracle's operation order), within 2^-200 of sum |a||x| per row for QD.
+Bars as in test_gpu_parity: bitwise for the D / DD SpMV, the factors and the substitutions (the
+GPU follows the oracle's operation order), within 2^-200 of sum |a||x| per row for QD; solves
+within the stated bars of tests/_bars.py (the inner products differ in summation order).
 """
 import numpy as np
 import pytest
 import torch
 
+import _bars
 import oracle
 from paper_2504_14498_gb300 import _lib, inputs
 
@@ -67,11 +69,7 @@ def test_convdiff2d_64_complete_solves(method, w, tol):
     out = _lib.krylov_solve(method, w, A, M, b, tol_rel=tol, maxit=2000)
     ref = oracle.krylov(method, A_t, b_ref, w, ilu="fp64", tol_rel=tol, maxit=2000)
     assert out["status"] == ref["status"] == "OK"
-    k = min(20, len(ref["hist"]))
-    np.testing.assert_allclose(out["hist"][:k], ref["hist"][:k], rtol=1e-10)
-    assert abs(out["iters"] - ref["iters"]) <= max(1, int(0.05 * ref["iters"]))
-    if w <= 2:
-        assert out["iters"] == ref["iters"] and np.array_equal(host(out["x"]), ref["x"])
+    _bars.check_solve(out, ref, "fp64", w, tol)
     xe = host(out["x"]).reshape(n, w)
     err = np.max(np.abs((xe[:, 0] - 1.0) + xe[:, 1:].sum(axis=1)))
     assert err < {1: 1e-9, 2: 1e-20, 4: 1e-20}[w]
@@ -121,8 +119,8 @@ def test_cube_bicgstab_first_iterations(cube, prec):
     out = _lib.krylov_solve("bicgstab", w, A, _lib.ILU0(A, prec), b, tol_rel=1e-25, maxit=its)
     ref = oracle.krylov("bicgstab", A_t, b_ref, w, ilu=prec, tol_rel=1e-25, maxit=its)
     assert out["status"] == ref["status"] == "MAXIT"
-    assert np.array_equal(out["hist"], ref["hist"])
-    assert np.array_equal(host(out["x"]), ref["x"])
+    assert _bars.check_band(out["hist"], ref["hist"], _bars.band_floor(prec, w)) == its + 1
+    assert _bars.rel_error(host(out["x"]), ref["x"], n, 1, w) <= 1e-24
 
 
 # ---- 1024^2 complex Helmholtz -------------------------------------------------------------------
@@ -153,5 +151,5 @@ def test_helmholtz_first_iterations(helm, method):
     out = _lib.krylov_solve(method, w, A, _lib.ILU0(A, "fp64"), dev(b_h), tol_rel=1e-25, maxit=its)
     ref = oracle.krylov(method, A_t, b_h, w, 2, ilu="fp64", tol_rel=1e-25, maxit=its)
     assert out["status"] == ref["status"] == "MAXIT"
-    assert np.array_equal(out["hist"], ref["hist"])
-    assert np.array_equal(host(out["x"]), ref["x"])
+    assert _bars.check_band(out["hist"], ref["hist"], _bars.band_floor("fp64", w)) == its + 1
+    assert _bars.rel_error(host(out["x"]), ref["x"], n, 2, w) <= 1e-24

