@@ -37,32 +37,57 @@ _IP = ctypes.POINTER(ctypes.c_int)
 _DP = ctypes.POINTER(ctypes.c_double)
 
 
+_lib_p = None
+
+
+def lib_p():
+    """The paper-like "_p" build (SpMV, vector updates and inner products on all host threads),
+    or None where OpenMP is unavailable.  Used only by the benchmark's CPU baseline."""
+    global _lib_p
+    if _lib_p is None:
+        path = _build.build_p()
+        if path is None:
+            return None
+        _lib_p = _declare(ctypes.CDLL(path))
+    return _lib_p
+
+
+def threads_p(k=0):
+    """Threads of the "_p" build (k > 0 sets them); None without it."""
+    L = lib_p()
+    return None if L is None else L.orc_threads(int(k))
+
+
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
-        L = ctypes.CDLL(path)
-        L.orc_two_sum.argtypes = [_D, _D, _f64p]
-        L.orc_two_prod.argtypes = [_D, _D, _f64p]
-        L.orc_mp_op.argtypes = [_I, _I, _f64p, _f64p, _f64p]
-        L.orc_spmv.argtypes = [_I, _i32p, _i32p, _f64p, _I, _I, _f64p, _f64p]
-        L.orc_spmv_mm.argtypes = [_I, _i32p, _i32p, _f64p, _I, _I, _f64p, _f64p]
-        L.orc_dot.argtypes = [_I, _I, _I, _f64p, _f64p, _f64p]
-        L.orc_check_pattern.argtypes = [_I, _i32p, _i32p, ctypes.c_void_p, _IP]
-        L.orc_check_pattern.restype = _I
-        L.orc_ilu0.argtypes = [_I, _i32p, _i32p, _f64p, _I, _I, _f64p, _IP]
-        L.orc_ilu0.restype = _I
-        L.orc_ilu0_mp.argtypes = [_I, _i32p, _i32p, _f64p, _I, _I, _f64p, _IP]
-        L.orc_ilu0_mp.restype = _I
-        L.orc_precond.argtypes = [_I, _i32p, _i32p, _f64p, _I, _I, _I, _I, _f64p, _f64p]
-        L.orc_krylov.argtypes = [_I, _I, _i32p, _i32p, _f64p, _I, _I, _I, ctypes.c_void_p, _f64p, _f64p,
-                                 _D, _D, _I, _I, _f64p, _IP, _DP, _I, ctypes.c_void_p, _IP]
-        L.orc_krylov_hooks.argtypes = [_I, _I, _i32p, _i32p, _f64p, _I, _I, _I, ctypes.c_void_p, _f64p, _f64p,
-                                       _D, _D, _I, _I, _f64p, _IP, _DP, ctypes.c_void_p, ctypes.c_void_p,
-                                       _I, _f64p, _IP]
-        L.orc_krylov.restype = _I
-        _lib = L
+        _lib = _declare(ctypes.CDLL(_build.build()))
     return _lib
+
+
+def _declare(L):
+    L.orc_two_sum.argtypes = [_D, _D, _f64p]
+    L.orc_two_prod.argtypes = [_D, _D, _f64p]
+    L.orc_mp_op.argtypes = [_I, _I, _f64p, _f64p, _f64p]
+    L.orc_spmv.argtypes = [_I, _i32p, _i32p, _f64p, _I, _I, _f64p, _f64p]
+    L.orc_spmv_mm.argtypes = [_I, _i32p, _i32p, _f64p, _I, _I, _f64p, _f64p]
+    L.orc_dot.argtypes = [_I, _I, _I, _f64p, _f64p, _f64p]
+    L.orc_check_pattern.argtypes = [_I, _i32p, _i32p, ctypes.c_void_p, _IP]
+    L.orc_check_pattern.restype = _I
+    L.orc_ilu0.argtypes = [_I, _i32p, _i32p, _f64p, _I, _I, _f64p, _IP]
+    L.orc_ilu0.restype = _I
+    L.orc_ilu0_mp.argtypes = [_I, _i32p, _i32p, _f64p, _I, _I, _f64p, _IP]
+    L.orc_ilu0_mp.restype = _I
+    L.orc_precond.argtypes = [_I, _i32p, _i32p, _f64p, _I, _I, _I, _I, _f64p, _f64p]
+    L.orc_krylov.argtypes = [_I, _I, _i32p, _i32p, _f64p, _I, _I, _I, ctypes.c_void_p, _f64p, _f64p,
+                             _D, _D, _I, _I, _f64p, _IP, _DP, _I, ctypes.c_void_p, _IP]
+    L.orc_krylov_hooks.argtypes = [_I, _I, _i32p, _i32p, _f64p, _I, _I, _I, ctypes.c_void_p, _f64p, _f64p,
+                                   _D, _D, _I, _I, _f64p, _IP, _DP, ctypes.c_void_p, ctypes.c_void_p,
+                                   _I, _f64p, _IP]
+    L.orc_krylov.restype = _I
+    L.orc_threads.argtypes = [_I]
+    L.orc_threads.restype = _I
+    return L
 
 
 def _c(a, dt):
@@ -146,14 +171,17 @@ TRUE_RES_PERIOD = 50  # default period of the true-residual check (0: none)
 
 
 def krylov(method, A, b, w, c=1, ilu="none", fac=None, x0=None, tol_rel=1e-25, tol_abs=0.0, maxit=1000,
-           force_eta0=False, mp_matrix=False, shadow=None, trace=False, true_res_period=TRUE_RES_PERIOD):
+           force_eta0=False, mp_matrix=False, shadow=None, trace=False, true_res_period=TRUE_RES_PERIOD,
+           parallel=False):
     """Run one solve; returns dict(status, iters, x, hist, relres_true, hist_true, replacements).
     mp_matrix: every SpMV with the matrix promoted to w components (the rows without "_d").
     true_res_period: P > 0 recomputes b - A x every P iterations and when the recursive residual
     passes the stopping test, replacing r when the true norm is above 10x the target (then a
     passed test is withdrawn); hist_true[k] is that norm at the checked iterations, NaN elsewhere.
     Test hooks: shadow, the initial shadow residual instead of r0; trace, also return "trace"
-    (per iteration the normalised inner products that exact arithmetic makes zero)."""
+    (per iteration the normalised inner products that exact arithmetic makes zero).
+    parallel: run on the "_p" build (benchmark baseline only; its inner products are summed per
+    thread range, so its bits differ from the plain oracle's)."""
     n, rp, ci, val = A
     x = np.zeros(n * c * w) if x0 is None else _c(x0, np.float64).copy()
     hist = np.zeros(maxit + 2)
@@ -172,7 +200,10 @@ def krylov(method, A, b, w, c=1, ilu="none", fac=None, x0=None, tol_rel=1e-25, t
     tr = np.zeros(2 * (maxit + 2)) if trace else None
     htrue = np.full(maxit + 2, np.nan)
     nrep = ctypes.c_int(0)
-    st = lib().orc_krylov_hooks(METHODS[method], n, _c(rp, np.int32), _c(ci, np.int32), _c(val, np.float64), c, w,
+    L = lib_p() if parallel else lib()
+    if L is None:
+        raise RuntimeError("the OpenMP build of the oracle is unavailable")
+    st = L.orc_krylov_hooks(METHODS[method], n, _c(rp, np.int32), _c(ci, np.int32), _c(val, np.float64), c, w,
                                 ILUS[ilu], facp, _c(b, np.float64), x, float(tol_rel), float(tol_abs), int(maxit),
                                 (1 if force_eta0 else 0) | (2 if mp_matrix else 0), hist, ctypes.byref(it),
                                 ctypes.byref(rr), None if sh is None else sh.ctypes.data_as(ctypes.c_void_p),

@@ -39,6 +39,13 @@
  * Built with -ffp-contract=off so that every a*b+c written below is two roundings unless
  * fma() is called explicitly.
  *
+ * Paper-like "_p" build (the paper's 32-thread OpenMP rows, Sec. 4): compiled once more with
+ * -fopenmp into liboracle_p.so, the SpMV, the vector updates and the inner products run on all
+ * host threads (static row ranges).  Each row and each entry is computed as above; an inner
+ * product is summed left to right within each thread's contiguous range, and the thread sums
+ * are added in thread order.  ILU(0) and the substitutions stay sequential, as in the paper.
+ * The plain build (no -fopenmp) ignores the pragmas: it is the oracle the tests use.
+ *
  * Layout: an MP real number is w doubles (leading component first); a complex one is 2w
  * doubles (real part, then imaginary part).  A vector of n entries is n*c*w doubles, c = 1
  * (real) or 2 (complex).  Matrices are CSR with int32 row pointers and column indices and
@@ -48,6 +55,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_OK 0
 #define ORC_MAXIT 1
@@ -82,6 +92,16 @@ static inline void two_prod(double a, double b, double *p, double *e) {
 }
 
 void orc_two_sum(double a, double b, double *out) { two_sum(a, b, &out[0], &out[1]); }
+/* Threads of the "_p" build (no effect in the plain build); returns the count in use. */
+int orc_threads(int k) {
+#ifdef _OPENMP
+  if (k > 0) omp_set_num_threads(k);
+  return omp_get_max_threads();
+#else
+  (void)k;
+  return 1;
+#endif
+}
 void orc_two_prod(double a, double b, double *out) { two_prod(a, b, &out[0], &out[1]); }
 
 /* ------------------------------------------------------------------------------------------
@@ -422,8 +442,12 @@ static int n_is_zero(num a) { return a.re.c[0] == 0.0 && a.im.c[0] == 0.0; }
  * full multiplication with the matrix entry first: the SpMV of the rows without "_d".
  * ---------------------------------------------------------------------------------------- */
 static void spmv(int n, const int *rp, const int *ci, const double *val, ctx t, const double *x, double *y) {
-  int s = t.c * t.w, i, p;
+  int s = t.c * t.w, i;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
   for (i = 0; i < n; ++i) {
+    int p;
     num acc = n_zero();
     for (p = rp[i]; p < rp[i + 1]; ++p) {
       num xj = n_load(x + (size_t)ci[p] * s, t);
@@ -455,6 +479,23 @@ void orc_spmv_mm(int n, const int *rp, const int *ci, const double *val, int c, 
 static num dot(int n, ctx t, const double *a, const double *b) {
   int s = t.c * t.w, i;
   num acc = n_zero();
+#ifdef _OPENMP
+  if (omp_get_max_threads() > 1 && n >= 4096) { /* "_p" build: per-thread ranges, sums in thread order */
+    int nth = omp_get_max_threads(), k;
+    num *part = (num *)malloc(sizeof(num) * (size_t)nth);
+#pragma omp parallel num_threads(nth)
+    {
+      int tid = omp_get_thread_num(), j;
+      int lo = (int)((long long)n * tid / nth), hi = (int)((long long)n * (tid + 1) / nth);
+      num pa = n_zero();
+      for (j = lo; j < hi; ++j) pa = n_add(pa, n_mul_conj(n_load(a + (size_t)j * s, t), n_load(b + (size_t)j * s, t), t), t);
+      part[tid] = pa;
+    }
+    for (k = 0; k < nth; ++k) acc = n_add(acc, part[k], t);
+    free(part);
+    return acc;
+  }
+#endif
   for (i = 0; i < n; ++i) acc = n_add(acc, n_mul_conj(n_load(a + (size_t)i * s, t), n_load(b + (size_t)i * s, t), t), t);
   return acc;
 }
@@ -866,6 +907,9 @@ static void apply_m(const sys_t *S, int trans, const double *r, double *z) {
 /* y := a + alpha * b  (alpha multiplies the vector entry from the left: alpha * b_i) */
 static void vaxpy(const sys_t *S, double *y, const double *a, num alpha, const double *b) {
   int s = S->t.c * S->t.w, i;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
   for (i = 0; i < S->n; ++i) {
     num v = n_add(n_load(a + (size_t)i * s, S->t), n_mul(alpha, n_load(b + (size_t)i * s, S->t), S->t), S->t);
     n_store(y + (size_t)i * s, v, S->t);
@@ -1079,11 +1123,17 @@ int orc_krylov(int method, int n, const int *rp, const int *ci, const double *va
       vaxpy(&S, tmp, tmp, beta, uh);          /*   + beta u^ */
       {
         int s2 = s;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
         for (i = 0; i < n; ++i) {             /* u^ = zeta q^ + eta (...) */
           num a = n_mul(zeta, n_load(qh + (size_t)i * s2, t), t);
           num bb = n_mul(eta, n_load(tmp + (size_t)i * s2, t), t);
           n_store(uh + (size_t)i * s2, n_add(a, bb, t), t);
         }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
         for (i = 0; i < n; ++i) {             /* z^ = zeta r^ + eta z^ - alpha u^ */
           num a = n_mul(zeta, n_load(rh + (size_t)i * s2, t), t);
           num bb = n_mul(eta, n_load(zh + (size_t)i * s2, t), t);
