@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--m", type=int, default=128, help="grid points per axis")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--learned-steps", type=int, default=400,
+                    help="training steps of the learned correction for its 128^3 variant (0: skip it)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=2, help="oracle iterations in the CPU sample")
@@ -78,7 +80,10 @@ def parse():
     ap.add_argument("--m-complex", type=int, default=1024, help="plainrows: Helmholtz grid points per axis")
     ap.add_argument("--formats", default="DD", help="tables: comma-separated formats among DD,TD,QD")
     ap.add_argument("--helm-maxit32", type=int, default=20000, help="helmholtz: iteration limit, binary32 factor")
-    ap.add_argument("--helm-maxit64", type=int, default=2000, help="helmholtz: iteration limit, binary64 factor")
+    ap.add_argument("--helm-maxit64", type=int, default=20000, help="helmholtz: iteration limit, binary64 factor")
+    ap.add_argument("--helm-methods", default="bicgstab,bicg,cgs,gpbicg",
+                    help="helmholtz: methods to run; name:P runs that method with check period P")
+    ap.add_argument("--helm-period", type=int, default=50, help="helmholtz: true-residual check period")
     ap.add_argument("--complex-iters", type=int, default=20, help="plainrows: Helmholtz iterations per solve")
     ap.add_argument("--train-instances", type=int, default=20000)
     ap.add_argument("--eval-instances", type=int, default=200)
@@ -293,9 +298,9 @@ def run_mpk(args):
     b = _lib.spmv_mp(A, xs, w)
     torch.cuda.synchronize()
 
-    def solve(prec):
+    def solve(prec, method="bicgstab"):
         M = _lib.ILU0(A, prec)
-        out = _lib.krylov_solve("bicgstab", w, A, M, b, tol_rel=TOL, maxit=20000, check_every=10, history=False)
+        out = _lib.krylov_solve(method, w, A, M, b, tol_rel=TOL, maxit=20000, check_every=10, history=False)
         out["schedule"] = M.schedule()
         M.close()
         return out
@@ -358,6 +363,17 @@ def run_mpk(args):
             variants[prec] = {"s": v0.elapsed_time(v1) / reps / 1e3, "iters": o["iters"], "status": o["status"],
                               "relres_true": o["relres_true"], "relerr_true": relerr(o, w),
                               "substitution_schedule": list(o["schedule"])}
+        # GPBiCG (the other method the 128^3 configuration names) with the binary64 and binary32 factors
+        for prec in ("fp64", "fp32"):
+            solve(prec, "gpbicg")
+            torch.cuda.synchronize()
+            g0_, g1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0_.record()
+            o = solve(prec, "gpbicg")
+            g1_.record()
+            torch.cuda.synchronize()
+            variants["gpbicg_" + prec] = {"s": g0_.elapsed_time(g1_) / 1e3, "iters": o["iters"], "status": o["status"],
+                                         "relres_true": o["relres_true"], "relerr_true": relerr(o, w)}
         # accuracy: the same solves continued to 1e-29, near the DD rounding level; the binary32
         # factor wins the accuracy back through the DD iteration (final error against x*)
         acc = {}
@@ -371,23 +387,53 @@ def run_mpk(args):
         # QD (w = 4) BiCGSTAB to 1e-55 with the binary64 factor, one timed solve after one untimed
         b4 = _lib.spmv_mp(A, torch.as_tensor(inputs.ones(n, 4), device="cuda"), 4)
 
-        def solve_qd():
+        def solve_qd(method):
             M = _lib.ILU0(A, "fp64")
-            o = _lib.krylov_solve("bicgstab", 4, A, M, b4, tol_rel=1e-55, maxit=2000, check_every=10, history=False)
+            o = _lib.krylov_solve(method, 4, A, M, b4, tol_rel=1e-55, maxit=2000, check_every=10, history=False)
             M.close()
             return o
 
-        solve_qd()
-        torch.cuda.synchronize()
-        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        q0.record()
-        o = solve_qd()
-        q1.record()
-        torch.cuda.synchronize()
-        variants["qd_fp64"] = {"s": q0.elapsed_time(q1) / 1e3, "iters": o["iters"], "status": o["status"],
-                               "relres_true": o["relres_true"], "relerr_true": relerr(o, 4), "tol_rel": 1e-55,
-                               "vectors": "QD (w=4)"}
+        for method, key in (("bicgstab", "qd_fp64"), ("gpbicg", "qd_gpbicg_fp64")):
+            solve_qd(method)
+            torch.cuda.synchronize()
+            q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            q0.record()
+            o = solve_qd(method)
+            q1.record()
+            torch.cuda.synchronize()
+            variants[key] = {"s": q0.elapsed_time(q1) / 1e3, "iters": o["iters"], "status": o["status"],
+                             "relres_true": o["relres_true"], "relerr_true": relerr(o, 4), "tol_rel": 1e-55,
+                             "vectors": "QD (w=4)", "method": method}
         del b4
+        # learned correction of the factor (network trained here on 3-D instances of the same
+        # recipe, other seeds); plain ILU(0) judges: the learned factor counts only where it
+        # needs no more iterations than the plain one at the same true-residual level
+        if args.learned_steps > 0:
+            net, trec = train_learned3d(args.learned_steps)
+            lv = {"train": trec}
+            for prec in ("fp64", "fp32"):
+                def solve_l(prec=prec):
+                    M = _lib.ILU0(A, prec)
+                    net.correct(A, M)
+                    o = _lib.krylov_solve("bicgstab", w, A, M, b, tol_rel=TOL, maxit=20000, check_every=10,
+                                          history=False)
+                    M.close()
+                    return o
+
+                solve_l()
+                torch.cuda.synchronize()
+                l0_, l1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                l0_.record()
+                o = solve_l()
+                l1_.record()
+                torch.cuda.synchronize()
+                plain_it = extra["iters"] if prec == args.prec else variants.get(prec, {}).get("iters")
+                lv[prec] = {"s": l0_.elapsed_time(l1_) / 1e3, "iters": o["iters"], "status": o["status"],
+                            "relres_true": o["relres_true"], "relerr_true": relerr(o, w),
+                            "plain_iters": plain_it,
+                            "kept_by_plain_judge": bool(o["status"] == "OK" and plain_it is not None
+                                                        and o["iters"] <= plain_it)}
+            variants["learned"] = lv
 
     # ---- kernel rooflines (CUDA events on the launching stream) -------------------------------
     def time_launches(fn, reps=20, warm=5):
@@ -696,11 +742,12 @@ def run_plainrows(args):
 
 def run_helmholtz(args):
     """The complex workload: shifted-Laplacian Helmholtz h^2(-Lap - k^2 (1 - 0.5 i)) on a 1024^2
-    grid, k = 20 pi, b with N(0, 1) real and imaginary parts; complex DD BiCGSTAB to 1e-25 with the
-    complex binary32 factor (maxit --helm-maxit32) and with the complex binary64 factor (maxit
-    --helm-maxit64: at about 84 ms per iteration a complete run takes minutes).  Reports
-    iterations, seconds (factorisation + solve, CUDA events), ms per iteration and the true
-    relative residual of each."""
+    grid, k = 20 pi, b with N(0, 1) real and imaginary parts; complex DD BiCG, CGS, BiCGSTAB and
+    GPBiCG (--helm-methods) to 1e-25 with the complex binary32 factor (maxit --helm-maxit32) and
+    the complex binary64 factor (maxit --helm-maxit64).  Reports per solve the status, iterations,
+    seconds (factorisation + solve, CUDA events), ms per iteration, the true relative residual,
+    the residual replacements, and the recursive and true relative residuals at every check of
+    the replacement rule (period --helm-period)."""
     import torch
 
     from paper_2504_14498_gb300 import _lib, inputs
@@ -711,24 +758,36 @@ def run_helmholtz(args):
     A = _lib.Matrix.from_tuple(A_t, is_complex=True)
     b = torch.as_tensor(inputs.normal_rhs(n, w), device="cuda")
     rows = {}
-    for prec, maxit in (("fp32", args.helm_maxit32), ("fp64", args.helm_maxit64)):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        M = _lib.ILU0(A, prec)
-        out = _lib.krylov_solve("bicgstab", w, A, M, b, tol_rel=TOL, maxit=maxit, check_every=50, history=True)
-        e1.record()
-        torch.cuda.synchronize()
-        M.close()
-        t = e0.elapsed_time(e1) / 1e3
-        h = out["hist"]
-        rows[prec] = {"status": out["status"], "iters": out["iters"], "maxit": maxit, "s": t,
-                      "ms_per_iter": 1e3 * t / max(1, out["iters"]), "relres_true": out["relres_true"],
-                      "relres_rec_by_1000": [float(h[k] / h[0]) for k in range(0, len(h), 1000)]}
-        print("%s: %s %d it %.1f s" % (prec, out["status"], out["iters"], t), file=sys.stderr, flush=True)
-    line = {"metric": "complex DD BiCGSTAB + ILU(0) on 1024^2 shifted-Laplacian Helmholtz (k = 20 pi) to 1e-25",
-            "value": rows["fp32"]["s"], "unit": "s (binary32 factor)", "higher_is_better": False, "n_gpus": 1,
+    for token in args.helm_methods.split(","):
+        method, _, per = token.partition(":")  # "cgs:0": this method with its own check period
+        period = int(per) if per else args.helm_period
+        for prec, maxit in (("fp32", args.helm_maxit32), ("fp64", args.helm_maxit64)):
+            if maxit <= 0:
+                continue
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            M = _lib.ILU0(A, prec)
+            out = _lib.krylov_solve(method, w, A, M, b, tol_rel=TOL, maxit=maxit, check_every=50, history=True,
+                                    true_res_period=period)
+            e1.record()
+            torch.cuda.synchronize()
+            M.close()
+            t = e0.elapsed_time(e1) / 1e3
+            h, ht = out["hist"], out["hist_true"]
+            checks = [[k, float(h[k] / h[0]), float(ht[k] / h[0])] for k in range(len(ht)) if not np.isnan(ht[k])]
+            rows["%s_%s" % (method, prec)] = {
+                "status": out["status"], "iters": out["iters"], "maxit": maxit, "s": t,
+                "ms_per_iter": 1e3 * t / max(1, out["iters"]), "relres_true": out["relres_true"],
+                "replacements": out["replacements"], "true_res_period": period, "checks_k_rec_true": checks}
+            print("%s %s: %s %d it %.1f s rr %.2e rep %d" % (method, prec, out["status"], out["iters"], t,
+                                                            out["relres_true"], out["replacements"]),
+                  file=sys.stderr, flush=True)
+    first = next(iter(rows.values()))
+    line = {"metric": "complex DD Krylov + ILU(0) on 1024^2 shifted-Laplacian Helmholtz (k = 20 pi) to 1e-25",
+            "value": first["s"], "unit": "s (%s)" % next(iter(rows)), "higher_is_better": False, "n_gpus": 1,
             "data": "synthetic", "dtype": "f64",
-            "config": {"workload": "helmholtz2d 1024^2 (N=1048576, nnz=5238784), complex DD vectors, b ~ N(0,1)"},
+            "config": {"workload": "helmholtz2d 1024^2 (N=1048576, nnz=5238784), complex DD vectors, b ~ N(0,1)",
+                       "true_res_period": args.helm_period},
             "solves": rows}
     print(json.dumps(line))
     return 0
@@ -805,6 +864,51 @@ def _gen_batch(job):
     B_t, roff = inputs.block_diagonal(systems)
     W = inputs.training_probes(m, len(seeds), nprobe, probe_seed) if nprobe else None
     return (B_t[0], B_t[1].astype(np.int32), B_t[2], B_t[3]), roff, W
+
+
+def _gen_batch3d(job):
+    """Worker of the input pool: one block-diagonal batch of seeded 3-D instances and its probes."""
+    from paper_2504_14498_gb300 import inputs
+
+    m, seeds, nprobe, probe_seed = job
+    systems = [inputs.convdiff3d_random(m, int(s)) for s in seeds]
+    B_t, roff = inputs.block_diagonal(systems)
+    W = inputs.training_probes3d(m, len(seeds), nprobe, probe_seed) if nprobe else None
+    return (B_t[0], B_t[1].astype(np.int32), B_t[2], B_t[3]), roff, W
+
+
+def train_learned3d(steps, m=24, bs=8, K=4, lr=2e-3, base=2504_14498 + 70000):
+    """Train the learned ILU(0) correction on seeded m^3 instances of the 3-D recipe (batches of
+    bs block-diagonal systems, K probes, Adam) with the library's kernels; the inputs are made by a
+    spawned process pool while the GPU trains.  Returns (network, record)."""
+    import multiprocessing as mp
+
+    import torch
+
+    from paper_2504_14498_gb300 import _lib, learned
+
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(max(1, min(8, (os.cpu_count() or 2) - 1)))
+    jobs = [(m, list(range(base + k * bs, base + (k + 1) * bs)), K, base + 7 * k) for k in range(steps)]
+    net = learned.LearnedILU(seed=base + 1)
+    ws, losses, t_gpu = None, [], 0.0
+    t0 = time.perf_counter()
+    for B_t, roff, W in pool.imap(_gen_batch3d, jobs, chunksize=2):
+        g0 = time.perf_counter()
+        B = _lib.Matrix.from_tuple(B_t)
+        M = _lib.ILU0(B, "fp32")
+        if ws is None:
+            ws = learned.Workspace(B.n, B.nnz, K, bs)
+        losses.append(net.train_step(B, M, torch.as_tensor(W, device="cuda"), ws, roff, lr=lr))
+        M.close()
+        torch.cuda.synchronize()
+        t_gpu += time.perf_counter() - g0
+    pool.close()
+    losses = [float(x.item()) for x in losses]
+    rec = {"instances": steps * bs, "grid": "%d^3" % m, "steps": steps, "batch": bs, "probes": K, "lr": lr,
+           "s_total": time.perf_counter() - t0, "s_gpu": t_gpu,
+           "loss_first": float(np.mean(losses[:10])), "loss_last": float(np.mean(losses[-10:]))}
+    return net, rec
 
 
 def run_learned(args):

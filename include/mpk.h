@@ -26,7 +26,8 @@
  *     mpk_krylov_solve); device waits are bounded (about one second each) and never hang.
  *
  * Arithmetic: see paper_2504_14498_gb300/csrc/mp.cuh (DD: Joldes-Muller-Popescu double-word
- * algorithms; TD/QD: exact evaluation then greedy rounding to w components).
+ * algorithms; TD/QD: renormalisation of the exact terms, relative error about 2^(-53 w));
+ * mpk_mp_op exposes each operation.
  *
  * Environment variables (none changes a result; all choose how the same operations run):
  *   MPK_SUBST_SCHEDULE=static|owner|cluster8|cluster16  substitution schedule (mpk_ilu0_schedule);
@@ -185,6 +186,26 @@ int mpk_dot(int n, int is_complex, int w, const double* a_dev, const double* b_d
 #define MPK_DOT_NOALLOC_MAX_N 16777216
 int mpk_dot_noalloc(int n, int is_complex, int w, const double* a_dev, const double* b_dev, double* out_dev,
                     void* stream);
+
+/* Elementwise real w-component arithmetic on device arrays: out_i = a_i op b_i for i < n, each
+ * entry w doubles (leading component first).  These are the operations every kernel of the
+ * library performs on the formats of Sec. 2 (binary64 with w components): w = 1 plain binary64,
+ * w = 2 the double-word algorithms of Joldes, Muller and Popescu (TOMS 2017), w = 3, 4 a
+ * magnitude sort, an exact TwoSum chain and a top-down renormalisation to w components
+ * (relative error at most about 2^(-53 w) of the exact result).  They are exported so that
+ * callers and tests can check the arithmetic on its own against exact values.
+ *   op: MPK_OP_ADD, MPK_OP_SUB, MPK_OP_MUL (a * b), MPK_OP_MUL_FP (a times the binary64 b_i[0]),
+ *       MPK_OP_DIV (a / b), MPK_OP_DIV_FP (a / b_i[0]), MPK_OP_SQRT (square root of a; b unused,
+ *       may be NULL).
+ * a_dev, b_dev, out_dev: n*w doubles; out_dev may alias neither input.  n = 0 does nothing. */
+#define MPK_OP_ADD 0
+#define MPK_OP_SUB 1
+#define MPK_OP_MUL 2
+#define MPK_OP_MUL_FP 3
+#define MPK_OP_DIV 4
+#define MPK_OP_DIV_FP 5
+#define MPK_OP_SQRT 6
+int mpk_mp_op(int op, int w, int n, const double* a_dev, const double* b_dev, double* out_dev, void* stream);
 
 /* ILU(0) of A (Algorithm 1; the "!= 0" tests read as membership in A's stored pattern; the
  * update A_ij -= L_ik U_kj is one fused multiply-add; a zero pivot is an error instead of

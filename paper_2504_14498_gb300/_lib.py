@@ -55,6 +55,7 @@ SIGNATURES = [
     ("mpk_spmv_mp_matrix", _I, [ctypes.POINTER(CsrDesc), _I, _VP, _VP, _VP]),
     ("mpk_dot", _I, [_I, _I, _I, _VP, _VP, _VP, _VP]),
     ("mpk_dot_noalloc", _I, [_I, _I, _I, _VP, _VP, _VP, _VP]),
+    ("mpk_mp_op", _I, [_I, _I, _I, _VP, _VP, _VP, _VP]),
     ("mpk_ilu0_factor", _I, [ctypes.POINTER(CsrDesc), _I, ctypes.POINTER(_VP), ctypes.POINTER(_I), _VP]),
     ("mpk_ilu0_factor_mp", _I, [ctypes.POINTER(CsrDesc), _I, ctypes.POINTER(_VP), ctypes.POINTER(_I), _VP]),
     ("mpk_ilu0_values", _I, [_VP, _VP, _VP]),
@@ -188,6 +189,22 @@ def dot_noalloc(a: torch.Tensor, b: torch.Tensor, n: int, w: int, is_complex=Fal
     m = n * c * w
     _check(lib().mpk_dot_noalloc(n, int(is_complex), w, _vec(a, m, "a"), _vec(b, m, "b"), _vec(out, c * w, "out"),
                                  _stream()))
+    return out
+
+
+MP_OPS = {"add": 0, "sub": 1, "mul": 2, "mul_fp": 3, "div": 4, "div_fp": 5, "sqrt": 6}
+
+
+def mp_op(op: str, w: int, a: torch.Tensor, b: torch.Tensor = None, out: torch.Tensor = None) -> torch.Tensor:
+    """Elementwise real w-component arithmetic (mpk_mp_op): a, b hold n*w doubles (entries of w
+    components); mul_fp / div_fp use each b entry's leading component as the binary64 operand."""
+    m = a.numel()
+    if m % w:
+        raise ValueError("a must hold whole w-component entries")
+    if out is None:
+        out = torch.empty_like(a)
+    pb = None if b is None else _vec(b, m, "b")
+    _check(lib().mpk_mp_op(MP_OPS[op], w, m // w, _vec(a, m, "a"), pb, _vec(out, m, "out"), _stream()))
     return out
 
 

@@ -1,9 +1,11 @@
-// capi.cu -- library-wide helpers and the stateless C-ABI entry points (SpMV, inner product).
+// capi.cu -- library-wide helpers and the stateless C-ABI entry points (SpMV, inner product,
+// elementwise multi-component arithmetic).
 #include <atomic>
 #include <cstdlib>
 #include <string>
 
 #include "internal.h"
+#include "mp.cuh"
 
 namespace mpk {
 
@@ -107,5 +109,52 @@ extern "C" int mpk_dot(int n, int is_complex, int w, const double* a_dev, const 
   o->dots(n, 1, av, bv, ov, ws, nullptr, s);
   MPK_CUDA(cudaGetLastError());
   MPK_CUDA(cudaFreeAsync(buf, s));
+  return MPK_OK;
+}
+
+// Elementwise real w-component arithmetic (the operations of mp.cuh every kernel uses).
+template <int W>
+__global__ void k_mp_op(int op, int n, const double* __restrict__ a, const double* __restrict__ b,
+                        double* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    R<W> x, y;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      x.c[k] = a[(int64_t)i * W + k];
+      y.c[k] = b != nullptr ? b[(int64_t)i * W + k] : 0.0;
+    }
+    R<W> z;
+    switch (op) {
+      case MPK_OP_ADD: z = add<W>(x, y); break;
+      case MPK_OP_SUB: z = sub<W>(x, y); break;
+      case MPK_OP_MUL: z = mul<W>(x, y); break;
+      case MPK_OP_MUL_FP: z = mul_fp<W>(x, y.c[0]); break;
+      case MPK_OP_DIV: z = div<W>(x, y); break;
+      case MPK_OP_DIV_FP: z = div_fp<W>(x, y.c[0]); break;
+      default: z = rsqrt_mp<W>(x); break;
+    }
+#pragma unroll
+    for (int k = 0; k < W; ++k) out[(int64_t)i * W + k] = z.c[k];
+  }
+}
+
+extern "C" int mpk_mp_op(int op, int w, int n, const double* a_dev, const double* b_dev, double* out_dev,
+                         void* stream) {
+  if (op < MPK_OP_ADD || op > MPK_OP_SQRT) return fail(MPK_INVALID_ARG, "unknown operation");
+  if (w < 1 || w > 4) return fail(MPK_INVALID_ARG, "w must be 1..4");
+  if (n < 0 || a_dev == nullptr || out_dev == nullptr || (b_dev == nullptr && op != MPK_OP_SQRT))
+    return fail(MPK_INVALID_ARG, "bad argument");
+  if (n == 0) return MPK_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  int g = (n + 255) / 256;
+  if (g > 4096) g = 4096;
+  count_launch();
+  switch (w) {
+    case 1: k_mp_op<1><<<g, 256, 0, s>>>(op, n, a_dev, b_dev, out_dev); break;
+    case 2: k_mp_op<2><<<g, 256, 0, s>>>(op, n, a_dev, b_dev, out_dev); break;
+    case 3: k_mp_op<3><<<g, 256, 0, s>>>(op, n, a_dev, b_dev, out_dev); break;
+    default: k_mp_op<4><<<g, 256, 0, s>>>(op, n, a_dev, b_dev, out_dev); break;
+  }
+  MPK_CUDA(cudaGetLastError());
   return MPK_OK;
 }

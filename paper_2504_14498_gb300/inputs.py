@@ -464,6 +464,39 @@ def smooth_probes(m, nsys, k, seed, modes=4):
     return out.reshape(nsys * m * m, k)
 
 
+def convdiff3d_random(m, seed, sigma=1.0, pe_range=(1.0, 50.0), direction=(1.0, 0.5, 0.25)):
+    """Training instances of the learned correction for the 3-D workload: the 7-point recipe of
+    convdiff3d on an m^3 grid with its own seeded log-normal diffusivity field and Peclet
+    number (the same distribution as the 128^3 configuration, other seeds)."""
+    A, _ = convdiff3d(m, sigma=sigma, pe_range=pe_range, direction=direction, seed=seed)
+    return A
+
+
+def smooth_probes3d(m, nsys, k, seed, modes=3):
+    """k smooth probe vectors per m^3 grid system (binary32, (nsys m^3) x k row-major): sums of
+    the lowest sine modes sin(a pi x) sin(b pi y) sin(c pi z), a, b, c = 1..modes, with
+    N(0,1) / (a b c) coefficients; natural ordering (x fastest)."""
+    rng = np.random.default_rng(seed)
+    x = (np.arange(m) + 1.0) / (m + 1.0)
+    S = np.stack([np.sin(a * np.pi * x) for a in range(1, modes + 1)])  # [modes, m]
+    f = np.arange(1, modes + 1, dtype=np.float64)
+    w = 1.0 / (f[:, None, None] * f[None, :, None] * f[None, None, :])  # [c, b, a]
+    out = np.empty((nsys, m ** 3, k), dtype=np.float32)
+    for s_ in range(nsys):
+        for col in range(k):
+            C = rng.standard_normal((modes, modes, modes)) * w
+            out[s_, :, col] = np.einsum("cba,cz,by,ax->zyx", C, S, S, S).reshape(-1)
+    return out.reshape(nsys * m ** 3, k)
+
+
+def training_probes3d(m, nsys, k, seed):
+    """Probe vectors for 3-D training batches: half smooth (smooth_probes3d), half N(0,1)."""
+    ks = k // 2
+    sm = smooth_probes3d(m, nsys, ks, seed)
+    rn = probe_vectors(nsys * m ** 3, k - ks, seed + 1)
+    return np.ascontiguousarray(np.concatenate([sm, rn], axis=1), dtype=np.float32)
+
+
 def training_probes(m, nsys, k, seed):
     """Probe vectors of the learned correction's training: half smooth (smooth_probes), half
     N(0,1) (probe_vectors)."""

@@ -72,10 +72,23 @@ def check_solve(out, ref, ilu, w, tol, indefinite=False, same_status=True):
 
 
 def rel_error(x, x_star, n, c, w):
-    """max_i |x_i - x*_i| / max_i |x*_i| with x, x* as n*c*w components (all components summed,
-    differences taken component-wise first so that nothing below the leading part is lost)."""
-    X = np.asarray(x, dtype=np.float64).reshape(n, c, w)
+    """max_i |x_i - x*_i| / max_i |x*_i| with x, x* as n*c*w components; each difference is the
+    correctly rounded value difference of the two w-component numbers (mp_diff)."""
     S = np.asarray(x_star, dtype=np.float64).reshape(n, c, w)
-    d = X - S  # exact per component for values this close
-    err = np.abs(d.sum(axis=2)).max()
+    err = np.abs(mp_diff(x, x_star, w)).max()
     return err / np.abs(S[:, :, 0]).max()
+
+
+def mp_diff(y, ref, w):
+    """Value differences of multi-component numbers, entry by entry: sum_k y_k - sum_k ref_k
+    correctly rounded (math.fsum over the 2w components).  Two representations of one value may
+    split it differently between components (the device's TD / QD renormalisation and the
+    oracle's greedy rounding do), so components are never compared one by one."""
+    import math
+
+    Y = np.asarray(y, dtype=np.float64).reshape(-1, w)
+    R = np.asarray(ref, dtype=np.float64).reshape(-1, w)
+    if w == 1:
+        return Y[:, 0] - R[:, 0]
+    both = np.concatenate([Y, -R], axis=1)
+    return np.array([math.fsum(row) for row in both])

@@ -92,7 +92,7 @@ def test_cube_spmv_qd_sampled(cube):
     ref = oracle.spmv(sub, x, 4).reshape(len(rows), 4)
     X = np.abs(x.reshape(n, 4)[:, 0])
     mag = np.add.reduceat(np.abs(sub[3]) * X[sub[2]], sub[1][:-1])
-    err = np.abs(y[rows] - ref).sum(axis=1)
+    err = np.abs(_bars.mp_diff(y[rows], ref, 4))
     assert np.all(err <= 2.0 ** -200 * mag * 4)
 
 

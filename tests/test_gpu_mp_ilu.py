@@ -5,7 +5,8 @@ Bars:
   * factor: identical for w <= 2 (the kernel applies the KIJ updates in their sequential order,
     every step the same double-word algorithm); w = 3, 4 within 2^-150 / 2^-200 of the entry's
     magnitude per step count (exact expansions rounded greedily: in practice identical);
-  * substitutions M z = r and M^H z = r: identical for w <= 2, w = 3, 4 within 2^-190 of max |z|;
+  * substitutions M z = r and M^H z = r: identical for w <= 2, w = 3, 4 within 2^-140 / 2^-190 of
+    max |z|;
   * Krylov with the factor: the stated bars of tests/_bars.py against the oracle's runs (the
     inner products differ in summation order);
   * a factor built for one w is refused by a solve with another w, and by the learned correction;
@@ -58,8 +59,8 @@ def test_mp_factor_parity(mat, w):
     if w <= 2:
         assert np.array_equal(got, ref)
     else:
-        g, r = got.reshape(-1, c, w), ref.reshape(-1, c, w)
-        err = np.abs(g - r).sum(axis=2)
+        r = ref.reshape(-1, c, w)
+        err = np.abs(_bars.mp_diff(got, ref, w)).reshape(-1, c)
         mag = np.abs(r[:, :, 0])
         assert np.all(err <= 64 * TOL[w] * np.maximum(mag, np.max(mag) * 2.0 ** -40))
 
@@ -79,7 +80,7 @@ def test_mp_precond_parity(mat, w, trans):
     if w <= 2:
         assert np.array_equal(z, ref), np.max(np.abs(z - ref))
     else:
-        assert np.max(np.abs(z - ref)) <= np.max(np.abs(ref)) * 2.0 ** -190
+        assert np.max(np.abs(_bars.mp_diff(z, ref, w))) <= np.max(np.abs(ref)) * 2.0 ** (-190 if w == 4 else -140)
 
 
 def _solve_pair(method, A_t, c, w, tol, maxit=600):
@@ -181,7 +182,7 @@ def test_mp_matrix_spmv_parity(w, c):
         assert np.array_equal(y, ref)
     else:
         lead = np.abs(ref.reshape(n, c, w)[:, :, 0])
-        err = np.abs((y - ref).reshape(n, c, w)).sum(axis=2)
+        err = np.abs(_bars.mp_diff(y, ref, w)).reshape(n, c)
         assert np.all(err <= TOL[w] * 64 * np.maximum(lead, np.max(lead) * 2.0 ** -30))
 
 

@@ -59,7 +59,7 @@ def test_precond_both_schedules(schedule, mat, prec, trans):
         if prec in ("fp32", "bf16") or w <= 2:
             assert np.array_equal(z, ref), (w, np.max(np.abs(z - ref)))
         else:
-            assert np.max(np.abs(z - ref)) <= np.max(np.abs(ref)) * 2.0 ** -190
+            assert np.max(np.abs(_bars.mp_diff(z, ref, w))) <= np.max(np.abs(ref)) * 2.0 ** -190
 
 
 @pytest.mark.parametrize("method", ["bicg", "bicgstab", "gpbicg"])
