@@ -45,6 +45,11 @@ FP64_PEAK_OPS = 152 * 4 * 0.5 * 2.07e9 / 1e12
 # 128^3 workload: dram__bytes_read.sum + dram__bytes_write.sum from an ncu capture of the current
 # kernel (its summary is under profiles/); None once the kernel changes.
 TRSV_MP_TRAFFIC = 151249152 + 18557952 + 168018688 + 17200128
+# binary64 warp instructions one 32-row chunk of the binary64-factor DD substitution issues on
+# its chain (lower unit triangle, upper triangle with the division), from an ncu count of the
+# static-schedule kernel on the 7-point matrix (sm__inst_executed_pipe_fp64 / chunks; summary
+# under profiles/).  Each takes 64 cycles of its sub-partition's FP64 unit.
+CHAIN_FP64_INSTR = {"lower": 65, "upper": 89}
 
 
 def parse():
@@ -451,11 +456,21 @@ def run_mpk(args):
     x = torch.as_tensor(inputs.random_vector(n, w, 1, seed=3), device="cuda")
     y = torch.empty_like(x)
     t_spmv = time_launches(lambda: _lib.spmv_mp(A, x, w, y))
+    # the same SpMV with D (w = 1) and QD (w = 4) vectors
+    x1 = torch.as_tensor(inputs.random_vector(n, 1, 1, seed=3), device="cuda")
+    y1 = torch.empty_like(x1)
+    t_spmv1 = time_launches(lambda: _lib.spmv_mp(A, x1, 1, y1))
+    x4 = torch.as_tensor(inputs.random_vector(n, 4, 1, seed=3), device="cuda")
+    y4 = torch.empty_like(x4)
+    t_spmv4 = time_launches(lambda: _lib.spmv_mp(A, x4, 4, y4), reps=10, warm=3)
+    del x1, y1, x4, y4
     M64 = _lib.ILU0(A, "fp64")
     M32 = _lib.ILU0(A, "fp32")
     z = torch.empty_like(x)
     t_pre64 = time_launches(lambda: M64.apply(x, w, False, z), reps=10, warm=3)
     t_pre32 = time_launches(lambda: M32.apply(x, w, False, z), reps=10, warm=3)
+    levels = (M64.levels(0)[0], M64.levels(1)[0])
+    hop_ns = statistics.median(_lib.probe_notify_ns(2000) for _ in range(3))
     M64.close()
     M32.close()
     hbm = float(pk.get("hbm_gbs", 6800.0))
@@ -469,6 +484,9 @@ def run_mpk(args):
     # DW*FP 6 + DW+DW 14 (TwoSum as FastTwoSum on exponent-ordered operands) = 20 per multiply-add;
     # DW/FP 10 (two divisions counted as one operation each)
     spmv_ops = 20 * nnz
+    spmv1_bytes = 12 * nnz + 4 * (n + 1) + 2 * 8 * n
+    spmv1_ops = 2 * nnz  # D: one multiply and one add per entry (no contraction)
+    spmv4_bytes = 12 * nnz + 4 * (n + 1) + 2 * 32 * n
     pre64_ops = 20 * nod + 10 * n
     alu = FP64_PEAK_OPS
     def rl(bound, work, t, peak, unit, per_unit):
@@ -480,11 +498,28 @@ def run_mpk(args):
                               "binary64 operations of one M^-1 (both triangles; k_trsv_mp x2)"),
         "spmv_dd": rl("alu", spmv_ops, t_spmv, alu, "T FP64 op/s", "binary64 operations of one SpMV (k_spmv)"),
         "spmv_dd_hbm": rl("hbm", spmv_bytes, t_spmv, hbm, "GB/s", "HBM bytes of one SpMV"),
+        "spmv_d": rl("alu", spmv1_ops, t_spmv1, alu, "T FP64 op/s", "binary64 operations of one D SpMV (k_spmv, w=1)"),
+        "spmv_d_hbm": rl("hbm", spmv1_bytes, t_spmv1, hbm, "GB/s", "HBM bytes of one D SpMV (w=1)"),
+        "spmv_qd_hbm": rl("hbm", spmv4_bytes, t_spmv4, hbm, "GB/s", "HBM bytes of one QD SpMV (w=4)"),
         "precond_fp64_dd_hbm": rl("hbm", pre64_bytes, t_pre64, hbm, "GB/s", "HBM bytes of one M^-1"),
         "precond_fp32_hbm": rl("hbm", pre32_bytes, t_pre32, hbm, "GB/s", "HBM bytes of one M^-1 (k_trsv_lp x2)"),
     }
     for k in rooflines:
         rooflines[k]["peak_note"] = "of derived nominal" if rooflines[k]["bound"] == "alu" else pk_note
+    # latency roof of one M^-1: every level of a triangle waits for one cross-SM notification
+    # (measured now by the probe) and then runs one chunk's chain of binary64 instructions at 64
+    # cycles each (counts from ncu, clock from the samples of the timed region)
+    if CHAIN_FP64_INSTR["lower"] is not None:
+        mhz = clk.get("sm_mhz") or 2070.0
+        chain_ns = {t: CHAIN_FP64_INSTR[t] * 64 / (mhz * 1e-3) for t in ("lower", "upper")}
+        floor_s = (levels[0] * (hop_ns + chain_ns["lower"]) + levels[1] * (hop_ns + chain_ns["upper"])) * 1e-9
+        nlev = levels[0] + levels[1]
+        rooflines["precond_fp64_dd_latency"] = {
+            "bound": "latency", "achieved": nlev / t_pre64 / 1e3, "peak": nlev / floor_s / 1e3,
+            "unit": "levels/ms", "frac": floor_s / t_pre64, "traffic": None, "s_per_launch": t_pre64,
+            "floor_s": floor_s, "levels": list(levels), "notify_ns": hop_ns, "chain_ns": chain_ns,
+            "sm_mhz": mhz, "unit_of_work": "levels of one M^-1 (both triangles)",
+            "peak_note": "latency floor: levels x (measured notification + chunk chain of binary64 instructions)"}
     # the dominant kernel of the timed solve is the binary64-factor substitution (latency-bound
     # chain of levels; FP64 issue while a level computes); its counters, where taken, are in profiles/
     # (counters of the static-schedule kernel: reported only when the tuner chose that schedule)

@@ -207,6 +207,14 @@ int mpk_dot_noalloc(int n, int is_complex, int w, const double* a_dev, const dou
 #define MPK_OP_SQRT 6
 int mpk_mp_op(int op, int w, int n, const double* a_dev, const double* b_dev, double* out_dev, void* stream);
 
+/* Measurement aid: the one-way latency of a cross-SM notification on this GPU -- a strong relaxed
+ * store by one SM seen by a strong relaxed polling load on another -- from `rounds` (1..10^6)
+ * round trips of a counter between two co-resident blocks (cooperative launch), timed with the
+ * device's global timer.  It is the synchronisation cost that the level-scheduled substitutions
+ * and ILU(0) pay per level.  *one_way_ns (host) receives the mean one-way time.  Waits are
+ * bounded; MPK_TIMEOUT if one ran out.  Synchronises `stream`. */
+int mpk_probe_notify_ns(int rounds, double* one_way_ns, void* stream);
+
 /* ILU(0) of A (Algorithm 1; the "!= 0" tests read as membership in A's stored pattern; the
  * update A_ij -= L_ik U_kj is one fused multiply-add; a zero pivot is an error instead of
  * being skipped).  Rows are factored in the level order of the lower triangle, either level by

@@ -56,6 +56,7 @@ SIGNATURES = [
     ("mpk_dot", _I, [_I, _I, _I, _VP, _VP, _VP, _VP]),
     ("mpk_dot_noalloc", _I, [_I, _I, _I, _VP, _VP, _VP, _VP]),
     ("mpk_mp_op", _I, [_I, _I, _I, _VP, _VP, _VP, _VP]),
+    ("mpk_probe_notify_ns", _I, [_I, ctypes.POINTER(ctypes.c_double), _VP]),
     ("mpk_ilu0_factor", _I, [ctypes.POINTER(CsrDesc), _I, ctypes.POINTER(_VP), ctypes.POINTER(_I), _VP]),
     ("mpk_ilu0_factor_mp", _I, [ctypes.POINTER(CsrDesc), _I, ctypes.POINTER(_VP), ctypes.POINTER(_I), _VP]),
     ("mpk_ilu0_values", _I, [_VP, _VP, _VP]),
@@ -190,6 +191,13 @@ def dot_noalloc(a: torch.Tensor, b: torch.Tensor, n: int, w: int, is_complex=Fal
     _check(lib().mpk_dot_noalloc(n, int(is_complex), w, _vec(a, m, "a"), _vec(b, m, "b"), _vec(out, c * w, "out"),
                                  _stream()))
     return out
+
+
+def probe_notify_ns(rounds=2000) -> float:
+    """One-way cross-SM notification latency in ns (mpk_probe_notify_ns)."""
+    v = ctypes.c_double(0.0)
+    _check(lib().mpk_probe_notify_ns(int(rounds), ctypes.byref(v), _stream()))
+    return v.value
 
 
 MP_OPS = {"add": 0, "sub": 1, "mul": 2, "mul_fp": 3, "div": 4, "div_fp": 5, "sqrt": 6}

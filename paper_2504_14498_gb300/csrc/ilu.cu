@@ -407,6 +407,46 @@ __global__ void k_depth_count(int m, const int* __restrict__ depth, int* __restr
 }
 __global__ void k_scan_single(int n, const int* __restrict__ cnt, int* __restrict__ out);
 
+// Fingerprint of a sparsity pattern (row pointers and column indices): the XOR over all entries
+// of a 64-bit mix (splitmix64's finaliser) of (array, position, value).  Order-independent, so a
+// grid-stride loop with atomic XOR gives the same value every time; two patterns that differ
+// anywhere differ in their fingerprints except with probability about 2^-64.
+__device__ __forceinline__ unsigned long long fp_mix(unsigned long long z) {
+  z += 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+__global__ void k_pattern_fp(int n, int nnz, const int* __restrict__ rp, const int* __restrict__ ci,
+                             unsigned long long* __restrict__ out) {
+  unsigned long long h = 0ull;
+  const int64_t total = (int64_t)n + 1 + nnz;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    const bool is_rp = k <= n;
+    const unsigned v = (unsigned)(is_rp ? rp[k] : ci[k - n - 1]);
+    h ^= fp_mix(((unsigned long long)k << 32) ^ v ^ (is_rp ? 0ull : 0x8000000000000000ull));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) h ^= __shfl_xor_sync(0xffffffffu, h, off);
+  if ((threadIdx.x & 31) == 0 && h != 0ull) atomicXor(out, h);
+}
+int pattern_fingerprint(int n, int nnz, const int* rp, const int* ci, uint64_t* out, cudaStream_t s) {
+  unsigned long long* d = nullptr;
+  MPK_CUDA(cudaMallocAsync((void**)&d, sizeof(unsigned long long), s));
+  MPK_CUDA(cudaMemsetAsync(d, 0, sizeof(unsigned long long), s));
+  count_launch();
+  const int64_t total = (int64_t)n + 1 + nnz;
+  int g = (int)((total + kBlock - 1) / kBlock);
+  if (g > sm_count() * 8) g = sm_count() * 8;
+  k_pattern_fp<<<g < 1 ? 1 : g, kBlock, 0, s>>>(n, nnz, rp, ci, d);
+  unsigned long long h = 0ull;
+  MPK_CUDA(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
+  MPK_CUDA(cudaFreeAsync(d, s));
+  MPK_CUDA(cudaStreamSynchronize(s));
+  *out = (uint64_t)h;
+  return MPK_OK;
+}
+
 // ---------------------------------------------------------------------------------------------
 // Conjugate transpose of a CSR matrix with CP values of type T per entry: counts, a single-
 // block scan, scatter, then an insertion sort of every row so columns are ascending.
@@ -1195,7 +1235,7 @@ int refresh_factor(mpk_ilu* M, cudaStream_t s) {
 // per SM, runs only when selected so; tests use it to cover each).
 int read_ctl_err(const mpk_ilu* M, cudaStream_t s);
 struct TrsvTune {
-  const void* rp;
+  uint64_t fp;  // pattern fingerprint of the factored matrix
   int n, nnz, prec, w, cp, forced, wpb, sched;
 };
 static std::mutex g_trsv_mu;
@@ -1212,7 +1252,7 @@ static int forced_schedule() {
 static bool cached_choice(const mpk_ilu* M, int w, int forced, int* wpb, int* sched) {
   std::lock_guard<std::mutex> lk(g_trsv_mu);
   for (const TrsvTune& t : g_trsv)
-    if (t.rp == M->src_rp && t.n == M->n && t.nnz == M->nnz && t.prec == M->prec && t.w == w && t.cp == M->cp &&
+    if (t.fp == M->pattern_fp && t.n == M->n && t.nnz == M->nnz && t.prec == M->prec && t.w == w && t.cp == M->cp &&
         t.forced == forced) {
       *wpb = t.wpb;
       *sched = t.sched;
@@ -1282,7 +1322,7 @@ int tune_substitution(mpk_ilu* M, const Ops* o, int w, double* r, double* z, cud
   {
     std::lock_guard<std::mutex> lk(g_trsv_mu);
     if (g_trsv.size() < 256)
-      g_trsv.push_back(TrsvTune{M->src_rp, M->n, M->nnz, M->prec, w, M->cp, forced, best_wpb, best_sched});
+      g_trsv.push_back(TrsvTune{M->pattern_fp, M->n, M->nnz, M->prec, w, M->cp, forced, best_wpb, best_sched});
   }
   return ensure_current(M, s);
 }
@@ -1352,8 +1392,13 @@ static int factor_impl(const mpk_csr* A, int prec, int w, mpk_ilu** out, int* fa
   MPK_CUDA(cudaStreamSynchronize(s));
   if (head[0] != 0 || head[1] != nnz) return fail(MPK_INVALID_ARG, "row_ptr[0] must be 0 and row_ptr[n] == nnz");
 
+  uint64_t pfp = 0;
+  {
+    const int st_fp = pattern_fingerprint(n, nnz, A->row_ptr, A->col_idx, &pfp, s);
+    if (st_fp != MPK_OK) return st_fp;
+  }
   mpk_ilu* M = new mpk_ilu();
-  M->src_rp = A->row_ptr;
+  M->pattern_fp = pfp;
   M->n = n;
   M->nnz = nnz;
   M->cp = cp;

@@ -240,6 +240,9 @@ void count_launch(unsigned k = 1);  // every kernel launch of the library is cou
 unsigned long long launch_count();
 void uncount_launch(unsigned long long k);  // launches recorded into a graph run only when it is launched
 void launch_trsv_prep(const IluHandleView& M, const int* done, cudaStream_t s);
+// Fingerprint of a CSR pattern (row_ptr[0..n], col_idx[0..nnz)), synchronises s: the key of the
+// tuning caches (two patterns that differ anywhere collide with probability about 2^-64).
+int pattern_fingerprint(int n, int nnz, const int* rp, const int* ci, uint64_t* out, cudaStream_t s);
 // Pick the substitution kernels' warps per SM for this handle and w by timing the candidates
 // (r, z: scratch vectors of n*c*w doubles); cached per (matrix pattern, factor precision, w, c).
 int tune_substitution(mpk_ilu* M, const Ops* o, int w, double* r, double* z, cudaStream_t s);
@@ -283,7 +286,7 @@ struct mpk_ilu {
   int wpb = 4;                   // warps per SM of the substitution kernels (autotuned per pattern)
   int sched = 0;                 // substitution schedule (autotuned per pattern)
   int withhold = -1;             // testing aid (mpk_ilu0_test_withhold): a row left unpublished
-  const void* src_rp = nullptr;  // the factored matrix's row_ptr address: the tuning cache's key
+  uint64_t pattern_fp = 0;       // fingerprint of the factored matrix's pattern: the tuning cache's key
   mpk::IluHandleView view(bool trans) const;
   int vals_per_entry() const { return cp * wf; }  // doubles (or narrower values) per factor entry
 };

@@ -263,9 +263,8 @@ static int validate_csr(const mpk_csr* A) {
 // ---------------------------------------------------------------------------------------------
 // Autotuner of the SpMV row order.  Candidates: natural order, and rows grouped by length
 // (longest first; counting sort on the row lengths).  Both compute every row in CSR order, so the
-// choice changes timing only.  The decision (and the order) is cached per matrix pattern
-// (row_ptr address, n, nnz, w, c) for the process; any permutation of the rows is a valid order,
-// so a stale entry can only cost speed.
+// choice changes timing only.  The decision (and the order) is cached per matrix pattern (its
+// fingerprint, n, nnz, w, c) for the process.
 // ---------------------------------------------------------------------------------------------
 constexpr int kLenBuckets = 1024;
 __global__ void k_len_hist(int n, const int* __restrict__ rp, int* __restrict__ cnt) {
@@ -289,7 +288,7 @@ __global__ void k_len_scatter(int n, const int* __restrict__ rp, int* __restrict
   }
 }
 struct SpmvTune {
-  const int* rp;
+  uint64_t fp;
   int n, nnz, w, cp;
   int* order;  // nullptr: natural order wins
 };
@@ -297,10 +296,15 @@ static std::mutex g_tune_mu;
 static std::vector<SpmvTune> g_tune;
 
 static const int* spmv_order(const Ops* o, const Csr& A, int w, int cp, double* x, double* y, cudaStream_t s) {
+  uint64_t fp = 0;
+  if (pattern_fingerprint(A.n, A.nnz, A.rp, A.ci, &fp, s) != MPK_OK) {
+    cudaGetLastError();
+    return nullptr;
+  }
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     for (const SpmvTune& t : g_tune)
-      if (t.rp == A.rp && t.n == A.n && t.nnz == A.nnz && t.w == w && t.cp == cp) return t.order;
+      if (t.fp == fp && t.n == A.n && t.nnz == A.nnz && t.w == w && t.cp == cp) return t.order;
   }
   int* order = nullptr;
   int* cnt = nullptr;
@@ -354,7 +358,7 @@ static const int* spmv_order(const Ops* o, const Csr& A, int w, int cp, double* 
     order = nullptr;
   }
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  if (g_tune.size() < 64) g_tune.push_back(SpmvTune{A.rp, A.n, A.nnz, w, cp, order});
+  if (g_tune.size() < 64) g_tune.push_back(SpmvTune{fp, A.n, A.nnz, w, cp, order});
   else if (order != nullptr) {
     // cache full: keep this solve untuned rather than grow without bound
     cudaFree(order);
