@@ -32,6 +32,10 @@
  * Environment variables (none changes a result; all choose how the same operations run):
  *   MPK_SUBST_SCHEDULE=static|owner|cluster8|cluster16  substitution schedule (mpk_ilu0_schedule);
  *                                                        read at every call; default: tuned.
+ *   MPK_SUBST_POLL=lane0|all                             dependency polling of the substitutions
+ *                                                        (lane 0 polls a chunk's latest dependency
+ *                                                        first, or every lane its own); read at
+ *                                                        every call; default: tuned.
  *   MPK_ILU_SCHEDULE=levels|dataflow                     ILU(0) schedule (mpk_ilu0_factor); read
  *                                                        at every factorisation; default: by the
  *                                                        width of the levels.
@@ -209,11 +213,12 @@ int mpk_mp_op(int op, int w, int n, const double* a_dev, const double* b_dev, do
 
 /* Measurement aid: the one-way latency of a cross-SM notification on this GPU -- a strong relaxed
  * store by one SM seen by a strong relaxed polling load on another -- from `rounds` (1..10^6)
- * round trips of a counter between two co-resident blocks (cooperative launch), timed with the
- * device's global timer.  It is the synchronisation cost that the level-scheduled substitutions
- * and ILU(0) pay per level.  *one_way_ns (host) receives the mean one-way time.  Waits are
+ * round trips of a counter between block 0 and block `partner` (1 .. SMs-1) of a cooperative
+ * grid with one block per SM, timed with the device's global timer.  It is the synchronisation
+ * cost that the level-scheduled substitutions and ILU(0) pay per level.  *one_way_ns (host)
+ * receives the mean one-way time; sm_pair (host, nullable) the two blocks' SM ids.  Waits are
  * bounded; MPK_TIMEOUT if one ran out.  Synchronises `stream`. */
-int mpk_probe_notify_ns(int rounds, double* one_way_ns, void* stream);
+int mpk_probe_notify_ns(int rounds, int partner, double* one_way_ns, int* sm_pair, void* stream);
 
 /* ILU(0) of A (Algorithm 1; the "!= 0" tests read as membership in A's stored pattern; the
  * update A_ij -= L_ik U_kj is one fused multiply-add; a zero pivot is an error instead of

@@ -56,7 +56,7 @@ SIGNATURES = [
     ("mpk_dot", _I, [_I, _I, _I, _VP, _VP, _VP, _VP]),
     ("mpk_dot_noalloc", _I, [_I, _I, _I, _VP, _VP, _VP, _VP]),
     ("mpk_mp_op", _I, [_I, _I, _I, _VP, _VP, _VP, _VP]),
-    ("mpk_probe_notify_ns", _I, [_I, ctypes.POINTER(ctypes.c_double), _VP]),
+    ("mpk_probe_notify_ns", _I, [_I, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I), _VP]),
     ("mpk_ilu0_factor", _I, [ctypes.POINTER(CsrDesc), _I, ctypes.POINTER(_VP), ctypes.POINTER(_I), _VP]),
     ("mpk_ilu0_factor_mp", _I, [ctypes.POINTER(CsrDesc), _I, ctypes.POINTER(_VP), ctypes.POINTER(_I), _VP]),
     ("mpk_ilu0_values", _I, [_VP, _VP, _VP]),
@@ -193,11 +193,13 @@ def dot_noalloc(a: torch.Tensor, b: torch.Tensor, n: int, w: int, is_complex=Fal
     return out
 
 
-def probe_notify_ns(rounds=2000) -> float:
-    """One-way cross-SM notification latency in ns (mpk_probe_notify_ns)."""
+def probe_notify_ns(rounds=2000, partner=1, with_sms=False):
+    """One-way cross-SM notification latency in ns between block 0 and block `partner` of a grid
+    with one block per SM (mpk_probe_notify_ns); with_sms: also the two SM ids."""
     v = ctypes.c_double(0.0)
-    _check(lib().mpk_probe_notify_ns(int(rounds), ctypes.byref(v), _stream()))
-    return v.value
+    sms = (_I * 2)()
+    _check(lib().mpk_probe_notify_ns(int(rounds), int(partner), ctypes.byref(v), sms, _stream()))
+    return (v.value, (sms[0], sms[1])) if with_sms else v.value
 
 
 MP_OPS = {"add": 0, "sub": 1, "mul": 2, "mul_fp": 3, "div": 4, "div_fp": 5, "sqrt": 6}

@@ -159,21 +159,22 @@ extern "C" int mpk_mp_op(int op, int w, int n, const double* a_dev, const double
   return MPK_OK;
 }
 
-// Cross-SM notification latency: two co-resident blocks (cooperative launch; each asks for more
-// than half an SM's shared memory, so they sit on different SMs) pass a counter back and forth
-// through one word of global memory with the strong relaxed loads and stores the
-// dependency-driven kernels use.  Block 0 times `rounds` round trips with the global timer.  Every
-// wait is bounded (kProbeSpin polls); a wait that runs out records the failure and both blocks
-// leave.
+// Cross-SM notification latency: block 0 and block `partner` of a cooperative grid of partner + 1
+// blocks (each asks for more than half an SM's shared memory, so every block sits on its own SM)
+// pass a counter back and forth through one word of global memory with the strong relaxed loads
+// and stores the dependency-driven kernels use; the other blocks leave at once.  Block 0 times
+// `rounds` round trips with the global timer.  Every wait is bounded (kProbeSpin polls); a wait
+// that runs out records the failure and both blocks leave.
 constexpr long long kProbeSpin = 1ll << 20;  // about a second of polls
-__global__ void k_probe_hop(int rounds, int* __restrict__ word, unsigned long long* __restrict__ res) {
+__global__ void k_probe_hop(int rounds, int partner, int* __restrict__ word, unsigned long long* __restrict__ res) {
   if (threadIdx.x != 0) return;
-  const int me = blockIdx.x;
+  if (blockIdx.x != 0 && (int)blockIdx.x != partner) return;
+  const int me = blockIdx.x == 0 ? 0 : 1;
   unsigned long long t0 = 0, t1 = 0;
   if (me == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
   bool ok = true;
   for (int r = 0; r < rounds && ok; ++r) {
-    const int want = 2 * r + me;  // block 0 waits for even values, block 1 for odd ones
+    const int want = 2 * r + me;  // block 0 waits for even values, the partner for odd ones
     long long spins = 0;
     int v;
     do {
@@ -197,19 +198,20 @@ __global__ void k_probe_hop(int rounds, int* __restrict__ word, unsigned long lo
   if (!ok) atomicExch(word, -1);  // release the other block's wait
 }
 
-extern "C" int mpk_probe_notify_ns(int rounds, double* one_way_ns, void* stream) {
+extern "C" int mpk_probe_notify_ns(int rounds, int partner, double* one_way_ns, int* sm_pair, void* stream) {
   if (rounds < 1 || rounds > 1000000 || one_way_ns == nullptr) return fail(MPK_INVALID_ARG, "bad argument");
+  if (partner < 1 || partner >= sm_count()) return fail(MPK_INVALID_ARG, "partner must be 1 .. SMs - 1");
   cudaStream_t s = (cudaStream_t)stream;
   char* buf = nullptr;
   MPK_CUDA(cudaMallocAsync((void**)&buf, 64, s));
   int* word = (int*)buf;  // res: elapsed ns, ok, the two blocks' SM ids
   unsigned long long* res = (unsigned long long*)(buf + 16);
   MPK_CUDA(cudaMemsetAsync(buf, 0, 64, s));
-  void* args[] = {(void*)&rounds, (void*)&word, (void*)&res};
+  void* args[] = {(void*)&rounds, (void*)&partner, (void*)&word, (void*)&res};
   constexpr int kSmem = 160 * 1024;  // more than half of an SM: one block per SM
   MPK_CUDA(cudaFuncSetAttribute((const void*)k_probe_hop, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
   count_launch();
-  MPK_CUDA(cudaLaunchCooperativeKernel((const void*)k_probe_hop, dim3(2), dim3(32), args, kSmem, s));
+  MPK_CUDA(cudaLaunchCooperativeKernel((const void*)k_probe_hop, dim3(partner + 1), dim3(32), args, kSmem, s));
   unsigned long long h[4] = {0, 0, 0, 0};
   MPK_CUDA(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, s));
   MPK_CUDA(cudaFreeAsync(buf, s));
@@ -217,5 +219,9 @@ extern "C" int mpk_probe_notify_ns(int rounds, double* one_way_ns, void* stream)
   if (h[1] != 1ull) return fail(MPK_TIMEOUT, "notification probe: a bounded wait ran out");
   if (h[2] == h[3]) return fail(MPK_INVALID_ARG, "notification probe: both blocks ran on one SM");
   *one_way_ns = (double)h[0] / (2.0 * rounds);
+  if (sm_pair != nullptr) {
+    sm_pair[0] = (int)h[2];
+    sm_pair[1] = (int)h[3];
+  }
   return MPK_OK;
 }

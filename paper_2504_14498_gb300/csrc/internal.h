@@ -221,6 +221,8 @@ struct IluHandleView {
   int wpb = 4;                       // warps per block (per SM) of the substitution kernels
   int sched = 0;                     // see kScheds
   int withhold = -1;                 // testing aid: a row whose value is never published
+  int poll = 0;                      // 0: lane 0 polls the chunk's latest dependency, then every lane
+                                     // loads its own; 1: every lane polls its own from the start
 };
 enum CtlIdx : int {
   CTL_EPOCH = 0,
@@ -285,6 +287,7 @@ struct mpk_ilu {
   int* depth[4] = {nullptr, nullptr, nullptr, nullptr};      // level of every row, per triangle
   int wpb = 4;                   // warps per SM of the substitution kernels (autotuned per pattern)
   int sched = 0;                 // substitution schedule (autotuned per pattern)
+  int poll = 0;                  // dependency polling of the substitutions (autotuned; see IluHandleView)
   int withhold = -1;             // testing aid (mpk_ilu0_test_withhold): a row left unpublished
   uint64_t pattern_fp = 0;       // fingerprint of the factored matrix's pattern: the tuning cache's key
   mpk::IluHandleView view(bool trans) const;

@@ -1211,7 +1211,7 @@ __device__ __forceinline__ bool mp_finish(const SellTri& T, const IluHandleView&
   bool timeout = false;
   const long long t0 = clock64();
   int polls = 0;
-  if (lane == 0 && c.rep >= 0) {  // the chunk's latest dependency, polled by one lane
+  if (lane == 0 && c.rep >= 0 && M.poll == 0) {  // the chunk's latest dependency, polled by one lane
     N<W, CP> r;
     while (!n_poll<W, CP>(out, c.rep, r)) {
       if (wait_expired(t0, polls, M.ctl)) { timeout = true; break; }
@@ -1241,7 +1241,10 @@ __device__ __forceinline__ bool mp_finish(const SellTri& T, const IluHandleView&
         if (((need >> k) & 1u) && n_ready<W, CP>(v[k])) got |= 1u << k;
       need &= ~got;
       if (need != 0u && !timeout && wait_expired(t0, polls, M.ctl)) timeout = true;
-      if (__any_sync(FULL, need != 0u)) __nanosleep(64);
+      if (__any_sync(FULL, need != 0u)) {
+        if (M.poll == 1) wait_pause(t0, 64);
+        else __nanosleep(64);
+      }
     }
     __syncwarp();
     if (!timeout && c.i >= 0) {
@@ -1285,6 +1288,122 @@ __global__ void __launch_bounds__(WPB * 32, 1)
     if (mp_finish<W, CP, MF, false>(T, M, unit, out, c, RingRef(), 0)) {
       if (lane == 0) atomicCAS(M.ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
       return;
+    }
+  }
+}
+
+// Complex substitution with a binary64 factor, each 32-row chunk shared by a pair of warps of one
+// block (consecutive warps, so different sub-partitions): the even warp computes the real parts
+// of the chunk's rows, the odd warp the imaginary parts.  Every step is the one the single-warp
+// kernel performs for that part -- the product's part re = a.re fr - a.im fi or
+// im = a.im fr + a.re fi, then acc_part - product_part, in CSR order -- so the results are the
+// same bits; the division by the diagonal needs both parts of the accumulator, which the two
+// warps exchange through shared memory (double-buffered, one named barrier per chunk).  A binary64
+// warp instruction costs its sub-partition 64 cycles however many lanes run, so splitting a row's
+// chain over two sub-partitions halves the time of a narrow level.  Both warps poll the chunk's
+// dependencies (both parts of each value are needed) and publish their own part; a consumer sees
+// a value once all its words are published.  Deadlock-free as the single-warp kernel (pairs walk
+// their chunks in increasing order, dependencies lie in earlier chunks); a timed-out wait ends
+// both warps of the pair after the barrier they share.
+__device__ __forceinline__ void pair_barrier(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(64) : "memory");
+}
+template <int W, int WPB>
+__global__ void __launch_bounds__(WPB * 32, 1)
+    k_trsv_mp_cx(IluHandleView M, bool lower, bool unit, const double* __restrict__ in, double* __restrict__ out,
+                 const int* __restrict__ done) {
+  static_assert(WPB % 2 == 0 && WPB / 2 <= 14, "pairs of warps, named barriers 1..14");
+  constexpr int CP = 2, NP = WPB / 2;
+  constexpr int KG = MpChunk<W, CP, false>::KG;
+  __shared__ __align__(16) double xch[2][NP][2][W][32];  // [buffer][pair][part][component][lane]
+  __shared__ int xto[2][NP][2];                           // timeout flags, same buffering
+  if (is_done(done)) return;
+  const SellTri T = lower ? M.sl_lo : M.sl_up;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int pair = warp >> 1, part = warp & 1;
+  const int G = gridDim.x * NP;
+  const int g = pair * gridDim.x + blockIdx.x;
+  MpChunk<W, CP, false> c, nx;
+  if (g < T.nchunks) mp_meta<W, CP, false>(T, g, nx);
+  int buf = 0;
+  for (int chunk = g; chunk < T.nchunks; chunk += G) {
+    c.i = nx.i;
+    c.b0 = nx.b0;
+    c.w = nx.w;
+    c.rep = nx.rep;
+    mp_operands<W, CP, false>(T, unit, in, chunk, c);
+    if (chunk + G < T.nchunks) mp_meta<W, CP, false>(T, chunk + G, nx);
+    bool timeout = false;
+    const long long t0 = clock64();
+    int polls = 0;
+    if (lane == 0 && c.rep >= 0) {
+      N<W, CP> r;
+      while (!n_poll<W, CP>(out, c.rep, r)) {
+        if (wait_expired(t0, polls, M.ctl)) { timeout = true; break; }
+        wait_pause(t0, 128);
+      }
+    }
+    timeout = __any_sync(FULL, timeout);
+    R<W> acc = part == 0 ? c.acc.re : c.acc.im;
+    for (int k0 = 0; k0 < c.w && !timeout; k0 += KG) {
+      if (k0 > 0) mp_group<W, CP, false>(T, k0, c);
+      N<W, CP> v[KG];
+      unsigned need = 0u;
+#pragma unroll
+      for (int k = 0; k < KG; ++k) {
+        v[k] = n_zero<W, CP>();
+        if (c.jj[k] >= 0) need |= 1u << k;
+      }
+      while (__any_sync(FULL, need != 0u && !timeout)) {
+#pragma unroll
+        for (int k = 0; k < KG; ++k)
+          if ((need >> k) & 1u) n_fetch<W, CP>(out, c.jj[k], v[k]);
+        unsigned got = 0u;
+#pragma unroll
+        for (int k = 0; k < KG; ++k)
+          if (((need >> k) & 1u) && n_ready<W, CP>(v[k])) got |= 1u << k;
+        need &= ~got;
+        if (need != 0u && !timeout && wait_expired(t0, polls, M.ctl)) timeout = true;
+        if (__any_sync(FULL, need != 0u)) __nanosleep(64);
+      }
+      timeout = __any_sync(FULL, timeout);
+      if (!timeout && c.i >= 0) {
+#pragma unroll
+        for (int k = 0; k < KG; ++k) {
+          if (c.jj[k] == -1) continue;
+          const R<W> p = part == 0 ? sub<W>(mul_fp<W>(v[k].re, c.fr[k]), mul_fp<W>(v[k].im, c.fi[k]))
+                                   : add<W>(mul_fp<W>(v[k].im, c.fr[k]), mul_fp<W>(v[k].re, c.fi[k]));
+          acc = sub<W>(acc, p);
+        }
+      }
+    }
+    if (!unit) {  // the division needs the partner's part: exchange, then each warp its own part
+#pragma unroll
+      for (int k = 0; k < W; ++k) xch[buf][pair][part][k][lane] = acc.c[k];
+      if (lane == 0) xto[buf][pair][part] = timeout ? 1 : 0;
+      pair_barrier(1 + pair);
+      timeout = timeout || xto[buf][pair][part ^ 1] != 0;
+      if (!timeout && c.i >= 0) {
+        R<W> other;
+#pragma unroll
+        for (int k = 0; k < W; ++k) other.c[k] = xch[buf][pair][part ^ 1][k][lane];
+        const R<W> are = part == 0 ? acc : other, aim = part == 0 ? other : acc;
+        const R<W> den = add<W>(mul_fp<W>(r_from<W>(c.dr), c.dr), mul_fp<W>(r_from<W>(c.di), c.di));
+        const R<W> num = part == 0 ? add<W>(mul_fp<W>(are, c.dr), mul_fp<W>(aim, c.di))
+                                   : sub<W>(mul_fp<W>(aim, c.dr), mul_fp<W>(are, c.di));
+        acc = div<W>(num, den);
+      }
+      buf ^= 1;
+    }
+    if (timeout) {
+      if (lane == 0) atomicCAS(M.ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
+      return;
+    }
+    if (c.i >= 0 && c.i != M.withhold) {
+      double* p = out + (int64_t)c.i * (CP * W) + part * W;
+#pragma unroll
+      for (int k = 0; k < W; ++k) st_relaxed_f64(p + k, acc.c[k]);
     }
   }
 }
@@ -1534,7 +1653,7 @@ __device__ __forceinline__ bool lp_finish(const SellTri& T, const IluHandleView&
   bool timeout = false;
   const long long t0 = clock64();
   int polls = 0;
-  if (lane == 0 && c.rep >= 0) {  // the chunk's latest dependency, polled by one lane
+  if (lane == 0 && c.rep >= 0 && M.poll == 0) {  // the chunk's latest dependency, polled by one lane
     float xr, xi;
     while (!f_poll<CP>(mine, c.rep, xr, xi)) {
       if (wait_expired(t0, polls, M.ctl)) { timeout = true; break; }
@@ -1572,7 +1691,10 @@ __device__ __forceinline__ bool lp_finish(const SellTri& T, const IluHandleView&
           got |= 1u << k;
       need &= ~got;
       if (need != 0u && !timeout && wait_expired(t0, polls, M.ctl)) timeout = true;
-      if (__any_sync(FULL, need != 0u)) __nanosleep(64);
+      if (__any_sync(FULL, need != 0u)) {
+        if (M.poll == 1) wait_pause(t0, 64);
+        else __nanosleep(64);
+      }
     }
     __syncwarp();
     if (!timeout && c.i >= 0) {
@@ -1911,6 +2033,14 @@ struct Launch {
         default: return (const void*)k_trsv_mp_ob<W, CP, 4, MF>;
       }
     } else {
+      if constexpr (CP == 2 && !MF) {  // complex, binary64 factor: a pair of warps per chunk
+        switch (wpb) {
+          case 8: return (const void*)k_trsv_mp_cx<W, 8>;
+          case 16: return (const void*)k_trsv_mp_cx<W, 16>;
+          case 32: return (const void*)k_trsv_mp<W, CP, 32, MF>;
+          default: return (const void*)k_trsv_mp_cx<W, 4>;
+        }
+      }
       switch (wpb) {
         case 8: return (const void*)k_trsv_mp<W, CP, 8, MF>;
         case 16: return (const void*)k_trsv_mp<W, CP, 16, MF>;

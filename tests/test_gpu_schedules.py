@@ -107,3 +107,24 @@ def test_auto_tuner_picks_a_schedule(monkeypatch):
     sched, wpb = M.schedule()
     assert out["status"] == "OK" and sched in ("static", "owner") and wpb in (4, 8, 16, 32)
     print("tuned schedule at 32^3:", sched, wpb)
+
+
+@pytest.mark.parametrize("poll", ["lane0", "all"])
+@pytest.mark.parametrize("mat", ["convdiff3d", "helmholtz", "random_cplx"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_precond_both_polling_modes(monkeypatch, poll, mat, prec):
+    """The substitutions' two ways of waiting for dependencies (lane 0 on the chunk's latest one,
+    or every lane on its own) give the oracle's bits, M and M^H (the complex binary64 factor runs
+    the paired-warp kernel, real and imaginary parts on two sub-partitions)."""
+    monkeypatch.setenv("MPK_SUBST_SCHEDULE", "static")
+    monkeypatch.setenv("MPK_SUBST_POLL", poll)
+    A_t, c = MATS[mat]()
+    n = A_t[0]
+    A = _lib.Matrix.from_tuple(A_t, is_complex=(c == 2))
+    M = _lib.ILU0(A, prec)
+    fac = oracle.ilu0(A_t, prec, c)[1]
+    for trans in (False, True):
+        for w in (1, 2):
+            r = inputs.random_vector(n, w, c, seed=90 + w)
+            z = host(M.apply(dev(r), w, trans))
+            assert np.array_equal(z, oracle.precond(A_t, fac, r, w, prec, c, trans)), (trans, w)
