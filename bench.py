@@ -44,7 +44,7 @@ FP64_PEAK_OPS = 152 * 4 * 0.5 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one k_trsv_mp launch pair (both triangles, static schedule) on the
 # 128^3 workload: dram__bytes_read.sum + dram__bytes_write.sum from an ncu capture of the current
 # kernel (its summary is under profiles/); None once the kernel changes.
-TRSV_MP_TRAFFIC = 151249152 + 18557952 + 168018688 + 17200128
+TRSV_MP_TRAFFIC = 151203840 + 18551552 + 167994112 + 17050112
 # binary64 warp instructions one 32-row chunk of the binary64-factor DD substitution issues on
 # its chain (lower unit triangle, upper triangle with the division), from an ncu count of the
 # static-schedule kernel on the 7-point matrix (sm__inst_executed_pipe_fp64 / chunks; summary
@@ -470,7 +470,10 @@ def run_mpk(args):
     t_pre64 = time_launches(lambda: M64.apply(x, w, False, z), reps=10, warm=3)
     t_pre32 = time_launches(lambda: M32.apply(x, w, False, z), reps=10, warm=3)
     levels = (M64.levels(0)[0], M64.levels(1)[0])
-    hop_ns = statistics.median(_lib.probe_notify_ns(2000) for _ in range(3))
+    # notification latency: mean over block 0 paired with every 10th SM of the grid (measured on
+    # GB300: 225 ns between nearby SMs, 365-430 ns to the others, no slower class across dies)
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    hop_ns = statistics.mean(_lib.probe_notify_ns(500, p_) for p_ in range(1, nsm, 10))
     M64.close()
     M32.close()
     hbm = float(pk.get("hbm_gbs", 6800.0))
@@ -485,7 +488,7 @@ def run_mpk(args):
     # DW/FP 10 (two divisions counted as one operation each)
     spmv_ops = 20 * nnz
     spmv1_bytes = 12 * nnz + 4 * (n + 1) + 2 * 8 * n
-    spmv1_ops = 2 * nnz  # D: one multiply and one add per entry (no contraction)
+    spmv1_ops = nnz  # real D: one fused multiply-add per entry
     spmv4_bytes = 12 * nnz + 4 * (n + 1) + 2 * 32 * n
     pre64_ops = 20 * nod + 10 * n
     alu = FP64_PEAK_OPS

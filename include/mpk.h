@@ -156,7 +156,7 @@ uint64_t mpk_kernel_launches(void);
 
 /* y = A x (Sec. 3 "mixed-precision SpMV": binary64 A, w-component vectors).  Row i is
  * accumulated in CSR order from 0: y_i = (((0 + a_i,j1 x_j1) + a_i,j2 x_j2) + ...), each
- * product and sum in w-component arithmetic.  x_dev, y_dev: n*c*w doubles (c from A), must
+ * product and sum in w-component arithmetic (real D: one fused multiply-add per entry).  x_dev, y_dev: n*c*w doubles (c from A), must
  * not overlap. */
 int mpk_spmv_mp(const mpk_csr* A, int w, const double* x_dev, double* y_dev, void* stream);
 

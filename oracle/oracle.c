@@ -435,7 +435,8 @@ static num n_div_d(num x, double fr, double fi, ctx t) {
 static int n_is_zero(num a) { return a.re.c[0] == 0.0 && a.im.c[0] == 0.0; }
 
 /* ------------------------------------------------------------------------------------------
- * Vector kernels: mixed SpMV y = A x (binary64 matrix, MP vector; CSR order, starting from 0),
+ * Vector kernels: mixed SpMV y = A x (binary64 matrix, MP vector; CSR order, starting from 0; a
+ * real D row accumulates each entry with one fused multiply-add, acc := fma(a_ij, x_j, acc)),
  * inner product <a,b> = sum conj(a_i) b_i (sequential), 2-norm = sqrt(Re <r,r>).
  * With t.mm the matrix entry is first promoted to a w-component number (a, 0, ..., 0) -- the
  * value is unchanged, the paper's matrices being binary64 -- and the product is the format's
@@ -453,7 +454,9 @@ static void spmv(int n, const int *rp, const int *ci, const double *val, ctx t, 
       num xj = n_load(x + (size_t)ci[p] * s, t);
       double ar = t.c == 2 ? val[2 * (size_t)p] : val[p];
       double ai = t.c == 2 ? val[2 * (size_t)p + 1] : 0.0;
-      if (t.mm) {
+      if (t.w == 1 && t.c == 1) {
+        acc.re.c[0] = fma(ar, xj.re.c[0], acc.re.c[0]); /* D, real: one fused multiply-add per entry */
+      } else if (t.mm) {
         num a = n_zero();
         a.re.c[0] = ar;
         a.im.c[0] = ai;

@@ -51,7 +51,8 @@ __device__ __forceinline__ N<W, CP> warp_sum(N<W, CP> a) {  // fixed tree order
 }
 
 // ---------------------------------------------------------------------------------------------
-// y = A x  (b != nullptr: y = b - A x), one thread per row, CSR order from 0.
+// y = A x  (b != nullptr: y = b - A x), one thread per row, CSR order from 0.  A real D row
+// accumulates each entry with one fused multiply-add (one binary64 instruction per nonzero).
 // ---------------------------------------------------------------------------------------------
 // A batch (sysid != nullptr) skips the rows of systems whose state sst has ST_DONE set, or, with
 // gate >= 0, a nonzero sst[gate].
@@ -87,7 +88,9 @@ __global__ void __launch_bounds__(kBlock) k_spmv(int n, const int* __restrict__ 
       ar = v.x;
       ai = v.y;
     }
-    if constexpr (MM) {
+    if constexpr (W == 1 && CP == 1) {
+      acc.re.c[0] = fma(ar, x[j], acc.re.c[0]);  // D, real: one fused multiply-add per entry
+    } else if constexpr (MM) {
       N<W, CP> a = n_zero<W, CP>();
       a.re.c[0] = ar;
       a.im.c[0] = ai;
