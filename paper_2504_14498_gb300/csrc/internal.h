@@ -48,6 +48,7 @@ constexpr int kSlotDoubles = 8;
 enum StateIdx : int {
   ST_DONE = 0, ST_STATUS, ST_ITERS, ST_IT, ST_MAXIT, ST_FLAGS,
   ST_PERIOD, ST_NOCHK, ST_NOREPL, ST_CHECK, ST_CHK_IT, ST_NREP,
+  ST_TRUEKNOWN,  // 1: the solve ended on an accepted check, whose true norm is already in S_D4
   ST_COUNT
 };
 

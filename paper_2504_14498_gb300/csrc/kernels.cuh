@@ -454,6 +454,9 @@ __global__ void k_scalar(int method, int phase, double* __restrict__ S, int* __r
   if (done != nullptr && sst[ST_DONE] != 0) return;
   scalar_phase<W, CP>(method, phase, S + (int64_t)sy * kSysDoubles, sst,
                       hist != nullptr ? hist + (int64_t)sy * hist_stride : nullptr);
+  // batch: a system that asked for a replacement check opens the check launches' gate, the word
+  // after *alldone (cleared again at the end of the check)
+  if (alldone != nullptr && phase == PH_NORM && sst[ST_NOCHK] == 0) alldone[1] = 0;
   if (fin != nullptr && sst[ST_DONE] != 0 && atomicAdd(fin, 1) == nsys - 1) *alldone = 1;
 }
 template <int W, int CP>
@@ -485,6 +488,7 @@ __device__ void scalar_phase(int method, int phase, double* __restrict__ S, int*
       break;
     }
     case PH_TRUE: {  // ||b - A x|| of the final iterate (S_D5) into S_D4 component 0
+      if (st[ST_TRUEKNOWN] != 0) break;  // already there from the accepted check
       R<W> nr = rsqrt_mp<W>(slot<W, CP>(S, S_D5).re);
       S[S_D4 * kSlotDoubles] = nr.c[0];
       break;
@@ -590,6 +594,8 @@ __device__ void scalar_phase(int method, int phase, double* __restrict__ S, int*
         st[ST_NREP] += 1;
         if (passed) after_norm<W, CP>(method, S, st, k);
       } else if (passed) {
+        S[S_D4 * kSlotDoubles] = nt.c[0];  // the final true norm: no recomputation after the loop
+        st[ST_TRUEKNOWN] = 1;
         finish(st, MPK_OK, k);
       }
       break;

@@ -26,6 +26,9 @@ int transpose_matrix(const Csr& A, int* rpT, int* ciT, double* vT, cudaStream_t 
 
 using namespace mpk;
 
+// one word of device state set from the stream (graph-capturable)
+__global__ void k_set_flag(int* p, int v) { *p = v; }
+
 namespace {
 
 // A solve of nsys systems (nsys == 1: the plain single-system solve; a batch otherwise, with
@@ -97,16 +100,21 @@ struct Ctx {
     if (period <= 0) return;
     const double* av[1] = {rtrue};
     if (bt) {
+      // every launch leaves at once unless some system asked for a check (nopend == 0); within
+      // them, the systems that did not are skipped by their own state words
+      int* nopend = alldone + 1;
       Batch g = *bt;
       g.gate = ST_NOCHK;
-      o->spmv(A, x, rtrue, b, done, &g, s);
-      o->dots_seg(g, 1, av, av, S, S_D5, seg_partial, seg_counters, done, s);
-      o->scalar(method, PH_TRUECHK, S, st, hist_true, done, nsys(), hist_stride, fin, alldone, s);
+      o->spmv(A, x, rtrue, b, nopend, &g, s);
+      o->dots_seg(g, 1, av, av, S, S_D5, seg_partial, seg_counters, nopend, s);
+      o->scalar(method, PH_TRUECHK, S, st, hist_true, nopend, nsys(), hist_stride, fin, alldone, s);
       Batch gr = *bt;
       gr.gate = ST_NOREPL;
       const double* coef[1] = {nullptr};
       const double* v[1] = {rtrue};
-      o->lincomb(n, r, 1, coef, v, nullptr, done, &gr, s);
+      o->lincomb(n, r, 1, coef, v, nullptr, nopend, &gr, s);
+      count_launch();
+      k_set_flag<<<1, 1, 0, s>>>(nopend, 1);
       return;
     }
     const int* g1 = st + ST_NOCHK;
@@ -523,7 +531,9 @@ static int solve_impl(int method, int w, const mpk_csr* Ac, const mpk_ilu* Mc, c
   double* partial = (double*)tail;
   tail += part_bytes;
   c.st = (int*)tail;
-  int* gstate = c.st + (size_t)ST_COUNT * nsys;  // [0] finished systems, [1] all finished
+  // [0] finished systems, [1] all finished, [2] no replacement check pending in any system (the
+  // gate of the batch's check launches; k_scalar's PH_NORM clears it at alldone + 1)
+  int* gstate = c.st + (size_t)ST_COUNT * nsys;
   tail += st_bytes;
   unsigned* counters = (unsigned*)tail;
   tail += cnt_bytes;
@@ -613,8 +623,11 @@ static int solve_impl(int method, int w, const mpk_csr* Ac, const mpk_ilu* Mc, c
       q[ST_CHECK] = 0;
       q[ST_CHK_IT] = 0;
       q[ST_NREP] = 0;
+      q[ST_TRUEKNOWN] = 0;
     }
     MPK_CUDA(cudaMemcpyAsync(c.st, st_init.data(), sizeof(int) * st_init.size(), cudaMemcpyHostToDevice, s));
+    const int one = 1;
+    MPK_CUDA(cudaMemcpyAsync(gstate + 2, &one, sizeof(int), cudaMemcpyHostToDevice, s));
     std::vector<double> tolv((size_t)2 * nsys);
     for (int sy = 0; sy < nsys; ++sy) {
       tolv[2 * sy] = opts->tol_rel;
@@ -719,18 +732,23 @@ static int solve_impl(int method, int w, const mpk_csr* Ac, const mpk_ilu* Mc, c
   int dev_err = MPK_OK;
   if (M != nullptr) dev_err = read_ctl_err(M, s);
 
-  // true residual b - A x with the final x (no done-gating: every system)
-  o->spmv(c.A, x, V[16], b, nullptr, nullptr, s);
+  // true residual b - A x with the final x, for every system that did not end on an accepted
+  // replacement check (those have it already).  The batch launches skip a system through the
+  // state word they read as ST_DONE, here shifted to ST_TRUEKNOWN (every system is done now).
   {
     const double* av[1] = {V[16]};
     const double* bv[1] = {V[16]};
     if (batched) {
       Batch all = bt;
-      all.st = nullptr;
+      all.st = c.st + (ST_TRUEKNOWN - ST_DONE);
+      all.gate = -1;
+      o->spmv(c.A, x, V[16], b, nullptr, &all, s);
       o->dots_seg(all, 1, av, bv, c.S, S_D5, partial, counters, nullptr, s);
     } else {
+      const int* known = c.st + ST_TRUEKNOWN;
+      o->spmv(c.A, x, V[16], b, known, nullptr, s);
       double* ov[1] = {c.slot(S_D5)};
-      o->dots(n, 1, av, bv, ov, c.dws, nullptr, s);
+      o->dots(n, 1, av, bv, ov, c.dws, known, s);
     }
     o->scalar(method, PH_TRUE, c.S, c.st, nullptr, nullptr, nsys, 0, nullptr, nullptr, s);
   }
