@@ -151,25 +151,54 @@ __device__ __forceinline__ float upd_pre(const float* sWu, const float* sbu, flo
   return q;
 }
 
+// Forward message layer.  Lane k keeps column k of the message and update weights in registers,
+// and a warp evaluates the messages of up to kEU stored entries of its row at once (independent
+// multiply-add chains, their neighbour rows loaded together); each message is the same chain
+// msg_pre evaluates, and the messages are summed in CSR order, so the result is that of one entry
+// at a time.
+constexpr int kEU = 4;
 __global__ void __launch_bounds__(kThreads) k_layer(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                                     const float4* __restrict__ xe, const float* __restrict__ PL,
                                                     const __nv_bfloat16* __restrict__ hin,
                                                     __nv_bfloat16* __restrict__ aout, __nv_bfloat16* __restrict__ hout) {
-  __shared__ float sWm[(H + FE) * kStride], sbm[H], sWu[2 * H * kStride], sbu[H];
-  load_w(sWm, PL + L_WM, H + FE);
+  __shared__ float sWu[2 * H * kStride], sbu[H];
   load_w(sWu, PL + L_WU, 2 * H);
-  for (int t = threadIdx.x; t < H; t += blockDim.x) {
-    sbm[t] = PL[L_BM + t];
-    sbu[t] = PL[L_BU + t];
-  }
+  for (int t = threadIdx.x; t < H; t += blockDim.x) sbu[t] = PL[L_BU + t];
   __syncthreads();
   const int k = threadIdx.x & 31;
+  float wm[H + FE];
+#pragma unroll
+  for (int l = 0; l < H + FE; ++l) wm[l] = PL[L_WM + l * H + k];
+  const float bm = PL[L_BM + k];
   for (int i = warp_id_global(); i < n; i += warps_total()) {
     float acc = 0.0f;
-    for (int p = rp[i]; p < rp[i + 1]; ++p) {
-      const int j = ci[p];
-      if (j == i) continue;
-      acc += fmaxf(msg_pre(sWm, sbm, bf(hin[(int64_t)j * H + k]), xe[p], k), 0.0f);
+    const int p1 = rp[i + 1];
+    for (int p = rp[i]; p < p1; p += kEU) {
+      int j[kEU];
+      float hj[kEU], pre[kEU];
+      float4 e[kEU];
+#pragma unroll
+      for (int u = 0; u < kEU; ++u) {
+        j[u] = p + u < p1 ? ci[p + u] : i;
+        hj[u] = bf(hin[(int64_t)j[u] * H + k]);
+        e[u] = p + u < p1 ? xe[p + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+        pre[u] = bm;
+      }
+#pragma unroll
+      for (int l = 0; l < H; ++l) {
+#pragma unroll
+        for (int u = 0; u < kEU; ++u) pre[u] = fmaf(wm[l], shfl(hj[u], l), pre[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < kEU; ++u) {
+        pre[u] = fmaf(wm[H + 0], e[u].x, pre[u]);
+        pre[u] = fmaf(wm[H + 1], e[u].y, pre[u]);
+        pre[u] = fmaf(wm[H + 2], e[u].z, pre[u]);
+        pre[u] = fmaf(wm[H + 3], e[u].w, pre[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < kEU; ++u)
+        if (p + u < p1 && j[u] != i) acc += fmaxf(pre[u], 0.0f);
     }
     const __nv_bfloat16 ab = tobf(acc);
     aout[(int64_t)i * H + k] = ab;
@@ -192,22 +221,52 @@ __device__ __forceinline__ float dec_pre(const float* sWd, const float* sbd, flo
   return pre;
 }
 
+// Forward decoder, one output per stored entry: column k of the decoder weights in registers,
+// kEU entries of the row at once; each output is the chain dec_pre evaluates.
 __global__ void __launch_bounds__(kThreads) k_decode(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                                      const float4* __restrict__ xe, const float* __restrict__ PD,
                                                      const __nv_bfloat16* __restrict__ h, float* __restrict__ o) {
-  __shared__ float sWd[(2 * H + FE) * kStride], sbd[H];
-  load_w(sWd, PD + D_WD, 2 * H + FE);
-  for (int t = threadIdx.x; t < H; t += blockDim.x) sbd[t] = PD[D_BD + t];
-  __syncthreads();
   const int k = threadIdx.x & 31;
-  const float wo = PD[D_WO + k], bo = PD[D_BO];
+  float wd[2 * H + FE];
+#pragma unroll
+  for (int l = 0; l < 2 * H + FE; ++l) wd[l] = PD[D_WD + l * H + k];
+  const float bd = PD[D_BD + k], wo = PD[D_WO + k], bo = PD[D_BO];
   for (int i = warp_id_global(); i < n; i += warps_total()) {
     const float hi = bf(h[(int64_t)i * H + k]);
-    for (int p = rp[i]; p < rp[i + 1]; ++p) {
-      const int j = ci[p];
-      const float pre = dec_pre(sWd, sbd, hi, bf(h[(int64_t)j * H + k]), xe[p], k);
-      const float out = warp_sum(wo * fmaxf(pre, 0.0f)) + bo;
-      if (k == 0) o[p] = out;
+    const int p1 = rp[i + 1];
+    for (int p = rp[i]; p < p1; p += kEU) {
+      float hj[kEU], pre[kEU];
+      float4 e[kEU];
+#pragma unroll
+      for (int u = 0; u < kEU; ++u) {
+        const int j = p + u < p1 ? ci[p + u] : i;
+        hj[u] = bf(h[(int64_t)j * H + k]);
+        e[u] = p + u < p1 ? xe[p + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+        pre[u] = bd;
+      }
+#pragma unroll
+      for (int l = 0; l < H; ++l) {
+        const float hl = shfl(hi, l);
+#pragma unroll
+        for (int u = 0; u < kEU; ++u) pre[u] = fmaf(wd[l], hl, pre[u]);
+      }
+#pragma unroll
+      for (int l = 0; l < H; ++l) {
+#pragma unroll
+        for (int u = 0; u < kEU; ++u) pre[u] = fmaf(wd[H + l], shfl(hj[u], l), pre[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < kEU; ++u) {
+        pre[u] = fmaf(wd[2 * H + 0], e[u].x, pre[u]);
+        pre[u] = fmaf(wd[2 * H + 1], e[u].y, pre[u]);
+        pre[u] = fmaf(wd[2 * H + 2], e[u].z, pre[u]);
+        pre[u] = fmaf(wd[2 * H + 3], e[u].w, pre[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < kEU; ++u) {
+        const float out = warp_sum(wo * fmaxf(pre[u], 0.0f)) + bo;
+        if (k == 0 && p + u < p1) o[p + u] = out;
+      }
     }
   }
 }
