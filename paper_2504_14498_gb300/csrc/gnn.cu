@@ -151,69 +151,16 @@ __device__ __forceinline__ float upd_pre(const float* sWu, const float* sbu, flo
   return q;
 }
 
-// Forward message layer.  Lane k keeps column k of the message and update weights in registers,
-// and a warp evaluates the messages of up to kEU stored entries of its row at once (independent
-// multiply-add chains, their neighbour rows loaded together); each message is the same chain
-// msg_pre evaluates, and the messages are summed in CSR order, so the result is that of one entry
-// at a time.
-constexpr int kEU = 4;
-__global__ void __launch_bounds__(kThreads) k_layer(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                                                    const float4* __restrict__ xe, const float* __restrict__ PL,
-                                                    const __nv_bfloat16* __restrict__ hin,
-                                                    __nv_bfloat16* __restrict__ aout, __nv_bfloat16* __restrict__ hout) {
-  __shared__ float sWu[2 * H * kStride], sbu[H];
-  load_w(sWu, PL + L_WU, 2 * H);
-  for (int t = threadIdx.x; t < H; t += blockDim.x) sbu[t] = PL[L_BU + t];
-  __syncthreads();
-  const int k = threadIdx.x & 31;
-  float wm[H + FE];
-#pragma unroll
-  for (int l = 0; l < H + FE; ++l) wm[l] = PL[L_WM + l * H + k];
-  const float bm = PL[L_BM + k];
-  for (int i = warp_id_global(); i < n; i += warps_total()) {
-    float acc = 0.0f;
-    const int p1 = rp[i + 1];
-    for (int p = rp[i]; p < p1; p += kEU) {
-      int j[kEU];
-      float hj[kEU], pre[kEU];
-      float4 e[kEU];
-#pragma unroll
-      for (int u = 0; u < kEU; ++u) {
-        j[u] = p + u < p1 ? ci[p + u] : i;
-        hj[u] = bf(hin[(int64_t)j[u] * H + k]);
-        e[u] = p + u < p1 ? xe[p + u] : make_float4(0.f, 0.f, 0.f, 0.f);
-        pre[u] = bm;
-      }
-#pragma unroll
-      for (int l = 0; l < H; ++l) {
-#pragma unroll
-        for (int u = 0; u < kEU; ++u) pre[u] = fmaf(wm[l], shfl(hj[u], l), pre[u]);
-      }
-#pragma unroll
-      for (int u = 0; u < kEU; ++u) {
-        pre[u] = fmaf(wm[H + 0], e[u].x, pre[u]);
-        pre[u] = fmaf(wm[H + 1], e[u].y, pre[u]);
-        pre[u] = fmaf(wm[H + 2], e[u].z, pre[u]);
-        pre[u] = fmaf(wm[H + 3], e[u].w, pre[u]);
-      }
-#pragma unroll
-      for (int u = 0; u < kEU; ++u)
-        if (p + u < p1 && j[u] != i) acc += fmaxf(pre[u], 0.0f);
-    }
-    const __nv_bfloat16 ab = tobf(acc);
-    aout[(int64_t)i * H + k] = ab;
-    const float hi = bf(hin[(int64_t)i * H + k]);
-    const float q = upd_pre(sWu, sbu, hi, bf(ab), k);
-    hout[(int64_t)i * H + k] = tobf(hi + fmaxf(q, 0.0f));
-  }
-}
-
+// The decoder's pre-activation of entry (i, j): the h_i part (with the bias) and the h_j part are
+// two separate chains, added, then the edge terms.  The forward pass tabulates both parts per
+// node (k_node<NODE_PQ>); this per-entry form, used by the backward pass, gives the same bits.
 __device__ __forceinline__ float dec_pre(const float* sWd, const float* sbd, float hi, float hj, float4 e, int k) {
-  float pre = sbd[k];
+  float pi = sbd[k], qj = 0.0f;
 #pragma unroll
-  for (int l = 0; l < H; ++l) pre = fmaf(sWd[l * kStride + k], shfl(hi, l), pre);
+  for (int l = 0; l < H; ++l) pi = fmaf(sWd[l * kStride + k], shfl(hi, l), pi);
 #pragma unroll
-  for (int l = 0; l < H; ++l) pre = fmaf(sWd[(H + l) * kStride + k], shfl(hj, l), pre);
+  for (int l = 0; l < H; ++l) qj = fmaf(sWd[(H + l) * kStride + k], shfl(hj, l), qj);
+  float pre = pi + qj;
   pre = fmaf(sWd[(2 * H + 0) * kStride + k], e.x, pre);
   pre = fmaf(sWd[(2 * H + 1) * kStride + k], e.y, pre);
   pre = fmaf(sWd[(2 * H + 2) * kStride + k], e.z, pre);
@@ -221,52 +168,167 @@ __device__ __forceinline__ float dec_pre(const float* sWd, const float* sbd, flo
   return pre;
 }
 
-// Forward decoder, one output per stored entry: column k of the decoder weights in registers,
-// kEU entries of the row at once; each output is the chain dec_pre evaluates.
-__global__ void __launch_bounds__(kThreads) k_decode(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                                                     const float4* __restrict__ xe, const float* __restrict__ PD,
-                                                     const __nv_bfloat16* __restrict__ h, float* __restrict__ o) {
-  const int k = threadIdx.x & 31;
-  float wd[2 * H + FE];
+// Node-level products of the forward pass.  The node-state part of a message, Wm^T h_j + bm,
+// depends on j alone, so it is formed once per node (NODE_G) instead of once per stored entry,
+// with the chain msg_pre uses (bias, then the H inputs in order): the per-entry kernel then only
+// adds the edge terms and gives the bits of msg_pre.  NODE_UPD is the update
+// h' = h + relu(Wu^T [h, a] + bu) (upd_pre's chain); NODE_PQ forms the decoder's two tables
+// P_i = Wd[0:H]^T h_i + bd and Q_j = Wd[H:2H]^T h_j (dec_pre's chains).
+// One warp takes kNB nodes at a time; lane k holds column k of the weights in registers and
+// reads the nodes' inputs, staged in shared memory as binary32, four at a time by broadcast.
+constexpr int kNB = 4;
+enum { NODE_G = 0, NODE_UPD = 1, NODE_PQ = 2 };
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_node(int n, const float* __restrict__ W, const float* __restrict__ bias, const float* __restrict__ W2,
+           const __nv_bfloat16* __restrict__ x0, const __nv_bfloat16* __restrict__ x1,
+           __nv_bfloat16* __restrict__ hout, float* __restrict__ y0, float* __restrict__ y1) {
+  constexpr int DI = MODE == NODE_UPD ? 2 * H : H;
+  constexpr int D2 = MODE == NODE_PQ ? H : 1;
+  __shared__ float4 sx[kThreads / 32][kNB][2 * H / 4];
+  const int k = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  float* sxw = reinterpret_cast<float*>(&sx[wib][0][0]);
+  float w[DI], w2[D2];
 #pragma unroll
-  for (int l = 0; l < 2 * H + FE; ++l) wd[l] = PD[D_WD + l * H + k];
-  const float bd = PD[D_BD + k], wo = PD[D_WO + k], bo = PD[D_BO];
+  for (int l = 0; l < DI; ++l) w[l] = W[l * H + k];
+#pragma unroll
+  for (int l = 0; l < D2; ++l) w2[l] = MODE == NODE_PQ ? W2[l * H + k] : 0.0f;
+  const float b = bias[k];
+  for (int base = warp_id_global() * kNB; base < n; base += warps_total() * kNB) {
+    float xk[kNB], xa[kNB];
+#pragma unroll
+    for (int u = 0; u < kNB; ++u) {
+      const bool ok = base + u < n;
+      const int64_t r = (int64_t)(base + u) * H + k;
+      xk[u] = ok ? bf(x0[r]) : 0.0f;
+      xa[u] = (MODE == NODE_UPD && ok) ? bf(x1[r]) : 0.0f;
+    }
+    __syncwarp();  // the previous nodes' inputs have been read
+#pragma unroll
+    for (int u = 0; u < kNB; ++u) {
+      sxw[u * 2 * H + k] = xk[u];
+      if (MODE == NODE_UPD) sxw[u * 2 * H + H + k] = xa[u];
+    }
+    __syncwarp();
+    float q[kNB], q2[kNB];
+#pragma unroll
+    for (int u = 0; u < kNB; ++u) {
+      q[u] = b;
+      q2[u] = 0.0f;
+    }
+#pragma unroll
+    for (int l4 = 0; l4 < DI / 4; ++l4) {
+#pragma unroll
+      for (int u = 0; u < kNB; ++u) {
+        const float4 x = sx[wib][u][l4];
+        q[u] = fmaf(w[4 * l4 + 0], x.x, q[u]);
+        q[u] = fmaf(w[4 * l4 + 1], x.y, q[u]);
+        q[u] = fmaf(w[4 * l4 + 2], x.z, q[u]);
+        q[u] = fmaf(w[4 * l4 + 3], x.w, q[u]);
+        if (MODE == NODE_PQ) {
+          q2[u] = fmaf(w2[4 * l4 + 0], x.x, q2[u]);
+          q2[u] = fmaf(w2[4 * l4 + 1], x.y, q2[u]);
+          q2[u] = fmaf(w2[4 * l4 + 2], x.z, q2[u]);
+          q2[u] = fmaf(w2[4 * l4 + 3], x.w, q2[u]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kNB; ++u) {
+      if (base + u >= n) continue;
+      const int64_t r = (int64_t)(base + u) * H + k;
+      if (MODE == NODE_UPD) hout[r] = tobf(xk[u] + fmaxf(q[u], 0.0f));
+      else y0[r] = q[u];
+      if (MODE == NODE_PQ) y1[r] = q2[u];
+    }
+  }
+}
+
+// Sum over the warp of four values at once: on return lane k holds the total of value
+// (k >> 3) & 3.  Two halving exchanges hand each half, then each quarter, of the warp one value,
+// and three more steps finish each quarter's sum (6 shuffles for 4 sums instead of 20).
+__device__ __forceinline__ float warp_sum4(float v0, float v1, float v2, float v3, int k) {
+  const bool hi16 = (k >> 4) & 1;
+  const float s0 = hi16 ? v0 : v2, s1 = hi16 ? v1 : v3;
+  const float w0 = (hi16 ? v2 : v0) + __shfl_xor_sync(0xffffffffu, s0, 16);
+  const float w1 = (hi16 ? v3 : v1) + __shfl_xor_sync(0xffffffffu, s1, 16);
+  const bool hi8 = (k >> 3) & 1;
+  float x = (hi8 ? w1 : w0) + __shfl_xor_sync(0xffffffffu, hi8 ? w0 : w1, 8);
+  x += __shfl_xor_sync(0xffffffffu, x, 4);
+  x += __shfl_xor_sync(0xffffffffu, x, 2);
+  x += __shfl_xor_sync(0xffffffffu, x, 1);
+  return x;
+}
+
+// Forward messages of one layer: a_i = bf16(sum over the stored off-diagonal (i, j), in CSR order,
+// of relu(G_j + We^T e_ij)), G_j from k_node<NODE_G>.  One warp per row, lane k for component k,
+// kEU entries of the row loaded at once.
+constexpr int kEU = 4;
+static_assert(kEU == 4, "warp_sum4 reduces four entries");
+__global__ void __launch_bounds__(kThreads) k_msg(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                  const float4* __restrict__ xe, const float* __restrict__ PL,
+                                                  const float* __restrict__ G, __nv_bfloat16* __restrict__ aout) {
+  const int k = threadIdx.x & 31;
+  const float we0 = PL[L_WM + (H + 0) * H + k], we1 = PL[L_WM + (H + 1) * H + k],
+              we2 = PL[L_WM + (H + 2) * H + k], we3 = PL[L_WM + (H + 3) * H + k];
   for (int i = warp_id_global(); i < n; i += warps_total()) {
-    const float hi = bf(h[(int64_t)i * H + k]);
+    float acc = 0.0f;
     const int p1 = rp[i + 1];
     for (int p = rp[i]; p < p1; p += kEU) {
-      float hj[kEU], pre[kEU];
+      bool use[kEU];
+      float g[kEU];
       float4 e[kEU];
 #pragma unroll
       for (int u = 0; u < kEU; ++u) {
-        const int j = p + u < p1 ? ci[p + u] : i;
-        hj[u] = bf(h[(int64_t)j * H + k]);
-        e[u] = p + u < p1 ? xe[p + u] : make_float4(0.f, 0.f, 0.f, 0.f);
-        pre[u] = bd;
-      }
-#pragma unroll
-      for (int l = 0; l < H; ++l) {
-        const float hl = shfl(hi, l);
-#pragma unroll
-        for (int u = 0; u < kEU; ++u) pre[u] = fmaf(wd[l], hl, pre[u]);
-      }
-#pragma unroll
-      for (int l = 0; l < H; ++l) {
-#pragma unroll
-        for (int u = 0; u < kEU; ++u) pre[u] = fmaf(wd[H + l], shfl(hj[u], l), pre[u]);
+        const bool ok = p + u < p1;
+        const int j = ok ? ci[p + u] : i;
+        use[u] = ok && j != i;
+        g[u] = use[u] ? G[(int64_t)j * H + k] : 0.0f;
+        e[u] = use[u] ? xe[p + u] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
 #pragma unroll
       for (int u = 0; u < kEU; ++u) {
-        pre[u] = fmaf(wd[2 * H + 0], e[u].x, pre[u]);
-        pre[u] = fmaf(wd[2 * H + 1], e[u].y, pre[u]);
-        pre[u] = fmaf(wd[2 * H + 2], e[u].z, pre[u]);
-        pre[u] = fmaf(wd[2 * H + 3], e[u].w, pre[u]);
+        float pre = fmaf(we0, e[u].x, g[u]);
+        pre = fmaf(we1, e[u].y, pre);
+        pre = fmaf(we2, e[u].z, pre);
+        pre = fmaf(we3, e[u].w, pre);
+        if (use[u]) acc += fmaxf(pre, 0.0f);
       }
+    }
+    aout[(int64_t)i * H + k] = tobf(acc);
+  }
+}
+
+// Forward decoder, one output per stored entry: o_ij = wo . relu(P_i + Q_j + We^T e_ij) + bo with
+// the tables of k_node<NODE_PQ>; one warp per row, four entries reduced together.
+__global__ void __launch_bounds__(kThreads) k_dec(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                  const float4* __restrict__ xe, const float* __restrict__ PD,
+                                                  const float* __restrict__ Pt, const float* __restrict__ Qt,
+                                                  float* __restrict__ o) {
+  const int k = threadIdx.x & 31;
+  const float we0 = PD[D_WD + (2 * H + 0) * H + k], we1 = PD[D_WD + (2 * H + 1) * H + k],
+              we2 = PD[D_WD + (2 * H + 2) * H + k], we3 = PD[D_WD + (2 * H + 3) * H + k];
+  const float wo = PD[D_WO + k], bo = PD[D_BO];
+  const int mine = (k >> 3) & 3;  // the entry of each group of four whose sum this lane ends with
+  for (int i = warp_id_global(); i < n; i += warps_total()) {
+    const float pi = Pt[(int64_t)i * H + k];
+    const int p1 = rp[i + 1];
+    for (int p = rp[i]; p < p1; p += kEU) {
+      float v[kEU];
 #pragma unroll
       for (int u = 0; u < kEU; ++u) {
-        const float out = warp_sum(wo * fmaxf(pre[u], 0.0f)) + bo;
-        if (k == 0 && p + u < p1) o[p + u] = out;
+        const bool ok = p + u < p1;
+        const int j = ok ? ci[p + u] : i;
+        const float4 e = ok ? xe[p + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float pre = pi + Qt[(int64_t)j * H + k];
+        pre = fmaf(we0, e.x, pre);
+        pre = fmaf(we1, e.y, pre);
+        pre = fmaf(we2, e.z, pre);
+        pre = fmaf(we3, e.w, pre);
+        v[u] = wo * fmaxf(pre, 0.0f);
       }
+      const float out = warp_sum4(v[0], v[1], v[2], v[3], k) + bo;
+      if ((k & 7) == 0 && p + mine < p1) o[p + mine] = out;
     }
   }
 }
@@ -801,16 +863,28 @@ extern "C" int mpk_gnn_forward(const mpk_csr* A, const mpk_ilu* M, const float* 
   cudaStream_t s = (cudaStream_t)stream;
   const int n = A->n;
   Work w = carve(work, n, A->nnz, 1, 1);
-  count_launch(3 + NL);
+  count_launch(3);
   k_tpos<<<grid_for(n), kBlock, 0, s>>>(n, M->rp, M->ci, w.tpos);
   k_features<<<grid_for(n), kBlock, 0, s>>>(n, M->rp, M->ci, A->val, M->fac, M->prec, w.tpos, M->diag, w.xn, w.xe);
   k_encode<<<blocks_for(n), kThreads, 0, s>>>(n, w.xn, params, w.h);
-  for (int L = 0; L < NL; ++L)
-    k_layer<<<blocks_for(n), kThreads, 0, s>>>(n, M->rp, M->ci, w.xe, params + P_L0 + L * L_SIZE,
-                                               w.h + (size_t)L * n * H, w.a + (size_t)L * n * H,
-                                               w.h + (size_t)(L + 1) * n * H);
-  count_launch();
-  k_decode<<<blocks_for(n), kThreads, 0, s>>>(n, M->rp, M->ci, w.xe, params + P_DEC, w.h + (size_t)NL * n * H, o);
+  const size_t nh = (size_t)n * H;
+  const int nb = blocks_for((n + kNB - 1) / kNB);
+  float* G = w.gh;  // the backward pass's scratch is free during the forward pass
+  for (int L = 0; L < NL; ++L) {
+    const float* PL = params + P_L0 + L * L_SIZE;
+    const __nv_bfloat16* hL = w.h + (size_t)L * nh;
+    __nv_bfloat16* aL = w.a + (size_t)L * nh;
+    count_launch(3);
+    k_node<NODE_G><<<nb, kThreads, 0, s>>>(n, PL + L_WM, PL + L_BM, nullptr, hL, nullptr, nullptr, G, nullptr);
+    k_msg<<<blocks_for(n), kThreads, 0, s>>>(n, M->rp, M->ci, w.xe, PL, G, aL);
+    k_node<NODE_UPD><<<nb, kThreads, 0, s>>>(n, PL + L_WU, PL + L_BU, nullptr, hL, aL, w.h + (size_t)(L + 1) * nh,
+                                             nullptr, nullptr);
+  }
+  const float* PD = params + P_DEC;
+  count_launch(2);
+  k_node<NODE_PQ><<<nb, kThreads, 0, s>>>(n, PD + D_WD, PD + D_BD, PD + D_WD + H * H, w.h + (size_t)NL * nh, nullptr,
+                                          nullptr, w.gh, w.gh + nh);
+  k_dec<<<blocks_for(n), kThreads, 0, s>>>(n, M->rp, M->ci, w.xe, PD, w.gh, w.gh + nh, o);
   MPK_CUDA(cudaGetLastError());
   return MPK_OK;
 }
