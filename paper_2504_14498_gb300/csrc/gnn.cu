@@ -13,11 +13,15 @@
 //               a_i = bf16(sum_j m_ij)           (CSR order)
 //               h'_i = bf16(h_i + relu(Wu^T [h_i, a_i] + bu))
 //   decoder     o_ij = wo . relu(Wd^T [h_i, h_j, e_ij] + bd) + bo for every stored entry (i, j)
-// Training loss (probe estimate of the factorisation error, per system of a batch):
-//   loss = mean_s  sum_{i in s} ||(L'U' W - A W)_i||^2 / sum_{i in s} ||(A W)_i||^2
-// over nprobe probe vectors W (L' unit lower with the corrected strict lower part, U' the
-// corrected upper part).  Forward, loss gradient and backward are hand-written; parameters live
-// in one binary32 array (layout below, weight matrices stored input-major [in][out]).
+//               (evaluated as P_i + Q_j + We^T e_ij with per-node tables P, Q)
+// Two losses over nprobe probe vectors W, each a mean over the systems s of a batch (L' unit
+// lower with the corrected strict lower part, U' the corrected upper part):
+//   preconditioned operator (the training loss, mpk_gnn_loss_precond):
+//     loss = mean_s  sum_{i in s} ||(U'^-1 L'^-1 A W - W)_i||^2 / sum_{i in s} ||W_i||^2
+//   factorisation error (mpk_gnn_loss, a cheaper diagnostic):
+//     loss = mean_s  sum_{i in s} ||(L'U' W - A W)_i||^2 / sum_{i in s} ||(A W)_i||^2
+// Forward, loss gradients and backward are hand-written; parameters live in one binary32 array
+// (layout below, weight matrices stored input-major [in][out]).
 #include <cuda_bf16.h>
 
 #include <climits>

@@ -1285,15 +1285,37 @@ __global__ void __launch_bounds__(WPB * 32, 1)
   const int lane = threadIdx.x & 31;
   const int G = gridDim.x * (blockDim.x >> 5);
   const int g = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
-  MpChunk<W, CP, MF> c, nx;
-  if (g < T.nchunks) mp_meta<W, CP, MF>(T, g, nx);
+  // Two chunks ahead: the next chunk's operands (right-hand side, diagonal, first group of
+  // factor entries; none of them written by this launch) and the rows of the one after it are
+  // loaded before the current chunk waits, so a warp that finishes a chunk late starts the next
+  // one without a load round trip.  At 32 warps per SM (64 registers a thread) the warps hide
+  // that latency instead, and only the next chunk's rows are loaded ahead.
+  constexpr bool AHEAD = WPB < 32;
+  MpChunk<W, CP, MF> c, nx, mm;
+  if (g < T.nchunks) {
+    mp_meta<W, CP, MF>(T, g, nx);
+    if constexpr (AHEAD) mp_operands<W, CP, MF>(T, unit, in, g, nx);
+  }
+  if (AHEAD && g + G < T.nchunks) mp_meta<W, CP, MF>(T, g + G, mm);
   for (int chunk = g; chunk < T.nchunks; chunk += G) {
-    c.i = nx.i;
-    c.b0 = nx.b0;
-    c.w = nx.w;
-    c.rep = nx.rep;
-    mp_operands<W, CP, MF>(T, unit, in, chunk, c);
-    if (chunk + G < T.nchunks) mp_meta<W, CP, MF>(T, chunk + G, nx);  // the next chunk's rows, ahead
+    if constexpr (AHEAD) {
+      c = nx;
+      if (chunk + G < T.nchunks) {
+        nx.i = mm.i;
+        nx.b0 = mm.b0;
+        nx.w = mm.w;
+        nx.rep = mm.rep;
+        mp_operands<W, CP, MF>(T, unit, in, chunk + G, nx);
+      }
+      if (chunk + 2 * G < T.nchunks) mp_meta<W, CP, MF>(T, chunk + 2 * G, mm);
+    } else {
+      c.i = nx.i;
+      c.b0 = nx.b0;
+      c.w = nx.w;
+      c.rep = nx.rep;
+      mp_operands<W, CP, MF>(T, unit, in, chunk, c);
+      if (chunk + G < T.nchunks) mp_meta<W, CP, MF>(T, chunk + G, nx);
+    }
     if (mp_finish<W, CP, MF, false>(T, M, unit, out, c, RingRef(), 0)) {
       if (lane == 0) atomicCAS(M.ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
       return;
@@ -1333,16 +1355,27 @@ __global__ void __launch_bounds__(WPB * 32, 1)
   const int pair = warp >> 1, part = warp & 1;
   const int G = gridDim.x * NP;
   const int g = pair * gridDim.x + blockIdx.x;
-  MpChunk<W, CP, false> c, nx;
-  if (g < T.nchunks) mp_meta<W, CP, false>(T, g, nx);
+  MpChunk<W, CP, false> c, nx, mm;  // two chunks ahead, as in k_trsv_mp
+  if (g < T.nchunks) {
+    mp_meta<W, CP, false>(T, g, nx);
+    mp_operands<W, CP, false>(T, unit, in, g, nx);
+  }
+  if (g + G < T.nchunks) mp_meta<W, CP, false>(T, g + G, mm);
   int buf = 0;
   for (int chunk = g; chunk < T.nchunks; chunk += G) {
-    c.i = nx.i;
-    c.b0 = nx.b0;
-    c.w = nx.w;
-    c.rep = nx.rep;
-    mp_operands<W, CP, false>(T, unit, in, chunk, c);
-    if (chunk + G < T.nchunks) mp_meta<W, CP, false>(T, chunk + G, nx);
+    c = nx;
+    if (chunk + G < T.nchunks) {
+      nx.i = mm.i;
+      nx.b0 = mm.b0;
+      nx.w = mm.w;
+      nx.rep = mm.rep;
+      mp_operands<W, CP, false>(T, unit, in, chunk + G, nx);
+    }
+    if (chunk + 2 * G < T.nchunks) mp_meta<W, CP, false>(T, chunk + 2 * G, mm);
+    // |f_ii|^2 depends on the factor alone: formed while the dependencies are outstanding, not
+    // on the chain after them (the sub-partition's binary64 unit is idle during the wait)
+    R<W> den = r_from<W>(1.0);
+    if (!unit) den = add<W>(mul_fp<W>(r_from<W>(c.dr), c.dr), mul_fp<W>(r_from<W>(c.di), c.di));
     bool timeout = false;
     const long long t0 = clock64();
     int polls = 0;
@@ -1398,7 +1431,6 @@ __global__ void __launch_bounds__(WPB * 32, 1)
 #pragma unroll
         for (int k = 0; k < W; ++k) other.c[k] = xch[buf][pair][part ^ 1][k][lane];
         const R<W> are = part == 0 ? acc : other, aim = part == 0 ? other : acc;
-        const R<W> den = add<W>(mul_fp<W>(r_from<W>(c.dr), c.dr), mul_fp<W>(r_from<W>(c.di), c.di));
         const R<W> num = part == 0 ? add<W>(mul_fp<W>(are, c.dr), mul_fp<W>(aim, c.di))
                                    : sub<W>(mul_fp<W>(aim, c.dr), mul_fp<W>(are, c.di));
         acc = div<W>(num, den);
@@ -1759,15 +1791,35 @@ __global__ void __launch_bounds__(WPB * 32, 1)
   const int lane = threadIdx.x & 31;
   const int G = gridDim.x * (blockDim.x >> 5);
   const int g = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
-  LpChunk<TS> c, nx;
-  if (g < T.nchunks) lp_meta<TS>(T, g, nx);
+  // Two chunks ahead below 32 warps per SM, as in k_trsv_mp: the operands read here (the
+  // right-hand side, or the lower pass's binary32 output, and the factor) are not written by
+  // this launch.
+  constexpr bool AHEAD = WPB < 32;
+  LpChunk<TS> c, nx, mm;
+  if (g < T.nchunks) {
+    lp_meta<TS>(T, g, nx);
+    if constexpr (AHEAD) lp_operands<W, CP, TS>(T, M, lower, unit, in, g, e1, nx);
+  }
+  if (AHEAD && g + G < T.nchunks) lp_meta<TS>(T, g + G, mm);
   for (int chunk = g; chunk < T.nchunks; chunk += G) {
-    c.i = nx.i;
-    c.b0 = nx.b0;
-    c.w = nx.w;
-    c.rep = nx.rep;
-    lp_operands<W, CP, TS>(T, M, lower, unit, in, chunk, e1, c);
-    if (chunk + G < T.nchunks) lp_meta<TS>(T, chunk + G, nx);  // the next chunk's rows, ahead
+    if constexpr (AHEAD) {
+      c = nx;
+      if (chunk + G < T.nchunks) {
+        nx.i = mm.i;
+        nx.b0 = mm.b0;
+        nx.w = mm.w;
+        nx.rep = mm.rep;
+        lp_operands<W, CP, TS>(T, M, lower, unit, in, chunk + G, e1, nx);
+      }
+      if (chunk + 2 * G < T.nchunks) lp_meta<TS>(T, chunk + 2 * G, mm);
+    } else {
+      c.i = nx.i;
+      c.b0 = nx.b0;
+      c.w = nx.w;
+      c.rep = nx.rep;
+      lp_operands<W, CP, TS>(T, M, lower, unit, in, chunk, e1, c);
+      if (chunk + G < T.nchunks) lp_meta<TS>(T, chunk + G, nx);
+    }
     if (lp_finish<W, CP, TS, false>(T, M, lower, unit, out, c, RingRef(), 0)) {
       if (lane == 0) atomicCAS(M.ctl + CTL_ERR, 0, (int)MPK_TIMEOUT);
       return;
