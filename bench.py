@@ -306,7 +306,7 @@ def run_mpk(args):
     def solve(prec, method="bicgstab"):
         M = _lib.ILU0(A, prec)
         out = _lib.krylov_solve(method, w, A, M, b, tol_rel=TOL, maxit=20000, check_every=10, history=False)
-        out["schedule"] = M.schedule()
+        out["schedule"] = M.schedule() + (M.polling(),)
         M.close()
         return out
 
@@ -348,7 +348,8 @@ def run_mpk(args):
 
     extra = {"iters": last["iters"], "status": last["status"], "relres_true": last["relres_true"],
              "relres_rec": last["relres_rec"], "relerr_true": relerr(last, w),
-             "substitution_schedule": {"schedule": last["schedule"][0], "warps_per_sm": last["schedule"][1]}}
+             "substitution_schedule": {"schedule": last["schedule"][0], "warps_per_sm": last["schedule"][1],
+                                       "polling": last["schedule"][2]}}
     del outs
     # ---- variants: other factor precisions at equal final accuracy ----------------------------
     variants = {}
@@ -605,7 +606,7 @@ def run_only(args):
         fn()
     e1.record()
     torch.cuda.synchronize()
-    sched = M.schedule() if args.only.startswith("precond") else None
+    sched = M.schedule() + (M.polling(),) if args.only.startswith("precond") else None
     print(json.dumps({"only": args.only, "on": args.only_on, "m": args.m, "w": w, "reps": args.reps,
                       "ms_per_rep": e0.elapsed_time(e1) / args.reps, "schedule": sched}))
     return 0

@@ -34,8 +34,9 @@
  *                                                        read at every call; default: tuned.
  *   MPK_SUBST_POLL=lane0|all                             dependency polling of the substitutions
  *                                                        (lane 0 polls a chunk's latest dependency
- *                                                        first, or every lane its own); read at
- *                                                        every call; default: tuned.
+ *                                                        first, or every lane its own;
+ *                                                        mpk_ilu0_polling); read at every call;
+ *                                                        default: tuned.
  *   MPK_ILU_SCHEDULE=levels|dataflow                     ILU(0) schedule (mpk_ilu0_factor); read
  *                                                        at every factorisation; default: by the
  *                                                        width of the levels.
@@ -261,6 +262,12 @@ int mpk_ilu0_width(const mpk_ilu* M);
  * solve times schedules 0 and 1 once per matrix pattern and keeps the faster; the environment
  * variable MPK_SUBST_SCHEDULE=static|owner|cluster8|cluster16 selects one instead. */
 int mpk_ilu0_schedule(const mpk_ilu* M, int* wpb_out);
+
+/* Dependency polling the substitutions last used or were tuned to (with the schedule, or forced by
+ * MPK_SUBST_POLL): 0 = lane 0 polls each 32-row chunk's latest dependency, then every lane loads
+ * its own; 1 = every lane polls its own from the start.  The results do not depend on it.  -2 for
+ * a NULL handle. */
+int mpk_ilu0_polling(const mpk_ilu* M);
 
 /* Level structure of the factor's triangles (the substitutions of Algorithm 2 and the ILU(0)
  * kernels run in this order): tri = 0 for L~, 1 for U~.  *nlevels_out (if not NULL) receives the

@@ -63,6 +63,7 @@ SIGNATURES = [
     ("mpk_ilu0_prec", _I, [_VP]),
     ("mpk_ilu0_width", _I, [_VP]),
     ("mpk_ilu0_schedule", _I, [_VP, ctypes.POINTER(_I)]),
+    ("mpk_ilu0_polling", _I, [_VP]),
     ("mpk_ilu0_levels", _I, [_VP, _I, ctypes.POINTER(_I), _VP, _VP]),
     ("mpk_ilu0_test_withhold", _I, [_VP, _I]),
     ("mpk_ilu0_destroy", None, [_VP]),
@@ -245,6 +246,10 @@ class ILU0:
         wpb = ctypes.c_int(0)
         sc = lib().mpk_ilu0_schedule(self.handle, ctypes.byref(wpb))
         return ("static", "owner", "cluster8", "cluster16")[sc], wpb.value
+
+    def polling(self):
+        """Dependency polling of the substitutions: 'lane0' or 'all'."""
+        return ("lane0", "all")[lib().mpk_ilu0_polling(self.handle)]
 
     def levels(self, tri: int):
         """(number of levels, level of every row as a device int32 tensor) of L~ (tri 0) or U~

@@ -1595,6 +1595,8 @@ extern "C" int mpk_ilu0_schedule(const mpk_ilu* M, int* wpb_out) {
   return M->sched;
 }
 
+extern "C" int mpk_ilu0_polling(const mpk_ilu* M) { return M == nullptr ? -2 : M->poll; }
+
 extern "C" void mpk_ilu0_destroy(mpk_ilu* M) { free_handle(M); }
 
 extern "C" int mpk_precond_apply(const mpk_ilu* M, int w, int trans, const double* r_dev, double* z_dev,

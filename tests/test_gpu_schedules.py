@@ -115,7 +115,8 @@ def test_auto_tuner_picks_a_schedule(monkeypatch):
 def test_precond_both_polling_modes(monkeypatch, poll, mat, prec):
     """The substitutions' two ways of waiting for dependencies (lane 0 on the chunk's latest one,
     or every lane on its own) give the oracle's bits, M and M^H (the complex binary64 factor runs
-    the paired-warp kernel, real and imaginary parts on two sub-partitions)."""
+    the paired-warp kernel, real and imaginary parts on two sub-partitions), and the handle
+    reports the mode it ran."""
     monkeypatch.setenv("MPK_SUBST_SCHEDULE", "static")
     monkeypatch.setenv("MPK_SUBST_POLL", poll)
     A_t, c = MATS[mat]()
@@ -128,3 +129,4 @@ def test_precond_both_polling_modes(monkeypatch, poll, mat, prec):
             r = inputs.random_vector(n, w, c, seed=90 + w)
             z = host(M.apply(dev(r), w, trans))
             assert np.array_equal(z, oracle.precond(A_t, fac, r, w, prec, c, trans)), (trans, w)
+    assert M.polling() == poll
