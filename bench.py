@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=2, help="oracle iterations in the CPU sample")
+    ap.add_argument("--nvtx", action="store_true",
+                    help="wrap the timed steps in an NVTX range 'timed' (ncu --nvtx --nvtx-include timed/ then "
+                         "lists exactly the launches of the timed region)")
     ap.add_argument("--cpu-full", action="store_true",
                     help="cpu_baseline: time the oracle's complete solve (about 80 s on one core) instead of a sample")
     ap.add_argument("--only", default=None, choices=["spmv", "spmv_mm", "precond_fp64", "precond_fp32", "precond_bf16",
@@ -325,9 +328,13 @@ def run_mpk(args):
     clocks.start()
     l0 = _lib.kernel_launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.nvtx:
+        torch.cuda.nvtx.range_push("timed")
     e0.record()
     outs = [solve(args.prec) for _ in range(args.steps)]
     e1.record()
+    if args.nvtx:
+        torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier()
     launches = _lib.kernel_launches() - l0
@@ -648,9 +655,13 @@ def run_batch(args):
     clocks.start()
     l0 = _lib.kernel_launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.nvtx:
+        torch.cuda.nvtx.range_push("timed")
     e0.record()
     outs = [solve() for _ in range(args.steps)]
     e1.record()
+    if args.nvtx:
+        torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     launches = _lib.kernel_launches() - l0
     clk = clocks.stop()
