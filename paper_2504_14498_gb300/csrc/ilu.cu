@@ -74,7 +74,7 @@ struct RowIlu {
   // k's pivot and first RK upper entries are fetched ahead of consume (Val), so that the
   // eliminations need no memory round trip per entry; longer rows take the memory path, with
   // the same operations in the same order.
-  static constexpr int RI = 8, RK = 4;
+  static constexpr int RI = 8, RK = 4, kMG = 8;
   struct Val {
     int dk, ek;
     int uc[RK];       // columns of row k's upper entries dk+1 .. (-1 past its end)
@@ -192,21 +192,31 @@ struct RowIlu {
       a[(int64_t)p * CP] = lr;
       if constexpr (CP == 2) a[(int64_t)p * CP + 1] = li;
     }
+    // row k's upper columns are loaded kMG at a time (one round trip per group instead of one per
+    // entry), then merged with row i's remaining columns in ascending order as before
     int r = p + 1;
-    for (int q = dk + 1; q < ek; ++q) {
-      const int j = ci[q];
-      while (r < ei && ci[r] < j) ++r;
-      if (r >= ei) break;
-      if (ci[r] != j) continue;
-      T u[CP], av[CP];
+    for (int q0 = dk + 1; q0 < ek && r < ei; q0 += kMG) {
+      int jq[kMG];
 #pragma unroll
-      for (int h = 0; h < CP; ++h) {
-        u[h] = a[(int64_t)q * CP + h];
-        av[h] = a[(int64_t)r * CP + h];
+      for (int g = 0; g < kMG; ++g) jq[g] = q0 + g < ek ? ci[q0 + g] : INT_MAX;
+#pragma unroll
+      for (int g = 0; g < kMG; ++g) {
+        const int j = jq[g];
+        if (j == INT_MAX) break;
+        while (r < ei && ci[r] < j) ++r;
+        if (r >= ei) break;
+        if (ci[r] != j) continue;
+        const int q = q0 + g;
+        T u[CP], av[CP];
+#pragma unroll
+        for (int h = 0; h < CP; ++h) {
+          u[h] = a[(int64_t)q * CP + h];
+          av[h] = a[(int64_t)r * CP + h];
+        }
+        update(lr, li, u, av);
+#pragma unroll
+        for (int h = 0; h < CP; ++h) a[(int64_t)r * CP + h] = av[h];
       }
-      update(lr, li, u, av);
-#pragma unroll
-      for (int h = 0; h < CP; ++h) a[(int64_t)r * CP + h] = av[h];
     }
   }
   __device__ Val finish() {
