@@ -356,14 +356,21 @@ def krylov_solve_batched(method, w, A: Matrix, sys_rows, M: ILU0, b: torch.Tenso
 
 
 def solve_host(method, w, prec, A_tuple, b: np.ndarray, x0: np.ndarray = None, is_complex=False, tol_rel=1e-25,
-               tol_abs=0.0, maxit=1000, check_every=25, true_res_period=TRUE_RES_PERIOD):
-    """End to end from host arrays: H2D copies, ILU(0), solve, D2H of x inside one C call."""
+               tol_abs=0.0, maxit=1000, check_every=25, true_res_period=TRUE_RES_PERIOD, x_inplace=False):
+    """End to end from host arrays: H2D copies, ILU(0), solve, D2H of x inside one C call.
+    x_inplace: x0 (float64, contiguous) is itself the in/out buffer of x (no host copy of it; pass
+    page-locked arrays for full-speed copies)."""
     n, rp, ci, val = A_tuple
     rp = np.ascontiguousarray(rp, dtype=np.int32)
     ci = np.ascontiguousarray(ci, dtype=np.int32)
     val = np.ascontiguousarray(val, dtype=np.float64)
     b = np.ascontiguousarray(b, dtype=np.float64)
-    x = np.zeros_like(b) if x0 is None else np.ascontiguousarray(x0, dtype=np.float64).copy()
+    if x_inplace:
+        if x0 is None or x0.dtype != np.float64 or not x0.flags["C_CONTIGUOUS"]:
+            raise ValueError("x_inplace needs x0 as a contiguous float64 array")
+        x = x0
+    else:
+        x = np.zeros_like(b) if x0 is None else np.ascontiguousarray(x0, dtype=np.float64).copy()
     opts = Opts(float(tol_rel), float(tol_abs), int(maxit), int(check_every), 0, int(true_res_period), None, None)
     info = Info()
     st = lib().mpk_solve_host(METHODS[method], w, ILUS[prec], n, int(is_complex), rp.ctypes.data, ci.ctypes.data,

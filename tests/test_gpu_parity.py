@@ -316,3 +316,22 @@ def test_solve_host_end_to_end():
     assert out["status"] == "OK"
     assert abs(out["iters"] - ref["iters"]) <= max(1, int(0.05 * ref["iters"]))
     assert np.max(np.abs(out["x"].reshape(n, w)[:, 0] - 1.0)) < 1e-20
+
+
+def test_solve_host_pinned_in_place():
+    """The host-buffer call with page-locked inputs and x returned into x0's own buffer gives the
+    bits of the copying call."""
+    A_t = inputs.convdiff2d(30, pe=10.0)
+    n, w = A_t[0], 2
+    b = host(_lib.spmv_mp(_lib.Matrix.from_tuple(A_t), dev(inputs.ones(n, w)), w))
+    ref = _lib.solve_host("bicgstab", w, "fp64", A_t, b, tol_rel=1e-25)
+
+    def pinned(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+
+    Ap = (A_t[0], pinned(A_t[1].astype(np.int32)), pinned(A_t[2].astype(np.int32)), pinned(A_t[3]))
+    x0 = pinned(np.zeros(n * w))
+    out = _lib.solve_host("bicgstab", w, "fp64", Ap, pinned(b), x0, tol_rel=1e-25, x_inplace=True)
+    assert out["x"] is x0
+    assert out["status"] == ref["status"] == "OK" and out["iters"] == ref["iters"]
+    assert np.array_equal(x0, ref["x"])
