@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--m", type=int, default=128, help="grid points per axis")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--learned-steps", type=int, default=400,
+    ap.add_argument("--learned-steps", type=int, default=1200,
                     help="training steps of the learned correction for its 128^3 variant (0: skip it)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -937,8 +937,10 @@ def _gen_batch3d(job):
 
 def train_learned3d(steps, m=24, bs=8, K=4, lr=2e-3, base=2504_14498 + 70000):
     """Train the learned ILU(0) correction on seeded m^3 instances of the 3-D recipe (batches of
-    bs block-diagonal systems, K probes, Adam) with the library's kernels; the inputs are made by a
-    spawned process pool while the GPU trains.  Returns (network, record)."""
+    bs block-diagonal systems, K probes, Adam with a cosine-decayed learning rate, lr at the first
+    step) with the library's kernels; the inputs are made by a spawned process pool while the GPU
+    trains.  Returns (network, record)."""
+    import math
     import multiprocessing as mp
 
     import torch
@@ -951,19 +953,21 @@ def train_learned3d(steps, m=24, bs=8, K=4, lr=2e-3, base=2504_14498 + 70000):
     net = learned.LearnedILU(seed=base + 1)
     ws, losses, t_gpu = None, [], 0.0
     t0 = time.perf_counter()
-    for B_t, roff, W in pool.imap(_gen_batch3d, jobs, chunksize=2):
+    for k, (B_t, roff, W) in enumerate(pool.imap(_gen_batch3d, jobs, chunksize=2)):
         g0 = time.perf_counter()
         B = _lib.Matrix.from_tuple(B_t)
         M = _lib.ILU0(B, "fp32")
         if ws is None:
             ws = learned.Workspace(B.n, B.nnz, K, bs)
-        losses.append(net.train_step(B, M, torch.as_tensor(W, device="cuda"), ws, roff, lr=lr))
+        lr_k = lr * 0.5 * (1.0 + math.cos(math.pi * k / steps))
+        losses.append(net.train_step(B, M, torch.as_tensor(W, device="cuda"), ws, roff, lr=lr_k))
         M.close()
         torch.cuda.synchronize()
         t_gpu += time.perf_counter() - g0
     pool.close()
     losses = [float(x.item()) for x in losses]
     rec = {"instances": steps * bs, "grid": "%d^3" % m, "steps": steps, "batch": bs, "probes": K, "lr": lr,
+           "lr_schedule": "cosine to 0",
            "s_total": time.perf_counter() - t0, "s_gpu": t_gpu,
            "loss_first": float(np.mean(losses[:10])), "loss_last": float(np.mean(losses[-10:]))}
     return net, rec
