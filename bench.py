@@ -980,6 +980,7 @@ def run_learned(args):
     512^2 instances: DD BiCGSTAB to 1e-25 iterations and time with plain binary64 and binary32
     ILU(0) and with the corrected factors; plain ILU(0) judges every instance (the learned factor
     is kept only when it needs no more iterations)."""
+    import math
     import multiprocessing as mp
 
     import torch
@@ -997,14 +998,15 @@ def run_learned(args):
     losses, t_gpu = [], 0.0
     t0 = time.perf_counter()
     ws = None
-    for B_t, roff, W in pool.imap(_gen_batch, jobs, chunksize=2):
+    for k, (B_t, roff, W) in enumerate(pool.imap(_gen_batch, jobs, chunksize=2)):
         g0 = time.perf_counter()
         B = _lib.Matrix.from_tuple(B_t)
         M = _lib.ILU0(B, "fp32")
         if ws is None:
             ws = learned.Workspace(B.n, B.nnz, K, bs)
         Wd = torch.as_tensor(W, device="cuda")
-        losses.append(net.train_step(B, M, Wd, ws, roff, lr=lr))
+        lr_k = lr * 0.5 * (1.0 + math.cos(math.pi * k / nb))  # cosine decay to 0
+        losses.append(net.train_step(B, M, Wd, ws, roff, lr=lr_k))
         M.close()
         torch.cuda.synchronize()
         t_gpu += time.perf_counter() - g0
@@ -1051,7 +1053,8 @@ def run_learned(args):
             "value": summary["judged_fp32"]["mean_iters"], "unit": "iterations (mean, judged learned binary32)",
             "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "dtype": "f64",
             "config": {"workload": "learned ILU(0) correction: GNN 3 layers x hidden 32, trained on %d seeded 256^2 "
-                                   "convection-diffusion instances (batches of %d, %d probes, Adam lr %g), evaluated "
+                                   "convection-diffusion instances (batches of %d, %d probes, Adam lr %g decayed to 0 "
+                                   "on a cosine), evaluated "
                                    "on %d held-out 512^2 instances" % (nb * bs, bs, K, lr, ne)},
             "train": {"instances": nb * bs, "steps": nb, "s_total": t_train, "s_gpu": t_gpu,
                       "loss_first": float(np.mean(losses[:10])), "loss_last": float(np.mean(losses[-10:]))},
