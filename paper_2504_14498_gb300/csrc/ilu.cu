@@ -405,12 +405,23 @@ __global__ void k_trsv_prep(int* ctl, unsigned long long* absmax, const int* don
 constexpr unsigned kDepthEpoch0 = 0x40000000u;  // epochs of the ordering passes, distinct from others
 
 // counts per depth; cnt[L] (L = array length - 1, passed as maxslot) collects the largest depth
+// Levels below kHistBins are counted per block in shared memory and added once per block (a few
+// dozen levels over millions of rows would otherwise serialise on a few global counters).
+constexpr int kHistBins = 4096;
 __global__ void k_depth_count(int m, const int* __restrict__ depth, int* __restrict__ cnt, int* __restrict__ maxd) {
+  __shared__ int h[kHistBins];
+  for (int t = threadIdx.x; t < kHistBins; t += blockDim.x) h[t] = 0;
+  __syncthreads();
   int mx = 0;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
-    atomicAdd(cnt + depth[c], 1);
-    mx = max(mx, depth[c]);
+    const int d = depth[c];
+    if (d < kHistBins) atomicAdd(&h[d], 1);
+    else atomicAdd(cnt + d, 1);
+    mx = max(mx, d);
   }
+  __syncthreads();
+  for (int t = threadIdx.x; t < kHistBins; t += blockDim.x)
+    if (h[t] != 0) atomicAdd(cnt + t, h[t]);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
   if ((threadIdx.x & 31) == 0) atomicMax(maxd, mx);
@@ -679,8 +690,17 @@ __device__ __forceinline__ int tri_len(const int* rp, const int* diag, bool lowe
 }
 __global__ void k_key_count(int n, const int* __restrict__ depth, const int* __restrict__ rp,
                             const int* __restrict__ diag, bool lower, int* __restrict__ cnt2) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    atomicAdd(cnt2 + depth[i] * kLenB + (kLenB - 1 - min(tri_len(rp, diag, lower, i), kLenB - 1)), 1);
+  __shared__ int h[kHistBins];  // keys below kHistBins counted per block first
+  for (int t = threadIdx.x; t < kHistBins; t += blockDim.x) h[t] = 0;
+  __syncthreads();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int key = depth[i] * kLenB + (kLenB - 1 - min(tri_len(rp, diag, lower, i), kLenB - 1));
+    if (key < kHistBins) atomicAdd(&h[key], 1);
+    else atomicAdd(cnt2 + key, 1);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < kHistBins; t += blockDim.x)
+    if (h[t] != 0) atomicAdd(cnt2 + t, h[t]);
 }
 __global__ void k_key_offsets(int nlevels, const int* __restrict__ off, const int* __restrict__ cnt2,
                               int* __restrict__ sub) {
@@ -695,9 +715,17 @@ __global__ void k_key_offsets(int nlevels, const int* __restrict__ off, const in
 __global__ void k_level_scatter(int n, const int* __restrict__ depth, const int* __restrict__ rp,
                                 const int* __restrict__ diag, bool lower, int* __restrict__ sub,
                                 int* __restrict__ perm, int* __restrict__ pos) {
+  // the lanes of a warp with equal keys take their positions with one reservation (the order
+  // inside a key's group is arbitrary either way)
+  const int lane = threadIdx.x & 31;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int key = depth[i] * kLenB + (kLenB - 1 - min(tri_len(rp, diag, lower, i), kLenB - 1));
-    const int q = atomicAdd(sub + key, 1);
+    const unsigned peers = __match_any_sync(__activemask(), key);
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(sub + key, __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    const int q = base + __popc(peers & ((1u << lane) - 1u));
     perm[q] = i;
     pos[i] = q;
   }
@@ -850,22 +878,39 @@ __global__ void k_sell_fill(int nchunks, const int* __restrict__ perm, const int
     const int bi = (enc.blk != nullptr && i >= 0) ? enc.blk[i] : -1;
     const int gend = enc.blk != nullptr ? enc.cgend[c] : 0;
     int last = -1;
-    for (int k = 0; k < w; ++k) {
-      const int64_t e = ((int64_t)(b0 + k) << 5) + lane;
-      int cv = -1;
-      if (k < len) {
-        const int j = ci[p + k], qj = pos[j];
-        if (bi >= 0 && enc.blk[j] == bi && qj + kRing >= gend) {
-          const int rank = ((qj >> 5) - enc.cgstart[qj >> 5]) % enc.csize;
-          cv = -2 - (rank * kRing + (qj - enc.bstart[bi]) % kRing);
-        } else {
-          cv = j;
-          last = max(last, qj);
-        }
-      }
-      col[e] = cv;
+    // four entries at a time: their columns, then the columns' positions and the values, each
+    // loaded together (a chain of dependent loads per entry otherwise)
+    for (int k0 = 0; k0 < w; k0 += 4) {
+      int j4[4], q4[4];
+      T v4[4][CP];
 #pragma unroll
-      for (int t = 0; t < CP; ++t) val[e * CP + t] = k < len ? fac[(int64_t)(p + k) * CP + t] : T(0);
+      for (int u = 0; u < 4; ++u) j4[u] = k0 + u < len ? ci[p + k0 + u] : -1;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        q4[u] = j4[u] >= 0 ? pos[j4[u]] : -1;
+#pragma unroll
+        for (int t = 0; t < CP; ++t) v4[u][t] = j4[u] >= 0 ? fac[(int64_t)(p + k0 + u) * CP + t] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int k = k0 + u;
+        if (k >= w) break;
+        const int64_t e = ((int64_t)(b0 + k) << 5) + lane;
+        int cv = -1;
+        if (k < len) {
+          const int j = j4[u], qj = q4[u];
+          if (bi >= 0 && enc.blk[j] == bi && qj + kRing >= gend) {
+            const int rank = ((qj >> 5) - enc.cgstart[qj >> 5]) % enc.csize;
+            cv = -2 - (rank * kRing + (qj - enc.bstart[bi]) % kRing);
+          } else {
+            cv = j;
+            last = max(last, qj);
+          }
+        }
+        col[e] = cv;
+#pragma unroll
+        for (int t = 0; t < CP; ++t) val[e * CP + t] = v4[u][t];
+      }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) last = max(last, __shfl_xor_sync(0xffffffffu, last, off));
