@@ -68,13 +68,15 @@ __global__ void k_widen(int64_t m, const T* __restrict__ v, double* __restrict__
 __device__ __forceinline__ float fm(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fm(double a, double b, double c) { return fma(a, b, c); }
 
-template <typename T, int CP>
+template <typename T, int CP, bool LONG = false>
 struct RowIlu {
   // Rows of up to RI entries are held in registers while they are factored, and a finished row
   // k's pivot and first RK upper entries are fetched ahead of consume (Val), so that the
   // eliminations need no memory round trip per entry; longer rows take the memory path, with
-  // the same operations in the same order.
-  static constexpr int RI = 8, RK = 4, kMG = 8;
+  // the same operations in the same order.  LONG (matrices whose rows average more than RI
+  // entries): the memory path only, without the registers of the short-row path, so that more
+  // warps fit on an SM.
+  static constexpr int RI = LONG ? 1 : 8, RK = LONG ? 1 : 4, kMG = 8;
   struct Val {
     int dk, ek;
     int uc[RK];       // columns of row k's upper entries dk+1 .. (-1 past its end)
@@ -94,7 +96,7 @@ struct RowIlu {
     i = i_;
     p0 = rp[i_];
     len = rp[i_ + 1] - p0;
-    reg = len <= RI;
+    reg = !LONG && len <= RI;
 #pragma unroll
     for (int t = 0; t < RI; ++t) {
       rc[t] = -1;
@@ -115,12 +117,14 @@ struct RowIlu {
     v.ek = rp[k + 1];
 #pragma unroll
     for (int h = 0; h < CP; ++h) v.piv[h] = a[(int64_t)v.dk * CP + h];
+    if constexpr (!LONG) {
 #pragma unroll
-    for (int u = 0; u < RK; ++u) {
-      const int q = v.dk + 1 + u;
-      v.uc[u] = q < v.ek ? ci[q] : -1;
+      for (int u = 0; u < RK; ++u) {
+        const int q = v.dk + 1 + u;
+        v.uc[u] = q < v.ek ? ci[q] : -1;
 #pragma unroll
-      for (int h = 0; h < CP; ++h) v.uv[u * CP + h] = q < v.ek ? a[(int64_t)q * CP + h] : T(0);
+        for (int h = 0; h < CP; ++h) v.uv[u * CP + h] = q < v.ek ? a[(int64_t)q * CP + h] : T(0);
+      }
     }
     return v;
   }
@@ -156,8 +160,10 @@ struct RowIlu {
     reg = false;
   }
   __device__ void consume(int p, int k, const Val& vk) {
-    if (reg && vk.ek - vk.dk - 1 > RK) spill();
-    if (reg) {
+    if constexpr (!LONG) {
+      if (reg && vk.ek - vk.dk - 1 > RK) spill();
+    }
+    if (!LONG && reg) {
       const int tk = p - p0;  // position of (i, k) in row i
       T x[CP];
 #pragma unroll
@@ -220,7 +226,7 @@ struct RowIlu {
     }
   }
   __device__ Val finish() {
-    if (reg) spill();
+    if (!LONG && reg) spill();
     const int d = diag[i];
     bool zero;
     if constexpr (CP == 1) zero = a[d] == T(0);
@@ -233,10 +239,10 @@ struct RowIlu {
 
 constexpr int kIluEpoch = 1;  // the substitutions use epochs >= 2 on the same chunk flags
 
-template <typename T, int CP>
+template <typename T, int CP, bool LONG>
 __global__ void __launch_bounds__(kBlock) k_ilu(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                                 const int* __restrict__ diag, const LevelOrder lo, T* a, int* ctl) {
-  RowIlu<T, CP> row;
+  RowIlu<T, CP, LONG> row;
   row.rp = rp;
   row.ci = ci;
   row.diag = diag;
@@ -246,10 +252,10 @@ __global__ void __launch_bounds__(kBlock) k_ilu(int n, const int* __restrict__ r
 }
 
 // The same rows level by level (level_rows): a cooperative launch, grid barriers between levels.
-template <typename T, int CP>
+template <typename T, int CP, bool LONG>
 __global__ void __launch_bounds__(kBlock) k_ilu_lv(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                                    const int* __restrict__ diag, const LevelOrder lo, T* a, int* ctl) {
-  RowIlu<T, CP> row;
+  RowIlu<T, CP, LONG> row;
   row.rp = rp;
   row.ci = ci;
   row.diag = diag;
@@ -365,12 +371,18 @@ static int launch_ilu_kernel(const void* lv, const void* df, int blocks_lv, int 
   }
   return MPK_OK;
 }
+// long_rows: rows average more than RowIlu's register capacity (the memory-path-only kernels)
 template <typename T, int CP>
-static int launch_ilu(int n, const int* rp, const int* ci, const int* diag, const LevelOrder& lo, T* a, int* ctl,
-                      cudaStream_t s) {
-  static const int blv = persistent_blocks(k_ilu_lv<T, CP>), bdf = persistent_blocks(k_ilu<T, CP>);
-  return launch_ilu_kernel<T>((const void*)k_ilu_lv<T, CP>, (const void*)k_ilu<T, CP>, blv, bdf, n, rp, ci, diag, lo,
-                              a, ctl, s);
+static int launch_ilu(int n, int nnz, const int* rp, const int* ci, const int* diag, const LevelOrder& lo, T* a,
+                      int* ctl, cudaStream_t s) {
+  if ((int64_t)nnz > (int64_t)RowIlu<T, CP>::RI * n) {
+    static const int blv = persistent_blocks(k_ilu_lv<T, CP, true>), bdf = persistent_blocks(k_ilu<T, CP, true>);
+    return launch_ilu_kernel<T>((const void*)k_ilu_lv<T, CP, true>, (const void*)k_ilu<T, CP, true>, blv, bdf, n, rp,
+                                ci, diag, lo, a, ctl, s);
+  }
+  static const int blv = persistent_blocks(k_ilu_lv<T, CP, false>), bdf = persistent_blocks(k_ilu<T, CP, false>);
+  return launch_ilu_kernel<T>((const void*)k_ilu_lv<T, CP, false>, (const void*)k_ilu<T, CP, false>, blv, bdf, n, rp,
+                              ci, diag, lo, a, ctl, s);
 }
 template <int W, int CP>
 static int launch_ilu_mp_wc(int n, const int* rp, const int* ci, const int* diag, const LevelOrder& lo, double* a,
@@ -1543,11 +1555,11 @@ static int factor_impl(const mpk_csr* A, int prec, int w, mpk_ilu** out, int* fa
   if (prec == MPK_ILU_MP) {
     lst = launch_ilu_mp(w, cp, n, M->rp, M->ci, M->diag, lv_lo, (double*)work, M->ctl, s);
   } else if (prec == MPK_ILU_FP64) {
-    if (cp == 1) lst = launch_ilu<double, 1>(n, M->rp, M->ci, M->diag, lv_lo, (double*)work, M->ctl, s);
-    else lst = launch_ilu<double, 2>(n, M->rp, M->ci, M->diag, lv_lo, (double*)work, M->ctl, s);
+    if (cp == 1) lst = launch_ilu<double, 1>(n, M->nnz, M->rp, M->ci, M->diag, lv_lo, (double*)work, M->ctl, s);
+    else lst = launch_ilu<double, 2>(n, M->nnz, M->rp, M->ci, M->diag, lv_lo, (double*)work, M->ctl, s);
   } else {
-    if (cp == 1) lst = launch_ilu<float, 1>(n, M->rp, M->ci, M->diag, lv_lo, (float*)work, M->ctl, s);
-    else lst = launch_ilu<float, 2>(n, M->rp, M->ci, M->diag, lv_lo, (float*)work, M->ctl, s);
+    if (cp == 1) lst = launch_ilu<float, 1>(n, M->nnz, M->rp, M->ci, M->diag, lv_lo, (float*)work, M->ctl, s);
+    else lst = launch_ilu<float, 2>(n, M->nnz, M->rp, M->ci, M->diag, lv_lo, (float*)work, M->ctl, s);
   }
   if (lst != MPK_OK) return bail(lst);
   MPK_TRY(cudaGetLastError());
