@@ -1018,9 +1018,29 @@ __device__ __forceinline__ void st_relaxed_f64(double* p, double x) {
   if (v == kSent) v = 0x7FF8000000000000ull;  // never publish the sentinel
   asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+// Double-word values as one 16-byte strong access where the vector is 16-byte aligned (one request
+// instead of two; each word is still checked on its own, so a value seen half-written is polled
+// again), else word by word.
+__device__ __forceinline__ void ld_relaxed_f64x2(const double* p, double& a, double& b) {
+  asm volatile("ld.relaxed.gpu.global.v2.f64 {%0, %1}, [%2];" : "=d"(a), "=d"(b) : "l"(p) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_f64x2(double* p, double a, double b) {
+  unsigned long long ua = (unsigned long long)__double_as_longlong(a), ub = (unsigned long long)__double_as_longlong(b);
+  if (ua == kSent) ua = 0x7FF8000000000000ull;  // never publish the sentinel
+  if (ub == kSent) ub = 0x7FF8000000000000ull;
+  asm volatile("st.relaxed.gpu.global.v2.b64 [%0], {%1, %2};" ::"l"(p), "l"(ua), "l"(ub) : "memory");
+}
+__device__ __forceinline__ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 template <int W, int CP>
 __device__ __forceinline__ void n_fetch(const double* __restrict__ v, int64_t i, N<W, CP>& z) {
   const double* p = v + i * (CP * W);
+  if constexpr (W == 2) {
+    if (aligned16(v)) {
+      ld_relaxed_f64x2(p, z.re.c[0], z.re.c[1]);
+      if constexpr (CP == 2) ld_relaxed_f64x2(p + 2, z.im.c[0], z.im.c[1]);
+      return;
+    }
+  }
 #pragma unroll
   for (int k = 0; k < W; ++k) z.re.c[k] = ld_relaxed_f64(p + k);
   if constexpr (CP == 2) {
@@ -1047,6 +1067,13 @@ __device__ __forceinline__ bool n_poll(const double* __restrict__ v, int64_t i, 
 template <int W, int CP>
 __device__ __forceinline__ void n_publish(double* __restrict__ v, int64_t i, const N<W, CP>& z) {
   double* p = v + i * (CP * W);
+  if constexpr (W == 2) {
+    if (aligned16(v)) {
+      st_relaxed_f64x2(p, z.re.c[0], z.re.c[1]);
+      if constexpr (CP == 2) st_relaxed_f64x2(p + 2, z.im.c[0], z.im.c[1]);
+      return;
+    }
+  }
 #pragma unroll
   for (int k = 0; k < W; ++k) st_relaxed_f64(p + k, z.re.c[k]);
   if constexpr (CP == 2) {
