@@ -44,7 +44,7 @@ FP64_PEAK_OPS = 152 * 4 * 0.5 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one k_trsv_mp launch pair (both triangles, static schedule) on the
 # 128^3 workload: dram__bytes_read.sum + dram__bytes_write.sum from an ncu capture of the current
 # kernel (its summary is under profiles/); None once the kernel changes.
-TRSV_MP_TRAFFIC = 151203840 + 18551552 + 167994112 + 17050112
+TRSV_MP_TRAFFIC = 151328256 + 18579456 + 168283136 + 17025792
 # binary64 warp instructions one 32-row chunk of the binary64-factor DD substitution issues on
 # its chain (lower unit triangle, upper triangle with the division), from an ncu count of the
 # static-schedule kernel on the 7-point matrix (sm__inst_executed_pipe_fp64 / chunks; summary
