@@ -9,6 +9,9 @@
  * Conventions shared by every entry point
  *   - Pointers named *_dev are DEVICE pointers (e.g. torch CUDA tensors), owned by the caller,
  *     16-byte aligned, and must stay valid until the stream work that uses them completes.
+ *     Vectors and complex matrix values are accessed 16 bytes at a time: a misaligned vector
+ *     pointer, or a misaligned val of a complex matrix, is refused with MPK_INVALID_ARG
+ *     before any work is queued.
  *     Pointers named *_host are host pointers.  `stream` is a cudaStream_t (NULL = default
  *     stream); every call is ordered on it.
  *   - Multi-component numbers: w = 1 (D), 2 (DD), 3 (TD), 4 (QD) binary64 components,

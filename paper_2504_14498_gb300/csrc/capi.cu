@@ -74,6 +74,8 @@ static int spmv_entry(const mpk_csr* A, int w, const double* x_dev, double* y_de
     return fail(MPK_INVALID_ARG, "invalid CSR descriptor");
   if (A->is_complex != 0 && A->is_complex != 1) return fail(MPK_INVALID_ARG, "is_complex must be 0 or 1");
   if (w < 1 || w > 4) return fail(MPK_INVALID_ARG, "w must be 1..4");
+  if (misaligned(x_dev) || misaligned(y_dev) || (A->is_complex && misaligned(A->val)))
+    return fail(MPK_INVALID_ARG, "device vectors (and complex values) must be 16-byte aligned");
   const Ops* o = get_ops(w, A->is_complex ? 2 : 1);
   Csr c{A->n, A->nnz, A->row_ptr, A->col_idx, A->val, A->is_complex};
   c.mm = mm;
@@ -94,6 +96,8 @@ extern "C" int mpk_dot(int n, int is_complex, int w, const double* a_dev, const 
                        void* stream) {
   if (n < 1 || a_dev == nullptr || b_dev == nullptr || out_dev == nullptr) return fail(MPK_INVALID_ARG, "bad argument");
   if (w < 1 || w > 4 || (is_complex != 0 && is_complex != 1)) return fail(MPK_INVALID_ARG, "bad w / is_complex");
+  if (misaligned(a_dev) || misaligned(b_dev) || misaligned(out_dev))
+    return fail(MPK_INVALID_ARG, "device vectors must be 16-byte aligned");
   cudaStream_t s = (cudaStream_t)stream;
   const Ops* o = get_ops(w, is_complex ? 2 : 1);
   DotWs ws;
@@ -144,6 +148,8 @@ extern "C" int mpk_mp_op(int op, int w, int n, const double* a_dev, const double
   if (w < 1 || w > 4) return fail(MPK_INVALID_ARG, "w must be 1..4");
   if (n < 0 || a_dev == nullptr || out_dev == nullptr || (b_dev == nullptr && op != MPK_OP_SQRT))
     return fail(MPK_INVALID_ARG, "bad argument");
+  if (misaligned(a_dev) || (b_dev != nullptr && misaligned(b_dev)) || misaligned(out_dev))
+    return fail(MPK_INVALID_ARG, "device vectors must be 16-byte aligned");
   if (n == 0) return MPK_OK;
   cudaStream_t s = (cudaStream_t)stream;
   int g = (n + 255) / 256;

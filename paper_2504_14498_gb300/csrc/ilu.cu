@@ -1601,6 +1601,7 @@ extern "C" int mpk_ilu0_factor(const mpk_csr* A, int prec, mpk_ilu** out, int* f
   if (A->n < 1 || A->nnz < 0 || A->row_ptr == nullptr || (A->nnz > 0 && (A->col_idx == nullptr || A->val == nullptr)))
     return fail(MPK_INVALID_ARG, "invalid CSR descriptor");
   if (A->is_complex != 0 && A->is_complex != 1) return fail(MPK_INVALID_ARG, "is_complex must be 0 or 1");
+  if (A->is_complex && misaligned(A->val)) return fail(MPK_INVALID_ARG, "complex values must be 16-byte aligned");
   if (prec != MPK_ILU_FP64 && prec != MPK_ILU_FP32 && prec != MPK_ILU_BF16)
     return fail(MPK_INVALID_ARG, "prec must be MPK_ILU_FP64, MPK_ILU_FP32 or MPK_ILU_BF16");
   return factor_impl(A, prec, 1, out, fail_row, (cudaStream_t)stream);
@@ -1613,12 +1614,14 @@ extern "C" int mpk_ilu0_factor_mp(const mpk_csr* A, int w, mpk_ilu** out, int* f
   if (A->n < 1 || A->nnz < 0 || A->row_ptr == nullptr || (A->nnz > 0 && (A->col_idx == nullptr || A->val == nullptr)))
     return fail(MPK_INVALID_ARG, "invalid CSR descriptor");
   if (A->is_complex != 0 && A->is_complex != 1) return fail(MPK_INVALID_ARG, "is_complex must be 0 or 1");
+  if (A->is_complex && misaligned(A->val)) return fail(MPK_INVALID_ARG, "complex values must be 16-byte aligned");
   if (w < 1 || w > 4) return fail(MPK_INVALID_ARG, "w must be 1..4");
   return factor_impl(A, MPK_ILU_MP, w, out, fail_row, (cudaStream_t)stream);
 }
 
 extern "C" int mpk_ilu0_values(const mpk_ilu* M, double* out_dev, void* stream) {
   if (M == nullptr || out_dev == nullptr) return fail(MPK_INVALID_ARG, "null argument");
+  if (misaligned(out_dev)) return fail(MPK_INVALID_ARG, "device vectors must be 16-byte aligned");
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t m = (int64_t)M->nnz * M->cp;
   if (m == 0) return MPK_OK;
@@ -1671,6 +1674,7 @@ extern "C" int mpk_precond_apply(const mpk_ilu* M, int w, int trans, const doubl
   if (M == nullptr || r_dev == nullptr || z_dev == nullptr || r_dev == z_dev)
     return fail(MPK_INVALID_ARG, "null or aliased argument");
   if (w < 1 || w > 4) return fail(MPK_INVALID_ARG, "w must be 1..4");
+  if (misaligned(r_dev) || misaligned(z_dev)) return fail(MPK_INVALID_ARG, "device vectors must be 16-byte aligned");
   cudaStream_t s = (cudaStream_t)stream;
   if (trans) {
     int st = build_transpose(const_cast<mpk_ilu*>(M), s);

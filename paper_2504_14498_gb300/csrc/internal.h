@@ -12,6 +12,9 @@ namespace mpk {
 // Error reporting (thread-local last error; see mpk_last_error).
 void set_error(const std::string& msg);
 int fail(int status, const std::string& msg);
+// Multi-component vectors (and complex matrix values) are read and written with 16-byte accesses:
+// every entry point refuses a misaligned device pointer (MPK_INVALID_ARG) before any launch.
+inline bool misaligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) != 0; }
 #define MPK_CUDA(call)                                                                      \
   do {                                                                                      \
     cudaError_t err_ = (call);                                                              \

@@ -265,6 +265,7 @@ static int validate_csr(const mpk_csr* A) {
   if (A->n < 1 || A->nnz < 0 || A->row_ptr == nullptr || (A->nnz > 0 && (A->col_idx == nullptr || A->val == nullptr)))
     return fail(MPK_INVALID_ARG, "invalid CSR descriptor");
   if (A->is_complex != 0 && A->is_complex != 1) return fail(MPK_INVALID_ARG, "is_complex must be 0 or 1");
+  if (A->is_complex && misaligned(A->val)) return fail(MPK_INVALID_ARG, "complex values must be 16-byte aligned");
   return MPK_OK;
 }
 
@@ -807,6 +808,7 @@ extern "C" int mpk_krylov_solve(int method, int w, const mpk_csr* A, const mpk_i
   if (w < 1 || w > 4) return fail(MPK_INVALID_ARG, "w must be 1..4");
   if (b_dev == nullptr || x_dev == nullptr || opts == nullptr || b_dev == x_dev)
     return fail(MPK_INVALID_ARG, "null or aliased vector / options");
+  if (misaligned(b_dev) || misaligned(x_dev)) return fail(MPK_INVALID_ARG, "device vectors must be 16-byte aligned");
   if (opts->maxit < 0) return fail(MPK_INVALID_ARG, "maxit must be >= 0");
   if (M != nullptr && (M->n != A->n || M->cp != (A->is_complex ? 2 : 1)))
     return fail(MPK_INVALID_ARG, "preconditioner does not match the matrix");
@@ -832,6 +834,7 @@ extern "C" int mpk_krylov_solve_batched(int method, int w, const mpk_csr* A, int
   if (w < 1 || w > 4) return fail(MPK_INVALID_ARG, "w must be 1..4");
   if (b_dev == nullptr || x_dev == nullptr || opts == nullptr || b_dev == x_dev)
     return fail(MPK_INVALID_ARG, "null or aliased vector / options");
+  if (misaligned(b_dev) || misaligned(x_dev)) return fail(MPK_INVALID_ARG, "device vectors must be 16-byte aligned");
   if (sys_rows_host == nullptr || sys_rows_dev == nullptr) return fail(MPK_INVALID_ARG, "null system row offsets");
   if (sys_rows_host[0] != 0 || sys_rows_host[nsys] != A->n)
     return fail(MPK_INVALID_ARG, "system row offsets must start at 0 and end at n");

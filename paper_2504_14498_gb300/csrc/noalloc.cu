@@ -57,6 +57,8 @@ extern "C" int mpk_dot_noalloc(int n, int is_complex, int w, const double* a_dev
                                double* out_dev, void* stream) {
   if (n < 1 || a_dev == nullptr || b_dev == nullptr || out_dev == nullptr) return fail(MPK_INVALID_ARG, "bad argument");
   if (w < 1 || w > 4 || (is_complex != 0 && is_complex != 1)) return fail(MPK_INVALID_ARG, "bad w / is_complex");
+  if (misaligned(a_dev) || misaligned(b_dev) || misaligned(out_dev))
+    return fail(MPK_INVALID_ARG, "device vectors must be 16-byte aligned");
   if (n > kNoAllocMaxN)
     return fail(MPK_INVALID_ARG, "mpk_dot_noalloc: n = " + std::to_string(n) + " exceeds the fixed scratch limit of " +
                                      std::to_string(kNoAllocMaxN) + " entries (use mpk_dot)");

@@ -93,3 +93,36 @@ def test_binding_refuses_host_and_malformed_tensors():
         _lib.spmv_mp(FakeA(), torch.zeros(6, dtype=torch.float64), 2)
     with pytest.raises(ValueError, match="device memory"):
         _lib.dot(torch.zeros(6, dtype=torch.float64), torch.zeros(6, dtype=torch.float64), 3, 2)
+
+
+def test_misaligned_device_pointers_refused_before_any_launch(libmpk):
+    """Vectors (and complex matrix values) are accessed 16 bytes at a time, so every entry point
+    refuses a misaligned device pointer with MPK_INVALID_ARG (6) before it queues any work: the
+    fake addresses below are never dereferenced, here or on a GPU."""
+    from paper_2504_14498_gb300._lib import CsrDesc, Info, Opts
+
+    vp = ctypes.c_void_p
+    bad, good = vp(0x100008), vp(0x200000)
+    libmpk.mpk_last_error.restype = ctypes.c_char_p
+    A = CsrDesc(4, 0, good, good, good, 0)
+    Ac = CsrDesc(4, 0, good, good, bad, 1)  # complex values misaligned
+    opts = Opts(1e-10, 0.0, 10, 1, 0, 0, None, None)
+    info = Info()
+    calls = [
+        ("mpk_spmv_mp", lambda: libmpk.mpk_spmv_mp(ctypes.byref(A), 2, bad, good, None)),
+        ("mpk_spmv_mp y", lambda: libmpk.mpk_spmv_mp(ctypes.byref(A), 2, good, bad, None)),
+        ("mpk_spmv_mp complex val", lambda: libmpk.mpk_spmv_mp(ctypes.byref(Ac), 2, good, vp(0x300000), None)),
+        ("mpk_dot", lambda: libmpk.mpk_dot(8, 0, 2, good, bad, vp(0x300000), None)),
+        ("mpk_dot_noalloc", lambda: libmpk.mpk_dot_noalloc(8, 0, 2, bad, good, vp(0x300000), None)),
+        ("mpk_mp_op", lambda: libmpk.mpk_mp_op(0, 2, 4, good, good, bad, None)),
+        ("mpk_krylov_solve", lambda: libmpk.mpk_krylov_solve(2, 2, ctypes.byref(A), None, bad, good,
+                                                             ctypes.byref(opts), ctypes.byref(info), None)),
+        ("mpk_krylov_solve complex val", lambda: libmpk.mpk_krylov_solve(2, 2, ctypes.byref(Ac), None, good,
+                                                                         vp(0x300000), ctypes.byref(opts),
+                                                                         ctypes.byref(info), None)),
+        ("mpk_ilu0_factor complex val", lambda: libmpk.mpk_ilu0_factor(ctypes.byref(Ac), 1, ctypes.byref(vp()),
+                                                                       None, None)),
+    ]
+    for name, call in calls:
+        assert call() == 6, name
+        assert b"16-byte aligned" in libmpk.mpk_last_error(), name

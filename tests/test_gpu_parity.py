@@ -335,3 +335,18 @@ def test_solve_host_pinned_in_place():
     assert out["x"] is x0
     assert out["status"] == ref["status"] == "OK" and out["iters"] == ref["iters"]
     assert np.array_equal(x0, ref["x"])
+
+
+def test_misaligned_vectors_refused():
+    """A vector view that is not 16-byte aligned (offset by one binary64 word) is refused with
+    INVALID_ARG before any launch; the aligned call on the same data works."""
+    A_t = inputs.convdiff2d(8, pe=1.0)
+    n, w = A_t[0], 2
+    A = _lib.Matrix.from_tuple(A_t)
+    buf = torch.zeros(n * w + 2, dtype=torch.float64, device="cuda")
+    x = dev(inputs.ones(n, w))
+    with pytest.raises(_lib.MpkError) as e:
+        _lib.spmv_mp(A, x, w, buf[1:1 + n * w])
+    assert e.value.status == "INVALID_ARG"
+    y = _lib.spmv_mp(A, x, w, buf[2:2 + n * w])
+    assert np.array_equal(host(y), oracle.spmv(A_t, inputs.ones(n, w), w))
