@@ -829,6 +829,7 @@ def run_helmholtz(args):
                                     true_res_period=period)
             e1.record()
             torch.cuda.synchronize()
+            sched = list(M.schedule()) + [M.polling()]
             M.close()
             t = e0.elapsed_time(e1) / 1e3
             h, ht = out["hist"], out["hist_true"]
@@ -836,7 +837,8 @@ def run_helmholtz(args):
             rows["%s_%s" % (method, prec)] = {
                 "status": out["status"], "iters": out["iters"], "maxit": maxit, "s": t,
                 "ms_per_iter": 1e3 * t / max(1, out["iters"]), "relres_true": out["relres_true"],
-                "replacements": out["replacements"], "true_res_period": period, "checks_k_rec_true": checks}
+                "replacements": out["replacements"], "true_res_period": period, "substitution_schedule": sched,
+                "checks_k_rec_true": checks}
             print("%s %s: %s %d it %.1f s rr %.2e rep %d" % (method, prec, out["status"], out["iters"], t,
                                                             out["relres_true"], out["replacements"]),
                   file=sys.stderr, flush=True)

@@ -35,9 +35,10 @@
  * Environment variables (none changes a result; all choose how the same operations run):
  *   MPK_SUBST_SCHEDULE=static|owner|cluster8|cluster16  substitution schedule (mpk_ilu0_schedule);
  *                                                        read at every call; default: tuned.
- *   MPK_SUBST_POLL=lane0|all                             dependency polling of the substitutions
+ *   MPK_SUBST_POLL=lane0|all|allsleep                    dependency polling of the substitutions
  *                                                        (lane 0 polls a chunk's latest dependency
- *                                                        first, or every lane its own;
+ *                                                        first, or every lane its own, spinning
+ *                                                        or sleeping between rounds;
  *                                                        mpk_ilu0_polling); read at every call;
  *                                                        default: tuned.
  *   MPK_ILU_SCHEDULE=levels|dataflow                     ILU(0) schedule (mpk_ilu0_factor); read
@@ -268,8 +269,8 @@ int mpk_ilu0_schedule(const mpk_ilu* M, int* wpb_out);
 
 /* Dependency polling the substitutions last used or were tuned to (with the schedule, or forced by
  * MPK_SUBST_POLL): 0 = lane 0 polls each 32-row chunk's latest dependency, then every lane loads
- * its own; 1 = every lane polls its own from the start.  The results do not depend on it.  -2 for
- * a NULL handle. */
+ * its own; 1 = every lane polls its own from the start; 2 = as 1, sleeping a fixed short time
+ * between polling rounds.  The results do not depend on it.  -2 for a NULL handle. */
 int mpk_ilu0_polling(const mpk_ilu* M);
 
 /* Level structure of the factor's triangles (the substitutions of Algorithm 2 and the ILU(0)

@@ -248,8 +248,8 @@ class ILU0:
         return ("static", "owner", "cluster8", "cluster16")[sc], wpb.value
 
     def polling(self):
-        """Dependency polling of the substitutions: 'lane0' or 'all'."""
-        return ("lane0", "all")[lib().mpk_ilu0_polling(self.handle)]
+        """Dependency polling of the substitutions: 'lane0', 'all' or 'allsleep'."""
+        return ("lane0", "all", "allsleep")[lib().mpk_ilu0_polling(self.handle)]
 
     def levels(self, tri: int):
         """(number of levels, level of every row as a device int32 tensor) of L~ (tri 0) or U~

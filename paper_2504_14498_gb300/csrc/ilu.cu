@@ -1307,12 +1307,13 @@ struct TrsvTune {
 };
 static std::mutex g_trsv_mu;
 static std::vector<TrsvTune> g_trsv;
-// MPK_SUBST_POLL=lane0|all forces the dependency polling of the substitutions (-1: tuned).
+// MPK_SUBST_POLL=lane0|all|allsleep forces the dependency polling of the substitutions (-1: tuned).
 static int forced_poll() {
   const char* e = std::getenv("MPK_SUBST_POLL");
   if (e == nullptr) return -1;
   if (std::strcmp(e, "lane0") == 0) return 0;
   if (std::strcmp(e, "all") == 0) return 1;
+  if (std::strcmp(e, "allsleep") == 0) return 2;
   return -1;
 }
 static int forced_schedule() {
@@ -1324,6 +1325,9 @@ static int forced_schedule() {
   if (std::strcmp(e, "cluster16") == 0) return 3;
   return -1;
 }
+// applications of M^-1 timed per candidate (after one untimed): candidates within a few percent
+// of each other need more than two to be told apart
+constexpr int kTuneReps = 4;
 static bool cached_choice(const mpk_ilu* M, int w, int forced, int fpoll, int* wpb, int* sched, int* poll) {
   std::lock_guard<std::mutex> lk(g_trsv_mu);
   for (const TrsvTune& t : g_trsv)
@@ -1372,15 +1376,16 @@ int tune_substitution(mpk_ilu* M, const Ops* o, int w, double* r, double* z, cud
       if (sc >= 2 && wp > 8) continue;  // cluster CTAs: one per SM, 4 or 8 warps
       if (!o->trsv_fits(M->prec, wp, sc, M->lay[sc][0].nblocks)) continue;
       M->wpb = wp;
-      for (int pm = 0; pm < 2; ++pm) {
-        // polling: lane 0 on the latest dependency first, or every lane on its own (the static
-        // schedule only; measured: each wins on some workloads, by up to ~10 %)
-        if ((fpoll >= 0 && pm != fpoll) || (fpoll < 0 && pm == 1 && sc != 0)) continue;
+      for (int pm = 0; pm < 3; ++pm) {
+        // polling: lane 0 on the latest dependency first, or every lane on its own, spinning or
+        // sleeping between rounds (the static schedule only for 1 and 2; measured: each wins on
+        // some workloads)
+        if ((fpoll >= 0 && pm != fpoll) || (fpoll < 0 && pm >= 1 && sc != 0)) continue;
         M->poll = pm;
         int st = precond_apply(M, o, false, r, z, nullptr, nullptr, s);  // warm
         if (st != MPK_OK) continue;
         cudaEventRecord(e0, s);
-        for (int k = 0; k < 2; ++k) precond_apply(M, o, false, r, z, nullptr, nullptr, s);
+        for (int k = 0; k < kTuneReps; ++k) precond_apply(M, o, false, r, z, nullptr, nullptr, s);
         cudaEventRecord(e1, s);
         if (cudaEventSynchronize(e1) != cudaSuccess) break;
         float ms = 0.f;

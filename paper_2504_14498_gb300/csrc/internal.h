@@ -226,7 +226,8 @@ struct IluHandleView {
   int sched = 0;                     // see kScheds
   int withhold = -1;                 // testing aid: a row whose value is never published
   int poll = 0;                      // 0: lane 0 polls the chunk's latest dependency, then every lane
-                                     // loads its own; 1: every lane polls its own from the start
+                                     // loads its own; 1: every lane polls its own from the start;
+                                     // 2: as 1 with a short sleep between polling rounds
 };
 enum CtlIdx : int {
   CTL_EPOCH = 0,

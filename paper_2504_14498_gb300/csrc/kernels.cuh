@@ -1006,6 +1006,7 @@ __device__ __forceinline__ void level_rows(const LevelOrder lo, const int* __res
 // ctl[CTL_ERR] and all warps leave).
 constexpr int kTrsvWpbChoices[4] = {4, 8, 16, 32};  // candidate warps per block (per SM)
 constexpr long long kSpinCycles = 40000;            // ~20 us of polling without sleeping
+constexpr int kPollSleepNs = 256;  // polling mode 2: every lane polls its own, sleeping between rounds
 constexpr unsigned long long kSent = 0xFFFFFFFFFFFFFFFFull;
 
 __device__ __forceinline__ double ld_relaxed_f64(const double* p) {
@@ -1279,7 +1280,7 @@ __device__ __forceinline__ bool mp_finish(const SellTri& T, const IluHandleView&
       if (need != 0u && !timeout && wait_expired(t0, polls, M.ctl)) timeout = true;
       if (__any_sync(FULL, need != 0u)) {
         if (M.poll == 1) wait_pause(t0, 64);
-        else __nanosleep(64);
+        else __nanosleep(M.poll == 2 ? kPollSleepNs : 64);
       }
     }
     __syncwarp();
@@ -1406,7 +1407,7 @@ __global__ void __launch_bounds__(WPB * 32, 1)
     bool timeout = false;
     const long long t0 = clock64();
     int polls = 0;
-    if (lane == 0 && c.rep >= 0) {
+    if (lane == 0 && c.rep >= 0 && M.poll == 0) {  // lane 0 first on the latest dependency
       N<W, CP> r;
       while (!n_poll<W, CP>(out, c.rep, r)) {
         if (wait_expired(t0, polls, M.ctl)) { timeout = true; break; }
@@ -1434,7 +1435,10 @@ __global__ void __launch_bounds__(WPB * 32, 1)
           if (((need >> k) & 1u) && n_ready<W, CP>(v[k])) got |= 1u << k;
         need &= ~got;
         if (need != 0u && !timeout && wait_expired(t0, polls, M.ctl)) timeout = true;
-        if (__any_sync(FULL, need != 0u)) __nanosleep(64);
+        if (__any_sync(FULL, need != 0u)) {
+          if (M.poll == 1) wait_pause(t0, 64);
+          else __nanosleep(M.poll == 2 ? kPollSleepNs : 64);
+        }
       }
       timeout = __any_sync(FULL, timeout);
       if (!timeout && c.i >= 0) {
@@ -1761,7 +1765,7 @@ __device__ __forceinline__ bool lp_finish(const SellTri& T, const IluHandleView&
       if (need != 0u && !timeout && wait_expired(t0, polls, M.ctl)) timeout = true;
       if (__any_sync(FULL, need != 0u)) {
         if (M.poll == 1) wait_pause(t0, 64);
-        else __nanosleep(64);
+        else __nanosleep(M.poll == 2 ? kPollSleepNs : 64);
       }
     }
     __syncwarp();

@@ -109,14 +109,14 @@ def test_auto_tuner_picks_a_schedule(monkeypatch):
     print("tuned schedule at 32^3:", sched, wpb)
 
 
-@pytest.mark.parametrize("poll", ["lane0", "all"])
+@pytest.mark.parametrize("poll", ["lane0", "all", "allsleep"])
 @pytest.mark.parametrize("mat", ["convdiff3d", "helmholtz", "random_cplx"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_precond_both_polling_modes(monkeypatch, poll, mat, prec):
-    """The substitutions' two ways of waiting for dependencies (lane 0 on the chunk's latest one,
-    or every lane on its own) give the oracle's bits, M and M^H (the complex binary64 factor runs
-    the paired-warp kernel, real and imaginary parts on two sub-partitions), and the handle
-    reports the mode it ran."""
+    """The substitutions' ways of waiting for dependencies (lane 0 on the chunk's latest one, or
+    every lane on its own, spinning or sleeping between rounds) give the oracle's bits, M and M^H
+    (the complex binary64 factor runs the paired-warp kernel, real and imaginary parts on two
+    sub-partitions), and the handle reports the mode it ran."""
     monkeypatch.setenv("MPK_SUBST_SCHEDULE", "static")
     monkeypatch.setenv("MPK_SUBST_POLL", poll)
     A_t, c = MATS[mat]()
