@@ -1019,9 +1019,9 @@ __device__ __forceinline__ void st_relaxed_f64(double* p, double x) {
   if (v == kSent) v = 0x7FF8000000000000ull;  // never publish the sentinel
   asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
-// Double-word values as one 16-byte strong access where the vector is 16-byte aligned (one request
-// instead of two; each word is still checked on its own, so a value seen half-written is polled
-// again), else word by word.
+// Double-word (and quad-word) values as one (two) 16-byte strong accesses where the vector is
+// 16-byte aligned (half the requests; each word is still checked on its own, so a value seen
+// half-written is polled again), else word by word.
 __device__ __forceinline__ void ld_relaxed_f64x2(const double* p, double& a, double& b) {
   asm volatile("ld.relaxed.gpu.global.v2.f64 {%0, %1}, [%2];" : "=d"(a), "=d"(b) : "l"(p) : "memory");
 }
@@ -1035,10 +1035,14 @@ __device__ __forceinline__ bool aligned16(const void* p) { return (reinterpret_c
 template <int W, int CP>
 __device__ __forceinline__ void n_fetch(const double* __restrict__ v, int64_t i, N<W, CP>& z) {
   const double* p = v + i * (CP * W);
-  if constexpr (W == 2) {
+  if constexpr (W == 2 || W == 4) {  // (a TD value's 24-byte stride breaks the alignment)
     if (aligned16(v)) {
-      ld_relaxed_f64x2(p, z.re.c[0], z.re.c[1]);
-      if constexpr (CP == 2) ld_relaxed_f64x2(p + 2, z.im.c[0], z.im.c[1]);
+#pragma unroll
+      for (int k = 0; k < W; k += 2) ld_relaxed_f64x2(p + k, z.re.c[k], z.re.c[k + 1]);
+      if constexpr (CP == 2) {
+#pragma unroll
+        for (int k = 0; k < W; k += 2) ld_relaxed_f64x2(p + W + k, z.im.c[k], z.im.c[k + 1]);
+      }
       return;
     }
   }
@@ -1068,10 +1072,14 @@ __device__ __forceinline__ bool n_poll(const double* __restrict__ v, int64_t i, 
 template <int W, int CP>
 __device__ __forceinline__ void n_publish(double* __restrict__ v, int64_t i, const N<W, CP>& z) {
   double* p = v + i * (CP * W);
-  if constexpr (W == 2) {
+  if constexpr (W == 2 || W == 4) {
     if (aligned16(v)) {
-      st_relaxed_f64x2(p, z.re.c[0], z.re.c[1]);
-      if constexpr (CP == 2) st_relaxed_f64x2(p + 2, z.im.c[0], z.im.c[1]);
+#pragma unroll
+      for (int k = 0; k < W; k += 2) st_relaxed_f64x2(p + k, z.re.c[k], z.re.c[k + 1]);
+      if constexpr (CP == 2) {
+#pragma unroll
+        for (int k = 0; k < W; k += 2) st_relaxed_f64x2(p + W + k, z.im.c[k], z.im.c[k + 1]);
+      }
       return;
     }
   }
