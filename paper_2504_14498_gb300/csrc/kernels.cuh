@@ -1646,6 +1646,31 @@ __device__ __forceinline__ void st_relaxed_f32(float* p, float x) {
   if (v == kSent32) v = 0x7FC00000u;  // never publish the sentinel
   asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+// A complex binary32 value (real, imaginary) as one 8-byte strong access where it is 8-byte
+// aligned (the handle's own buffers always are); each half is still checked on its own.
+__device__ __forceinline__ bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
+__device__ __forceinline__ void ld_relaxed_f32x2(const float* p, float& a, float& b) {
+  unsigned x, y;
+  if (aligned8(p)) {
+    asm volatile("ld.relaxed.gpu.global.v2.b32 {%0, %1}, [%2];" : "=r"(x), "=r"(y) : "l"(p) : "memory");
+    a = __uint_as_float(x);
+    b = __uint_as_float(y);
+  } else {
+    a = ld_relaxed_f32(p);
+    b = ld_relaxed_f32(p + 1);
+  }
+}
+__device__ __forceinline__ void st_relaxed_f32x2(float* p, float a, float b) {
+  if (!aligned8(p)) {
+    st_relaxed_f32(p, a);
+    st_relaxed_f32(p + 1, b);
+    return;
+  }
+  unsigned x = __float_as_uint(a), y = __float_as_uint(b);
+  if (x == kSent32) x = 0x7FC00000u;  // never publish the sentinel
+  if (y == kSent32) y = 0x7FC00000u;
+  asm volatile("st.relaxed.gpu.global.v2.b32 [%0], {%1, %2};" ::"l"(p), "r"(x), "r"(y) : "memory");
+}
 static __global__ void __launch_bounds__(kBlock) k_fill_sent32(int64_t m, float* __restrict__ a,
                                                               const int* __restrict__ done) {
   if (is_done(done)) return;
@@ -1654,8 +1679,12 @@ static __global__ void __launch_bounds__(kBlock) k_fill_sent32(int64_t m, float*
 }
 template <int CP>
 __device__ __forceinline__ bool f_poll(const float* __restrict__ v, int j, float& xr, float& xi) {
-  xr = ld_relaxed_f32(v + (int64_t)j * CP);
-  xi = CP == 2 ? ld_relaxed_f32(v + (int64_t)j * CP + 1) : 0.0f;
+  if constexpr (CP == 2) {
+    ld_relaxed_f32x2(v + (int64_t)j * CP, xr, xi);
+  } else {
+    xr = ld_relaxed_f32(v + (int64_t)j);
+    xi = 0.0f;
+  }
   return __float_as_uint(xr) != kSent32 && (CP == 1 || __float_as_uint(xi) != kSent32);
 }
 
@@ -1760,8 +1789,8 @@ __device__ __forceinline__ bool lp_finish(const SellTri& T, const IluHandleView&
 #pragma unroll
       for (int k = 0; k < KG; ++k)
         if ((need >> k) & 1u) {
-          vr[k] = ld_relaxed_f32(mine + (int64_t)c.jj[k] * CP);
-          if constexpr (CP == 2) vi[k] = ld_relaxed_f32(mine + (int64_t)c.jj[k] * CP + 1);
+          if constexpr (CP == 2) ld_relaxed_f32x2(mine + (int64_t)c.jj[k] * CP, vr[k], vi[k]);
+          else vr[k] = ld_relaxed_f32(mine + (int64_t)c.jj[k]);
         }
       unsigned got = 0u;
 #pragma unroll
@@ -1803,8 +1832,8 @@ __device__ __forceinline__ bool lp_finish(const SellTri& T, const IluHandleView&
         ai = ni / den;
       }
     }
-    st_relaxed_f32(mine + (int64_t)c.i * CP, ar);
-    if constexpr (CP == 2) st_relaxed_f32(mine + (int64_t)c.i * CP + 1, ai);
+    if constexpr (CP == 2) st_relaxed_f32x2(mine + (int64_t)c.i * CP, ar, ai);
+    else st_relaxed_f32(mine + (int64_t)c.i, ar);
     if constexpr (RING) {
       float* ring = (float*)R.base;
       ring[own_slot * CP] = ar;
