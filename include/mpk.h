@@ -41,6 +41,8 @@
  *                                                        or sleeping between rounds;
  *                                                        mpk_ilu0_polling); read at every call;
  *                                                        default: tuned.
+ *   MPK_SUBST_POLL_SLEEP_NS=16..4096                     the sleep of the sleeping polling mode;
+ *                                                        read at every call; default 256.
  *   MPK_ILU_SCHEDULE=levels|dataflow                     ILU(0) schedule (mpk_ilu0_factor); read
  *                                                        at every factorisation; default: by the
  *                                                        width of the levels.

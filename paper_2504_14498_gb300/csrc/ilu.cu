@@ -1316,6 +1316,13 @@ static int forced_poll() {
   if (std::strcmp(e, "allsleep") == 0) return 2;
   return -1;
 }
+// MPK_SUBST_POLL_SLEEP_NS=16..4096: the sleep between polling rounds of polling mode 2 (256 ns).
+static int poll_sleep_ns() {
+  const char* e = std::getenv("MPK_SUBST_POLL_SLEEP_NS");
+  if (e == nullptr) return 256;
+  const int v = std::atoi(e);
+  return v < 16 ? 16 : (v > 4096 ? 4096 : v);
+}
 static int forced_schedule() {
   const char* e = std::getenv("MPK_SUBST_SCHEDULE");
   if (e == nullptr) return -1;
@@ -1473,6 +1480,7 @@ IluHandleView mpk_ilu::view(bool trans) const {
   v.sched = sched;
   v.withhold = withhold;
   v.poll = poll;
+  v.poll_ns = poll_sleep_ns();
   return v;
 }
 

@@ -228,6 +228,7 @@ struct IluHandleView {
   int poll = 0;                      // 0: lane 0 polls the chunk's latest dependency, then every lane
                                      // loads its own; 1: every lane polls its own from the start;
                                      // 2: as 1 with a short sleep between polling rounds
+  int poll_ns = 256;                 // that sleep (MPK_SUBST_POLL_SLEEP_NS, default 256 ns)
 };
 enum CtlIdx : int {
   CTL_EPOCH = 0,

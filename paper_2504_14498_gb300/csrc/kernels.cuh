@@ -1006,7 +1006,6 @@ __device__ __forceinline__ void level_rows(const LevelOrder lo, const int* __res
 // ctl[CTL_ERR] and all warps leave).
 constexpr int kTrsvWpbChoices[4] = {4, 8, 16, 32};  // candidate warps per block (per SM)
 constexpr long long kSpinCycles = 40000;            // ~20 us of polling without sleeping
-constexpr int kPollSleepNs = 256;  // polling mode 2: every lane polls its own, sleeping between rounds
 constexpr unsigned long long kSent = 0xFFFFFFFFFFFFFFFFull;
 
 __device__ __forceinline__ double ld_relaxed_f64(const double* p) {
@@ -1288,7 +1287,7 @@ __device__ __forceinline__ bool mp_finish(const SellTri& T, const IluHandleView&
       if (need != 0u && !timeout && wait_expired(t0, polls, M.ctl)) timeout = true;
       if (__any_sync(FULL, need != 0u)) {
         if (M.poll == 1) wait_pause(t0, 64);
-        else __nanosleep(M.poll == 2 ? kPollSleepNs : 64);
+        else __nanosleep(M.poll == 2 ? (unsigned)M.poll_ns : 64u);
       }
     }
     __syncwarp();
@@ -1445,7 +1444,7 @@ __global__ void __launch_bounds__(WPB * 32, 1)
         if (need != 0u && !timeout && wait_expired(t0, polls, M.ctl)) timeout = true;
         if (__any_sync(FULL, need != 0u)) {
           if (M.poll == 1) wait_pause(t0, 64);
-          else __nanosleep(M.poll == 2 ? kPollSleepNs : 64);
+          else __nanosleep(M.poll == 2 ? (unsigned)M.poll_ns : 64u);
         }
       }
       timeout = __any_sync(FULL, timeout);
@@ -1802,7 +1801,7 @@ __device__ __forceinline__ bool lp_finish(const SellTri& T, const IluHandleView&
       if (need != 0u && !timeout && wait_expired(t0, polls, M.ctl)) timeout = true;
       if (__any_sync(FULL, need != 0u)) {
         if (M.poll == 1) wait_pause(t0, 64);
-        else __nanosleep(M.poll == 2 ? kPollSleepNs : 64);
+        else __nanosleep(M.poll == 2 ? (unsigned)M.poll_ns : 64u);
       }
     }
     __syncwarp();
