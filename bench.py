@@ -494,7 +494,9 @@ def run_mpk(args):
     # algorithmic binary64 operations (add, mul or fma) of the double-word algorithms as run:
     # DW*FP 6 + DW+DW 14 (TwoSum as FastTwoSum on exponent-ordered operands) = 20 per multiply-add;
     # DW/FP 10 (two divisions counted as one operation each)
-    spmv_ops = 20 * nnz
+    # DD: 6 (product) + 14 (DW+DW addition) binary64 operations per entry, less the addition of
+    # each row's first product, which the kernel does not execute (every row here has entries)
+    spmv_ops = 20 * nnz - 14 * n
     spmv1_bytes = 12 * nnz + 4 * (n + 1) + 2 * 8 * n
     spmv1_ops = nnz  # real D: one fused multiply-add per entry
     spmv4_bytes = 12 * nnz + 4 * (n + 1) + 2 * 32 * n
